@@ -1,0 +1,644 @@
+"""Oracle (TEST INFRASTRUCTURE ONLY): finite-T orbital-free DFT in plain FP64.
+
+Written from arXiv:1406.0835 (Karasiev, Sjostrom, Trickey), section by
+section; each function names the equation it follows.  Only tests/,
+``__graft_entry__.smoke()`` and bench.py's CPU-baseline legs may use it.
+It shares no code with the CUDA library and imports nothing from it.
+
+Discretisation (a reading; the paper works in the continuum): integrals are
+dV * sum over a periodic orthorhombic grid; n(G) = fftn(n)/N over the full FFT
+box with integer wave numbers k in {-n/2+1, ..., n/2}.  Even-order operators
+(G^2, Hartree, local pseudopotential) use k = +n/2 on a Nyquist plane and the
+real part of the inverse transform; first derivatives i G_a are zeroed on the
+a-Nyquist plane, so gradient and divergence are exact adjoints and the
+potential is the exact derivative of the discrete free energy.
+
+Units: Hartree atomic units; temperatures at the interface in kelvin.
+"""
+import ctypes
+import math
+
+import numpy as np
+
+from . import build as _build
+
+# ---------------------------------------------------------------- constants
+KB_HA_PER_K = 3.166811563e-6          # Boltzmann constant, hartree / kelvin
+C_TF = 0.3 * (3.0 * math.pi ** 2) ** (2.0 / 3.0)   # Eq. (tauTFdefn)
+AMU_ME = 1822.888486209               # atomic mass unit / electron mass
+FS_AU = 41.341373335                  # femtosecond in atomic time units
+
+# ------------------------------------------------------- Fermi-Dirac (C part)
+_lib = None
+_P = ctypes.POINTER(ctypes.c_double)
+
+
+def _c():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_build.build())
+        for name in ("oracle_fd_moments", "oracle_eta_of_t", "oracle_kappa_h"):
+            getattr(_lib, name).argtypes = [ctypes.c_long, _P, _P]
+            getattr(_lib, name).restype = ctypes.c_int
+    return _lib
+
+
+def fd_moments(eta):
+    """I_{-1/2}, I_{1/2}, I_{3/2}, I'_{-1/2}, I''_{-1/2}, I'''_{-1/2} at eta."""
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    out = np.empty(eta.shape + (6,))
+    _c().oracle_fd_moments(eta.size, eta.ctypes.data_as(_P), out.ctypes.data_as(_P))
+    return out
+
+
+def eta_of_t(t):
+    """eta solving I_{1/2}(eta) = (2/3) t^{-3/2} (Eq. (tred) with n of the ideal gas)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    out = np.empty(t.shape)
+    _c().oracle_eta_of_t(t.size, t.ctypes.data_as(_P), out.ctypes.data_as(_P))
+    return out
+
+
+def kappa_h(t):
+    """Per t: eta, kappa, kappa', kappa'', h~, h~', h~'' (footnote a of Table I).
+
+    Returned as a tuple of arrays shaped like t.
+    """
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    out = np.empty(t.shape + (7,))
+    _c().oracle_kappa_h(t.size, t.ctypes.data_as(_P), out.ctypes.data_as(_P))
+    return tuple(out[..., k] for k in range(7))
+
+
+def xi_zeta(t):
+    """xi = kappa - t kappa', zeta = -t kappa' (Eq. (xizeta)) and t-derivatives."""
+    _, kap, dk, d2k, h, dh, d2h = kappa_h(t)
+    xi = kap - t * dk
+    zeta = -t * dk
+    dxi = -t * d2k
+    dzeta = -dk - t * d2k
+    return dict(kappa=kap, dkappa=dk, xi=xi, zeta=zeta, dxi=dxi, dzeta=dzeta,
+                h=h, dh=dh, d2h=d2h)
+
+
+# ------------------------------------------------------------- grid & cell
+class Grid:
+    """Periodic orthorhombic grid, C order [ix][iy][iz] with iz fastest."""
+
+    def __init__(self, L, shape):
+        self.L = np.asarray(L, dtype=np.float64).reshape(3)
+        self.shape = tuple(int(s) for s in shape)
+        self.N = int(np.prod(self.shape))
+        self.omega = float(np.prod(self.L))
+        self.dV = self.omega / self.N
+        kint = []
+        for n in self.shape:
+            k = np.fft.fftfreq(n, 1.0 / n)
+            if n % 2 == 0:
+                k[n // 2] = n // 2          # Nyquist taken as +n/2
+            kint.append(k)
+        self.kint = kint
+        g1 = [2.0 * math.pi * kint[a] / self.L[a] for a in range(3)]
+        self.Gx = g1[0][:, None, None]
+        self.Gy = g1[1][None, :, None]
+        self.Gz = g1[2][None, None, :]
+        self.G2 = self.Gx ** 2 + self.Gy ** 2 + self.Gz ** 2
+        # first-derivative multipliers with the a-Nyquist plane zeroed
+        gd = []
+        for a in range(3):
+            g = g1[a].copy()
+            n = self.shape[a]
+            if n % 2 == 0:
+                g[n // 2] = 0.0
+            gd.append(g)
+        self.Dx = gd[0][:, None, None]
+        self.Dy = gd[1][None, :, None]
+        self.Dz = gd[2][None, None, :]
+
+    def to_G(self, f):
+        """n(G) = (1/N) sum_j f_j exp(-i G.r_j)."""
+        return np.fft.fftn(f) / self.N
+
+    def to_r(self, fG):
+        """Real part of sum_G f(G) exp(i G.r_j)."""
+        return np.real(np.fft.ifftn(fG)) * self.N
+
+    def grad(self, f):
+        fG = self.to_G(f)
+        return np.stack([self.to_r(1j * D * fG) for D in (self.Dx, self.Dy, self.Dz)])
+
+    def div(self, W):
+        acc = 1j * self.Dx * self.to_G(W[0])
+        acc = acc + 1j * self.Dy * self.to_G(W[1])
+        acc = acc + 1j * self.Dz * self.to_G(W[2])
+        return self.to_r(acc)
+
+    def integrate(self, f):
+        return self.dV * float(np.sum(f))
+
+
+# --------------------------------------------- enhancement factors (Sec. III B)
+def F_sga(mu):
+    """Eq. (SGA-F): F_tau = 1 + mu x with x = s_tau^2 (mu = 5/27 SGA, 5/3 VWTF)."""
+    def F(x):
+        return 1.0 + mu * x, np.full_like(x, mu)
+    return F
+
+
+def F_kst2(C1, a1):
+    """Eq. (KST2F): F_tau = 1 + C1 x / (1 + a1 x)."""
+    def F(x):
+        den = 1.0 + a1 * x
+        return 1.0 + C1 * x / den, C1 / den ** 2
+    return F
+
+
+def F_vt84f(x, mu=2.778, alpha=1.2965):
+    """Eq. (VT84F) with m = 8, n = 4 written in x = s^2 (s^{m/2} = x^2, s^{-n/2} = 1/x).
+
+    F = 1 - mu x e^{-alpha x}/(1 + mu x) + (1 - e^{-alpha x^2})(1/x - 1) + (5/3) x.
+    Reading: the removable 0/0 at x = 0 takes its limit F = 1,
+    dF/dx = -mu + alpha + 5/3.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    xs = np.where(x > 0.0, x, 1.0)
+    e1 = np.exp(-alpha * xs)
+    em = -np.expm1(-alpha * xs * xs)                 # 1 - exp(-alpha x^2)
+    den = 1.0 + mu * xs
+    F = 1.0 - mu * xs * e1 / den + em * (1.0 / xs - 1.0) + (5.0 / 3.0) * xs
+    dF = (-mu * e1 * (1.0 - alpha * xs - alpha * mu * xs * xs) / den ** 2
+          + 2.0 * alpha * (1.0 - em) * (1.0 - xs) - em / (xs * xs) + 5.0 / 3.0)
+    F = np.where(x > 0.0, F, 1.0)
+    dF = np.where(x > 0.0, dF, -mu + alpha + 5.0 / 3.0)
+    return F, dF
+
+
+FUNCTIONALS = {
+    "fttf": None,
+    "sga": F_sga(5.0 / 27.0),
+    "vwtf": F_sga(5.0 / 3.0),
+    "vt84f": F_vt84f,
+    "kst2": F_kst2(2.03087, 0.29424),
+    "tw": F_kst2(0.2319, 0.2748),
+    "apbef": F_kst2(0.23889, 0.23889 / 0.804),
+}
+
+
+# ------------------------------------------- non-interacting free energy
+def reduced_t(n, T):
+    """Eq. (tred): t = 2 T / (3 pi^2 n)^{2/3}."""
+    return 2.0 * T / (3.0 * math.pi ** 2 * n) ** (2.0 / 3.0)
+
+
+def fs_fttf(n, T):
+    """Finite-T Thomas-Fermi: f = tau0 kappa (Eq. (fTF)), v by Eq. (vTF).
+
+    Returns dict with f, dfdn, f_kin = tau0 xi (internal), f_ent = tau0 zeta (T s).
+    """
+    tau0 = C_TF * n ** (5.0 / 3.0)
+    dtau0 = (5.0 / 3.0) * C_TF * n ** (2.0 / 3.0)
+    t = reduced_t(n, T)
+    dtdn = -2.0 * t / (3.0 * n)
+    z = xi_zeta(t)
+    f = tau0 * z["kappa"]
+    v = dtau0 * z["kappa"] + tau0 * z["dkappa"] * dtdn
+    return dict(f=f, dfdn=v, f_kin=tau0 * z["xi"], f_ent=tau0 * z["zeta"],
+                W=None)
+
+
+def fs_gga(n, gradn, T, Fenh):
+    """Generic finite-T GGA, Eqs. (FGGA), (xizeta), (s_s), (s_0defn), (vftGGA).
+
+    f = tau0 xi F_tau(s_tau^2) - tau0 zeta F_sigma(s_sigma^2), F_sigma = 2 - F_tau.
+    The sigma terms of Eq. (vftGGA) are all taken with a minus sign (the exact
+    derivative of Eq. (FGGA)); W = df/d(grad n) is the argument of the
+    divergence in its last line.
+    """
+    tau0 = C_TF * n ** (5.0 / 3.0)
+    dtau0 = (5.0 / 3.0) * C_TF * n ** (2.0 / 3.0)
+    t = reduced_t(n, T)
+    dtdn = -2.0 * t / (3.0 * n)
+    z = xi_zeta(t)
+    xi, zeta, dxi, dzeta = z["xi"], z["zeta"], z["dxi"], z["dzeta"]
+    h, dh, d2h = z["h"], z["dh"], z["d2h"]
+    g2 = np.sum(gradn * gradn, axis=0)
+    cs = 1.0 / (4.0 * (3.0 * math.pi ** 2) ** (2.0 / 3.0) * n ** (8.0 / 3.0))
+    s2 = g2 * cs                                   # Eq. (s_0defn) squared
+    A = (h - t * dh) / xi                          # s_tau^2 = s^2 A (Eq. (s_s))
+    B = t * dh / zeta                              # s_sigma^2 = s^2 B
+    dA = -t * d2h / xi - (h - t * dh) * dxi / xi ** 2
+    dB = (dh + t * d2h) / zeta - t * dh * dzeta / zeta ** 2
+    x_t = s2 * A
+    x_s = s2 * B
+    Ft, dFt = Fenh(x_t)
+    Fs_tau, dFs_tau = Fenh(x_s)
+    Fs, dFs = 2.0 - Fs_tau, -dFs_tau               # F_sigma = 2 - F_tau(s_sigma)
+    f_kin = tau0 * xi * Ft
+    f_ent = tau0 * zeta * Fs
+    f = f_kin - f_ent
+    dxt_dn = -(8.0 / 3.0) * x_t / n
+    dxs_dn = -(8.0 / 3.0) * x_s / n
+    dxt_dt = s2 * dA
+    dxs_dt = s2 * dB
+    dfdn = (dtau0 * xi * Ft + tau0 * dxi * dtdn * Ft
+            + tau0 * xi * dFt * (dxt_dn + dxt_dt * dtdn)
+            - dtau0 * zeta * Fs - tau0 * dzeta * dtdn * Fs
+            - tau0 * zeta * dFs * (dxs_dn + dxs_dt * dtdn))
+    coef = (tau0 * xi * dFt * A - tau0 * zeta * dFs * B) * 2.0 * cs
+    W = coef[None] * gradn
+    return dict(f=f, dfdn=dfdn, f_kin=f_kin, f_ent=f_ent, W=W)
+
+
+# ------------------------------------------------------------- XC (Sec. IV)
+PZ = dict(gamma=-0.1423, beta1=1.0529, beta2=0.3334,
+          A=0.0311, B=-0.048, C=0.0020, D=-0.0116)
+EX_COEF = 0.75 * (3.0 / math.pi) ** (1.0 / 3.0)   # eps_x = -EX_COEF n^{1/3}
+
+
+def pz81(n):
+    """Perdew-Zunger 1981 unpolarised LDA (cited in Sec. IV, used for all timings).
+
+    eps_xc = eps_x + eps_c(r_s); v_xc = eps_xc + n d eps_xc/dn with
+    dr_s/dn = -r_s/(3n) (Eq. (vxc1) at T = 0).  Reading: r_s >= 1 takes the
+    Pade branch.  Returns eps_xc, v_xc.
+    """
+    rs = (3.0 / (4.0 * math.pi * n)) ** (1.0 / 3.0)
+    ex = -EX_COEF * n ** (1.0 / 3.0)
+    dex = -ex / rs                                  # d eps_x / d r_s (eps_x ~ 1/r_s)
+    hi = rs >= 1.0
+    r = np.where(hi, rs, 1.0)
+    sq = np.sqrt(r)
+    den = 1.0 + PZ["beta1"] * sq + PZ["beta2"] * r
+    ec_hi = PZ["gamma"] / den
+    dec_hi = -PZ["gamma"] * (PZ["beta1"] / (2.0 * sq) + PZ["beta2"]) / den ** 2
+    rl = np.where(hi, 0.5, rs)
+    lr = np.log(rl)
+    ec_lo = PZ["A"] * lr + PZ["B"] + PZ["C"] * rl * lr + PZ["D"] * rl
+    dec_lo = PZ["A"] / rl + PZ["C"] * (lr + 1.0) + PZ["D"]
+    ec = np.where(hi, ec_hi, ec_lo)
+    dec = np.where(hi, dec_hi, dec_lo)
+    eps = ex + ec
+    v = eps - rs / 3.0 * (dex + dec)
+    return eps, v
+
+
+# -------------------------------------------- local pseudopotential (Sec. V A)
+def lpp_form(G2, omega, rc):
+    """Gaussian-ion local pseudopotential per unit charge:
+    w(G) = -4 pi exp(-G^2 rc^2 / 4) / (Omega G^2), G = 0 dropped
+    (the Fourier transform of -erf(r/rc)/r)."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        w = -4.0 * math.pi * np.exp(-G2 * rc * rc / 4.0) / (omega * G2)
+    w[G2 == 0.0] = 0.0
+    return w
+
+
+def structure_phase(grid, R):
+    """exp(-i G.R) on the full box (separable in x, y, z), + Nyquist convention."""
+    return (np.exp(-1j * grid.Gx * R[0]) * np.exp(-1j * grid.Gy * R[1])
+            * np.exp(-1j * grid.Gz * R[2]))
+
+
+def lpp_vG(grid, R, Z, rc):
+    """v_ext(G) = sum_I Z_I w(G) exp(-i G.R_I) on the full box."""
+    w = lpp_form(grid.G2, grid.omega, rc)
+    vG = np.zeros(grid.shape, dtype=np.complex128)
+    for I in range(len(Z)):
+        vG += Z[I] * w * structure_phase(grid, R[I])
+    return vG
+
+
+# ------------------------------------------------------------------ Ewald
+def ewald(L, R, Z, alpha=None):
+    """Ion-ion energy E_ion of Eq. (E1) by the textbook Ewald sum.
+
+    E = 1/2 sum'_{I,J,L} Z_I Z_J erfc(a r)/r + (2 pi/Omega) sum_{G!=0}
+        exp(-G^2/4a^2)/G^2 |S(G)|^2 - a/sqrt(pi) sum Z^2 - pi (sum Z)^2/(2 Omega a^2).
+    Returns (E, forces [nat,3]).  Pressure is E/(3 Omega) (Coulomb scaling).
+    """
+    from scipy.special import erfc
+    L = np.asarray(L, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64).reshape(-1, 3)
+    Z = np.asarray(Z, dtype=np.float64)
+    nat = len(Z)
+    omega = float(np.prod(L))
+    if alpha is None:
+        alpha = math.sqrt(math.pi) * (nat / omega ** 2) ** (1.0 / 6.0)
+    rcut = 6.5 / alpha
+    gcut = 2.0 * alpha * 6.5
+    # real space
+    E = 0.0
+    F = np.zeros((nat, 3))
+    nimg = [int(math.ceil(rcut / L[a])) + 1 for a in range(3)]
+    shifts = np.array([(i, j, k) for i in range(-nimg[0], nimg[0] + 1)
+                       for j in range(-nimg[1], nimg[1] + 1)
+                       for k in range(-nimg[2], nimg[2] + 1)], dtype=np.float64) * L
+    for I in range(nat):
+        d = R[I][None, None, :] - R[None, :, :] - shifts[:, None, :]   # [img, J, 3]
+        r = np.sqrt(np.sum(d * d, axis=2))
+        mask = (r > 1e-12) & (r < rcut)
+        rr = np.where(mask, r, 1.0)
+        zz = Z[I] * Z[None, :]
+        e = np.where(mask, zz * erfc(alpha * rr) / rr, 0.0)
+        E += 0.5 * float(np.sum(e))
+        fmag = np.where(mask, zz * (erfc(alpha * rr) / rr ** 2
+                                    + 2.0 * alpha / math.sqrt(math.pi)
+                                    * np.exp(-(alpha * rr) ** 2) / rr), 0.0)
+        F[I] += np.sum(fmag[:, :, None] * d / rr[:, :, None], axis=(0, 1))
+    # reciprocal space
+    km = [int(math.ceil(gcut * L[a] / (2.0 * math.pi))) for a in range(3)]
+    kx = np.arange(-km[0], km[0] + 1)
+    ky = np.arange(-km[1], km[1] + 1)
+    kz = np.arange(-km[2], km[2] + 1)
+    K = np.array(np.meshgrid(kx, ky, kz, indexing="ij")).reshape(3, -1).T
+    G = 2.0 * math.pi * K / L
+    G2 = np.sum(G * G, axis=1)
+    sel = (G2 > 0) & (G2 < gcut * gcut)
+    G = G[sel]
+    G2 = G2[sel]
+    wG = np.exp(-G2 / (4.0 * alpha * alpha)) / G2
+    ph = np.exp(1j * (G @ R.T))                    # [nG, nat] = exp(i G.R_I)
+    S = ph @ Z
+    E += (2.0 * math.pi / omega) * float(np.sum(wG * np.abs(S) ** 2))
+    F += (4.0 * math.pi / omega) * Z[:, None] * (
+        (wG[:, None] * np.imag(np.conj(S)[:, None] * ph)).T @ G)
+    E -= alpha / math.sqrt(math.pi) * float(np.sum(Z * Z))
+    E -= math.pi * float(np.sum(Z)) ** 2 / (2.0 * omega * alpha * alpha)
+    return E, F
+
+
+# -------------------------------------------------------------- the system
+class System:
+    """Cell, ions, grid, temperature and functional choice (Sec. II, V C).
+
+    ions: Cartesian bohr [nat,3]; Z: valence charges; T_kelvin (keyword TEMP).
+    """
+
+    def __init__(self, L, shape, ions, Z, T_kelvin, functional="fttf",
+                 rc=0.25, xc=True):
+        self.grid = Grid(L, shape)
+        self.R = np.array(ions, dtype=np.float64).reshape(-1, 3)
+        self.Z = np.array(Z, dtype=np.float64).reshape(-1)
+        self.T = float(T_kelvin) * KB_HA_PER_K
+        self.functional = functional
+        self.rc = float(rc)
+        self.xc = xc
+        self.Ne = float(np.sum(self.Z))
+        self.set_positions(self.R)
+
+    def set_positions(self, R):
+        self.R = np.array(R, dtype=np.float64).reshape(-1, 3)
+        self.vG = lpp_vG(self.grid, self.R, self.Z, self.rc)
+        self.v_ext = self.grid.to_r(self.vG)
+        self.E_ion, self.F_ion = ewald(self.grid.L, self.R, self.Z)
+
+    def uniform_phi(self):
+        return np.full(self.grid.shape, math.sqrt(self.Ne / self.grid.omega))
+
+
+def evaluate(sys, phi):
+    """Free energy F_tot[n] (Eq. (E1) with the constraint term left out) and
+    its functional derivative v = dF/dn at n = phi^2, plus the pressure terms.
+
+    F_tot = F_s + F_H + F_xc + int n v_ext + E_ion  (Eqs. (E1)-(E4), (E2)).
+    """
+    g = sys.grid
+    n = phi * phi
+    nG = g.to_G(n)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kH = 4.0 * math.pi / g.G2
+    kH[g.G2 == 0.0] = 0.0
+    vHG = kH * nG
+    vH = g.to_r(vHG)
+    E_H = 0.5 * g.integrate(n * vH)                                  # Eq. (E2)
+    E_loc = g.integrate(n * sys.v_ext)
+    fun = FUNCTIONALS[sys.functional]
+    if fun is None:
+        fs = fs_fttf(n, sys.T)
+        gradn = None
+        v_s = fs["dfdn"]
+        WdotG = 0.0
+    else:
+        gradn = g.grad(n)
+        fs = fs_gga(n, gradn, sys.T, fun)
+        v_s = fs["dfdn"] - g.div(fs["W"])                            # Eq. (vftGGA)
+        WdotG = g.integrate(np.sum(fs["W"] * gradn, axis=0))
+    F_s = g.integrate(fs["f"])
+    TS = g.integrate(fs["f_ent"])
+    if sys.xc:
+        eps, vxc = pz81(n)
+        F_xc = g.integrate(n * eps)
+        P_xc = g.integrate(n * (vxc - eps)) / g.omega               # Eq. (stressLSDAxc)
+    else:
+        eps = vxc = np.zeros_like(n)
+        F_xc = 0.0
+        P_xc = 0.0
+    v = v_s + vH + sys.v_ext + vxc
+    F_el = F_s + E_H + E_loc + F_xc
+    F_tot = F_el + sys.E_ion
+    # pressure: P = -(1/3) Tr Sigma (Eq. (pressure)), term by term
+    P_s = (g.integrate(n * v_s - fs["f"]) + WdotG / 3.0) / g.omega  # Eqs. (stressTF_a,b)
+    P_H = E_H / (3.0 * g.omega)
+    P_loc = (1.0 / 3.0) * float(np.real(np.sum(
+        np.conj(nG) * sys.vG * (1.0 - g.G2 * sys.rc ** 2 / 2.0))))
+    P_ion = sys.E_ion / (3.0 * g.omega)
+    E_alphaZ = sys.Ne * float(np.sum(math.pi * sys.Z * sys.rc ** 2)) / g.omega
+    return dict(F_tot=F_tot, F_el=F_el, F_s=F_s, minus_TS=-TS, E_H=E_H,
+                E_loc=E_loc, F_xc=F_xc, E_ion=sys.E_ion, E_int=F_tot + TS,
+                v=v, v_s=v_s, n=n, nG=nG, gradn=gradn,
+                P=P_s + P_xc + P_H + P_loc + P_ion, P_s=P_s, P_xc=P_xc,
+                P_H=P_H, P_loc=P_loc, P_ion=P_ion, E_alphaZ=E_alphaZ)
+
+
+# ---------------------------------------------------- minimisation (Sec. II)
+def _mu_grad(sys, phi, v):
+    """mu = int phi^2 v / int phi^2, g = 2 phi (v - mu), ||g|| = (dV sum g^2)^{1/2}."""
+    mu = float(np.sum(phi * phi * v) / np.sum(phi * phi))
+    gr = 2.0 * phi * (v - mu)
+    return mu, gr, math.sqrt(sys.grid.dV * float(np.sum(gr * gr)))
+
+
+def minimize(sys, phi0=None, gtol=1e-8, maxit=2000, theta0=0.05, ls_tol=0.1,
+             max_ls=20, callback=None):
+    """Direct minimisation of F_tot[n = phi^2] under int n = N_e (Sec. II).
+
+    Nonlinear conjugate gradients; the paper names CG without details, so the
+    scheme is a reading: Polak-Ribiere+ direction projected orthogonal to phi,
+    restart along -g when not a descent direction, norm-preserving rotation
+    phi(theta) = phi cos(theta) + dhat sin(theta) with ||dhat|| = ||phi||, and
+    a line search on dE/dtheta (secant, regula falsi once bracketed) until
+    |dE/dtheta| <= ls_tol |dE/dtheta(0)|.  Stops when ||g|| < gtol.
+    Returns (phi, evaluation dict, stats dict).
+    """
+    g = sys.grid
+    phi = (sys.uniform_phi() if phi0 is None else np.array(phi0, dtype=np.float64))
+    phi *= math.sqrt(sys.Ne / g.integrate(phi * phi))     # dV sum phi^2 = N_e
+    ev = evaluate(sys, phi)
+    nevals = 1
+    mu, gr, gnorm = _mu_grad(sys, phi, ev["v"])
+    d_prev = gr_prev = None
+    theta_prev = theta0
+    it = 0
+    status = "maxit"
+    while it < maxit:
+        if gnorm < gtol:
+            status = "converged"
+            break
+        if gr_prev is None:
+            d = -gr
+        else:
+            beta = max(0.0, float(np.sum(gr * (gr - gr_prev)) / np.sum(gr_prev * gr_prev)))
+            d = -gr + beta * d_prev
+        pp = float(np.sum(phi * phi))
+        d = d - phi * (float(np.sum(phi * d)) / pp)
+        if float(np.sum(d * gr)) >= 0.0:
+            d = -gr
+        dhat = d * math.sqrt(pp / float(np.sum(d * d)))
+        D0 = g.dV * float(np.sum(2.0 * phi * ev["v"] * dhat))
+        th, ev_new, phi_new, nls = _line_search(sys, phi, dhat, D0, theta_prev,
+                                                ls_tol, max_ls)
+        nevals += nls
+        if th is None:
+            if gr_prev is None:
+                status = "linesearch"
+                break
+            d_prev = gr_prev = None          # restart along steepest descent
+            continue
+        theta_prev = th
+        phi, ev = phi_new, ev_new
+        gr_prev, d_prev = gr, d
+        mu, gr, gnorm = _mu_grad(sys, phi, ev["v"])
+        it += 1
+        if callback is not None:
+            callback(it, ev, gnorm)
+    return phi, ev, dict(iterations=it, evaluations=nevals, gnorm=gnorm,
+                         mu=mu, status=status)
+
+
+def _line_search(sys, phi, dhat, D0, theta1, ls_tol, max_ls):
+    """Derivative line search in theta (reading of the CG step, Sec. II)."""
+    g = sys.grid
+    lo, Dlo = 0.0, D0
+    hi = Dhi = None
+    pa, Da = 0.0, D0            # last two points for the unbracketed secant
+    th = theta1
+    for k in range(max_ls):
+        c, s = math.cos(th), math.sin(th)
+        p = phi * c + dhat * s
+        ev = evaluate(sys, p)
+        D = g.dV * float(np.sum(2.0 * p * ev["v"] * (-phi * s + dhat * c)))
+        if abs(D) <= ls_tol * abs(D0):
+            return th, ev, p, k + 1
+        if D < 0.0:
+            lo, Dlo = th, D
+        else:
+            hi, Dhi = th, D
+        if hi is None:
+            nxt = 4.0 * th
+            if D > Da:
+                sec = th - D * (th - pa) / (D - Da)
+                nxt = min(sec, 4.0 * th)
+            nxt = max(nxt, 1.1 * th)
+            pa, Da = th, D
+        else:
+            nxt = lo - Dlo * (hi - lo) / (Dhi - Dlo)
+            w = hi - lo
+            nxt = min(max(nxt, lo + 0.01 * w), hi - 0.01 * w)
+        th = min(nxt, 1.5)
+    if lo > 0.0:
+        c, s = math.cos(lo), math.sin(lo)
+        p = phi * c + dhat * s
+        return lo, evaluate(sys, p), p, max_ls + 1
+    return None, None, None, max_ls
+
+
+# ------------------------------------------------ forces and pressure (Eq. M12)
+def forces(sys, ev):
+    """F_I = -int n grad_I v_ext - grad_I E_ion (Eq. (M12)).
+
+    With the discrete v_ext = Re sum_G v(G) e^{iG.r}:
+    F_I^loc = Omega Re sum_G i G Z_I w(G) e^{-iG.R_I} conj(n(G)).
+    """
+    g = sys.grid
+    w = lpp_form(g.G2, g.omega, sys.rc)
+    F = np.zeros((len(sys.Z), 3))
+    cn = np.conj(ev["nG"])
+    for I in range(len(sys.Z)):
+        base = sys.Z[I] * w * structure_phase(g, sys.R[I]) * cn
+        for a, Ga in enumerate((g.Gx, g.Gy, g.Gz)):
+            F[I, a] = g.omega * float(np.real(np.sum(1j * Ga * base)))
+    return F + sys.F_ion
+
+
+# ------------------------------------------------------------ MD (Sec. V C)
+class MDState:
+    """Ion positions/velocities, a Nose-Hoover thermostat and the density
+    history used for extrapolation."""
+
+    def __init__(self, R, V, masses, T_ion_kelvin, dt_fs, tau_steps=100.0):
+        self.R = np.array(R, dtype=np.float64)
+        self.V = np.array(V, dtype=np.float64)
+        self.m = np.array(masses, dtype=np.float64)
+        self.dt = dt_fs * FS_AU
+        self.kT = T_ion_kelvin * KB_HA_PER_K
+        self.ndof = 3 * len(self.m) - 3
+        tau = tau_steps * self.dt
+        self.Q = self.ndof * self.kT * tau * tau / (4.0 * math.pi ** 2)
+        self.xi = 0.0
+        self.eta = 0.0
+        self.phi = None
+        self.phi_prev = None
+        self.F = None
+        self.ev = None
+
+    def kinetic(self):
+        return 0.5 * float(np.sum(self.m[:, None] * self.V * self.V))
+
+
+def _nh_half(st):
+    """Quarter-kick of xi, velocity scaling by exp(-xi dt/2), quarter-kick."""
+    h = 0.5 * st.dt
+    K = st.kinetic()
+    st.xi += 0.5 * h * (2.0 * K - st.ndof * st.kT) / st.Q
+    st.V *= math.exp(-st.xi * h)
+    st.eta += st.xi * h
+    K = st.kinetic()
+    st.xi += 0.5 * h * (2.0 * K - st.ndof * st.kT) / st.Q
+
+
+def md_prepare(sys, st, gtol=1e-8):
+    """Minimise at the initial geometry and compute forces (step 0)."""
+    sys.set_positions(st.R)
+    phi, ev, stats = minimize(sys, None, gtol=gtol)
+    st.phi, st.phi_prev, st.ev = phi, phi, ev
+    st.F = forces(sys, ev)
+    return stats
+
+
+def md_step(sys, st, gtol=1e-8, thermostat=True):
+    """One velocity-Verlet step with a Nose-Hoover thermostat (Trotter split).
+
+    Readings (the paper's runs used QE's integrators, Fig. (P-QE)): density
+    extrapolated as phi0 = normalise(2 phi_n - phi_{n-1}); COM velocity is
+    not touched inside the step.
+    """
+    if thermostat:
+        _nh_half(st)
+    st.V += 0.5 * st.dt * st.F / st.m[:, None]
+    st.R += st.dt * st.V
+    sys.set_positions(st.R)
+    guess = 2.0 * st.phi - st.phi_prev
+    guess *= math.sqrt(sys.Ne / (sys.grid.dV * float(np.sum(guess * guess))))
+    phi, ev, stats = minimize(sys, guess, gtol=gtol)
+    st.phi_prev, st.phi, st.ev = st.phi, phi, ev
+    st.F = forces(sys, ev)
+    st.V += 0.5 * st.dt * st.F / st.m[:, None]
+    if thermostat:
+        _nh_half(st)
+    return stats
+
+
+def md_conserved(st):
+    """Nose-Hoover extended energy K + F_tot + Q xi^2/2 + g kT eta."""
+    return (st.kinetic() + st.ev["F_tot"] + 0.5 * st.Q * st.xi ** 2
+            + st.ndof * st.kT * st.eta)
