@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark: finite-T OF-DFT molecular dynamics on GB300.
+
+Workload (default): 128 H at 1.0 g/cm^3, 31.25 kK, 96^3 grid, ftGGA (VT84F) +
+PZ LDA, FP64, velocity Verlet (0.2 fs) with a Nose-Hoover thermostat and
+density extrapolation; one step = one MD step (ion update, v_ext and Ewald,
+CG minimisation to ||dF/dphi|| < 1e-8, forces, pressure).  Metric: MD steps/s.
+
+  python bench.py --gpus N --steps K --warmup W [--impl reference]
+
+N > 1 runs independent replicas (one per rank, launched by torchrun); value
+is the steps of all ranks over the slowest rank's time (weak scaling).
+--impl reference times the FP64 CPU oracle on bounded samples of the same
+workload and prints the same metric.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# CG evaluations (energy + potential) per MD step of the default workload,
+# measured on the GPU path; converts the oracle's evaluations/s to MD steps/s.
+EVALS_PER_MD_STEP = 60.0
+
+WORKLOADS = {
+    "md-vt84f-96": dict(functional="vt84f", grid=96, precision="fp64"),
+    "md-sga-96": dict(functional="sga", grid=96, precision="fp64"),
+    "md-vt84f-96-mixed": dict(functional="vt84f", grid=96, precision="mixed"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="md-vt84f-96", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.device = device
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[5 + k].lower() in ("active", "1")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def fft_flops(n):
+    return 5.0 * n * math.log2(n)
+
+
+def kernel_model(name, g):
+    """Algorithmic FLOPs and HBM bytes of one launch (FP64) of a timed kernel
+    class: FFT flops 5 n log2 n per complex line, 2.5 n log2 n per real line;
+    bytes = fields read + written once."""
+    nx, ny, nz = g
+    K = nz // 2 + 1
+    N = nx * ny * nz
+    NH = nx * ny * K
+    if name == "zgga":
+        flops = 6 * (nx * ny / 2) * fft_flops(nz)          # 3 C2R + 3 R2C, pair packed
+        byts = 16 * NH * 3 * 2 + 8 * N * 2                 # grad spectra in, W spectra out, phi in, vpart out
+    elif name == "ypass":
+        flops = nx * K * fft_flops(ny)
+        byts = 16 * NH * 2
+    elif name == "xgrad":
+        flops = 4 * ny * K * fft_flops(nx)
+        byts = 16 * NH * 2 + 16 * NH + 16 * NH * 3          # n in/out, vext in, 3 grads out
+    elif name == "xdiv":
+        flops = 4 * ny * K * fft_flops(nx)
+        byts = 16 * NH * 5 + 16 * NH                       # n, vext, 3 W in; D out
+    else:
+        flops, byts = 0.0, 0.0
+    return flops, byts
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1406_0835_gb300 import inputs, ofdft
+
+    wl = WORKLOADS[args.workload]
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    cfg = inputs.config_md(wl["functional"], grid=wl["grid"])
+    mdT = cfg["T"]
+    ctx = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
+                        precision=wl["precision"], device=dev, stream=stream.cuda_stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    # step 0: minimise at the initial geometry and compute forces
+    ctx.md_step(0.2, mdT, nsteps=0, pos=cfg["ions"], vel=cfg["vel"])
+    for _ in range(args.warmup):
+        ctx.md_step(0.2, mdT, nsteps=1)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    dominant = "zgga" if wl["functional"] != "fttf" else "zfinal"
+    ofdft.ofdft_timer_select(ctx.ctx, dominant)
+    ofdft.ofdft_timer_read(ctx.ctx, reset=True)
+    launches0 = ctx.kernel_launches()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    times = []
+    evals = iters = 0
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1.0)                              # evict L2 between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = ctx.md_step(0.2, mdT, nsteps=1)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            evals += out["stats"]["evaluations"]
+            iters += out["stats"]["iterations"]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = ctx.kernel_launches() - launches0
+    kms, kcount = ofdft.ofdft_timer_read(ctx.ctx, reset=True)
+    ofdft.ofdft_timer_select(ctx.ctx, 0)
+    t_total = sum(times)
+    if world > 1:
+        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = world * args.steps / t_total
+    # end to end through the C ABI with host buffers each step
+    e2e = None
+    if not args.no_e2e:
+        pos, vel = ctx.md_state()
+        t_e2e = 0.0
+        ne = max(2, min(args.steps, 3))
+        for _ in range(ne):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = ctx.md_step(0.2, mdT, nsteps=1, pos=pos, vel=vel)
+            t_e2e += time.perf_counter() - t0
+            pos, vel = out["pos"], out["vel"]
+        nat = len(cfg["Z"])
+        e2e = {"value": world * ne / t_e2e if world == 1 else None, "unit": "MD steps/s",
+               "h2d_bytes_per_step": 2 * nat * 3 * 8,
+               "d2h_bytes_per_step": 3 * nat * 3 * 8 + 16 * 8}
+        if world > 1:
+            tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e["value"] = world * ne / float(tt.item())
+    peaks = read_peaks()
+    flops, byts = kernel_model(dominant, cfg["grid"])
+    avg_s = (kms / 1e3) / max(kcount, 1)
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # FP64 FMA issue: 2 per SM per clock (GB300); 152 SMs
+    fp64_peak = 152 * 2 * 2 * (sm_mhz * 1e6) / 1e12
+    roofline = {"bound": "alu", "kernel": dominant, "achieved": flops / avg_s / 1e12 if kcount else None,
+                "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
+                "frac": (flops / avg_s / 1e12) / fp64_peak if kcount else None,
+                "traffic": None, "launches": kcount, "avg_launch_us": avg_s * 1e6,
+                "hbm_gbs": byts / avg_s / 1e9 if kcount else None,
+                "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_note": "FP64 peak derived from 152 SMs x 2 DFMA/clk x median SM clock"}
+    res = {"metric": "MD steps/s", "value": value, "unit": "MD steps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["precision"] == "fp64" else "f32+f64",
+           "data": "synthetic (seeded hydrogen, random positions and Maxwell-Boltzmann velocities)",
+           "config": {"workload": args.workload, "atoms": len(cfg["Z"]), "grid": list(cfg["grid"]),
+                      "functional": wl["functional"], "xc": "PZ81", "T_K": mdT, "rho_gcc": 1.0,
+                      "dt_fs": 0.2, "gtol": 1e-8, "parallelism": "replicas" if world > 1 else "single GPU",
+                      "l2": "flushed (256 MB write) before every timed step"},
+           "evals_per_s": world * evals / t_total, "evals_per_step": evals / args.steps,
+           "cg_iterations_per_step": iters / args.steps,
+           "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roofline}
+    ctx.close()
+    return res, evals / args.steps
+
+
+def cpu_baseline(args, evals_per_step, budget_s=15.0):
+    """The oracle timed on a bounded sample: full-size energy + potential
+    evaluations for about budget_s seconds, converted to MD steps/s with the
+    CG evaluations per MD step."""
+    import numpy as np
+    import oracle as O
+    from paper_1406_0835_gb300 import inputs
+    wl = WORKLOADS[args.workload]
+    cfg = inputs.config_md(wl["functional"], grid=wl["grid"])
+    so = O.System(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"])
+    phi = so.uniform_phi() * (1.0 + 0.05 * np.random.default_rng(1).standard_normal(cfg["grid"]))
+    O.evaluate(so, phi)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        O.evaluate(so, phi)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    eps = n / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": eps / evals_per_step, "unit": "MD steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d full-size (%s) energy+potential evaluations in %.1f s = %.3f evals/s, "
+                      "divided by %.1f evaluations per MD step" % (n, "x".join(map(str, cfg["grid"])),
+                                                                   dt, eps, evals_per_step)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on bounded samples of the workload."""
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    for _ in range(args.warmup):
+        cpu_baseline(args, EVALS_PER_MD_STEP, budget_s=2.0)
+    vals = []
+    samples = []
+    for _ in range(args.steps):
+        cb = cpu_baseline(args, EVALS_PER_MD_STEP, budget_s=8.0)
+        vals.append(cb["value"])
+        samples.append(cb["sample"])
+    value = statistics.mean(vals)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"impl": "reference", "metric": "MD steps/s", "value": value, "unit": "MD steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": wl["grid"], "functional": wl["functional"]},
+            "cpu_baseline": {"value": value, "unit": "MD steps/s", "cores": cores, "kind": "oracle",
+                             "sample": samples[0]},
+            "e2e": {"value": value, "unit": "MD steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res, eps = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu:
+            res["cpu_baseline"] = cpu_baseline(args, eps)
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

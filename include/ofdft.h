@@ -1,0 +1,226 @@
+/*
+ * libofdft: finite-temperature orbital-free DFT on one GB300 GPU.
+ *
+ * C ABI for the data-parallel hot path of finite-T OF-DFT molecular dynamics
+ * (arXiv:1406.0835, Karasiev, Sjostrom, Trickey): the non-interacting free
+ * energy (ftTF, SGA, ftGGA/VT84F, KST2-family) plus Hartree, local
+ * pseudopotential and LDA XC terms and their functional derivative on a
+ * periodic 3D grid, its minimisation over phi = sqrt(n) under the
+ * electron-number constraint, Hellmann-Feynman and Ewald forces, the pressure
+ * and the MD step.  The calls mirror the paper's interface
+ *   profess(nat, tau, force, pressure, etot, einternel)   (Sec. V C)
+ * split into setup / energy / minimise / forces / MD step.
+ *
+ * Conventions (all calls):
+ *  - Hartree atomic units (Sec. I units note); temperatures in kelvin (the
+ *    TEMP keyword of Sec. V B).  Positions are Cartesian bohr.
+ *  - Grid fields are C-order [ix][iy][iz] with iz fastest, point
+ *    (ix,iy,iz) at (ix Lx/nx, iy Ly/ny, iz Lz/nz).
+ *  - Every host pointer belongs to the caller and is only read or written
+ *    during the call; the library copies what it keeps.  The library owns all
+ *    device memory of a context until ofdft_destroy.
+ *  - Calls on one context are not thread-safe; distinct contexts are.
+ *  - Every call returns an ofdft_status.  On error, outputs are left
+ *    untouched (except ofdft_minimize, which fills its stats and keeps the
+ *    last state on OFDFT_ENOCONV) and ofdft_last_error() describes it.
+ */
+#ifndef OFDFT_H
+#define OFDFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ofdft_ctx ofdft_ctx;
+
+typedef enum {
+    OFDFT_OK = 0,
+    OFDFT_EINVAL = -1,    /* bad argument (sizes, cell, temperature, pointer) */
+    OFDFT_ENOMEM = -2,    /* device or host allocation failed */
+    OFDFT_ENOCONV = -3,   /* minimisation did not reach the tolerance */
+    OFDFT_ENUMERIC = -4,  /* NaN/Inf or non-positive density met */
+    OFDFT_ETIMEOUT = -5,  /* reserved: a bounded device wait ran out */
+    OFDFT_EDEVICE = -6,   /* CUDA error (message in ofdft_last_error) */
+    OFDFT_EBUSY = -7      /* reserved */
+} ofdft_status;
+
+/* Non-interacting free-energy functional (Table I keywords, Sec. III). */
+typedef enum {
+    OFDFT_FTTF = 0,   /* KINE TTF: finite-T Thomas-Fermi, Eqs. (TF), (fTF) */
+    OFDFT_SGA = 1,    /* KINE HVWTF, PARA MU 5/27: Eq. (SGA-F) */
+    OFDFT_VT84F = 2,  /* KINE VT84F: Eq. (VT84F), the "ftGGA" of this library */
+    OFDFT_KST2 = 3,   /* KINE KST2: Eq. (KST2F) */
+    OFDFT_VWTF = 4,   /* KINE HVWTF, PARA MU 5/3: Sec. III B item (vi) */
+    OFDFT_TW = 5,     /* KINE PBETWF: Sec. III B item (iv) */
+    OFDFT_APBEF = 6   /* KINE APBEF: Sec. III B item (iii) */
+} ofdft_functional;
+
+typedef enum {
+    OFDFT_FP64 = 0,   /* every field and reduction in FP64 */
+    OFDFT_MIXED = 1   /* FP32 FFTs and pointwise terms, FP64 reductions, line
+                         search, Ewald and forces; final energies in FP64 */
+} ofdft_precision;
+
+typedef struct {
+    int xc;           /* 1: Perdew-Zunger LDA XC (Sec. IV, used in Sec. VI); 0: none */
+    double rc;        /* Gaussian local pseudopotential radius in bohr:
+                         v(G) = -4 pi Z exp(-G^2 rc^2/4)/(Omega G^2), G=0 dropped */
+    int precision;    /* ofdft_precision */
+    int device;       /* CUDA device ordinal */
+    void *stream;     /* cudaStream_t to run on, or NULL for a library stream */
+} ofdft_params;
+
+/* Energy partition (Sec. V C sample output) and pressure terms; hartree,
+ * hartree/bohr^3.  F_tot = F_s + E_H + E_loc + F_xc + E_ion. */
+typedef struct {
+    double F_tot;     /* total free energy (QE "free energy Etot") */
+    double F_s;       /* non-interacting free energy, Eq. (E4) */
+    double minus_TS;  /* non-interacting entropic part -T S_s */
+    double E_H;       /* Hartree, Eq. (E2) */
+    double E_loc;     /* int n v_ext */
+    double F_xc;      /* XC free energy */
+    double E_ion;     /* ion-ion (Ewald) energy of Eq. (E1) */
+    double E_int;     /* internal energy F_tot + T S_s */
+    double mu;        /* chemical potential (Euler equation, Eq. (E10)) */
+    double E_alphaZ;  /* dropped G=0 non-Coulomb LPP term, reported only */
+    double P;         /* pressure -Tr(Sigma)/3, Eq. (pressure); no ion kinetic part */
+    double P_s, P_xc, P_H, P_loc, P_ion;
+} ofdft_energy;
+
+typedef struct {
+    int iterations;   /* CG iterations */
+    int evaluations;  /* energy+potential evaluations */
+    double gnorm;     /* final ||dF/dphi|| = (dV sum g^2)^{1/2}, g = 2 phi (v - mu) */
+    int status;       /* ofdft_status of the minimisation */
+} ofdft_stats;
+
+typedef struct {
+    double dt_fs;       /* time step in femtoseconds */
+    double T_kelvin;    /* thermostat temperature; <= 0 switches it off (NVE) */
+    double tau_steps;   /* Nose-Hoover period in time steps (Q = g kT tau^2 / 4 pi^2) */
+    double gtol;        /* electronic tolerance on ||dF/dphi|| per MD step */
+    int maxit;          /* CG iteration cap per MD step */
+} ofdft_md_params;
+
+/* Fill *p with defaults: xc = 1, rc = 0.25, FP64, device 0, library stream. */
+void ofdft_default_params(ofdft_params *p);
+
+/*
+ * Create a context: cell, ions, grid, temperature and functional
+ * (Sec. V C, create_ofdftgeom + the PROFESS input of Sec. V B).
+ *  cell[9]     rows a, b, c in bohr; must be orthorhombic (off-diagonals 0),
+ *              else OFDFT_EINVAL.
+ *  grid[3]     nx, ny, nz: even, factors in {2,3,5} only, 8 <= n <= 512.
+ *  nat, ions   ions[nat][3] Cartesian bohr; Z[nat] valence charges (> 0).
+ *  T_kelvin    electron temperature (> 0).
+ *  functional  ofdft_functional.
+ *  params      NULL for defaults.
+ * The density starts uniform, phi = (N_e/Omega)^{1/2}, N_e = sum Z.
+ */
+ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat,
+                         const double *ions, const double *Z, double T_kelvin,
+                         int functional, const ofdft_params *params, ofdft_ctx **out);
+
+/* New ion positions ions[nat][3] (bohr); recomputes v_ext(G) and Ewald terms. */
+ofdft_status ofdft_set_positions(ofdft_ctx *ctx, const double *ions);
+
+/* Replace phi by host phi[N] (renormalised to N_e), or by the uniform
+ * density if phi is NULL. */
+ofdft_status ofdft_set_phi(ofdft_ctx *ctx, const double *phi);
+
+/*
+ * One evaluation of F_tot[n] and v = dF/dn at n = phi^2 (Eqs. (E1)-(E4),
+ * (vTF) or (vftGGA), (vxc1), (E2)), where phi is host phi[N] or, if NULL,
+ * the context's current phi.  Fills *E (may be NULL) and, if v is not NULL,
+ * the host array v[N] (hartree).
+ */
+ofdft_status ofdft_energy_potential(ofdft_ctx *ctx, const double *phi,
+                                    ofdft_energy *E, double *v);
+
+/*
+ * Minimise F_tot over phi with dV sum phi^2 = N_e by nonlinear CG
+ * (Sec. II; the CG details are this library's reading, identical to the
+ * oracle's): Polak-Ribiere+ directions projected orthogonal to phi,
+ * norm-preserving rotations, derivative line search; stops when
+ * ||dF/dphi|| < gtol or after maxit iterations (OFDFT_ENOCONV).
+ * Starts from the context's current phi and leaves the minimiser there.
+ */
+ofdft_status ofdft_minimize(ofdft_ctx *ctx, double gtol, int maxit,
+                            ofdft_energy *E, ofdft_stats *stats);
+
+/*
+ * Hellmann-Feynman plus Ewald forces at the current density, Eq. (M12):
+ * F[nat][3] in hartree/bohr (may be NULL), and the pressure P
+ * (hartree/bohr^3, may be NULL).
+ */
+ofdft_status ofdft_forces(ofdft_ctx *ctx, double *F, double *pressure);
+
+/* Copy the current density n = phi^2 to host n[N]. */
+ofdft_status ofdft_get_density(ofdft_ctx *ctx, double *n);
+
+/* Ion masses m[nat] in electron masses (default: hydrogen, 1.00794 u). */
+ofdft_status ofdft_set_masses(ofdft_ctx *ctx, const double *m);
+
+/*
+ * Advance the MD state by nsteps velocity-Verlet steps with a Nose-Hoover
+ * thermostat (the QE integrator of Fig. (P-QE); the paper's runs used an
+ * Andersen thermostat).  Each step: thermostat half step, half kick, drift,
+ * new v_ext and Ewald terms, density extrapolated as 2 phi_n - phi_{n-1},
+ * CG minimisation, forces (Eq. (M12)), half kick, thermostat half step.
+ *  pos, vel   [nat][3] in/out on the host (bohr, bohr per atomic time unit),
+ *             or NULL to use and keep the device-resident state.  On entry a
+ *             pos that differs from the current positions starts a new
+ *             trajectory there (thermostat reset, density re-minimised); a
+ *             pos equal to them (e.g. what the previous call returned) only
+ *             costs the copies.  vel on entry replaces the velocities.  On
+ *             return both hold the state after the last step.
+ *  F          [nat][3] out (may be NULL); E, stats out (may be NULL).
+ * The first call at a new geometry minimises and computes forces first;
+ * nsteps = 0 does only that.
+ */
+ofdft_status ofdft_md_step(ofdft_ctx *ctx, const ofdft_md_params *mp, int nsteps,
+                           double *pos, double *vel, double *F,
+                           ofdft_energy *E, ofdft_stats *stats);
+
+/* Copy the MD state out: pos, vel [nat][3] (either may be NULL). */
+ofdft_status ofdft_md_state(ofdft_ctx *ctx, double *pos, double *vel);
+
+/* Nose-Hoover extended energy K + F_tot + Q xi^2/2 + g kT eta of the last step. */
+ofdft_status ofdft_md_conserved(ofdft_ctx *ctx, double *H);
+
+/* Grid size N and the number of ions of a context. */
+ofdft_status ofdft_sizes(ofdft_ctx *ctx, long long *N, int *nat);
+
+/*
+ * Diagnostics: record CUDA events around every launch of one kernel class on
+ * the context's stream (no extra synchronisation).  id: 0 off,
+ * 1 z pass with the pointwise GGA functional, 2 x pass with gradients,
+ * 3 x pass with the divergence, 4 y pass, 5 z forward pass, 6 z final pass,
+ * 7 x pass of the ftTF potential.  ofdft_timer_read synchronises the stream,
+ * returns the summed event time (ms) and the launch count, and optionally
+ * clears them.
+ */
+ofdft_status ofdft_timer_select(ofdft_ctx *ctx, int id);
+ofdft_status ofdft_timer_read(ofdft_ctx *ctx, double *total_ms, long long *launches, int reset);
+
+/* Number of CUDA kernels this context has launched since setup. */
+long long ofdft_kernel_launches(ofdft_ctx *ctx);
+
+/* Message for the last error on ctx (or of the last failed setup if ctx is
+ * NULL).  Valid until the next call on ctx. */
+const char *ofdft_last_error(ofdft_ctx *ctx);
+
+/*
+ * Host-side evaluation of the tabulated temperature functions used by the
+ * kernels (no GPU needed): for each t[i], out[i*8 + k] = xi, zeta, A, B and
+ * their t-derivatives, with xi = kappa - t kappa', zeta = -t kappa'
+ * (Eq. (xizeta)), A = (h~ - t h~')/xi, B = t h~'/zeta (Eq. (s_s)).
+ */
+ofdft_status ofdft_tfunc_eval(long long n, const double *t, double *out);
+
+void ofdft_destroy(ofdft_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFDFT_H */

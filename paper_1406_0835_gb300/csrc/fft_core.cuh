@@ -1,0 +1,184 @@
+// Batched mixed-radix (2, 3, 4, 5, 8) Stockham FFT on lines held in shared
+// memory.  All threads of the block take part; each stage reads one buffer
+// and writes the other, with a barrier between stages.
+//
+// Stage with radix R, Ns = product of earlier radices, for butterfly j of
+// n/R:  k = j mod Ns, inputs x[j + r n/R] twiddled by w^{r k n/(Ns R)},
+// R-point DFT, outputs to ((j div Ns) Ns R + k) + r Ns.  Forward uses
+// w = exp(-2 pi i / n), inverse its conjugate (unnormalised).
+#pragma once
+
+#include "ofdft_internal.h"
+
+namespace ofdft {
+
+template <typename C, bool INV> __device__ __forceinline__ void dft2(C *v)
+{
+    C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft4(C *v)
+{
+    C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    C s13 = cadd(v[1], v[3]), d13 = cmuli<C, INV>(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft3(C *v)
+{
+    typedef decltype(C::x) T;
+    const T s3 = T(0.86602540378443864676);   // sin(2 pi/3)
+    C t1 = cadd(v[1], v[2]);
+    C t2 = csub(v[0], cscale(t1, T(0.5)));
+    C t3 = cmuli<C, INV>(cscale(csub(v[1], v[2]), s3));
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(t2, t3);
+    v[2] = csub(t2, t3);
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft5(C *v)
+{
+    typedef decltype(C::x) T;
+    const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);
+    const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);
+    C p14 = cadd(v[1], v[4]), m14 = csub(v[1], v[4]);
+    C p23 = cadd(v[2], v[3]), m23 = csub(v[2], v[3]);
+    C a1 = cadd(v[0], cadd(cscale(p14, c1), cscale(p23, c2)));
+    C a2 = cadd(v[0], cadd(cscale(p14, c2), cscale(p23, c1)));
+    C b1 = cmuli<C, INV>(cadd(cscale(m14, s1), cscale(m23, s2)));
+    C b2 = cmuli<C, INV>(csub(cscale(m14, s2), cscale(m23, s1)));
+    v[0] = cadd(v[0], cadd(p14, p23));
+    v[1] = cadd(a1, b1);
+    v[4] = csub(a1, b1);
+    v[2] = cadd(a2, b2);
+    v[3] = csub(a2, b2);
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft8(C *v)
+{
+    typedef decltype(C::x) T;
+    const T r = T(0.70710678118654752440);
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<C, INV>(e);
+    dft4<C, INV>(o);
+    // o[k] *= W8^k (forward W8 = exp(-i pi/4))
+    o[1] = INV ? cmk<C>(r * (o[1].x - o[1].y), r * (o[1].x + o[1].y))
+               : cmk<C>(r * (o[1].x + o[1].y), r * (o[1].y - o[1].x));
+    o[2] = cmuli<C, INV>(o[2]);
+    o[3] = INV ? cmk<C>(-r * (o[3].x + o[3].y), r * (o[3].x - o[3].y))
+               : cmk<C>(r * (o[3].y - o[3].x), -r * (o[3].x + o[3].y));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = cadd(e[k], o[k]);
+        v[k + 4] = csub(e[k], o[k]);
+    }
+}
+
+template <typename C, int R, bool INV> __device__ __forceinline__ void dftR(C *v)
+{
+    if (R == 2) dft2<C, INV>(v);
+    else if (R == 3) dft3<C, INV>(v);
+    else if (R == 4) dft4<C, INV>(v);
+    else if (R == 5) dft5<C, INV>(v);
+    else dft8<C, INV>(v);
+}
+
+// One Stockham stage over nl lines.  Element e of line l lives at
+// buf[l * lstride + e * estride].  lines_fast selects whether consecutive
+// threads walk lines (column tiles) or butterflies (contiguous lines).
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void stage(const C *__restrict__ src, C *__restrict__ dst, int n, int Ns,
+                                      const C *__restrict__ tw, int nl, int lstride, int estride,
+                                      bool lines_fast)
+{
+    const int nb = n / R;
+    const int total = nb * nl;
+    const int tws = n / (Ns * R);
+    for (int it = threadIdx.x; it < total; it += blockDim.x) {
+        int l, j;
+        if (lines_fast) {
+            l = it % nl;
+            j = it / nl;
+        } else {
+            j = it % nb;
+            l = it / nb;
+        }
+        const C *s = src + l * lstride;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * estride];
+        const int k = j % Ns;
+        if (k != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = __ldg(tw + r * k * tws);
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dftR<C, R, INV>(v);
+        C *d = dst + l * lstride;
+        const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[(base + r * Ns) * estride] = v[r];
+    }
+}
+
+// Full transform of nl lines; data starts in a, b is scratch.  Returns the
+// buffer holding the result.  Callers must __syncthreads() before the call
+// (data written) and may read the result right after it returns.
+template <typename C, bool INV>
+__device__ C *fft_lines(C *a, C *b, const FftAxis &ax, int nl, int lstride, int estride, bool lines_fast)
+{
+    const C *tw = reinterpret_cast<const C *>(ax.tw);
+    for (int s = 0; s < ax.nst; ++s) {
+        const int R = ax.rad[s], Ns = ax.ns[s];
+        switch (R) {
+        case 2: stage<C, 2, INV>(a, b, ax.n, Ns, tw, nl, lstride, estride, lines_fast); break;
+        case 3: stage<C, 3, INV>(a, b, ax.n, Ns, tw, nl, lstride, estride, lines_fast); break;
+        case 4: stage<C, 4, INV>(a, b, ax.n, Ns, tw, nl, lstride, estride, lines_fast); break;
+        case 5: stage<C, 5, INV>(a, b, ax.n, Ns, tw, nl, lstride, estride, lines_fast); break;
+        default: stage<C, 8, INV>(a, b, ax.n, Ns, tw, nl, lstride, estride, lines_fast); break;
+        }
+        __syncthreads();
+        C *t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Deterministic block sum of NQ doubles; thread 0 returns the totals in v.
+template <int NQ> __device__ __forceinline__ void block_sum(double *v)
+{
+    __shared__ double red[32][NQ];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        v[q] = x;
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) red[wid][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w][q];
+            v[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace ofdft

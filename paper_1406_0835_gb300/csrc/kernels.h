@@ -1,0 +1,90 @@
+// Host-side launchers of the libofdft kernels (templated on the field type).
+#pragma once
+
+#include "ofdft_internal.h"
+
+namespace ofdft {
+
+// ---- grid fields (kernels_fields.cu)
+template <typename T>
+void launch_zfwd(const GridInfo &g, const FftAxis &az, int mode, const T *in, const T *phi,
+                 const T *dhat, T c, T s, T *phit, cplx<T> *out, cudaStream_t st);
+template <typename T>
+int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, cplx<T> *g2,
+                const T *phit, T temp, const FuncParams &fp, const T *tab, int xc, T *vpart,
+                double *part, cudaStream_t st);
+template <typename T>
+int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T> *dspec,
+                  const T *vpart, const T *phit, const T *phi, const T *dhat, T c, T s, T temp,
+                  const FuncParams &fp, const T *tab, int xc, T *vout, double *part,
+                  cudaStream_t st);
+template <typename T>
+void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data, int nfields,
+                  long long fstride, cudaStream_t st);
+template <typename T>
+int launch_xgrad(const GridInfo &g, const FftAxis &ax, cplx<T> *nspec, const cplx<T> *vext,
+                 cplx<T> *g0, cplx<T> *g1, cplx<T> *g2, double *part, cudaStream_t st);
+template <typename T>
+int launch_xhl(const GridInfo &g, const FftAxis &ax, cplx<T> *spec, const cplx<T> *vext,
+               cplx<T> *nG_out, int inverse, double *part, cudaStream_t st);
+template <typename T>
+void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const cplx<T> *vext,
+                 cplx<T> *w0, const cplx<T> *w1, const cplx<T> *w2, cudaStream_t st);
+size_t field_smem_max(const GridInfo &g, size_t csize);
+template <typename T> void set_field_smem_limits(size_t bytes);
+
+// ---- vectors, reductions, ions (kernels_misc.cu)
+// Sum part[q * nblk + b] over b for q < nq into out[q] (one block per q, fixed order).
+void launch_reduce(const double *part, int nblk, int nq, double *out, cudaStream_t st);
+template <typename T> void launch_fill(long long n, T *x, T val, cudaStream_t st);
+template <typename T> void launch_scale(long long n, T *x, double s, cudaStream_t st);
+template <typename T, typename U> void launch_convert(long long n, const T *x, U *y, cudaStream_t st);
+// sum x^2 -> part (returns blocks)
+template <typename T> int launch_sumsq(long long n, const T *x, double *part, cudaStream_t st);
+// y = 2 x - xp; part: sum y^2
+template <typename T>
+int launch_extrap(long long n, const T *x, const T *xp, T *y, double *part, cudaStream_t st);
+// g = 2 phi (v - mu); part: sum g^2, sum g.gprev
+template <typename T>
+int launch_cg_grad(long long n, const T *phi, const T *v, double mu, T *g, const T *gprev,
+                   double *part, cudaStream_t st);
+// d = -g + beta d; part: sum phi d, sum d^2, sum d g, sum phi^2, sum phi g
+template <typename T>
+int launch_cg_dir(long long n, const T *g, T *d, double beta, const T *phi, double *part,
+                  cudaStream_t st);
+// restart: d = -g; else d -= c1 phi; dhat = c2 d; part: sum 2 phi v dhat
+template <typename T>
+int launch_cg_dhat(long long n, const T *g, T *d, const T *phi, const T *v, double c1, double c2,
+                   int restart, T *dhat, double *part, cudaStream_t st);
+
+// Per-ion axis phase tables exp(-i G_a R_a) for a = x, y, z (complex double,
+// [nat][nx], [nat][ny], [nat][K]).
+void launch_phases(const GridInfo &g, int nat, const double *R, double2 *px, double2 *py,
+                   double2 *pz, cudaStream_t st);
+// v_ext(G) on the half spectrum, Hermitian-symmetrised on Nyquist planes.
+template <typename T>
+void launch_vext(const GridInfo &g, int nat, const double *Z, const double2 *px,
+                 const double2 *py, const double2 *pz, cplx<T> *vext, cudaStream_t st);
+// Local-pseudopotential forces from n(G): part[(I * nchunk + c) * 3 + a]; returns nchunk.
+template <typename T>
+int launch_lpp_forces(const GridInfo &g, int nat, const double *Z, const double2 *px,
+                      const double2 *py, const double2 *pz, const cplx<T> *nG, double *part,
+                      cudaStream_t st);
+// Sum force partials over chunks into F[nat][3] (+= if accumulate).
+void launch_force_reduce(int nat, int nchunk, const double *part, double *F, int accumulate,
+                         cudaStream_t st);
+
+// Ewald: real-space part per ion -> eparts[nat], F[nat][3];
+// reciprocal part over the G list -> S[nG], energy partials, forces added.
+void launch_ewald_real(int nat, const double *R, const double *Z, const double *L, double alpha,
+                       double rcut, int3 nimg, double *eion, double *F, cudaStream_t st);
+int launch_ewald_recip(int nat, const double *R, const double *Z, int nG, const double *Gv,
+                       const double *wG, double2 *S, double *epart, double *F, cudaStream_t st);
+
+// MD: half step A (thermostat half, kick, drift) and B (kick, thermostat half).
+void launch_md_a(int nat, const double *m, double *R, double *V, const double *F, double dt,
+                 double kT, double Q, int ndof, int thermo, double *nh, cudaStream_t st);
+void launch_md_b(int nat, const double *m, double *V, const double *F, double dt, double kT,
+                 double Q, int ndof, int thermo, double *nh, cudaStream_t st);
+
+}  // namespace ofdft

@@ -1,0 +1,587 @@
+// Vector kernels of the CG minimiser, deterministic reductions, the local
+// pseudopotential structure factor and forces (Eq. (M12)), the Ewald ion-ion
+// terms and the MD integrator.  Every reduction writes per-block partial
+// sums that a second kernel adds in a fixed order, so results do not depend
+// on scheduling.
+#include "fft_core.cuh"
+#include "kernels.h"
+
+namespace ofdft {
+
+namespace {
+
+constexpr int kVecThreads = 256;
+
+int vec_blocks(long long n)
+{
+    long long b = (n + kVecThreads - 1) / kVecThreads;
+    return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);   // 8 blocks per SM at most
+}
+
+__global__ void k_reduce(const double *__restrict__ part, int nblk, double *__restrict__ out)
+{
+    double v[1] = {0.0};
+    const double *p = part + (size_t)blockIdx.x * nblk;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) v[0] += p[i];
+    block_sum<1>(v);
+    if (threadIdx.x == 0) out[blockIdx.x] = v[0];
+}
+
+template <typename T> __global__ void k_fill(long long n, T *x, T val)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] = val;
+}
+
+template <typename T> __global__ void k_scale(long long n, T *x, double s)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] = (T)((double)x[i] * s);
+}
+
+template <typename T, typename U> __global__ void k_convert(long long n, const T *x, U *y)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = (U)x[i];
+}
+
+template <typename T> __global__ void k_sumsq(long long n, const T *__restrict__ x, double *part)
+{
+    double v[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double a = (double)x[i];
+        v[0] += a * a;
+    }
+    block_sum<1>(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+template <typename T>
+__global__ void k_extrap(long long n, const T *__restrict__ x, const T *__restrict__ xp,
+                         T *__restrict__ y, double *part)
+{
+    double v[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T a = T(2) * x[i] - xp[i];
+        y[i] = a;
+        v[0] += (double)a * (double)a;
+    }
+    block_sum<1>(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+template <typename T>
+__global__ void k_cg_grad(long long n, const T *__restrict__ phi, const T *__restrict__ v,
+                          double mu, T *__restrict__ g, const T *__restrict__ gprev, double *part)
+{
+    double acc[2] = {0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T gi = T(2) * phi[i] * (v[i] - T(mu));
+        g[i] = gi;
+        acc[0] += (double)gi * (double)gi;
+        if (gprev != nullptr) acc[1] += (double)gi * (double)gprev[i];
+    }
+    block_sum<2>(acc);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = acc[0];
+        part[gridDim.x + blockIdx.x] = acc[1];
+    }
+}
+
+template <typename T>
+__global__ void k_cg_dir(long long n, const T *__restrict__ g, T *__restrict__ d, double beta,
+                         const T *__restrict__ phi, double *part)
+{
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T gi = g[i];
+        T di = (beta == 0.0) ? -gi : (T)(-(double)gi + beta * (double)d[i]);
+        d[i] = di;
+        double p = (double)phi[i];
+        acc[0] += p * (double)di;
+        acc[1] += (double)di * (double)di;
+        acc[2] += (double)di * (double)gi;
+        acc[3] += p * p;
+        acc[4] += p * (double)gi;
+    }
+    block_sum<5>(acc);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 5; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = acc[q];
+}
+
+template <typename T>
+__global__ void k_cg_dhat(long long n, const T *__restrict__ g, T *__restrict__ d,
+                          const T *__restrict__ phi, const T *__restrict__ v, double c1, double c2,
+                          int restart, T *__restrict__ dhat, double *part)
+{
+    double acc[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double di = restart ? -(double)g[i] : (double)d[i] - c1 * (double)phi[i];
+        d[i] = (T)di;
+        T dh = (T)(c2 * di);
+        dhat[i] = dh;
+        acc[0] += 2.0 * (double)phi[i] * (double)v[i] * (double)dh;
+    }
+    block_sum<1>(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+}
+
+// ------------------------------------------------ structure factor, forces
+__global__ void k_phases(GridInfo g, int nat, const double *__restrict__ R, double2 *px,
+                         double2 *py, double2 *pz)
+{
+    const double tp = 6.283185307179586477;
+    const int per = g.nx + g.ny + g.K;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nat * per; i += gridDim.x * blockDim.x) {
+        const int I = i / per, j = i - I * per;
+        double G, r;
+        double2 *dst;
+        if (j < g.nx) {
+            int k = j <= g.nx / 2 ? j : j - g.nx;
+            G = tp * k / g.Lx;
+            r = R[3 * I];
+            dst = px + (size_t)I * g.nx + j;
+        } else if (j < g.nx + g.ny) {
+            int jj = j - g.nx;
+            int k = jj <= g.ny / 2 ? jj : jj - g.ny;
+            G = tp * k / g.Ly;
+            r = R[3 * I + 1];
+            dst = py + (size_t)I * g.ny + jj;
+        } else {
+            int jj = j - g.nx - g.ny;
+            G = tp * jj / g.Lz;
+            r = R[3 * I + 2];
+            dst = pz + (size_t)I * g.K + jj;
+        }
+        double s, c;
+        sincos(G * r, &s, &c);
+        *dst = make_double2(c, -s);      // exp(-i G r)
+    }
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Local pseudopotential form factor per unit charge (Gaussian ion):
+// w(G) = -4 pi exp(-G^2 rc^2/4) / (Omega G^2), 0 at G = 0.
+__device__ __forceinline__ double lpp_w(const GridInfo &g, double g2)
+{
+    return g2 > 0.0 ? -12.566370614359172954 * exp(-0.25 * g2 * g.rc * g.rc) / (g.omega * g2) : 0.0;
+}
+
+struct Hk {
+    int ix, iy, kz;
+    bool nx_, ny_, nz_;
+    double gx, gy, gz, g2, wk;
+};
+
+__device__ __forceinline__ Hk hidx(const GridInfo &g, long long q)
+{
+    Hk h;
+    h.kz = (int)(q % g.K);
+    long long r = q / g.K;
+    h.iy = (int)(r % g.ny);
+    h.ix = (int)(r / g.ny);
+    const double tp = 6.283185307179586477;
+    int kx = h.ix <= g.nx / 2 ? h.ix : h.ix - g.nx;
+    int ky = h.iy <= g.ny / 2 ? h.iy : h.iy - g.ny;
+    h.gx = tp * kx / g.Lx;
+    h.gy = tp * ky / g.Ly;
+    h.gz = tp * h.kz / g.Lz;
+    h.g2 = h.gx * h.gx + h.gy * h.gy + h.gz * h.gz;
+    h.nx_ = 2 * h.ix == g.nx;
+    h.ny_ = 2 * h.iy == g.ny;
+    h.nz_ = 2 * h.kz == g.nz;
+    h.wk = (h.kz == 0 || h.nz_) ? 1.0 : 2.0;
+    return h;
+}
+
+// v(G) = w(G) sum_I Z_I (P_I + P'_I)/2 with P = exp(-i G.R), P' = exp(i G'.R),
+// G' = -G except on Nyquist axes where G'_a = +G_a (the Hermitian partner
+// folded onto the stored plane).  Off the Nyquist planes P' = P.
+template <typename T>
+__global__ void k_vext(GridInfo g, int nat, const double *__restrict__ Z,
+                       const double2 *__restrict__ px, const double2 *__restrict__ py,
+                       const double2 *__restrict__ pz, cplx<T> *__restrict__ vext)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.NH;
+         q += (long long)gridDim.x * blockDim.x) {
+        Hk h = hidx(g, q);
+        double w = lpp_w(g, h.g2);
+        double2 acc = make_double2(0.0, 0.0);
+        const bool nyq = h.nx_ || h.ny_ || h.nz_;
+        if (w != 0.0) {
+            for (int I = 0; I < nat; ++I) {
+                double2 a = px[(size_t)I * g.nx + h.ix], b = py[(size_t)I * g.ny + h.iy],
+                        c = pz[(size_t)I * g.K + h.kz];
+                double2 P = zmul(zmul(a, b), c);
+                if (nyq) {
+                    if (h.nx_) a.y = -a.y;
+                    if (h.ny_) b.y = -b.y;
+                    if (h.nz_) c.y = -c.y;
+                    double2 Pp = zmul(zmul(a, b), c);
+                    P = make_double2(0.5 * (P.x + Pp.x), 0.5 * (P.y + Pp.y));
+                }
+                acc.x += Z[I] * P.x;
+                acc.y += Z[I] * P.y;
+            }
+        }
+        vext[q] = cmk<cplx<T>>((T)(w * acc.x), (T)(w * acc.y));
+    }
+}
+
+// F_I,a = -Omega sum_half w_k Re(conj(n(G)) dv_I(G)/dR_I,a),
+// dv_I/dR_a = Z_I w(G) (-i G_a P + i G'_a P')/2.
+template <typename T>
+__global__ void k_lpp_forces(GridInfo g, int nat, const double *__restrict__ Z,
+                             const double2 *__restrict__ px, const double2 *__restrict__ py,
+                             const double2 *__restrict__ pz, const cplx<T> *__restrict__ nG,
+                             double *__restrict__ part)
+{
+    const int I = blockIdx.x, chunk = blockIdx.y, nchunk = gridDim.y;
+    const long long per = (g.NH + nchunk - 1) / nchunk;
+    const long long q0 = chunk * per;
+    const long long q1 = min(g.NH, q0 + per);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        Hk h = hidx(g, q);
+        double w = lpp_w(g, h.g2);
+        if (w == 0.0) continue;
+        double2 a = px[(size_t)I * g.nx + h.ix], b = py[(size_t)I * g.ny + h.iy],
+                c = pz[(size_t)I * g.K + h.kz];
+        double2 P = zmul(zmul(a, b), c);
+        cplx<T> nv = nG[q];
+        double nr = (double)nv.x, ni = (double)nv.y;
+        // Re(conj(n) * (-i G P)) = G * Im(conj(n) P) ... with sign folded below
+        double imP = nr * P.y - ni * P.x;        // Im(conj(n) P)
+        double pre = -g.omega * h.wk * Z[I] * w;
+        if (!(h.nx_ || h.ny_ || h.nz_)) {
+            // Re(conj(n)(-i G_a P)) = G_a Im(conj(n) P)
+            acc[0] += pre * h.gx * imP;
+            acc[1] += pre * h.gy * imP;
+            acc[2] += pre * h.gz * imP;
+        } else {
+            if (h.nx_) a.y = -a.y;
+            if (h.ny_) b.y = -b.y;
+            if (h.nz_) c.y = -c.y;
+            double2 Pp = zmul(zmul(a, b), c);
+            double imPp = nr * Pp.y - ni * Pp.x;   // Im(conj(n) P')
+            // Re(conj(n)(i G'_a P')) = -G'_a Im(conj(n) P'); G'_a = +G_a on Nyquist axes
+            double gpx = h.nx_ ? h.gx : -h.gx, gpy = h.ny_ ? h.gy : -h.gy, gpz = h.nz_ ? h.gz : -h.gz;
+            acc[0] += pre * 0.5 * (h.gx * imP - gpx * imPp);
+            acc[1] += pre * 0.5 * (h.gy * imP - gpy * imPp);
+            acc[2] += pre * 0.5 * (h.gz * imP - gpz * imPp);
+        }
+    }
+    block_sum<3>(acc);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) part[((size_t)I * nchunk + chunk) * 3 + k] = acc[k];
+}
+
+__global__ void k_force_reduce(int nat, int nchunk, const double *__restrict__ part, double *F,
+                               int accumulate)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nat * 3; i += gridDim.x * blockDim.x) {
+        const int I = i / 3, k = i - I * 3;
+        double s = 0.0;
+        for (int c = 0; c < nchunk; ++c) s += part[((size_t)I * nchunk + c) * 3 + k];
+        F[i] = accumulate ? F[i] + s : s;
+    }
+}
+
+// ---------------------------------------------------------------- Ewald
+__global__ void k_ewald_real(int nat, const double *__restrict__ R, const double *__restrict__ Z,
+                             double Lx, double Ly, double Lz, double alpha, double rcut, int3 nimg,
+                             double *eion, double *F)
+{
+    const int I = blockIdx.x;
+    const int ix = 2 * nimg.x + 1, iy = 2 * nimg.y + 1, iz = 2 * nimg.z + 1;
+    const long long total = (long long)nat * ix * iy * iz;
+    const double twosqpi = 1.1283791670955125739;   // 2/sqrt(pi)
+    double acc[4] = {0, 0, 0, 0};
+    const double xi = R[3 * I], yi = R[3 * I + 1], zi = R[3 * I + 2], ZI = Z[I];
+    for (long long q = threadIdx.x; q < total; q += blockDim.x) {
+        long long r0 = q;
+        const int J = (int)(r0 % nat);
+        r0 /= nat;
+        const int a = (int)(r0 % ix) - nimg.x;
+        r0 /= ix;
+        const int b = (int)(r0 % iy) - nimg.y;
+        const int c = (int)(r0 / iy) - nimg.z;
+        // minimum image of R_I - R_J, then the lattice shift
+        double dx = xi - R[3 * J], dy = yi - R[3 * J + 1], dz = zi - R[3 * J + 2];
+        dx -= Lx * rint(dx / Lx);
+        dy -= Ly * rint(dy / Ly);
+        dz -= Lz * rint(dz / Lz);
+        dx -= a * Lx;
+        dy -= b * Ly;
+        dz -= c * Lz;
+        double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < 1e-24 || r2 >= rcut * rcut) continue;
+        double r = sqrt(r2);
+        double zz = ZI * Z[J];
+        double ec = erfc(alpha * r) / r;
+        acc[0] += 0.5 * zz * ec;
+        double fm = zz * (ec / r + twosqpi * alpha * exp(-alpha * alpha * r2) / r) / r;
+        acc[1] += fm * dx;
+        acc[2] += fm * dy;
+        acc[3] += fm * dz;
+    }
+    block_sum<4>(acc);
+    if (threadIdx.x == 0) {
+        eion[I] = acc[0];
+        F[3 * I] = acc[1];
+        F[3 * I + 1] = acc[2];
+        F[3 * I + 2] = acc[3];
+    }
+}
+
+// S(G) = sum_I Z_I exp(i G.R_I); energy partial sum wG |S|^2.
+__global__ void k_ewald_S(int nat, const double *__restrict__ R, const double *__restrict__ Z,
+                          int nG, const double *__restrict__ Gv, const double *__restrict__ wG,
+                          double2 *S, double *epart)
+{
+    double acc[1] = {0.0};
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nG; q += gridDim.x * blockDim.x) {
+        const double gx = Gv[3 * q], gy = Gv[3 * q + 1], gz = Gv[3 * q + 2];
+        double sr = 0.0, si = 0.0;
+        for (int I = 0; I < nat; ++I) {
+            double s, c;
+            sincos(gx * R[3 * I] + gy * R[3 * I + 1] + gz * R[3 * I + 2], &s, &c);
+            sr += Z[I] * c;
+            si += Z[I] * s;
+        }
+        S[q] = make_double2(sr, si);
+        acc[0] += wG[q] * (sr * sr + si * si);
+    }
+    block_sum<1>(acc);
+    if (threadIdx.x == 0) epart[blockIdx.x] = acc[0];
+}
+
+// F_I += 2 Z_I sum_G wG G Im(conj(S(G)) exp(i G.R_I)).
+__global__ void k_ewald_F(int nat, const double *__restrict__ R, const double *__restrict__ Z,
+                          int nG, const double *__restrict__ Gv, const double *__restrict__ wG,
+                          const double2 *__restrict__ S, double *F)
+{
+    const int I = blockIdx.x;
+    double acc[3] = {0, 0, 0};
+    for (int q = threadIdx.x; q < nG; q += blockDim.x) {
+        const double gx = Gv[3 * q], gy = Gv[3 * q + 1], gz = Gv[3 * q + 2];
+        double s, c;
+        sincos(gx * R[3 * I] + gy * R[3 * I + 1] + gz * R[3 * I + 2], &s, &c);
+        double2 Sq = S[q];
+        double im = Sq.x * s - Sq.y * c;        // Im(conj(S) e^{i G.R})
+        double f = 2.0 * Z[I] * wG[q] * im;
+        acc[0] += f * gx;
+        acc[1] += f * gy;
+        acc[2] += f * gz;
+    }
+    block_sum<3>(acc);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) F[3 * I + k] += acc[k];
+}
+
+// ------------------------------------------------------------------- MD
+// nh[0] = xi (thermostat velocity), nh[1] = eta (its position), nh[2] = K.
+__device__ void md_thermo_half(int nat, const double *m, double *V, double h, double kT, double Q,
+                               int ndof, double *nh)
+{
+    double k[1] = {0.0};
+    for (int i = threadIdx.x; i < nat; i += blockDim.x)
+        k[0] += 0.5 * m[i] * (V[3 * i] * V[3 * i] + V[3 * i + 1] * V[3 * i + 1] + V[3 * i + 2] * V[3 * i + 2]);
+    block_sum<1>(k);
+    __shared__ double sh[2];
+    if (threadIdx.x == 0) {
+        double K = k[0];
+        double xi = nh[0] + 0.5 * h * (2.0 * K - ndof * kT) / Q;
+        double sc = exp(-xi * h);
+        nh[1] += xi * h;
+        K *= sc * sc;
+        xi += 0.5 * h * (2.0 * K - ndof * kT) / Q;
+        nh[0] = xi;
+        sh[0] = sc;
+    }
+    __syncthreads();
+    const double sc = sh[0];
+    for (int i = threadIdx.x; i < 3 * nat; i += blockDim.x) V[i] *= sc;
+    __syncthreads();
+}
+
+__global__ void k_md_a(int nat, const double *m, double *R, double *V, const double *F, double dt,
+                       double kT, double Q, int ndof, int thermo, double *nh)
+{
+    if (thermo) md_thermo_half(nat, m, V, 0.5 * dt, kT, Q, ndof, nh);
+    for (int i = threadIdx.x; i < 3 * nat; i += blockDim.x) {
+        V[i] += 0.5 * dt * F[i] / m[i / 3];
+        R[i] += dt * V[i];
+    }
+}
+
+__global__ void k_md_b(int nat, const double *m, double *V, const double *F, double dt, double kT,
+                       double Q, int ndof, int thermo, double *nh)
+{
+    for (int i = threadIdx.x; i < 3 * nat; i += blockDim.x) V[i] += 0.5 * dt * F[i] / m[i / 3];
+    __syncthreads();
+    if (thermo) md_thermo_half(nat, m, V, 0.5 * dt, kT, Q, ndof, nh);
+    double k[1] = {0.0};
+    for (int i = threadIdx.x; i < nat; i += blockDim.x)
+        k[0] += 0.5 * m[i] * (V[3 * i] * V[3 * i] + V[3 * i + 1] * V[3 * i + 1] + V[3 * i + 2] * V[3 * i + 2]);
+    block_sum<1>(k);
+    if (threadIdx.x == 0) nh[2] = k[0];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+void launch_reduce(const double *part, int nblk, int nq, double *out, cudaStream_t st)
+{
+    k_reduce<<<nq, 256, 0, st>>>(part, nblk, out);
+}
+
+template <typename T> void launch_fill(long long n, T *x, T val, cudaStream_t st)
+{
+    k_fill<T><<<vec_blocks(n), kVecThreads, 0, st>>>(n, x, val);
+}
+template <typename T> void launch_scale(long long n, T *x, double s, cudaStream_t st)
+{
+    k_scale<T><<<vec_blocks(n), kVecThreads, 0, st>>>(n, x, s);
+}
+template <typename T, typename U> void launch_convert(long long n, const T *x, U *y, cudaStream_t st)
+{
+    k_convert<T, U><<<vec_blocks(n), kVecThreads, 0, st>>>(n, x, y);
+}
+template <typename T> int launch_sumsq(long long n, const T *x, double *part, cudaStream_t st)
+{
+    int b = vec_blocks(n);
+    k_sumsq<T><<<b, kVecThreads, 0, st>>>(n, x, part);
+    return b;
+}
+template <typename T>
+int launch_extrap(long long n, const T *x, const T *xp, T *y, double *part, cudaStream_t st)
+{
+    int b = vec_blocks(n);
+    k_extrap<T><<<b, kVecThreads, 0, st>>>(n, x, xp, y, part);
+    return b;
+}
+template <typename T>
+int launch_cg_grad(long long n, const T *phi, const T *v, double mu, T *g, const T *gprev,
+                   double *part, cudaStream_t st)
+{
+    int b = vec_blocks(n);
+    k_cg_grad<T><<<b, kVecThreads, 0, st>>>(n, phi, v, mu, g, gprev, part);
+    return b;
+}
+template <typename T>
+int launch_cg_dir(long long n, const T *g, T *d, double beta, const T *phi, double *part,
+                  cudaStream_t st)
+{
+    int b = vec_blocks(n);
+    k_cg_dir<T><<<b, kVecThreads, 0, st>>>(n, g, d, beta, phi, part);
+    return b;
+}
+template <typename T>
+int launch_cg_dhat(long long n, const T *g, T *d, const T *phi, const T *v, double c1, double c2,
+                   int restart, T *dhat, double *part, cudaStream_t st)
+{
+    int b = vec_blocks(n);
+    k_cg_dhat<T><<<b, kVecThreads, 0, st>>>(n, g, d, phi, v, c1, c2, restart, dhat, part);
+    return b;
+}
+
+void launch_phases(const GridInfo &g, int nat, const double *R, double2 *px, double2 *py,
+                   double2 *pz, cudaStream_t st)
+{
+    int total = nat * (g.nx + g.ny + g.K);
+    int b = (total + 255) / 256;
+    k_phases<<<b, 256, 0, st>>>(g, nat, R, px, py, pz);
+}
+
+template <typename T>
+void launch_vext(const GridInfo &g, int nat, const double *Z, const double2 *px,
+                 const double2 *py, const double2 *pz, cplx<T> *vext, cudaStream_t st)
+{
+    long long b = (g.NH + 255) / 256;
+    k_vext<T><<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(g, nat, Z, px, py, pz, vext);
+}
+
+template <typename T>
+int launch_lpp_forces(const GridInfo &g, int nat, const double *Z, const double2 *px,
+                      const double2 *py, const double2 *pz, const cplx<T> *nG, double *part,
+                      cudaStream_t st)
+{
+    int nchunk = 608 / (nat > 0 ? nat : 1);
+    if (nchunk < 1) nchunk = 1;
+    long long maxc = (g.NH + 1023) / 1024;
+    if (nchunk > maxc) nchunk = (int)maxc;
+    dim3 grid(nat, nchunk);
+    k_lpp_forces<T><<<grid, 256, 0, st>>>(g, nat, Z, px, py, pz, nG, part);
+    return nchunk;
+}
+
+void launch_force_reduce(int nat, int nchunk, const double *part, double *F, int accumulate,
+                         cudaStream_t st)
+{
+    k_force_reduce<<<(3 * nat + 255) / 256, 256, 0, st>>>(nat, nchunk, part, F, accumulate);
+}
+
+void launch_ewald_real(int nat, const double *R, const double *Z, const double *L, double alpha,
+                       double rcut, int3 nimg, double *eion, double *F, cudaStream_t st)
+{
+    k_ewald_real<<<nat, 256, 0, st>>>(nat, R, Z, L[0], L[1], L[2], alpha, rcut, nimg, eion, F);
+}
+
+int launch_ewald_recip(int nat, const double *R, const double *Z, int nG, const double *Gv,
+                       const double *wG, double2 *S, double *epart, double *F, cudaStream_t st)
+{
+    int b = (nG + 255) / 256;
+    if (b < 1) b = 1;
+    k_ewald_S<<<b, 256, 0, st>>>(nat, R, Z, nG, Gv, wG, S, epart);
+    k_ewald_F<<<nat, 256, 0, st>>>(nat, R, Z, nG, Gv, wG, S, F);
+    return b;
+}
+
+void launch_md_a(int nat, const double *m, double *R, double *V, const double *F, double dt,
+                 double kT, double Q, int ndof, int thermo, double *nh, cudaStream_t st)
+{
+    k_md_a<<<1, 256, 0, st>>>(nat, m, R, V, F, dt, kT, Q, ndof, thermo, nh);
+}
+
+void launch_md_b(int nat, const double *m, double *V, const double *F, double dt, double kT,
+                 double Q, int ndof, int thermo, double *nh, cudaStream_t st)
+{
+    k_md_b<<<1, 256, 0, st>>>(nat, m, V, F, dt, kT, Q, ndof, thermo, nh);
+}
+
+#define OFDFT_MISC_INST(T)                                                                         \
+    template void launch_fill<T>(long long, T *, T, cudaStream_t);                                 \
+    template void launch_scale<T>(long long, T *, double, cudaStream_t);                           \
+    template int launch_sumsq<T>(long long, const T *, double *, cudaStream_t);                    \
+    template int launch_extrap<T>(long long, const T *, const T *, T *, double *, cudaStream_t);   \
+    template int launch_cg_grad<T>(long long, const T *, const T *, double, T *, const T *,        \
+                                   double *, cudaStream_t);                                       \
+    template int launch_cg_dir<T>(long long, const T *, T *, double, const T *, double *,         \
+                                  cudaStream_t);                                                  \
+    template int launch_cg_dhat<T>(long long, const T *, T *, const T *, const T *, double,       \
+                                   double, int, T *, double *, cudaStream_t);                     \
+    template void launch_vext<T>(const GridInfo &, int, const double *, const double2 *,          \
+                                 const double2 *, const double2 *, cplx<T> *, cudaStream_t);      \
+    template int launch_lpp_forces<T>(const GridInfo &, int, const double *, const double2 *,     \
+                                      const double2 *, const double2 *, const cplx<T> *,          \
+                                      double *, cudaStream_t);
+
+OFDFT_MISC_INST(double)
+OFDFT_MISC_INST(float)
+template void launch_convert<float, double>(long long, const float *, double *, cudaStream_t);
+template void launch_convert<double, float>(long long, const double *, float *, cudaStream_t);
+
+}  // namespace ofdft

@@ -1,0 +1,101 @@
+// Internal declarations shared by the CUDA translation units of libofdft.
+// Not part of the public C ABI (see include/ofdft.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ofdft.h"
+
+namespace ofdft {
+
+// ----------------------------------------------------------------- complex
+template <typename T> struct CT;
+template <> struct CT<double> { typedef double2 type; };
+template <> struct CT<float> { typedef float2 type; };
+template <typename T> using cplx = typename CT<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b)
+{
+    C r;
+    r.x = a;
+    r.y = b;
+    return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b)
+{
+    return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+template <typename C> __host__ __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmk<C>(a.x * s, a.y * s); }
+// multiply by -i (forward sign) or +i (inverse sign)
+template <typename C, bool INV> __host__ __device__ __forceinline__ C cmuli(C a)
+{
+    return INV ? cmk<C>(-a.y, a.x) : cmk<C>(a.y, -a.x);
+}
+
+// ------------------------------------------------------------ FFT plans
+constexpr int kMaxStages = 16;
+
+// One axis of a 3D transform: a mixed-radix Stockham schedule and a
+// twiddle table w[m] = exp(-2 pi i m / n), m = 0..n-1, in device memory.
+struct FftAxis {
+    int n;
+    int nst;
+    int rad[kMaxStages];
+    int ns[kMaxStages];      // product of the radices before each stage
+    const void *tw;          // cplx<T>[n]
+};
+
+// Geometry of the periodic orthorhombic grid, C order [ix][iy][iz], and of
+// the half spectrum [ix][iy][kz], kz = 0..nz/2.
+struct GridInfo {
+    int nx, ny, nz, K;
+    long long N, NH;
+    double Lx, Ly, Lz, omega, dV;
+    double rc;               // Gaussian local pseudopotential radius
+};
+
+// Tabulated temperature functions xi, zeta, A, B of t (see tfunc_table.cpp).
+constexpr int kTfDeg = 10;                 // polynomial degree per panel
+constexpr int kTfNc = kTfDeg + 1;
+constexpr int kTfSub = 4;                  // panels per octave of t
+constexpr int kTfEmin = -20;               // t range [2^kTfEmin, 2^kTfEmax)
+constexpr int kTfEmax = 34;
+constexpr int kTfPanels = (kTfEmax - kTfEmin) * kTfSub;
+constexpr int kTfFuncs = 4;                // xi, zeta, A, B
+constexpr int kTfSize = kTfPanels * kTfFuncs * kTfNc;
+
+// Build the table on the host (FP64 monomial coefficients per panel).
+const std::vector<double> &tfunc_table_host();
+
+// Functional selector and constants for the enhancement factors.
+struct FuncParams {
+    int kind;       // 0 ftTF, 1 SGA-form (mu), 2 VT84F, 3 KST2-form (C1, a1)
+    double p0, p1;  // mu | C1, a1
+};
+FuncParams functional_params(int functional);
+
+// Reduction quantities (indices into the scalar block).
+enum Quantity {
+    Q_FS = 0,      // sum f_s
+    Q_TS,          // sum tau0 zeta F_sigma (T S density)
+    Q_FXC,         // sum n eps_xc
+    Q_PS,          // sum (n df/dn - f)
+    Q_WG,          // sum W . grad n
+    Q_PXC,         // sum n (v_xc - eps_xc)
+    Q_PHI2V,       // sum phi^2 v
+    Q_PHI2,        // sum phi^2
+    Q_DTH,         // sum 2 phi v dphi/dtheta
+    Q_EH,          // Hartree energy (already scaled)
+    Q_ELOC,        // local pseudopotential energy (scaled)
+    Q_PLOC,        // LPP pressure (scaled)
+    Q_COUNT_EVAL,
+};
+
+}  // namespace ofdft

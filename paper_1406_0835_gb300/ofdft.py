@@ -1,0 +1,319 @@
+"""ctypes binding of libofdft (include/ofdft.h): argument marshalling only.
+
+Every function named ``ofdft_*`` here calls the C entry point of the same
+name; :class:`Context` is a small convenience wrapper over them.  There is no
+CPU fallback: if the CUDA library is missing, loading raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libofdft.so")
+
+FUNCTIONALS = {"fttf": 0, "sga": 1, "vt84f": 2, "kst2": 3, "vwtf": 4, "tw": 5, "apbef": 6}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+STATUS = {0: "OFDFT_OK", -1: "OFDFT_EINVAL", -2: "OFDFT_ENOMEM", -3: "OFDFT_ENOCONV",
+          -4: "OFDFT_ENUMERIC", -5: "OFDFT_ETIMEOUT", -6: "OFDFT_EDEVICE", -7: "OFDFT_EBUSY"}
+
+_P = ctypes.POINTER(ctypes.c_double)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("xc", ctypes.c_int), ("rc", ctypes.c_double), ("precision", ctypes.c_int),
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Energy(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "F_tot", "F_s", "minus_TS", "E_H", "E_loc", "F_xc", "E_ion", "E_int", "mu", "E_alphaZ",
+        "P", "P_s", "P_xc", "P_H", "P_loc", "P_ion")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("evaluations", ctypes.c_int),
+                ("gnorm", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class MDParams(ctypes.Structure):
+    _fields_ = [("dt_fs", ctypes.c_double), ("T_kelvin", ctypes.c_double),
+                ("tau_steps", ctypes.c_double), ("gtol", ctypes.c_double), ("maxit", ctypes.c_int)]
+
+
+class OfdftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+SIGNATURES = {
+    "ofdft_default_params": (None, [ctypes.POINTER(Params)]),
+    "ofdft_setup": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _P, _P,
+                                   ctypes.c_double, ctypes.c_int, ctypes.POINTER(Params),
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    "ofdft_set_positions": (ctypes.c_int, [ctypes.c_void_p, _P]),
+    "ofdft_set_phi": (ctypes.c_int, [ctypes.c_void_p, _P]),
+    "ofdft_energy_potential": (ctypes.c_int, [ctypes.c_void_p, _P, ctypes.POINTER(Energy), _P]),
+    "ofdft_minimize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                      ctypes.POINTER(Energy), ctypes.POINTER(Stats)]),
+    "ofdft_forces": (ctypes.c_int, [ctypes.c_void_p, _P, _P]),
+    "ofdft_get_density": (ctypes.c_int, [ctypes.c_void_p, _P]),
+    "ofdft_set_masses": (ctypes.c_int, [ctypes.c_void_p, _P]),
+    "ofdft_md_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(MDParams), ctypes.c_int, _P, _P,
+                                     _P, ctypes.POINTER(Energy), ctypes.POINTER(Stats)]),
+    "ofdft_md_state": (ctypes.c_int, [ctypes.c_void_p, _P, _P]),
+    "ofdft_md_conserved": (ctypes.c_int, [ctypes.c_void_p, _P]),
+    "ofdft_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_int)]),
+    "ofdft_timer_select": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ofdft_timer_read": (ctypes.c_int, [ctypes.c_void_p, _P, ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.c_int]),
+    "ofdft_kernel_launches": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "ofdft_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "ofdft_tfunc_eval": (ctypes.c_int, [ctypes.c_longlong, _P, _P]),
+    "ofdft_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def load(path=LIB_PATH):
+    """Load libofdft.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libofdft.so not built (run __graft_entry__.build()): %s" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_P)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _check(ctx, status):
+    if status != 0:
+        msg = load().ofdft_last_error(ctx)
+        raise OfdftError(status, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------- ABI-named functions
+def ofdft_default_params():
+    p = Params()
+    load().ofdft_default_params(ctypes.byref(p))
+    return p
+
+
+def ofdft_setup(cell, grid, ions, Z, T_kelvin, functional, params=None):
+    lib = load()
+    cell = _f64(cell).reshape(-1)
+    if cell.size == 3:
+        cell = np.diag(cell).reshape(-1)
+    grid = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    ions = _f64(ions, (-1, 3))
+    Z = _f64(Z, (-1,))
+    f = FUNCTIONALS[functional] if isinstance(functional, str) else int(functional)
+    p = params if params is not None else ofdft_default_params()
+    out = ctypes.c_void_p()
+    st = lib.ofdft_setup(_ptr(cell), grid, ions.shape[0], _ptr(ions), _ptr(Z), float(T_kelvin), f,
+                         ctypes.byref(p), ctypes.byref(out))
+    _check(None, st)
+    return out.value
+
+
+def ofdft_set_positions(ctx, ions):
+    _check(ctx, load().ofdft_set_positions(ctx, _ptr(_f64(ions, (-1, 3)))))
+
+
+def ofdft_set_phi(ctx, phi=None):
+    _check(ctx, load().ofdft_set_phi(ctx, None if phi is None else _ptr(_f64(phi))))
+
+
+def ofdft_energy_potential(ctx, phi=None, want_v=False):
+    N = ofdft_sizes(ctx)[0]
+    E = Energy()
+    v = np.empty(N) if want_v else None
+    ph = None if phi is None else _f64(phi).reshape(-1)
+    _check(ctx, load().ofdft_energy_potential(ctx, _ptr(ph), ctypes.byref(E), _ptr(v)))
+    return E.as_dict(), v
+
+
+def ofdft_minimize(ctx, gtol=1e-8, maxit=5000, raise_on_noconv=True):
+    E, S = Energy(), Stats()
+    st = load().ofdft_minimize(ctx, float(gtol), int(maxit), ctypes.byref(E), ctypes.byref(S))
+    if st != -3 or raise_on_noconv:
+        _check(ctx, st)
+    return E.as_dict(), S.as_dict()
+
+
+def ofdft_forces(ctx):
+    nat = ofdft_sizes(ctx)[1]
+    F = np.empty((nat, 3))
+    P = np.zeros(1)
+    _check(ctx, load().ofdft_forces(ctx, _ptr(F), _ptr(P)))
+    return F, float(P[0])
+
+
+def ofdft_get_density(ctx):
+    n = np.empty(ofdft_sizes(ctx)[0])
+    _check(ctx, load().ofdft_get_density(ctx, _ptr(n)))
+    return n
+
+
+def ofdft_set_masses(ctx, m):
+    _check(ctx, load().ofdft_set_masses(ctx, _ptr(_f64(m, (-1,)))))
+
+
+def ofdft_md_step(ctx, dt_fs, T_kelvin, nsteps=1, pos=None, vel=None, tau_steps=100.0,
+                  gtol=1e-8, maxit=5000):
+    mp = MDParams(float(dt_fs), float(T_kelvin), float(tau_steps), float(gtol), int(maxit))
+    nat = ofdft_sizes(ctx)[1]
+    pos = None if pos is None else _f64(pos, (-1, 3)).copy()
+    vel = None if vel is None else _f64(vel, (-1, 3)).copy()
+    F = np.empty((nat, 3))
+    E, S = Energy(), Stats()
+    _check(ctx, load().ofdft_md_step(ctx, ctypes.byref(mp), int(nsteps), _ptr(pos), _ptr(vel),
+                                     _ptr(F), ctypes.byref(E), ctypes.byref(S)))
+    return dict(pos=pos, vel=vel, F=F, E=E.as_dict(), stats=S.as_dict())
+
+
+def ofdft_md_state(ctx):
+    nat = ofdft_sizes(ctx)[1]
+    pos = np.empty((nat, 3))
+    vel = np.empty((nat, 3))
+    _check(ctx, load().ofdft_md_state(ctx, _ptr(pos), _ptr(vel)))
+    return pos, vel
+
+
+def ofdft_md_conserved(ctx):
+    H = np.zeros(1)
+    _check(ctx, load().ofdft_md_conserved(ctx, _ptr(H)))
+    return float(H[0])
+
+
+def ofdft_sizes(ctx):
+    N = ctypes.c_longlong()
+    nat = ctypes.c_int()
+    _check(ctx, load().ofdft_sizes(ctx, ctypes.byref(N), ctypes.byref(nat)))
+    return N.value, nat.value
+
+
+TIMERS = {"zgga": 1, "xgrad": 2, "xdiv": 3, "ypass": 4, "zfwd": 5, "zfinal": 6, "xhl": 7}
+
+
+def ofdft_timer_select(ctx, which):
+    _check(ctx, load().ofdft_timer_select(ctx, TIMERS.get(which, which) if which else 0))
+
+
+def ofdft_timer_read(ctx, reset=True):
+    ms = np.zeros(1)
+    n = ctypes.c_longlong()
+    _check(ctx, load().ofdft_timer_read(ctx, _ptr(ms), ctypes.byref(n), int(reset)))
+    return float(ms[0]), n.value
+
+
+def ofdft_kernel_launches(ctx):
+    return int(load().ofdft_kernel_launches(ctx))
+
+
+def ofdft_last_error(ctx=None):
+    m = load().ofdft_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def ofdft_tfunc_eval(t):
+    t = _f64(t).reshape(-1)
+    out = np.empty((t.size, 8))
+    st = load().ofdft_tfunc_eval(t.size, _ptr(t), _ptr(out))
+    if st != 0:
+        raise OfdftError(st, "bad t")
+    return out
+
+
+def ofdft_destroy(ctx):
+    if ctx:
+        load().ofdft_destroy(ctx)
+
+
+# ------------------------------------------------------------ convenience
+class Context:
+    """One OF-DFT system on one GPU (owns a libofdft context)."""
+
+    def __init__(self, L, grid, ions, Z, T_kelvin, functional="fttf", xc=True, rc=0.25,
+                 precision="fp64", device=0, stream=None):
+        p = ofdft_default_params()
+        p.xc = int(bool(xc))
+        p.rc = float(rc)
+        p.precision = PRECISIONS[precision]
+        p.device = int(device)
+        p.stream = stream
+        self.ctx = ofdft_setup(np.diag(np.asarray(L, dtype=np.float64)), grid, ions, Z, T_kelvin,
+                               functional, p)
+        self.grid = tuple(int(x) for x in grid)
+
+    def close(self):
+        if self.ctx:
+            ofdft_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_positions(self, ions):
+        ofdft_set_positions(self.ctx, ions)
+
+    def set_phi(self, phi=None):
+        ofdft_set_phi(self.ctx, phi)
+
+    def energy_potential(self, phi=None, want_v=True):
+        E, v = ofdft_energy_potential(self.ctx, phi, want_v)
+        return E, (None if v is None else v.reshape(self.grid))
+
+    def minimize(self, gtol=1e-8, maxit=5000, raise_on_noconv=True):
+        return ofdft_minimize(self.ctx, gtol, maxit, raise_on_noconv)
+
+    def forces(self):
+        return ofdft_forces(self.ctx)
+
+    def density(self):
+        return ofdft_get_density(self.ctx).reshape(self.grid)
+
+    def md_step(self, dt_fs, T_kelvin, nsteps=1, pos=None, vel=None, **kw):
+        return ofdft_md_step(self.ctx, dt_fs, T_kelvin, nsteps, pos, vel, **kw)
+
+    def md_state(self):
+        return ofdft_md_state(self.ctx)
+
+    def md_conserved(self):
+        return ofdft_md_conserved(self.ctx)
+
+    def kernel_launches(self):
+        return ofdft_kernel_launches(self.ctx)
