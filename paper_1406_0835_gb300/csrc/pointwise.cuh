@@ -66,8 +66,39 @@ OF_HD float split_pow2(float t, int &e, float &inv2e)
     return m;
 }
 
-// out[0..3] = xi, zeta, A, B; out[4..7] = d/dt of each.
-template <typename T>
+// n^{-1/3} for n > 0: seed from the exponent split n = m 2^(3q + r), m 2^r in
+// [1, 8), with a single-precision power of that factor, then Newton steps
+// y <- y (4 - n y^3)/3 (quadratic convergence; 2 steps reach double rounding
+// from a ~1e-7 seed, 1 step reaches float rounding).
+OF_HD double inv_cbrt(double n)
+{
+    int e;
+    double s;
+    double m = split_pow2(n, e, s);
+    int q = (e >= 0) ? e / 3 : -((2 - e) / 3);      // floor(e / 3)
+    int r = e - 3 * q;                                 // 0, 1, 2
+    double mm = m * (double)(1 << r);
+    double y = (double)powf((float)mm, -1.0f / 3.0f);
+    int64_t ib = (int64_t)(1023 - q) << 52;            // 2^-q
+    double sc;
+#ifdef __CUDA_ARCH__
+    sc = __longlong_as_double(ib);
+#else
+    memcpy(&sc, &ib, 8);
+#endif
+    y *= sc;
+    for (int k = 0; k < 2; ++k) y = y * (4.0 - n * (y * y * y)) * (1.0 / 3.0);
+    return y;
+}
+
+OF_HD float inv_cbrt(float n)
+{
+    float y = powf(n, -1.0f / 3.0f);
+    return y * (4.0f - n * (y * y * y)) * (1.0f / 3.0f);
+}
+
+// out[0..3] = xi, zeta, A, B; out[4..7] = d/dt of each (nf functions: 2 or 4).
+template <typename T, int NF = kTfFuncs>
 OF_HD void tfunc_eval(const T *__restrict__ tab, T t, T out[8])
 {
     const T pi2 = T(9.8696044010893586188);
@@ -104,7 +135,7 @@ OF_HD void tfunc_eval(const T *__restrict__ tab, T t, T out[8])
     const T *c = tab + ((size_t)((e - kTfEmin) * kTfSub + sub) * kTfFuncs) * kTfNc;
     T dudt = T(8) * inv2e;
 #pragma unroll
-    for (int q = 0; q < kTfFuncs; ++q) {
+    for (int q = 0; q < NF; ++q) {
         const T *cq = c + q * kTfNc;
         T p = cq[kTfDeg], dp = T(0);
 #pragma unroll
@@ -139,8 +170,10 @@ OF_HD void enhance(const FuncParams &fp, T x, T &F, T &dF)
         T e1 = exp(-al * x);
         T x2 = x * x;
         T em = -expm1(-al * x2);              // 1 - exp(-al x^2)
-        T rx = T(1) / x;
-        T den = T(1) / (T(1) + mu * x);
+        T q = T(1) + mu * x;
+        T inv = T(1) / (x * q);               // one division for 1/x and 1/(1 + mu x)
+        T rx = q * inv;
+        T den = x * inv;
         F = T(1) - mu * x * e1 * den + em * (rx - T(1)) + T(5.0 / 3.0) * x;
         dF = -mu * e1 * (T(1) - al * x - al * mu * x2) * den * den
              + T(2) * al * (T(1) - em) * (T(1) - x) - em * rx * rx + T(5.0 / 3.0);
@@ -164,27 +197,31 @@ template <typename T>
 OF_HD FsOut<T> fs_point(const FuncParams &fp, const T *__restrict__ tab, T temp, T n, T g2)
 {
     FsOut<T> o;
-    T c13 = cbrt(n);
+    T y = inv_cbrt(n);                                  // n^{-1/3}
+    T y2 = y * y;
+    T c13 = n * y2;                                     // n^{1/3}
     T n23 = c13 * c13;
-    T rn = T(1) / n;
+    T rn = y2 * y;                                      // 1/n
     T tau0 = T(OF_CTF) * n * n23;                       // Eq. (tauTFdefn)
     T dtau0 = T(5.0 / 3.0 * OF_CTF) * n23;
-    T t = T(2) * temp / (T(OF_K23) * n23);              // Eq. (tred)
+    T t = T(2.0 / OF_K23) * temp * y2;                  // Eq. (tred)
     T dtdn = T(-2.0 / 3.0) * t * rn;
     T tf[8];
-    tfunc_eval<T>(tab, t, tf);
-    T xi = tf[0], ze = tf[1], A = tf[2], B = tf[3];
-    T dxi = tf[4], dze = tf[5], dA = tf[6], dB = tf[7];
     if (fp.kind == 0) {                                 // ftTF: f = tau0 kappa, kappa = xi - zeta
+        tfunc_eval<T, 2>(tab, t, tf);
+        T xi = tf[0], ze = tf[1], dxi = tf[4], dze = tf[5];
         o.f = tau0 * (xi - ze);
         o.ts = tau0 * ze;
         o.dfdn = dtau0 * (xi - ze) + tau0 * (dxi - dze) * dtdn;   // Eq. (vTF)
         o.wc = T(0);
         return o;
     }
+    tfunc_eval<T>(tab, t, tf);
+    T xi = tf[0], ze = tf[1], A = tf[2], B = tf[3];
+    T dxi = tf[4], dze = tf[5], dA = tf[6], dB = tf[7];
     // s^2 = |grad n|^2 / (4 (3 pi^2)^{2/3} n^{8/3})  (Eq. (s_0defn))
-    T rn43 = rn / c13;
-    T s2 = g2 * T(OF_CS) * rn43 * rn43;
+    T rn43 = rn * y;
+    T s2 = (g2 * rn43) * rn43 * T(OF_CS);               // ordered so n^{-8/3} never forms alone
     T xt = s2 * A, xs = s2 * B;                          // s_tau^2, s_sigma^2 (Eq. (s_s))
     T Ft, dFt, Fsg, dFsg;
     enhance<T>(fp, xt, Ft, dFt);
@@ -199,7 +236,7 @@ OF_HD FsOut<T> fs_point(const FuncParams &fp, const T *__restrict__ tab, T temp,
              + kin * dFt * (e83 * xt + s2 * dA * dtdn)
              - ent * dFs * (e83 * xs + s2 * dB * dtdn);
     // last line: W = [tau0 xi F_tau' A - tau0 zeta F_sigma' B] d s^2/d grad n
-    o.wc = (kin * dFt * A - ent * dFs * B) * T(2 * OF_CS) * rn43 * rn43;
+    o.wc = ((kin * dFt * A - ent * dFs * B) * rn43) * rn43 * T(2 * OF_CS);
     return o;
 }
 
@@ -207,9 +244,9 @@ OF_HD FsOut<T> fs_point(const FuncParams &fp, const T *__restrict__ tab, T temp,
 template <typename T>
 OF_HD void pz81_point(T n, T &eps, T &v)
 {
-    T c13 = cbrt(n);
-    T rs = T(0.62035049089940001667) / c13;            // (3/(4 pi n))^{1/3}
-    T ex = T(-0.73855876638202240587) * c13;           // -(3/4)(3/pi)^{1/3} n^{1/3}
+    T y = inv_cbrt(n);                                 // n^{-1/3}
+    T rs = T(0.62035049089940001667) * y;              // (3/(4 pi n))^{1/3}
+    T ex = T(-0.73855876638202240587) * n * y * y;     // -(3/4)(3/pi)^{1/3} n^{1/3}
     T ec, vc;
     if (rs >= T(1)) {
         T sq = sqrt(rs);
