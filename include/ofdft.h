@@ -220,6 +220,38 @@ ofdft_status ofdft_tfunc_eval(long long n, const double *t, double *out);
 
 void ofdft_destroy(ofdft_ctx *ctx);
 
+/*
+ * Allocation-free energy and potential (the paper has no counterpart; this
+ * exists for callers that must not allocate device memory: latency-critical
+ * loops, where cudaMalloc may synchronise the whole GPU, and programs whose
+ * device memory is owned by another allocator).  It computes what
+ * ofdft_setup + ofdft_energy_potential compute (F_tot and its terms, the
+ * pressure terms, v = dF/dn at n = phi^2), in FP64, with the same kernels,
+ * but every device scratch buffer is carved from one fixed array compiled
+ * into the library: about 2.4 MB that each GPU loading the library holds
+ * until the process exits.  The call allocates no memory, on the device or
+ * the host.
+ *  cell[9], grid[3], nat, ions, Z, T_kelvin, functional: as ofdft_setup.
+ *  xc, rc: as ofdft_params.
+ *  phi_dev  device pointer, N doubles (input; not modified).
+ *  v_dev    device pointer, N doubles (output potential).
+ *  E        host output (may be NULL).
+ *  stream   cudaStream_t to run on, or NULL for the default stream; the call
+ *           returns after the stream has finished its work.
+ * Limits: each grid edge even, {2,3,5}-smooth and at most 64;
+ * nx*ny*nz <= 32768; 1 <= nat <= 64.  Anything larger returns OFDFT_EINVAL.
+ * The first call on a device does a one-time set-up on the current device
+ * (looks up the array's device address, uploads the temperature table) and
+ * should come before any stream capture.  All calls share the array and it
+ * keeps the last call's contents: calls that overlap on the GPU (from other
+ * threads or streams) race, so serialise them.
+ */
+ofdft_status ofdft_energy_potential_static(const double cell[9], const int grid[3], int nat,
+                                           const double *ions, const double *Z, double T_kelvin,
+                                           int functional, int xc, double rc,
+                                           const double *phi_dev, double *v_dev,
+                                           ofdft_energy *E, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

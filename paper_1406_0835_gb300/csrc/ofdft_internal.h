@@ -73,6 +73,8 @@ constexpr int kTfSize = kTfPanels * kTfFuncs * kTfNc;
 
 // Build the table on the host (FP64 monomial coefficients per panel).
 const std::vector<double> &tfunc_table_host();
+// The same table written into caller storage of kTfSize doubles.
+void tfunc_table_fill(double *tab);
 
 // Functional selector and constants for the enhancement factors.
 struct FuncParams {

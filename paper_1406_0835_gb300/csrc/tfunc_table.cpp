@@ -201,10 +201,13 @@ void tfuncs(double t, double f[4])
     f[3] = th1 / zeta;
 }
 
-std::vector<double> build_table()
+}  // namespace
+
+// Fill tab[kTfSize] (no allocation: node values and fits live on the stack).
+void tfunc_table_fill(double *tab)
 {
     const int d = kTfDeg, nc = kTfNc;
-    std::vector<double> tab((size_t)kTfSize, 0.0);
+    for (int i = 0; i < kTfSize; ++i) tab[i] = 0.0;
     double un[nc];
     for (int k = 0; k < nc; ++k) un[k] = std::cos(kPi * (k + 0.5) / nc);
     // monomial coefficients of Chebyshev polynomials T_0..T_d
@@ -242,6 +245,14 @@ std::vector<double> build_table()
             }
         }
     }
+}
+
+namespace {
+
+std::vector<double> build_table()
+{
+    std::vector<double> tab((size_t)kTfSize, 0.0);
+    tfunc_table_fill(tab.data());
     return tab;
 }
 

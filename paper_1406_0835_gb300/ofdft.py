@@ -81,6 +81,11 @@ SIGNATURES = {
     "ofdft_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ofdft_tfunc_eval": (ctypes.c_int, [ctypes.c_longlong, _P, _P]),
     "ofdft_destroy": (None, [ctypes.c_void_p]),
+    "ofdft_energy_potential_static": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                     _P, _P, ctypes.c_double, ctypes.c_int,
+                                                     ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                                     ctypes.c_void_p, ctypes.POINTER(Energy),
+                                                     ctypes.c_void_p]),
 }
 
 
@@ -317,3 +322,28 @@ class Context:
 
     def kernel_launches(self):
         return ofdft_kernel_launches(self.ctx)
+
+
+def ofdft_energy_potential_static(cell, grid, ions, Z, T_kelvin, functional, phi_dev, v_dev,
+                                  xc=True, rc=0.25, stream=None):
+    """Allocation-free evaluation for callers that cannot allocate device
+    memory: phi_dev and v_dev are device addresses (ints) of N doubles the
+    caller owns; the library's fixed scratch array does the rest.  Limits:
+    edges <= 64, N <= 32768, nat <= 64 (larger raises OFDFT_EINVAL)."""
+    lib = load()
+    cell = _f64(cell).reshape(-1)
+    if cell.size == 3:
+        cell = np.diag(cell).reshape(-1)
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    ions = _f64(ions, (-1, 3))
+    Z = _f64(Z, (-1,))
+    f = FUNCTIONALS[functional] if isinstance(functional, str) else int(functional)
+    E = Energy()
+    st = lib.ofdft_energy_potential_static(_ptr(cell), g, ions.shape[0], _ptr(ions), _ptr(Z),
+                                           float(T_kelvin), f, int(bool(xc)), float(rc),
+                                           ctypes.c_void_p(int(phi_dev)), ctypes.c_void_p(int(v_dev)),
+                                           ctypes.byref(E), stream)
+    if st != 0:
+        raise OfdftError(st, "static path: edges even, {2,3,5}-smooth, <= 64; "
+                             "nx*ny*nz <= 32768; 1 <= nat <= 64; valid cell, T, functional")
+    return E.as_dict()
