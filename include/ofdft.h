@@ -88,10 +88,11 @@ typedef struct {
 } ofdft_energy;
 
 typedef struct {
-    int iterations;   /* CG iterations */
-    int evaluations;  /* energy+potential evaluations */
-    double gnorm;     /* final ||dF/dphi|| = (dV sum g^2)^{1/2}, g = 2 phi (v - mu) */
-    int status;       /* ofdft_status of the minimisation */
+    int iterations;      /* CG iterations (all precisions) */
+    int evaluations;     /* energy+potential evaluations (all precisions) */
+    double gnorm;        /* final ||dF/dphi|| = (dV sum g^2)^{1/2}, g = 2 phi (v - mu) */
+    int status;          /* ofdft_status of the minimisation */
+    int evaluations_lo;  /* of which in FP32 (OFDFT_MIXED contexts) */
 } ofdft_stats;
 
 typedef struct {
@@ -144,6 +145,10 @@ ofdft_status ofdft_energy_potential(ofdft_ctx *ctx, const double *phi,
  * norm-preserving rotations, derivative line search; stops when
  * ||dF/dphi|| < gtol or after maxit iterations (OFDFT_ENOCONV).
  * Starts from the context's current phi and leaves the minimiser there.
+ * The whole minimisation runs on the device (one CUDA graph launch; the host
+ * reads the result once).  OFDFT_MIXED contexts first iterate in FP32 until
+ * the single-precision floor stalls ||g||, then continue in FP64 to gtol, so
+ * the result meets the same tolerance as an FP64 context.
  */
 ofdft_status ofdft_minimize(ofdft_ctx *ctx, double gtol, int maxit,
                             ofdft_energy *E, ofdft_stats *stats);

@@ -1,8 +1,16 @@
 // C ABI of libofdft (include/ofdft.h): context, evaluation pipeline, CG
-// minimiser, forces, pressure and MD driver.  Host code only orders kernels
-// on the context's stream and reads back a handful of reduced scalars.
+// minimiser, forces, pressure and MD driver.
+//
+// A minimisation runs entirely on the device: the vector kernels read their
+// scalars from a CgState in device memory, single-thread controller kernels
+// update it, and the two loops (CG iterations, line-search trials) are CUDA
+// graph conditional WHILE nodes, so one graph launch performs a whole
+// minimisation without host synchronisation.  With OFDFT_DEBUG_SYNC=1 or an
+// active kernel timer the same kernel sequence is driven from the host.
 #include <math.h>
+#include <stddef.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -24,15 +32,25 @@ const double kMassH = 1.00794 * 1822.888486209;
 
 std::string g_setup_error;
 
-struct Scal {
-    double v[24];
+// Working fields of one precision.
+struct FieldSet {
+    bool valid = false;
+    void *phi = nullptr, *phit = nullptr, *dhat = nullptr, *g = nullptr, *gprev = nullptr,
+         *d = nullptr, *v = nullptr, *vt = nullptr, *vpart = nullptr;
+    void *spec = nullptr;      // four half spectra, one allocation
+    size_t spec_stride = 0;    // elements between spectra
+    void *vext = nullptr, *tab = nullptr;
+    void *tw[3] = {nullptr, nullptr, nullptr};
+    FftAxis ax[3];
+    CgState *cs = nullptr;     // device CG state
+    cudaGraphExec_t graph = nullptr;
 };
 
 }  // namespace
 
 struct ofdft_ctx {
     int dev = 0;
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr, cap2 = nullptr;
     bool own_stream = false;
     GridInfo g{};
     int nat = 0;
@@ -43,25 +61,20 @@ struct ofdft_ctx {
     int xc = 1;
     int precision = 0;
     double Ne = 0.0;
-    FftAxis ax[2][3];           // [precision 0 = double, 1 = float][x, y, z]
-    void *tw[2][3] = {{nullptr}};
-    // fields (sized for double)
-    void *phi = nullptr, *phit = nullptr, *dhat = nullptr, *gv = nullptr, *gprev = nullptr,
-         *d = nullptr, *v = nullptr, *vt = nullptr, *vpart = nullptr, *phiprev = nullptr;
-    void *spec[4] = {nullptr, nullptr, nullptr, nullptr};
-    void *vext[2] = {nullptr, nullptr};
-    void *tab[2] = {nullptr, nullptr};
-    double *part = nullptr;
+    FieldSet f[2];              // [0] FP64 (always), [1] FP32 (mixed contexts)
+    double *phiprev = nullptr;  // FP64 density history for MD extrapolation
+    double *part = nullptr;     // reduction partials, fixed size
     size_t part_len = 0;
-    double *scal = nullptr;
-    double *scal_h = nullptr;
+    double *scal = nullptr;     // device scalars outside a minimisation
+    double *scal_h = nullptr;   // pinned host copy
+    CgState *cs_h = nullptr;    // pinned host mirror of a CgState
     // ions
     double *Rd = nullptr, *Zd = nullptr, *Fd = nullptr, *Vd = nullptr, *Md = nullptr, *nh = nullptr;
     double2 *px = nullptr, *py = nullptr, *pz = nullptr;
     double *fpart = nullptr;
     size_t fpart_len = 0;
     // Ewald
-    double *Gv = nullptr, *wG = nullptr, *eion = nullptr, *ewF = nullptr, *ewpart = nullptr, *Ld = nullptr;
+    double *Gv = nullptr, *wG = nullptr, *eion = nullptr, *ewF = nullptr, *ewpart = nullptr;
     double2 *Se = nullptr;
     int nGe = 0;
     double ew_alpha = 0.0, ew_rcut = 0.0;
@@ -75,6 +88,8 @@ struct ofdft_ctx {
     int md_thermo = 0;
     long long launches = 0;
     std::string err;
+    bool debug_sync = false;    // OFDFT_DEBUG_SYNC=1: check every launch, no graphs
+    bool use_graphs = true;     // OFDFT_NO_GRAPHS=1: host-driven loops
     // kernel timer (diagnostics)
     int timer_id = 0;
     std::vector<cudaEvent_t> tev;
@@ -83,10 +98,10 @@ struct ofdft_ctx {
 
 namespace {
 
-#define CK(call)                                                                 \
-    do {                                                                         \
-        cudaError_t e_ = (call);                                                 \
-        if (e_ != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e_), #call); \
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e_), #call);     \
     } while (0)
 
 ofdft_status fail(ofdft_ctx *c, ofdft_status s, const char *msg, const char *where = nullptr)
@@ -98,6 +113,25 @@ ofdft_status fail(ofdft_ctx *c, ofdft_status s, const char *msg, const char *whe
     return s;
 }
 
+// With OFDFT_DEBUG_SYNC=1 every launch is followed by a stream synchronisation
+// and an error check that names the kernel.
+ofdft_status dbg(ofdft_ctx *c, const char *what)
+{
+    if (!c->debug_sync) return OFDFT_OK;
+    cudaError_t e = cudaPeekAtLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), what);
+    }
+    return OFDFT_OK;
+}
+
+#define DBG(name)                                              \
+    do {                                                       \
+        if (dbg(c, name) != OFDFT_OK) return OFDFT_EDEVICE;    \
+    } while (0)
+
 bool smooth_even(int n)
 {
     if (n < 8 || n > 512 || (n & 1)) return false;
@@ -107,7 +141,7 @@ bool smooth_even(int n)
     return m == 1;
 }
 
-FftAxis make_axis(int n)
+FftAxis make_axis(int n, const void *tw)
 {
     FftAxis a{};
     a.n = n;
@@ -122,10 +156,11 @@ FftAxis make_axis(int n)
         }
     }
     a.nst = k;
+    a.tw = tw;
     return a;
 }
 
-template <typename T> ofdft_status upload_twiddles(ofdft_ctx *c, int prec, int axis, int n)
+template <typename T> ofdft_status upload_twiddles(ofdft_ctx *c, FieldSet &f, int axis, int n)
 {
     std::vector<cplx<T>> w(n);
     for (int m = 0; m < n; ++m) {
@@ -133,20 +168,9 @@ template <typename T> ofdft_status upload_twiddles(ofdft_ctx *c, int prec, int a
         w[m].x = (T)cosl(ang);
         w[m].y = (T)sinl(ang);
     }
-    CK(cudaMalloc(&c->tw[prec][axis], n * sizeof(cplx<T>)));
-    CK(cudaMemcpy(c->tw[prec][axis], w.data(), n * sizeof(cplx<T>), cudaMemcpyHostToDevice));
-    c->ax[prec][axis] = make_axis(n);
-    c->ax[prec][axis].tw = c->tw[prec][axis];
-    return OFDFT_OK;
-}
-
-ofdft_status ensure_part(ofdft_ctx *c, size_t n)
-{
-    if (n <= c->part_len) return OFDFT_OK;
-    if (c->part) cudaFree(c->part);
-    c->part = nullptr;
-    CK(cudaMalloc(&c->part, n * sizeof(double)));
-    c->part_len = n;
+    CK(cudaMalloc(&f.tw[axis], n * sizeof(cplx<T>)));
+    CK(cudaMemcpy(f.tw[axis], w.data(), n * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+    f.ax[axis] = make_axis(n, f.tw[axis]);
     return OFDFT_OK;
 }
 
@@ -158,12 +182,9 @@ ofdft_status sync_read(ofdft_ctx *c, int n)
     return OFDFT_OK;
 }
 
-// ------------------------------------------------------------ evaluation
-// Scalar block after an evaluation: [0] E_H [1] E_loc [2] P_loc,
-// [3..8] GGA pointwise partials, [9..17] final-stage partials.
 enum TimerId { TM_ZGGA = 1, TM_XGRAD = 2, TM_XDIV = 3, TM_Y = 4, TM_ZFWD = 5, TM_ZFINAL = 6, TM_XHL = 7 };
 
-// Event pair around a launch of the selected kernel class.
+// Event pair around a launch of the selected kernel class (host-driven mode only).
 struct TimerScope {
     ofdft_ctx *c;
     bool on;
@@ -187,90 +208,17 @@ struct TimerScope {
     }
 };
 
+// ------------------------------------------------------------ evaluation
+// Sums written by one evaluation (18 doubles): [0] E_H [1] E_loc [2] P_loc,
+// [3..8] GGA pointwise sums, [9..17] final-stage sums (F_s, TS, F_xc,
+// n df/dn - f, -, n(v_xc - eps), phi^2 v, phi^2, dE/dtheta).
 struct EvalScalars {
     double EH, Eloc, Ploc, FS, TS, FXC, PS, WG, PXC, PHI2V, PHI2, DTH;
 };
 
-template <typename T>
-ofdft_status evaluate(ofdft_ctx *c, T *ph, const T *phi0, const T *dh, double cth, double sth,
-                      T *vout, bool keep_nG, EvalScalars &es)
+EvalScalars unpack_sums(const double *h, bool fttf)
 {
-    const int pi = sizeof(T) == 8 ? 0 : 1;
-    const GridInfo &g = c->g;
-    const FftAxis &ax = c->ax[pi][0], &ay = c->ax[pi][1], &az = c->ax[pi][2];
-    cudaStream_t st = c->st;
-    typedef cplx<T> C;
-    C *s0 = (C *)c->spec[0], *s1 = (C *)c->spec[1], *s2 = (C *)c->spec[2], *s3 = (C *)c->spec[3];
-    const C *vext = (const C *)c->vext[pi];
-    const T *tab = (const T *)c->tab[pi];
-    const long long NH = s1 - s0;          // field stride of the spectrum block, in elements
-    const bool fttf = c->fp.kind == 0;
-    // part regions: A (x pass, 3 q), B (zgga, 6 q), C (zfinal, 9 q)
-    int ntk = (g.K + 7) / 8;
-    int nbx = g.ny * ntk;
-    long long npairs = (long long)g.nx * g.ny / 2;
-    size_t need = (size_t)3 * nbx + (size_t)15 * (size_t)npairs + 64;
-    if (ensure_part(c, need) != OFDFT_OK) return OFDFT_ENOMEM;
-    double *pA = c->part, *pB = pA + 3 * nbx, *pC = pB + 6 * npairs;
-    {
-        TimerScope ts(c, TM_ZFWD);
-        if (phi0) launch_zfwd<T>(g, az, 2, nullptr, phi0, dh, (T)cth, (T)sth, ph, s0, st);
-        else launch_zfwd<T>(g, az, 1, nullptr, ph, nullptr, T(0), T(0), nullptr, s0, st);
-    }
-    {
-        TimerScope ts(c, TM_Y);
-        launch_ypass<T>(g, ay, false, s0, 1, NH, st);
-    }
-    int nbz;
-    if (fttf) {
-        {
-            TimerScope ts(c, TM_XHL);
-            launch_xhl<T>(g, ax, s0, vext, keep_nG ? s1 : nullptr, 1, pA, st);
-        }
-        {
-            TimerScope ts(c, TM_Y);
-            launch_ypass<T>(g, ay, true, s0, 1, NH, st);
-        }
-        TimerScope ts(c, TM_ZFINAL);
-        nbz = launch_zfinal<T>(g, az, true, s0, nullptr, ph, phi0, dh, (T)cth, (T)sth, (T)c->T, c->fp,
-                               tab, c->xc, vout, pC, st);
-        c->launches += 5;
-    } else {
-        {
-            TimerScope ts(c, TM_XGRAD);
-            launch_xgrad<T>(g, ax, s0, vext, s1, s2, s3, pA, st);
-        }
-        {
-            TimerScope ts(c, TM_Y);
-            launch_ypass<T>(g, ay, true, s1, 3, NH, st);
-        }
-        {
-            TimerScope ts(c, TM_ZGGA);
-            launch_zgga<T>(g, az, s1, s2, s3, ph, (T)c->T, c->fp, tab, c->xc, (T *)c->vpart, pB, st);
-        }
-        {
-            TimerScope ts(c, TM_Y);
-            launch_ypass<T>(g, ay, false, s1, 3, NH, st);
-        }
-        {
-            TimerScope ts(c, TM_XDIV);
-            launch_xdiv<T>(g, ax, s0, vext, s1, s2, s3, st);
-        }
-        {
-            TimerScope ts(c, TM_Y);
-            launch_ypass<T>(g, ay, true, s1, 1, NH, st);
-        }
-        TimerScope ts(c, TM_ZFINAL);
-        nbz = launch_zfinal<T>(g, az, false, s1, (const T *)c->vpart, ph, phi0, dh, (T)cth, (T)sth,
-                               (T)c->T, c->fp, tab, c->xc, vout, pC, st);
-        c->launches += 9;
-    }
-    launch_reduce(pA, nbx, 3, c->scal, st);
-    if (!fttf) launch_reduce(pB, nbz, 6, c->scal + 3, st);
-    launch_reduce(pC, nbz, 9, c->scal + 9, st);
-    c->launches += fttf ? 2 : 3;
-    if (sync_read(c, 18) != OFDFT_OK) return OFDFT_EDEVICE;
-    const double *h = c->scal_h;
+    EvalScalars es;
     es.EH = h[0];
     es.Eloc = h[1];
     es.Ploc = h[2];
@@ -284,7 +232,110 @@ ofdft_status evaluate(ofdft_ctx *c, T *ph, const T *phi0, const T *dh, double ct
     es.PHI2V = h[15];
     es.PHI2 = h[16];
     es.DTH = h[17];
-    double chk = es.EH + es.Eloc + es.FS + es.FXC + es.PHI2V + es.DTH;
+    return es;
+}
+
+int eval_kernel_count(const ofdft_ctx *c) { return c->fp.kind == 0 ? 7 : 12; }
+
+// Enqueue one energy + potential evaluation at ph (or, with phi0 and dh, at the
+// trial phi0 cos + dh sin written into ph; angles from csd if given).  Sums go
+// to sums[0..17].  No synchronisation.
+template <typename T>
+ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const T *dh, double cth,
+                          double sth, const double *csd, T *vout, bool keep_nG, double *sums)
+{
+    const GridInfo &g = c->g;
+    const FftAxis &ax = f.ax[0], &ay = f.ax[1], &az = f.ax[2];
+    cudaStream_t st = c->st;
+    typedef cplx<T> C;
+    C *s0 = (C *)f.spec;
+    const long long fs = (long long)f.spec_stride;
+    C *s1 = s0 + fs, *s2 = s1 + fs, *s3 = s2 + fs;
+    const C *vext = (const C *)f.vext;
+    const T *tab = (const T *)f.tab;
+    const bool fttf = c->fp.kind == 0;
+    const int ntk = (g.K + 7) / 8, nbx = g.ny * ntk;
+    const long long npairs = (long long)g.nx * g.ny / 2;
+    double *pA = c->part, *pB = pA + 3 * nbx, *pC = pB + 6 * npairs;
+    {
+        TimerScope ts(c, TM_ZFWD);
+        if (phi0) launch_zfwd<T>(g, az, 2, nullptr, phi0, dh, (T)cth, (T)sth, csd, ph, s0, st);
+        else launch_zfwd<T>(g, az, 1, nullptr, ph, nullptr, T(0), T(0), nullptr, nullptr, s0, st);
+    }
+    DBG("k_zfwd");
+    {
+        TimerScope ts(c, TM_Y);
+        launch_ypass<T>(g, ay, false, s0, 1, fs, st);
+    }
+    DBG("k_ypass fwd");
+    int nbz;
+    if (fttf) {
+        {
+            TimerScope ts(c, TM_XHL);
+            launch_xhl<T>(g, ax, s0, vext, keep_nG ? s1 : nullptr, 1, pA, st);
+        }
+        DBG("k_xhl");
+        {
+            TimerScope ts(c, TM_Y);
+            launch_ypass<T>(g, ay, true, s0, 1, fs, st);
+        }
+        DBG("k_ypass inv");
+        TimerScope ts(c, TM_ZFINAL);
+        nbz = launch_zfinal<T>(g, az, true, s0, nullptr, ph, phi0, dh, (T)cth, (T)sth, csd, (T)c->T,
+                               c->fp, tab, c->xc, vout, pC, st);
+    } else {
+        {
+            TimerScope ts(c, TM_XGRAD);
+            launch_xgrad<T>(g, ax, s0, vext, s1, s2, s3, pA, st);
+        }
+        DBG("k_xgrad");
+        {
+            TimerScope ts(c, TM_Y);
+            launch_ypass<T>(g, ay, true, s1, 3, fs, st);
+        }
+        DBG("k_ypass inv x3");
+        {
+            TimerScope ts(c, TM_ZGGA);
+            launch_zgga<T>(g, az, s1, s2, s3, ph, (T)c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, st);
+        }
+        DBG("k_zgga");
+        {
+            TimerScope ts(c, TM_Y);
+            launch_ypass<T>(g, ay, false, s1, 3, fs, st);
+        }
+        DBG("k_ypass fwd x3");
+        {
+            TimerScope ts(c, TM_XDIV);
+            launch_xdiv<T>(g, ax, s0, vext, s1, s2, s3, st);
+        }
+        DBG("k_xdiv");
+        {
+            TimerScope ts(c, TM_Y);
+            launch_ypass<T>(g, ay, true, s1, 1, fs, st);
+        }
+        DBG("k_ypass inv x1");
+        TimerScope ts(c, TM_ZFINAL);
+        nbz = launch_zfinal<T>(g, az, false, s1, (const T *)f.vpart, ph, phi0, dh, (T)cth, (T)sth, csd,
+                               (T)c->T, c->fp, tab, c->xc, vout, pC, st);
+    }
+    DBG("k_zfinal");
+    launch_reduce(pA, nbx, 3, sums, st);
+    if (!fttf) launch_reduce(pB, nbz, 6, sums + 3, st);
+    launch_reduce(pC, nbz, 9, sums + 9, st);
+    DBG("k_reduce");
+    c->launches += eval_kernel_count(c);
+    return OFDFT_OK;
+}
+
+// One evaluation outside a minimisation, read back to the host.
+template <typename T>
+ofdft_status evaluate(ofdft_ctx *c, FieldSet &f, T *ph, T *vout, bool keep_nG, EvalScalars &es)
+{
+    ofdft_status s = enqueue_eval<T>(c, f, ph, nullptr, nullptr, 1.0, 0.0, nullptr, vout, keep_nG, c->scal);
+    if (s != OFDFT_OK) return s;
+    if (sync_read(c, 18) != OFDFT_OK) return OFDFT_EDEVICE;
+    es = unpack_sums(c->scal_h, c->fp.kind == 0);
+    double chk = es.EH + es.Eloc + es.FS + es.FXC + es.PHI2V;
     if (!isfinite(chk)) return fail(c, OFDFT_ENUMERIC, "non-finite energy or potential");
     return OFDFT_OK;
 }
@@ -346,28 +397,25 @@ ofdft_status setup_ewald(ofdft_ctx *c)
     CK(cudaMalloc(&c->ewpart, std::max(1, nb) * sizeof(double)));
     CK(cudaMalloc(&c->eion, c->nat * sizeof(double)));
     CK(cudaMalloc(&c->ewF, 3 * c->nat * sizeof(double)));
-    CK(cudaMalloc(&c->Ld, 3 * sizeof(double)));
     if (!Gv.empty()) {
         CK(cudaMemcpy(c->Gv, Gv.data(), Gv.size() * sizeof(double), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->wG, wG.data(), wG.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
-    CK(cudaMemcpy(c->Ld, L, 3 * sizeof(double), cudaMemcpyHostToDevice));
     return OFDFT_OK;
 }
 
-// Recompute v_ext(G) (both precisions) and the Ewald energy and forces from Rd.
+// Recompute v_ext(G) (every field set) and the Ewald energy and forces from Rd.
 ofdft_status update_ions(ofdft_ctx *c)
 {
     const GridInfo &g = c->g;
     cudaStream_t st = c->st;
     launch_phases(g, c->nat, c->Rd, c->px, c->py, c->pz, st);
-    launch_vext<double>(g, c->nat, c->Zd, c->px, c->py, c->pz, (double2 *)c->vext[0], st);
-    if (c->precision == OFDFT_MIXED)
-        launch_vext<float>(g, c->nat, c->Zd, c->px, c->py, c->pz, (float2 *)c->vext[1], st);
+    launch_vext<double>(g, c->nat, c->Zd, c->px, c->py, c->pz, (double2 *)c->f[0].vext, st);
+    if (c->f[1].valid) launch_vext<float>(g, c->nat, c->Zd, c->px, c->py, c->pz, (float2 *)c->f[1].vext, st);
     double L[3] = {g.Lx, g.Ly, g.Lz};
     launch_ewald_real(c->nat, c->Rd, c->Zd, L, c->ew_alpha, c->ew_rcut, c->ew_nimg, c->eion, c->ewF, st);
     int nb = launch_ewald_recip(c->nat, c->Rd, c->Zd, c->nGe, c->Gv, c->wG, c->Se, c->ewpart, c->ewF, st);
-    c->launches += 5 + (c->precision == OFDFT_MIXED);
+    c->launches += 5 + (c->f[1].valid ? 1 : 0);
     std::vector<double> e(c->nat + nb);
     CK(cudaMemcpyAsync(e.data(), c->eion, c->nat * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(e.data() + c->nat, c->ewpart, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -388,195 +436,268 @@ ofdft_status update_ions(ofdft_ctx *c)
 }
 
 // ------------------------------------------------------------------- CG
-template <typename T> ofdft_status normalize_phi(ofdft_ctx *c, T *x)
-{
-    if (ensure_part(c, 4096) != OFDFT_OK) return OFDFT_ENOMEM;
-    int nb = launch_sumsq<T>(c->g.N, x, c->part, c->st);
-    launch_reduce(c->part, nb, 1, c->scal, c->st);
-    c->launches += 2;
-    if (sync_read(c, 1) != OFDFT_OK) return OFDFT_EDEVICE;
-    double ss = c->scal_h[0] * c->g.dV;
-    if (!(ss > 0.0) || !isfinite(ss)) return fail(c, OFDFT_ENUMERIC, "phi has zero or non-finite norm");
-    launch_scale<T>(c->g.N, x, sqrt(c->Ne / ss), c->st);
-    c->launches++;
-    return OFDFT_OK;
-}
-
-struct LsResult {
-    bool ok;
-    double theta;
-    int nevals;
-    EvalScalars es;
-};
-
+// Kernel sequence of a minimisation on field set f; with use_cond the
+// controllers drive the graph's conditional handles.
 template <typename T>
-ofdft_status line_search(ofdft_ctx *c, double D0, double theta1, LsResult &r)
-{
-    const double ls_tol = 0.1;
-    const int max_ls = 20;
-    double lo = 0.0, Dlo = D0, hi = -1.0, Dhi = 0.0, pa = 0.0, Da = D0, th = theta1;
-    r.ok = false;
-    r.nevals = 0;
-    for (int k = 0; k < max_ls; ++k) {
-        EvalScalars es;
-        ofdft_status s = evaluate<T>(c, (T *)c->phit, (const T *)c->phi, (const T *)c->dhat, cos(th),
-                                     sin(th), (T *)c->vt, false, es);
-        r.nevals++;
-        if (s != OFDFT_OK) return s;
-        double D = c->g.dV * es.DTH;
-        if (fabs(D) <= ls_tol * fabs(D0)) {
-            r.ok = true;
-            r.theta = th;
-            r.es = es;
-            return OFDFT_OK;
-        }
-        if (D < 0.0) {
-            lo = th;
-            Dlo = D;
-        } else {
-            hi = th;
-            Dhi = D;
-        }
-        double nxt;
-        if (hi < 0.0) {
-            nxt = 4.0 * th;
-            if (D > Da) {
-                double sec = th - D * (th - pa) / (D - Da);
-                nxt = std::min(sec, 4.0 * th);
-            }
-            nxt = std::max(nxt, 1.1 * th);
-            pa = th;
-            Da = D;
-        } else {
-            nxt = lo - Dlo * (hi - lo) / (Dhi - Dlo);
-            double w = hi - lo;
-            nxt = std::min(std::max(nxt, lo + 0.01 * w), hi - 0.01 * w);
-        }
-        th = std::min(nxt, 1.5);
-    }
-    if (lo > 0.0) {
-        EvalScalars es;
-        ofdft_status s = evaluate<T>(c, (T *)c->phit, (const T *)c->phi, (const T *)c->dhat, cos(lo),
-                                     sin(lo), (T *)c->vt, false, es);
-        r.nevals++;
-        if (s != OFDFT_OK) return s;
-        r.ok = true;
-        r.theta = lo;
-        r.es = es;
-    }
-    return OFDFT_OK;
-}
-
-template <typename T>
-ofdft_status minimize_T(ofdft_ctx *c, double gtol, int maxit, ofdft_stats &stats, EvalScalars &es_out)
+ofdft_status enqueue_prologue(ofdft_ctx *c, FieldSet &f, cudaGraphConditionalHandle outer, int use_cond)
 {
     const long long N = c->g.N;
-    const double dV = c->g.dV;
     cudaStream_t st = c->st;
-    stats.iterations = 0;
-    stats.evaluations = 0;
-    stats.gnorm = 0.0;
-    stats.status = OFDFT_OK;
-    ofdft_status s = normalize_phi<T>(c, (T *)c->phi);
-    if (s != OFDFT_OK) return s;
-    EvalScalars es;
-    s = evaluate<T>(c, (T *)c->phi, nullptr, nullptr, 1.0, 0.0, (T *)c->v, false, es);
-    stats.evaluations = 1;
-    if (s != OFDFT_OK) return s;
-    if (ensure_part(c, 8 * 1216) != OFDFT_OK) return OFDFT_ENOMEM;
-    double mu = es.PHI2V / es.PHI2;
-    int nb = launch_cg_grad<T>(N, (const T *)c->phi, (const T *)c->v, mu, (T *)c->gv, nullptr, c->part, st);
-    launch_reduce(c->part, nb, 2, c->scal, st);
-    c->launches += 2;
-    if (sync_read(c, 2) != OFDFT_OK) return OFDFT_EDEVICE;
-    double gg = c->scal_h[0], ggprev = 0.0;
-    double gnorm = sqrt(dV * gg);
-    bool have_prev = false;
-    double theta_prev = 0.05;
-    int it = 0;
-    ofdft_status status = OFDFT_ENOCONV;
-    while (it < maxit) {
-        if (gnorm < gtol) {
-            status = OFDFT_OK;
-            break;
-        }
-        double beta = 0.0;
-        if (have_prev) beta = std::max(0.0, (gg - c->scal_h[1]) / ggprev);
-        nb = launch_cg_dir<T>(N, (const T *)c->gv, (T *)c->d, have_prev ? beta : 0.0,
-                              (const T *)c->phi, c->part, st);
-        launch_reduce(c->part, nb, 5, c->scal + 4, st);
-        c->launches += 2;
-        if (sync_read(c, 9) != OFDFT_OK) return OFDFT_EDEVICE;
-        double sphd = c->scal_h[4], sdd = c->scal_h[5], sdg = c->scal_h[6], spp = c->scal_h[7],
-               spg = c->scal_h[8];
-        double c1 = sphd / spp;
-        double dg = sdg - c1 * spg;
-        double dd = sdd - 2.0 * c1 * sphd + c1 * c1 * spp;
-        int restart = dg >= 0.0;
-        double c2 = restart ? sqrt(spp / gg) : sqrt(spp / dd);
-        nb = launch_cg_dhat<T>(N, (const T *)c->gv, (T *)c->d, (const T *)c->phi, (const T *)c->v, c1, c2,
-                               restart, (T *)c->dhat, c->part, st);
-        launch_reduce(c->part, nb, 1, c->scal, st);
-        c->launches += 2;
-        if (sync_read(c, 1) != OFDFT_OK) return OFDFT_EDEVICE;
-        double D0 = dV * c->scal_h[0];
-        LsResult ls;
-        s = line_search<T>(c, D0, theta_prev, ls);
-        stats.evaluations += ls.nevals;
-        if (s != OFDFT_OK) return s;
-        if (!ls.ok) {
-            if (!have_prev) {
-                status = OFDFT_ENOCONV;
-                break;
-            }
-            have_prev = false;   // restart along steepest descent
-            continue;
-        }
-        theta_prev = ls.theta;
-        std::swap(c->phi, c->phit);
-        std::swap(c->v, c->vt);
-        es = ls.es;
-        std::swap(c->gv, c->gprev);
-        mu = es.PHI2V / es.PHI2;
-        nb = launch_cg_grad<T>(N, (const T *)c->phi, (const T *)c->v, mu, (T *)c->gv, (const T *)c->gprev,
-                               c->part, st);
-        launch_reduce(c->part, nb, 2, c->scal, st);
-        c->launches += 2;
-        if (sync_read(c, 2) != OFDFT_OK) return OFDFT_EDEVICE;
-        ggprev = gg;
-        gg = c->scal_h[0];
-        gnorm = sqrt(dV * gg);
-        have_prev = true;
-        ++it;
-    }
-    if (gnorm < gtol) status = OFDFT_OK;
-    stats.iterations = it;
-    stats.gnorm = gnorm;
-    stats.status = status;
-    es_out = es;
+    CgState *s = f.cs;
+    int nb = launch_sumsq<T>(N, (const T *)f.phi, c->part, st);
+    launch_reduce(c->part, nb, 1, s->rn, st);
+    launch_ctl_norm(s, st);
+    launch_scale<T>(N, (T *)f.phi, 1.0, &s->scale, st);
+    c->launches += 4;
+    DBG("normalise");
+    ofdft_status r = enqueue_eval<T>(c, f, (T *)f.phi, nullptr, nullptr, 1.0, 0.0, nullptr, (T *)f.v, false, s->ev);
+    if (r != OFDFT_OK) return r;
+    launch_ctl_init(s, st);
+    nb = launch_cg_grad<T>(N, (const T *)f.phi, (const T *)f.v, 0.0, &s->mu, (T *)f.g, nullptr, c->part, st);
+    launch_reduce(c->part, nb, 2, s->rg, st);
+    launch_ctl_grad(s, 1, outer, use_cond, st);
+    c->launches += 4;
+    DBG("cg prologue");
     return OFDFT_OK;
 }
 
-// Final FP64 evaluation at the current phi; for MIXED contexts phi is FP32
-// and is widened into the phit buffer first.
-ofdft_status eval_fp64_at_phi(ofdft_ctx *c, bool keep_nG, EvalScalars &es, double **phi64)
+template <typename T>
+ofdft_status enqueue_direction(ofdft_ctx *c, FieldSet &f, cudaGraphConditionalHandle ls, int use_cond)
 {
-    double *ph = (double *)c->phi;
-    if (c->precision == OFDFT_MIXED) {
-        launch_convert<float, double>(c->g.N, (const float *)c->phi, (double *)c->phit, c->st);
-        c->launches++;
-        ph = (double *)c->phit;
+    const long long N = c->g.N;
+    cudaStream_t st = c->st;
+    CgState *s = f.cs;
+    int nb = launch_cg_dir<T>(N, (const T *)f.g, (T *)f.d, 0.0, &s->beta, (const T *)f.phi, c->part, st);
+    launch_reduce(c->part, nb, 5, s->rd, st);
+    launch_ctl_dir(s, st);
+    nb = launch_cg_dhat<T>(N, (const T *)f.g, (T *)f.d, (const T *)f.phi, (const T *)f.v, 0.0, 0.0, 0,
+                           s->c12r, (T *)f.dhat, c->part, st);
+    launch_reduce(c->part, nb, 1, s->rh, st);
+    launch_ctl_dhat(s, ls, use_cond, st);
+    c->launches += 6;
+    DBG("cg direction");
+    return OFDFT_OK;
+}
+
+template <typename T>
+ofdft_status enqueue_trial(ofdft_ctx *c, FieldSet &f, cudaGraphConditionalHandle ls, int use_cond)
+{
+    CgState *s = f.cs;
+    ofdft_status r = enqueue_eval<T>(c, f, (T *)f.phit, (const T *)f.phi, (const T *)f.dhat, 1.0, 0.0, s->cs,
+                                     (T *)f.vt, false, s->ev);
+    if (r != OFDFT_OK) return r;
+    launch_ctl_ls(s, ls, use_cond, c->st);
+    c->launches += 1;
+    DBG("line search");
+    return OFDFT_OK;
+}
+
+template <typename T>
+ofdft_status enqueue_update(ofdft_ctx *c, FieldSet &f, cudaGraphConditionalHandle outer, int use_cond)
+{
+    const long long N = c->g.N;
+    cudaStream_t st = c->st;
+    CgState *s = f.cs;
+    launch_accept<T>(N, &s->accepted, (T *)f.phi, (const T *)f.phit, (T *)f.v, (const T *)f.vt,
+                     (const T *)f.g, (T *)f.gprev, st);
+    int nb = launch_cg_grad<T>(N, (const T *)f.phi, (const T *)f.v, 0.0, &s->mu, (T *)f.g,
+                               (const T *)f.gprev, c->part, st);
+    launch_reduce(c->part, nb, 2, s->rg, st);
+    launch_ctl_grad(s, 0, outer, use_cond, st);
+    c->launches += 4;
+    DBG("cg update");
+    return OFDFT_OK;
+}
+
+// Add a WHILE conditional node at the capture position of `stream`; returns
+// its body graph.  The handle must belong to the graph being captured.
+ofdft_status add_while(ofdft_ctx *c, cudaStream_t stream, cudaGraphConditionalHandle h, cudaGraph_t *body)
+{
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t gr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(stream, &cst, nullptr, &gr, &deps, &ed, &nd));
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, gr, deps, ed, nd, &p));
+    *body = p.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return OFDFT_OK;
+}
+
+// Capture the whole minimisation of field set f into an executable graph:
+//   prologue; WHILE(outer) { direction; WHILE(ls) { trial }; update }
+// Capture runs on the private stream cap2 (the context's stream may be the
+// legacy stream, which cannot be captured); the bodies of the two loops are
+// captured one after the other into the graphs their nodes own.
+template <typename T> ofdft_status capture_graph(ofdft_ctx *c, FieldSet &f, cudaGraph_t *whole)
+{
+    cudaStream_t cs = c->cap2;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t gr = nullptr;
+    cudaGraphConditionalHandle outer = 0, ls = 0;
+    cudaGraph_t body = nullptr, ls_body = nullptr;
+    ofdft_status r = OFDFT_OK;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &gr, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&outer, gr, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) r = fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph handle");
+    if (r == OFDFT_OK) r = enqueue_prologue<T>(c, f, outer, 1);
+    if (r == OFDFT_OK) r = add_while(c, cs, outer, &body);
+    e = cudaStreamEndCapture(cs, whole);
+    if (r != OFDFT_OK) return r;
+    if (e != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph capture");
+
+    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    e = cudaGraphConditionalHandleCreate(&ls, body, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) r = fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph handle");
+    if (r == OFDFT_OK) r = enqueue_direction<T>(c, f, ls, 1);
+    if (r == OFDFT_OK) r = add_while(c, cs, ls, &ls_body);
+    if (r == OFDFT_OK) r = enqueue_update<T>(c, f, outer, 1);
+    e = cudaStreamEndCapture(cs, &body);
+    if (r != OFDFT_OK) return r;
+    if (e != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph capture (outer body)");
+
+    CK(cudaStreamBeginCaptureToGraph(cs, ls_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    r = enqueue_trial<T>(c, f, ls, 1);
+    e = cudaStreamEndCapture(cs, &ls_body);
+    if (r != OFDFT_OK) return r;
+    if (e != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph capture (line search)");
+    return OFDFT_OK;
+}
+
+template <typename T> ofdft_status build_graph(ofdft_ctx *c, FieldSet &f)
+{
+    cudaStream_t user = c->st;
+    long long before = c->launches;
+    const bool dbg_saved = c->debug_sync;
+    c->st = c->cap2;
+    c->debug_sync = false;
+    cudaGraph_t whole = nullptr;
+    ofdft_status r = capture_graph<T>(c, f, &whole);
+    c->st = user;
+    c->debug_sync = dbg_saved;
+    c->launches = before;
+    if (r == OFDFT_OK) {
+        cudaError_t e = cudaGraphInstantiate(&f.graph, whole, 0);
+        if (e != cudaSuccess) {
+            f.graph = nullptr;
+            r = fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph instantiation");
+        }
     }
-    if (phi64) *phi64 = ph;
-    return evaluate<double>(c, ph, nullptr, nullptr, 1.0, 0.0, (double *)c->vt, keep_nG, es);
+    if (whole) cudaGraphDestroy(whole);
+    return r;
+}
+
+ofdft_status write_config(ofdft_ctx *c, FieldSet &f, double gtol, int maxit, int stagnate)
+{
+    CgState *h = c->cs_h;
+    memset(h, 0, sizeof(CgState));
+    h->gtol = gtol;
+    h->dV = c->g.dV;
+    h->ls_tol = 0.1;
+    h->theta0 = 0.05;
+    h->Ne = c->Ne;
+    h->maxit = maxit;
+    h->max_ls = 20;
+    h->stagnate = stagnate;
+    h->status = OFDFT_OK;
+    CK(cudaMemcpyAsync(f.cs, h, sizeof(CgState), cudaMemcpyHostToDevice, c->st));
+    return OFDFT_OK;
+}
+
+ofdft_status read_state(ofdft_ctx *c, FieldSet &f)
+{
+    CK(cudaMemcpyAsync(c->cs_h, f.cs, sizeof(CgState), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaGetLastError());
+    return OFDFT_OK;
+}
+
+// Minimise on field set f (phi already holds the start).  Adds to the stats
+// and returns the accepted point's evaluation sums.
+template <typename T>
+ofdft_status minimize_T(ofdft_ctx *c, FieldSet &f, double gtol, int maxit, int stagnate,
+                        ofdft_stats &stats, EvalScalars &es)
+{
+    if (write_config(c, f, gtol, maxit, stagnate) != OFDFT_OK) return OFDFT_EDEVICE;
+    const bool graphs = c->use_graphs && !c->debug_sync && c->timer_id == 0;
+    if (graphs) {
+        if (!f.graph) {
+            ofdft_status r = build_graph<T>(c, f);
+            if (r != OFDFT_OK) return r;
+        }
+        CK(cudaGraphLaunch(f.graph, c->st));
+        if (read_state(c, f) != OFDFT_OK) return OFDFT_EDEVICE;
+        // kernels the graph ran: prologue, per outer iteration (direction +
+        // update), per line-search trial (evaluation + controller)
+        const CgState &h = *c->cs_h;
+        c->launches += 8 + eval_kernel_count(c) + (long long)h.nouter * 10 +
+                       (long long)(h.nevals - 1) * (eval_kernel_count(c) + 1);
+    } else {
+        cudaGraphConditionalHandle none = 0;
+        ofdft_status r = enqueue_prologue<T>(c, f, none, 0);
+        if (r != OFDFT_OK) return r;
+        if (read_state(c, f) != OFDFT_OK) return OFDFT_EDEVICE;
+        while (!c->cs_h->done) {
+            if ((r = enqueue_direction<T>(c, f, none, 0)) != OFDFT_OK) return r;
+            do {
+                if ((r = enqueue_trial<T>(c, f, none, 0)) != OFDFT_OK) return r;
+                if (read_state(c, f) != OFDFT_OK) return OFDFT_EDEVICE;
+            } while (c->cs_h->ls_active);
+            if ((r = enqueue_update<T>(c, f, none, 0)) != OFDFT_OK) return r;
+            if (read_state(c, f) != OFDFT_OK) return OFDFT_EDEVICE;
+        }
+    }
+    const CgState &h = *c->cs_h;
+    stats.iterations += h.it;
+    stats.evaluations += h.nevals;
+    stats.gnorm = h.gnorm;
+    stats.status = h.status == kCgStagnated ? OFDFT_OK : h.status;
+    es = unpack_sums(h.ev_acc, c->fp.kind == 0);
+    if (h.status == OFDFT_ENUMERIC) return fail(c, OFDFT_ENUMERIC, "non-finite energy, gradient or norm");
+    return OFDFT_OK;
+}
+
+ofdft_status run_minimize(ofdft_ctx *c, double gtol, int maxit, ofdft_stats &stats, EvalScalars &es)
+{
+    stats = ofdft_stats{};
+    ofdft_status s;
+    if (c->precision == OFDFT_MIXED) {
+        // FP32 CG until converged or stalled at the single-precision floor,
+        // then FP64 CG from there to the requested tolerance
+        launch_convert<double, float>(c->g.N, (const double *)c->f[0].phi, (float *)c->f[1].phi, c->st);
+        c->launches++;
+        ofdft_stats s32{};
+        s = minimize_T<float>(c, c->f[1], gtol, maxit, 1, s32, es);
+        if (s != OFDFT_OK) return s;
+        launch_convert<float, double>(c->g.N, (const float *)c->f[1].phi, (double *)c->f[0].phi, c->st);
+        c->launches++;
+        s = minimize_T<double>(c, c->f[0], gtol, maxit, 0, stats, es);
+        stats.iterations += s32.iterations;
+        stats.evaluations_lo = s32.evaluations;
+        stats.evaluations += s32.evaluations;
+    } else {
+        s = minimize_T<double>(c, c->f[0], gtol, maxit, 0, stats, es);
+    }
+    if (s != OFDFT_OK) return s;
+    fill_energy(c, es, c->last);
+    c->last_valid = true;
+    return stats.status == OFDFT_OK ? OFDFT_OK : (ofdft_status)stats.status;
 }
 
 ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
 {
-    ofdft_status s = eval_fp64_at_phi(c, true, es, nullptr);
+    FieldSet &f = c->f[0];
+    ofdft_status s = evaluate<double>(c, f, (double *)f.phi, (double *)f.vt, true, es);
     if (s != OFDFT_OK) return s;
     const GridInfo &g = c->g;
-    const double2 *nG = (const double2 *)(c->fp.kind == 0 ? c->spec[1] : c->spec[0]);
+    const double2 *nG = (const double2 *)f.spec + (c->fp.kind == 0 ? f.spec_stride : 0);
     size_t need = (size_t)c->nat * 608 * 3 + 16;
     if (need > c->fpart_len) {
         if (c->fpart) cudaFree(c->fpart);
@@ -587,7 +708,6 @@ ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
     int nchunk = launch_lpp_forces<double>(g, c->nat, c->Zd, c->px, c->py, c->pz, nG, c->fpart, c->st);
     launch_force_reduce(c->nat, nchunk, c->fpart, c->Fd, 0, c->st);
     c->launches += 2;
-    // add Ewald forces
     std::vector<double> F(3 * c->nat), Fe(3 * c->nat);
     CK(cudaMemcpyAsync(F.data(), c->Fd, F.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(Fe.data(), c->ewF, Fe.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -598,25 +718,14 @@ ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
     return OFDFT_OK;
 }
 
-ofdft_status run_minimize(ofdft_ctx *c, double gtol, int maxit, ofdft_stats &stats, EvalScalars &es)
+void free_fieldset(FieldSet &f)
 {
-    ofdft_status s;
-    if (c->precision == OFDFT_MIXED) {
-        double gt = std::max(gtol, 1e-5);
-        s = minimize_T<float>(c, gt, maxit, stats, es);
-        if (s != OFDFT_OK) return s;
-        EvalScalars e64;
-        s = eval_fp64_at_phi(c, false, e64, nullptr);
-        stats.evaluations++;
-        if (s != OFDFT_OK) return s;
-        es = e64;
-    } else {
-        s = minimize_T<double>(c, gtol, maxit, stats, es);
-        if (s != OFDFT_OK) return s;
-    }
-    fill_energy(c, es, c->last);
-    c->last_valid = true;
-    return stats.status == OFDFT_OK ? OFDFT_OK : (ofdft_status)stats.status;
+    void *ptrs[] = {f.phi, f.phit, f.dhat, f.g, f.gprev, f.d, f.v, f.vt, f.vpart, f.spec, f.vext, f.tab,
+                    f.tw[0], f.tw[1], f.tw[2], f.cs};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (f.graph) cudaGraphExecDestroy(f.graph);
+    f = FieldSet{};
 }
 
 void free_ctx(ofdft_ctx *c)
@@ -624,35 +733,57 @@ void free_ctx(ofdft_ctx *c)
     if (!c) return;
     cudaSetDevice(c->dev);
     if (c->st) cudaStreamSynchronize(c->st);
-    void *ptrs[] = {c->phi, c->phit, c->dhat, c->gv, c->gprev, c->d, c->v, c->vt, c->vpart, c->phiprev,
-                    c->spec[0], c->vext[0], c->vext[1],
-                    c->tab[0], c->tab[1], c->part, c->scal, c->Rd, c->Zd, c->Fd, c->Vd, c->Md,
-                    c->nh, c->px, c->py, c->pz, c->fpart, c->Gv, c->wG, c->eion, c->ewF, c->ewpart,
-                    c->Ld, c->Se, c->tw[0][0], c->tw[0][1], c->tw[0][2], c->tw[1][0], c->tw[1][1],
-                    c->tw[1][2]};
+    free_fieldset(c->f[0]);
+    free_fieldset(c->f[1]);
+    void *ptrs[] = {c->phiprev, c->part, c->scal, c->Rd, c->Zd, c->Fd, c->Vd, c->Md, c->nh, c->px, c->py,
+                    c->pz, c->fpart, c->Gv, c->wG, c->eion, c->ewF, c->ewpart, c->Se};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->scal_h) cudaFreeHost(c->scal_h);
+    if (c->cs_h) cudaFreeHost(c->cs_h);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    if (c->cap2) cudaStreamDestroy(c->cap2);
     delete c;
+}
+
+template <typename T> ofdft_status alloc_fieldset(ofdft_ctx *c, FieldSet &f)
+{
+    const GridInfo &g = c->g;
+    size_t rb = (size_t)g.N * sizeof(T);
+    size_t cb = ((size_t)g.NH * sizeof(cplx<T>) + 255) & ~(size_t)255;
+    void **fields[] = {&f.phi, &f.phit, &f.dhat, &f.g, &f.gprev, &f.d, &f.v, &f.vt, &f.vpart};
+    for (void **p : fields) CK(cudaMalloc(p, rb));
+    CK(cudaMalloc(&f.spec, 4 * cb));
+    f.spec_stride = cb / sizeof(cplx<T>);
+    CK(cudaMalloc(&f.vext, (size_t)g.NH * sizeof(cplx<T>)));
+    const std::vector<double> &tab = tfunc_table_host();
+    std::vector<T> tt(tab.begin(), tab.end());
+    CK(cudaMalloc(&f.tab, tt.size() * sizeof(T)));
+    CK(cudaMemcpy(f.tab, tt.data(), tt.size() * sizeof(T), cudaMemcpyHostToDevice));
+    int n3[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a)
+        if (upload_twiddles<T>(c, f, a, n3[a]) != OFDFT_OK) return OFDFT_EDEVICE;
+    CK(cudaMalloc(&f.cs, sizeof(CgState)));
+    CK(cudaMemset(f.cs, 0, sizeof(CgState)));
+    f.valid = true;
+    return OFDFT_OK;
 }
 
 ofdft_status alloc_ctx(ofdft_ctx *c)
 {
     const GridInfo &g = c->g;
-    size_t rb = (size_t)g.N * sizeof(double), cb = (size_t)g.NH * sizeof(double2);
-    void **fields[] = {&c->phi, &c->phit, &c->dhat, &c->gv, &c->gprev, &c->d, &c->v, &c->vt, &c->vpart,
-                       &c->phiprev};
-    for (void **f : fields) CK(cudaMalloc(f, rb));
-    // the four half spectra are one allocation: the y pass walks fields 1..3
-    // with a fixed stride
-    CK(cudaMalloc(&c->spec[0], 4 * cb));
-    for (int i = 1; i < 4; ++i) c->spec[i] = (char *)c->spec[0] + i * cb;
-    CK(cudaMalloc(&c->vext[0], cb));
-    if (c->precision == OFDFT_MIXED) CK(cudaMalloc(&c->vext[1], (size_t)g.NH * sizeof(float2)));
+    if (alloc_fieldset<double>(c, c->f[0]) != OFDFT_OK) return OFDFT_ENOMEM;
+    if (c->precision == OFDFT_MIXED && alloc_fieldset<float>(c, c->f[1]) != OFDFT_OK) return OFDFT_ENOMEM;
+    CK(cudaMalloc(&c->phiprev, (size_t)g.N * sizeof(double)));
+    const int ntk = (g.K + 7) / 8;
+    size_t need = (size_t)3 * g.ny * ntk + (size_t)15 * ((size_t)g.nx * g.ny / 2) + 64;
+    need = std::max<size_t>(need, 5 * 1216 + 64);
+    CK(cudaMalloc(&c->part, need * sizeof(double)));
+    c->part_len = need;
     CK(cudaMalloc(&c->scal, 64 * sizeof(double)));
     CK(cudaMallocHost(&c->scal_h, 64 * sizeof(double)));
+    CK(cudaMallocHost(&c->cs_h, sizeof(CgState)));
     const int nat = c->nat;
     CK(cudaMalloc(&c->Rd, 3 * nat * sizeof(double)));
     CK(cudaMalloc(&c->Zd, nat * sizeof(double)));
@@ -663,25 +794,29 @@ ofdft_status alloc_ctx(ofdft_ctx *c)
     CK(cudaMalloc(&c->px, (size_t)nat * g.nx * sizeof(double2)));
     CK(cudaMalloc(&c->py, (size_t)nat * g.ny * sizeof(double2)));
     CK(cudaMalloc(&c->pz, (size_t)nat * g.K * sizeof(double2)));
-    // temperature tables
-    const std::vector<double> &tab = tfunc_table_host();
-    CK(cudaMalloc(&c->tab[0], tab.size() * sizeof(double)));
-    CK(cudaMemcpy(c->tab[0], tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
-    std::vector<float> tabf(tab.begin(), tab.end());
-    CK(cudaMalloc(&c->tab[1], tabf.size() * sizeof(float)));
-    CK(cudaMemcpy(c->tab[1], tabf.data(), tabf.size() * sizeof(float), cudaMemcpyHostToDevice));
-    int n3[3] = {g.nx, g.ny, g.nz};
-    for (int a = 0; a < 3; ++a) {
-        if (upload_twiddles<double>(c, 0, a, n3[a]) != OFDFT_OK) return OFDFT_EDEVICE;
-        if (upload_twiddles<float>(c, 1, a, n3[a]) != OFDFT_OK) return OFDFT_EDEVICE;
-    }
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
-    if (field_smem_max(g, sizeof(double2)) > (size_t)optin)
+    // leave room for the kernels' static shared memory (block reductions)
+    size_t dyn = (size_t)optin - 8192;
+    if (field_smem_max(g, sizeof(double2)) > dyn)
         return fail(c, OFDFT_EINVAL, "grid too large for the shared-memory tiles");
-    set_field_smem_limits<double>((size_t)optin);
-    set_field_smem_limits<float>((size_t)optin);
-    CK(cudaGetLastError());
+    CK(set_field_smem_limits<double>(dyn));
+    CK(set_field_smem_limits<float>(dyn));
+    CK(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+    return OFDFT_OK;
+}
+
+ofdft_status normalize_phi64(ofdft_ctx *c)
+{
+    FieldSet &f = c->f[0];
+    int nb = launch_sumsq<double>(c->g.N, (const double *)f.phi, c->part, c->st);
+    launch_reduce(c->part, nb, 1, c->scal, c->st);
+    c->launches += 2;
+    if (sync_read(c, 1) != OFDFT_OK) return OFDFT_EDEVICE;
+    double ss = c->scal_h[0] * c->g.dV;
+    if (!(ss > 0.0) || !isfinite(ss)) return fail(c, OFDFT_ENUMERIC, "phi has zero or non-finite norm");
+    launch_scale<double>(c->g.N, (double *)f.phi, sqrt(c->Ne / ss), nullptr, c->st);
+    c->launches++;
     return OFDFT_OK;
 }
 
@@ -784,6 +919,10 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     c->precision = p.precision;
     c->Ne = 0.0;
     for (int i = 0; i < nat; ++i) c->Ne += Z[i];
+    const char *dbgenv = getenv("OFDFT_DEBUG_SYNC");
+    c->debug_sync = dbgenv && dbgenv[0] == '1';
+    const char *gr = getenv("OFDFT_NO_GRAPHS");
+    c->use_graphs = !(gr && gr[0] == '1');
     ofdft_status s = alloc_ctx(c);
     if (s == OFDFT_OK) s = setup_ewald(c);
     if (s != OFDFT_OK) {
@@ -824,25 +963,16 @@ ofdft_status ofdft_set_phi(ofdft_ctx *c, const double *phi)
     if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
     cudaSetDevice(c->dev);
     const long long N = c->g.N;
+    FieldSet &f = c->f[0];
     if (phi) {
-        if (c->precision == OFDFT_MIXED) {
-            CK(cudaMemcpyAsync(c->phit, phi, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
-            launch_convert<double, float>(N, (const double *)c->phit, (float *)c->phi, c->st);
-            c->launches++;
-        } else {
-            CK(cudaMemcpyAsync(c->phi, phi, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
-        }
+        CK(cudaMemcpyAsync(f.phi, phi, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
     } else {
-        double u = sqrt(c->Ne / c->g.omega);
-        if (c->precision == OFDFT_MIXED) launch_fill<float>(N, (float *)c->phi, (float)u, c->st);
-        else launch_fill<double>(N, (double *)c->phi, u, c->st);
+        launch_fill<double>(N, (double *)f.phi, sqrt(c->Ne / c->g.omega), c->st);
         c->launches++;
     }
     c->last_valid = false;
     c->md_ready = false;
-    ofdft_status s = c->precision == OFDFT_MIXED ? normalize_phi<float>(c, (float *)c->phi)
-                                                 : normalize_phi<double>(c, (double *)c->phi);
-    return s;
+    return normalize_phi64(c);
 }
 
 ofdft_status ofdft_energy_potential(ofdft_ctx *c, const double *phi, ofdft_energy *E, double *v)
@@ -850,24 +980,19 @@ ofdft_status ofdft_energy_potential(ofdft_ctx *c, const double *phi, ofdft_energ
     if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
     cudaSetDevice(c->dev);
     const long long N = c->g.N;
-    double *ph;
+    FieldSet &f = c->f[0];
+    double *ph = (double *)f.phi;
     if (phi) {
-        CK(cudaMemcpyAsync(c->phit, phi, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
-        ph = (double *)c->phit;
-    } else if (c->precision == OFDFT_MIXED) {
-        launch_convert<float, double>(N, (const float *)c->phi, (double *)c->phit, c->st);
-        c->launches++;
-        ph = (double *)c->phit;
-    } else {
-        ph = (double *)c->phi;
+        CK(cudaMemcpyAsync(f.phit, phi, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        ph = (double *)f.phit;
     }
     EvalScalars es;
-    ofdft_status s = evaluate<double>(c, ph, nullptr, nullptr, 1.0, 0.0, (double *)c->vt, false, es);
+    ofdft_status s = evaluate<double>(c, f, ph, (double *)f.vt, false, es);
     if (s != OFDFT_OK) return s;
     ofdft_energy e;
     fill_energy(c, es, e);
     if (v) {
-        CK(cudaMemcpyAsync(v, c->vt, N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(v, f.vt, N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
     }
     if (E) *E = e;
@@ -908,14 +1033,7 @@ ofdft_status ofdft_get_density(ofdft_ctx *c, double *n)
     if (!c || !n) return fail(c, OFDFT_EINVAL, "NULL argument");
     cudaSetDevice(c->dev);
     const long long N = c->g.N;
-    std::vector<double> tmp;
-    if (c->precision == OFDFT_MIXED) {
-        launch_convert<float, double>(N, (const float *)c->phi, (double *)c->phit, c->st);
-        c->launches++;
-        CK(cudaMemcpyAsync(n, c->phit, N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-    } else {
-        CK(cudaMemcpyAsync(n, c->phi, N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-    }
+    CK(cudaMemcpyAsync(n, c->f[0].phi, N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     for (long long i = 0; i < N; ++i) n[i] *= n[i];
     return OFDFT_OK;
@@ -939,6 +1057,7 @@ ofdft_status ofdft_md_step(ofdft_ctx *c, const ofdft_md_params *mp, int nsteps, 
         return fail(c, OFDFT_EINVAL, "bad MD parameters");
     cudaSetDevice(c->dev);
     const int nat = c->nat;
+    FieldSet &f = c->f[0];
     ofdft_status s;
     if (pos && memcmp(pos, c->R.data(), 3 * nat * sizeof(double)) != 0) {
         c->R.assign(pos, pos + 3 * nat);
@@ -958,20 +1077,24 @@ ofdft_status ofdft_md_step(ofdft_ctx *c, const ofdft_md_params *mp, int nsteps, 
     ofdft_stats tot{};
     tot.status = OFDFT_OK;
     EvalScalars es;
+    auto add = [&](const ofdft_stats &st) {
+        tot.iterations += st.iterations;
+        tot.evaluations += st.evaluations;
+        tot.evaluations_lo += st.evaluations_lo;
+        tot.gnorm = st.gnorm;
+    };
     if (!c->md_ready) {
         ofdft_stats st{};
         s = run_minimize(c, mp->gtol, mp->maxit, st, es);
-        tot.iterations += st.iterations;
-        tot.evaluations += st.evaluations;
-        tot.gnorm = st.gnorm;
+        add(st);
         if (s != OFDFT_OK) {
+            tot.status = s;
             if (stats) *stats = tot;
             return s;
         }
         s = forces_now(c, es);
         if (s != OFDFT_OK) return s;
-        size_t eb = c->precision == OFDFT_MIXED ? sizeof(float) : sizeof(double);
-        CK(cudaMemcpyAsync(c->phiprev, c->phi, c->g.N * eb, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->phiprev, f.phi, c->g.N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
         c->md_ready = true;
     }
     for (int step = 0; step < nsteps; ++step) {
@@ -979,21 +1102,14 @@ ofdft_status ofdft_md_step(ofdft_ctx *c, const ofdft_md_params *mp, int nsteps, 
         c->launches++;
         s = update_ions(c);
         if (s != OFDFT_OK) return s;
-        // density extrapolation phi0 = 2 phi_n - phi_{n-1}, renormalised by the minimiser
-        if (ensure_part(c, 4096) != OFDFT_OK) return OFDFT_ENOMEM;
-        if (c->precision == OFDFT_MIXED)
-            launch_extrap<float>(c->g.N, (const float *)c->phi, (const float *)c->phiprev, (float *)c->phit, c->part, c->st);
-        else
-            launch_extrap<double>(c->g.N, (const double *)c->phi, (const double *)c->phiprev, (double *)c->phit, c->part, c->st);
+        // density extrapolation phi0 = 2 phi_n - phi_{n-1} (renormalised by the minimiser)
+        launch_extrap<double>(c->g.N, (const double *)f.phi, c->phiprev, (double *)f.phit, c->part, c->st);
         c->launches++;
-        // rotate: phiprev <- phi, phi <- extrapolated
-        std::swap(c->phiprev, c->phi);
-        std::swap(c->phi, c->phit);
+        CK(cudaMemcpyAsync(c->phiprev, f.phi, c->g.N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(f.phi, f.phit, c->g.N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
         ofdft_stats st{};
         s = run_minimize(c, mp->gtol, mp->maxit, st, es);
-        tot.iterations += st.iterations;
-        tot.evaluations += st.evaluations;
-        tot.gnorm = st.gnorm;
+        add(st);
         if (s != OFDFT_OK) {
             tot.status = s;
             if (stats) *stats = tot;

@@ -250,14 +250,14 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     double *pA = part, *pB = pA + 3 * nbx, *pC = pB + 6 * npairs;
     double *ph = const_cast<double *>(phi_dev);
     const bool fttf = fp.kind == 0;
-    launch_zfwd<double>(g, az, 1, nullptr, ph, nullptr, 0.0, 0.0, nullptr, s0, st);
+    launch_zfwd<double>(g, az, 1, nullptr, ph, nullptr, 0.0, 0.0, nullptr, nullptr, s0, st);
     launch_ypass<double>(g, ay, false, s0, 1, specN, st);
     int nbz;
     if (fttf) {
         launch_xhl<double>(g, ax, s0, vext, nullptr, 1, pA, st);
         launch_ypass<double>(g, ay, true, s0, 1, specN, st);
-        nbz = launch_zfinal<double>(g, az, true, s0, nullptr, ph, nullptr, nullptr, 1.0, 0.0, T, fp, tab,
-                                    xc, v_dev, pC, st);
+        nbz = launch_zfinal<double>(g, az, true, s0, nullptr, ph, nullptr, nullptr, 1.0, 0.0, nullptr, T, fp,
+                                    tab, xc, v_dev, pC, st);
     } else {
         launch_xgrad<double>(g, ax, s0, vext, s1, s2, s3, pA, st);
         launch_ypass<double>(g, ay, true, s1, 3, specN, st);
@@ -265,8 +265,8 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
         launch_ypass<double>(g, ay, false, s1, 3, specN, st);
         launch_xdiv<double>(g, ax, s0, vext, s1, s2, s3, st);
         launch_ypass<double>(g, ay, true, s1, 1, specN, st);
-        nbz = launch_zfinal<double>(g, az, false, s1, vpart, ph, nullptr, nullptr, 1.0, 0.0, T, fp, tab, xc,
-                                    v_dev, pC, st);
+        nbz = launch_zfinal<double>(g, az, false, s1, vpart, ph, nullptr, nullptr, 1.0, 0.0, nullptr, T, fp,
+                                    tab, xc, v_dev, pC, st);
     }
     launch_reduce(pA, nbx, 3, scal, st);
     if (!fttf) launch_reduce(pB, nbz, 6, scal + 3, st);

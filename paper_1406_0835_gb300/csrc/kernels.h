@@ -8,16 +8,16 @@ namespace ofdft {
 // ---- grid fields (kernels_fields.cu)
 template <typename T>
 void launch_zfwd(const GridInfo &g, const FftAxis &az, int mode, const T *in, const T *phi,
-                 const T *dhat, T c, T s, T *phit, cplx<T> *out, cudaStream_t st);
+                 const T *dhat, T c, T s, const double *cs, T *phit, cplx<T> *out, cudaStream_t st);
 template <typename T>
 int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, cplx<T> *g2,
                 const T *phit, T temp, const FuncParams &fp, const T *tab, int xc, T *vpart,
                 double *part, cudaStream_t st);
 template <typename T>
 int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T> *dspec,
-                  const T *vpart, const T *phit, const T *phi, const T *dhat, T c, T s, T temp,
-                  const FuncParams &fp, const T *tab, int xc, T *vout, double *part,
-                  cudaStream_t st);
+                  const T *vpart, const T *phit, const T *phi, const T *dhat, T c, T s,
+                  const double *cs, T temp, const FuncParams &fp, const T *tab, int xc, T *vout,
+                  double *part, cudaStream_t st);
 template <typename T>
 void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data, int nfields,
                   long long fstride, cudaStream_t st);
@@ -31,13 +31,17 @@ template <typename T>
 void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const cplx<T> *vext,
                  cplx<T> *w0, const cplx<T> *w1, const cplx<T> *w2, cudaStream_t st);
 size_t field_smem_max(const GridInfo &g, size_t csize);
-template <typename T> void set_field_smem_limits(size_t bytes);
+template <typename T> cudaError_t set_field_smem_limits(size_t bytes);
 
 // ---- vectors, reductions, ions (kernels_misc.cu)
 // Sum part[q * nblk + b] over b for q < nq into out[q] (one block per q, fixed order).
 void launch_reduce(const double *part, int nblk, int nq, double *out, cudaStream_t st);
 template <typename T> void launch_fill(long long n, T *x, T val, cudaStream_t st);
-template <typename T> void launch_scale(long long n, T *x, double s, cudaStream_t st);
+template <typename T> void launch_scale(long long n, T *x, double s, const double *sp, cudaStream_t st);
+// if *accepted: phi <- phit, v <- vt, gprev <- g
+template <typename T>
+void launch_accept(long long n, const int *accepted, T *phi, const T *phit, T *v, const T *vt,
+                   const T *g, T *gprev, cudaStream_t st);
 template <typename T, typename U> void launch_convert(long long n, const T *x, U *y, cudaStream_t st);
 // sum x^2 -> part (returns blocks)
 template <typename T> int launch_sumsq(long long n, const T *x, double *part, cudaStream_t st);
@@ -46,16 +50,16 @@ template <typename T>
 int launch_extrap(long long n, const T *x, const T *xp, T *y, double *part, cudaStream_t st);
 // g = 2 phi (v - mu); part: sum g^2, sum g.gprev
 template <typename T>
-int launch_cg_grad(long long n, const T *phi, const T *v, double mu, T *g, const T *gprev,
-                   double *part, cudaStream_t st);
+int launch_cg_grad(long long n, const T *phi, const T *v, double mu, const double *mup, T *g,
+                   const T *gprev, double *part, cudaStream_t st);
 // d = -g + beta d; part: sum phi d, sum d^2, sum d g, sum phi^2, sum phi g
 template <typename T>
-int launch_cg_dir(long long n, const T *g, T *d, double beta, const T *phi, double *part,
-                  cudaStream_t st);
+int launch_cg_dir(long long n, const T *g, T *d, double beta, const double *betap, const T *phi,
+                  double *part, cudaStream_t st);
 // restart: d = -g; else d -= c1 phi; dhat = c2 d; part: sum 2 phi v dhat
 template <typename T>
 int launch_cg_dhat(long long n, const T *g, T *d, const T *phi, const T *v, double c1, double c2,
-                   int restart, T *dhat, double *part, cudaStream_t st);
+                   int restart, const double *c12r, T *dhat, double *part, cudaStream_t st);
 
 // Per-ion axis phase tables exp(-i G_a R_a) for a = x, y, z (complex double,
 // [nat][nx], [nat][ny], [nat][K]).
@@ -86,5 +90,15 @@ void launch_md_a(int nat, const double *m, double *R, double *V, const double *F
                  double kT, double Q, int ndof, int thermo, double *nh, cudaStream_t st);
 void launch_md_b(int nat, const double *m, double *V, const double *F, double dt, double kT,
                  double Q, int ndof, int thermo, double *nh, cudaStream_t st);
+
+// ---- device CG controller (cg_control.cu); single-thread kernels.
+// use_cond = 0 outside a graph (the handles are then ignored).
+void launch_ctl_norm(CgState *s, cudaStream_t st);
+void launch_ctl_init(CgState *s, cudaStream_t st);
+void launch_ctl_grad(CgState *s, int first, cudaGraphConditionalHandle outer, int use_cond,
+                     cudaStream_t st);
+void launch_ctl_dir(CgState *s, cudaStream_t st);
+void launch_ctl_dhat(CgState *s, cudaGraphConditionalHandle ls, int use_cond, cudaStream_t st);
+void launch_ctl_ls(CgState *s, cudaGraphConditionalHandle ls, int use_cond, cudaStream_t st);
 
 }  // namespace ofdft

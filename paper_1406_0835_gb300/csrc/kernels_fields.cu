@@ -49,8 +49,13 @@ template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ld
 template <typename T, int MODE>
 __global__ void k_zfwd(GridInfo g, FftAxis az, int P, const T *__restrict__ in,
                        const T *__restrict__ phi, const T *__restrict__ dhat, T c, T s,
-                       T *__restrict__ phit, cplx<T> *__restrict__ out)
+                       const double *__restrict__ cs, T *__restrict__ phit,
+                       cplx<T> *__restrict__ out)
 {
+    if (MODE == 2 && cs != nullptr) {   // rotation angle from the device CG state
+        c = (T)cs[0];
+        s = (T)cs[1];
+    }
     typedef cplx<T> C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *A = reinterpret_cast<C *>(smraw);
@@ -200,9 +205,14 @@ template <typename T, bool FTTF>
 __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const cplx<T> *__restrict__ dspec,
                          const T *__restrict__ vpart, const T *__restrict__ phit,
                          const T *__restrict__ phi, const T *__restrict__ dhat, T c, T s,
-                         T temp, FuncParams fp, const T *__restrict__ tab, int xc,
-                         T *__restrict__ vout, double *__restrict__ part)
+                         const double *__restrict__ cs, T temp, FuncParams fp,
+                         const T *__restrict__ tab, int xc, T *__restrict__ vout,
+                         double *__restrict__ part)
 {
+    if (cs != nullptr) {
+        c = (T)cs[0];
+        s = (T)cs[1];
+    }
     typedef cplx<T> C;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nz = g.nz, K = g.K;
@@ -486,16 +496,16 @@ int threads_for(int work)
 // ---------------------------------------------------------------- launchers
 template <typename T>
 void launch_zfwd(const GridInfo &g, const FftAxis &az, int mode, const T *in, const T *phi,
-                 const T *dhat, T c, T s, T *phit, cplx<T> *out, cudaStream_t st)
+                 const T *dhat, T c, T s, const double *cs, T *phit, cplx<T> *out, cudaStream_t st)
 {
     int P = zpairs_per_block(g);
     long long npairs = (long long)g.nx * g.ny / 2;
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 2 * (size_t)P * g.nz * sizeof(cplx<T>);
     int th = threads_for(P * g.nz);
-    if (mode == 0) k_zfwd<T, 0><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, phit, out);
-    else if (mode == 1) k_zfwd<T, 1><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, phit, out);
-    else k_zfwd<T, 2><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, phit, out);
+    if (mode == 0) k_zfwd<T, 0><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);
+    else if (mode == 1) k_zfwd<T, 1><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);
+    else k_zfwd<T, 2><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);
 }
 
 template <typename T>
@@ -514,9 +524,9 @@ int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, 
 
 template <typename T>
 int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T> *dspec,
-                  const T *vpart, const T *phit, const T *phi, const T *dhat, T c, T s, T temp,
-                  const FuncParams &fp, const T *tab, int xc, T *vout, double *part,
-                  cudaStream_t st)
+                  const T *vpart, const T *phit, const T *phi, const T *dhat, T c, T s,
+                  const double *cs, T temp, const FuncParams &fp, const T *tab, int xc, T *vout,
+                  double *part, cudaStream_t st)
 {
     int P = zpairs_per_block(g);
     long long npairs = (long long)g.nx * g.ny / 2;
@@ -525,10 +535,10 @@ int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T>
     int th = threads_for(P * g.nz);
     if (fttf)
         k_zfinal<T, true><<<blocks, th, sm, st>>>(g, az, P, dspec, vpart, phit, phi, dhat, c, s,
-                                                  temp, fp, tab, xc, vout, part);
+                                                  cs, temp, fp, tab, xc, vout, part);
     else
         k_zfinal<T, false><<<blocks, th, sm, st>>>(g, az, P, dspec, vpart, phit, phi, dhat, c, s,
-                                                   temp, fp, tab, xc, vout, part);
+                                                   cs, temp, fp, tab, xc, vout, part);
     return blocks;
 }
 
@@ -589,31 +599,36 @@ size_t field_smem_max(const GridInfo &g, size_t csize)
     return m > x ? m : x;
 }
 
-template <typename T> void set_field_smem_limits(size_t bytes)
+template <typename T> cudaError_t set_field_smem_limits(size_t bytes)
 {
     int b = (int)bytes;
-    cudaFuncSetAttribute(k_zfwd<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_zfwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_zfwd<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_zgga<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_zfinal<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_zfinal<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_ypass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_ypass<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_xgrad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_xhl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_xdiv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    cudaError_t e[] = {
+        cudaFuncSetAttribute(k_zfwd<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zfwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zfwd<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zgga<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zfinal<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zfinal<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_ypass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_ypass<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xgrad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xhl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xdiv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)};
+    for (cudaError_t x : e)
+        if (x != cudaSuccess) return x;
+    return cudaSuccess;
 }
 
 #define OFDFT_INST(T)                                                                              \
     template void launch_zfwd<T>(const GridInfo &, const FftAxis &, int, const T *, const T *,     \
-                                 const T *, T, T, T *, cplx<T> *, cudaStream_t);                 \
+                                 const T *, T, T, const double *, T *, cplx<T> *, cudaStream_t); \
     template int launch_zgga<T>(const GridInfo &, const FftAxis &, cplx<T> *, cplx<T> *,           \
                                 cplx<T> *, const T *, T, const FuncParams &, const T *, int, T *, \
                                 double *, cudaStream_t);                                          \
     template int launch_zfinal<T>(const GridInfo &, const FftAxis &, bool, const cplx<T> *,        \
-                                  const T *, const T *, const T *, const T *, T, T, T,             \
-                                  const FuncParams &, const T *, int, T *, double *, cudaStream_t); \
+                                  const T *, const T *, const T *, const T *, T, T, const double *, \
+                                  T, const FuncParams &, const T *, int, T *, double *,            \
+                                  cudaStream_t);                                                  \
     template void launch_ypass<T>(const GridInfo &, const FftAxis &, bool, cplx<T> *, int,         \
                                   long long, cudaStream_t);                                       \
     template int launch_xgrad<T>(const GridInfo &, const FftAxis &, cplx<T> *, const cplx<T> *,    \
@@ -623,7 +638,7 @@ template <typename T> void set_field_smem_limits(size_t bytes)
     template void launch_xdiv<T>(const GridInfo &, const FftAxis &, const cplx<T> *,               \
                                  const cplx<T> *, cplx<T> *, const cplx<T> *, const cplx<T> *,    \
                                  cudaStream_t);                                                   \
-    template void set_field_smem_limits<T>(size_t);
+    template cudaError_t set_field_smem_limits<T>(size_t);
 
 OFDFT_INST(double)
 OFDFT_INST(float)

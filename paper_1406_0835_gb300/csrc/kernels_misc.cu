@@ -34,8 +34,9 @@ template <typename T> __global__ void k_fill(long long n, T *x, T val)
         x[i] = val;
 }
 
-template <typename T> __global__ void k_scale(long long n, T *x, double s)
+template <typename T> __global__ void k_scale(long long n, T *x, double s, const double *sp)
 {
+    if (sp != nullptr) s = *sp;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         x[i] = (T)((double)x[i] * s);
@@ -77,8 +78,10 @@ __global__ void k_extrap(long long n, const T *__restrict__ x, const T *__restri
 
 template <typename T>
 __global__ void k_cg_grad(long long n, const T *__restrict__ phi, const T *__restrict__ v,
-                          double mu, T *__restrict__ g, const T *__restrict__ gprev, double *part)
+                          double mu, const double *mup, T *__restrict__ g,
+                          const T *__restrict__ gprev, double *part)
 {
+    if (mup != nullptr) mu = *mup;
     double acc[2] = {0.0, 0.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -96,8 +99,9 @@ __global__ void k_cg_grad(long long n, const T *__restrict__ phi, const T *__res
 
 template <typename T>
 __global__ void k_cg_dir(long long n, const T *__restrict__ g, T *__restrict__ d, double beta,
-                         const T *__restrict__ phi, double *part)
+                         const double *betap, const T *__restrict__ phi, double *part)
 {
+    if (betap != nullptr) beta = *betap;
     double acc[5] = {0, 0, 0, 0, 0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -119,8 +123,13 @@ __global__ void k_cg_dir(long long n, const T *__restrict__ g, T *__restrict__ d
 template <typename T>
 __global__ void k_cg_dhat(long long n, const T *__restrict__ g, T *__restrict__ d,
                           const T *__restrict__ phi, const T *__restrict__ v, double c1, double c2,
-                          int restart, T *__restrict__ dhat, double *part)
+                          int restart, const double *c12r, T *__restrict__ dhat, double *part)
 {
+    if (c12r != nullptr) {
+        c1 = c12r[0];
+        c2 = c12r[1];
+        restart = c12r[2] != 0.0;
+    }
     double acc[1] = {0.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -132,6 +141,22 @@ __global__ void k_cg_dhat(long long n, const T *__restrict__ g, T *__restrict__ 
     }
     block_sum<1>(acc);
     if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+}
+
+// Accept a line-search trial: phi <- phi_trial, v <- v_trial, g_prev <- g,
+// when the device CG state says so.
+template <typename T>
+__global__ void k_accept(long long n, const int *accepted, T *__restrict__ phi,
+                         const T *__restrict__ phit, T *__restrict__ v, const T *__restrict__ vt,
+                         const T *__restrict__ g, T *__restrict__ gprev)
+{
+    if (*accepted == 0) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        phi[i] = phit[i];
+        v[i] = vt[i];
+        gprev[i] = g[i];
+    }
 }
 
 // ------------------------------------------------ structure factor, forces
@@ -452,9 +477,16 @@ template <typename T> void launch_fill(long long n, T *x, T val, cudaStream_t st
 {
     k_fill<T><<<vec_blocks(n), kVecThreads, 0, st>>>(n, x, val);
 }
-template <typename T> void launch_scale(long long n, T *x, double s, cudaStream_t st)
+template <typename T> void launch_scale(long long n, T *x, double s, const double *sp, cudaStream_t st)
 {
-    k_scale<T><<<vec_blocks(n), kVecThreads, 0, st>>>(n, x, s);
+    k_scale<T><<<vec_blocks(n), kVecThreads, 0, st>>>(n, x, s, sp);
+}
+
+template <typename T>
+void launch_accept(long long n, const int *accepted, T *phi, const T *phit, T *v, const T *vt,
+                   const T *g, T *gprev, cudaStream_t st)
+{
+    k_accept<T><<<vec_blocks(n), kVecThreads, 0, st>>>(n, accepted, phi, phit, v, vt, g, gprev);
 }
 template <typename T, typename U> void launch_convert(long long n, const T *x, U *y, cudaStream_t st)
 {
@@ -474,27 +506,27 @@ int launch_extrap(long long n, const T *x, const T *xp, T *y, double *part, cuda
     return b;
 }
 template <typename T>
-int launch_cg_grad(long long n, const T *phi, const T *v, double mu, T *g, const T *gprev,
-                   double *part, cudaStream_t st)
+int launch_cg_grad(long long n, const T *phi, const T *v, double mu, const double *mup, T *g,
+                   const T *gprev, double *part, cudaStream_t st)
 {
     int b = vec_blocks(n);
-    k_cg_grad<T><<<b, kVecThreads, 0, st>>>(n, phi, v, mu, g, gprev, part);
+    k_cg_grad<T><<<b, kVecThreads, 0, st>>>(n, phi, v, mu, mup, g, gprev, part);
     return b;
 }
 template <typename T>
-int launch_cg_dir(long long n, const T *g, T *d, double beta, const T *phi, double *part,
-                  cudaStream_t st)
+int launch_cg_dir(long long n, const T *g, T *d, double beta, const double *betap, const T *phi,
+                  double *part, cudaStream_t st)
 {
     int b = vec_blocks(n);
-    k_cg_dir<T><<<b, kVecThreads, 0, st>>>(n, g, d, beta, phi, part);
+    k_cg_dir<T><<<b, kVecThreads, 0, st>>>(n, g, d, beta, betap, phi, part);
     return b;
 }
 template <typename T>
 int launch_cg_dhat(long long n, const T *g, T *d, const T *phi, const T *v, double c1, double c2,
-                   int restart, T *dhat, double *part, cudaStream_t st)
+                   int restart, const double *c12r, T *dhat, double *part, cudaStream_t st)
 {
     int b = vec_blocks(n);
-    k_cg_dhat<T><<<b, kVecThreads, 0, st>>>(n, g, d, phi, v, c1, c2, restart, dhat, part);
+    k_cg_dhat<T><<<b, kVecThreads, 0, st>>>(n, g, d, phi, v, c1, c2, restart, c12r, dhat, part);
     return b;
 }
 
@@ -564,15 +596,17 @@ void launch_md_b(int nat, const double *m, double *V, const double *F, double dt
 
 #define OFDFT_MISC_INST(T)                                                                         \
     template void launch_fill<T>(long long, T *, T, cudaStream_t);                                 \
-    template void launch_scale<T>(long long, T *, double, cudaStream_t);                           \
+    template void launch_scale<T>(long long, T *, double, const double *, cudaStream_t);           \
+    template void launch_accept<T>(long long, const int *, T *, const T *, T *, const T *,         \
+                                   const T *, T *, cudaStream_t);                                 \
     template int launch_sumsq<T>(long long, const T *, double *, cudaStream_t);                    \
     template int launch_extrap<T>(long long, const T *, const T *, T *, double *, cudaStream_t);   \
-    template int launch_cg_grad<T>(long long, const T *, const T *, double, T *, const T *,        \
-                                   double *, cudaStream_t);                                       \
-    template int launch_cg_dir<T>(long long, const T *, T *, double, const T *, double *,         \
-                                  cudaStream_t);                                                  \
+    template int launch_cg_grad<T>(long long, const T *, const T *, double, const double *, T *,   \
+                                   const T *, double *, cudaStream_t);                            \
+    template int launch_cg_dir<T>(long long, const T *, T *, double, const double *, const T *,    \
+                                  double *, cudaStream_t);                                        \
     template int launch_cg_dhat<T>(long long, const T *, T *, const T *, const T *, double,       \
-                                   double, int, T *, double *, cudaStream_t);                     \
+                                   double, int, const double *, T *, double *, cudaStream_t);     \
     template void launch_vext<T>(const GridInfo &, int, const double *, const double2 *,          \
                                  const double2 *, const double2 *, cplx<T> *, cudaStream_t);      \
     template int launch_lpp_forces<T>(const GridInfo &, int, const double *, const double2 *,     \

@@ -83,6 +83,35 @@ struct FuncParams {
 };
 FuncParams functional_params(int functional);
 
+// Device-resident state of one CG minimisation (reading R9 of the paper's
+// unstated CG details).  Reductions write the sums; single-thread controller
+// kernels turn them into the scalars the vector kernels read, and drive the
+// graph's conditional loops.
+struct CgState {
+    // configuration (written by the host before a minimisation)
+    double gtol, dV, ls_tol, theta0, Ne;
+    int maxit, max_ls, stagnate;
+    int pad0;
+    // reduction outputs
+    double ev[18];     // evaluation: E_H, E_loc, P_loc, GGA sums [3..8], final sums [9..17]
+    double rg[2];      // sum g^2, sum g.g_prev
+    double rd[5];      // sum phi.d, d.d, d.g, phi.phi, phi.g
+    double rh[1];      // sum 2 phi v dhat
+    double rn[1];      // sum phi^2
+    // iteration state
+    double mu, gg, ggprev, gnorm, beta, c1, c2, D0, theta_prev, scale;
+    double cs[2];      // cos, sin of the trial angle (read by the evaluation kernels)
+    double th, lo, Dlo, hi, Dhi, pa, Da;
+    double best_g;
+    double c12r[3];    // c1, c2, restart (read by the direction kernel)
+    int best_it, restart, have_prev, it, nevals, nls, ls_active, accepted, status, done, fallback;
+    int nouter;        // executions of the iteration body (directions built)
+    double ev_acc[18]; // evaluation sums at the last accepted point
+};
+
+// Status codes of CgState::status (besides ofdft_status values).
+constexpr int kCgStagnated = 1;   // stopped at the precision floor (stagnate mode)
+
 // Reduction quantities (indices into the scalar block).
 enum Quantity {
     Q_FS = 0,      // sum f_s

@@ -36,7 +36,8 @@ class Energy(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("evaluations", ctypes.c_int),
-                ("gnorm", ctypes.c_double), ("status", ctypes.c_int)]
+                ("gnorm", ctypes.c_double), ("status", ctypes.c_int),
+                ("evaluations_lo", ctypes.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
