@@ -26,10 +26,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# CG evaluations (energy + potential) per MD step, measured on the GPU path
+# CG evaluations (energy + potential) per step, measured on the GPU path
 # (bench.py reports evals_per_step); converts the oracle's evaluations/s to
 # MD steps/s in the reference arm, which runs without a GPU.
-EVALS_PER_MD_STEP = {"md-vt84f-96": 762.0, "md-sga-96": 300.0, "md-vt84f-96-mixed": 762.0}
+EVALS_PER_STEP = {"md-vt84f-96": 920.0, "md-sga-96": 300.0, "md-vt84f-96-mixed": 1013.0,
+                  "solve-vt84f-128": 541.0, "solve-vt84f-128-mixed": 630.0, "eval-vt84f-128": 1.0}
 
 WORKLOADS = {
     "md-vt84f-96": dict(kind="md", functional="vt84f", grid=96, precision="fp64"),
@@ -37,7 +38,34 @@ WORKLOADS = {
     "md-vt84f-96-mixed": dict(kind="md", functional="vt84f", grid=96, precision="mixed"),
     # one energy + potential evaluation per step (256 H, 4 g/cm^3, 128^3, 250 kK)
     "eval-vt84f-128": dict(kind="eval", functional="vt84f", grid=128, precision="fp64"),
+    # one single-point minimisation per step (256 H, 4 g/cm^3, 128^3, 250 kK)
+    "solve-vt84f-128": dict(kind="solve", functional="vt84f", grid=128, precision="fp64", T=2.5e5),
+    "solve-vt84f-128-mixed": dict(kind="solve", functional="vt84f", grid=128, precision="mixed", T=2.5e5),
 }
+
+
+def workload_meta(name):
+    """Metric, unit and config of a workload (shared by both arms)."""
+    from paper_1406_0835_gb300 import inputs
+    wl = WORKLOADS[name]
+    if wl["kind"] == "md":
+        cfg = inputs.config_md(wl["functional"], grid=wl["grid"])
+        conf = {"workload": name, "atoms": len(cfg["Z"]), "grid": list(cfg["grid"]),
+                "functional": wl["functional"], "xc": "PZ81", "T_K": cfg["T"], "rho_gcc": 1.0,
+                "dt_fs": 0.2, "gtol": 1e-8, "l2": "flushed (256 MB write) before every timed step"}
+        return "MD steps/s", "MD steps/s", conf
+    if wl["kind"] == "solve":
+        cfg = inputs.config_mixed(wl["T"], grid=wl["grid"])
+        conf = {"workload": name, "atoms": len(cfg["Z"]), "grid": list(cfg["grid"]),
+                "functional": wl["functional"], "xc": "PZ81", "T_K": cfg["T"], "rho_gcc": 4.0,
+                "gtol": 1e-8, "start": "uniform density",
+                "l2": "flushed (256 MB write) before every timed step"}
+        return "single-point solves/s", "solves/s", conf
+    cfg = inputs.config_mixed(2.5e5, grid=wl["grid"])
+    conf = {"workload": name, "atoms": len(cfg["Z"]), "grid": list(cfg["grid"]),
+            "functional": wl["functional"], "T_K": cfg["T"], "rho_gcc": 4.0,
+            "l2": "flushed (256 MB write) before every timed step"}
+    return "functional+grad evals/s", "evals/s", conf
 
 
 def parse():
@@ -49,6 +77,9 @@ def parse():
     ap.add_argument("--workload", default="md-vt84f-96", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--maxit", type=int, default=20000,
+                    help="CG iteration cap per solve (solve workloads; a small cap makes a short "
+                         "profiling case, whose solves then stop unconverged)")
     return ap.parse_args()
 
 
@@ -156,8 +187,9 @@ def run_eval(args, rank, world):
     cfg = inputs.config_mixed(2.5e5, grid=wl["grid"])
     ctx = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
                         precision=wl["precision"], device=dev, stream=stream.cuda_stream)
-    # a minimised density is the realistic input; the evaluation repeats at it
-    ctx.minimize(gtol=1e-4 if wl["precision"] == "mixed" else 1e-6, maxit=200, raise_on_noconv=False)
+    # a partly minimised density (60 CG iterations from the uniform start)
+    # is the realistic input; the evaluation repeats at it
+    ctx.minimize(gtol=1e-8, maxit=60, raise_on_noconv=False)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         ofdft.ofdft_energy_potential(ctx.ctx, None, False)
@@ -185,7 +217,49 @@ def run_eval(args, rank, world):
     return res, 1.0
 
 
+def roofline_entry(dominant, grid, kms, kcount, clk, peaks):
+    flops, byts = kernel_model(dominant, grid)
+    avg_s = (kms / 1e3) / max(kcount, 1)
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # FP64 FMA issue: 2 per SM per clock (GB300); 152 SMs
+    fp64_peak = 152 * 2 * 2 * (sm_mhz * 1e6) / 1e12
+    ok = kcount > 0
+    return {"bound": "alu", "kernel": dominant, "achieved": flops / avg_s / 1e12 if ok else None,
+            "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
+            "frac": (flops / avg_s / 1e12) / fp64_peak if ok else None,
+            "traffic": None, "launches": kcount, "avg_launch_us": avg_s * 1e6,
+            "hbm_gbs": byts / avg_s / 1e9 if ok else None,
+            "hbm_peak_gbs": peaks.get("hbm_gbs"),
+            "peak_note": "FP64 peak derived from 152 SMs x 2 DFMA/clk x median SM clock; "
+                         "kernel time from events around every launch in one extra host-driven step"}
+
+
+def time_dominant(ctx, ofdft, dominant, stream, work):
+    """Average duration of the dominant kernel class: events on the launching
+    stream around each of its launches during one more (host-driven) step."""
+    import torch
+    ofdft.ofdft_timer_select(ctx.ctx, dominant)
+    ofdft.ofdft_timer_read(ctx.ctx, reset=True)
+    with torch.cuda.stream(stream):
+        work()
+    torch.cuda.synchronize()
+    kms, kcount = ofdft.ofdft_timer_read(ctx.ctx, reset=True)
+    ofdft.ofdft_timer_select(ctx.ctx, 0)
+    return kms, kcount
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    tt = torch.tensor([x], device="cuda", dtype=torch.float64)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def run_ours(args, rank, world):
+    """MD workloads: one step = one MD step (ions, v_ext, Ewald, CG
+    minimisation, forces, pressure, thermostat)."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -198,13 +272,18 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream(device=dev)
     cfg = inputs.config_md(wl["functional"], grid=wl["grid"])
     mdT = cfg["T"]
-    ctx = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
-                        precision=wl["precision"], device=dev, stream=stream.cuda_stream)
+
+    def prepared_context():
+        c = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
+                          precision=wl["precision"], device=dev, stream=stream.cuda_stream)
+        # step 0: minimise at the initial geometry and compute forces
+        c.md_step(0.2, mdT, nsteps=0, pos=cfg["ions"], vel=cfg["vel"])
+        for _ in range(args.warmup):
+            c.md_step(0.2, mdT, nsteps=1)
+        return c
+
+    ctx = prepared_context()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    # step 0: minimise at the initial geometry and compute forces
-    ctx.md_step(0.2, mdT, nsteps=0, pos=cfg["ions"], vel=cfg["vel"])
-    for _ in range(args.warmup):
-        ctx.md_step(0.2, mdT, nsteps=1)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -229,59 +308,37 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = ctx.kernel_launches() - launches0
-    # The timed steps run each minimisation as one graph launch, which has no
-    # place for events around single kernels.  One more MD step, driven from
-    # the host with the same kernels, brackets every launch of the dominant
-    # kernel with events on its stream.
-    ofdft.ofdft_timer_select(ctx.ctx, dominant)
-    ofdft.ofdft_timer_read(ctx.ctx, reset=True)
-    with torch.cuda.stream(stream):
-        ctx.md_step(0.2, mdT, nsteps=1)
-    torch.cuda.synchronize()
-    kms, kcount = ofdft.ofdft_timer_read(ctx.ctx, reset=True)
-    ofdft.ofdft_timer_select(ctx.ctx, 0)
-    t_total = sum(times)
-    if world > 1:
-        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = max_over_ranks(sum(times), world)
     value = world * args.steps / t_total
-    # end to end through the C ABI with host buffers each step
+    kms, kcount = time_dominant(ctx, ofdft, dominant, stream, lambda: ctx.md_step(0.2, mdT, nsteps=1))
+    ctx.close()
+    # End to end through the C ABI with host position and velocity buffers
+    # every step: a second context replays the same trajectory (the path is
+    # deterministic), so the timed steps do the same CG work as above.
     e2e = None
     if not args.no_e2e:
-        pos, vel = ctx.md_state()
+        ctx2 = prepared_context()
+        pos, vel = ctx2.md_state()
         t_e2e = 0.0
-        ne = max(2, min(args.steps, 3))
-        for _ in range(ne):
+        evals2 = 0
+        for _ in range(args.steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            out = ctx.md_step(0.2, mdT, nsteps=1, pos=pos, vel=vel)
+            out = ctx2.md_step(0.2, mdT, nsteps=1, pos=pos, vel=vel)
             t_e2e += time.perf_counter() - t0
             pos, vel = out["pos"], out["vel"]
+            evals2 += out["stats"]["evaluations"]
+        ctx2.close()
         nat = len(cfg["Z"])
-        e2e = {"value": world * ne / t_e2e if world == 1 else None, "unit": "MD steps/s",
+        e2e = {"value": world * args.steps / max_over_ranks(t_e2e, world), "unit": "MD steps/s",
                "h2d_bytes_per_step": 2 * nat * 3 * 8,
-               "d2h_bytes_per_step": 3 * nat * 3 * 8 + 16 * 8}
-        if world > 1:
-            tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e2e["value"] = world * ne / float(tt.item())
-    peaks = read_peaks()
-    flops, byts = kernel_model(dominant, cfg["grid"])
-    avg_s = (kms / 1e3) / max(kcount, 1)
-    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # FP64 FMA issue: 2 per SM per clock (GB300); 152 SMs
-    fp64_peak = 152 * 2 * 2 * (sm_mhz * 1e6) / 1e12
-    roofline = {"bound": "alu", "kernel": dominant, "achieved": flops / avg_s / 1e12 if kcount else None,
-                "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
-                "frac": (flops / avg_s / 1e12) / fp64_peak if kcount else None,
-                "traffic": None, "launches": kcount, "avg_launch_us": avg_s * 1e6,
-                "hbm_gbs": byts / avg_s / 1e9 if kcount else None,
-                "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_note": "FP64 peak derived from 152 SMs x 2 DFMA/clk x median SM clock"}
+               "d2h_bytes_per_step": 3 * nat * 3 * 8 + 16 * 8,
+               "evals_per_step": evals2 / args.steps}
     res = {"metric": "MD steps/s", "value": value, "unit": "MD steps/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["precision"] == "fp64" else "f32+f64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if wl["precision"] == "fp64" else "f32+f64",
            "data": "synthetic (seeded hydrogen, random positions and Maxwell-Boltzmann velocities)",
            "config": {"workload": args.workload, "atoms": len(cfg["Z"]), "grid": list(cfg["grid"]),
                       "functional": wl["functional"], "xc": "PZ81", "T_K": mdT, "rho_gcc": 1.0,
@@ -289,20 +346,113 @@ def run_ours(args, rank, world):
                       "l2": "flushed (256 MB write) before every timed step"},
            "evals_per_s": world * evals / t_total, "evals_per_step": evals / args.steps,
            "cg_iterations_per_step": iters / args.steps,
-           "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roofline}
+           "gpu_launches": launches, "clocks": clk, "e2e": e2e,
+           "roofline": roofline_entry(dominant, cfg["grid"], kms, kcount, clk, read_peaks())}
+    return res, evals / args.steps
+
+
+def run_solve(args, rank, world):
+    """Single-point workloads: one step = one free-energy minimisation from
+    the uniform start to ||g|| < 1e-8, then forces and pressure (256 H at
+    4 g/cm^3, 250 kK, 128^3, VT84F + PZ81)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1406_0835_gb300 import inputs, ofdft
+
+    wl = WORKLOADS[args.workload]
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    cfg = inputs.config_mixed(wl["T"], grid=wl["grid"])
+    ctx = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
+                        precision=wl["precision"], device=dev, stream=stream.cuda_stream)
+
+    def solve(c):
+        c.set_phi(None)
+        E, st = c.minimize(gtol=1e-8, maxit=args.maxit, raise_on_noconv=args.maxit >= 20000)
+        F, P = c.forces()
+        return st
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        solve(ctx)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.kernel_launches()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    times, evals, evals_lo, iters = [], 0, 0, 0
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = solve(ctx)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            evals += st["evaluations"]
+            evals_lo += st["evaluations_lo"]
+            iters += st["iterations"]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = ctx.kernel_launches() - launches0
+    t_total = max_over_ranks(sum(times), world)
+    dominant = "zgga" if wl["functional"] != "fttf" else "zfinal"
+    kms, kcount = time_dominant(ctx, ofdft, dominant, stream, lambda: solve(ctx))
+    e2e = None
+    if not args.no_e2e:
+        # public API with host buffers: ion positions in, forces and pressure out
+        t_e2e = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.set_positions(cfg["ions"])
+            solve(ctx)
+            t_e2e += time.perf_counter() - t0
+        nat = len(cfg["Z"])
+        e2e = {"value": world * args.steps / max_over_ranks(t_e2e, world), "unit": "solves/s",
+               "h2d_bytes_per_step": nat * 3 * 8, "d2h_bytes_per_step": nat * 3 * 8 + 8 + 16 * 8}
     ctx.close()
+    res = {"metric": "single-point solves/s", "value": world * args.steps / t_total, "unit": "solves/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if wl["precision"] == "fp64" else "f32+f64",
+           "data": "synthetic (seeded hydrogen, random positions)",
+           "config": {"workload": args.workload, "atoms": len(cfg["Z"]), "grid": list(cfg["grid"]),
+                      "functional": wl["functional"], "xc": "PZ81", "T_K": cfg["T"], "rho_gcc": 4.0,
+                      "gtol": 1e-8, "start": "uniform density",
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "l2": "flushed (256 MB write) before every timed step"},
+           "evals_per_step": evals / args.steps, "fp32_evals_per_step": evals_lo / args.steps,
+           "cg_iterations_per_step": iters / args.steps, "evals_per_s": world * evals / t_total,
+           "gpu_launches": launches, "clocks": clk, "e2e": e2e,
+           "roofline": roofline_entry(dominant, cfg["grid"], kms, kcount, clk, read_peaks())}
     return res, evals / args.steps
 
 
 def cpu_baseline(args, evals_per_step, budget_s=15.0):
     """The oracle timed on a bounded sample: full-size energy + potential
-    evaluations for about budget_s seconds, converted to MD steps/s with the
-    CG evaluations per MD step."""
+    evaluations for about budget_s seconds, converted to the workload's
+    metric with the CG evaluations per step (MD step or solve)."""
     import numpy as np
     import oracle as O
     from paper_1406_0835_gb300 import inputs
     wl = WORKLOADS[args.workload]
-    cfg = inputs.config_md(wl["functional"], grid=wl["grid"])
+    if wl["kind"] == "solve":
+        cfg = inputs.config_mixed(wl["T"], grid=wl["grid"])
+        unit = "solves/s"
+    elif wl["kind"] == "eval":
+        cfg = inputs.config_mixed(2.5e5, grid=wl["grid"])
+        unit = "evals/s"
+    else:
+        cfg = inputs.config_md(wl["functional"], grid=wl["grid"])
+        unit = "MD steps/s"
     so = O.System(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"])
     phi = so.uniform_phi() * (1.0 + 0.05 * np.random.default_rng(1).standard_normal(cfg["grid"]))
     O.evaluate(so, phi)
@@ -316,9 +466,9 @@ def cpu_baseline(args, evals_per_step, budget_s=15.0):
     dt = time.perf_counter() - t0
     eps = n / dt
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": eps / evals_per_step, "unit": "MD steps/s", "cores": cores, "kind": "oracle",
+    return {"value": eps / evals_per_step, "unit": unit, "cores": cores, "kind": "oracle",
             "sample": "%d full-size (%s) energy+potential evaluations in %.1f s = %.3f evals/s, "
-                      "divided by %.1f evaluations per MD step" % (n, "x".join(map(str, cfg["grid"])),
+                      "divided by %.1f evaluations per step" % (n, "x".join(map(str, cfg["grid"])),
                                                                    dt, eps, evals_per_step)}
 
 
@@ -329,23 +479,25 @@ def run_reference(args):
     if rank != 0:
         return None
     for _ in range(args.warmup):
-        cpu_baseline(args, EVALS_PER_MD_STEP[args.workload], budget_s=2.0)
+        cpu_baseline(args, EVALS_PER_STEP[args.workload], budget_s=2.0)
     vals = []
     samples = []
     for _ in range(args.steps):
-        cb = cpu_baseline(args, EVALS_PER_MD_STEP[args.workload], budget_s=8.0)
+        cb = cpu_baseline(args, EVALS_PER_STEP[args.workload], budget_s=8.0)
         vals.append(cb["value"])
         samples.append(cb["sample"])
     value = statistics.mean(vals)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"impl": "reference", "metric": "MD steps/s", "value": value, "unit": "MD steps/s",
+    metric, unit, conf = workload_meta(args.workload)
+    conf["parallelism"] = "single process (host cores)"
+    return {"impl": "reference", "metric": metric, "value": value, "unit": unit,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "grid": wl["grid"], "functional": wl["functional"]},
-            "cpu_baseline": {"value": value, "unit": "MD steps/s", "cores": cores, "kind": "oracle",
+            "config": conf,
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
                              "sample": samples[0]},
-            "e2e": {"value": value, "unit": "MD steps/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 
@@ -361,9 +513,12 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    if WORKLOADS[args.workload]["kind"] == "eval":
+    kind = WORKLOADS[args.workload]["kind"]
+    if kind == "eval":
         args.no_cpu = True
         res, eps = run_eval(args, rank, world)
+    elif kind == "solve":
+        res, eps = run_solve(args, rank, world)
     else:
         res, eps = run_ours(args, rank, world)
     if rank == 0:

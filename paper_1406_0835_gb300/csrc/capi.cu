@@ -410,8 +410,9 @@ ofdft_status update_ions(ofdft_ctx *c)
     const GridInfo &g = c->g;
     cudaStream_t st = c->st;
     launch_phases(g, c->nat, c->Rd, c->px, c->py, c->pz, st);
-    launch_vext<double>(g, c->nat, c->Zd, c->px, c->py, c->pz, (double2 *)c->f[0].vext, st);
-    if (c->f[1].valid) launch_vext<float>(g, c->nat, c->Zd, c->px, c->py, c->pz, (float2 *)c->f[1].vext, st);
+    launch_vext(g, c->nat, c->Zd, c->px, c->py, c->pz, (double2 *)c->f[0].vext, st);
+    if (c->f[1].valid)
+        launch_convert<double, float>(2 * g.NH, (const double *)c->f[0].vext, (float *)c->f[1].vext, st);
     double L[3] = {g.Lx, g.Ly, g.Lz};
     launch_ewald_real(c->nat, c->Rd, c->Zd, L, c->ew_alpha, c->ew_rcut, c->ew_nimg, c->eion, c->ewF, st);
     int nb = launch_ewald_recip(c->nat, c->Rd, c->Zd, c->nGe, c->Gv, c->wG, c->Se, c->ewpart, c->ewF, st);
@@ -698,16 +699,18 @@ ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
     if (s != OFDFT_OK) return s;
     const GridInfo &g = c->g;
     const double2 *nG = (const double2 *)f.spec + (c->fp.kind == 0 ? f.spec_stride : 0);
-    size_t need = (size_t)c->nat * 608 * 3 + 16;
+    size_t need = (size_t)c->nat * 1216 * 3 + 16;
     if (need > c->fpart_len) {
         if (c->fpart) cudaFree(c->fpart);
         c->fpart = nullptr;
         CK(cudaMalloc(&c->fpart, need * sizeof(double)));
         c->fpart_len = need;
     }
-    int nchunk = launch_lpp_forces<double>(g, c->nat, c->Zd, c->px, c->py, c->pz, nG, c->fpart, c->st);
+    // the third spectrum is free after an evaluation (ftTF and GGA alike)
+    double2 *cn = (double2 *)f.spec + 2 * f.spec_stride;
+    int nchunk = launch_lpp_forces<double>(g, c->nat, c->Zd, c->px, c->py, c->pz, nG, cn, c->fpart, c->st);
     launch_force_reduce(c->nat, nchunk, c->fpart, c->Fd, 0, c->st);
-    c->launches += 2;
+    c->launches += 3;
     std::vector<double> F(3 * c->nat), Fe(3 * c->nat);
     CK(cudaMemcpyAsync(F.data(), c->Fd, F.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(Fe.data(), c->ewF, Fe.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -908,6 +911,7 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     g.omega = g.Lx * g.Ly * g.Lz;
     g.dV = g.omega / (double)g.N;
     g.rc = p.rc;
+    grid_reciprocal(g);
     c->nat = nat;
     c->R.assign(ions, ions + 3 * nat);
     c->Z.assign(Z, Z + nat);

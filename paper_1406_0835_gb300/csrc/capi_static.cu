@@ -214,6 +214,7 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     g.omega = g.Lx * g.Ly * g.Lz;
     g.dV = g.omega / (double)N;
     g.rc = rc;
+    grid_reciprocal(g);
     const double T = T_kelvin * 3.166811563e-6;
 
     // twiddles for the three axes (host stack -> scratch)
@@ -236,7 +237,7 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     double2 *py = px + (size_t)nat * g.nx, *pz = py + (size_t)nat * g.ny;
     double2 *vext = (double2 *)(base + kOffVext);
     launch_phases(g, nat, Rd, px, py, pz, st);
-    launch_vext<double>(g, nat, Zd, px, py, pz, vext, st);
+    launch_vext(g, nat, Zd, px, py, pz, vext, st);
 
     // evaluation (same kernel sequence as the context path)
     const size_t specN = kSpecBytes / sizeof(double2);

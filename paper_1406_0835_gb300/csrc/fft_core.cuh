@@ -154,31 +154,45 @@ __device__ C *fft_lines(C *a, C *b, const FftAxis &ax, int nl, int lstride, int 
     return a;
 }
 
-// Deterministic block sum of NQ doubles; thread 0 returns the totals in v.
-template <int NQ> __device__ __forceinline__ void block_sum(double *v)
+// Per-thread accumulator type of the reductions: FP64 fields accumulate in
+// FP64; FP32 fields accumulate per thread and per warp in FP32 (a few hundred
+// terms) and across warps and blocks in FP64, which keeps the FP64 pipe out
+// of the single-precision kernels.
+template <typename T> struct AccT { typedef double type; };
+template <> struct AccT<float> { typedef float type; };
+
+// Deterministic block sum of NQ values; thread 0 returns the totals in tot
+// (FP64).  Warp sums in the accumulator type, the cross-warp sum in FP64.
+template <int NQ, typename A> __device__ __forceinline__ void block_sum(A *v, double *tot)
 {
     __shared__ double red[32][NQ];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        double x = v[q];
+        A x = v[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         v[q] = x;
     }
     if (lane == 0)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) red[wid][q] = v[q];
+        for (int q = 0; q < NQ; ++q) red[wid][q] = (double)v[q];
     __syncthreads();
     if (threadIdx.x == 0) {
         const int nw = (blockDim.x + 31) >> 5;
         for (int q = 0; q < NQ; ++q) {
             double s = 0.0;
             for (int w = 0; w < nw; ++w) s += red[w][q];
-            v[q] = s;
+            tot[q] = s;
         }
     }
     __syncthreads();
+}
+
+// In-place form for FP64 accumulators.
+template <int NQ> __device__ __forceinline__ void block_sum(double *v)
+{
+    block_sum<NQ, double>(v, v);
 }
 
 }  // namespace ofdft

@@ -66,14 +66,15 @@ int launch_cg_dhat(long long n, const T *g, T *d, const T *phi, const T *v, doub
 void launch_phases(const GridInfo &g, int nat, const double *R, double2 *px, double2 *py,
                    double2 *pz, cudaStream_t st);
 // v_ext(G) on the half spectrum, Hermitian-symmetrised on Nyquist planes.
-template <typename T>
+// (FP64; a single-precision copy is made with launch_convert.)
 void launch_vext(const GridInfo &g, int nat, const double *Z, const double2 *px,
-                 const double2 *py, const double2 *pz, cplx<T> *vext, cudaStream_t st);
+                 const double2 *py, const double2 *pz, double2 *vext, cudaStream_t st);
 // Local-pseudopotential forces from n(G): part[(I * nchunk + c) * 3 + a]; returns nchunk.
+// cn is scratch of NH double2.
 template <typename T>
 int launch_lpp_forces(const GridInfo &g, int nat, const double *Z, const double2 *px,
-                      const double2 *py, const double2 *pz, const cplx<T> *nG, double *part,
-                      cudaStream_t st);
+                      const double2 *py, const double2 *pz, const cplx<T> *nG, double2 *cn,
+                      double *part, cudaStream_t st);
 // Sum force partials over chunks into F[nat][3] (+= if accumulate).
 void launch_force_reduce(int nat, int nchunk, const double *part, double *F, int accumulate,
                          cudaStream_t st);

@@ -18,26 +18,28 @@ namespace {
 
 constexpr int kTK = 8;  // half-spectrum columns per y/x tile
 
-struct Gk {
-    double gx, gy, gz, g2;  // G with +n/2 on Nyquist planes
-    double dx, dy, dz;      // first-derivative multipliers (0 on the own-axis Nyquist plane)
-    double w;               // Hermitian weight of the half spectrum (1 on kz = 0, nz/2)
+// G vector of the half-spectrum point (ix, iy, kz) in the accumulator
+// precision A, from the per-axis reciprocal spacings (no divisions).
+template <typename A> struct Gk {
+    A gx, gy, gz, g2;  // G with +n/2 on Nyquist planes
+    A dx, dy, dz;      // first-derivative multipliers (0 on the own-axis Nyquist plane)
+    A w;               // Hermitian weight of the half spectrum (1 on kz = 0, nz/2)
 };
 
-__device__ __forceinline__ Gk gvec(const GridInfo &g, int ix, int iy, int kz)
+template <typename A>
+__device__ __forceinline__ Gk<A> gvec(const GridInfo &g, A bx, A by, A bz, int ix, int iy, int kz)
 {
-    Gk r;
-    const double tp = 6.283185307179586477;
+    Gk<A> r;
     int kx = ix <= g.nx / 2 ? ix : ix - g.nx;
     int ky = iy <= g.ny / 2 ? iy : iy - g.ny;
-    r.gx = tp * kx / g.Lx;
-    r.gy = tp * ky / g.Ly;
-    r.gz = tp * kz / g.Lz;
+    r.gx = A(kx) * bx;
+    r.gy = A(ky) * by;
+    r.gz = A(kz) * bz;
     r.g2 = r.gx * r.gx + r.gy * r.gy + r.gz * r.gz;
-    r.dx = (2 * ix == g.nx) ? 0.0 : r.gx;
-    r.dy = (2 * iy == g.ny) ? 0.0 : r.gy;
-    r.dz = (2 * kz == g.nz) ? 0.0 : r.gz;
-    r.w = (kz == 0 || 2 * kz == g.nz) ? 1.0 : 2.0;
+    r.dx = (2 * ix == g.nx) ? A(0) : r.gx;
+    r.dy = (2 * iy == g.ny) ? A(0) : r.gy;
+    r.dz = (2 * kz == g.nz) ? A(0) : r.gz;
+    r.w = (kz == 0 || 2 * kz == g.nz) ? A(1) : A(2);
     return r;
 }
 
@@ -159,7 +161,8 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, cplx<T> *__restrict__ g0,
         res[a] = fft_lines<C, true>(buf[a], scratch, az, nl, nz, 1, false);
         if (res[a] == scratch) scratch = buf[a];
     }
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    typedef typename AccT<T>::type A;
+    A acc[6] = {0, 0, 0, 0, 0, 0};
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
         const int line = i / nz, e = i - line * nz;
         const int p = line >> 1, hi = line & 1;
@@ -173,12 +176,12 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, cplx<T> *__restrict__ g0,
         T eps = T(0), vxc = T(0);
         if (xc) pz81_point<T>(n, eps, vxc);
         vpart[rbase + i] = o.dfdn + vxc;
-        acc[0] += (double)o.f;
-        acc[1] += (double)o.ts;
-        acc[2] += (double)(n * eps);
-        acc[3] += (double)(n * o.dfdn - o.f);
-        acc[4] += (double)(o.wc * gg);
-        acc[5] += (double)(n * (vxc - eps));
+        acc[0] += (A)o.f;
+        acc[1] += (A)o.ts;
+        acc[2] += (A)(n * eps);
+        acc[3] += (A)(n * o.dfdn - o.f);
+        acc[4] += (A)(o.wc * gg);
+        acc[5] += (A)(n * (vxc - eps));
         for (int a = 0; a < 3; ++a) {
             T *d = reinterpret_cast<T *>(&res[a][p * nz + e]);
             d[hi] = o.wc * gr[a];
@@ -192,9 +195,10 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, cplx<T> *__restrict__ g0,
         __syncthreads();
         if (X == scratch) scratch = res[a];
     }
-    block_sum<6>(acc);
+    double tot[6];
+    block_sum<6, A>(acc, tot);
     if (threadIdx.x == 0)
-        for (int q = 0; q < 6; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = acc[q];
+        for (int q = 0; q < 6; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
 }
 
 // Final stage: C2R of D(G); v = D(r) + v_part (GGA) or, for ftTF, the
@@ -226,7 +230,8 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const cplx<T> *__restric
     pack_c2r(dspec, obase, nl, nz, K, A);
     __syncthreads();
     C *X = fft_lines<C, true>(A, B, az, nl, nz, 1, false);
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    typedef typename AccT<T>::type Ac;
+    Ac acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
         const int line = i / nz, e = i - line * nz;
         C d = X[(line >> 1) * nz + e];
@@ -239,25 +244,26 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const cplx<T> *__restric
             T eps = T(0), vxc = T(0);
             if (xc) pz81_point<T>(n, eps, vxc);
             v = o.dfdn + vxc + dr;
-            acc[0] += (double)o.f;
-            acc[1] += (double)o.ts;
-            acc[2] += (double)(n * eps);
-            acc[3] += (double)(n * o.dfdn - o.f);
-            acc[5] += (double)(n * (vxc - eps));
+            acc[0] += (Ac)o.f;
+            acc[1] += (Ac)o.ts;
+            acc[2] += (Ac)(n * eps);
+            acc[3] += (Ac)(n * o.dfdn - o.f);
+            acc[5] += (Ac)(n * (vxc - eps));
         } else {
             v = vpart[rbase + i] + dr;
         }
         vout[rbase + i] = v;
-        acc[6] += (double)(n * v);
-        acc[7] += (double)n;
+        acc[6] += (Ac)(n * v);
+        acc[7] += (Ac)n;
         if (dhat != nullptr) {
             T dphi = -s * phi[rbase + i] + c * dhat[rbase + i];
-            acc[8] += 2.0 * (double)(ph * v) * (double)dphi;
+            acc[8] += Ac(2) * (Ac)(ph * v) * (Ac)dphi;
         }
     }
-    block_sum<9>(acc);
+    double tot[9];
+    block_sum<9, Ac>(acc, tot);
     if (threadIdx.x == 0)
-        for (int q = 0; q < 9; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = acc[q];
+        for (int q = 0; q < 9; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
 }
 
 // ------------------------------------------------------------- y/x passes
@@ -338,22 +344,23 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, cplx<T> *__restrict__ nspec,
     load_tile(nspec, t, nx, A);
     __syncthreads();
     C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, kTK, true);
-    const double invN = 1.0 / (double)g.N;
-    const double fourpi = 12.566370614359172954;
-    double acc[3] = {0, 0, 0};
+    typedef typename AccT<T>::type Ac;
+    const Ac bx = Ac(g.bx), by = Ac(g.by), bz = Ac(g.bz), hr = Ac(0.5 * g.rc * g.rc);
+    const T invN = T(1.0 / (double)g.N);
+    Ac acc[3] = {0, 0, 0};     // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
     for (int i = threadIdx.x; i < nx * kTK; i += blockDim.x) {
         const int r = i / kTK, c = i - r * kTK;
         if (c >= t.ncol) continue;
-        C nG = cscale(X[i], T(invN));
+        C nG = cscale(X[i], invN);
         N[i] = nG;
-        Gk k = gvec(g, r, t.outer, t.kz0 + c);
-        if (k.g2 > 0.0) {
+        Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
+        if (k.g2 > Ac(0)) {
             C ve = vext[t.base + r * t.rstride + c];
-            double n2 = (double)nG.x * nG.x + (double)nG.y * nG.y;
-            double re = (double)nG.x * ve.x + (double)nG.y * ve.y;
-            acc[0] += k.w * 0.5 * g.omega * fourpi * n2 / k.g2;
-            acc[1] += k.w * g.omega * re;
-            acc[2] += k.w * (1.0 / 3.0) * re * (1.0 - 0.5 * k.g2 * g.rc * g.rc);
+            Ac n2 = (Ac)nG.x * nG.x + (Ac)nG.y * nG.y;
+            Ac re = (Ac)nG.x * ve.x + (Ac)nG.y * ve.y;
+            acc[0] += k.w * n2 / k.g2;
+            acc[1] += k.w * re;
+            acc[2] += k.w * re * (Ac(1) - hr * k.g2);
         }
     }
     __syncthreads();
@@ -362,7 +369,7 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, cplx<T> *__restrict__ nspec,
     for (int a = 0; a < 3; ++a) {
         for (int i = threadIdx.x; i < nx * kTK; i += blockDim.x) {
             const int r = i / kTK, c = i - r * kTK;
-            Gk k = gvec(g, r, t.outer, t.kz0 + min(c, t.ncol - 1));
+            Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + min(c, t.ncol - 1));
             T d = T(a == 0 ? k.dx : (a == 1 ? k.dy : k.dz));
             C v = N[i];
             A[i] = cmk<C>(-d * v.y, d * v.x);      // i D_a n(G)
@@ -372,9 +379,15 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, cplx<T> *__restrict__ nspec,
         store_tile(outs[a], t, nx, Y);
         __syncthreads();
     }
-    block_sum<3>(acc);
-    if (threadIdx.x == 0)
-        for (int q = 0; q < 3; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = acc[q];
+    double tot[3];
+    block_sum<3, Ac>(acc, tot);
+    if (threadIdx.x == 0) {
+        // E_H = (Omega/2) sum 4 pi |n|^2/G^2, E_loc = Omega sum Re(n* v_ext),
+        // P_loc = (1/3) sum Re(n* v_ext)(1 - G^2 rc^2/2)
+        part[blockIdx.x] = 0.5 * g.omega * 12.566370614359172954 * tot[0];
+        part[(size_t)gridDim.x + blockIdx.x] = g.omega * tot[1];
+        part[(size_t)2 * gridDim.x + blockIdx.x] = (1.0 / 3.0) * tot[2];
+    }
 }
 
 // x pass, ftTF variant: forward x -> energies -> v_HL(G) = 4 pi n/G^2 + v_ext
@@ -393,22 +406,24 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, cplx<T> *__restrict__ spec,
     load_tile(spec, t, nx, A);
     __syncthreads();
     C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, kTK, true);
-    const double invN = 1.0 / (double)g.N;
-    const double fourpi = 12.566370614359172954;
-    double acc[3] = {0, 0, 0};
+    typedef typename AccT<T>::type Ac;
+    const Ac bx = Ac(g.bx), by = Ac(g.by), bz = Ac(g.bz), hr = Ac(0.5 * g.rc * g.rc);
+    const Ac fourpi = Ac(12.566370614359172954);
+    const T invN = T(1.0 / (double)g.N);
+    Ac acc[3] = {0, 0, 0};
     for (int i = threadIdx.x; i < nx * kTK; i += blockDim.x) {
         const int r = i / kTK, c = i - r * kTK;
         if (c >= t.ncol) continue;
-        C nG = cscale(X[i], T(invN));
-        Gk k = gvec(g, r, t.outer, t.kz0 + c);
+        C nG = cscale(X[i], invN);
+        Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
         C ve = vext[t.base + r * t.rstride + c];
         C out = cmk<C>(T(0), T(0));
-        if (k.g2 > 0.0) {
-            double n2 = (double)nG.x * nG.x + (double)nG.y * nG.y;
-            double re = (double)nG.x * ve.x + (double)nG.y * ve.y;
-            acc[0] += k.w * 0.5 * g.omega * fourpi * n2 / k.g2;
-            acc[1] += k.w * g.omega * re;
-            acc[2] += k.w * (1.0 / 3.0) * re * (1.0 - 0.5 * k.g2 * g.rc * g.rc);
+        if (k.g2 > Ac(0)) {
+            Ac n2 = (Ac)nG.x * nG.x + (Ac)nG.y * nG.y;
+            Ac re = (Ac)nG.x * ve.x + (Ac)nG.y * ve.y;
+            acc[0] += k.w * n2 / k.g2;
+            acc[1] += k.w * re;
+            acc[2] += k.w * re * (Ac(1) - hr * k.g2);
             T kh = T(fourpi / k.g2);
             out = cmk<C>(kh * nG.x + ve.x, kh * nG.y + ve.y);
         }
@@ -421,9 +436,13 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, cplx<T> *__restrict__ spec,
         C *Y = fft_lines<C, true>(X, other, ax, t.ncol, 1, kTK, true);
         store_tile(spec, t, nx, Y);
     }
-    block_sum<3>(acc);
-    if (threadIdx.x == 0)
-        for (int q = 0; q < 3; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = acc[q];
+    double tot[3];
+    block_sum<3, Ac>(acc, tot);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = 0.5 * g.omega * 12.566370614359172954 * tot[0];
+        part[(size_t)gridDim.x + blockIdx.x] = g.omega * tot[1];
+        part[(size_t)2 * gridDim.x + blockIdx.x] = (1.0 / 3.0) * tot[2];
+    }
 }
 
 // x pass, divergence variant: D(G) = v_H(G) + v_ext(G) - sum_a i D_a W_a(G)
@@ -440,14 +459,16 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const cplx<T> *__restrict__ nG,
     C *B = A + nx * kTK;
     C *D = B + nx * kTK;
     ColTile t = col_tile(g, true);
-    const double fourpi = 12.566370614359172954;
+    typedef typename AccT<T>::type Ac;
+    const Ac bx = Ac(g.bx), by = Ac(g.by), bz = Ac(g.bz);
+    const Ac fourpi = Ac(12.566370614359172954);
     const T invN = T(1.0 / (double)g.N);
     for (int i = threadIdx.x; i < nx * kTK; i += blockDim.x) {
         const int r = i / kTK, c = i - r * kTK;
         if (c >= t.ncol) continue;
-        Gk k = gvec(g, r, t.outer, t.kz0 + c);
+        Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
         C out = cmk<C>(T(0), T(0));
-        if (k.g2 > 0.0) {
+        if (k.g2 > Ac(0)) {
             C n = nG[t.base + r * t.rstride + c];
             C ve = vext[t.base + r * t.rstride + c];
             T kh = T(fourpi / k.g2);
@@ -463,7 +484,7 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const cplx<T> *__restrict__ nG,
         for (int i = threadIdx.x; i < nx * kTK; i += blockDim.x) {
             const int r = i / kTK, c = i - r * kTK;
             if (c >= t.ncol) continue;
-            Gk k = gvec(g, r, t.outer, t.kz0 + c);
+            Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
             T d = T(a == 0 ? k.dx : (a == 1 ? k.dy : k.dz)) * invN;
             C wv = X[i];
             D[i] = cmk<C>(D[i].x + d * wv.y, D[i].y - d * wv.x);   // -= i d W

@@ -37,9 +37,10 @@ template <typename T> __global__ void k_fill(long long n, T *x, T val)
 template <typename T> __global__ void k_scale(long long n, T *x, double s, const double *sp)
 {
     if (sp != nullptr) s = *sp;
+    const T st = (T)s;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        x[i] = (T)((double)x[i] * s);
+        x[i] = x[i] * st;
 }
 
 template <typename T, typename U> __global__ void k_convert(long long n, const T *x, U *y)
@@ -51,14 +52,16 @@ template <typename T, typename U> __global__ void k_convert(long long n, const T
 
 template <typename T> __global__ void k_sumsq(long long n, const T *__restrict__ x, double *part)
 {
-    double v[1] = {0.0};
+    typedef typename AccT<T>::type A;
+    A v[1] = {A(0)};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        double a = (double)x[i];
+        A a = (A)x[i];
         v[0] += a * a;
     }
-    block_sum<1>(v);
-    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+    double tot[1];
+    block_sum<1, A>(v, tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
 }
 
 template <typename T>
@@ -82,18 +85,21 @@ __global__ void k_cg_grad(long long n, const T *__restrict__ phi, const T *__res
                           const T *__restrict__ gprev, double *part)
 {
     if (mup != nullptr) mu = *mup;
-    double acc[2] = {0.0, 0.0};
+    typedef typename AccT<T>::type A;
+    const T mut = T(mu);
+    A acc[2] = {A(0), A(0)};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        T gi = T(2) * phi[i] * (v[i] - T(mu));
+        T gi = T(2) * phi[i] * (v[i] - mut);
         g[i] = gi;
-        acc[0] += (double)gi * (double)gi;
-        if (gprev != nullptr) acc[1] += (double)gi * (double)gprev[i];
+        acc[0] += (A)gi * (A)gi;
+        if (gprev != nullptr) acc[1] += (A)gi * (A)gprev[i];
     }
-    block_sum<2>(acc);
+    double tot[2];
+    block_sum<2, A>(acc, tot);
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = acc[0];
-        part[gridDim.x + blockIdx.x] = acc[1];
+        part[blockIdx.x] = tot[0];
+        part[gridDim.x + blockIdx.x] = tot[1];
     }
 }
 
@@ -102,22 +108,25 @@ __global__ void k_cg_dir(long long n, const T *__restrict__ g, T *__restrict__ d
                          const double *betap, const T *__restrict__ phi, double *part)
 {
     if (betap != nullptr) beta = *betap;
-    double acc[5] = {0, 0, 0, 0, 0};
+    typedef typename AccT<T>::type A;
+    const A ba = A(beta);
+    A acc[5] = {0, 0, 0, 0, 0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         T gi = g[i];
-        T di = (beta == 0.0) ? -gi : (T)(-(double)gi + beta * (double)d[i]);
+        T di = (beta == 0.0) ? -gi : (T)(-(A)gi + ba * (A)d[i]);
         d[i] = di;
-        double p = (double)phi[i];
-        acc[0] += p * (double)di;
-        acc[1] += (double)di * (double)di;
-        acc[2] += (double)di * (double)gi;
+        A p = (A)phi[i];
+        acc[0] += p * (A)di;
+        acc[1] += (A)di * (A)di;
+        acc[2] += (A)di * (A)gi;
         acc[3] += p * p;
-        acc[4] += p * (double)gi;
+        acc[4] += p * (A)gi;
     }
-    block_sum<5>(acc);
+    double tot[5];
+    block_sum<5, A>(acc, tot);
     if (threadIdx.x == 0)
-        for (int q = 0; q < 5; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = acc[q];
+        for (int q = 0; q < 5; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
 }
 
 template <typename T>
@@ -130,17 +139,20 @@ __global__ void k_cg_dhat(long long n, const T *__restrict__ g, T *__restrict__ 
         c2 = c12r[1];
         restart = c12r[2] != 0.0;
     }
-    double acc[1] = {0.0};
+    typedef typename AccT<T>::type A;
+    const A c1a = A(c1), c2a = A(c2);
+    A acc[1] = {A(0)};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        double di = restart ? -(double)g[i] : (double)d[i] - c1 * (double)phi[i];
+        A di = restart ? -(A)g[i] : (A)d[i] - c1a * (A)phi[i];
         d[i] = (T)di;
-        T dh = (T)(c2 * di);
+        T dh = (T)(c2a * di);
         dhat[i] = dh;
-        acc[0] += 2.0 * (double)phi[i] * (double)v[i] * (double)dh;
+        acc[0] += A(2) * (A)phi[i] * (A)v[i] * (A)dh;
     }
-    block_sum<1>(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+    double tot[1];
+    block_sum<1, A>(acc, tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
 }
 
 // Accept a line-search trial: phi <- phi_trial, v <- v_trial, g_prev <- g,
@@ -163,7 +175,6 @@ __global__ void k_accept(long long n, const int *accepted, T *__restrict__ phi,
 __global__ void k_phases(GridInfo g, int nat, const double *__restrict__ R, double2 *px,
                          double2 *py, double2 *pz)
 {
-    const double tp = 6.283185307179586477;
     const int per = g.nx + g.ny + g.K;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nat * per; i += gridDim.x * blockDim.x) {
         const int I = i / per, j = i - I * per;
@@ -171,18 +182,18 @@ __global__ void k_phases(GridInfo g, int nat, const double *__restrict__ R, doub
         double2 *dst;
         if (j < g.nx) {
             int k = j <= g.nx / 2 ? j : j - g.nx;
-            G = tp * k / g.Lx;
+            G = (double)k * g.bx;
             r = R[3 * I];
             dst = px + (size_t)I * g.nx + j;
         } else if (j < g.nx + g.ny) {
             int jj = j - g.nx;
             int k = jj <= g.ny / 2 ? jj : jj - g.ny;
-            G = tp * k / g.Ly;
+            G = (double)k * g.by;
             r = R[3 * I + 1];
             dst = py + (size_t)I * g.ny + jj;
         } else {
             int jj = j - g.nx - g.ny;
-            G = tp * jj / g.Lz;
+            G = (double)jj * g.bz;
             r = R[3 * I + 2];
             dst = pz + (size_t)I * g.K + jj;
         }
@@ -204,113 +215,157 @@ __device__ __forceinline__ double lpp_w(const GridInfo &g, double g2)
     return g2 > 0.0 ? -12.566370614359172954 * exp(-0.25 * g2 * g.rc * g.rc) / (g.omega * g2) : 0.0;
 }
 
+// Half-spectrum point (ix, iy, kz): G from the reciprocal spacings, Nyquist
+// flags and Hermitian weight.
 struct Hk {
     int ix, iy, kz;
     bool nx_, ny_, nz_;
     double gx, gy, gz, g2, wk;
 };
 
-__device__ __forceinline__ Hk hidx(const GridInfo &g, long long q)
+__device__ __forceinline__ Hk hk_at(const GridInfo &g, int ix, int iy, int kz)
 {
     Hk h;
-    h.kz = (int)(q % g.K);
-    long long r = q / g.K;
-    h.iy = (int)(r % g.ny);
-    h.ix = (int)(r / g.ny);
-    const double tp = 6.283185307179586477;
-    int kx = h.ix <= g.nx / 2 ? h.ix : h.ix - g.nx;
-    int ky = h.iy <= g.ny / 2 ? h.iy : h.iy - g.ny;
-    h.gx = tp * kx / g.Lx;
-    h.gy = tp * ky / g.Ly;
-    h.gz = tp * h.kz / g.Lz;
+    h.ix = ix;
+    h.iy = iy;
+    h.kz = kz;
+    int kx = ix <= g.nx / 2 ? ix : ix - g.nx;
+    int ky = iy <= g.ny / 2 ? iy : iy - g.ny;
+    h.gx = (double)kx * g.bx;
+    h.gy = (double)ky * g.by;
+    h.gz = (double)kz * g.bz;
     h.g2 = h.gx * h.gx + h.gy * h.gy + h.gz * h.gz;
-    h.nx_ = 2 * h.ix == g.nx;
-    h.ny_ = 2 * h.iy == g.ny;
-    h.nz_ = 2 * h.kz == g.nz;
-    h.wk = (h.kz == 0 || h.nz_) ? 1.0 : 2.0;
+    h.nx_ = 2 * ix == g.nx;
+    h.ny_ = 2 * iy == g.ny;
+    h.nz_ = 2 * kz == g.nz;
+    h.wk = (kz == 0 || h.nz_) ? 1.0 : 2.0;
     return h;
+}
+
+// Flat half-spectrum index (< 2^31 for every supported grid) to (ix, iy, kz).
+__device__ __forceinline__ Hk hk_flat(const GridInfo &g, int q)
+{
+    const int kz = q % g.K, r = q / g.K;
+    return hk_at(g, r / g.ny, r % g.ny, kz);
 }
 
 // v(G) = w(G) sum_I Z_I (P_I + P'_I)/2 with P = exp(-i G.R), P' = exp(i G'.R),
 // G' = -G except on Nyquist axes where G'_a = +G_a (the Hermitian partner
 // folded onto the stored plane).  Off the Nyquist planes P' = P.
-template <typename T>
+// One block per (ix, iy) row; the row factors Z_I e^{-i(Gx X_I + Gy Y_I)} are
+// staged in shared memory in chunks of atoms, and thread kz sums over atoms.
 __global__ void k_vext(GridInfo g, int nat, const double *__restrict__ Z,
                        const double2 *__restrict__ px, const double2 *__restrict__ py,
-                       const double2 *__restrict__ pz, cplx<T> *__restrict__ vext)
+                       const double2 *__restrict__ pz, double2 *__restrict__ vext)
 {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.NH;
-         q += (long long)gridDim.x * blockDim.x) {
-        Hk h = hidx(g, q);
-        double w = lpp_w(g, h.g2);
-        double2 acc = make_double2(0.0, 0.0);
-        const bool nyq = h.nx_ || h.ny_ || h.nz_;
-        if (w != 0.0) {
-            for (int I = 0; I < nat; ++I) {
-                double2 a = px[(size_t)I * g.nx + h.ix], b = py[(size_t)I * g.ny + h.iy],
-                        c = pz[(size_t)I * g.K + h.kz];
-                double2 P = zmul(zmul(a, b), c);
-                if (nyq) {
-                    if (h.nx_) a.y = -a.y;
-                    if (h.ny_) b.y = -b.y;
-                    if (h.nz_) c.y = -c.y;
-                    double2 Pp = zmul(zmul(a, b), c);
-                    P = make_double2(0.5 * (P.x + Pp.x), 0.5 * (P.y + Pp.y));
-                }
-                acc.x += Z[I] * P.x;
-                acc.y += Z[I] * P.y;
+    constexpr int kChunk = 256;
+    __shared__ double2 a[kChunk], b[kChunk];
+    const int ix = blockIdx.x / g.ny, iy = blockIdx.x - ix * g.ny;
+    const bool rnyq = (2 * ix == g.nx) || (2 * iy == g.ny);
+    double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    double2 acc2[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    for (int I0 = 0; I0 < nat; I0 += kChunk) {
+        const int nI = min(kChunk, nat - I0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < nI; j += blockDim.x) {
+            const int I = I0 + j;
+            double2 u = px[(size_t)I * g.nx + ix], v = py[(size_t)I * g.ny + iy];
+            double2 p = zmul(u, v);
+            a[j] = make_double2(Z[I] * p.x, Z[I] * p.y);
+            if (rnyq) {
+                if (2 * ix == g.nx) u.y = -u.y;
+                if (2 * iy == g.ny) v.y = -v.y;
+                double2 pp = zmul(u, v);
+                b[j] = make_double2(Z[I] * pp.x, Z[I] * pp.y);
             }
         }
-        vext[q] = cmk<cplx<T>>((T)(w * acc.x), (T)(w * acc.y));
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kz = threadIdx.x + h * blockDim.x;
+            if (kz >= g.K) continue;
+            const bool znyq = 2 * kz == g.nz;
+            const double2 *pzc = pz + (size_t)I0 * g.K + kz;
+            for (int j = 0; j < nI; ++j) {
+                double2 c = pzc[(size_t)j * g.K];
+                double2 t = zmul(a[j], c);
+                acc[h].x += t.x;
+                acc[h].y += t.y;
+                if (rnyq || znyq) {
+                    double2 bb = rnyq ? b[j] : a[j];
+                    if (znyq) c.y = -c.y;
+                    double2 t2 = zmul(bb, c);
+                    acc2[h].x += t2.x;
+                    acc2[h].y += t2.y;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int kz = threadIdx.x + h * blockDim.x;
+        if (kz >= g.K) continue;
+        Hk k = hk_at(g, ix, iy, kz);
+        const double w = lpp_w(g, k.g2);
+        double2 v = acc[h];
+        if (rnyq || k.nz_) v = make_double2(0.5 * (v.x + acc2[h].x), 0.5 * (v.y + acc2[h].y));
+        vext[(size_t)blockIdx.x * g.K + kz] = make_double2(w * v.x, w * v.y);
+    }
+}
+
+// Per-point weight of the local forces: cn(G) = -Omega w_k w(G) conj(n(G)).
+template <typename T>
+__global__ void k_lpp_prep(GridInfo g, const cplx<T> *__restrict__ nG, double2 *__restrict__ cn)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < (int)g.NH; q += gridDim.x * blockDim.x) {
+        Hk h = hk_flat(g, q);
+        const double s = -g.omega * h.wk * lpp_w(g, h.g2);
+        cplx<T> n = nG[q];
+        cn[q] = make_double2(s * (double)n.x, -s * (double)n.y);
     }
 }
 
 // F_I,a = -Omega sum_half w_k Re(conj(n(G)) dv_I(G)/dR_I,a),
-// dv_I/dR_a = Z_I w(G) (-i G_a P + i G'_a P')/2.
-template <typename T>
+// dv_I/dR_a = Z_I w(G) (-i G_a P + i G'_a P')/2, i.e. with cn from k_lpp_prep
+// F_I,a = Z_I sum G_a Im(cn P) off the Nyquist planes.  Block (atom, chunk).
 __global__ void k_lpp_forces(GridInfo g, int nat, const double *__restrict__ Z,
                              const double2 *__restrict__ px, const double2 *__restrict__ py,
-                             const double2 *__restrict__ pz, const cplx<T> *__restrict__ nG,
+                             const double2 *__restrict__ pz, const double2 *__restrict__ cn,
                              double *__restrict__ part)
 {
     const int I = blockIdx.x, chunk = blockIdx.y, nchunk = gridDim.y;
-    const long long per = (g.NH + nchunk - 1) / nchunk;
-    const long long q0 = chunk * per;
-    const long long q1 = min(g.NH, q0 + per);
+    const int NH = (int)g.NH;
+    const int per = (NH + nchunk - 1) / nchunk;
+    const int q0 = chunk * per;
+    const int q1 = min(NH, q0 + per);
+    const double2 *pxI = px + (size_t)I * g.nx, *pyI = py + (size_t)I * g.ny, *pzI = pz + (size_t)I * g.K;
     double acc[3] = {0.0, 0.0, 0.0};
-    for (long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-        Hk h = hidx(g, q);
-        double w = lpp_w(g, h.g2);
-        if (w == 0.0) continue;
-        double2 a = px[(size_t)I * g.nx + h.ix], b = py[(size_t)I * g.ny + h.iy],
-                c = pz[(size_t)I * g.K + h.kz];
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        Hk h = hk_flat(g, q);
+        double2 a = pxI[h.ix], b = pyI[h.iy], c = pzI[h.kz];
         double2 P = zmul(zmul(a, b), c);
-        cplx<T> nv = nG[q];
-        double nr = (double)nv.x, ni = (double)nv.y;
-        // Re(conj(n) * (-i G P)) = G * Im(conj(n) P) ... with sign folded below
-        double imP = nr * P.y - ni * P.x;        // Im(conj(n) P)
-        double pre = -g.omega * h.wk * Z[I] * w;
+        double2 w = cn[q];
+        double imP = w.x * P.y + w.y * P.x;        // Im(cn P)
         if (!(h.nx_ || h.ny_ || h.nz_)) {
-            // Re(conj(n)(-i G_a P)) = G_a Im(conj(n) P)
-            acc[0] += pre * h.gx * imP;
-            acc[1] += pre * h.gy * imP;
-            acc[2] += pre * h.gz * imP;
+            acc[0] += h.gx * imP;
+            acc[1] += h.gy * imP;
+            acc[2] += h.gz * imP;
         } else {
             if (h.nx_) a.y = -a.y;
             if (h.ny_) b.y = -b.y;
             if (h.nz_) c.y = -c.y;
             double2 Pp = zmul(zmul(a, b), c);
-            double imPp = nr * Pp.y - ni * Pp.x;   // Im(conj(n) P')
-            // Re(conj(n)(i G'_a P')) = -G'_a Im(conj(n) P'); G'_a = +G_a on Nyquist axes
+            double imPp = w.x * Pp.y + w.y * Pp.x;  // Im(cn P')
+            // i G'_a P' enters with the opposite sign; G'_a = +G_a on Nyquist axes
             double gpx = h.nx_ ? h.gx : -h.gx, gpy = h.ny_ ? h.gy : -h.gy, gpz = h.nz_ ? h.gz : -h.gz;
-            acc[0] += pre * 0.5 * (h.gx * imP - gpx * imPp);
-            acc[1] += pre * 0.5 * (h.gy * imP - gpy * imPp);
-            acc[2] += pre * 0.5 * (h.gz * imP - gpz * imPp);
+            acc[0] += 0.5 * (h.gx * imP - gpx * imPp);
+            acc[1] += 0.5 * (h.gy * imP - gpy * imPp);
+            acc[2] += 0.5 * (h.gz * imP - gpz * imPp);
         }
     }
     block_sum<3>(acc);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) part[((size_t)I * nchunk + chunk) * 3 + k] = acc[k];
+        for (int k = 0; k < 3; ++k) part[((size_t)I * nchunk + chunk) * 3 + k] = Z[I] * acc[k];
 }
 
 __global__ void k_force_reduce(int nat, int nchunk, const double *__restrict__ part, double *F,
@@ -538,25 +593,27 @@ void launch_phases(const GridInfo &g, int nat, const double *R, double2 *px, dou
     k_phases<<<b, 256, 0, st>>>(g, nat, R, px, py, pz);
 }
 
-template <typename T>
 void launch_vext(const GridInfo &g, int nat, const double *Z, const double2 *px,
-                 const double2 *py, const double2 *pz, cplx<T> *vext, cudaStream_t st)
+                 const double2 *py, const double2 *pz, double2 *vext, cudaStream_t st)
 {
-    long long b = (g.NH + 255) / 256;
-    k_vext<T><<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(g, nat, Z, px, py, pz, vext);
+    int th = 32 * ((g.K + 31) / 32);
+    if (th > 128) th = 32 * ((((g.K + 1) / 2) + 31) / 32);    // two columns per thread
+    k_vext<<<g.nx * g.ny, th, 0, st>>>(g, nat, Z, px, py, pz, vext);
 }
 
 template <typename T>
 int launch_lpp_forces(const GridInfo &g, int nat, const double *Z, const double2 *px,
-                      const double2 *py, const double2 *pz, const cplx<T> *nG, double *part,
-                      cudaStream_t st)
+                      const double2 *py, const double2 *pz, const cplx<T> *nG, double2 *cn,
+                      double *part, cudaStream_t st)
 {
-    int nchunk = 608 / (nat > 0 ? nat : 1);
+    long long b = (g.NH + 255) / 256;
+    k_lpp_prep<T><<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(g, nG, cn);
+    int nchunk = 1216 / (nat > 0 ? nat : 1);
     if (nchunk < 1) nchunk = 1;
     long long maxc = (g.NH + 1023) / 1024;
     if (nchunk > maxc) nchunk = (int)maxc;
     dim3 grid(nat, nchunk);
-    k_lpp_forces<T><<<grid, 256, 0, st>>>(g, nat, Z, px, py, pz, nG, part);
+    k_lpp_forces<<<grid, 256, 0, st>>>(g, nat, Z, px, py, pz, cn, part);
     return nchunk;
 }
 
@@ -607,11 +664,9 @@ void launch_md_b(int nat, const double *m, double *V, const double *F, double dt
                                   double *, cudaStream_t);                                        \
     template int launch_cg_dhat<T>(long long, const T *, T *, const T *, const T *, double,       \
                                    double, int, const double *, T *, double *, cudaStream_t);     \
-    template void launch_vext<T>(const GridInfo &, int, const double *, const double2 *,          \
-                                 const double2 *, const double2 *, cplx<T> *, cudaStream_t);      \
     template int launch_lpp_forces<T>(const GridInfo &, int, const double *, const double2 *,     \
                                       const double2 *, const double2 *, const cplx<T> *,          \
-                                      double *, cudaStream_t);
+                                      double2 *, double *, cudaStream_t);
 
 OFDFT_MISC_INST(double)
 OFDFT_MISC_INST(float)

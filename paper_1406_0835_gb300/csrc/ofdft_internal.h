@@ -59,7 +59,16 @@ struct GridInfo {
     long long N, NH;
     double Lx, Ly, Lz, omega, dV;
     double rc;               // Gaussian local pseudopotential radius
+    double bx, by, bz;       // reciprocal spacing 2 pi / L per axis
 };
+
+inline void grid_reciprocal(GridInfo &g)
+{
+    const double tp = 6.283185307179586477;
+    g.bx = tp / g.Lx;
+    g.by = tp / g.Ly;
+    g.bz = tp / g.Lz;
+}
 
 // Tabulated temperature functions xi, zeta, A, B of t (see tfunc_table.cpp).
 constexpr int kTfDeg = 10;                 // polynomial degree per panel
