@@ -41,6 +41,13 @@ WORKLOADS = {
     # one single-point minimisation per step (256 H, 4 g/cm^3, 128^3, 250 kK)
     "solve-vt84f-128": dict(kind="solve", functional="vt84f", grid=128, precision="fp64", T=2.5e5),
     "solve-vt84f-128-mixed": dict(kind="solve", functional="vt84f", grid=128, precision="mixed", T=2.5e5),
+    # batched form: 64 uneven single-point solves (8-512 H, 0.1-10 g/cm^3,
+    # 2 kK-4 MK, 32^3-160^3, ftTF/SGA/VT84F) per step, all in flight at once
+    "batch-64-mixed": dict(kind="batch", precision="mixed", count=64),
+    "batch-64-fp64": dict(kind="batch", precision="fp64", count=64),
+    # serving form: Poisson arrivals (50/s) of EOS requests, each an initial
+    # minimisation and 5 VT84F MD steps (16-128 H, 0.1-20 g/cm^3, <= 96^3)
+    "serve-eos-mixed": dict(kind="serve", precision="mixed", count=24, md_steps=5),
 }
 
 
@@ -77,6 +84,8 @@ def parse():
     ap.add_argument("--workload", default="md-vt84f-96", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ref", action="store_true",
+                    help="batch/serve workloads: skip the sequential FP64 reference run")
     ap.add_argument("--maxit", type=int, default=20000,
                     help="CG iteration cap per solve (solve workloads; a small cap makes a short "
                          "profiling case, whose solves then stop unconverged)")
@@ -436,6 +445,163 @@ def run_solve(args, rank, world):
     return res, evals / args.steps
 
 
+def run_batch(args, rank, world):
+    """Batched form: one step = the 64 single-point solves of the uneven batch
+    (each from the uniform start to ||g|| < 1e-8), started together on 64
+    streams (one graph launch each) and waited for together.  The same
+    instances solved one after another with FP64 contexts are timed once as
+    the plain-FP64 reference."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1406_0835_gb300 import inputs, ofdft
+
+    wl = WORKLOADS[args.workload]
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    systems = inputs.config_batch(count=wl["count"])
+    ctxs = [ofdft.Context(d["L"], d["grid"], d["ions"], d["Z"], d["T"], d["functional"],
+                          precision=wl["precision"], device=dev) for d in systems]
+    t0 = time.perf_counter()
+    for c in ctxs:
+        c.autotune(reps=2)
+    t_tune = time.perf_counter() - t0
+
+    def batch_step():
+        for c in ctxs:
+            c.set_phi(None)
+        E, S, st = ofdft.ofdft_batch_minimize([c.ctx for c in ctxs], gtol=1e-8, maxit=20000)
+        return E, S, st
+
+    for _ in range(args.warmup):
+        batch_step()
+    torch.cuda.synchronize()
+    launches0 = sum(c.kernel_launches() for c in ctxs)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    times = []
+    evals = evals_lo = 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E, S, st = batch_step()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        evals += sum(x["evaluations"] for x in S)
+        evals_lo += sum(x["evaluations_lo"] for x in S)
+    clk = clocks.stop()
+    launches = sum(c.kernel_launches() for c in ctxs) - launches0
+    nconv = sum(1 for x in S if x["status"] == 0)
+    for c in ctxs:
+        c.close()
+    t_total = sum(times)
+    value = wl["count"] * args.steps / t_total
+    ref = None
+    if not args.no_ref:
+        # plain FP64 path, one instance after another
+        t_ref = 0.0
+        dF = []
+        for d, e in zip(systems, E):
+            with ofdft.Context(d["L"], d["grid"], d["ions"], d["Z"], d["T"], d["functional"],
+                               precision="fp64", device=dev) as c:
+                c.minimize(gtol=1e-8, maxit=1, raise_on_noconv=False)          # graph build
+                c.set_phi(None)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                Er, Sr = c.minimize(gtol=1e-8, maxit=20000, raise_on_noconv=False)
+                torch.cuda.synchronize()
+                t_ref += time.perf_counter() - t0
+                dF.append(abs(Er["F_tot"] - e["F_tot"]) / len(d["Z"]))
+        ref = {"fp64_sequential_solves_per_s": wl["count"] / t_ref, "speedup": value * t_ref / wl["count"],
+               "max_abs_dF_per_atom_Ha": max(dF)}
+    grids = sorted({d["grid"][0] for d in systems})
+    res = {"metric": "batched solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if wl["precision"] == "fp64" else "f32+f64",
+           "data": "synthetic (seeded hydrogen instances)",
+           "config": {"workload": args.workload, "instances": wl["count"], "grid_edges": grids,
+                      "atoms": [min(len(d["Z"]) for d in systems), max(len(d["Z"]) for d in systems)],
+                      "functionals": sorted({d["functional"] for d in systems}), "gtol": 1e-8,
+                      "l2": "inputs (all instances) larger than L2"},
+           "converged": nconv, "evals_per_step": evals / args.steps,
+           "fp32_evals_per_step": evals_lo / args.steps, "autotune_s": t_tune,
+           "gpu_launches": launches, "clocks": clk, "reference_fp64": ref}
+    return res, evals / args.steps
+
+
+def run_serve(args, rank, world):
+    """Serving form: EOS requests arrive as a Poisson stream (50/s); each is an
+    initial minimisation plus md_steps VT84F MD steps on its own context; the
+    server admits them by HBM footprint into up to 8 slots.  Reports p50/p99
+    latency (submit to result) and throughput, and the same requests run one
+    at a time on FP64 contexts."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1406_0835_gb300 import inputs, ofdft
+
+    wl = WORKLOADS[args.workload]
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = inputs.config_serve(count=wl["count"])
+
+    def serve(precision, slots, paced):
+        with ofdft.Server(max_slots=slots, device=dev) as s:
+            ids = []
+            start = s.clock()
+            for t_arr, d in stream:
+                if paced:
+                    while s.clock() - start < t_arr:
+                        time.sleep(0.0005)
+                ids.append(s.submit(d["L"], d["grid"], d["ions"], d["Z"], d["T"], "vt84f", precision,
+                                    md_steps=wl["md_steps"], dt_fs=0.2, vel=d["vel"], maxit=20000))
+            s.drain()
+            res = [s.poll(i) for i in ids]
+            peak = s.peaks()
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+        span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        return res, lat, span, peak
+
+    # warm-up: one small request per precision (library load, first graphs)
+    with ofdft.Server(max_slots=1, device=dev) as s:
+        d = stream[0][1]
+        for p in (wl["precision"], "fp64"):
+            s.submit(d["L"], d["grid"], d["ions"], d["Z"], d["T"], "vt84f", p, md_steps=1, vel=d["vel"])
+        s.drain()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    res, lat, span, peak = serve(wl["precision"], 8, True)
+    clk = clocks.stop()
+    ok = sum(1 for r in res if r["status"] == 0)
+    ref = None
+    if not args.no_ref:
+        rres, rlat, rspan, _ = serve("fp64", 1, False)
+        dF = max(abs(a["E"]["F_tot"] - b["E"]["F_tot"]) / len(d["Z"])
+                 for a, b, (_, d) in zip(res, rres, stream))
+        ref = {"fp64_sequential_requests_per_s": len(stream) / rspan,
+               "fp64_sequential_p50_s": float(np.percentile(rlat, 50)),
+               "fp64_sequential_p99_s": float(np.percentile(rlat, 99)),
+               "speedup": (len(stream) / span) / (len(stream) / rspan),
+               "max_abs_dF_per_atom_Ha": dF}
+    value = len(stream) / span
+    out = {"metric": "served requests/s", "value": value, "unit": "requests/s", "n_gpus": world,
+           "steps": len(stream), "warmup": 1, "ms_per_step": 1e3 * span / len(stream),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if wl["precision"] == "mixed" else "f64",
+           "data": "synthetic (seeded Poisson EOS request stream)",
+           "config": {"workload": args.workload, "requests": len(stream), "rate_per_s": 50.0,
+                      "md_steps": wl["md_steps"], "slots": 8, "grid_max": 96,
+                      "atoms": [16, 128], "rho_gcc": [0.1, 20.0], "T_K": [2e3, 4e6]},
+           "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+           "completed": ok, "peak_admitted_bytes": peak[0], "peak_running": peak[1],
+           "evaluations": int(sum(r["evaluations"] for r in res)),
+           "clocks": clk, "reference_fp64": ref}
+    return out, 1.0
+
+
 def cpu_baseline(args, evals_per_step, budget_s=15.0):
     """The oracle timed on a bounded sample: full-size energy + potential
     evaluations for about budget_s seconds, converted to the workload's
@@ -478,6 +644,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
+    if wl["kind"] in ("batch", "serve"):
+        return {"impl": "reference", "unavailable": "the oracle is timed on the md, solve and eval "
+                "workloads; the batched and serving forms are GPU-only and carry their own "
+                "sequential FP64 reference"}
     for _ in range(args.warmup):
         cpu_baseline(args, EVALS_PER_STEP[args.workload], budget_s=2.0)
     vals = []
@@ -519,6 +689,9 @@ def main():
         res, eps = run_eval(args, rank, world)
     elif kind == "solve":
         res, eps = run_solve(args, rank, world)
+    elif kind in ("batch", "serve"):
+        args.no_cpu = True
+        res, eps = (run_batch if kind == "batch" else run_serve)(args, rank, world)
     else:
         res, eps = run_ours(args, rank, world)
     if rank == 0:

@@ -41,7 +41,7 @@ typedef enum {
     OFDFT_ENUMERIC = -4,  /* NaN/Inf or non-positive density met */
     OFDFT_ETIMEOUT = -5,  /* reserved: a bounded device wait ran out */
     OFDFT_EDEVICE = -6,   /* CUDA error (message in ofdft_last_error) */
-    OFDFT_EBUSY = -7      /* reserved */
+    OFDFT_EBUSY = -7      /* work still in flight (ofdft_minimize_query, ofdft_serve_poll) */
 } ofdft_status;
 
 /* Non-interacting free-energy functional (Table I keywords, Sec. III). */
@@ -154,6 +154,45 @@ ofdft_status ofdft_minimize(ofdft_ctx *ctx, double gtol, int maxit,
                             ofdft_energy *E, ofdft_stats *stats);
 
 /*
+ * ofdft_minimize in two halves, so that many contexts (each on its own
+ * stream) minimise concurrently: _start enqueues the whole minimisation on
+ * the context's stream and returns at once; _query returns OFDFT_OK once it
+ * has finished and OFDFT_EBUSY before; _wait blocks until it has finished and
+ * reports as ofdft_minimize does.  Every other call on the context returns
+ * OFDFT_EBUSY between _start and _wait.  With OFDFT_DEBUG_SYNC=1 or an active
+ * kernel timer _start runs the minimisation to completion itself.
+ */
+ofdft_status ofdft_minimize_start(ofdft_ctx *ctx, double gtol, int maxit);
+ofdft_status ofdft_minimize_query(ofdft_ctx *ctx);
+ofdft_status ofdft_minimize_wait(ofdft_ctx *ctx, ofdft_energy *E, ofdft_stats *stats);
+
+/*
+ * Batched single-point solves: minimise n independent contexts at once (the
+ * uneven-size batch of the library's batched form).  Each context's
+ * minimisation is one graph launch on its own stream, so the solves overlap
+ * on the device; E[n] and stats[n] (either may be NULL) receive the results.
+ * Returns OFDFT_OK when every solve converged, else the first failing
+ * status (all results are still filled).
+ */
+ofdft_status ofdft_batch_minimize(int n, ofdft_ctx *const *ctxs, double gtol, int maxit,
+                                  ofdft_energy *E, ofdft_stats *stats);
+
+/*
+ * Device memory a context with this grid, ion count and precision holds
+ * (bytes, an upper estimate), for admission control before ofdft_setup.
+ */
+ofdft_status ofdft_footprint(const int grid[3], int nat, int precision, double *bytes);
+
+/*
+ * Autotune the launch shapes of this context's field kernels (pairs of z
+ * lines per block of the z passes, column-tile width of the y and x passes):
+ * every candidate is timed on this context's grid and the fastest kept.
+ * Results are cached per (grid, precision) for the process, so contexts of
+ * the same shape reuse them.  reps >= 1 timed evaluations per candidate.
+ */
+ofdft_status ofdft_autotune(ofdft_ctx *ctx, int reps);
+
+/*
  * Hellmann-Feynman plus Ewald forces at the current density, Eq. (M12):
  * F[nat][3] in hartree/bohr (may be NULL), and the pressure P
  * (hartree/bohr^3, may be NULL).
@@ -256,6 +295,73 @@ ofdft_status ofdft_energy_potential_static(const double cell[9], const int grid[
                                            int functional, int xc, double rc,
                                            const double *phi_dev, double *v_dev,
                                            ofdft_energy *E, void *stream);
+
+/*
+ * Serving: a request loop for equation-of-state points.  Each request is
+ * one system (cell, ions, grid, temperature, functional, precision) and a
+ * number of MD steps; requests queue in arrival order and are admitted while
+ * a slot is free and the request's device footprint (ofdft_footprint) fits
+ * in the memory budget.  An admitted request gets its own context and
+ * stream, so requests arriving while others run overlap with them on the
+ * device (continuous batching), and each keeps its density, CG state and FFT
+ * tables resident until it finishes.  Contexts are independent, so a
+ * request's results do not depend on what else runs.
+ */
+typedef struct ofdft_server ofdft_server;
+
+typedef struct {
+    int device;               /* CUDA device ordinal */
+    int max_slots;            /* requests running at once (worker threads), >= 1 */
+    double hbm_budget_bytes;  /* admission budget; <= 0: 90% of the device memory free at start */
+    int dry_run;              /* 1: no device work, each request sleeps dry_run_ms (host tests) */
+    double dry_run_ms;
+} ofdft_serve_params;
+
+typedef struct {
+    double cell[9];           /* as ofdft_setup */
+    int grid[3];
+    int nat;
+    const double *ions;       /* [nat][3], copied at submit */
+    const double *Z;          /* [nat], copied at submit */
+    const double *vel;        /* [nat][3] initial velocities or NULL (zero), copied */
+    double T_kelvin;          /* electron temperature and thermostat temperature */
+    int functional;           /* ofdft_functional */
+    int precision;            /* ofdft_precision */
+    int xc;
+    double rc;
+    int md_steps;             /* MD steps after the initial minimisation (>= 0) */
+    double dt_fs;
+    double gtol;
+    int maxit;
+} ofdft_request;
+
+typedef struct {
+    long long id;
+    int status;               /* ofdft_status of the request */
+    ofdft_energy E;           /* after the last step */
+    double P_mean;            /* mean pressure over the MD steps (or the single point) */
+    int steps_done;
+    long long evaluations;    /* energy+potential evaluations, all steps */
+    double t_submit, t_admit, t_done;   /* seconds on the server clock */
+    double footprint_bytes;
+} ofdft_result;
+
+ofdft_status ofdft_serve_start(const ofdft_serve_params *p, ofdft_server **out);
+/* Queue a request; *id receives its id.  OFDFT_ENOMEM if its footprint
+ * exceeds the whole budget, OFDFT_EINVAL for bad sizes. */
+ofdft_status ofdft_serve_submit(ofdft_server *s, const ofdft_request *r, long long *id);
+/* OFDFT_OK and *res filled once request id has finished, OFDFT_EBUSY while
+ * it is queued or running, OFDFT_EINVAL for an unknown id. */
+ofdft_status ofdft_serve_poll(ofdft_server *s, long long id, ofdft_result *res);
+/* Block until every submitted request has finished (timeout_s <= 0: no limit;
+ * OFDFT_ETIMEOUT when it runs out). */
+ofdft_status ofdft_serve_drain(ofdft_server *s, double timeout_s);
+/* Seconds since ofdft_serve_start on the server clock (steady). */
+double ofdft_serve_clock(ofdft_server *s);
+/* Peak bytes of admitted footprints and peak concurrent requests so far. */
+ofdft_status ofdft_serve_peaks(ofdft_server *s, double *bytes, int *running);
+/* Finish queued and running requests, join the workers, free the server. */
+ofdft_status ofdft_serve_stop(ofdft_server *s);
 
 #ifdef __cplusplus
 }

@@ -250,8 +250,22 @@ def fs_gga(n, gradn, T, Fenh):
 
 
 # ------------------------------------------------------------- XC (Sec. IV)
-PZ = dict(gamma=-0.1423, beta1=1.0529, beta2=0.3334,
-          A=0.0311, B=-0.048, C=0.0020, D=-0.0116)
+def _pz81_constants():
+    """PZ81 correlation constants.  gamma, beta1, beta2, A, B as published;
+    C and D from the two conditions the parametrisation was built on: eps_c
+    and d eps_c/d r_s continuous at r_s = 1 (the published C = 0.0020,
+    D = -0.0116 are these values rounded, and the rounding leaves a 3e-5 Ha
+    jump in eps_c at r_s = 1 that stalls the minimiser near that density)."""
+    g, b1, b2, A, B = -0.1423, 1.0529, 0.3334, 0.0311, -0.048
+    den = 1.0 + b1 + b2
+    e1 = g / den                                   # Pade branch at r_s = 1
+    de1 = -g * (0.5 * b1 + b2) / den ** 2          # its r_s derivative
+    D = e1 - B                                     # A ln 1 + B + C 0 + D = e1
+    C = de1 - A - D                                # A + C (ln 1 + 1) + D = de1
+    return dict(gamma=g, beta1=b1, beta2=b2, A=A, B=B, C=C, D=D)
+
+
+PZ = _pz81_constants()
 EX_COEF = 0.75 * (3.0 / math.pi) ** (1.0 / 3.0)   # eps_x = -EX_COEF n^{1/3}
 
 
@@ -260,7 +274,8 @@ def pz81(n):
 
     eps_xc = eps_x + eps_c(r_s); v_xc = eps_xc + n d eps_xc/dn with
     dr_s/dn = -r_s/(3n) (Eq. (vxc1) at T = 0).  Reading: r_s >= 1 takes the
-    Pade branch.  Returns eps_xc, v_xc.
+    Pade branch; C and D make both branches meet with equal value and slope
+    (see _pz81_constants).  Returns eps_xc, v_xc.
     """
     rs = (3.0 / (4.0 * math.pi * n)) ** (1.0 / 3.0)
     ex = -EX_COEF * n ** (1.0 / 3.0)

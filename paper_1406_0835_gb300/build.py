@@ -14,7 +14,7 @@ LIB = os.path.join(OUT_DIR, "libofdft.so")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["kernels_fields.cu", "kernels_misc.cu", "cg_control.cu", "capi.cu", "capi_static.cu",
-           "tfunc_table.cpp"]
+           "tfunc_table.cpp", "serve.cpp"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
               "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]

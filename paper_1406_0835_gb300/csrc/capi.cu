@@ -14,6 +14,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -30,7 +33,7 @@ const double kKbHa = 3.166811563e-6;        // hartree / kelvin
 const double kFsAu = 41.341373335;          // atomic time units per fs
 const double kMassH = 1.00794 * 1822.888486209;
 
-std::string g_setup_error;
+thread_local std::string g_setup_error;   // setup errors (no context yet), per thread
 
 // Working fields of one precision.
 struct FieldSet {
@@ -44,6 +47,7 @@ struct FieldSet {
     FftAxis ax[3];
     CgState *cs = nullptr;     // device CG state
     cudaGraphExec_t graph = nullptr;
+    GridInfo gt{};             // the grid with this set's launch shapes (ofdft_autotune)
 };
 
 }  // namespace
@@ -67,7 +71,10 @@ struct ofdft_ctx {
     size_t part_len = 0;
     double *scal = nullptr;     // device scalars outside a minimisation
     double *scal_h = nullptr;   // pinned host copy
-    CgState *cs_h = nullptr;    // pinned host mirror of a CgState
+    CgState *cfg_h[2] = {nullptr, nullptr};   // pinned CG configuration per field set
+    CgState *st_h[2] = {nullptr, nullptr};    // pinned final CG state per field set
+    cudaEvent_t done_ev = nullptr;             // end of the minimisation in flight
+    bool pending = false, pend_graph = false;
     // ions
     double *Rd = nullptr, *Zd = nullptr, *Fd = nullptr, *Vd = nullptr, *Md = nullptr, *nh = nullptr;
     double2 *px = nullptr, *py = nullptr, *pz = nullptr;
@@ -168,8 +175,8 @@ template <typename T> ofdft_status upload_twiddles(ofdft_ctx *c, FieldSet &f, in
         w[m].x = (T)cosl(ang);
         w[m].y = (T)sinl(ang);
     }
-    CK(cudaMalloc(&f.tw[axis], n * sizeof(cplx<T>)));
-    CK(cudaMemcpy(f.tw[axis], w.data(), n * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+    CK(cudaMallocAsync((void **)&f.tw[axis], n * sizeof(cplx<T>), c->st));
+    CK(cudaMemcpyAsync(f.tw[axis], w.data(), n * sizeof(cplx<T>), cudaMemcpyHostToDevice, c->st));
     f.ax[axis] = make_axis(n, f.tw[axis]);
     return OFDFT_OK;
 }
@@ -244,7 +251,7 @@ template <typename T>
 ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const T *dh, double cth,
                           double sth, const double *csd, T *vout, bool keep_nG, double *sums)
 {
-    const GridInfo &g = c->g;
+    const GridInfo &g = f.gt;
     const FftAxis &ax = f.ax[0], &ay = f.ax[1], &az = f.ax[2];
     cudaStream_t st = c->st;
     typedef cplx<T> C;
@@ -254,7 +261,7 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
     const C *vext = (const C *)f.vext;
     const T *tab = (const T *)f.tab;
     const bool fttf = c->fp.kind == 0;
-    const int ntk = (g.K + 7) / 8, nbx = g.ny * ntk;
+    const int ntk = (g.K + g.tk - 1) / g.tk, nbx = g.ny * ntk;
     const long long npairs = (long long)g.nx * g.ny / 2;
     double *pA = c->part, *pB = pA + 3 * nbx, *pC = pB + 6 * npairs;
     {
@@ -391,15 +398,15 @@ ofdft_status setup_ewald(ofdft_ctx *c)
             }
     c->nGe = (int)wG.size();
     int nb = (c->nGe + 255) / 256;
-    CK(cudaMalloc(&c->Gv, std::max<size_t>(1, Gv.size()) * sizeof(double)));
-    CK(cudaMalloc(&c->wG, std::max<size_t>(1, wG.size()) * sizeof(double)));
-    CK(cudaMalloc(&c->Se, std::max(1, c->nGe) * sizeof(double2)));
-    CK(cudaMalloc(&c->ewpart, std::max(1, nb) * sizeof(double)));
-    CK(cudaMalloc(&c->eion, c->nat * sizeof(double)));
-    CK(cudaMalloc(&c->ewF, 3 * c->nat * sizeof(double)));
+    CK(cudaMallocAsync((void **)&c->Gv, std::max<size_t>(1, Gv.size()) * sizeof(double), c->st));
+    CK(cudaMallocAsync((void **)&c->wG, std::max<size_t>(1, wG.size()) * sizeof(double), c->st));
+    CK(cudaMallocAsync((void **)&c->Se, std::max(1, c->nGe) * sizeof(double2), c->st));
+    CK(cudaMallocAsync((void **)&c->ewpart, std::max(1, nb) * sizeof(double), c->st));
+    CK(cudaMallocAsync((void **)&c->eion, c->nat * sizeof(double), c->st));
+    CK(cudaMallocAsync((void **)&c->ewF, 3 * c->nat * sizeof(double), c->st));
     if (!Gv.empty()) {
-        CK(cudaMemcpy(c->Gv, Gv.data(), Gv.size() * sizeof(double), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(c->wG, wG.data(), wG.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(c->Gv, Gv.data(), Gv.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(c->wG, wG.data(), wG.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
     }
     return OFDFT_OK;
 }
@@ -595,9 +602,11 @@ template <typename T> ofdft_status build_graph(ofdft_ctx *c, FieldSet &f)
     return r;
 }
 
-ofdft_status write_config(ofdft_ctx *c, FieldSet &f, double gtol, int maxit, int stagnate)
+// Field set k's CG configuration is staged in pinned memory (one buffer per
+// set, so the two copies of a mixed-precision minimisation never race).
+ofdft_status write_config(ofdft_ctx *c, int k, double gtol, int maxit, int stagnate)
 {
-    CgState *h = c->cs_h;
+    CgState *h = c->cfg_h[k];
     memset(h, 0, sizeof(CgState));
     h->gtol = gtol;
     h->dV = c->g.dV;
@@ -608,88 +617,127 @@ ofdft_status write_config(ofdft_ctx *c, FieldSet &f, double gtol, int maxit, int
     h->max_ls = 20;
     h->stagnate = stagnate;
     h->status = OFDFT_OK;
-    CK(cudaMemcpyAsync(f.cs, h, sizeof(CgState), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->f[k].cs, h, sizeof(CgState), cudaMemcpyHostToDevice, c->st));
     return OFDFT_OK;
 }
 
-ofdft_status read_state(ofdft_ctx *c, FieldSet &f)
+ofdft_status read_state(ofdft_ctx *c, int k)
 {
-    CK(cudaMemcpyAsync(c->cs_h, f.cs, sizeof(CgState), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(c->st_h[k], c->f[k].cs, sizeof(CgState), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     CK(cudaGetLastError());
     return OFDFT_OK;
 }
 
-// Minimise on field set f (phi already holds the start).  Adds to the stats
-// and returns the accepted point's evaluation sums.
+bool graphs_on(const ofdft_ctx *c) { return c->use_graphs && !c->debug_sync && c->timer_id == 0; }
+
+// Enqueue the minimisation of field set k as one graph launch (phi already
+// holds the start) and the copy of its final CG state to st_h[k].
 template <typename T>
-ofdft_status minimize_T(ofdft_ctx *c, FieldSet &f, double gtol, int maxit, int stagnate,
-                        ofdft_stats &stats, EvalScalars &es)
+ofdft_status enqueue_minimize_graph(ofdft_ctx *c, int k, double gtol, int maxit, int stagnate)
 {
-    if (write_config(c, f, gtol, maxit, stagnate) != OFDFT_OK) return OFDFT_EDEVICE;
-    const bool graphs = c->use_graphs && !c->debug_sync && c->timer_id == 0;
-    if (graphs) {
-        if (!f.graph) {
-            ofdft_status r = build_graph<T>(c, f);
-            if (r != OFDFT_OK) return r;
-        }
-        CK(cudaGraphLaunch(f.graph, c->st));
-        if (read_state(c, f) != OFDFT_OK) return OFDFT_EDEVICE;
-        // kernels the graph ran: prologue, per outer iteration (direction +
-        // update), per line-search trial (evaluation + controller)
-        const CgState &h = *c->cs_h;
-        c->launches += 8 + eval_kernel_count(c) + (long long)h.nouter * 10 +
-                       (long long)(h.nevals - 1) * (eval_kernel_count(c) + 1);
-    } else {
-        cudaGraphConditionalHandle none = 0;
-        ofdft_status r = enqueue_prologue<T>(c, f, none, 0);
+    FieldSet &f = c->f[k];
+    if (write_config(c, k, gtol, maxit, stagnate) != OFDFT_OK) return OFDFT_EDEVICE;
+    if (!f.graph) {
+        ofdft_status r = build_graph<T>(c, f);
         if (r != OFDFT_OK) return r;
-        if (read_state(c, f) != OFDFT_OK) return OFDFT_EDEVICE;
-        while (!c->cs_h->done) {
-            if ((r = enqueue_direction<T>(c, f, none, 0)) != OFDFT_OK) return r;
-            do {
-                if ((r = enqueue_trial<T>(c, f, none, 0)) != OFDFT_OK) return r;
-                if (read_state(c, f) != OFDFT_OK) return OFDFT_EDEVICE;
-            } while (c->cs_h->ls_active);
-            if ((r = enqueue_update<T>(c, f, none, 0)) != OFDFT_OK) return r;
-            if (read_state(c, f) != OFDFT_OK) return OFDFT_EDEVICE;
-        }
     }
-    const CgState &h = *c->cs_h;
-    stats.iterations += h.it;
-    stats.evaluations += h.nevals;
+    CK(cudaGraphLaunch(f.graph, c->st));
+    CK(cudaMemcpyAsync(c->st_h[k], f.cs, sizeof(CgState), cudaMemcpyDeviceToHost, c->st));
+    return OFDFT_OK;
+}
+
+// The same kernel sequence driven from the host (debugging, kernel timers).
+template <typename T>
+ofdft_status minimize_host(ofdft_ctx *c, int k, double gtol, int maxit, int stagnate)
+{
+    FieldSet &f = c->f[k];
+    if (write_config(c, k, gtol, maxit, stagnate) != OFDFT_OK) return OFDFT_EDEVICE;
+    cudaGraphConditionalHandle none = 0;
+    ofdft_status r = enqueue_prologue<T>(c, f, none, 0);
+    if (r != OFDFT_OK) return r;
+    if (read_state(c, k) != OFDFT_OK) return OFDFT_EDEVICE;
+    while (!c->st_h[k]->done) {
+        if ((r = enqueue_direction<T>(c, f, none, 0)) != OFDFT_OK) return r;
+        do {
+            if ((r = enqueue_trial<T>(c, f, none, 0)) != OFDFT_OK) return r;
+            if (read_state(c, k) != OFDFT_OK) return OFDFT_EDEVICE;
+        } while (c->st_h[k]->ls_active);
+        if ((r = enqueue_update<T>(c, f, none, 0)) != OFDFT_OK) return r;
+        if (read_state(c, k) != OFDFT_OK) return OFDFT_EDEVICE;
+    }
+    return OFDFT_OK;
+}
+
+// Start a minimisation.  With graphs the whole solve (both precisions of a
+// mixed context: FP32 CG until converged or stalled at the single-precision
+// floor, then FP64 CG from there to gtol) is enqueued on the context's
+// stream and this returns at once; otherwise it runs to completion here.
+ofdft_status minimize_start(ofdft_ctx *c, double gtol, int maxit)
+{
+    if (c->pending) return fail(c, OFDFT_EBUSY, "a minimisation is already in flight");
+    const bool mixed = c->precision == OFDFT_MIXED;
+    const bool graphs = graphs_on(c);
+    ofdft_status s = OFDFT_OK;
+    c->pend_graph = graphs;
+    if (mixed) {
+        launch_convert<double, float>(c->g.N, (const double *)c->f[0].phi, (float *)c->f[1].phi, c->st);
+        c->launches++;
+        s = graphs ? enqueue_minimize_graph<float>(c, 1, gtol, maxit, 1) : minimize_host<float>(c, 1, gtol, maxit, 1);
+        if (s != OFDFT_OK) return s;
+        launch_convert<float, double>(c->g.N, (const float *)c->f[1].phi, (double *)c->f[0].phi, c->st);
+        c->launches++;
+    }
+    s = graphs ? enqueue_minimize_graph<double>(c, 0, gtol, maxit, 0) : minimize_host<double>(c, 0, gtol, maxit, 0);
+    if (s != OFDFT_OK) return s;
+    CK(cudaEventRecord(c->done_ev, c->st));
+    c->pending = true;
+    return OFDFT_OK;
+}
+
+// Launches of one graph-driven minimisation: prologue, per outer iteration
+// (direction + update), per line-search trial (evaluation + controller).
+long long graph_launches(const ofdft_ctx *c, const CgState &h)
+{
+    return 8 + eval_kernel_count(c) + (long long)h.nouter * 10 +
+           (long long)(h.nevals - 1) * (eval_kernel_count(c) + 1);
+}
+
+// Wait for the minimisation started last; fill stats and the energies.
+ofdft_status minimize_wait(ofdft_ctx *c, ofdft_stats &stats, EvalScalars &es)
+{
+    stats = ofdft_stats{};
+    if (!c->pending) return fail(c, OFDFT_EINVAL, "no minimisation in flight");
+    c->pending = false;
+    CK(cudaEventSynchronize(c->done_ev));
+    CK(cudaGetLastError());
+    const bool mixed = c->precision == OFDFT_MIXED;
+    const CgState &h = *c->st_h[0];
+    stats.iterations = h.it;
+    stats.evaluations = h.nevals;
     stats.gnorm = h.gnorm;
     stats.status = h.status == kCgStagnated ? OFDFT_OK : h.status;
+    if (c->pend_graph) c->launches += graph_launches(c, h);
+    if (mixed) {
+        const CgState &l = *c->st_h[1];
+        stats.iterations += l.it;
+        stats.evaluations_lo = l.nevals;
+        stats.evaluations += l.nevals;
+        if (c->pend_graph) c->launches += graph_launches(c, l);
+    }
     es = unpack_sums(h.ev_acc, c->fp.kind == 0);
     if (h.status == OFDFT_ENUMERIC) return fail(c, OFDFT_ENUMERIC, "non-finite energy, gradient or norm");
-    return OFDFT_OK;
+    fill_energy(c, es, c->last);
+    c->last_valid = true;
+    return stats.status == OFDFT_OK ? OFDFT_OK : (ofdft_status)stats.status;
 }
 
 ofdft_status run_minimize(ofdft_ctx *c, double gtol, int maxit, ofdft_stats &stats, EvalScalars &es)
 {
     stats = ofdft_stats{};
-    ofdft_status s;
-    if (c->precision == OFDFT_MIXED) {
-        // FP32 CG until converged or stalled at the single-precision floor,
-        // then FP64 CG from there to the requested tolerance
-        launch_convert<double, float>(c->g.N, (const double *)c->f[0].phi, (float *)c->f[1].phi, c->st);
-        c->launches++;
-        ofdft_stats s32{};
-        s = minimize_T<float>(c, c->f[1], gtol, maxit, 1, s32, es);
-        if (s != OFDFT_OK) return s;
-        launch_convert<float, double>(c->g.N, (const float *)c->f[1].phi, (double *)c->f[0].phi, c->st);
-        c->launches++;
-        s = minimize_T<double>(c, c->f[0], gtol, maxit, 0, stats, es);
-        stats.iterations += s32.iterations;
-        stats.evaluations_lo = s32.evaluations;
-        stats.evaluations += s32.evaluations;
-    } else {
-        s = minimize_T<double>(c, c->f[0], gtol, maxit, 0, stats, es);
-    }
+    ofdft_status s = minimize_start(c, gtol, maxit);
     if (s != OFDFT_OK) return s;
-    fill_energy(c, es, c->last);
-    c->last_valid = true;
-    return stats.status == OFDFT_OK ? OFDFT_OK : (ofdft_status)stats.status;
+    return minimize_wait(c, stats, es);
 }
 
 ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
@@ -701,9 +749,9 @@ ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
     const double2 *nG = (const double2 *)f.spec + (c->fp.kind == 0 ? f.spec_stride : 0);
     size_t need = (size_t)c->nat * 1216 * 3 + 16;
     if (need > c->fpart_len) {
-        if (c->fpart) cudaFree(c->fpart);
+        if (c->fpart) cudaFreeAsync(c->fpart, c->st);
         c->fpart = nullptr;
-        CK(cudaMalloc(&c->fpart, need * sizeof(double)));
+        CK(cudaMallocAsync((void **)&c->fpart, need * sizeof(double), c->st));
         c->fpart_len = need;
     }
     // the third spectrum is free after an evaluation (ftTF and GGA alike)
@@ -721,29 +769,37 @@ ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
     return OFDFT_OK;
 }
 
-void free_fieldset(FieldSet &f)
+void free_fieldset(FieldSet &f, cudaStream_t st)
 {
     void *ptrs[] = {f.phi, f.phit, f.dhat, f.g, f.gprev, f.d, f.v, f.vt, f.vpart, f.spec, f.vext, f.tab,
                     f.tw[0], f.tw[1], f.tw[2], f.cs};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, st);
     if (f.graph) cudaGraphExecDestroy(f.graph);
     f = FieldSet{};
 }
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// context's stream), so creating and destroying contexts never waits for
+// the work of other contexts on the device.
 void free_ctx(ofdft_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->dev);
     if (c->st) cudaStreamSynchronize(c->st);
-    free_fieldset(c->f[0]);
-    free_fieldset(c->f[1]);
+    free_fieldset(c->f[0], c->st);
+    free_fieldset(c->f[1], c->st);
     void *ptrs[] = {c->phiprev, c->part, c->scal, c->Rd, c->Zd, c->Fd, c->Vd, c->Md, c->nh, c->px, c->py,
                     c->pz, c->fpart, c->Gv, c->wG, c->eion, c->ewF, c->ewpart, c->Se};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, c->st);
+    if (c->st) cudaStreamSynchronize(c->st);
     if (c->scal_h) cudaFreeHost(c->scal_h);
-    if (c->cs_h) cudaFreeHost(c->cs_h);
+    for (int k = 0; k < 2; ++k) {
+        if (c->cfg_h[k]) cudaFreeHost(c->cfg_h[k]);
+        if (c->st_h[k]) cudaFreeHost(c->st_h[k]);
+    }
+    if (c->done_ev) cudaEventDestroy(c->done_ev);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     if (c->cap2) cudaStreamDestroy(c->cap2);
@@ -756,19 +812,20 @@ template <typename T> ofdft_status alloc_fieldset(ofdft_ctx *c, FieldSet &f)
     size_t rb = (size_t)g.N * sizeof(T);
     size_t cb = ((size_t)g.NH * sizeof(cplx<T>) + 255) & ~(size_t)255;
     void **fields[] = {&f.phi, &f.phit, &f.dhat, &f.g, &f.gprev, &f.d, &f.v, &f.vt, &f.vpart};
-    for (void **p : fields) CK(cudaMalloc(p, rb));
-    CK(cudaMalloc(&f.spec, 4 * cb));
+    for (void **p : fields) CK(cudaMallocAsync(p, rb, c->st));
+    CK(cudaMallocAsync((void **)&f.spec, 4 * cb, c->st));
     f.spec_stride = cb / sizeof(cplx<T>);
-    CK(cudaMalloc(&f.vext, (size_t)g.NH * sizeof(cplx<T>)));
+    CK(cudaMallocAsync((void **)&f.vext, (size_t)g.NH * sizeof(cplx<T>), c->st));
     const std::vector<double> &tab = tfunc_table_host();
     std::vector<T> tt(tab.begin(), tab.end());
-    CK(cudaMalloc(&f.tab, tt.size() * sizeof(T)));
-    CK(cudaMemcpy(f.tab, tt.data(), tt.size() * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaMallocAsync((void **)&f.tab, tt.size() * sizeof(T), c->st));
+    CK(cudaMemcpyAsync(f.tab, tt.data(), tt.size() * sizeof(T), cudaMemcpyHostToDevice, c->st));
     int n3[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a)
         if (upload_twiddles<T>(c, f, a, n3[a]) != OFDFT_OK) return OFDFT_EDEVICE;
-    CK(cudaMalloc(&f.cs, sizeof(CgState)));
-    CK(cudaMemset(f.cs, 0, sizeof(CgState)));
+    CK(cudaMallocAsync((void **)&f.cs, sizeof(CgState), c->st));
+    f.gt = c->g;
+    CK(cudaMemsetAsync(f.cs, 0, sizeof(CgState), c->st));
     f.valid = true;
     return OFDFT_OK;
 }
@@ -778,25 +835,30 @@ ofdft_status alloc_ctx(ofdft_ctx *c)
     const GridInfo &g = c->g;
     if (alloc_fieldset<double>(c, c->f[0]) != OFDFT_OK) return OFDFT_ENOMEM;
     if (c->precision == OFDFT_MIXED && alloc_fieldset<float>(c, c->f[1]) != OFDFT_OK) return OFDFT_ENOMEM;
-    CK(cudaMalloc(&c->phiprev, (size_t)g.N * sizeof(double)));
-    const int ntk = (g.K + 7) / 8;
+    CK(cudaMallocAsync((void **)&c->phiprev, (size_t)g.N * sizeof(double), c->st));
+    const int ntk = (g.K + 3) / 4;              // narrowest column tile the autotuner tries
     size_t need = (size_t)3 * g.ny * ntk + (size_t)15 * ((size_t)g.nx * g.ny / 2) + 64;
     need = std::max<size_t>(need, 5 * 1216 + 64);
-    CK(cudaMalloc(&c->part, need * sizeof(double)));
+    CK(cudaMallocAsync((void **)&c->part, need * sizeof(double), c->st));
     c->part_len = need;
-    CK(cudaMalloc(&c->scal, 64 * sizeof(double)));
+    CK(cudaMallocAsync((void **)&c->scal, 64 * sizeof(double), c->st));
     CK(cudaMallocHost(&c->scal_h, 64 * sizeof(double)));
-    CK(cudaMallocHost(&c->cs_h, sizeof(CgState)));
+    for (int k = 0; k < 2; ++k) {
+        CK(cudaMallocHost(&c->cfg_h[k], sizeof(CgState)));
+        CK(cudaMallocHost(&c->st_h[k], sizeof(CgState)));
+        memset(c->st_h[k], 0, sizeof(CgState));
+    }
+    CK(cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming));
     const int nat = c->nat;
-    CK(cudaMalloc(&c->Rd, 3 * nat * sizeof(double)));
-    CK(cudaMalloc(&c->Zd, nat * sizeof(double)));
-    CK(cudaMalloc(&c->Fd, 3 * nat * sizeof(double)));
-    CK(cudaMalloc(&c->Vd, 3 * nat * sizeof(double)));
-    CK(cudaMalloc(&c->Md, nat * sizeof(double)));
-    CK(cudaMalloc(&c->nh, 4 * sizeof(double)));
-    CK(cudaMalloc(&c->px, (size_t)nat * g.nx * sizeof(double2)));
-    CK(cudaMalloc(&c->py, (size_t)nat * g.ny * sizeof(double2)));
-    CK(cudaMalloc(&c->pz, (size_t)nat * g.K * sizeof(double2)));
+    CK(cudaMallocAsync((void **)&c->Rd, 3 * nat * sizeof(double), c->st));
+    CK(cudaMallocAsync((void **)&c->Zd, nat * sizeof(double), c->st));
+    CK(cudaMallocAsync((void **)&c->Fd, 3 * nat * sizeof(double), c->st));
+    CK(cudaMallocAsync((void **)&c->Vd, 3 * nat * sizeof(double), c->st));
+    CK(cudaMallocAsync((void **)&c->Md, nat * sizeof(double), c->st));
+    CK(cudaMallocAsync((void **)&c->nh, 4 * sizeof(double), c->st));
+    CK(cudaMallocAsync((void **)&c->px, (size_t)nat * g.nx * sizeof(double2), c->st));
+    CK(cudaMallocAsync((void **)&c->py, (size_t)nat * g.ny * sizeof(double2), c->st));
+    CK(cudaMallocAsync((void **)&c->pz, (size_t)nat * g.K * sizeof(double2), c->st));
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
     // leave room for the kernels' static shared memory (block reductions)
@@ -820,6 +882,130 @@ ofdft_status normalize_phi64(ofdft_ctx *c)
     if (!(ss > 0.0) || !isfinite(ss)) return fail(c, OFDFT_ENUMERIC, "phi has zero or non-finite norm");
     launch_scale<double>(c->g.N, (double *)f.phi, sqrt(c->Ne / ss), nullptr, c->st);
     c->launches++;
+    return OFDFT_OK;
+}
+
+// Device bytes of one context (upper estimate mirroring alloc_ctx and
+// setup_ewald; the Ewald G count is bounded by its cube, which depends on
+// nat only for the splitting used there).
+double footprint_bytes(const int grid[3], int nat, int precision)
+{
+    const double nx = grid[0], ny = grid[1], nz = grid[2];
+    const double K = std::floor(nz / 2) + 1, N = nx * ny * nz, NH = nx * ny * K;
+    const double tab = (double)tfunc_table_host().size();
+    auto fieldset = [&](double sz) {
+        double cb = std::ceil(NH * 2 * sz / 256.0) * 256.0;
+        return 9 * N * sz + 4 * cb + NH * 2 * sz + tab * sz + (nx + ny + nz) * 2 * sz + sizeof(CgState);
+    };
+    double b = fieldset(8.0) + (precision == OFDFT_MIXED ? fieldset(4.0) : 0.0);
+    b += N * 8;                                                        // phiprev
+    b += (3 * ny * std::ceil(K / 4) + 15 * (nx * ny / 2) + 64) * 8 + 64 * 8;  // partials, scalars
+    b += nat * 11.0 * 8 + 32 + nat * (nx + ny + K) * 16.0;             // ions, phase factors
+    b += nat * 1216.0 * 3 * 8 + 16 * 8;                                // force partials
+    double km = std::ceil(4.27 * std::pow((double)nat, 1.0 / 6.0)) + 1;
+    b += std::pow(2 * km + 1, 3) * 6 * 8 + nat * 4.0 * 8;             // Ewald tables
+    return 1.05 * b + 8.0 * (1 << 20);                                 // pool granularity, graphs
+}
+
+ofdft_status busy(ofdft_ctx *c)
+{
+    return c->pending ? fail(c, OFDFT_EBUSY, "a minimisation is in flight (call ofdft_minimize_wait)") : OFDFT_OK;
+}
+
+#define NOT_BUSY(c)                              \
+    do {                                         \
+        if (busy(c) != OFDFT_OK) return OFDFT_EBUSY; \
+    } while (0)
+
+// ------------------------------------------------------------ autotuner
+struct TuneKey {
+    int nx, ny, nz, prec;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(nx, ny, nz, prec) < std::tie(o.nx, o.ny, o.nz, o.prec);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;   // -> (zP, tk)
+
+// Mean time of `reps` evaluations of field set f at its current phi.
+template <typename T> ofdft_status time_evals(ofdft_ctx *c, FieldSet &f, int reps, float &ms)
+{
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    ofdft_status r = enqueue_eval<T>(c, f, (T *)f.phi, nullptr, nullptr, 1.0, 0.0, nullptr, (T *)f.vt, false, c->scal);
+    cudaEventRecord(e0, c->st);
+    for (int i = 0; i < reps && r == OFDFT_OK; ++i)
+        r = enqueue_eval<T>(c, f, (T *)f.phi, nullptr, nullptr, 1.0, 0.0, nullptr, (T *)f.vt, false, c->scal);
+    cudaEventRecord(e1, c->st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != OFDFT_OK) return r;
+    if (e != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "autotune timing");
+    ms /= (float)reps;
+    return OFDFT_OK;
+}
+
+// Pick the column-tile width of the y/x passes (the z kernels do not depend
+// on it), then the z line pairs per block, by timing whole evaluations.
+template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
+{
+    FieldSet &f = c->f[k];
+    const TuneKey key{c->g.nx, c->g.ny, c->g.nz, (int)sizeof(T)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            f.gt.zP = it->second.first;
+            f.gt.tk = it->second.second;
+            if (f.graph) cudaGraphExecDestroy(f.graph);
+            f.graph = nullptr;
+            return OFDFT_OK;
+        }
+    }
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
+    const size_t dyn = (size_t)optin - 8192;
+    GridInfo best = f.gt;
+    float best_ms = 1e30f;
+    for (int tk : {4, 8, 16}) {
+        GridInfo g = best;
+        g.tk = tk;
+        if (tk > g.K && tk != 4) continue;
+        if (field_smem_max(g, sizeof(cplx<T>)) > dyn) continue;
+        f.gt = g;
+        float ms;
+        ofdft_status r = time_evals<T>(c, f, reps, ms);
+        if (r != OFDFT_OK) return r;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = g;
+        }
+    }
+    best_ms = 1e30f;
+    GridInfo base = best;
+    for (int zp : {1, 2, 4, 8}) {
+        GridInfo g = base;
+        g.zP = zp;
+        if ((long long)zp * g.nz > 2048 || (long long)zp > (long long)g.nx * g.ny / 2) continue;
+        if (field_smem_max(g, sizeof(cplx<T>)) > dyn) continue;
+        f.gt = g;
+        float ms;
+        ofdft_status r = time_evals<T>(c, f, reps, ms);
+        if (r != OFDFT_OK) return r;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = g;
+        }
+    }
+    f.gt = best;
+    if (f.graph) cudaGraphExecDestroy(f.graph);
+    f.graph = nullptr;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = std::make_pair(best.zP, best.tk);
     return OFDFT_OK;
 }
 
@@ -934,11 +1120,11 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
         free_ctx(c);
         return s == OFDFT_EDEVICE ? OFDFT_ENOMEM : s;
     }
-    cudaMemcpy(c->Rd, c->R.data(), 3 * nat * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(c->Zd, c->Z.data(), nat * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(c->Md, c->masses.data(), nat * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemset(c->Vd, 0, 3 * nat * sizeof(double));
-    cudaMemset(c->nh, 0, 4 * sizeof(double));
+    cudaMemcpyAsync(c->Rd, c->R.data(), 3 * nat * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->Zd, c->Z.data(), nat * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->Md, c->masses.data(), nat * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    cudaMemsetAsync(c->Vd, 0, 3 * nat * sizeof(double), c->st);
+    cudaMemsetAsync(c->nh, 0, 4 * sizeof(double), c->st);
     s = update_ions(c);
     if (s == OFDFT_OK) s = ofdft_set_phi(c, nullptr);
     if (s != OFDFT_OK) {
@@ -953,6 +1139,7 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
 ofdft_status ofdft_set_positions(ofdft_ctx *c, const double *ions)
 {
     if (!c || !ions) return fail(c, OFDFT_EINVAL, "NULL argument");
+    NOT_BUSY(c);
     cudaSetDevice(c->dev);
     for (int i = 0; i < 3 * c->nat; ++i)
         if (!isfinite(ions[i])) return fail(c, OFDFT_EINVAL, "non-finite ion position");
@@ -965,6 +1152,7 @@ ofdft_status ofdft_set_positions(ofdft_ctx *c, const double *ions)
 ofdft_status ofdft_set_phi(ofdft_ctx *c, const double *phi)
 {
     if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
+    NOT_BUSY(c);
     cudaSetDevice(c->dev);
     const long long N = c->g.N;
     FieldSet &f = c->f[0];
@@ -982,6 +1170,7 @@ ofdft_status ofdft_set_phi(ofdft_ctx *c, const double *phi)
 ofdft_status ofdft_energy_potential(ofdft_ctx *c, const double *phi, ofdft_energy *E, double *v)
 {
     if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
+    NOT_BUSY(c);
     cudaSetDevice(c->dev);
     const long long N = c->g.N;
     FieldSet &f = c->f[0];
@@ -1006,6 +1195,7 @@ ofdft_status ofdft_energy_potential(ofdft_ctx *c, const double *phi, ofdft_energ
 ofdft_status ofdft_minimize(ofdft_ctx *c, double gtol, int maxit, ofdft_energy *E, ofdft_stats *stats)
 {
     if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
+    NOT_BUSY(c);
     if (!(gtol > 0.0) || maxit <= 0) return fail(c, OFDFT_EINVAL, "gtol must be > 0 and maxit > 0");
     cudaSetDevice(c->dev);
     ofdft_stats st{};
@@ -1018,16 +1208,100 @@ ofdft_status ofdft_minimize(ofdft_ctx *c, double gtol, int maxit, ofdft_energy *
     return OFDFT_OK;
 }
 
+ofdft_status ofdft_minimize_start(ofdft_ctx *c, double gtol, int maxit)
+{
+    if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
+    if (!(gtol > 0.0) || maxit <= 0) return fail(c, OFDFT_EINVAL, "gtol must be > 0 and maxit > 0");
+    cudaSetDevice(c->dev);
+    return minimize_start(c, gtol, maxit);
+}
+
+ofdft_status ofdft_minimize_query(ofdft_ctx *c)
+{
+    if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
+    if (!c->pending) return OFDFT_OK;
+    cudaSetDevice(c->dev);
+    cudaError_t e = cudaEventQuery(c->done_ev);
+    if (e == cudaErrorNotReady) return OFDFT_EBUSY;
+    if (e != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "ofdft_minimize_query");
+    return OFDFT_OK;
+}
+
+ofdft_status ofdft_minimize_wait(ofdft_ctx *c, ofdft_energy *E, ofdft_stats *stats)
+{
+    if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
+    cudaSetDevice(c->dev);
+    ofdft_stats st{};
+    EvalScalars es;
+    ofdft_status s = minimize_wait(c, st, es);
+    if (stats) *stats = st;
+    if (s != OFDFT_OK && s != OFDFT_ENOCONV) return s;
+    if (E) *E = c->last;
+    if (s == OFDFT_ENOCONV) return fail(c, OFDFT_ENOCONV, "CG did not reach the tolerance");
+    return OFDFT_OK;
+}
+
+ofdft_status ofdft_batch_minimize(int n, ofdft_ctx *const *ctxs, double gtol, int maxit, ofdft_energy *E,
+                                  ofdft_stats *stats)
+{
+    if (n < 0 || (n > 0 && !ctxs)) return fail(nullptr, OFDFT_EINVAL, "bad batch");
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return fail(nullptr, OFDFT_EINVAL, "NULL context in batch");
+    ofdft_status first = OFDFT_OK;
+    std::vector<char> started(n, 0);
+    for (int i = 0; i < n; ++i) {
+        ofdft_status s = ofdft_minimize_start(ctxs[i], gtol, maxit);
+        started[i] = s == OFDFT_OK;
+        if (s != OFDFT_OK && first == OFDFT_OK) first = s;
+    }
+    for (int i = 0; i < n; ++i) {
+        ofdft_energy e{};
+        ofdft_stats st{};
+        ofdft_status s = started[i] ? ofdft_minimize_wait(ctxs[i], &e, &st) : OFDFT_EINVAL;
+        if (!started[i]) st.status = s;
+        if (E) E[i] = e;
+        if (stats) stats[i] = st;
+        if (s != OFDFT_OK && first == OFDFT_OK) first = s;
+    }
+    return first;
+}
+
+ofdft_status ofdft_footprint(const int grid[3], int nat, int precision, double *bytes)
+{
+    if (!grid || !bytes || nat <= 0) return fail(nullptr, OFDFT_EINVAL, "bad footprint arguments");
+    for (int a = 0; a < 3; ++a)
+        if (!smooth_even(grid[a])) return fail(nullptr, OFDFT_EINVAL, "bad grid");
+    *bytes = footprint_bytes(grid, nat, precision);
+    return OFDFT_OK;
+}
+
+ofdft_status ofdft_autotune(ofdft_ctx *c, int reps)
+{
+    if (!c || reps < 1) return fail(c, OFDFT_EINVAL, "NULL context or reps < 1");
+    NOT_BUSY(c);
+    cudaSetDevice(c->dev);
+    ofdft_status s = autotune_set<double>(c, 0, reps);
+    if (s == OFDFT_OK && c->f[1].valid) {
+        launch_convert<double, float>(c->g.N, (const double *)c->f[0].phi, (float *)c->f[1].phi, c->st);
+        s = autotune_set<float>(c, 1, reps);
+    }
+    return s;
+}
+
 ofdft_status ofdft_forces(ofdft_ctx *c, double *F, double *pressure)
 {
     if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
+    NOT_BUSY(c);
     cudaSetDevice(c->dev);
     EvalScalars es;
     ofdft_status s = forces_now(c, es);
     if (s != OFDFT_OK) return s;
     ofdft_energy e;
     fill_energy(c, es, e);
-    if (F) CK(cudaMemcpy(F, c->Fd, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToHost));
+    if (F) {
+        CK(cudaMemcpyAsync(F, c->Fd, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
     if (pressure) *pressure = e.P;
     return OFDFT_OK;
 }
@@ -1035,6 +1309,7 @@ ofdft_status ofdft_forces(ofdft_ctx *c, double *F, double *pressure)
 ofdft_status ofdft_get_density(ofdft_ctx *c, double *n)
 {
     if (!c || !n) return fail(c, OFDFT_EINVAL, "NULL argument");
+    NOT_BUSY(c);
     cudaSetDevice(c->dev);
     const long long N = c->g.N;
     CK(cudaMemcpyAsync(n, c->f[0].phi, N * sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -1046,10 +1321,11 @@ ofdft_status ofdft_get_density(ofdft_ctx *c, double *n)
 ofdft_status ofdft_set_masses(ofdft_ctx *c, const double *m)
 {
     if (!c || !m) return fail(c, OFDFT_EINVAL, "NULL argument");
+    NOT_BUSY(c);
     for (int i = 0; i < c->nat; ++i)
         if (!(m[i] > 0.0)) return fail(c, OFDFT_EINVAL, "masses must be > 0");
     c->masses.assign(m, m + c->nat);
-    CK(cudaMemcpy(c->Md, m, c->nat * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(c->Md, m, c->nat * sizeof(double), cudaMemcpyHostToDevice, c->st));
     return OFDFT_OK;
 }
 
@@ -1057,6 +1333,7 @@ ofdft_status ofdft_md_step(ofdft_ctx *c, const ofdft_md_params *mp, int nsteps, 
                            double *F, ofdft_energy *E, ofdft_stats *stats)
 {
     if (!c || !mp) return fail(c, OFDFT_EINVAL, "NULL argument");
+    NOT_BUSY(c);
     if (!(mp->dt_fs > 0.0) || !(mp->gtol > 0.0) || mp->maxit <= 0 || nsteps < 0)
         return fail(c, OFDFT_EINVAL, "bad MD parameters");
     cudaSetDevice(c->dev);
@@ -1130,7 +1407,8 @@ ofdft_status ofdft_md_step(ofdft_ctx *c, const ofdft_md_params *mp, int nsteps, 
     if (vel) CK(cudaMemcpyAsync(vel, c->Vd, 3 * nat * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     if (F) CK(cudaMemcpyAsync(F, c->Fd, 3 * nat * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    CK(cudaMemcpy(c->R.data(), c->Rd, 3 * nat * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(c->R.data(), c->Rd, 3 * nat * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
     if (E) *E = c->last;
     if (stats) *stats = tot;
     return OFDFT_OK;
@@ -1141,8 +1419,9 @@ ofdft_status ofdft_md_state(ofdft_ctx *c, double *pos, double *vel)
     if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
     cudaSetDevice(c->dev);
     CK(cudaStreamSynchronize(c->st));
-    if (pos) CK(cudaMemcpy(pos, c->Rd, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToHost));
-    if (vel) CK(cudaMemcpy(vel, c->Vd, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToHost));
+    if (pos) CK(cudaMemcpyAsync(pos, c->Rd, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (vel) CK(cudaMemcpyAsync(vel, c->Vd, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
     return OFDFT_OK;
 }
 
@@ -1151,7 +1430,8 @@ ofdft_status ofdft_md_conserved(ofdft_ctx *c, double *H)
     if (!c || !H) return fail(c, OFDFT_EINVAL, "NULL argument");
     if (!c->last_valid) return fail(c, OFDFT_EINVAL, "no MD step has run");
     double nh[4];
-    CK(cudaMemcpy(nh, c->nh, sizeof(nh), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(nh, c->nh, sizeof(nh), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
     int ndof = 3 * c->nat - 3;
     *H = nh[2] + c->last.F_tot + 0.5 * c->md_Q * nh[0] * nh[0] + ndof * c->md_kT * nh[1];
     return OFDFT_OK;

@@ -16,7 +16,6 @@ namespace ofdft {
 
 namespace {
 
-constexpr int kTK = 8;  // half-spectrum columns per y/x tile
 
 // G vector of the half-spectrum point (ix, iy, kz) in the accumulator
 // precision A, from the per-axis reciprocal spacings (no divisions).
@@ -267,22 +266,24 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const cplx<T> *__restric
 }
 
 // ------------------------------------------------------------- y/x passes
-// Tile: kTK consecutive kz columns of one ix-plane (y pass) or one iy-row
+// Tile: g.tk consecutive kz columns of one ix-plane (y pass) or one iy-row
 // (x pass); rows are the transformed axis.
 
 struct ColTile {
     long long base;   // offset of (row 0, kz0) in the field
     long long rstride;
-    int kz0, ncol, outer;
+    int kz0, ncol, outer, tk;
 };
 
 __device__ __forceinline__ ColTile col_tile(const GridInfo &g, bool xaxis)
 {
-    const int ntk = (g.K + kTK - 1) / kTK;
+    const int tk = g.tk;
+    const int ntk = (g.K + tk - 1) / tk;
     ColTile t;
+    t.tk = tk;
     t.outer = blockIdx.x / ntk;
-    t.kz0 = (blockIdx.x - t.outer * ntk) * kTK;
-    t.ncol = min(kTK, g.K - t.kz0);
+    t.kz0 = (blockIdx.x - t.outer * ntk) * tk;
+    t.ncol = min(tk, g.K - t.kz0);
     if (xaxis) {
         t.base = (long long)t.outer * g.K + t.kz0;   // outer = iy
         t.rstride = (long long)g.ny * g.K;
@@ -296,8 +297,8 @@ __device__ __forceinline__ ColTile col_tile(const GridInfo &g, bool xaxis)
 template <typename C>
 __device__ __forceinline__ void load_tile(const C *__restrict__ src, const ColTile &t, int nrows, C *dst)
 {
-    for (int i = threadIdx.x; i < nrows * kTK; i += blockDim.x) {
-        const int r = i / kTK, c = i - r * kTK;
+    for (int i = threadIdx.x; i < nrows * t.tk; i += blockDim.x) {
+        const int r = i / t.tk, c = i - r * t.tk;
         if (c < t.ncol) dst[i] = src[t.base + r * t.rstride + c];
     }
 }
@@ -305,8 +306,8 @@ __device__ __forceinline__ void load_tile(const C *__restrict__ src, const ColTi
 template <typename C>
 __device__ __forceinline__ void store_tile(C *__restrict__ dst, const ColTile &t, int nrows, const C *src)
 {
-    for (int i = threadIdx.x; i < nrows * kTK; i += blockDim.x) {
-        const int r = i / kTK, c = i - r * kTK;
+    for (int i = threadIdx.x; i < nrows * t.tk; i += blockDim.x) {
+        const int r = i / t.tk, c = i - r * t.tk;
         if (c < t.ncol) dst[t.base + r * t.rstride + c] = src[i];
     }
 }
@@ -317,12 +318,12 @@ __global__ void k_ypass(GridInfo g, FftAxis ay, cplx<T> *__restrict__ data, long
     typedef cplx<T> C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *A = reinterpret_cast<C *>(smraw);
-    C *B = A + g.ny * kTK;
+    C *B = A + g.ny * g.tk;
     ColTile t = col_tile(g, false);
     C *f = data + blockIdx.y * fstride;
     load_tile(f, t, g.ny, A);
     __syncthreads();
-    C *X = fft_lines<C, INV>(A, B, ay, t.ncol, 1, kTK, true);
+    C *X = fft_lines<C, INV>(A, B, ay, t.ncol, 1, g.tk, true);
     store_tile(f, t, g.ny, X);
 }
 
@@ -338,18 +339,18 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, cplx<T> *__restrict__ nspec,
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx;
     C *A = reinterpret_cast<C *>(smraw);
-    C *B = A + nx * kTK;
-    C *N = B + nx * kTK;
+    C *B = A + nx * g.tk;
+    C *N = B + nx * g.tk;
     ColTile t = col_tile(g, true);
     load_tile(nspec, t, nx, A);
     __syncthreads();
-    C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, kTK, true);
+    C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, g.tk, true);
     typedef typename AccT<T>::type Ac;
     const Ac bx = Ac(g.bx), by = Ac(g.by), bz = Ac(g.bz), hr = Ac(0.5 * g.rc * g.rc);
     const T invN = T(1.0 / (double)g.N);
     Ac acc[3] = {0, 0, 0};     // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
-    for (int i = threadIdx.x; i < nx * kTK; i += blockDim.x) {
-        const int r = i / kTK, c = i - r * kTK;
+    for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
+        const int r = i / g.tk, c = i - r * g.tk;
         if (c >= t.ncol) continue;
         C nG = cscale(X[i], invN);
         N[i] = nG;
@@ -367,15 +368,15 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, cplx<T> *__restrict__ nspec,
     store_tile(nspec, t, nx, N);
     C *outs[3] = {g0, g1, g2};
     for (int a = 0; a < 3; ++a) {
-        for (int i = threadIdx.x; i < nx * kTK; i += blockDim.x) {
-            const int r = i / kTK, c = i - r * kTK;
+        for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
+            const int r = i / g.tk, c = i - r * g.tk;
             Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + min(c, t.ncol - 1));
             T d = T(a == 0 ? k.dx : (a == 1 ? k.dy : k.dz));
             C v = N[i];
             A[i] = cmk<C>(-d * v.y, d * v.x);      // i D_a n(G)
         }
         __syncthreads();
-        C *Y = fft_lines<C, true>(A, B, ax, t.ncol, 1, kTK, true);
+        C *Y = fft_lines<C, true>(A, B, ax, t.ncol, 1, g.tk, true);
         store_tile(outs[a], t, nx, Y);
         __syncthreads();
     }
@@ -401,18 +402,18 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, cplx<T> *__restrict__ spec,
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx;
     C *A = reinterpret_cast<C *>(smraw);
-    C *B = A + nx * kTK;
+    C *B = A + nx * g.tk;
     ColTile t = col_tile(g, true);
     load_tile(spec, t, nx, A);
     __syncthreads();
-    C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, kTK, true);
+    C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, g.tk, true);
     typedef typename AccT<T>::type Ac;
     const Ac bx = Ac(g.bx), by = Ac(g.by), bz = Ac(g.bz), hr = Ac(0.5 * g.rc * g.rc);
     const Ac fourpi = Ac(12.566370614359172954);
     const T invN = T(1.0 / (double)g.N);
     Ac acc[3] = {0, 0, 0};
-    for (int i = threadIdx.x; i < nx * kTK; i += blockDim.x) {
-        const int r = i / kTK, c = i - r * kTK;
+    for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
+        const int r = i / g.tk, c = i - r * g.tk;
         if (c >= t.ncol) continue;
         C nG = cscale(X[i], invN);
         Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
@@ -433,7 +434,7 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, cplx<T> *__restrict__ spec,
     __syncthreads();
     if (inverse) {
         C *other = (X == A) ? B : A;
-        C *Y = fft_lines<C, true>(X, other, ax, t.ncol, 1, kTK, true);
+        C *Y = fft_lines<C, true>(X, other, ax, t.ncol, 1, g.tk, true);
         store_tile(spec, t, nx, Y);
     }
     double tot[3];
@@ -456,15 +457,15 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const cplx<T> *__restrict__ nG,
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx;
     C *A = reinterpret_cast<C *>(smraw);
-    C *B = A + nx * kTK;
-    C *D = B + nx * kTK;
+    C *B = A + nx * g.tk;
+    C *D = B + nx * g.tk;
     ColTile t = col_tile(g, true);
     typedef typename AccT<T>::type Ac;
     const Ac bx = Ac(g.bx), by = Ac(g.by), bz = Ac(g.bz);
     const Ac fourpi = Ac(12.566370614359172954);
     const T invN = T(1.0 / (double)g.N);
-    for (int i = threadIdx.x; i < nx * kTK; i += blockDim.x) {
-        const int r = i / kTK, c = i - r * kTK;
+    for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
+        const int r = i / g.tk, c = i - r * g.tk;
         if (c >= t.ncol) continue;
         Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
         C out = cmk<C>(T(0), T(0));
@@ -480,9 +481,9 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const cplx<T> *__restrict__ nG,
     for (int a = 0; a < 3; ++a) {
         load_tile(ws[a], t, nx, A);
         __syncthreads();
-        C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, kTK, true);
-        for (int i = threadIdx.x; i < nx * kTK; i += blockDim.x) {
-            const int r = i / kTK, c = i - r * kTK;
+        C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, g.tk, true);
+        for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
+            const int r = i / g.tk, c = i - r * g.tk;
             if (c >= t.ncol) continue;
             Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
             T d = T(a == 0 ? k.dx : (a == 1 ? k.dy : k.dz)) * invN;
@@ -491,12 +492,13 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const cplx<T> *__restrict__ nG,
         }
         __syncthreads();
     }
-    C *Y = fft_lines<C, true>(D, A, ax, t.ncol, 1, kTK, true);
+    C *Y = fft_lines<C, true>(D, A, ax, t.ncol, 1, g.tk, true);
     store_tile(w0, t, nx, Y);
 }
 
 int zpairs_per_block(const GridInfo &g)
 {
+    if (g.zP > 0) return g.zP;
     long long npairs = (long long)g.nx * g.ny / 2;
     int P = (int)(npairs / 608);
     if (P > 8) P = 8;
@@ -567,10 +569,10 @@ template <typename T>
 void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data, int nfields,
                   long long fstride, cudaStream_t st)
 {
-    int ntk = (g.K + kTK - 1) / kTK;
+    int ntk = (g.K + g.tk - 1) / g.tk;
     dim3 grid(g.nx * ntk, nfields);
-    size_t sm = 2 * (size_t)g.ny * kTK * sizeof(cplx<T>);
-    int th = threads_for(g.ny * kTK / 2);
+    size_t sm = 2 * (size_t)g.ny * g.tk * sizeof(cplx<T>);
+    int th = threads_for(g.ny * g.tk / 2);
     if (inv) k_ypass<T, true><<<grid, th, sm, st>>>(g, ay, data, fstride);
     else k_ypass<T, false><<<grid, th, sm, st>>>(g, ay, data, fstride);
 }
@@ -579,10 +581,10 @@ template <typename T>
 int launch_xgrad(const GridInfo &g, const FftAxis &ax, cplx<T> *nspec, const cplx<T> *vext,
                  cplx<T> *g0, cplx<T> *g1, cplx<T> *g2, double *part, cudaStream_t st)
 {
-    int ntk = (g.K + kTK - 1) / kTK;
+    int ntk = (g.K + g.tk - 1) / g.tk;
     int blocks = g.ny * ntk;
-    size_t sm = 3 * (size_t)g.nx * kTK * sizeof(cplx<T>);
-    int th = threads_for(g.nx * kTK / 2);
+    size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
+    int th = threads_for(g.nx * g.tk / 2);
     k_xgrad<T><<<blocks, th, sm, st>>>(g, ax, nspec, vext, g0, g1, g2, part);
     return blocks;
 }
@@ -591,10 +593,10 @@ template <typename T>
 int launch_xhl(const GridInfo &g, const FftAxis &ax, cplx<T> *spec, const cplx<T> *vext,
                cplx<T> *nG_out, int inverse, double *part, cudaStream_t st)
 {
-    int ntk = (g.K + kTK - 1) / kTK;
+    int ntk = (g.K + g.tk - 1) / g.tk;
     int blocks = g.ny * ntk;
-    size_t sm = 2 * (size_t)g.nx * kTK * sizeof(cplx<T>);
-    int th = threads_for(g.nx * kTK / 2);
+    size_t sm = 2 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
+    int th = threads_for(g.nx * g.tk / 2);
     k_xhl<T><<<blocks, th, sm, st>>>(g, ax, spec, vext, nG_out, inverse, part);
     return blocks;
 }
@@ -603,10 +605,10 @@ template <typename T>
 void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const cplx<T> *vext,
                  cplx<T> *w0, const cplx<T> *w1, const cplx<T> *w2, cudaStream_t st)
 {
-    int ntk = (g.K + kTK - 1) / kTK;
+    int ntk = (g.K + g.tk - 1) / g.tk;
     int blocks = g.ny * ntk;
-    size_t sm = 3 * (size_t)g.nx * kTK * sizeof(cplx<T>);
-    int th = threads_for(g.nx * kTK / 2);
+    size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
+    int th = threads_for(g.nx * g.tk / 2);
     k_xdiv<T><<<blocks, th, sm, st>>>(g, ax, nG, vext, w0, w1, w2);
 }
 
@@ -614,8 +616,8 @@ size_t field_smem_max(const GridInfo &g, size_t csize)
 {
     int P = zpairs_per_block(g);
     size_t z = 4 * (size_t)P * g.nz * csize;
-    size_t y = 2 * (size_t)g.ny * kTK * csize;
-    size_t x = 3 * (size_t)g.nx * kTK * csize;
+    size_t y = 2 * (size_t)g.ny * g.tk * csize;
+    size_t x = 3 * (size_t)g.nx * g.tk * csize;
     size_t m = z > y ? z : y;
     return m > x ? m : x;
 }

@@ -60,10 +60,13 @@ struct GridInfo {
     double Lx, Ly, Lz, omega, dV;
     double rc;               // Gaussian local pseudopotential radius
     double bx, by, bz;       // reciprocal spacing 2 pi / L per axis
+    int zP;                  // z passes: line pairs per block (0: default rule)
+    int tk;                  // y/x passes: half-spectrum columns per tile (4, 8 or 16)
 };
 
 inline void grid_reciprocal(GridInfo &g)
 {
+    if (g.tk <= 0) g.tk = 8;
     const double tp = 6.283185307179586477;
     g.bx = tp / g.Lx;
     g.by = tp / g.Ly;

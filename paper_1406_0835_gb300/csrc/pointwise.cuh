@@ -241,6 +241,13 @@ OF_HD FsOut<T> fs_point(const FuncParams &fp, const T *__restrict__ tab, T temp,
 }
 
 // Perdew-Zunger 1981 unpolarised LDA: eps_xc and v_xc = eps_xc - (r_s/3) d eps_xc/d r_s.
+// gamma, beta1, beta2, A, B as published; C and D are fixed by continuity of
+// eps_c and its r_s derivative at r_s = 1 (the published rounded C, D leave a
+// small jump there).
+constexpr double kPzDen = 1.0 + 1.0529 + 0.3334;
+constexpr double kPzD = -0.1423 / kPzDen + 0.048;                                // B + D = eps_pade(1)
+constexpr double kPzC = 0.1423 * (0.5 * 1.0529 + 0.3334) / (kPzDen * kPzDen) - 0.0311 - kPzD;
+
 template <typename T>
 OF_HD void pz81_point(T n, T &eps, T &v)
 {
@@ -255,9 +262,9 @@ OF_HD void pz81_point(T n, T &eps, T &v)
         vc = ec * (T(1) + T(7.0 / 6.0 * 1.0529) * sq + T(4.0 / 3.0 * 0.3334) * rs) * den;
     } else {
         T lr = log(rs);
-        ec = T(0.0311) * lr + T(-0.048) + T(0.0020) * rs * lr + T(-0.0116) * rs;
-        vc = T(0.0311) * lr + T(-0.048 - 0.0311 / 3.0) + T(2.0 / 3.0 * 0.0020) * rs * lr
-             + T((2.0 * -0.0116 - 0.0020) / 3.0) * rs;
+        ec = T(0.0311) * lr + T(-0.048) + T(kPzC) * rs * lr + T(kPzD) * rs;
+        vc = T(0.0311) * lr + T(-0.048 - 0.0311 / 3.0) + T(2.0 / 3.0 * kPzC) * rs * lr
+             + T((2.0 * kPzD - kPzC) / 3.0) * rs;
     }
     eps = ex + ec;
     v = T(4.0 / 3.0) * ex + vc;

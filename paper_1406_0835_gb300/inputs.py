@@ -116,3 +116,23 @@ def config_batch(count=64, seed=5, n_range=(8, 512), rho_range=(0.1, 10.0),
         g = grid_edge(L, 0.25, 32, grid_hi)
         out.append(hydrogen(na, rho, T, g, seed=1000 + i, functional=fn))
     return out
+
+
+def config_serve(count=24, seed=6, rate=50.0, n_range=(16, 128), rho_range=(0.1, 20.0),
+                 T_range=(2.0e3, 4.0e6), grid_hi=96, functional="vt84f"):
+    """Equation-of-state request stream: Poisson arrivals at `rate` per second
+    of (rho, T, N_atoms) points drawn log-uniform, grid by the 0.25-bohr rule
+    (32 .. grid_hi per edge).  Returns [(arrival_s, system dict)]."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += rng.exponential(1.0 / rate)
+        na = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        rho = math.exp(rng.uniform(math.log(rho_range[0]), math.log(rho_range[1])))
+        T = math.exp(rng.uniform(math.log(T_range[0]), math.log(T_range[1])))
+        L = cell_edge(na, rho)
+        g = grid_edge(L, 0.25, 32, grid_hi)
+        d = hydrogen(na, rho, T, g, seed=2000 + i, functional=functional, vel_seed=3000 + i)
+        out.append((t, d))
+    return out

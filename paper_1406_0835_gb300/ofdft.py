@@ -48,6 +48,33 @@ class MDParams(ctypes.Structure):
                 ("tau_steps", ctypes.c_double), ("gtol", ctypes.c_double), ("maxit", ctypes.c_int)]
 
 
+class ServeParams(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("max_slots", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_double), ("dry_run", ctypes.c_int),
+                ("dry_run_ms", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("cell", ctypes.c_double * 9), ("grid", ctypes.c_int * 3), ("nat", ctypes.c_int),
+                ("ions", _P), ("Z", _P), ("vel", _P), ("T_kelvin", ctypes.c_double),
+                ("functional", ctypes.c_int), ("precision", ctypes.c_int), ("xc", ctypes.c_int),
+                ("rc", ctypes.c_double), ("md_steps", ctypes.c_int), ("dt_fs", ctypes.c_double),
+                ("gtol", ctypes.c_double), ("maxit", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("E", Energy),
+                ("P_mean", ctypes.c_double), ("steps_done", ctypes.c_int),
+                ("evaluations", ctypes.c_longlong), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {n: getattr(self, n) for n, _ in self._fields_ if n != "E"}
+        d["E"] = self.E.as_dict()
+        return d
+
+
 class OfdftError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS.get(status, status), msg))
@@ -82,6 +109,23 @@ SIGNATURES = {
     "ofdft_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ofdft_tfunc_eval": (ctypes.c_int, [ctypes.c_longlong, _P, _P]),
     "ofdft_destroy": (None, [ctypes.c_void_p]),
+    "ofdft_minimize_start": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
+    "ofdft_minimize_query": (ctypes.c_int, [ctypes.c_void_p]),
+    "ofdft_minimize_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Energy),
+                                           ctypes.POINTER(Stats)]),
+    "ofdft_batch_minimize": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.c_double, ctypes.c_int, ctypes.POINTER(Energy),
+                                            ctypes.POINTER(Stats)]),
+    "ofdft_footprint": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, _P]),
+    "ofdft_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ofdft_serve_start": (ctypes.c_int, [ctypes.POINTER(ServeParams), ctypes.POINTER(ctypes.c_void_p)]),
+    "ofdft_serve_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request),
+                                          ctypes.POINTER(ctypes.c_longlong)]),
+    "ofdft_serve_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.POINTER(Result)]),
+    "ofdft_serve_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "ofdft_serve_clock": (ctypes.c_double, [ctypes.c_void_p]),
+    "ofdft_serve_peaks": (ctypes.c_int, [ctypes.c_void_p, _P, ctypes.POINTER(ctypes.c_int)]),
+    "ofdft_serve_stop": (ctypes.c_int, [ctypes.c_void_p]),
     "ofdft_energy_potential_static": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                                      _P, _P, ctypes.c_double, ctypes.c_int,
                                                      ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
@@ -169,6 +213,48 @@ def ofdft_minimize(ctx, gtol=1e-8, maxit=5000, raise_on_noconv=True):
     if st != -3 or raise_on_noconv:
         _check(ctx, st)
     return E.as_dict(), S.as_dict()
+
+
+def ofdft_minimize_start(ctx, gtol=1e-8, maxit=5000):
+    _check(ctx, load().ofdft_minimize_start(ctx, float(gtol), int(maxit)))
+
+
+def ofdft_minimize_query(ctx):
+    """True once the minimisation started last has finished."""
+    st = load().ofdft_minimize_query(ctx)
+    if st == -7:
+        return False
+    _check(ctx, st)
+    return True
+
+
+def ofdft_minimize_wait(ctx, raise_on_noconv=True):
+    E, S = Energy(), Stats()
+    st = load().ofdft_minimize_wait(ctx, ctypes.byref(E), ctypes.byref(S))
+    if st != -3 or raise_on_noconv:
+        _check(ctx, st)
+    return E.as_dict(), S.as_dict()
+
+
+def ofdft_batch_minimize(ctxs, gtol=1e-8, maxit=5000):
+    """Minimise every context concurrently; returns ([E], [stats], status)."""
+    n = len(ctxs)
+    arr = (ctypes.c_void_p * n)(*ctxs)
+    E = (Energy * n)()
+    S = (Stats * n)()
+    st = load().ofdft_batch_minimize(n, arr, float(gtol), int(maxit), E, S)
+    return [e.as_dict() for e in E], [x.as_dict() for x in S], st
+
+
+def ofdft_footprint(grid, nat, precision="fp64"):
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    b = np.zeros(1)
+    _check(None, load().ofdft_footprint(g, int(nat), PRECISIONS.get(precision, precision), _ptr(b)))
+    return float(b[0])
+
+
+def ofdft_autotune(ctx, reps=3):
+    _check(ctx, load().ofdft_autotune(ctx, int(reps)))
 
 
 def ofdft_forces(ctx):
@@ -306,6 +392,15 @@ class Context:
     def minimize(self, gtol=1e-8, maxit=5000, raise_on_noconv=True):
         return ofdft_minimize(self.ctx, gtol, maxit, raise_on_noconv)
 
+    def minimize_start(self, gtol=1e-8, maxit=5000):
+        ofdft_minimize_start(self.ctx, gtol, maxit)
+
+    def minimize_wait(self, raise_on_noconv=True):
+        return ofdft_minimize_wait(self.ctx, raise_on_noconv)
+
+    def autotune(self, reps=3):
+        ofdft_autotune(self.ctx, reps)
+
     def forces(self):
         return ofdft_forces(self.ctx)
 
@@ -348,3 +443,76 @@ def ofdft_energy_potential_static(cell, grid, ions, Z, T_kelvin, functional, phi
         raise OfdftError(st, "static path: edges even, {2,3,5}-smooth, <= 64; "
                              "nx*ny*nz <= 32768; 1 <= nat <= 64; valid cell, T, functional")
     return E.as_dict()
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """Request loop of the serving form (ofdft_serve_*): submit systems with
+    a number of MD steps, poll or drain for results."""
+
+    def __init__(self, max_slots=4, hbm_budget_bytes=0.0, device=0, dry_run_ms=None):
+        p = ServeParams(int(device), int(max_slots), float(hbm_budget_bytes),
+                        0 if dry_run_ms is None else 1, float(dry_run_ms or 0.0))
+        h = ctypes.c_void_p()
+        st = load().ofdft_serve_start(ctypes.byref(p), ctypes.byref(h))
+        if st != 0:
+            raise OfdftError(st, "ofdft_serve_start failed")
+        self.h = h.value
+
+    def submit(self, L, grid, ions, Z, T_kelvin, functional="vt84f", precision="mixed",
+               md_steps=0, dt_fs=0.2, vel=None, gtol=1e-8, maxit=5000, xc=True, rc=0.25):
+        ions = _f64(ions, (-1, 3))
+        Z = _f64(Z, (-1,))
+        vel = None if vel is None else _f64(vel, (-1, 3))
+        r = Request()
+        cell = np.diag(np.asarray(L, dtype=np.float64)).reshape(-1) if np.size(L) == 3 else _f64(L).reshape(-1)
+        for i in range(9):
+            r.cell[i] = float(cell[i])
+        for i in range(3):
+            r.grid[i] = int(grid[i])
+        r.nat = len(Z)
+        r.ions, r.Z, r.vel = _ptr(ions), _ptr(Z), _ptr(vel)
+        r.T_kelvin = float(T_kelvin)
+        r.functional = FUNCTIONALS[functional] if isinstance(functional, str) else int(functional)
+        r.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        r.xc, r.rc = int(bool(xc)), float(rc)
+        r.md_steps, r.dt_fs, r.gtol, r.maxit = int(md_steps), float(dt_fs), float(gtol), int(maxit)
+        rid = ctypes.c_longlong()
+        st = load().ofdft_serve_submit(self.h, ctypes.byref(r), ctypes.byref(rid))
+        if st != 0:
+            raise OfdftError(st, "ofdft_serve_submit failed")
+        return rid.value
+
+    def poll(self, rid):
+        res = Result()
+        st = load().ofdft_serve_poll(self.h, int(rid), ctypes.byref(res))
+        if st == -7:
+            return None
+        if st != 0:
+            raise OfdftError(st, "ofdft_serve_poll failed")
+        return res.as_dict()
+
+    def drain(self, timeout_s=0.0):
+        st = load().ofdft_serve_drain(self.h, float(timeout_s))
+        if st != 0:
+            raise OfdftError(st, "ofdft_serve_drain")
+
+    def clock(self):
+        return load().ofdft_serve_clock(self.h)
+
+    def peaks(self):
+        b = np.zeros(1)
+        n = ctypes.c_int()
+        load().ofdft_serve_peaks(self.h, _ptr(b), ctypes.byref(n))
+        return float(b[0]), n.value
+
+    def stop(self):
+        if self.h:
+            load().ofdft_serve_stop(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.stop()

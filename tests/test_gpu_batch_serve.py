@@ -1,0 +1,104 @@
+"""GPU: the asynchronous minimiser, the batched form (ofdft_batch_minimize,
+ofdft_autotune) and the serving loop (ofdft_serve_*), all through the C ABI.
+
+Contexts share no device state and every reduction has a fixed order, so a
+solve gives bit-identical results alone, in a batch or in a serving mix; the
+autotuner only changes launch shapes (block partial sums are grouped
+differently), so its results agree to rounding."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1406_0835_gb300 import inputs, ofdft
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _ctx(d, precision="fp64"):
+    return ofdft.Context(d["L"], d["grid"], d["ions"], d["Z"], d["T"], d["functional"],
+                         precision=precision)
+
+
+def test_async_minimize_matches_blocking_and_guards_the_context():
+    d = inputs.config_single_point()
+    with _ctx(d) as a:
+        E1, s1 = a.minimize(gtol=1e-8)
+    with _ctx(d) as b:
+        b.minimize_start(gtol=1e-8)
+        with pytest.raises(ofdft.OfdftError) as e:
+            b.set_phi(None)                     # busy until the wait
+        assert e.value.status == -7
+        t0 = time.time()
+        while not ofdft.ofdft_minimize_query(b.ctx):
+            assert time.time() - t0 < 60
+            time.sleep(0.001)
+        E2, s2 = b.minimize_wait()
+    assert E2["F_tot"] == E1["F_tot"]
+    assert s2["iterations"] == s1["iterations"] and s2["evaluations"] == s1["evaluations"]
+
+
+def test_batch_equals_individual_solves():
+    systems = inputs.config_batch(count=6, seed=11, n_range=(8, 24), rho_range=(0.5, 4.0),
+                                  T_range=(2.0e4, 1.0e6), grid_hi=40)
+    precs = ["fp64", "mixed"] * 3
+    alone = []
+    for d, p in zip(systems, precs):
+        with _ctx(d, p) as c:
+            alone.append(c.minimize(gtol=1e-8, maxit=5000)[0])
+    ctxs = [_ctx(d, p) for d, p in zip(systems, precs)]
+    try:
+        E, S, st = ofdft.ofdft_batch_minimize([c.ctx for c in ctxs], gtol=1e-8, maxit=5000)
+    finally:
+        for c in ctxs:
+            c.close()
+    assert st == 0
+    for e, a, s in zip(E, alone, S):
+        assert s["status"] == 0 and s["gnorm"] < 1e-8
+        assert e["F_tot"] == a["F_tot"] and e["P"] == a["P"]
+
+
+def test_autotune_changes_only_rounding():
+    d = inputs.config_mixed(2.5e5, grid=48, n_atoms=16)
+    with _ctx(d, "mixed") as c:
+        rng = np.random.default_rng(3)
+        phi = np.sqrt(16 / np.prod(d["L"])) * (1 + 0.1 * rng.standard_normal(d["grid"]))
+        E0, v0 = c.energy_potential(phi)
+        c.autotune(reps=2)
+        E1, v1 = c.energy_potential(phi)
+        assert abs(E1["F_tot"] - E0["F_tot"]) <= 1e-13 * abs(E0["F_tot"])
+        assert np.max(np.abs(v1 - v0)) <= 1e-12 * np.max(np.abs(v0))
+        c.set_phi(None)
+        E2, s2 = c.minimize(gtol=1e-8)
+    with _ctx(d, "mixed") as c:
+        E3, s3 = c.minimize(gtol=1e-8)
+    assert abs(E2["F_tot"] - E3["F_tot"]) <= 1e-10 * abs(E3["F_tot"])
+
+
+def test_serving_results_are_the_same_alone_and_in_the_mix():
+    stream = inputs.config_serve(count=4, seed=12, n_range=(8, 24), rho_range=(0.5, 4.0),
+                                 T_range=(2.0e4, 1.0e6), grid_hi=40)
+    precs = ["mixed", "fp64", "mixed", "fp64"]
+
+    def run(slots):
+        with ofdft.Server(max_slots=slots) as s:
+            ids = [s.submit(d["L"], d["grid"], d["ions"], d["Z"], d["T"], "vt84f", p, md_steps=2,
+                            dt_fs=0.2, vel=d["vel"]) for (_, d), p in zip(stream, precs)]
+            s.drain(timeout_s=600)
+            res = [s.poll(i) for i in ids]
+            return res, s.peaks()
+
+    alone, (_, peak1) = run(1)
+    mix, (_, peak4) = run(4)
+    assert peak1 == 1 and peak4 > 1
+    for a, m in zip(alone, mix):
+        assert a["status"] == 0 and m["status"] == 0 and m["steps_done"] == 2
+        assert m["E"]["F_tot"] == a["E"]["F_tot"]
+        assert m["P_mean"] == a["P_mean"]
+        assert m["evaluations"] == a["evaluations"]

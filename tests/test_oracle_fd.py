@@ -246,6 +246,19 @@ def test_enhancement_factors_match_printed_constants():
             assert (Fp - Fm) / (2 * hs) == pytest.approx(d, rel=1e-7, abs=1e-9)
 
 
+def test_pz81_branches_meet_at_rs_1():
+    """The two PZ81 correlation branches meet with equal eps_c and v_c at
+    r_s = 1, and the derived C, D round to the published 0.0020, -0.0116."""
+    assert round(O.PZ["C"], 4) == 0.0020 and round(O.PZ["D"], 4) == -0.0116
+    n1 = 3.0 / (4.0 * math.pi)                       # r_s = 1
+    e_lo, v_lo = O.pz81(np.array([n1 * (1 + 1e-12)]))  # r_s just below 1: log branch
+    e_hi, v_hi = O.pz81(np.array([n1 * (1 - 1e-12)]))  # just above: Pade branch
+    assert abs(e_lo[0] - e_hi[0]) < 1e-12 and abs(v_lo[0] - v_hi[0]) < 1e-11
+    # Pade value at r_s = 1 plus exchange, written out
+    ex = -0.4581652932831429
+    assert e_hi[0] == pytest.approx(ex - 0.1423 / (1 + 1.0529 + 0.3334), abs=1e-12)
+
+
 def test_pz81_exchange_and_potential():
     n = np.array([1e-3, 0.05, 0.0885, 0.2387, 0.4, 3.0])
     eps, v = O.pz81(n)

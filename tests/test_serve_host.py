@@ -1,0 +1,71 @@
+"""Host logic of the serving loop (ofdft_serve_*) in dry-run mode: admission
+in arrival order while a slot is free and the footprint fits the budget,
+budget and slot limits never exceeded, oversize requests refused.  No GPU
+work runs (each request only sleeps)."""
+import numpy as np
+import pytest
+
+from paper_1406_0835_gb300 import ofdft
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _req(server, grid, nat=8):
+    ions = np.random.default_rng(nat).uniform(0, 5.0, (nat, 3))
+    return server.submit((5.0, 5.0, 5.0), grid, ions, np.ones(nat), 1e5, "vt84f", "fp64", md_steps=1)
+
+
+def test_footprint_grows_with_grid_and_precision():
+    a = ofdft.ofdft_footprint((32, 32, 32), 8, "fp64")
+    b = ofdft.ofdft_footprint((64, 64, 64), 8, "fp64")
+    c = ofdft.ofdft_footprint((64, 64, 64), 8, "mixed")
+    assert 0 < a < b < c
+    # FP64 fields: at least nine real fields and four half spectra of N doubles
+    assert b > (9 + 4) * 64 ** 3 * 8
+    assert ofdft.ofdft_footprint((30, 32, 32), 8, "fp64") > 0      # 30 = 2 3 5
+    with pytest.raises(ofdft.OfdftError):
+        ofdft.ofdft_footprint((31, 32, 32), 8, "fp64")
+
+
+def test_admission_order_budget_and_slots():
+    small = ofdft.ofdft_footprint((32, 32, 32), 8, "fp64")
+    big = ofdft.ofdft_footprint((64, 64, 64), 8, "fp64")
+    budget = big + 1.5 * small          # the big one and one small, never two small beside it
+    with ofdft.Server(max_slots=3, hbm_budget_bytes=budget, dry_run_ms=60) as s:
+        ids = [_req(s, (64, 64, 64)), _req(s, (32, 32, 32)), _req(s, (32, 32, 32)),
+               _req(s, (32, 32, 32)), _req(s, (64, 64, 64))]
+        assert s.poll(ids[-1]) is None or s.poll(ids[-1])["status"] == 0
+        s.drain(timeout_s=30.0)
+        res = [s.poll(i) for i in ids]
+        peak_bytes, peak_running = s.peaks()
+    assert all(r["status"] == 0 and r["steps_done"] == 1 for r in res)
+    assert peak_bytes <= budget
+    assert 2 <= peak_running <= 3                  # requests overlapped, never beyond the slots
+    admits = [r["t_admit"] for r in res]
+    assert admits == sorted(admits)                # first come, first admitted
+    for r in res:
+        assert r["t_submit"] <= r["t_admit"] < r["t_done"]
+    # the last big request had to wait for the memory the others held
+    assert res[4]["t_admit"] >= max(r["t_done"] for r in res[:3]) - 1e-3
+
+
+def test_oversize_and_bad_requests_are_refused():
+    small = ofdft.ofdft_footprint((32, 32, 32), 8, "fp64")
+    with ofdft.Server(max_slots=1, hbm_budget_bytes=2 * small, dry_run_ms=1) as s:
+        with pytest.raises(ofdft.OfdftError) as e:
+            _req(s, (128, 128, 128))
+        assert e.value.status == -2
+        with pytest.raises(ofdft.OfdftError) as e:
+            _req(s, (33, 32, 32))
+        assert e.value.status == -1
+        with pytest.raises(ofdft.OfdftError):
+            s.poll(12345)                          # never submitted
+
+
+def test_dry_run_needs_a_budget():
+    with pytest.raises(ofdft.OfdftError):
+        ofdft.Server(max_slots=1, hbm_budget_bytes=0.0, dry_run_ms=1)
