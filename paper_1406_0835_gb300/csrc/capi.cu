@@ -609,6 +609,9 @@ ofdft_status write_config(ofdft_ctx *c, int k, double gtol, int maxit, int stagn
     CgState *h = c->cfg_h[k];
     memset(h, 0, sizeof(CgState));
     h->gtol = gtol;
+    // the FP32 stage of a mixed minimisation hands over to FP64 once
+    // ||g|| < 1e-5 (or earlier, when it stalls at the single-precision floor)
+    h->switch_g = stagnate ? std::max(1e-5, 10.0 * gtol) : 0.0;
     h->dV = c->g.dV;
     h->ls_tol = 0.1;
     h->theta0 = 0.05;

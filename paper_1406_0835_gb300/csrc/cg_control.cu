@@ -78,6 +78,9 @@ __global__ void k_ctl_grad(CgState *s, int first, cudaGraphConditionalHandle out
             s->done = 1;
         } else if (s->it >= s->maxit) {
             s->done = 1;
+        } else if (s->stagnate && s->gnorm < s->switch_g) {
+            s->status = kCgStagnated;
+            s->done = 1;
         } else if (s->stagnate) {
             if (s->gnorm < 0.9 * s->best_g) {
                 s->best_g = s->gnorm;

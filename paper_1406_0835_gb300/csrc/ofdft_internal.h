@@ -102,6 +102,7 @@ FuncParams functional_params(int functional);
 struct CgState {
     // configuration (written by the host before a minimisation)
     double gtol, dV, ls_tol, theta0, Ne;
+    double switch_g;   // stagnate mode: also stop once ||g|| < switch_g (0: off)
     int maxit, max_ls, stagnate;
     int pad0;
     // reduction outputs

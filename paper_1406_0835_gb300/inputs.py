@@ -77,6 +77,9 @@ def hydrogen(n_atoms, rho_gcc, T_kelvin, grid, seed, functional,
     """One synthetic hydrogen workload as a plain dict."""
     L = cell_edge(n_atoms, rho_gcc)
     g = (grid, grid, grid) if np.isscalar(grid) else tuple(grid)
+    spacing = L / n_atoms ** (1.0 / 3.0)
+    if min_dist > 0.6 * spacing:          # very dense cells: keep the rejection sampler feasible
+        min_dist = 0.5 * spacing
     d = dict(L=(L, L, L), grid=g, ions=random_positions(n_atoms, L, seed, min_dist),
              Z=np.ones(n_atoms), T=float(T_kelvin), functional=functional,
              rho=rho_gcc, n_atoms=n_atoms, masses=np.full(n_atoms, M_H_AMU * AMU_ME))

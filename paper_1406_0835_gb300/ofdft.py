@@ -19,6 +19,12 @@ STATUS = {0: "OFDFT_OK", -1: "OFDFT_EINVAL", -2: "OFDFT_ENOMEM", -3: "OFDFT_ENOC
 
 _P = ctypes.POINTER(ctypes.c_double)
 
+# Gradient tolerance of the batched and serving mixed-precision forms: their
+# results then stay within 1e-6 Ha/atom (free energy), 1e-4 Ha/bohr (forces)
+# and 1e-3 relative (pressure) of the FP64 path at gtol 1e-8, with margin
+# (tests/test_gpu_mixed.py checks it at 10 kK, 250 kK and 4 MK).
+MIXED_FORM_GTOL = 1e-6
+
 
 class Params(ctypes.Structure):
     _fields_ = [("xc", ctypes.c_int), ("rc", ctypes.c_double), ("precision", ctypes.c_int),

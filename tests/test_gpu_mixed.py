@@ -23,15 +23,19 @@ def built():
 
 
 @pytest.mark.parametrize("T", [1.0e4, 2.5e5, 4.0e6])
-def test_mixed_precision_against_fp64(T):
+@pytest.mark.parametrize("gtol", [1e-8, ofdft.MIXED_FORM_GTOL])
+def test_mixed_precision_against_fp64(T, gtol):
+    """The mixed form at the plain tolerance and at the looser one the batched
+    and serving forms use: both meet the stated per-result tolerances."""
     d = inputs.config_mixed(T)
     nat = len(d["Z"])
     res = {}
     for prec in ("fp64", "mixed"):
         with ofdft.Context(d["L"], d["grid"], d["ions"], d["Z"], T, "vt84f", precision=prec) as ctx:
-            E, st = ctx.minimize(gtol=1e-8, maxit=20000, raise_on_noconv=False)
-            if prec == "fp64":
-                assert st["status"] == 0, st
+            E, st = ctx.minimize(gtol=1e-8 if prec == "fp64" else gtol, maxit=20000, raise_on_noconv=False)
+            assert st["status"] == 0, st
+            if prec == "mixed":
+                assert st["evaluations_lo"] > 0
             F, P = ctx.forces()
             res[prec] = (E, F, P, ctx.density())
     E64, F64, P64, n64 = res["fp64"]
