@@ -148,24 +148,6 @@ bool smooth_even(int n)
     return m == 1;
 }
 
-FftAxis make_axis(int n, const void *tw)
-{
-    FftAxis a{};
-    a.n = n;
-    int m = n, ns = 1, k = 0;
-    for (int r : {8, 4, 2, 3, 5}) {
-        while (m % r == 0) {
-            a.rad[k] = r;
-            a.ns[k] = ns;
-            ns *= r;
-            m /= r;
-            ++k;
-        }
-    }
-    a.nst = k;
-    a.tw = tw;
-    return a;
-}
 
 template <typename T> ofdft_status upload_twiddles(ofdft_ctx *c, FieldSet &f, int axis, int n)
 {
@@ -177,7 +159,7 @@ template <typename T> ofdft_status upload_twiddles(ofdft_ctx *c, FieldSet &f, in
     }
     CK(cudaMallocAsync((void **)&f.tw[axis], n * sizeof(cplx<T>), c->st));
     CK(cudaMemcpyAsync(f.tw[axis], w.data(), n * sizeof(cplx<T>), cudaMemcpyHostToDevice, c->st));
-    f.ax[axis] = make_axis(n, f.tw[axis]);
+    f.ax[axis] = fft_axis(n, f.tw[axis]);
     return OFDFT_OK;
 }
 
@@ -245,11 +227,12 @@ EvalScalars unpack_sums(const double *h, bool fttf)
 int eval_kernel_count(const ofdft_ctx *c) { return c->fp.kind == 0 ? 7 : 12; }
 
 // Enqueue one energy + potential evaluation at ph (or, with phi0 and dh, at the
-// trial phi0 cos + dh sin written into ph; angles from csd if given).  Sums go
+// trial phi0 cos + dh sin written into ph; angles from csd (two T values in
+// device memory) if given).  Sums go
 // to sums[0..17].  No synchronisation.
 template <typename T>
 ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const T *dh, double cth,
-                          double sth, const double *csd, T *vout, bool keep_nG, double *sums)
+                          double sth, const void *csd, T *vout, bool keep_nG, double *sums)
 {
     const GridInfo &g = f.gt;
     const FftAxis &ax = f.ax[0], &ay = f.ax[1], &az = f.ax[2];
@@ -491,7 +474,8 @@ template <typename T>
 ofdft_status enqueue_trial(ofdft_ctx *c, FieldSet &f, cudaGraphConditionalHandle ls, int use_cond)
 {
     CgState *s = f.cs;
-    ofdft_status r = enqueue_eval<T>(c, f, (T *)f.phit, (const T *)f.phi, (const T *)f.dhat, 1.0, 0.0, s->cs,
+    const void *cs = sizeof(T) == 8 ? (const void *)s->cs : (const void *)s->csf;   // angle in T
+    ofdft_status r = enqueue_eval<T>(c, f, (T *)f.phit, (const T *)f.phi, (const T *)f.dhat, 1.0, 0.0, cs,
                                      (T *)f.vt, false, s->ev);
     if (r != OFDFT_OK) return r;
     launch_ctl_ls(s, ls, use_cond, c->st);

@@ -74,23 +74,6 @@ bool edge_ok(int n)
     return n == 1;
 }
 
-FftAxis axis_plan(int n, const void *tw)
-{
-    FftAxis a{};
-    a.n = n;
-    int m = n, ns = 1, k = 0;
-    for (int r : {8, 4, 2, 3, 5})
-        while (m % r == 0) {
-            a.rad[k] = r;
-            a.ns[k] = ns;
-            ns *= r;
-            m /= r;
-            ++k;
-        }
-    a.nst = k;
-    a.tw = tw;
-    return a;
-}
 
 // One-time set-up on the current device: scratch address, table, smem limits.
 ofdft_status device_setup(int dev, unsigned char **base)
@@ -227,8 +210,8 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
         }
     double2 *twd = (double2 *)(base + kOffTw);
     SCK(cudaMemcpyAsync(twd, tw, sizeof(tw), cudaMemcpyHostToDevice, st), "twiddle upload failed");
-    FftAxis ax = axis_plan(g.nx, twd), ay = axis_plan(g.ny, twd + kSMaxEdge),
-            az = axis_plan(g.nz, twd + 2 * kSMaxEdge);
+    FftAxis ax = fft_axis(g.nx, twd), ay = fft_axis(g.ny, twd + kSMaxEdge),
+            az = fft_axis(g.nz, twd + 2 * kSMaxEdge);
     // ions -> phases -> v_ext(G)
     double *Rd = (double *)(base + kOffIons), *Zd = (double *)(base + kOffZ);
     SCK(cudaMemcpyAsync(Rd, ions, 3 * nat * sizeof(double), cudaMemcpyHostToDevice, st), "ion upload failed");

@@ -125,6 +125,8 @@ __global__ void k_ctl_dhat(CgState *s, cudaGraphConditionalHandle ls, int use)
     s->accepted = 0;
     s->cs[0] = cos(s->th);
     s->cs[1] = sin(s->th);
+    s->csf[0] = (float)s->cs[0];
+    s->csf[1] = (float)s->cs[1];
     s->ls_active = 1;
     set_cond(ls, use, 1u);
 }
@@ -192,6 +194,8 @@ __global__ void k_ctl_ls(CgState *s, cudaGraphConditionalHandle ls, int use)
     } else {
         s->cs[0] = cos(s->th);
         s->cs[1] = sin(s->th);
+        s->csf[0] = (float)s->cs[0];
+        s->csf[1] = (float)s->cs[1];
     }
     set_cond(ls, use, s->ls_active ? 1u : 0u);
 }

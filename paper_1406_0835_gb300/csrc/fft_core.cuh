@@ -155,17 +155,18 @@ __device__ C *fft_lines(C *a, C *b, const FftAxis &ax, int nl, int lstride, int 
 }
 
 // Per-thread accumulator type of the reductions: FP64 fields accumulate in
-// FP64; FP32 fields accumulate per thread and per warp in FP32 (a few hundred
-// terms) and across warps and blocks in FP64, which keeps the FP64 pipe out
-// of the single-precision kernels.
+// FP64; FP32 fields accumulate within a block in FP32 (a few thousand terms)
+// and across blocks in FP64, which keeps the FP64 pipe out of the
+// single-precision kernels.
 template <typename T> struct AccT { typedef double type; };
 template <> struct AccT<float> { typedef float type; };
 
 // Deterministic block sum of NQ values; thread 0 returns the totals in tot
-// (FP64).  Warp sums in the accumulator type, the cross-warp sum in FP64.
+// (FP64).  Warp and cross-warp sums in the accumulator type; the block totals
+// are added in FP64 by the second reduction stage.
 template <int NQ, typename A> __device__ __forceinline__ void block_sum(A *v, double *tot)
 {
-    __shared__ double red[32][NQ];
+    __shared__ A red[32][NQ];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -176,14 +177,14 @@ template <int NQ, typename A> __device__ __forceinline__ void block_sum(A *v, do
     }
     if (lane == 0)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) red[wid][q] = (double)v[q];
+        for (int q = 0; q < NQ; ++q) red[wid][q] = v[q];
     __syncthreads();
     if (threadIdx.x == 0) {
         const int nw = (blockDim.x + 31) >> 5;
         for (int q = 0; q < NQ; ++q) {
-            double s = 0.0;
+            A s = A(0);
             for (int w = 0; w < nw; ++w) s += red[w][q];
-            tot[q] = s;
+            tot[q] = (double)s;
         }
     }
     __syncthreads();

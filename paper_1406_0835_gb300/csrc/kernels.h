@@ -8,7 +8,7 @@ namespace ofdft {
 // ---- grid fields (kernels_fields.cu)
 template <typename T>
 void launch_zfwd(const GridInfo &g, const FftAxis &az, int mode, const T *in, const T *phi,
-                 const T *dhat, T c, T s, const double *cs, T *phit, cplx<T> *out, cudaStream_t st);
+                 const T *dhat, T c, T s, const void *cs, T *phit, cplx<T> *out, cudaStream_t st);
 template <typename T>
 int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, cplx<T> *g2,
                 const T *phit, T temp, const FuncParams &fp, const T *tab, int xc, T *vpart,
@@ -16,7 +16,7 @@ int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, 
 template <typename T>
 int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T> *dspec,
                   const T *vpart, const T *phit, const T *phi, const T *dhat, T c, T s,
-                  const double *cs, T temp, const FuncParams &fp, const T *tab, int xc, T *vout,
+                  const void *cs, T temp, const FuncParams &fp, const T *tab, int xc, T *vout,
                   double *part, cudaStream_t st);
 template <typename T>
 void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data, int nfields,

@@ -50,12 +50,12 @@ template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ld
 template <typename T, int MODE>
 __global__ void k_zfwd(GridInfo g, FftAxis az, int P, const T *__restrict__ in,
                        const T *__restrict__ phi, const T *__restrict__ dhat, T c, T s,
-                       const double *__restrict__ cs, T *__restrict__ phit,
+                       const void *__restrict__ cs, T *__restrict__ phit,
                        cplx<T> *__restrict__ out)
 {
-    if (MODE == 2 && cs != nullptr) {   // rotation angle from the device CG state
-        c = (T)cs[0];
-        s = (T)cs[1];
+    if (MODE == 2 && cs != nullptr) {   // rotation angle (two T) from the device CG state
+        c = reinterpret_cast<const T *>(cs)[0];
+        s = reinterpret_cast<const T *>(cs)[1];
     }
     typedef cplx<T> C;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -208,13 +208,13 @@ template <typename T, bool FTTF>
 __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const cplx<T> *__restrict__ dspec,
                          const T *__restrict__ vpart, const T *__restrict__ phit,
                          const T *__restrict__ phi, const T *__restrict__ dhat, T c, T s,
-                         const double *__restrict__ cs, T temp, FuncParams fp,
+                         const void *__restrict__ cs, T temp, FuncParams fp,
                          const T *__restrict__ tab, int xc, T *__restrict__ vout,
                          double *__restrict__ part)
 {
     if (cs != nullptr) {
-        c = (T)cs[0];
-        s = (T)cs[1];
+        c = reinterpret_cast<const T *>(cs)[0];
+        s = reinterpret_cast<const T *>(cs)[1];
     }
     typedef cplx<T> C;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -346,8 +346,9 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, cplx<T> *__restrict__ nspec,
     __syncthreads();
     C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, g.tk, true);
     typedef typename AccT<T>::type Ac;
-    const Ac bx = Ac(g.bx), by = Ac(g.by), bz = Ac(g.bz), hr = Ac(0.5 * g.rc * g.rc);
-    const T invN = T(1.0 / (double)g.N);
+    const Ac bx = gsel<Ac>(g.bx, g.bxf), by = gsel<Ac>(g.by, g.byf), bz = gsel<Ac>(g.bz, g.bzf);
+    const Ac hr = gsel<Ac>(g.hr, g.hrf);
+    const T invN = gsel<T>(g.invN, g.invNf);
     Ac acc[3] = {0, 0, 0};     // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i / g.tk, c = i - r * g.tk;
@@ -408,9 +409,10 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, cplx<T> *__restrict__ spec,
     __syncthreads();
     C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, g.tk, true);
     typedef typename AccT<T>::type Ac;
-    const Ac bx = Ac(g.bx), by = Ac(g.by), bz = Ac(g.bz), hr = Ac(0.5 * g.rc * g.rc);
-    const Ac fourpi = Ac(12.566370614359172954);
-    const T invN = T(1.0 / (double)g.N);
+    const Ac bx = gsel<Ac>(g.bx, g.bxf), by = gsel<Ac>(g.by, g.byf), bz = gsel<Ac>(g.bz, g.bzf);
+    const Ac hr = gsel<Ac>(g.hr, g.hrf);
+    const Ac fourpi = gsel<Ac>(12.566370614359172954, 12.566370614359172954f);
+    const T invN = gsel<T>(g.invN, g.invNf);
     Ac acc[3] = {0, 0, 0};
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i / g.tk, c = i - r * g.tk;
@@ -461,9 +463,9 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const cplx<T> *__restrict__ nG,
     C *D = B + nx * g.tk;
     ColTile t = col_tile(g, true);
     typedef typename AccT<T>::type Ac;
-    const Ac bx = Ac(g.bx), by = Ac(g.by), bz = Ac(g.bz);
-    const Ac fourpi = Ac(12.566370614359172954);
-    const T invN = T(1.0 / (double)g.N);
+    const Ac bx = gsel<Ac>(g.bx, g.bxf), by = gsel<Ac>(g.by, g.byf), bz = gsel<Ac>(g.bz, g.bzf);
+    const Ac fourpi = gsel<Ac>(12.566370614359172954, 12.566370614359172954f);
+    const T invN = gsel<T>(g.invN, g.invNf);
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i / g.tk, c = i - r * g.tk;
         if (c >= t.ncol) continue;
@@ -519,7 +521,7 @@ int threads_for(int work)
 // ---------------------------------------------------------------- launchers
 template <typename T>
 void launch_zfwd(const GridInfo &g, const FftAxis &az, int mode, const T *in, const T *phi,
-                 const T *dhat, T c, T s, const double *cs, T *phit, cplx<T> *out, cudaStream_t st)
+                 const T *dhat, T c, T s, const void *cs, T *phit, cplx<T> *out, cudaStream_t st)
 {
     int P = zpairs_per_block(g);
     long long npairs = (long long)g.nx * g.ny / 2;
@@ -548,7 +550,7 @@ int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, 
 template <typename T>
 int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T> *dspec,
                   const T *vpart, const T *phit, const T *phi, const T *dhat, T c, T s,
-                  const double *cs, T temp, const FuncParams &fp, const T *tab, int xc, T *vout,
+                  const void *cs, T temp, const FuncParams &fp, const T *tab, int xc, T *vout,
                   double *part, cudaStream_t st)
 {
     int P = zpairs_per_block(g);
@@ -644,12 +646,12 @@ template <typename T> cudaError_t set_field_smem_limits(size_t bytes)
 
 #define OFDFT_INST(T)                                                                              \
     template void launch_zfwd<T>(const GridInfo &, const FftAxis &, int, const T *, const T *,     \
-                                 const T *, T, T, const double *, T *, cplx<T> *, cudaStream_t); \
+                                 const T *, T, T, const void *, T *, cplx<T> *, cudaStream_t); \
     template int launch_zgga<T>(const GridInfo &, const FftAxis &, cplx<T> *, cplx<T> *,           \
                                 cplx<T> *, const T *, T, const FuncParams &, const T *, int, T *, \
                                 double *, cudaStream_t);                                          \
     template int launch_zfinal<T>(const GridInfo &, const FftAxis &, bool, const cplx<T> *,        \
-                                  const T *, const T *, const T *, const T *, T, T, const double *, \
+                                  const T *, const T *, const T *, const T *, T, T, const void *,   \
                                   T, const FuncParams &, const T *, int, T *, double *,            \
                                   cudaStream_t);                                                  \
     template void launch_ypass<T>(const GridInfo &, const FftAxis &, bool, cplx<T> *, int,         \

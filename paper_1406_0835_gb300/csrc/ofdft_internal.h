@@ -39,6 +39,28 @@ template <typename C, bool INV> __host__ __device__ __forceinline__ C cmuli(C a)
     return INV ? cmk<C>(-a.y, a.x) : cmk<C>(a.y, -a.x);
 }
 
+// ------------------------------------------------- division by constants
+// Division by a fixed d (1 <= d < 2^16) of dividends 0 <= x < 2^16 with one
+// wide multiply: with m = ceil(2^32 / d), floor(x m / 2^32) = floor(x / d),
+// since the excess x (m d - 2^32) / (d 2^32) < x / 2^32 < 1 / d.
+struct FastDiv {
+    unsigned long long m;
+    int d;
+};
+
+inline FastDiv make_fastdiv(int d)
+{
+    FastDiv f;
+    f.d = d;
+    f.m = ((1ull << 32) + (unsigned long long)d - 1) / (unsigned long long)d;
+    return f;
+}
+
+__host__ __device__ __forceinline__ int fdiv(int x, const FastDiv &f)
+{
+    return (int)(((unsigned long long)(unsigned)x * f.m) >> 32);
+}
+
 // ------------------------------------------------------------ FFT plans
 constexpr int kMaxStages = 16;
 
@@ -49,8 +71,34 @@ struct FftAxis {
     int nst;
     int rad[kMaxStages];
     int ns[kMaxStages];      // product of the radices before each stage
+    int tws[kMaxStages];     // twiddle stride n / (ns * rad)
+    FastDiv nbd[kMaxStages]; // division by n / rad (butterflies per line)
+    FastDiv nsd[kMaxStages]; // division by ns
     const void *tw;          // cplx<T>[n]
 };
+
+// Stockham schedule of one axis: radix-8 stages first, then 4, 2, 3, 5.
+inline FftAxis fft_axis(int n, const void *tw)
+{
+    FftAxis a{};
+    a.n = n;
+    int m = n, ns = 1, k = 0;
+    for (int r : {8, 4, 2, 3, 5}) {
+        while (m % r == 0 && k < kMaxStages) {
+            a.rad[k] = r;
+            a.ns[k] = ns;
+            a.tws[k] = n / (ns * r);
+            a.nbd[k] = make_fastdiv(n / r);
+            a.nsd[k] = make_fastdiv(ns);
+            ns *= r;
+            m /= r;
+            ++k;
+        }
+    }
+    a.nst = k;
+    a.tw = tw;
+    return a;
+}
 
 // Geometry of the periodic orthorhombic grid, C order [ix][iy][iz], and of
 // the half spectrum [ix][iy][kz], kz = 0..nz/2.
@@ -60,10 +108,14 @@ struct GridInfo {
     double Lx, Ly, Lz, omega, dV;
     double rc;               // Gaussian local pseudopotential radius
     double bx, by, bz;       // reciprocal spacing 2 pi / L per axis
+    double invN, hr;         // 1 / N, rc^2 / 2
+    float bxf, byf, bzf, invNf, hrf;   // the same in FP32 (for the FP32 kernels)
+    FastDiv dnz, dK;         // division by nz and by K
     int zP;                  // z passes: line pairs per block (0: default rule)
     int tk;                  // y/x passes: half-spectrum columns per tile (4, 8 or 16)
 };
 
+// Derived quantities of a grid (call after setting sizes, cell and rc).
 inline void grid_reciprocal(GridInfo &g)
 {
     if (g.tk <= 0) g.tk = 8;
@@ -71,7 +123,21 @@ inline void grid_reciprocal(GridInfo &g)
     g.bx = tp / g.Lx;
     g.by = tp / g.Ly;
     g.bz = tp / g.Lz;
+    g.invN = 1.0 / (double)g.N;
+    g.hr = 0.5 * g.rc * g.rc;
+    g.bxf = (float)g.bx;
+    g.byf = (float)g.by;
+    g.bzf = (float)g.bz;
+    g.invNf = (float)g.invN;
+    g.hrf = (float)g.hr;
+    g.dnz = make_fastdiv(g.nz);
+    g.dK = make_fastdiv(g.K);
 }
+
+// The FP64 or FP32 copy of a grid constant, for kernels templated on A.
+template <typename A> __host__ __device__ __forceinline__ A gsel(double d, float f);
+template <> __host__ __device__ __forceinline__ double gsel<double>(double d, float) { return d; }
+template <> __host__ __device__ __forceinline__ float gsel<float>(double, float f) { return f; }
 
 // Tabulated temperature functions xi, zeta, A, B of t (see tfunc_table.cpp).
 constexpr int kTfDeg = 10;                 // polynomial degree per panel
@@ -113,7 +179,8 @@ struct CgState {
     double rn[1];      // sum phi^2
     // iteration state
     double mu, gg, ggprev, gnorm, beta, c1, c2, D0, theta_prev, scale;
-    double cs[2];      // cos, sin of the trial angle (read by the evaluation kernels)
+    double cs[2];      // cos, sin of the trial angle (read by the FP64 evaluation kernels)
+    float csf[2];      // the same for the FP32 kernels
     double th, lo, Dlo, hi, Dhi, pa, Da;
     double best_g;
     double c12r[3];    // c1, c2, restart (read by the direction kernel)
