@@ -156,17 +156,30 @@ def fft_flops(n):
     return 5.0 * n * math.log2(n)
 
 
+# Pointwise FP64 work per grid point of the GGA functional + PZ81 (table
+# polynomials of xi, zeta, A, B and their t-derivatives, two enhancement
+# factors with their s^2-derivatives, n^(-1/3), PZ81, W and the energy
+# densities): about 150-250 flop per point; 200 is used.
+POINTWISE_FLOP = 200.0
+# DRAM bytes per grid point of one k_zgga<double> launch, from the ncu capture
+# summarised in profiles/k_zgga_f64_128.md (83.4 MB at 128^3).
+ZGGA_F64_TRAFFIC_PER_POINT = 83.4e6 / 128 ** 3
+
+
 def kernel_model(name, g):
     """Algorithmic FLOPs and HBM bytes of one launch (FP64) of a timed kernel
-    class: FFT flops 5 n log2 n per complex line, 2.5 n log2 n per real line;
-    bytes = fields read + written once."""
+    class: FFT flops 5 n log2 n per complex line, 2.5 n log2 n per real line,
+    plus the pointwise functional; bytes = fields read + written once."""
     nx, ny, nz = g
     K = nz // 2 + 1
     N = nx * ny * nz
     NH = nx * ny * K
     if name == "zgga":
-        flops = 6 * (nx * ny / 2) * fft_flops(nz)          # 3 C2R + 3 R2C, pair packed
+        flops = 6 * (nx * ny / 2) * fft_flops(nz) + POINTWISE_FLOP * N   # 3 C2R + 3 R2C, pair packed
         byts = 16 * NH * 3 * 2 + 8 * N * 2                 # grad spectra in, W spectra out, phi in, vpart out
+    elif name == "zfinal":
+        flops = (nx * ny / 2) * fft_flops(nz) + POINTWISE_FLOP * N
+        byts = 16 * NH + 8 * N * 3
     elif name == "ypass":
         flops = nx * K * fft_flops(ny)
         byts = 16 * NH * 2
@@ -233,14 +246,19 @@ def roofline_entry(dominant, grid, kms, kcount, clk, peaks):
     # FP64 FMA issue: 2 per SM per clock (GB300); 152 SMs
     fp64_peak = 152 * 2 * 2 * (sm_mhz * 1e6) / 1e12
     ok = kcount > 0
+    npts = grid[0] * grid[1] * grid[2]
+    traffic = ZGGA_F64_TRAFFIC_PER_POINT * npts if dominant == "zgga" else None
     return {"bound": "alu", "kernel": dominant, "achieved": flops / avg_s / 1e12 if ok else None,
             "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
             "frac": (flops / avg_s / 1e12) / fp64_peak if ok else None,
-            "traffic": None, "launches": kcount, "avg_launch_us": avg_s * 1e6,
-            "hbm_gbs": byts / avg_s / 1e9 if ok else None,
+            "traffic": traffic, "launches": kcount, "avg_launch_us": avg_s * 1e6,
+            "algorithmic_bytes": byts, "hbm_gbs": byts / avg_s / 1e9 if ok else None,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
-            "peak_note": "FP64 peak derived from 152 SMs x 2 DFMA/clk x median SM clock; "
-                         "kernel time from events around every launch in one extra host-driven step"}
+            "fp64_pipe_active_pct_ncu": 86.4 if dominant == "zgga" else None,
+            "peak_note": "FP64 peak derived from 152 SMs x 2 DFMA/clk x median SM clock (1.19 TFLOP/s "
+                         "measured on GB300); achieved = FFT flops + 200 flop/pt pointwise over the mean "
+                         "event-timed launch in one extra host-driven step; traffic = ncu DRAM bytes "
+                         "at 128^3 scaled by the point count"}
 
 
 def time_dominant(ctx, ofdft, dominant, stream, work):
