@@ -276,12 +276,24 @@ def time_dominant(ctx, ofdft, dominant, stream, work):
 
 
 def max_over_ranks(x, world):
+    """Largest x over the ranks (the slowest rank's time).  Replicas exchange
+    only this scalar, on the process group's device (GPU for NCCL, host for
+    gloo)."""
     if world == 1:
         return x
     import torch
-    tt = torch.tensor([x], device="cuda", dtype=torch.float64)
-    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
     return float(tt.item())
+
+
+def replica_throughput(units_per_rank, seconds, world):
+    """Whole-job throughput of independent replicas (weak scaling): the units
+    every rank processed over the slowest rank's time.  Returns (value, time)."""
+    t = max_over_ranks(seconds, world)
+    return world * units_per_rank / t, t
 
 
 def run_ours(args, rank, world):
@@ -335,8 +347,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = ctx.kernel_launches() - launches0
-    t_total = max_over_ranks(sum(times), world)
-    value = world * args.steps / t_total
+    value, t_total = replica_throughput(args.steps, sum(times), world)
     kms, kcount = time_dominant(ctx, ofdft, dominant, stream, lambda: ctx.md_step(0.2, mdT, nsteps=1))
     ctx.close()
     # End to end through the C ABI with host position and velocity buffers
