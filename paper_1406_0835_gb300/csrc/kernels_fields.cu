@@ -173,7 +173,7 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, cplx<T> *__restrict__ g0,
         T gg = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
         FsOut<T> o = fs_point<T>(fp, tab, temp, n, gg);
         T eps = T(0), vxc = T(0);
-        if (xc) pz81_point<T>(n, eps, vxc);
+        if (xc) pz81_point<T>(n, o.y13, eps, vxc);
         vpart[rbase + i] = o.dfdn + vxc;
         acc[0] += (A)o.f;
         acc[1] += (A)o.ts;
@@ -241,7 +241,7 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const cplx<T> *__restric
         if (FTTF) {
             FsOut<T> o = fs_point<T>(fp, tab, temp, n, T(0));
             T eps = T(0), vxc = T(0);
-            if (xc) pz81_point<T>(n, eps, vxc);
+            if (xc) pz81_point<T>(n, o.y13, eps, vxc);
             v = o.dfdn + vxc + dr;
             acc[0] += (Ac)o.f;
             acc[1] += (Ac)o.ts;

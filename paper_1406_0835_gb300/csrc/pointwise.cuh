@@ -186,6 +186,7 @@ template <typename T> struct FsOut {
     T ts;     // tau0 zeta F_sigma (entropic density T s)
     T dfdn;   // partial f / partial n (without the divergence term)
     T wc;     // W = wc * grad n
+    T y13;    // n^{-1/3} (reused by the XC term)
 };
 
 // Constants: C_TF = (3/10)(3 pi^2)^{2/3}; (3 pi^2)^{2/3}; cs = 1/(4 (3 pi^2)^{2/3}).
@@ -198,6 +199,7 @@ OF_HD FsOut<T> fs_point(const FuncParams &fp, const T *__restrict__ tab, T temp,
 {
     FsOut<T> o;
     T y = inv_cbrt(n);                                  // n^{-1/3}
+    o.y13 = y;
     T y2 = y * y;
     T c13 = n * y2;                                     // n^{1/3}
     T n23 = c13 * c13;
@@ -248,10 +250,10 @@ constexpr double kPzDen = 1.0 + 1.0529 + 0.3334;
 constexpr double kPzD = -0.1423 / kPzDen + 0.048;                                // B + D = eps_pade(1)
 constexpr double kPzC = 0.1423 * (0.5 * 1.0529 + 0.3334) / (kPzDen * kPzDen) - 0.0311 - kPzD;
 
+// y = n^{-1/3} as computed by the caller.
 template <typename T>
-OF_HD void pz81_point(T n, T &eps, T &v)
+OF_HD void pz81_point(T n, T y, T &eps, T &v)
 {
-    T y = inv_cbrt(n);                                 // n^{-1/3}
     T rs = T(0.62035049089940001667) * y;              // (3/(4 pi n))^{1/3}
     T ex = T(-0.73855876638202240587) * n * y * y;     // -(3/4)(3/pi)^{1/3} n^{1/3}
     T ec, vc;
@@ -268,6 +270,12 @@ OF_HD void pz81_point(T n, T &eps, T &v)
     }
     eps = ex + ec;
     v = T(4.0 / 3.0) * ex + vc;
+}
+
+template <typename T>
+OF_HD void pz81_point(T n, T &eps, T &v)
+{
+    pz81_point<T>(n, inv_cbrt(n), eps, v);
 }
 
 }  // namespace ofdft
