@@ -132,6 +132,27 @@ def test_md_steps_match_oracle():
         np.testing.assert_allclose(out2["pos"], st.R, rtol=0, atol=1e-10)
 
 
+@pytest.mark.parametrize("fn", ["fttf", "vt84f"])
+@pytest.mark.parametrize("grid,L,nat", [
+    ((512, 8, 8), (40.0, 3.0, 3.0), 3),      # longest supported axis (8 x 8 x 8 stages)
+    ((10, 12, 18), (3.0, 3.5, 4.5), 1),      # radix-5 and radix-3 axes, orthorhombic cell, one ion
+    ((8, 8, 8), (2.2, 2.2, 2.2), 2),         # smallest grid
+])
+def test_edge_shapes_match_oracle(fn, grid, L, nat):
+    """Edge shapes: the maximum axis length, radices 3 and 5 on an
+    orthorhombic cell, the minimum grid, one and two ions."""
+    rng = np.random.default_rng(sum(grid) + nat)
+    ions = rng.uniform(0, 1, (nat, 3)) * np.asarray(L)
+    Z = np.ones(nat)
+    so = O.System(L, grid, ions, Z, 5.0e4, fn)
+    phi = so.uniform_phi() * (1.0 + 0.1 * rng.standard_normal(grid))
+    ev = O.evaluate(so, phi)
+    with ofdft.Context(L, grid, ions, Z, 5.0e4, fn) as ctx:
+        E, v = ctx.energy_potential(phi)
+        check_energy(E, ev)
+        assert np.max(np.abs(v - ev["v"])) <= 1e-9 * np.max(np.abs(ev["v"]))
+
+
 def test_invalid_inputs_are_rejected():
     cfg = inputs.config_single_point()
     with pytest.raises(ofdft.OfdftError):
