@@ -913,7 +913,10 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune;   // -> (zP, tk)
+struct Tuned {
+    int zP, tk, zth, xth;
+};
+std::map<TuneKey, Tuned> g_tune;
 
 // Mean time of `reps` evaluations of field set f at its current phi.
 template <typename T> ofdft_status time_evals(ofdft_ctx *c, FieldSet &f, int reps, float &ms)
@@ -946,8 +949,10 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            f.gt.zP = it->second.first;
-            f.gt.tk = it->second.second;
+            f.gt.zP = it->second.zP;
+            f.gt.tk = it->second.tk;
+            f.gt.zth = it->second.zth;
+            f.gt.xth = it->second.xth;
             if (f.graph) cudaGraphExecDestroy(f.graph);
             f.graph = nullptr;
             return OFDFT_OK;
@@ -988,11 +993,32 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
             best = g;
         }
     }
+    // threads per block of the z passes, then of the y/x passes (the register
+    // budget of the FP64 kernels allows 256 at most)
+    const int thmax = sizeof(T) == 8 ? 256 : 512;
+    for (int pass = 0; pass < 2; ++pass) {
+        best_ms = 1e30f;
+        GridInfo base2 = best;
+        for (int th : {128, 256, 512}) {
+            if (th > thmax) continue;
+            GridInfo g = base2;
+            if (pass == 0) g.zth = th;
+            else g.xth = th;
+            f.gt = g;
+            float ms;
+            ofdft_status r = time_evals<T>(c, f, reps, ms);
+            if (r != OFDFT_OK) return r;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = g;
+            }
+        }
+    }
     f.gt = best;
     if (f.graph) cudaGraphExecDestroy(f.graph);
     f.graph = nullptr;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = std::make_pair(best.zP, best.tk);
+    g_tune[key] = Tuned{best.zP, best.tk, best.zth, best.xth};
     return OFDFT_OK;
 }
 

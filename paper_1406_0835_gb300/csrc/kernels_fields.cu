@@ -527,7 +527,7 @@ void launch_zfwd(const GridInfo &g, const FftAxis &az, int mode, const T *in, co
     long long npairs = (long long)g.nx * g.ny / 2;
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 2 * (size_t)P * g.nz * sizeof(cplx<T>);
-    int th = threads_for(P * g.nz);
+    int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
     if (mode == 0) k_zfwd<T, 0><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);
     else if (mode == 1) k_zfwd<T, 1><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);
     else k_zfwd<T, 2><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);
@@ -542,7 +542,7 @@ int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, 
     long long npairs = (long long)g.nx * g.ny / 2;
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 4 * (size_t)P * g.nz * sizeof(cplx<T>);
-    int th = threads_for(P * g.nz);
+    int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
     k_zgga<T><<<blocks, th, sm, st>>>(g, az, P, g0, g1, g2, phit, temp, fp, tab, xc, vpart, part);
     return blocks;
 }
@@ -557,7 +557,7 @@ int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T>
     long long npairs = (long long)g.nx * g.ny / 2;
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 2 * (size_t)P * g.nz * sizeof(cplx<T>);
-    int th = threads_for(P * g.nz);
+    int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
     if (fttf)
         k_zfinal<T, true><<<blocks, th, sm, st>>>(g, az, P, dspec, vpart, phit, phi, dhat, c, s,
                                                   cs, temp, fp, tab, xc, vout, part);
@@ -574,7 +574,7 @@ void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data,
     int ntk = (g.K + g.tk - 1) / g.tk;
     dim3 grid(g.nx * ntk, nfields);
     size_t sm = 2 * (size_t)g.ny * g.tk * sizeof(cplx<T>);
-    int th = threads_for(g.ny * g.tk / 2);
+    int th = g.xth > 0 ? g.xth : threads_for(g.ny * g.tk / 2);
     if (inv) k_ypass<T, true><<<grid, th, sm, st>>>(g, ay, data, fstride);
     else k_ypass<T, false><<<grid, th, sm, st>>>(g, ay, data, fstride);
 }
@@ -586,7 +586,7 @@ int launch_xgrad(const GridInfo &g, const FftAxis &ax, cplx<T> *nspec, const cpl
     int ntk = (g.K + g.tk - 1) / g.tk;
     int blocks = g.ny * ntk;
     size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
-    int th = threads_for(g.nx * g.tk / 2);
+    int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
     k_xgrad<T><<<blocks, th, sm, st>>>(g, ax, nspec, vext, g0, g1, g2, part);
     return blocks;
 }
@@ -598,7 +598,7 @@ int launch_xhl(const GridInfo &g, const FftAxis &ax, cplx<T> *spec, const cplx<T
     int ntk = (g.K + g.tk - 1) / g.tk;
     int blocks = g.ny * ntk;
     size_t sm = 2 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
-    int th = threads_for(g.nx * g.tk / 2);
+    int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
     k_xhl<T><<<blocks, th, sm, st>>>(g, ax, spec, vext, nG_out, inverse, part);
     return blocks;
 }
@@ -610,7 +610,7 @@ void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const 
     int ntk = (g.K + g.tk - 1) / g.tk;
     int blocks = g.ny * ntk;
     size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
-    int th = threads_for(g.nx * g.tk / 2);
+    int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
     k_xdiv<T><<<blocks, th, sm, st>>>(g, ax, nG, vext, w0, w1, w2);
 }
 

@@ -113,6 +113,7 @@ struct GridInfo {
     FastDiv dnz, dK;         // division by nz and by K
     int zP;                  // z passes: line pairs per block (0: default rule)
     int tk;                  // y/x passes: half-spectrum columns per tile (4, 8 or 16)
+    int zth, xth;            // threads per block of the z and of the y/x passes (0: default rule)
 };
 
 // Derived quantities of a grid (call after setting sizes, cell and rc).
