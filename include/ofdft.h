@@ -61,6 +61,18 @@ typedef enum {
                          search, Ewald and forces; final energies in FP64 */
 } ofdft_precision;
 
+/* Arithmetic of the pointwise functional (f_s, its derivatives and PZ81,
+ * Eqs. (FGGA), (vftGGA), (vxc1)) on FP64 field sets.  The FFTs, reductions
+ * and CG stay in binary64 either way. */
+typedef enum {
+    OFDFT_PW_F32X2 = 0,  /* double-float pairs on the FP32 units (about 48
+                            significant bits; agrees with binary64 to a few
+                            parts in 1e14); points outside its range (n
+                            outside [1e-18, 1e18], s^2 > 1e10, t outside the
+                            tabulated [2^-20, 2^34)) use binary64 */
+    OFDFT_PW_F64 = 1     /* binary64 throughout */
+} ofdft_pointwise;
+
 typedef struct {
     int xc;           /* 1: Perdew-Zunger LDA XC (Sec. IV, used in Sec. VI); 0: none */
     double rc;        /* Gaussian local pseudopotential radius in bohr:
@@ -68,6 +80,7 @@ typedef struct {
     int precision;    /* ofdft_precision */
     int device;       /* CUDA device ordinal */
     void *stream;     /* cudaStream_t to run on, or NULL for a library stream */
+    int pointwise;    /* ofdft_pointwise (FP64 field sets only) */
 } ofdft_params;
 
 /* Energy partition (Sec. V C sample output) and pressure terms; hartree,
@@ -103,7 +116,8 @@ typedef struct {
     int maxit;          /* CG iteration cap per MD step */
 } ofdft_md_params;
 
-/* Fill *p with defaults: xc = 1, rc = 0.25, FP64, device 0, library stream. */
+/* Fill *p with defaults: xc = 1, rc = 0.25, FP64, device 0, library stream,
+ * double-float pointwise functional. */
 void ofdft_default_params(ofdft_params *p);
 
 /*
@@ -261,6 +275,24 @@ const char *ofdft_last_error(ofdft_ctx *ctx);
  * (Eq. (xizeta)), A = (h~ - t h~')/xi, B = t h~'/zeta (Eq. (s_s)).
  */
 ofdft_status ofdft_tfunc_eval(long long n, const double *t, double *out);
+
+/*
+ * Host-side evaluation of the pointwise functional the field kernels apply
+ * (no GPU needed), for checks of its arithmetic.  For each of count points
+ * with density n[i] > 0 (bohr^-3) and g2[i] = |grad n|^2, at T_kelvin:
+ *   out[6 i + 0] = f_s            free-energy density, Eq. (FGGA) (ftTF: Eq. (fTF))
+ *   out[6 i + 1] = T s_s          entropic part tau0 zeta F_sigma
+ *   out[6 i + 2] = d f_s / d n    without the divergence term, Eq. (vftGGA)
+ *   out[6 i + 3] = W              d f_s / d(grad n) = W grad n
+ *   out[6 i + 4] = eps_xc         PZ81 energy per electron (0 when xc = 0)
+ *   out[6 i + 5] = v_xc           PZ81 potential (0 when xc = 0)
+ * arith: ofdft_pointwise; with OFDFT_PW_F32X2 the double-float routine runs
+ * as compiled for the host (same source as the kernels'), falling back to
+ * binary64 outside its domain; *n_f2 (optional) receives how many points it
+ * handled.  OFDFT_EINVAL for a bad functional, arith, count or pointer.
+ */
+ofdft_status ofdft_pointwise_eval(int functional, int xc, double T_kelvin, long long count, const double *n,
+                                  const double *g2, int arith, double *out, long long *n_f2);
 
 void ofdft_destroy(ofdft_ctx *ctx);
 

@@ -474,7 +474,7 @@ def _mu_grad(sys, phi, v):
 
 
 def minimize(sys, phi0=None, gtol=1e-8, maxit=2000, theta0=0.05, ls_tol=0.1,
-             max_ls=20, callback=None):
+             max_ls=20, callback=None, e_tol=1e-11):
     """Direct minimisation of F_tot[n = phi^2] under int n = N_e (Sec. II).
 
     Nonlinear conjugate gradients; the paper names CG without details, so the
@@ -482,8 +482,10 @@ def minimize(sys, phi0=None, gtol=1e-8, maxit=2000, theta0=0.05, ls_tol=0.1,
     restart along -g when not a descent direction, norm-preserving rotation
     phi(theta) = phi cos(theta) + dhat sin(theta) with ||dhat|| = ||phi||, and
     a line search on dE/dtheta (secant, regula falsi once bracketed) until
-    |dE/dtheta| <= ls_tol |dE/dtheta(0)|.  Stops when ||g|| < gtol.
-    Returns (phi, evaluation dict, stats dict).
+    |dE/dtheta| <= ls_tol |dE/dtheta(0)| at a point whose free energy lies
+    below the sufficient-decrease line E(0) + 1e-4 theta dE/dtheta(0) (with
+    a rounding allowance e_tol |E(0)|; a trial above it bounds the step).
+    Stops when ||g|| < gtol.  Returns (phi, evaluation dict, stats dict).
     """
     g = sys.grid
     phi = (sys.uniform_phi() if phi0 is None else np.array(phi0, dtype=np.float64))
@@ -511,7 +513,7 @@ def minimize(sys, phi0=None, gtol=1e-8, maxit=2000, theta0=0.05, ls_tol=0.1,
         dhat = d * math.sqrt(pp / float(np.sum(d * d)))
         D0 = g.dV * float(np.sum(2.0 * phi * ev["v"] * dhat))
         th, ev_new, phi_new, nls = _line_search(sys, phi, dhat, D0, theta_prev,
-                                                ls_tol, max_ls)
+                                                ls_tol, max_ls, ev["F_tot"], e_tol)
         nevals += nls
         if th is None:
             if gr_prev is None:
@@ -530,11 +532,18 @@ def minimize(sys, phi0=None, gtol=1e-8, maxit=2000, theta0=0.05, ls_tol=0.1,
                          mu=mu, status=status)
 
 
-def _line_search(sys, phi, dhat, D0, theta1, ls_tol, max_ls):
-    """Derivative line search in theta (reading of the CG step, Sec. II)."""
+def _line_search(sys, phi, dhat, D0, theta1, ls_tol, max_ls, E0=None, e_tol=0.0):
+    """Derivative line search in theta (reading of the CG step, Sec. II).
+
+    Trial theta is accepted when |D| <= ls_tol |D0| and E(theta) <= E0 +
+    1e-4 theta D0 + e_tol |E0|.  A trial above that line becomes the upper
+    bracket whatever the sign of D there (the energy went up, so a minimum
+    lies before it); with D <= 0 at that bracket the next trial bisects.
+    """
     g = sys.grid
     lo, Dlo = 0.0, D0
     hi = Dhi = None
+    hi_nod = False               # upper bracket from the energy test with D <= 0
     pa, Da = 0.0, D0            # last two points for the unbracketed secant
     th = theta1
     for k in range(max_ls):
@@ -542,12 +551,16 @@ def _line_search(sys, phi, dhat, D0, theta1, ls_tol, max_ls):
         p = phi * c + dhat * s
         ev = evaluate(sys, p)
         D = g.dV * float(np.sum(2.0 * p * ev["v"] * (-phi * s + dhat * c)))
-        if abs(D) <= ls_tol * abs(D0):
+        up = (e_tol > 0.0 and E0 is not None
+              and ev["F_tot"] > E0 + 1e-4 * th * D0 + e_tol * abs(E0))
+        if not up and abs(D) <= ls_tol * abs(D0):
             return th, ev, p, k + 1
-        if D < 0.0:
+        if up:
+            hi, Dhi, hi_nod = th, D, not (D > 0.0)
+        elif D < 0.0:
             lo, Dlo = th, D
         else:
-            hi, Dhi = th, D
+            hi, Dhi, hi_nod = th, D, False
         if hi is None:
             nxt = 4.0 * th
             if D > Da:
@@ -555,6 +568,8 @@ def _line_search(sys, phi, dhat, D0, theta1, ls_tol, max_ls):
                 nxt = min(sec, 4.0 * th)
             nxt = max(nxt, 1.1 * th)
             pa, Da = th, D
+        elif hi_nod:
+            nxt = 0.5 * (lo + hi)
         else:
             nxt = lo - Dlo * (hi - lo) / (Dhi - Dlo)
             w = hi - lo

@@ -17,7 +17,9 @@ SOURCES = ["kernels_fields.cu", "kernels_misc.cu", "cg_control.cu", "capi.cu", "
            "tfunc_table.cpp", "serve.cpp"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
               "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr"]
+              "--expt-relaxed-constexpr",
+              # double-float error-free transformations must not be fused into FMAs
+              "-Xcompiler", "-ffp-contract=off"]
 
 
 def _nvcc():

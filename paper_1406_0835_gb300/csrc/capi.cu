@@ -598,6 +598,9 @@ ofdft_status write_config(ofdft_ctx *c, int k, double gtol, int maxit, int stagn
     h->switch_g = stagnate ? std::max(1e-5, 10.0 * gtol) : 0.0;
     h->dV = c->g.dV;
     h->ls_tol = 0.1;
+    h->eoff = c->fp.kind == 0 ? 9 : 3;
+    // line-search energy test: rounding allowance of the energy sums
+    h->e_tol = k == 0 ? 1e-11 : 1e-5;
     h->theta0 = 0.05;
     h->Ne = c->Ne;
     h->maxit = maxit;
@@ -670,7 +673,8 @@ ofdft_status minimize_start(ofdft_ctx *c, double gtol, int maxit)
     if (mixed) {
         launch_convert<double, float>(c->g.N, (const double *)c->f[0].phi, (float *)c->f[1].phi, c->st);
         c->launches++;
-        s = graphs ? enqueue_minimize_graph<float>(c, 1, gtol, maxit, 1) : minimize_host<float>(c, 1, gtol, maxit, 1);
+        s = graphs ? enqueue_minimize_graph<float>(c, 1, gtol, maxit, kStagnateIts)
+                   : minimize_host<float>(c, 1, gtol, maxit, kStagnateIts);
         if (s != OFDFT_OK) return s;
         launch_convert<float, double>(c->g.N, (const float *)c->f[1].phi, (double *)c->f[0].phi, c->st);
         c->launches++;
@@ -803,8 +807,14 @@ template <typename T> ofdft_status alloc_fieldset(ofdft_ctx *c, FieldSet &f)
     CK(cudaMallocAsync((void **)&f.spec, 4 * cb, c->st));
     f.spec_stride = cb / sizeof(cplx<T>);
     CK(cudaMallocAsync((void **)&f.vext, (size_t)g.NH * sizeof(cplx<T>), c->st));
+    // temperature table; FP64 sets append its double-float split (hi, lo
+    // binary32 pairs) for the double-float pointwise functional
     const std::vector<double> &tab = tfunc_table_host();
     std::vector<T> tt(tab.begin(), tab.end());
+    if (sizeof(T) == 8) {
+        tt.resize(2 * (size_t)kTfSize);
+        tfunc_table_split(tab.data(), reinterpret_cast<float *>(tt.data() + kTfSize));
+    }
     CK(cudaMallocAsync((void **)&f.tab, tt.size() * sizeof(T), c->st));
     CK(cudaMemcpyAsync(f.tab, tt.data(), tt.size() * sizeof(T), cudaMemcpyHostToDevice, c->st));
     int n3[3] = {g.nx, g.ny, g.nz};
@@ -1051,6 +1061,7 @@ void ofdft_default_params(ofdft_params *p)
     p->precision = OFDFT_FP64;
     p->device = 0;
     p->stream = nullptr;
+    p->pointwise = OFDFT_PW_F32X2;
 }
 
 ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const double *ions,
@@ -1076,6 +1087,9 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     if (params) p = *params;
     if (!(p.rc > 0.0)) return fail(nullptr, OFDFT_EINVAL, "rc must be > 0");
     if (p.precision != OFDFT_FP64 && p.precision != OFDFT_MIXED) return fail(nullptr, OFDFT_EINVAL, "bad precision");
+    if (p.pointwise != OFDFT_PW_F32X2 && p.pointwise != OFDFT_PW_F64)
+        return fail(nullptr, OFDFT_EINVAL, "bad pointwise arithmetic");
+    fp.f2 = p.pointwise == OFDFT_PW_F32X2;
     for (int i = 0; i < nat; ++i) {
         if (!(Z[i] > 0.0)) return fail(nullptr, OFDFT_EINVAL, "Z must be > 0");
         for (int a = 0; a < 3; ++a)
@@ -1486,6 +1500,40 @@ ofdft_status ofdft_timer_read(ofdft_ctx *c, double *total_ms, long long *launche
 long long ofdft_kernel_launches(ofdft_ctx *c) { return c ? c->launches : 0; }
 
 const char *ofdft_last_error(ofdft_ctx *c) { return c ? c->err.c_str() : g_setup_error.c_str(); }
+
+ofdft_status ofdft_pointwise_eval(int functional, int xc, double T_kelvin, long long count, const double *n,
+                                  const double *g2, int arith, double *out, long long *n_f2)
+{
+    FuncParams fp = functional_params(functional);
+    if (fp.kind < 0 || count < 0 || !(T_kelvin > 0.0) || (arith != OFDFT_PW_F32X2 && arith != OFDFT_PW_F64))
+        return OFDFT_EINVAL;
+    if (count > 0 && (!n || !g2 || !out)) return OFDFT_EINVAL;
+    fp.f2 = arith == OFDFT_PW_F32X2;
+    const std::vector<double> &tab = tfunc_table_host();
+    std::vector<double> tt(tab.begin(), tab.end());
+    tt.resize(2 * (size_t)kTfSize);
+    tfunc_table_split(tab.data(), reinterpret_cast<float *>(tt.data() + kTfSize));
+    const double temp = T_kelvin * kKbHa;
+    const ff::f2 tcoef = ff::from_double(2.0 / OF_K23 * temp);
+    long long used = 0;
+    for (long long i = 0; i < count; ++i) {
+        PwOut<double> o;
+        if (fp.f2 && pw_point_f2(fp, reinterpret_cast<const ff::f2 *>(tt.data() + kTfSize), tcoef, n[i], g2[i],
+                                 xc, o))
+            ++used;
+        else
+            o = pw_point_native<double>(fp, tt.data(), temp, n[i], g2[i], xc);
+        double *r = out + 6 * i;
+        r[0] = o.f;
+        r[1] = o.ts;
+        r[2] = o.dfdn;
+        r[3] = o.wc;
+        r[4] = o.eps;
+        r[5] = o.vxc;
+    }
+    if (n_f2) *n_f2 = used;
+    return OFDFT_OK;
+}
 
 ofdft_status ofdft_tfunc_eval(long long n, const double *t, double *out)
 {

@@ -44,7 +44,7 @@ constexpr size_t kOffPart = kOffZ + align256(kSMaxAtoms * sizeof(double));
 constexpr size_t kOffScal = kOffPart + align256((size_t)kSMaxPart * sizeof(double));
 constexpr size_t kOffTw = kOffScal + align256(64 * sizeof(double));
 constexpr size_t kOffTab = kOffTw + align256(3 * kSMaxEdge * sizeof(double2));
-constexpr size_t kScratchBytes = kOffTab + align256((size_t)kTfSize * sizeof(double));
+constexpr size_t kScratchBytes = kOffTab + align256(2 * (size_t)kTfSize * sizeof(double));   // + split
 
 static __device__ __align__(256) unsigned char g_ofdft_scratch[kScratchBytes];
 
@@ -54,7 +54,7 @@ struct DevState {
     unsigned char *base;
 };
 DevState g_dev[kMaxDevices];
-double g_tab_host[kTfSize];   // host copy of the temperature table, filled once
+double g_tab_host[2 * kTfSize];   // host temperature table + its double-float split, filled once
 bool g_tab_ready = false;
 
 // Status only: the documented limits say what OFDFT_EINVAL means here.
@@ -86,6 +86,7 @@ ofdft_status device_setup(int dev, unsigned char **base)
         d.base = (unsigned char *)p;
         if (!g_tab_ready) {
             tfunc_table_fill(g_tab_host);
+            tfunc_table_split(g_tab_host, reinterpret_cast<float *>(g_tab_host + kTfSize));
             g_tab_ready = true;
         }
         SCK(cudaMemcpy(d.base + kOffTab, g_tab_host, sizeof(g_tab_host), cudaMemcpyHostToDevice),
@@ -176,6 +177,7 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     if (nat <= 0 || nat > kSMaxAtoms) return serr(OFDFT_EINVAL, "static path: nat must be in 1..64");
     if (!(T_kelvin > 0.0) || !(rc > 0.0)) return serr(OFDFT_EINVAL, "temperature and rc must be > 0");
     FuncParams fp = functional_params(functional);
+    fp.f2 = 1;   // double-float pointwise functional, as ofdft_setup's default
     if (fp.kind < 0) return serr(OFDFT_EINVAL, "unknown functional");
     int dev = 0;
     SCK(cudaGetDevice(&dev), "cudaGetDevice failed");

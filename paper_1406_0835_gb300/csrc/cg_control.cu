@@ -3,7 +3,9 @@
 // Polak-Ribiere+ directions projected orthogonal to phi, restart along -g when
 // not descending, norm-preserving rotation phi cos(theta) + dhat sin(theta),
 // line search on dE/dtheta (secant, regula falsi once bracketed) until
-// |dE/dtheta| <= ls_tol |dE/dtheta(0)|, stop at ||g|| < gtol.
+// |dE/dtheta| <= ls_tol |dE/dtheta(0)| at a point below the sufficient-decrease
+// line E(0) + 1e-4 theta dE/dtheta(0) (+ a rounding allowance), stop at
+// ||g|| < gtol.
 //
 // Each controller is one thread: it reads the sums the reductions wrote into
 // the CgState, updates the scalars the vector kernels read, and sets the
@@ -19,6 +21,12 @@ namespace {
 __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, unsigned v)
 {
     if (use) cudaGraphSetConditional(h, v);
+}
+
+// Electronic energy (E_H + E_loc + F_s + F_xc) from the evaluation sums.
+__device__ __forceinline__ double e_elec(const CgState *s, const double *ev)
+{
+    return ev[0] + ev[1] + s->dV * (ev[s->eoff] + ev[s->eoff + 2]);
 }
 
 __global__ void k_ctl_norm(CgState *s)
@@ -85,7 +93,7 @@ __global__ void k_ctl_grad(CgState *s, int first, cudaGraphConditionalHandle out
             if (s->gnorm < 0.9 * s->best_g) {
                 s->best_g = s->gnorm;
                 s->best_it = s->it;
-            } else if (s->it - s->best_it >= 40) {
+            } else if (s->it - s->best_it >= s->stagnate) {
                 s->status = kCgStagnated;
                 s->done = 1;
             }
@@ -119,6 +127,8 @@ __global__ void k_ctl_dhat(CgState *s, cudaGraphConditionalHandle ls, int use)
     s->Dhi = 0.0;
     s->pa = 0.0;
     s->Da = s->D0;
+    s->E0 = e_elec(s, s->ev_acc);
+    s->hi_nod = 0;
     s->th = s->theta_prev;
     s->nls = 0;
     s->fallback = 0;
@@ -137,17 +147,27 @@ __global__ void k_ctl_ls(CgState *s, cudaGraphConditionalHandle ls, int use)
     s->nevals += 1;
     const double D = s->dV * s->ev[17];
     bool accept = false, failed = false;
+    // energy safeguard: a trial above the sufficient-decrease line bounds the
+    // step from above whatever the sign of D there
+    bool up = false;
+    if (s->e_tol > 0.0)
+        up = e_elec(s, s->ev) > s->E0 + 1e-4 * s->th * s->D0 + s->e_tol * fabs(s->E0);
     if (s->fallback) {
         accept = true;
-    } else if (fabs(D) <= s->ls_tol * fabs(s->D0)) {
+    } else if (!up && fabs(D) <= s->ls_tol * fabs(s->D0)) {
         accept = true;
     } else {
-        if (D < 0.0) {
+        if (up) {
+            s->hi = s->th;
+            s->Dhi = D;
+            s->hi_nod = D > 0.0 ? 0 : 1;
+        } else if (D < 0.0) {
             s->lo = s->th;
             s->Dlo = D;
         } else {
             s->hi = s->th;
             s->Dhi = D;
+            s->hi_nod = 0;
         }
         if (s->nls >= s->max_ls) {
             if (s->lo > 0.0) {          // one more evaluation at the best descent point
@@ -167,6 +187,8 @@ __global__ void k_ctl_ls(CgState *s, cudaGraphConditionalHandle ls, int use)
                 nxt = nxt > 1.1 * s->th ? nxt : 1.1 * s->th;
                 s->pa = s->th;
                 s->Da = D;
+            } else if (s->hi_nod) {
+                nxt = 0.5 * (s->lo + s->hi);   // no slope sign change to interpolate
             } else {
                 nxt = s->lo - s->Dlo * (s->hi - s->lo) / (s->Dhi - s->Dlo);
                 double w = s->hi - s->lo;

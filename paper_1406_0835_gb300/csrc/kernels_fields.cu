@@ -162,6 +162,7 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, cplx<T> *__restrict__ g0,
     }
     typedef typename AccT<T>::type A;
     A acc[6] = {0, 0, 0, 0, 0, 0};
+    const ff::f2 tcoef = ff::from_double(2.0 / OF_K23 * (double)temp);
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
         const int line = i / nz, e = i - line * nz;
         const int p = line >> 1, hi = line & 1;
@@ -171,9 +172,8 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, cplx<T> *__restrict__ g0,
         T ph = phit[rbase + i];
         T n = ph * ph;
         T gg = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
-        FsOut<T> o = fs_point<T>(fp, tab, temp, n, gg);
-        T eps = T(0), vxc = T(0);
-        if (xc) pz81_point<T>(n, o.y13, eps, vxc);
+        PwOut<T> o = pw_point<T>(fp, tab, tcoef, temp, n, gg, xc);
+        const T eps = o.eps, vxc = o.vxc;
         vpart[rbase + i] = o.dfdn + vxc;
         acc[0] += (A)o.f;
         acc[1] += (A)o.ts;
@@ -231,6 +231,7 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const cplx<T> *__restric
     C *X = fft_lines<C, true>(A, B, az, nl, nz, 1, false);
     typedef typename AccT<T>::type Ac;
     Ac acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const ff::f2 tcoef = ff::from_double(2.0 / OF_K23 * (double)temp);
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
         const int line = i / nz, e = i - line * nz;
         C d = X[(line >> 1) * nz + e];
@@ -239,9 +240,8 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const cplx<T> *__restric
         T n = ph * ph;
         T v;
         if (FTTF) {
-            FsOut<T> o = fs_point<T>(fp, tab, temp, n, T(0));
-            T eps = T(0), vxc = T(0);
-            if (xc) pz81_point<T>(n, o.y13, eps, vxc);
+            PwOut<T> o = pw_point<T>(fp, tab, tcoef, temp, n, T(0), xc);
+            const T eps = o.eps, vxc = o.vxc;
             v = o.dfdn + vxc + dr;
             acc[0] += (Ac)o.f;
             acc[1] += (Ac)o.ts;

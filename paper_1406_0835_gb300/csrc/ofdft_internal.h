@@ -159,6 +159,7 @@ void tfunc_table_fill(double *tab);
 struct FuncParams {
     int kind;       // 0 ftTF, 1 SGA-form (mu), 2 VT84F, 3 KST2-form (C1, a1)
     double p0, p1;  // mu | C1, a1
+    int f2;         // FP64 kernels: pointwise functional in double-float
 };
 FuncParams functional_params(int functional);
 
@@ -170,8 +171,10 @@ struct CgState {
     // configuration (written by the host before a minimisation)
     double gtol, dV, ls_tol, theta0, Ne;
     double switch_g;   // stagnate mode: also stop once ||g|| < switch_g (0: off)
-    int maxit, max_ls, stagnate;
-    int pad0;
+    double e_tol;      // line search: reject trials whose energy rises above
+                       // E0 + 1e-4 theta D0 + e_tol |E0| (0: off)
+    int maxit, max_ls, stagnate;   // stagnate: window in iterations (0: off)
+    int eoff;          // index in ev[] of the F_s sum (F_xc follows two later)
     // reduction outputs
     double ev[18];     // evaluation: E_H, E_loc, P_loc, GGA sums [3..8], final sums [9..17]
     double rg[2];      // sum g^2, sum g.g_prev
@@ -183,6 +186,8 @@ struct CgState {
     double cs[2];      // cos, sin of the trial angle (read by the FP64 evaluation kernels)
     float csf[2];      // the same for the FP32 kernels
     double th, lo, Dlo, hi, Dhi, pa, Da;
+    double E0;         // electronic energy at theta = 0 of the current line search
+    int hi_nod;        // the upper bracket came from the energy test, not from D > 0
     double best_g;
     double c12r[3];    // c1, c2, restart (read by the direction kernel)
     int best_it, restart, have_prev, it, nevals, nls, ls_active, accepted, status, done, fallback;
@@ -192,6 +197,9 @@ struct CgState {
 
 // Status codes of CgState::status (besides ofdft_status values).
 constexpr int kCgStagnated = 1;   // stopped at the precision floor (stagnate mode)
+// Stagnate mode: the stage stops when ||g|| has not fallen by 10 % in this
+// many iterations.
+constexpr int kStagnateIts = 40;
 
 // Reduction quantities (indices into the scalar block).
 enum Quantity {

@@ -11,6 +11,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "ffmath.cuh"
 #include "ofdft_internal.h"
 
 namespace ofdft {
@@ -276,6 +277,229 @@ template <typename T>
 OF_HD void pz81_point(T n, T &eps, T &v)
 {
     pz81_point<T>(n, inv_cbrt(n), eps, v);
+}
+
+// ---------------------------------------------------------------------------
+// The same pointwise functional in double-float arithmetic (ffmath.cuh) for
+// the FP64 path: inputs and outputs are binary64, every intermediate is a
+// double-float, so the result agrees with the binary64 routines above to a
+// few parts in 1e14 while running on the FP32 units.  Quantities whose
+// exponent can leave the binary32 range (s^2 and W, which carry n^(-8/3)) are
+// formed in binary64.  Outside the domain below (and in the Sommerfeld and
+// classical branches of the temperature functions) pw_point_f2 returns false
+// and the caller uses the binary64 routines.
+
+template <typename T> struct PwOut {
+    T f, ts, dfdn, wc, eps, vxc;
+};
+
+constexpr double kPwNmin = 1e-18, kPwNmax = 1e18, kPwS2max = 1e10;
+
+// Table polynomials with a double-float table (same layout as tfunc_eval's).
+// The panel variable u = uh + ul: uh is exact in binary32 and the Horner
+// sums run with it; ul (below 5e-7) enters through the first and second
+// derivatives.
+template <int NF>
+OF_HD void tfunc_eval_f2(const ff::f2 *__restrict__ tab, ff::f2 t, ff::f2 out[8])
+{
+    int e;
+    float inv2e;
+    const float m = split_pow2(t.hi, e, inv2e);
+    const int sub = (int)((m - 1.0f) * 4.0f);
+    const float uh = 8.0f * (m - 1.0f) - (float)(2 * sub + 1);
+    const float ul = 8.0f * t.lo * inv2e;
+    const float dudt = 8.0f * inv2e;
+    const ff::f2 *c = tab + ((size_t)((e - kTfEmin) * kTfSub + sub) * kTfFuncs) * kTfNc;
+#pragma unroll
+    for (int q = 0; q < NF; ++q) {
+        const ff::f2 *cq = c + q * kTfNc;
+        ff::f2 p = cq[kTfDeg], dp = {0.0f, 0.0f};
+        float d2 = 0.0f;   // half the second derivative
+#pragma unroll
+        for (int j = kTfDeg - 1; j >= 0; --j) {
+            d2 = d2 * uh + dp.hi;
+            dp = ff::fma_step(dp, uh, p);
+            p = ff::fma_step(p, uh, cq[j]);
+        }
+        p = ff::add(p, dp.hi * ul);
+        dp = ff::add(dp, 2.0f * d2 * ul);
+        out[q] = p;
+        out[4 + q] = ff::scale(dp, dudt);
+    }
+}
+
+// Enhancement factor F(x) and dF/dx in double-float (forms as in enhance).
+OF_HD void enhance_f2(const FuncParams &fp, ff::f2 x, ff::f2 &F, ff::f2 &dF)
+{
+    using namespace ff;
+    if (fp.kind == 1) {                                     // SGA form
+        const f2 p0 = from_double(fp.p0);
+        F = add(mul(x, p0), 1.0f);
+        dF = p0;
+    } else if (fp.kind == 3) {                              // KST2 form
+        const f2 p0 = from_double(fp.p0), p1 = from_double(fp.p1);
+        f2 den = recip(add(mul(x, p1), 1.0f));
+        F = add(mul(mul(x, p0), den), 1.0f);
+        dF = mul(p0, mul(den, den));
+    } else {                                                // VT84F, m = 8, n = 4
+        const f2 mu = cst(2.778), al = cst(1.2965);
+        if (x.hi <= 1e-15f) {                               // F = 1 + O(x)
+            F = {1.0f, 0.0f};
+            dF = cst(-2.778 + 1.2965 + 5.0 / 3.0);
+            return;
+        }
+        const f2 ax = mul(x, al);
+        const f2 e1 = exp(neg(ax));                         // e^(-al x)
+        const f2 x2 = mul(x, x);
+        const f2 em = neg(expm1_neg(neg(mul(x2, al))));     // 1 - e^(-al x^2)
+        const f2 mx = mul(x, mu);
+        const f2 q = add(mx, 1.0f);                         // 1 + mu x
+        const f2 inv = recip(mul(x, q));
+        const f2 rx = mul(q, inv);                          // 1/x
+        const f2 den = mul(x, inv);                         // 1/(1 + mu x)
+        // F = 1 - mu x e1 den + em (rx - 1) + (5/3) x
+        f2 Fv = add(neg(mul(mul(mx, e1), den)), 1.0f);
+        Fv = add(Fv, mul(em, add(rx, -1.0f)));
+        F = add(Fv, mul(x, cst(5.0 / 3.0)));
+        // dF = -mu e1 (1 - al x - al mu x^2) den^2 + 2 al (1 - em)(1 - x) - em rx^2 + 5/3
+        const f2 poly = add(neg(add(ax, mul(mul(x2, al), mu))), 1.0f);
+        f2 d = neg(mul(mul(mul(mu, e1), poly), mul(den, den)));
+        d = add(d, mul(mul(al, add(neg(em), 1.0f)), scale(add(neg(x), 1.0f), 2.0f)));
+        d = sub(d, mul(em, mul(rx, rx)));
+        dF = add(d, cst(5.0 / 3.0));
+    }
+}
+
+// PZ81 (same branches and constants as pz81_point) from n, n^(1/3) and
+// y = n^(-1/3) in double-float.
+OF_HD void pz81_f2(ff::f2 c13, ff::f2 y, ff::f2 &eps, ff::f2 &v)
+{
+    using namespace ff;
+    const f2 rs = mul(y, cst(0.62035049089940001667));
+    const f2 ex = mul(c13, cst(-0.73855876638202240587));
+    f2 ec, vc;
+    if (rs.hi >= 1.0f) {
+        const f2 sq = sqrt(rs);
+        const f2 den = recip(add(add(mul(sq, cst(1.0529)), mul(rs, cst(0.3334))), 1.0f));
+        ec = mul(den, cst(-0.1423));
+        const f2 num = add(add(mul(sq, cst(7.0 / 6.0 * 1.0529)), mul(rs, cst(4.0 / 3.0 * 0.3334))), 1.0f);
+        vc = mul(mul(ec, num), den);
+    } else {
+        const f2 lr = log(rs);
+        const f2 rlr = mul(rs, lr);
+        ec = add(add(mul(lr, cst(0.0311)), cst(-0.048)), add(mul(rlr, cst(kPzC)), mul(rs, cst(kPzD))));
+        vc = add(add(mul(lr, cst(0.0311)), cst(-0.048 - 0.0311 / 3.0)),
+                 add(mul(rlr, cst(2.0 / 3.0 * kPzC)), mul(rs, cst((2.0 * kPzD - kPzC) / 3.0))));
+    }
+    eps = add(ex, ec);
+    v = add(mul(ex, cst(4.0 / 3.0)), vc);
+}
+
+// f_s, its derivatives and (xc != 0) PZ81 at one point; false when the point
+// is outside the double-float domain.  tcoef = 2 k_B T / (3 pi^2)^(2/3).
+OF_HD bool pw_point_f2(const FuncParams &fp, const ff::f2 *__restrict__ tab, ff::f2 tcoef, double n_d,
+                       double g2_d, int xc, PwOut<double> &o)
+{
+    using namespace ff;
+    if (!(n_d >= kPwNmin && n_d <= kPwNmax)) return false;
+    const f2 n = from_double(n_d);
+    const f2 y = rcbrt(n);                                   // n^(-1/3)
+    const f2 y2 = mul(y, y);
+    const f2 t = mul(tcoef, y2);                             // Eq. (tred)
+    if (!(t.hi >= 9.5367431640625e-07f && t.hi < 17179869184.0f)) return false;
+    const f2 c13 = mul(n, y2);                               // n^(1/3)
+    const f2 n23 = mul(c13, c13);
+    const f2 rn = mul(y2, y);                                // 1/n
+    const f2 tau0 = mul(mul(n, n23), cst(OF_CTF));           // Eq. (tauTFdefn)
+    const f2 dtau0 = mul(n23, cst(5.0 / 3.0 * OF_CTF));
+    const f2 dtdn = mul(mul(t, rn), cst(-2.0 / 3.0));
+    f2 tf[8];
+    if (fp.kind == 0) {                                      // ftTF
+        tfunc_eval_f2<2>(tab, t, tf);
+        const f2 kap = sub(tf[0], tf[1]);
+        o.f = to_double(mul(tau0, kap));
+        o.ts = to_double(mul(tau0, tf[1]));
+        o.dfdn = to_double(add(mul(dtau0, kap), mul(mul(tau0, sub(tf[4], tf[5])), dtdn)));   // Eq. (vTF)
+        o.wc = 0.0;
+    } else {
+        // s^2 in binary64: n^(-8/3) leaves the binary32 range at small n
+        const double yd = to_double(y), y2d = yd * yd, rn43 = y2d * y2d;
+        const double s2d = (g2_d * rn43) * rn43 * OF_CS;    // Eq. (s_0defn)
+        if (!(s2d <= kPwS2max)) return false;
+        tfunc_eval_f2<4>(tab, t, tf);
+        const f2 xi = tf[0], ze = tf[1], A = tf[2], B = tf[3];
+        const f2 dxi = tf[4], dze = tf[5], dA = tf[6], dB = tf[7];
+        const f2 s2 = from_double(s2d);
+        const f2 xt = mul(s2, A), xs = mul(s2, B);           // Eq. (s_s)
+        f2 Ft, dFt, Fsg, dFsg;
+        enhance_f2(fp, xt, Ft, dFt);
+        enhance_f2(fp, xs, Fsg, dFsg);
+        const f2 Fs = add(neg(Fsg), 2.0f), dFs = neg(dFsg); // F_sigma = 2 - F_tau(s_sigma)
+        const f2 kin = mul(tau0, xi), ent = mul(tau0, ze);
+        o.f = to_double(sub(mul(kin, Ft), mul(ent, Fs)));   // Eq. (FGGA)
+        o.ts = to_double(mul(ent, Fs));
+        const f2 e83 = mul(rn, cst(-8.0 / 3.0));
+        const f2 s2dt = mul(s2, dtdn);
+        // Eq. (vftGGA), first two lines
+        f2 d = mul(dtau0, sub(mul(xi, Ft), mul(ze, Fs)));
+        d = add(d, mul(mul(tau0, dtdn), sub(mul(dxi, Ft), mul(dze, Fs))));
+        d = add(d, mul(mul(kin, dFt), add(mul(e83, xt), mul(s2dt, dA))));
+        d = sub(d, mul(mul(ent, dFs), add(mul(e83, xs), mul(s2dt, dB))));
+        o.dfdn = to_double(d);
+        // last line: W = [tau0 xi F_tau' A - tau0 zeta F_sigma' B] d s^2 / d grad n
+        const double wpre = to_double(sub(mul(mul(kin, dFt), A), mul(mul(ent, dFs), B)));
+        o.wc = (wpre * rn43) * rn43 * (2.0 * OF_CS);
+    }
+    if (xc) {
+        f2 eps, v;
+        pz81_f2(c13, y, eps, v);
+        o.eps = to_double(eps);
+        o.vxc = to_double(v);
+    } else {
+        o.eps = 0.0;
+        o.vxc = 0.0;
+    }
+    return true;
+}
+
+// The routines of the precision T (binary64 or binary32) with the same output.
+template <typename T>
+OF_HD PwOut<T> pw_point_native(const FuncParams &fp, const T *__restrict__ tab, T temp, T n, T g2, int xc)
+{
+    FsOut<T> s = fs_point<T>(fp, tab, temp, n, g2);
+    PwOut<T> o;
+    o.f = s.f;
+    o.ts = s.ts;
+    o.dfdn = s.dfdn;
+    o.wc = s.wc;
+    o.eps = T(0);
+    o.vxc = T(0);
+    if (xc) pz81_point<T>(n, s.y13, o.eps, o.vxc);
+    return o;
+}
+
+// Pointwise functional of a field kernel.  FP64 kernels with fp.f2 set take
+// the double-float routine (its split table follows the binary64 one in tab)
+// and fall back to binary64 outside its domain; FP32 kernels run binary32.
+template <typename T>
+OF_HD PwOut<T> pw_point(const FuncParams &fp, const T *__restrict__ tab, ff::f2 tcoef, T temp, T n, T g2, int xc)
+{
+    if constexpr (sizeof(T) == 8) {
+        PwOut<double> o;
+        if (fp.f2 && pw_point_f2(fp, reinterpret_cast<const ff::f2 *>(tab + kTfSize), tcoef, n, g2, xc, o))
+            return o;
+    }
+    return pw_point_native<T>(fp, tab, temp, n, g2, xc);
+}
+
+// Double-float table written from the binary64 one (hi, lo per coefficient).
+inline void tfunc_table_split(const double *tab, float *out)
+{
+    for (int i = 0; i < kTfSize; ++i) {
+        ff::f2 c = ff::from_double(tab[i]);
+        out[2 * i] = c.hi;
+        out[2 * i + 1] = c.lo;
+    }
 }
 
 }  // namespace ofdft

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libofdft.so")
 
 FUNCTIONALS = {"fttf": 0, "sga": 1, "vt84f": 2, "kst2": 3, "vwtf": 4, "tw": 5, "apbef": 6}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+POINTWISE = {"f32x2": 0, "f64": 1}
 STATUS = {0: "OFDFT_OK", -1: "OFDFT_EINVAL", -2: "OFDFT_ENOMEM", -3: "OFDFT_ENOCONV",
           -4: "OFDFT_ENUMERIC", -5: "OFDFT_ETIMEOUT", -6: "OFDFT_EDEVICE", -7: "OFDFT_EBUSY"}
 
@@ -28,7 +29,7 @@ MIXED_FORM_GTOL = 1e-6
 
 class Params(ctypes.Structure):
     _fields_ = [("xc", ctypes.c_int), ("rc", ctypes.c_double), ("precision", ctypes.c_int),
-                ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("pointwise", ctypes.c_int)]
 
 
 class Energy(ctypes.Structure):
@@ -114,6 +115,8 @@ SIGNATURES = {
     "ofdft_kernel_launches": (ctypes.c_longlong, [ctypes.c_void_p]),
     "ofdft_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ofdft_tfunc_eval": (ctypes.c_int, [ctypes.c_longlong, _P, _P]),
+    "ofdft_pointwise_eval": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
+                                            _P, _P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong)]),
     "ofdft_destroy": (None, [ctypes.c_void_p]),
     "ofdft_minimize_start": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
     "ofdft_minimize_query": (ctypes.c_int, [ctypes.c_void_p]),
@@ -347,6 +350,24 @@ def ofdft_tfunc_eval(t):
     return out
 
 
+def ofdft_pointwise_eval(functional, xc, T_kelvin, n, g2, arith="f32x2"):
+    """Host evaluation of the kernels' pointwise functional: returns
+    (out[count, 6] = f_s, T s_s, df/dn, W, eps_xc, v_xc; points handled in
+    double-float)."""
+    n = _f64(n).reshape(-1)
+    g2 = _f64(g2).reshape(-1)
+    if g2.size != n.size:
+        raise ValueError("n and g2 differ in size")
+    out = np.empty((n.size, 6))
+    used = ctypes.c_longlong()
+    st = load().ofdft_pointwise_eval(FUNCTIONALS.get(functional, functional), int(bool(xc)), float(T_kelvin),
+                                     n.size, _ptr(n), _ptr(g2), POINTWISE.get(arith, arith), _ptr(out),
+                                     ctypes.byref(used))
+    if st != 0:
+        raise OfdftError(st, "bad argument")
+    return out, used.value
+
+
 def ofdft_destroy(ctx):
     if ctx:
         load().ofdft_destroy(ctx)
@@ -357,11 +378,12 @@ class Context:
     """One OF-DFT system on one GPU (owns a libofdft context)."""
 
     def __init__(self, L, grid, ions, Z, T_kelvin, functional="fttf", xc=True, rc=0.25,
-                 precision="fp64", device=0, stream=None):
+                 precision="fp64", device=0, stream=None, pointwise="f32x2"):
         p = ofdft_default_params()
         p.xc = int(bool(xc))
         p.rc = float(rc)
         p.precision = PRECISIONS[precision]
+        p.pointwise = POINTWISE[pointwise]
         p.device = int(device)
         p.stream = stream
         self.ctx = ofdft_setup(np.diag(np.asarray(L, dtype=np.float64)), grid, ions, Z, T_kelvin,

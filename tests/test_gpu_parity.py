@@ -57,6 +57,30 @@ def test_energy_and_potential_match_oracle(fn, grid):
         assert np.array_equal(v, v2)
 
 
+@pytest.mark.parametrize("fn", FUNCS)
+def test_double_float_pointwise_matches_binary64(fn):
+    """The FP64 kernels' default double-float pointwise functional against
+    the binary64 one (ofdft_params.pointwise) on the same density: energies
+    to 1e-12, potential to 1e-11 of its range; then both minimise to the
+    same free energy."""
+    cfg = inputs.config_mixed(2.5e5, grid=40, n_atoms=16)
+    cfg["ions"] = cfg["ions"][:16]
+    rng = np.random.default_rng(11)
+    phi = np.sqrt(16.0 / np.prod(cfg["L"])) * (1.0 + 0.2 * rng.standard_normal(cfg["grid"]))
+    out = {}
+    for pw in ("f32x2", "f64"):
+        with ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], fn, pointwise=pw) as ctx:
+            E, v = ctx.energy_potential(phi)
+            Em, st = ctx.minimize(gtol=1e-8)
+            assert st["status"] == 0
+            out[pw] = (E, v, Em)
+    (Ea, va, Ema), (Eb, vb, Emb) = out["f32x2"], out["f64"]
+    for k in ("F_tot", "F_s", "minus_TS", "F_xc", "P", "P_s", "P_xc"):
+        assert abs(Ea[k] - Eb[k]) <= 1e-12 * max(abs(Eb["F_tot"]), abs(Eb[k])), (k, Ea[k], Eb[k])
+    assert np.max(np.abs(va - vb)) <= 1e-11 * np.max(np.abs(vb))
+    assert rel(Ema["F_tot"], Emb["F_tot"]) <= 1e-11
+
+
 def test_uniform_density_and_temperature_extremes():
     """s = 0 exactly (removable 0/0 of VT84F) and t over the table's range."""
     for T, rho in ((2.0e3, 10.0), (4.0e6, 0.1), (1.0e5, 1.0)):
