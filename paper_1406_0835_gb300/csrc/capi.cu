@@ -157,9 +157,26 @@ template <typename T> ofdft_status upload_twiddles(ofdft_ctx *c, FieldSet &f, in
         w[m].x = (T)cosl(ang);
         w[m].y = (T)sinl(ang);
     }
-    CK(cudaMallocAsync((void **)&f.tw[axis], n * sizeof(cplx<T>), c->st));
-    CK(cudaMemcpyAsync(f.tw[axis], w.data(), n * sizeof(cplx<T>), cudaMemcpyHostToDevice, c->st));
+    // FP64 sets append the same twiddles as double-float pairs (ff::cf2)
+    std::vector<float> wf;
+    if (sizeof(T) == 8) {
+        wf.resize(4 * (size_t)n);
+        for (int m = 0; m < n; ++m) {
+            long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)n;
+            long double cv = cosl(ang), sv = sinl(ang);
+            float ch = (float)cv, sh = (float)sv;
+            wf[4 * m] = ch;
+            wf[4 * m + 1] = (float)(cv - (long double)ch);
+            wf[4 * m + 2] = sh;
+            wf[4 * m + 3] = (float)(sv - (long double)sh);
+        }
+    }
+    const size_t nb = n * sizeof(cplx<T>), nbf = wf.size() * sizeof(float);
+    CK(cudaMallocAsync((void **)&f.tw[axis], nb + nbf, c->st));
+    CK(cudaMemcpyAsync(f.tw[axis], w.data(), nb, cudaMemcpyHostToDevice, c->st));
+    if (nbf) CK(cudaMemcpyAsync((char *)f.tw[axis] + nb, wf.data(), nbf, cudaMemcpyHostToDevice, c->st));
     f.ax[axis] = fft_axis(n, f.tw[axis]);
+    f.ax[axis].twf = nbf ? (const void *)((const char *)f.tw[axis] + nb) : nullptr;
     return OFDFT_OK;
 }
 
@@ -1089,7 +1106,7 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     if (p.precision != OFDFT_FP64 && p.precision != OFDFT_MIXED) return fail(nullptr, OFDFT_EINVAL, "bad precision");
     if (p.pointwise != OFDFT_PW_F32X2 && p.pointwise != OFDFT_PW_F64)
         return fail(nullptr, OFDFT_EINVAL, "bad pointwise arithmetic");
-    fp.f2 = p.pointwise == OFDFT_PW_F32X2;
+    const bool dd = p.pointwise == OFDFT_PW_F32X2;
     for (int i = 0; i < nat; ++i) {
         if (!(Z[i] > 0.0)) return fail(nullptr, OFDFT_EINVAL, "Z must be > 0");
         for (int a = 0; a < 3; ++a)
@@ -1125,6 +1142,7 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     g.dV = g.omega / (double)g.N;
     g.rc = p.rc;
     grid_reciprocal(g);
+    g.dd = dd ? 1 : 0;
     c->nat = nat;
     c->R.assign(ions, ions + 3 * nat);
     c->Z.assign(Z, Z + nat);
@@ -1508,28 +1526,37 @@ ofdft_status ofdft_pointwise_eval(int functional, int xc, double T_kelvin, long 
     if (fp.kind < 0 || count < 0 || !(T_kelvin > 0.0) || (arith != OFDFT_PW_F32X2 && arith != OFDFT_PW_F64))
         return OFDFT_EINVAL;
     if (count > 0 && (!n || !g2 || !out)) return OFDFT_EINVAL;
-    fp.f2 = arith == OFDFT_PW_F32X2;
     const std::vector<double> &tab = tfunc_table_host();
     std::vector<double> tt(tab.begin(), tab.end());
     tt.resize(2 * (size_t)kTfSize);
     tfunc_table_split(tab.data(), reinterpret_cast<float *>(tt.data() + kTfSize));
+    const ff::f2 *tab2 = reinterpret_cast<const ff::f2 *>(tt.data() + kTfSize);
     const double temp = T_kelvin * kKbHa;
     const ff::f2 tcoef = ff::from_double(2.0 / OF_K23 * temp);
     long long used = 0;
     for (long long i = 0; i < count; ++i) {
         PwOut<double> o;
-        if (fp.f2 && pw_point_f2(fp, reinterpret_cast<const ff::f2 *>(tt.data() + kTfSize), tcoef, n[i], g2[i],
-                                 xc, o))
+        PwF2 r;
+        // the gradient as the double-float kernels see it: components; here (|grad n|, 0, 0)
+        const ff::f2 gr[3] = {ff::from_double(sqrt(g2[i])), ff::f2(0.0f, 0.0f), ff::f2(0.0f, 0.0f)};
+        if (arith == OFDFT_PW_F32X2 && pw_core_f2(fp, tab2, tcoef, ff::from_double(n[i]), gr, xc, r)) {
             ++used;
-        else
+            o.f = ff::to_double(r.f);
+            o.ts = ff::to_double(r.ts);
+            o.dfdn = ff::to_double(r.dfdn);
+            o.wc = g2[i] > 0.0 ? ff::to_double(r.w[0]) / sqrt(g2[i]) : 0.0;
+            o.eps = ff::to_double(r.eps);
+            o.vxc = ff::to_double(r.vxc);
+        } else {
             o = pw_point_native<double>(fp, tt.data(), temp, n[i], g2[i], xc);
-        double *r = out + 6 * i;
-        r[0] = o.f;
-        r[1] = o.ts;
-        r[2] = o.dfdn;
-        r[3] = o.wc;
-        r[4] = o.eps;
-        r[5] = o.vxc;
+        }
+        double *w = out + 6 * i;
+        w[0] = o.f;
+        w[1] = o.ts;
+        w[2] = o.dfdn;
+        w[3] = o.wc;
+        w[4] = o.eps;
+        w[5] = o.vxc;
     }
     if (n_f2) *n_f2 = used;
     return OFDFT_OK;

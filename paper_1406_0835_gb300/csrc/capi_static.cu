@@ -43,7 +43,7 @@ constexpr size_t kOffZ = kOffIons + align256(3 * kSMaxAtoms * sizeof(double));
 constexpr size_t kOffPart = kOffZ + align256(kSMaxAtoms * sizeof(double));
 constexpr size_t kOffScal = kOffPart + align256((size_t)kSMaxPart * sizeof(double));
 constexpr size_t kOffTw = kOffScal + align256(64 * sizeof(double));
-constexpr size_t kOffTab = kOffTw + align256(3 * kSMaxEdge * sizeof(double2));
+constexpr size_t kOffTab = kOffTw + align256(3 * kSMaxEdge * 2 * sizeof(double2));   // + double-float copy
 constexpr size_t kScratchBytes = kOffTab + align256(2 * (size_t)kTfSize * sizeof(double));   // + split
 
 static __device__ __align__(256) unsigned char g_ofdft_scratch[kScratchBytes];
@@ -177,7 +177,6 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     if (nat <= 0 || nat > kSMaxAtoms) return serr(OFDFT_EINVAL, "static path: nat must be in 1..64");
     if (!(T_kelvin > 0.0) || !(rc > 0.0)) return serr(OFDFT_EINVAL, "temperature and rc must be > 0");
     FuncParams fp = functional_params(functional);
-    fp.f2 = 1;   // double-float pointwise functional, as ofdft_setup's default
     if (fp.kind < 0) return serr(OFDFT_EINVAL, "unknown functional");
     int dev = 0;
     SCK(cudaGetDevice(&dev), "cudaGetDevice failed");
@@ -200,20 +199,33 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     g.dV = g.omega / (double)N;
     g.rc = rc;
     grid_reciprocal(g);
+    g.dd = 1;   // double-float FFT and pointwise arithmetic, as ofdft_setup's default
     const double T = T_kelvin * 3.166811563e-6;
 
-    // twiddles for the three axes (host stack -> scratch)
+    // twiddles for the three axes (host stack -> scratch), binary64 then
+    // double-float pairs
     double2 tw[3][kSMaxEdge];
+    float twf[3][kSMaxEdge][4];
     int n3[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a)
         for (int m = 0; m < n3[a]; ++m) {
             long double ang = -2.0L * 3.14159265358979323846264338327950288L * m / n3[a];
-            tw[a][m] = make_double2((double)cosl(ang), (double)sinl(ang));
+            long double cv = cosl(ang), sv = sinl(ang);
+            tw[a][m] = make_double2((double)cv, (double)sv);
+            twf[a][m][0] = (float)cv;
+            twf[a][m][1] = (float)(cv - (long double)twf[a][m][0]);
+            twf[a][m][2] = (float)sv;
+            twf[a][m][3] = (float)(sv - (long double)twf[a][m][2]);
         }
     double2 *twd = (double2 *)(base + kOffTw);
+    double2 *twfd = twd + 3 * kSMaxEdge;
     SCK(cudaMemcpyAsync(twd, tw, sizeof(tw), cudaMemcpyHostToDevice, st), "twiddle upload failed");
+    SCK(cudaMemcpyAsync(twfd, twf, sizeof(twf), cudaMemcpyHostToDevice, st), "twiddle upload failed");
     FftAxis ax = fft_axis(g.nx, twd), ay = fft_axis(g.ny, twd + kSMaxEdge),
             az = fft_axis(g.nz, twd + 2 * kSMaxEdge);
+    ax.twf = twfd;
+    ay.twf = twfd + kSMaxEdge;
+    az.twf = twfd + 2 * kSMaxEdge;
     // ions -> phases -> v_ext(G)
     double *Rd = (double *)(base + kOffIons), *Zd = (double *)(base + kOffZ);
     SCK(cudaMemcpyAsync(Rd, ions, 3 * nat * sizeof(double), cudaMemcpyHostToDevice, st), "ion upload failed");

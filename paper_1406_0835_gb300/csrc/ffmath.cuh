@@ -38,6 +38,16 @@ namespace ff {
 
 struct f2 {
     float hi, lo;
+    f2() = default;
+    FF_HD constexpr f2(float h, float l) : hi(h), lo(l) {}
+    // nearest double-float to a binary64 (constants and host code)
+    FF_HD constexpr explicit f2(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    FF_HD constexpr explicit f2(int i) : hi((float)i), lo(0.0f) {}   // exact for |i| < 2^24
+};
+
+// Complex double-float (the layout of a double2: 16 bytes).
+struct cf2 {
+    f2 x, y;
 };
 
 FF_HD float fadd(float a, float b)
@@ -104,9 +114,23 @@ FF_HD f2 from_double(double d)
 FF_HD double to_double(f2 x) { return (double)x.hi + (double)x.lo; }
 
 // Compile-time constant split of a double.
-constexpr f2 cst(double d) { return {(float)d, (float)(d - (double)(float)d)}; }
+constexpr f2 cst(double d) { return f2(d); }
 
 FF_HD f2 neg(f2 x) { return {-x.hi, -x.lo}; }
+
+FF_HD float int_bits_float(uint32_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+#endif
+}
+
+// 2^k as a binary32 for -126 <= k <= 127.
+FF_HD float pow2i(int k) { return int_bits_float((uint32_t)(k + 127) << 23); }
 
 // AccurateDWPlusDW: relative error <= 3u^2 even under cancellation.
 FF_HD f2 add(f2 x, f2 y)
@@ -149,6 +173,50 @@ FF_HD f2 mul(f2 x, float b)
 // Exact scaling by a power of two (no underflow or overflow in range).
 FF_HD f2 scale(f2 x, float p2) { return {fmul(x.hi, p2), fmul(x.lo, p2)}; }
 
+// SloppyDWPlusDW: absolute error a few u^2 (|x| + |y|) (no relative bound
+// under cancellation) -- enough for sums whose error is judged against the
+// size of the operands, as in FFT butterflies.
+FF_HD f2 add_s(f2 x, f2 y)
+{
+    f2 s = two_sum(x.hi, y.hi);
+    float t = fadd(x.lo, y.lo);
+    return fast_two_sum(s.hi, fadd(s.lo, t));
+}
+
+// Arithmetic operators for generic (FFT, G-space) code: sums use add_s.
+FF_HD f2 operator+(f2 x, f2 y) { return add_s(x, y); }
+FF_HD f2 operator-(f2 x, f2 y) { return add_s(x, neg(y)); }
+FF_HD f2 operator-(f2 x) { return neg(x); }
+FF_HD f2 operator*(f2 x, f2 y) { return mul(x, y); }
+FF_HD f2 &operator+=(f2 &x, f2 y) { return x = add_s(x, y); }
+FF_HD bool operator>(f2 x, f2 y) { return x.hi > y.hi || (x.hi == y.hi && x.lo > y.lo); }
+
+// Binary64 -> double-float with integer operations only: hi takes the
+// leading 24 significand bits (truncated), lo the next 23 (exact, built with
+// the 2^23 trick); the 6 bits left are dropped (relative error < 2^-46).
+// Magnitudes below 2^-126 (and zero) give zero; beyond the binary32 range
+// (and NaN) the binary32 conversion (inf, NaN) with lo = 0.  The result is a
+// valid double-float with |lo| < ulp(hi).
+FF_HD f2 split_int(double d)
+{
+    uint64_t b;
+#ifdef __CUDA_ARCH__
+    b = (uint64_t)__double_as_longlong(d);
+#else
+    memcpy(&b, &d, 8);
+#endif
+    const uint32_t top = (uint32_t)(b >> 32);
+    const int E = (int)((top >> 20) & 0x7ff) - 1023;
+    if (E < -126) return f2(0.0f, 0.0f);
+    if (E > 127) return f2((float)d, 0.0f);
+    const uint32_t sign = top & 0x80000000u;
+    const uint32_t hib = sign | ((uint32_t)(E + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffffu);
+    const uint32_t lint = (uint32_t)(b >> 6) & 0x7fffffu;    // significand bits 28..6
+    float lo = fsub(int_bits_float(0x4b000000u | lint), 8388608.0f);   // exact integer < 2^23
+    lo = fmul(fmul(lo, 1.4210854715202004e-14f), pow2i(E));              // * 2^-46 * 2^E
+    return f2(int_bits_float(hib), sign ? -lo : lo);
+}
+
 // p u + c for a Horner step with a binary32 variable: absolute error a few
 // u^2 (|p u| + |c|), which is what a polynomial evaluation needs.
 FF_HD f2 fma_step(f2 p, float u, f2 c)
@@ -160,18 +228,6 @@ FF_HD f2 fma_step(f2 p, float u, f2 c)
     return fast_two_sum(s.hi, w);
 }
 
-// 2^k as a binary32 for -126 <= k <= 127.
-FF_HD float pow2i(int k)
-{
-    int32_t b = (int32_t)(k + 127) << 23;
-#ifdef __CUDA_ARCH__
-    return __int_as_float(b);
-#else
-    float f;
-    memcpy(&f, &b, 4);
-    return f;
-#endif
-}
 
 // x / y: binary32 quotient q1, remainder r = x - q1 y in double-float, then
 // q1 + r/y.  Relative error a few u^2.
@@ -183,6 +239,7 @@ FF_HD f2 div(f2 x, f2 y)
     return fast_two_sum(q1, q2);
 }
 FF_HD f2 recip(f2 y) { return div(f2{1.0f, 0.0f}, y); }
+FF_HD f2 operator/(f2 x, f2 y) { return div(x, y); }
 
 // sqrt(x), x > 0: s = binary32 root, then s + (x - s^2)/(2 s).
 FF_HD f2 sqrt(f2 x)

@@ -8,9 +8,29 @@
 // w = exp(-2 pi i / n), inverse its conjugate (unnormalised).
 #pragma once
 
+#include "ffmath.cuh"
 #include "ofdft_internal.h"
 
 namespace ofdft {
+
+// Twiddle tables: cplx<T> at FftAxis::tw, double-float pairs at ::twf.
+template <typename C> __device__ __forceinline__ const C *axis_tw(const FftAxis &ax)
+{
+    return reinterpret_cast<const C *>(ax.tw);
+}
+template <> __device__ __forceinline__ const ff::cf2 *axis_tw<ff::cf2>(const FftAxis &ax)
+{
+    return reinterpret_cast<const ff::cf2 *>(ax.twf);
+}
+template <typename C> __device__ __forceinline__ C ld_tw(const C *p) { return __ldg(p); }
+template <> __device__ __forceinline__ ff::cf2 ld_tw<ff::cf2>(const ff::cf2 *p)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    ff::cf2 r;
+    r.x = ff::f2(v.x, v.y);
+    r.y = ff::f2(v.z, v.w);
+    return r;
+}
 
 template <typename C, bool INV> __device__ __forceinline__ void dft2(C *v)
 {
@@ -117,7 +137,7 @@ __device__ __forceinline__ void stage(const C *__restrict__ src, C *__restrict__
         if (k != 0) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C w = __ldg(tw + r * k * tws);
+                C w = ld_tw(tw + r * k * tws);
                 if (INV) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
@@ -136,7 +156,7 @@ __device__ __forceinline__ void stage(const C *__restrict__ src, C *__restrict__
 template <typename C, bool INV>
 __device__ C *fft_lines(C *a, C *b, const FftAxis &ax, int nl, int lstride, int estride, bool lines_fast)
 {
-    const C *tw = reinterpret_cast<const C *>(ax.tw);
+    const C *tw = axis_tw<C>(ax);
     for (int s = 0; s < ax.nst; ++s) {
         const int R = ax.rad[s], Ns = ax.ns[s];
         switch (R) {

@@ -8,6 +8,13 @@
 //   zfwd(n = phi^2) -> y -> x[grad] -> y^-1 (3) -> z[pointwise, W] -> y (3)
 //   -> x[div] -> y^-1 -> z^-1[potential, reductions]
 // (ftTF: zfwd -> y -> x[v_HL] -> y^-1 -> z^-1[pointwise, potential]).
+//
+// Every kernel is written once for a precision tag PR: float and double
+// compute in their own type; DD keeps the fields in binary64 in memory and
+// computes in double-float (ffmath.cuh) in registers and shared memory, so
+// the FP64 path runs on the FP32 units.  KT<PR> names the types.
+#include <type_traits>
+
 #include "fft_core.cuh"
 #include "kernels.h"
 #include "pointwise.cuh"
@@ -16,9 +23,64 @@ namespace ofdft {
 
 namespace {
 
+struct DD {};
 
-// G vector of the half-spectrum point (ix, iy, kz) in the accumulator
-// precision A, from the per-axis reciprocal spacings (no divisions).
+template <typename PR> struct KT {
+    typedef PR T;          // stored real
+    typedef cplx<PR> C;    // stored complex
+    typedef cplx<PR> CC;   // computed complex (shared memory)
+    typedef PR R;          // computed real (and per-thread accumulator)
+};
+template <> struct KT<DD> {
+    typedef double T;
+    typedef double2 C;
+    typedef ff::cf2 CC;
+    typedef ff::f2 R;
+};
+
+template <typename PR> constexpr bool is_dd() { return std::is_same<PR, DD>::value; }
+
+// loads and stores between the stored and the computed types; constants
+template <typename PR> __device__ __forceinline__ typename KT<PR>::R ldr(typename KT<PR>::T x) { return x; }
+template <> __device__ __forceinline__ ff::f2 ldr<DD>(double x) { return ff::split_int(x); }
+template <typename PR> __device__ __forceinline__ typename KT<PR>::T str(typename KT<PR>::R x) { return x; }
+template <> __device__ __forceinline__ double str<DD>(ff::f2 x) { return ff::to_double(x); }
+template <typename PR> __device__ __forceinline__ typename KT<PR>::CC ldc(typename KT<PR>::C v) { return v; }
+template <> __device__ __forceinline__ ff::cf2 ldc<DD>(double2 v)
+{
+    ff::cf2 r;
+    r.x = ff::split_int(v.x);
+    r.y = ff::split_int(v.y);
+    return r;
+}
+template <typename PR> __device__ __forceinline__ typename KT<PR>::C stc(typename KT<PR>::CC v) { return v; }
+template <> __device__ __forceinline__ double2 stc<DD>(ff::cf2 v)
+{
+    return make_double2(ff::to_double(v.x), ff::to_double(v.y));
+}
+// grid constant in the computed type (binary64 value d, its binary32 copy f)
+template <typename PR> __device__ __forceinline__ typename KT<PR>::R gcst(double d, float f) { return gsel<PR>(d, f); }
+template <> __device__ __forceinline__ ff::f2 gcst<DD>(double d, float) { return ff::f2(d); }
+// scalar read in binary64 (double-float: correctly rounded split)
+template <typename PR> __device__ __forceinline__ typename KT<PR>::R scal(typename KT<PR>::T x) { return x; }
+template <> __device__ __forceinline__ ff::f2 scal<DD>(double x) { return ff::f2(x); }
+
+// Block totals of per-thread accumulators (double-float ones are converted
+// to binary64 first).
+template <int NQ, typename PR> __device__ __forceinline__ void block_total(typename KT<PR>::R *acc, double *tot)
+{
+    if constexpr (is_dd<PR>()) {
+        double d[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) d[q] = ff::to_double(acc[q]);
+        block_sum<NQ, double>(d, tot);
+    } else {
+        block_sum<NQ, typename AccT<PR>::type>(acc, tot);
+    }
+}
+
+// G vector of the half-spectrum point (ix, iy, kz) in the computed
+// precision, from the per-axis reciprocal spacings (no divisions).
 template <typename A> struct Gk {
     A gx, gy, gz, g2;  // G with +n/2 on Nyquist planes
     A dx, dy, dz;      // first-derivative multipliers (0 on the own-axis Nyquist plane)
@@ -42,25 +104,45 @@ __device__ __forceinline__ Gk<A> gvec(const GridInfo &g, A bx, A by, A bz, int i
     return r;
 }
 
-template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+// Pointwise functional of the double-float z passes: the double-float
+// routine, and binary64 outside its domain.  n and gr[3] in double-float.
+__device__ __forceinline__ PwF2 pw_dd(const FuncParams &fp, const double *__restrict__ tab, ff::f2 tcoef,
+                                      double temp, ff::f2 n, const ff::f2 *gr, int xc)
+{
+    PwF2 o;
+    if (pw_core_f2(fp, reinterpret_cast<const ff::f2 *>(tab + kTfSize), tcoef, n, gr, xc, o)) return o;
+    const double nd = ff::to_double(n);
+    const double gd[3] = {ff::to_double(gr[0]), ff::to_double(gr[1]), ff::to_double(gr[2])};
+    PwOut<double> b = pw_point_native<double>(fp, tab, temp, nd, gd[0] * gd[0] + gd[1] * gd[1] + gd[2] * gd[2], xc);
+    o.f = ff::f2(b.f);
+    o.ts = ff::f2(b.ts);
+    o.dfdn = ff::f2(b.dfdn);
+    o.eps = ff::f2(b.eps);
+    o.vxc = ff::f2(b.vxc);
+    for (int a = 0; a < 3; ++a) o.w[a] = ff::f2(b.wc * gd[a]);
+    return o;
+}
 
 // ------------------------------------------------------------------ z pass
 // Pair p of a block holds real lines 2p (real part) and 2p+1 (imaginary part).
 
-template <typename T, int MODE>
-__global__ void k_zfwd(GridInfo g, FftAxis az, int P, const T *__restrict__ in,
-                       const T *__restrict__ phi, const T *__restrict__ dhat, T c, T s,
-                       const void *__restrict__ cs, T *__restrict__ phit,
-                       cplx<T> *__restrict__ out)
+template <typename PR, int MODE>
+__global__ void k_zfwd(GridInfo g, FftAxis az, int P, const typename KT<PR>::T *__restrict__ in,
+                       const typename KT<PR>::T *__restrict__ phi, const typename KT<PR>::T *__restrict__ dhat,
+                       typename KT<PR>::T c, typename KT<PR>::T s, const void *__restrict__ cs,
+                       typename KT<PR>::T *__restrict__ phit, typename KT<PR>::C *__restrict__ out)
 {
+    typedef typename KT<PR>::T T;
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::CC CC;
     if (MODE == 2 && cs != nullptr) {   // rotation angle (two T) from the device CG state
         c = reinterpret_cast<const T *>(cs)[0];
         s = reinterpret_cast<const T *>(cs)[1];
     }
-    typedef cplx<T> C;
+    const R cr = scal<PR>(c), sr = scal<PR>(s);
     extern __shared__ __align__(16) unsigned char smraw[];
-    C *A = reinterpret_cast<C *>(smraw);
-    C *B = A + P * g.nz;
+    CC *A = reinterpret_cast<CC *>(smraw);
+    CC *B = A + P * g.nz;
     const long long npairs = (long long)g.nx * g.ny / 2;
     const long long p0 = (long long)blockIdx.x * P;
     const int nl = (int)min((long long)P, npairs - p0);
@@ -68,134 +150,157 @@ __global__ void k_zfwd(GridInfo g, FftAxis az, int P, const T *__restrict__ in,
     const long long base = 2 * p0 * nz;
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
         const int line = i / nz, e = i - line * nz;
-        T val;
+        R val;
         if (MODE == 0) {
-            val = in[base + i];
+            val = ldr<PR>(in[base + i]);
         } else if (MODE == 1) {
-            T ph = phi[base + i];
+            R ph = ldr<PR>(phi[base + i]);
             val = ph * ph;
         } else {
-            T ph = c * phi[base + i] + s * dhat[base + i];
-            phit[base + i] = ph;
+            R ph = cr * ldr<PR>(phi[base + i]) + sr * ldr<PR>(dhat[base + i]);
+            phit[base + i] = str<PR>(ph);
             val = ph * ph;
         }
-        T *dstp = reinterpret_cast<T *>(&A[(line >> 1) * nz + e]);
+        R *dstp = reinterpret_cast<R *>(&A[(line >> 1) * nz + e]);
         dstp[line & 1] = val;
     }
     __syncthreads();
-    C *X = fft_lines<C, false>(A, B, az, nl, nz, 1, false);
+    CC *X = fft_lines<CC, false>(A, B, az, nl, nz, 1, false);
     const long long obase = 2 * p0 * K;
+    const R half = R(0.5), mhalf = R(-0.5);
     for (int i = threadIdx.x; i < 2 * nl * K; i += blockDim.x) {
         const int line = i / K, k = i - line * K;
-        const C *row = X + (line >> 1) * nz;
-        C z = row[k], zc = cconj(row[k == 0 ? 0 : nz - k]);
-        C r = (line & 1) ? cmk<C>(T(0.5) * (z.y - zc.y), T(-0.5) * (z.x - zc.x))
-                         : cmk<C>(T(0.5) * (z.x + zc.x), T(0.5) * (z.y + zc.y));
-        out[obase + i] = r;
+        const CC *row = X + (line >> 1) * nz;
+        CC z = row[k], zc = cconj(row[k == 0 ? 0 : nz - k]);
+        CC r = (line & 1) ? cmk<CC>(half * (z.y - zc.y), mhalf * (z.x - zc.x))
+                          : cmk<CC>(half * (z.x + zc.x), half * (z.y + zc.y));
+        out[obase + i] = stc<PR>(r);
     }
 }
 
 // Build the pair-packed complex line C_k = A_k + i B_k (k <= nz/2) and its
 // Hermitian completion C_{nz-k} = conj(A_k) + i conj(B_k); the imaginary
 // parts of A_0, A_{nz/2} (and B's) are dropped, as a real inverse does.
-template <typename C>
-__device__ __forceinline__ void pack_c2r(const C *__restrict__ src, long long obase, int nl, int nz,
-                                         int K, C *dst)
+template <typename PR>
+__device__ __forceinline__ void pack_c2r(const typename KT<PR>::C *__restrict__ src, long long obase, int nl,
+                                         int nz, int K, typename KT<PR>::CC *dst)
 {
-    typedef decltype(C::x) T;
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::CC CC;
     for (int i = threadIdx.x; i < nl * K; i += blockDim.x) {
         const int p = i / K, k = i - p * K;
-        C a = src[obase + (2 * p) * (long long)K + k];
-        C b = src[obase + (2 * p + 1) * (long long)K + k];
+        CC a = ldc<PR>(src[obase + (2 * p) * (long long)K + k]);
+        CC b = ldc<PR>(src[obase + (2 * p + 1) * (long long)K + k]);
         if (k == 0 || 2 * k == nz) {
-            a.y = T(0);
-            b.y = T(0);
+            a.y = R(0);
+            b.y = R(0);
         }
-        dst[p * nz + k] = cmk<C>(a.x - b.y, a.y + b.x);
-        if (k != 0 && 2 * k != nz) dst[p * nz + nz - k] = cmk<C>(a.x + b.y, b.x - a.y);
+        dst[p * nz + k] = cmk<CC>(a.x - b.y, a.y + b.x);
+        if (k != 0 && 2 * k != nz) dst[p * nz + nz - k] = cmk<CC>(a.x + b.y, b.x - a.y);
     }
 }
 
 // Unpack a forward-transformed pair-packed line into two half spectra.
-template <typename C>
-__device__ __forceinline__ void unpack_r2c(const C *X, long long obase, int nl, int nz, int K,
-                                           C *__restrict__ out)
+template <typename PR>
+__device__ __forceinline__ void unpack_r2c(const typename KT<PR>::CC *X, long long obase, int nl, int nz, int K,
+                                           typename KT<PR>::C *__restrict__ out)
 {
-    typedef decltype(C::x) T;
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::CC CC;
+    const R half = R(0.5), mhalf = R(-0.5);
     for (int i = threadIdx.x; i < 2 * nl * K; i += blockDim.x) {
         const int line = i / K, k = i - line * K;
-        const C *row = X + (line >> 1) * nz;
-        C z = row[k], zc = cconj(row[k == 0 ? 0 : nz - k]);
-        out[obase + i] = (line & 1) ? cmk<C>(T(0.5) * (z.y - zc.y), T(-0.5) * (z.x - zc.x))
-                                    : cmk<C>(T(0.5) * (z.x + zc.x), T(0.5) * (z.y + zc.y));
+        const CC *row = X + (line >> 1) * nz;
+        CC z = row[k], zc = cconj(row[k == 0 ? 0 : nz - k]);
+        out[obase + i] = stc<PR>((line & 1) ? cmk<CC>(half * (z.y - zc.y), mhalf * (z.x - zc.x))
+                                            : cmk<CC>(half * (z.x + zc.x), half * (z.y + zc.y)));
     }
 }
 
 // Fused GGA stage: C2R of grad n (3 fields), pointwise functional + XC,
 // R2C of W (3 fields, written over grad n).  Partials: F_s, TS, F_xc,
 // sum(n df/dn - f), sum W.grad n, sum n(v_xc - eps_xc).
-template <typename T>
-__global__ void k_zgga(GridInfo g, FftAxis az, int P, cplx<T> *__restrict__ g0,
-                       cplx<T> *__restrict__ g1, cplx<T> *__restrict__ g2,
-                       const T *__restrict__ phit, T temp, FuncParams fp,
-                       const T *__restrict__ tab, int xc, T *__restrict__ vpart,
+template <typename PR>
+__global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__restrict__ g0,
+                       typename KT<PR>::C *__restrict__ g1, typename KT<PR>::C *__restrict__ g2,
+                       const typename KT<PR>::T *__restrict__ phit, typename KT<PR>::T temp, FuncParams fp,
+                       const typename KT<PR>::T *__restrict__ tab, int xc, typename KT<PR>::T *__restrict__ vpart,
                        double *__restrict__ part)
 {
-    typedef cplx<T> C;
+    typedef typename KT<PR>::T T;
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::C C;
+    typedef typename KT<PR>::CC CC;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nz = g.nz, K = g.K;
-    C *buf[4];
-    for (int q = 0; q < 4; ++q) buf[q] = reinterpret_cast<C *>(smraw) + q * P * nz;
+    CC *buf[4];
+    for (int q = 0; q < 4; ++q) buf[q] = reinterpret_cast<CC *>(smraw) + q * P * nz;
     const long long npairs = (long long)g.nx * g.ny / 2;
     const long long p0 = (long long)blockIdx.x * P;
     const int nl = (int)min((long long)P, npairs - p0);
     const long long obase = 2 * p0 * K;
     const long long rbase = 2 * p0 * nz;
     C *spec[3] = {g0, g1, g2};
-    C *res[3];
-    C *scratch = buf[3];
+    CC *res[3];
+    CC *scratch = buf[3];
     for (int a = 0; a < 3; ++a) {
-        pack_c2r(spec[a], obase, nl, nz, K, buf[a]);
+        pack_c2r<PR>(spec[a], obase, nl, nz, K, buf[a]);
         __syncthreads();
-        res[a] = fft_lines<C, true>(buf[a], scratch, az, nl, nz, 1, false);
+        res[a] = fft_lines<CC, true>(buf[a], scratch, az, nl, nz, 1, false);
         if (res[a] == scratch) scratch = buf[a];
     }
-    typedef typename AccT<T>::type A;
-    A acc[6] = {0, 0, 0, 0, 0, 0};
-    const ff::f2 tcoef = ff::from_double(2.0 / OF_K23 * (double)temp);
+    R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
         const int line = i / nz, e = i - line * nz;
         const int p = line >> 1, hi = line & 1;
-        T gr[3];
+        R gr[3];
         for (int a = 0; a < 3; ++a)   // each thread owns one component of the packed pair
-            gr[a] = reinterpret_cast<const T *>(&res[a][p * nz + e])[hi];
-        T ph = phit[rbase + i];
-        T n = ph * ph;
-        T gg = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
-        PwOut<T> o = pw_point<T>(fp, tab, tcoef, temp, n, gg, xc);
-        const T eps = o.eps, vxc = o.vxc;
-        vpart[rbase + i] = o.dfdn + vxc;
-        acc[0] += (A)o.f;
-        acc[1] += (A)o.ts;
-        acc[2] += (A)(n * eps);
-        acc[3] += (A)(n * o.dfdn - o.f);
-        acc[4] += (A)(o.wc * gg);
-        acc[5] += (A)(n * (vxc - eps));
-        for (int a = 0; a < 3; ++a) {
-            T *d = reinterpret_cast<T *>(&res[a][p * nz + e]);
-            d[hi] = o.wc * gr[a];
+            gr[a] = reinterpret_cast<const R *>(&res[a][p * nz + e])[hi];
+        if constexpr (is_dd<PR>()) {
+            const ff::f2 tcoef(2.0 / OF_K23 * (double)temp);
+            const R ph = ldr<PR>(phit[rbase + i]);
+            const R n = ph * ph;
+            const PwF2 o = pw_dd(fp, tab, tcoef, (double)temp, n, gr, xc);
+            vpart[rbase + i] = str<PR>(o.dfdn + o.vxc);
+            acc[0] += o.f;
+            acc[1] += o.ts;
+            acc[2] += n * o.eps;
+            acc[3] += n * o.dfdn - o.f;
+            acc[4] += o.w[0] * gr[0] + o.w[1] * gr[1] + o.w[2] * gr[2];
+            acc[5] += n * (o.vxc - o.eps);
+            for (int a = 0; a < 3; ++a) {
+                R *d = reinterpret_cast<R *>(&res[a][p * nz + e]);
+                d[hi] = o.w[a];
+            }
+        } else {
+            T ph = phit[rbase + i];
+            T n = ph * ph;
+            T gg = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+            PwOut<T> o = pw_point_native<T>(fp, tab, temp, n, gg, xc);
+            const T eps = o.eps, vxc = o.vxc;
+            vpart[rbase + i] = o.dfdn + vxc;
+            acc[0] += o.f;
+            acc[1] += o.ts;
+            acc[2] += n * eps;
+            acc[3] += n * o.dfdn - o.f;
+            acc[4] += o.wc * gg;
+            acc[5] += n * (vxc - eps);
+            for (int a = 0; a < 3; ++a) {
+                T *d = reinterpret_cast<T *>(&res[a][p * nz + e]);
+                d[hi] = o.wc * gr[a];
+            }
         }
     }
     __syncthreads();
     // scratch is the one buffer not holding a field
     for (int a = 0; a < 3; ++a) {
-        C *X = fft_lines<C, false>(res[a], scratch, az, nl, nz, 1, false);
-        unpack_r2c(X, obase, nl, nz, K, spec[a]);
+        CC *X = fft_lines<CC, false>(res[a], scratch, az, nl, nz, 1, false);
+        unpack_r2c<PR>(X, obase, nl, nz, K, spec[a]);
         __syncthreads();
         if (X == scratch) scratch = res[a];
     }
     double tot[6];
-    block_sum<6, A>(acc, tot);
+    block_total<6, PR>(acc, tot);
     if (threadIdx.x == 0)
         for (int q = 0; q < 6; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
 }
@@ -204,63 +309,72 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, cplx<T> *__restrict__ g0,
 // pointwise functional is evaluated here and added.  Partials (ftTF only
 // for the first six): F_s, TS, F_xc, sum(n df/dn - f), 0, sum n(v_xc - eps),
 // then sum phi^2 v, sum phi^2, sum 2 phi v dphi/dtheta.
-template <typename T, bool FTTF>
-__global__ void k_zfinal(GridInfo g, FftAxis az, int P, const cplx<T> *__restrict__ dspec,
-                         const T *__restrict__ vpart, const T *__restrict__ phit,
-                         const T *__restrict__ phi, const T *__restrict__ dhat, T c, T s,
-                         const void *__restrict__ cs, T temp, FuncParams fp,
-                         const T *__restrict__ tab, int xc, T *__restrict__ vout,
-                         double *__restrict__ part)
+template <typename PR, bool FTTF>
+__global__ void k_zfinal(GridInfo g, FftAxis az, int P, const typename KT<PR>::C *__restrict__ dspec,
+                         const typename KT<PR>::T *__restrict__ vpart, const typename KT<PR>::T *__restrict__ phit,
+                         const typename KT<PR>::T *__restrict__ phi, const typename KT<PR>::T *__restrict__ dhat,
+                         typename KT<PR>::T c, typename KT<PR>::T s, const void *__restrict__ cs,
+                         typename KT<PR>::T temp, FuncParams fp, const typename KT<PR>::T *__restrict__ tab, int xc,
+                         typename KT<PR>::T *__restrict__ vout, double *__restrict__ part)
 {
+    typedef typename KT<PR>::T T;
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::CC CC;
     if (cs != nullptr) {
         c = reinterpret_cast<const T *>(cs)[0];
         s = reinterpret_cast<const T *>(cs)[1];
     }
-    typedef cplx<T> C;
+    const R cr = scal<PR>(c), sr = scal<PR>(s);
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nz = g.nz, K = g.K;
-    C *A = reinterpret_cast<C *>(smraw);
-    C *B = A + P * nz;
+    CC *A = reinterpret_cast<CC *>(smraw);
+    CC *B = A + P * nz;
     const long long npairs = (long long)g.nx * g.ny / 2;
     const long long p0 = (long long)blockIdx.x * P;
     const int nl = (int)min((long long)P, npairs - p0);
     const long long obase = 2 * p0 * K;
     const long long rbase = 2 * p0 * nz;
-    pack_c2r(dspec, obase, nl, nz, K, A);
+    pack_c2r<PR>(dspec, obase, nl, nz, K, A);
     __syncthreads();
-    C *X = fft_lines<C, true>(A, B, az, nl, nz, 1, false);
-    typedef typename AccT<T>::type Ac;
-    Ac acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    const ff::f2 tcoef = ff::from_double(2.0 / OF_K23 * (double)temp);
+    CC *X = fft_lines<CC, true>(A, B, az, nl, nz, 1, false);
+    R acc[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
         const int line = i / nz, e = i - line * nz;
-        C d = X[(line >> 1) * nz + e];
-        T dr = (line & 1) ? d.y : d.x;
-        T ph = phit[rbase + i];
-        T n = ph * ph;
-        T v;
+        CC d = X[(line >> 1) * nz + e];
+        R dr = (line & 1) ? d.y : d.x;
+        R ph = ldr<PR>(phit[rbase + i]);
+        R n = ph * ph;
+        R v;
         if (FTTF) {
-            PwOut<T> o = pw_point<T>(fp, tab, tcoef, temp, n, T(0), xc);
-            const T eps = o.eps, vxc = o.vxc;
-            v = o.dfdn + vxc + dr;
-            acc[0] += (Ac)o.f;
-            acc[1] += (Ac)o.ts;
-            acc[2] += (Ac)(n * eps);
-            acc[3] += (Ac)(n * o.dfdn - o.f);
-            acc[5] += (Ac)(n * (vxc - eps));
+            R f, ts, dfdn, eps, vxc;
+            if constexpr (is_dd<PR>()) {
+                const ff::f2 tcoef(2.0 / OF_K23 * (double)temp);
+                const R gz[3] = {R(0), R(0), R(0)};
+                const PwF2 o = pw_dd(fp, tab, tcoef, (double)temp, n, gz, xc);
+                f = o.f, ts = o.ts, dfdn = o.dfdn, eps = o.eps, vxc = o.vxc;
+            } else {
+                PwOut<T> o = pw_point_native<T>(fp, tab, temp, n, T(0), xc);
+                f = o.f, ts = o.ts, dfdn = o.dfdn, eps = o.eps, vxc = o.vxc;
+            }
+            v = dfdn + vxc + dr;
+            acc[0] += f;
+            acc[1] += ts;
+            acc[2] += n * eps;
+            acc[3] += n * dfdn - f;
+            acc[5] += n * (vxc - eps);
         } else {
-            v = vpart[rbase + i] + dr;
+            v = ldr<PR>(vpart[rbase + i]) + dr;
         }
-        vout[rbase + i] = v;
-        acc[6] += (Ac)(n * v);
-        acc[7] += (Ac)n;
+        vout[rbase + i] = str<PR>(v);
+        acc[6] += n * v;
+        acc[7] += n;
         if (dhat != nullptr) {
-            T dphi = -s * phi[rbase + i] + c * dhat[rbase + i];
-            acc[8] += Ac(2) * (Ac)(ph * v) * (Ac)dphi;
+            R dphi = -sr * ldr<PR>(phi[rbase + i]) + cr * ldr<PR>(dhat[rbase + i]);
+            acc[8] += R(2) * (ph * v) * dphi;
         }
     }
     double tot[9];
-    block_sum<9, Ac>(acc, tot);
+    block_total<9, PR>(acc, tot);
     if (threadIdx.x == 0)
         for (int q = 0; q < 9; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
 }
@@ -294,95 +408,99 @@ __device__ __forceinline__ ColTile col_tile(const GridInfo &g, bool xaxis)
     return t;
 }
 
-template <typename C>
-__device__ __forceinline__ void load_tile(const C *__restrict__ src, const ColTile &t, int nrows, C *dst)
+template <typename PR>
+__device__ __forceinline__ void load_tile(const typename KT<PR>::C *__restrict__ src, const ColTile &t, int nrows,
+                                          typename KT<PR>::CC *dst)
 {
     for (int i = threadIdx.x; i < nrows * t.tk; i += blockDim.x) {
         const int r = i / t.tk, c = i - r * t.tk;
-        if (c < t.ncol) dst[i] = src[t.base + r * t.rstride + c];
+        if (c < t.ncol) dst[i] = ldc<PR>(src[t.base + r * t.rstride + c]);
     }
 }
 
-template <typename C>
-__device__ __forceinline__ void store_tile(C *__restrict__ dst, const ColTile &t, int nrows, const C *src)
+template <typename PR>
+__device__ __forceinline__ void store_tile(typename KT<PR>::C *__restrict__ dst, const ColTile &t, int nrows,
+                                           const typename KT<PR>::CC *src)
 {
     for (int i = threadIdx.x; i < nrows * t.tk; i += blockDim.x) {
         const int r = i / t.tk, c = i - r * t.tk;
-        if (c < t.ncol) dst[t.base + r * t.rstride + c] = src[i];
+        if (c < t.ncol) dst[t.base + r * t.rstride + c] = stc<PR>(src[i]);
     }
 }
 
-template <typename T, bool INV>
-__global__ void k_ypass(GridInfo g, FftAxis ay, cplx<T> *__restrict__ data, long long fstride)
+template <typename PR, bool INV>
+__global__ void k_ypass(GridInfo g, FftAxis ay, typename KT<PR>::C *__restrict__ data, long long fstride)
 {
-    typedef cplx<T> C;
+    typedef typename KT<PR>::C C;
+    typedef typename KT<PR>::CC CC;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C *A = reinterpret_cast<C *>(smraw);
-    C *B = A + g.ny * g.tk;
+    CC *A = reinterpret_cast<CC *>(smraw);
+    CC *B = A + g.ny * g.tk;
     ColTile t = col_tile(g, false);
     C *f = data + blockIdx.y * fstride;
-    load_tile(f, t, g.ny, A);
+    load_tile<PR>(f, t, g.ny, A);
     __syncthreads();
-    C *X = fft_lines<C, INV>(A, B, ay, t.ncol, 1, g.tk, true);
-    store_tile(f, t, g.ny, X);
+    CC *X = fft_lines<CC, INV>(A, B, ay, t.ncol, 1, g.tk, true);
+    store_tile<PR>(f, t, g.ny, X);
 }
 
 // x pass, gradient variant: forward x -> n(G) (stored), energies, then
 // i D_a n(G) inverse-x for a = x, y, z.  Partials: E_H, E_loc, P_loc.
-template <typename T>
-__global__ void k_xgrad(GridInfo g, FftAxis ax, cplx<T> *__restrict__ nspec,
-                        const cplx<T> *__restrict__ vext, cplx<T> *__restrict__ g0,
-                        cplx<T> *__restrict__ g1, cplx<T> *__restrict__ g2,
+template <typename PR>
+__global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ nspec,
+                        const typename KT<PR>::C *__restrict__ vext, typename KT<PR>::C *__restrict__ g0,
+                        typename KT<PR>::C *__restrict__ g1, typename KT<PR>::C *__restrict__ g2,
                         double *__restrict__ part)
 {
-    typedef cplx<T> C;
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::C C;
+    typedef typename KT<PR>::CC CC;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx;
-    C *A = reinterpret_cast<C *>(smraw);
-    C *B = A + nx * g.tk;
-    C *N = B + nx * g.tk;
+    CC *A = reinterpret_cast<CC *>(smraw);
+    CC *B = A + nx * g.tk;
+    CC *N = B + nx * g.tk;
     ColTile t = col_tile(g, true);
-    load_tile(nspec, t, nx, A);
+    load_tile<PR>(nspec, t, nx, A);
     __syncthreads();
-    C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, g.tk, true);
-    typedef typename AccT<T>::type Ac;
-    const Ac bx = gsel<Ac>(g.bx, g.bxf), by = gsel<Ac>(g.by, g.byf), bz = gsel<Ac>(g.bz, g.bzf);
-    const Ac hr = gsel<Ac>(g.hr, g.hrf);
-    const T invN = gsel<T>(g.invN, g.invNf);
-    Ac acc[3] = {0, 0, 0};     // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
+    CC *X = fft_lines<CC, false>(A, B, ax, t.ncol, 1, g.tk, true);
+    const R bx = gcst<PR>(g.bx, g.bxf), by = gcst<PR>(g.by, g.byf), bz = gcst<PR>(g.bz, g.bzf);
+    const R hr = gcst<PR>(g.hr, g.hrf);
+    const R invN = gcst<PR>(g.invN, g.invNf);
+    R acc[3] = {R(0), R(0), R(0)};   // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i / g.tk, c = i - r * g.tk;
         if (c >= t.ncol) continue;
-        C nG = cscale(X[i], invN);
+        CC nG = cscale(X[i], invN);
         N[i] = nG;
-        Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
-        if (k.g2 > Ac(0)) {
-            C ve = vext[t.base + r * t.rstride + c];
-            Ac n2 = (Ac)nG.x * nG.x + (Ac)nG.y * nG.y;
-            Ac re = (Ac)nG.x * ve.x + (Ac)nG.y * ve.y;
+        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
+        if (k.g2 > R(0)) {
+            CC ve = ldc<PR>(vext[t.base + r * t.rstride + c]);
+            R n2 = nG.x * nG.x + nG.y * nG.y;
+            R re = nG.x * ve.x + nG.y * ve.y;
             acc[0] += k.w * n2 / k.g2;
             acc[1] += k.w * re;
-            acc[2] += k.w * re * (Ac(1) - hr * k.g2);
+            acc[2] += k.w * re * (R(1) - hr * k.g2);
         }
     }
     __syncthreads();
-    store_tile(nspec, t, nx, N);
+    store_tile<PR>(nspec, t, nx, N);
     C *outs[3] = {g0, g1, g2};
     for (int a = 0; a < 3; ++a) {
         for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
             const int r = i / g.tk, c = i - r * g.tk;
-            Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + min(c, t.ncol - 1));
-            T d = T(a == 0 ? k.dx : (a == 1 ? k.dy : k.dz));
-            C v = N[i];
-            A[i] = cmk<C>(-d * v.y, d * v.x);      // i D_a n(G)
+            Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + min(c, t.ncol - 1));
+            R d = a == 0 ? k.dx : (a == 1 ? k.dy : k.dz);
+            CC v = N[i];
+            A[i] = cmk<CC>(-d * v.y, d * v.x);      // i D_a n(G)
         }
         __syncthreads();
-        C *Y = fft_lines<C, true>(A, B, ax, t.ncol, 1, g.tk, true);
-        store_tile(outs[a], t, nx, Y);
+        CC *Y = fft_lines<CC, true>(A, B, ax, t.ncol, 1, g.tk, true);
+        store_tile<PR>(outs[a], t, nx, Y);
         __syncthreads();
     }
     double tot[3];
-    block_sum<3, Ac>(acc, tot);
+    block_total<3, PR>(acc, tot);
     if (threadIdx.x == 0) {
         // E_H = (Omega/2) sum 4 pi |n|^2/G^2, E_loc = Omega sum Re(n* v_ext),
         // P_loc = (1/3) sum Re(n* v_ext)(1 - G^2 rc^2/2)
@@ -394,53 +512,53 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, cplx<T> *__restrict__ nspec,
 
 // x pass, ftTF variant: forward x -> energies -> v_HL(G) = 4 pi n/G^2 + v_ext
 // inverse-x, written over the spectrum.  If keep_n, n(G) is also stored in nG_out.
-template <typename T>
-__global__ void k_xhl(GridInfo g, FftAxis ax, cplx<T> *__restrict__ spec,
-                      const cplx<T> *__restrict__ vext, cplx<T> *__restrict__ nG_out,
+template <typename PR>
+__global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ spec,
+                      const typename KT<PR>::C *__restrict__ vext, typename KT<PR>::C *__restrict__ nG_out,
                       int inverse, double *__restrict__ part)
 {
-    typedef cplx<T> C;
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::CC CC;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx;
-    C *A = reinterpret_cast<C *>(smraw);
-    C *B = A + nx * g.tk;
+    CC *A = reinterpret_cast<CC *>(smraw);
+    CC *B = A + nx * g.tk;
     ColTile t = col_tile(g, true);
-    load_tile(spec, t, nx, A);
+    load_tile<PR>(spec, t, nx, A);
     __syncthreads();
-    C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, g.tk, true);
-    typedef typename AccT<T>::type Ac;
-    const Ac bx = gsel<Ac>(g.bx, g.bxf), by = gsel<Ac>(g.by, g.byf), bz = gsel<Ac>(g.bz, g.bzf);
-    const Ac hr = gsel<Ac>(g.hr, g.hrf);
-    const Ac fourpi = gsel<Ac>(12.566370614359172954, 12.566370614359172954f);
-    const T invN = gsel<T>(g.invN, g.invNf);
-    Ac acc[3] = {0, 0, 0};
+    CC *X = fft_lines<CC, false>(A, B, ax, t.ncol, 1, g.tk, true);
+    const R bx = gcst<PR>(g.bx, g.bxf), by = gcst<PR>(g.by, g.byf), bz = gcst<PR>(g.bz, g.bzf);
+    const R hr = gcst<PR>(g.hr, g.hrf);
+    const R fourpi = gcst<PR>(12.566370614359172954, 12.566370614359172954f);
+    const R invN = gcst<PR>(g.invN, g.invNf);
+    R acc[3] = {R(0), R(0), R(0)};
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i / g.tk, c = i - r * g.tk;
         if (c >= t.ncol) continue;
-        C nG = cscale(X[i], invN);
-        Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
-        C ve = vext[t.base + r * t.rstride + c];
-        C out = cmk<C>(T(0), T(0));
-        if (k.g2 > Ac(0)) {
-            Ac n2 = (Ac)nG.x * nG.x + (Ac)nG.y * nG.y;
-            Ac re = (Ac)nG.x * ve.x + (Ac)nG.y * ve.y;
+        CC nG = cscale(X[i], invN);
+        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
+        CC ve = ldc<PR>(vext[t.base + r * t.rstride + c]);
+        CC out = cmk<CC>(R(0), R(0));
+        if (k.g2 > R(0)) {
+            R n2 = nG.x * nG.x + nG.y * nG.y;
+            R re = nG.x * ve.x + nG.y * ve.y;
             acc[0] += k.w * n2 / k.g2;
             acc[1] += k.w * re;
-            acc[2] += k.w * re * (Ac(1) - hr * k.g2);
-            T kh = T(fourpi / k.g2);
-            out = cmk<C>(kh * nG.x + ve.x, kh * nG.y + ve.y);
+            acc[2] += k.w * re * (R(1) - hr * k.g2);
+            R kh = fourpi / k.g2;
+            out = cmk<CC>(kh * nG.x + ve.x, kh * nG.y + ve.y);
         }
-        if (nG_out != nullptr) nG_out[t.base + r * t.rstride + c] = nG;
+        if (nG_out != nullptr) nG_out[t.base + r * t.rstride + c] = stc<PR>(nG);
         X[i] = out;
     }
     __syncthreads();
     if (inverse) {
-        C *other = (X == A) ? B : A;
-        C *Y = fft_lines<C, true>(X, other, ax, t.ncol, 1, g.tk, true);
-        store_tile(spec, t, nx, Y);
+        CC *other = (X == A) ? B : A;
+        CC *Y = fft_lines<CC, true>(X, other, ax, t.ncol, 1, g.tk, true);
+        store_tile<PR>(spec, t, nx, Y);
     }
     double tot[3];
-    block_sum<3, Ac>(acc, tot);
+    block_total<3, PR>(acc, tot);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = 0.5 * g.omega * 12.566370614359172954 * tot[0];
         part[(size_t)gridDim.x + blockIdx.x] = g.omega * tot[1];
@@ -450,52 +568,53 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, cplx<T> *__restrict__ spec,
 
 // x pass, divergence variant: D(G) = v_H(G) + v_ext(G) - sum_a i D_a W_a(G)
 // from n(G) and the y-transformed W_a; inverse-x result written over W_0.
-template <typename T>
-__global__ void k_xdiv(GridInfo g, FftAxis ax, const cplx<T> *__restrict__ nG,
-                       const cplx<T> *__restrict__ vext, cplx<T> *__restrict__ w0,
-                       const cplx<T> *__restrict__ w1, const cplx<T> *__restrict__ w2)
+template <typename PR>
+__global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restrict__ nG,
+                       const typename KT<PR>::C *__restrict__ vext, typename KT<PR>::C *__restrict__ w0,
+                       const typename KT<PR>::C *__restrict__ w1, const typename KT<PR>::C *__restrict__ w2)
 {
-    typedef cplx<T> C;
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::C C;
+    typedef typename KT<PR>::CC CC;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx;
-    C *A = reinterpret_cast<C *>(smraw);
-    C *B = A + nx * g.tk;
-    C *D = B + nx * g.tk;
+    CC *A = reinterpret_cast<CC *>(smraw);
+    CC *B = A + nx * g.tk;
+    CC *D = B + nx * g.tk;
     ColTile t = col_tile(g, true);
-    typedef typename AccT<T>::type Ac;
-    const Ac bx = gsel<Ac>(g.bx, g.bxf), by = gsel<Ac>(g.by, g.byf), bz = gsel<Ac>(g.bz, g.bzf);
-    const Ac fourpi = gsel<Ac>(12.566370614359172954, 12.566370614359172954f);
-    const T invN = gsel<T>(g.invN, g.invNf);
+    const R bx = gcst<PR>(g.bx, g.bxf), by = gcst<PR>(g.by, g.byf), bz = gcst<PR>(g.bz, g.bzf);
+    const R fourpi = gcst<PR>(12.566370614359172954, 12.566370614359172954f);
+    const R invN = gcst<PR>(g.invN, g.invNf);
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i / g.tk, c = i - r * g.tk;
         if (c >= t.ncol) continue;
-        Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
-        C out = cmk<C>(T(0), T(0));
-        if (k.g2 > Ac(0)) {
-            C n = nG[t.base + r * t.rstride + c];
-            C ve = vext[t.base + r * t.rstride + c];
-            T kh = T(fourpi / k.g2);
-            out = cmk<C>(kh * n.x + ve.x, kh * n.y + ve.y);
+        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
+        CC out = cmk<CC>(R(0), R(0));
+        if (k.g2 > R(0)) {
+            CC n = ldc<PR>(nG[t.base + r * t.rstride + c]);
+            CC ve = ldc<PR>(vext[t.base + r * t.rstride + c]);
+            R kh = fourpi / k.g2;
+            out = cmk<CC>(kh * n.x + ve.x, kh * n.y + ve.y);
         }
         D[i] = out;
     }
     const C *ws[3] = {w0, w1, w2};
     for (int a = 0; a < 3; ++a) {
-        load_tile(ws[a], t, nx, A);
+        load_tile<PR>(ws[a], t, nx, A);
         __syncthreads();
-        C *X = fft_lines<C, false>(A, B, ax, t.ncol, 1, g.tk, true);
+        CC *X = fft_lines<CC, false>(A, B, ax, t.ncol, 1, g.tk, true);
         for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
             const int r = i / g.tk, c = i - r * g.tk;
             if (c >= t.ncol) continue;
-            Gk<Ac> k = gvec<Ac>(g, bx, by, bz, r, t.outer, t.kz0 + c);
-            T d = T(a == 0 ? k.dx : (a == 1 ? k.dy : k.dz)) * invN;
-            C wv = X[i];
-            D[i] = cmk<C>(D[i].x + d * wv.y, D[i].y - d * wv.x);   // -= i d W
+            Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
+            R d = (a == 0 ? k.dx : (a == 1 ? k.dy : k.dz)) * invN;
+            CC wv = X[i];
+            D[i] = cmk<CC>(D[i].x + d * wv.y, D[i].y - d * wv.x);   // -= i d W
         }
         __syncthreads();
     }
-    C *Y = fft_lines<C, true>(D, A, ax, t.ncol, 1, g.tk, true);
-    store_tile(w0, t, nx, Y);
+    CC *Y = fft_lines<CC, true>(D, A, ax, t.ncol, 1, g.tk, true);
+    store_tile<PR>(w0, t, nx, Y);
 }
 
 int zpairs_per_block(const GridInfo &g)
@@ -516,6 +635,18 @@ int threads_for(int work)
     return t;
 }
 
+// Launch the double-float kernels when an FP64 grid asks for them.
+#define OFDFT_DISPATCH(T, g, CALL)                          \
+    do {                                                    \
+        if constexpr (std::is_same<T, double>::value) {     \
+            if ((g).dd) {                                   \
+                CALL(DD);                                   \
+                break;                                      \
+            }                                               \
+        }                                                   \
+        CALL(T);                                            \
+    } while (0)
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -528,9 +659,12 @@ void launch_zfwd(const GridInfo &g, const FftAxis &az, int mode, const T *in, co
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 2 * (size_t)P * g.nz * sizeof(cplx<T>);
     int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
-    if (mode == 0) k_zfwd<T, 0><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);
-    else if (mode == 1) k_zfwd<T, 1><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);
-    else k_zfwd<T, 2><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);
+#define CALL(PR)                                                                                          \
+    if (mode == 0) k_zfwd<PR, 0><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);     \
+    else if (mode == 1) k_zfwd<PR, 1><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out); \
+    else k_zfwd<PR, 2><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out)
+    OFDFT_DISPATCH(T, g, CALL);
+#undef CALL
 }
 
 template <typename T>
@@ -543,7 +677,9 @@ int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, 
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 4 * (size_t)P * g.nz * sizeof(cplx<T>);
     int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
-    k_zgga<T><<<blocks, th, sm, st>>>(g, az, P, g0, g1, g2, phit, temp, fp, tab, xc, vpart, part);
+#define CALL(PR) k_zgga<PR><<<blocks, th, sm, st>>>(g, az, P, g0, g1, g2, phit, temp, fp, tab, xc, vpart, part)
+    OFDFT_DISPATCH(T, g, CALL);
+#undef CALL
     return blocks;
 }
 
@@ -558,12 +694,15 @@ int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T>
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 2 * (size_t)P * g.nz * sizeof(cplx<T>);
     int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
-    if (fttf)
-        k_zfinal<T, true><<<blocks, th, sm, st>>>(g, az, P, dspec, vpart, phit, phi, dhat, c, s,
-                                                  cs, temp, fp, tab, xc, vout, part);
-    else
-        k_zfinal<T, false><<<blocks, th, sm, st>>>(g, az, P, dspec, vpart, phit, phi, dhat, c, s,
-                                                   cs, temp, fp, tab, xc, vout, part);
+#define CALL(PR)                                                                                       \
+    if (fttf)                                                                                          \
+        k_zfinal<PR, true><<<blocks, th, sm, st>>>(g, az, P, dspec, vpart, phit, phi, dhat, c, s, cs,  \
+                                                   temp, fp, tab, xc, vout, part);                     \
+    else                                                                                               \
+        k_zfinal<PR, false><<<blocks, th, sm, st>>>(g, az, P, dspec, vpart, phit, phi, dhat, c, s, cs, \
+                                                    temp, fp, tab, xc, vout, part)
+    OFDFT_DISPATCH(T, g, CALL);
+#undef CALL
     return blocks;
 }
 
@@ -575,8 +714,11 @@ void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data,
     dim3 grid(g.nx * ntk, nfields);
     size_t sm = 2 * (size_t)g.ny * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.ny * g.tk / 2);
-    if (inv) k_ypass<T, true><<<grid, th, sm, st>>>(g, ay, data, fstride);
-    else k_ypass<T, false><<<grid, th, sm, st>>>(g, ay, data, fstride);
+#define CALL(PR)                                                            \
+    if (inv) k_ypass<PR, true><<<grid, th, sm, st>>>(g, ay, data, fstride); \
+    else k_ypass<PR, false><<<grid, th, sm, st>>>(g, ay, data, fstride)
+    OFDFT_DISPATCH(T, g, CALL);
+#undef CALL
 }
 
 template <typename T>
@@ -587,7 +729,9 @@ int launch_xgrad(const GridInfo &g, const FftAxis &ax, cplx<T> *nspec, const cpl
     int blocks = g.ny * ntk;
     size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
-    k_xgrad<T><<<blocks, th, sm, st>>>(g, ax, nspec, vext, g0, g1, g2, part);
+#define CALL(PR) k_xgrad<PR><<<blocks, th, sm, st>>>(g, ax, nspec, vext, g0, g1, g2, part)
+    OFDFT_DISPATCH(T, g, CALL);
+#undef CALL
     return blocks;
 }
 
@@ -599,7 +743,9 @@ int launch_xhl(const GridInfo &g, const FftAxis &ax, cplx<T> *spec, const cplx<T
     int blocks = g.ny * ntk;
     size_t sm = 2 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
-    k_xhl<T><<<blocks, th, sm, st>>>(g, ax, spec, vext, nG_out, inverse, part);
+#define CALL(PR) k_xhl<PR><<<blocks, th, sm, st>>>(g, ax, spec, vext, nG_out, inverse, part)
+    OFDFT_DISPATCH(T, g, CALL);
+#undef CALL
     return blocks;
 }
 
@@ -611,7 +757,9 @@ void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const 
     int blocks = g.ny * ntk;
     size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
-    k_xdiv<T><<<blocks, th, sm, st>>>(g, ax, nG, vext, w0, w1, w2);
+#define CALL(PR) k_xdiv<PR><<<blocks, th, sm, st>>>(g, ax, nG, vext, w0, w1, w2)
+    OFDFT_DISPATCH(T, g, CALL);
+#undef CALL
 }
 
 size_t field_smem_max(const GridInfo &g, size_t csize)
@@ -624,24 +772,32 @@ size_t field_smem_max(const GridInfo &g, size_t csize)
     return m > x ? m : x;
 }
 
-template <typename T> cudaError_t set_field_smem_limits(size_t bytes)
+namespace {
+template <typename PR> cudaError_t smem_limits(int b)
 {
-    int b = (int)bytes;
     cudaError_t e[] = {
-        cudaFuncSetAttribute(k_zfwd<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_zfwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_zfwd<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_zgga<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_zfinal<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_zfinal<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_ypass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_ypass<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_xgrad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_xhl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_xdiv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)};
+        cudaFuncSetAttribute(k_zfwd<PR, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zfwd<PR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zfwd<PR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zgga<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zfinal<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zfinal<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_ypass<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_ypass<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xgrad<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xhl<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xdiv<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return x;
     return cudaSuccess;
+}
+}  // namespace
+
+template <typename T> cudaError_t set_field_smem_limits(size_t bytes)
+{
+    cudaError_t e = smem_limits<T>((int)bytes);
+    if (e == cudaSuccess && std::is_same<T, double>::value) e = smem_limits<DD>((int)bytes);
+    return e;
 }
 
 #define OFDFT_INST(T)                                                                              \

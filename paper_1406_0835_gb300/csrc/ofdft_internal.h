@@ -75,6 +75,7 @@ struct FftAxis {
     FastDiv nbd[kMaxStages]; // division by n / rad (butterflies per line)
     FastDiv nsd[kMaxStages]; // division by ns
     const void *tw;          // cplx<T>[n]
+    const void *twf;         // FP64 sets: the same twiddles as double-float pairs (ff::cf2[n])
 };
 
 // Stockham schedule of one axis: radix-8 stages first, then 4, 2, 3, 5.
@@ -114,6 +115,7 @@ struct GridInfo {
     int zP;                  // z passes: line pairs per block (0: default rule)
     int tk;                  // y/x passes: half-spectrum columns per tile (4, 8 or 16)
     int zth, xth;            // threads per block of the z and of the y/x passes (0: default rule)
+    int dd;                  // FP64 fields: FFT and G-space arithmetic in double-float
 };
 
 // Derived quantities of a grid (call after setting sizes, cell and rc).
@@ -159,7 +161,6 @@ void tfunc_table_fill(double *tab);
 struct FuncParams {
     int kind;       // 0 ftTF, 1 SGA-form (mu), 2 VT84F, 3 KST2-form (C1, a1)
     double p0, p1;  // mu | C1, a1
-    int f2;         // FP64 kernels: pointwise functional in double-float
 };
 FuncParams functional_params(int functional);
 

@@ -281,13 +281,12 @@ OF_HD void pz81_point(T n, T &eps, T &v)
 
 // ---------------------------------------------------------------------------
 // The same pointwise functional in double-float arithmetic (ffmath.cuh) for
-// the FP64 path: inputs and outputs are binary64, every intermediate is a
-// double-float, so the result agrees with the binary64 routines above to a
-// few parts in 1e14 while running on the FP32 units.  Quantities whose
-// exponent can leave the binary32 range (s^2 and W, which carry n^(-8/3)) are
-// formed in binary64.  Outside the domain below (and in the Sommerfeld and
-// classical branches of the temperature functions) pw_point_f2 returns false
-// and the caller uses the binary64 routines.
+// the FP64 path's double-float kernels: every intermediate is a double-float,
+// so the result agrees with the binary64 routines above to about 1e-13 of the
+// size of its terms while running on the FP32 units.  Outside the domain
+// below (and in the Sommerfeld and classical branches of the temperature
+// functions) pw_core_f2 returns false and the caller uses binary64.  The
+// split table (hi, lo per coefficient) follows the binary64 one.
 
 template <typename T> struct PwOut {
     T f, ts, dfdn, wc, eps, vxc;
@@ -395,14 +394,22 @@ OF_HD void pz81_f2(ff::f2 c13, ff::f2 y, ff::f2 &eps, ff::f2 &v)
     v = add(mul(ex, cst(4.0 / 3.0)), vc);
 }
 
-// f_s, its derivatives and (xc != 0) PZ81 at one point; false when the point
-// is outside the double-float domain.  tcoef = 2 k_B T / (3 pi^2)^(2/3).
-OF_HD bool pw_point_f2(const FuncParams &fp, const ff::f2 *__restrict__ tab, ff::f2 tcoef, double n_d,
-                       double g2_d, int xc, PwOut<double> &o)
+// Double-float outputs of the pointwise functional at one point.
+struct PwF2 {
+    ff::f2 f, ts, dfdn, eps, vxc;
+    ff::f2 w[3];    // W = d f_s / d(grad n), by component
+};
+
+// f_s, its derivatives and (xc != 0) PZ81 at one point from n and the
+// gradient components gr[3] in double-float; false when the point is
+// outside the double-float domain (s^2 is formed from (grad n) n^(-4/3), so
+// an s^2 past kPwS2max, or one that overflows, also returns false).
+// tcoef = 2 k_B T / (3 pi^2)^(2/3).
+OF_HD bool pw_core_f2(const FuncParams &fp, const ff::f2 *__restrict__ tab, ff::f2 tcoef, ff::f2 n,
+                      const ff::f2 *gr, int xc, PwF2 &o)
 {
     using namespace ff;
-    if (!(n_d >= kPwNmin && n_d <= kPwNmax)) return false;
-    const f2 n = from_double(n_d);
+    if (!(n.hi >= (float)kPwNmin && n.hi <= (float)kPwNmax)) return false;
     const f2 y = rcbrt(n);                                   // n^(-1/3)
     const f2 y2 = mul(y, y);
     const f2 t = mul(tcoef, y2);                             // Eq. (tred)
@@ -417,27 +424,26 @@ OF_HD bool pw_point_f2(const FuncParams &fp, const ff::f2 *__restrict__ tab, ff:
     if (fp.kind == 0) {                                      // ftTF
         tfunc_eval_f2<2>(tab, t, tf);
         const f2 kap = sub(tf[0], tf[1]);
-        o.f = to_double(mul(tau0, kap));
-        o.ts = to_double(mul(tau0, tf[1]));
-        o.dfdn = to_double(add(mul(dtau0, kap), mul(mul(tau0, sub(tf[4], tf[5])), dtdn)));   // Eq. (vTF)
-        o.wc = 0.0;
+        o.f = mul(tau0, kap);
+        o.ts = mul(tau0, tf[1]);
+        o.dfdn = add(mul(dtau0, kap), mul(mul(tau0, sub(tf[4], tf[5])), dtdn));   // Eq. (vTF)
+        o.w[0] = o.w[1] = o.w[2] = f2(0.0f, 0.0f);
     } else {
-        // s^2 in binary64: n^(-8/3) leaves the binary32 range at small n
-        const double yd = to_double(y), y2d = yd * yd, rn43 = y2d * y2d;
-        const double s2d = (g2_d * rn43) * rn43 * OF_CS;    // Eq. (s_0defn)
-        if (!(s2d <= kPwS2max)) return false;
+        const f2 rn43 = mul(y2, y2);                         // n^(-4/3)
+        const f2 q0 = mul(gr[0], rn43), q1 = mul(gr[1], rn43), q2 = mul(gr[2], rn43);
+        const f2 s2 = mul(add(add(mul(q0, q0), mul(q1, q1)), mul(q2, q2)), cst(OF_CS));   // Eq. (s_0defn)
+        if (!(s2.hi <= (float)kPwS2max)) return false;
         tfunc_eval_f2<4>(tab, t, tf);
         const f2 xi = tf[0], ze = tf[1], A = tf[2], B = tf[3];
         const f2 dxi = tf[4], dze = tf[5], dA = tf[6], dB = tf[7];
-        const f2 s2 = from_double(s2d);
         const f2 xt = mul(s2, A), xs = mul(s2, B);           // Eq. (s_s)
         f2 Ft, dFt, Fsg, dFsg;
         enhance_f2(fp, xt, Ft, dFt);
         enhance_f2(fp, xs, Fsg, dFsg);
         const f2 Fs = add(neg(Fsg), 2.0f), dFs = neg(dFsg); // F_sigma = 2 - F_tau(s_sigma)
         const f2 kin = mul(tau0, xi), ent = mul(tau0, ze);
-        o.f = to_double(sub(mul(kin, Ft), mul(ent, Fs)));   // Eq. (FGGA)
-        o.ts = to_double(mul(ent, Fs));
+        o.f = sub(mul(kin, Ft), mul(ent, Fs));              // Eq. (FGGA)
+        o.ts = mul(ent, Fs);
         const f2 e83 = mul(rn, cst(-8.0 / 3.0));
         const f2 s2dt = mul(s2, dtdn);
         // Eq. (vftGGA), first two lines
@@ -445,19 +451,17 @@ OF_HD bool pw_point_f2(const FuncParams &fp, const ff::f2 *__restrict__ tab, ff:
         d = add(d, mul(mul(tau0, dtdn), sub(mul(dxi, Ft), mul(dze, Fs))));
         d = add(d, mul(mul(kin, dFt), add(mul(e83, xt), mul(s2dt, dA))));
         d = sub(d, mul(mul(ent, dFs), add(mul(e83, xs), mul(s2dt, dB))));
-        o.dfdn = to_double(d);
+        o.dfdn = d;
         // last line: W = [tau0 xi F_tau' A - tau0 zeta F_sigma' B] d s^2 / d grad n
-        const double wpre = to_double(sub(mul(mul(kin, dFt), A), mul(mul(ent, dFs), B)));
-        o.wc = (wpre * rn43) * rn43 * (2.0 * OF_CS);
+        const f2 wpre = sub(mul(mul(kin, dFt), A), mul(mul(ent, dFs), B));
+        const f2 wr = mul(mul(wpre, rn43), cst(2.0 * OF_CS));
+        for (int a = 0; a < 3; ++a) o.w[a] = mul(wr, mul(gr[a], rn43));
     }
     if (xc) {
-        f2 eps, v;
-        pz81_f2(c13, y, eps, v);
-        o.eps = to_double(eps);
-        o.vxc = to_double(v);
+        pz81_f2(c13, y, o.eps, o.vxc);
     } else {
-        o.eps = 0.0;
-        o.vxc = 0.0;
+        o.eps = f2(0.0f, 0.0f);
+        o.vxc = f2(0.0f, 0.0f);
     }
     return true;
 }
@@ -478,19 +482,6 @@ OF_HD PwOut<T> pw_point_native(const FuncParams &fp, const T *__restrict__ tab, 
     return o;
 }
 
-// Pointwise functional of a field kernel.  FP64 kernels with fp.f2 set take
-// the double-float routine (its split table follows the binary64 one in tab)
-// and fall back to binary64 outside its domain; FP32 kernels run binary32.
-template <typename T>
-OF_HD PwOut<T> pw_point(const FuncParams &fp, const T *__restrict__ tab, ff::f2 tcoef, T temp, T n, T g2, int xc)
-{
-    if constexpr (sizeof(T) == 8) {
-        PwOut<double> o;
-        if (fp.f2 && pw_point_f2(fp, reinterpret_cast<const ff::f2 *>(tab + kTfSize), tcoef, n, g2, xc, o))
-            return o;
-    }
-    return pw_point_native<T>(fp, tab, temp, n, g2, xc);
-}
 
 // Double-float table written from the binary64 one (hi, lo per coefficient).
 inline void tfunc_table_split(const double *tab, float *out)
