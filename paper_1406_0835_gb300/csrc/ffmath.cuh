@@ -104,14 +104,32 @@ FF_HD f2 two_prod(float a, float b)
     return {p, ffma(a, b, -p)};
 }
 
+// binary32 -> binary64 by rebuilding the bit pattern (exact; zero and
+// subnormal inputs give zero, inf and NaN stay so): integer operations only,
+// where the conversion instruction would occupy the FP64 unit.
+FF_HD double widen_bits(float f)
+{
+#ifdef __CUDA_ARCH__
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+    if (e == 0u) return __longlong_as_double((long long)sign);
+    const uint64_t de = e == 0xffu ? 0x7ffull : (uint64_t)(e + 896u);
+    return __longlong_as_double((long long)(sign | (de << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
+#else
+    return (double)f;
+#endif
+}
+
 // Conversions.  from_double rounds to the nearest double-float (error
-// <= 2^-48 relative); to_double is exact.
+// <= 2^-48 relative); to_double returns hi + lo rounded to binary64, with
+// one binary64 addition.
 FF_HD f2 from_double(double d)
 {
     float h = (float)d;
     return {h, (float)(d - (double)h)};
 }
-FF_HD double to_double(f2 x) { return (double)x.hi + (double)x.lo; }
+FF_HD double to_double(f2 x) { return widen_bits(x.hi) + widen_bits(x.lo); }
 
 // Compile-time constant split of a double.
 constexpr f2 cst(double d) { return f2(d); }

@@ -58,9 +58,18 @@ template <> __device__ __forceinline__ double2 stc<DD>(ff::cf2 v)
 {
     return make_double2(ff::to_double(v.x), ff::to_double(v.y));
 }
-// grid constant in the computed type (binary64 value d, its binary32 copy f)
-template <typename PR> __device__ __forceinline__ typename KT<PR>::R gcst(double d, float f) { return gsel<PR>(d, f); }
-template <> __device__ __forceinline__ ff::f2 gcst<DD>(double d, float) { return ff::f2(d); }
+// grid constant in the computed type (binary64 value d, binary32 copy f,
+// double-float pair p)
+template <typename PR>
+__device__ __forceinline__ typename KT<PR>::R gcst(double d, float f, const float *) { return gsel<PR>(d, f); }
+template <> __device__ __forceinline__ ff::f2 gcst<DD>(double, float, const float *p) { return ff::f2(p[0], p[1]); }
+constexpr double kFourPi = 12.566370614359172954;
+template <typename PR> __device__ __forceinline__ typename KT<PR>::R fourpi() { return (typename KT<PR>::R)kFourPi; }
+template <> __device__ __forceinline__ ff::f2 fourpi<DD>()
+{
+    constexpr ff::f2 c(kFourPi);
+    return c;
+}
 // scalar read in binary64 (double-float: correctly rounded split)
 template <typename PR> __device__ __forceinline__ typename KT<PR>::R scal(typename KT<PR>::T x) { return x; }
 template <> __device__ __forceinline__ ff::f2 scal<DD>(double x) { return ff::f2(x); }
@@ -250,6 +259,7 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__rest
         if (res[a] == scratch) scratch = buf[a];
     }
     R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    const ff::f2 tcoef = is_dd<PR>() ? ff::f2(2.0 / OF_K23 * (double)temp) : ff::f2(0.0f, 0.0f);
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
         const int line = i / nz, e = i - line * nz;
         const int p = line >> 1, hi = line & 1;
@@ -257,7 +267,6 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__rest
         for (int a = 0; a < 3; ++a)   // each thread owns one component of the packed pair
             gr[a] = reinterpret_cast<const R *>(&res[a][p * nz + e])[hi];
         if constexpr (is_dd<PR>()) {
-            const ff::f2 tcoef(2.0 / OF_K23 * (double)temp);
             const R ph = ldr<PR>(phit[rbase + i]);
             const R n = ph * ph;
             const PwF2 o = pw_dd(fp, tab, tcoef, (double)temp, n, gr, xc);
@@ -338,6 +347,7 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const typename KT<PR>::C
     __syncthreads();
     CC *X = fft_lines<CC, true>(A, B, az, nl, nz, 1, false);
     R acc[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    const ff::f2 tcoef = is_dd<PR>() && FTTF ? ff::f2(2.0 / OF_K23 * (double)temp) : ff::f2(0.0f, 0.0f);
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
         const int line = i / nz, e = i - line * nz;
         CC d = X[(line >> 1) * nz + e];
@@ -348,7 +358,6 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const typename KT<PR>::C
         if (FTTF) {
             R f, ts, dfdn, eps, vxc;
             if constexpr (is_dd<PR>()) {
-                const ff::f2 tcoef(2.0 / OF_K23 * (double)temp);
                 const R gz[3] = {R(0), R(0), R(0)};
                 const PwF2 o = pw_dd(fp, tab, tcoef, (double)temp, n, gz, xc);
                 f = o.f, ts = o.ts, dfdn = o.dfdn, eps = o.eps, vxc = o.vxc;
@@ -464,9 +473,10 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
     load_tile<PR>(nspec, t, nx, A);
     __syncthreads();
     CC *X = fft_lines<CC, false>(A, B, ax, t.ncol, 1, g.tk, true);
-    const R bx = gcst<PR>(g.bx, g.bxf), by = gcst<PR>(g.by, g.byf), bz = gcst<PR>(g.bz, g.bzf);
-    const R hr = gcst<PR>(g.hr, g.hrf);
-    const R invN = gcst<PR>(g.invN, g.invNf);
+    const R bx = gcst<PR>(g.bx, g.bxf, g.bx2), by = gcst<PR>(g.by, g.byf, g.by2),
+            bz = gcst<PR>(g.bz, g.bzf, g.bz2);
+    const R hr = gcst<PR>(g.hr, g.hrf, g.hr2);
+    const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
     R acc[3] = {R(0), R(0), R(0)};   // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i / g.tk, c = i - r * g.tk;
@@ -527,10 +537,11 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
     load_tile<PR>(spec, t, nx, A);
     __syncthreads();
     CC *X = fft_lines<CC, false>(A, B, ax, t.ncol, 1, g.tk, true);
-    const R bx = gcst<PR>(g.bx, g.bxf), by = gcst<PR>(g.by, g.byf), bz = gcst<PR>(g.bz, g.bzf);
-    const R hr = gcst<PR>(g.hr, g.hrf);
-    const R fourpi = gcst<PR>(12.566370614359172954, 12.566370614359172954f);
-    const R invN = gcst<PR>(g.invN, g.invNf);
+    const R bx = gcst<PR>(g.bx, g.bxf, g.bx2), by = gcst<PR>(g.by, g.byf, g.by2),
+            bz = gcst<PR>(g.bz, g.bzf, g.bz2);
+    const R hr = gcst<PR>(g.hr, g.hrf, g.hr2);
+    const R fpi = fourpi<PR>();
+    const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
     R acc[3] = {R(0), R(0), R(0)};
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i / g.tk, c = i - r * g.tk;
@@ -545,7 +556,7 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
             acc[0] += k.w * n2 / k.g2;
             acc[1] += k.w * re;
             acc[2] += k.w * re * (R(1) - hr * k.g2);
-            R kh = fourpi / k.g2;
+            R kh = fpi / k.g2;
             out = cmk<CC>(kh * nG.x + ve.x, kh * nG.y + ve.y);
         }
         if (nG_out != nullptr) nG_out[t.base + r * t.rstride + c] = stc<PR>(nG);
@@ -582,9 +593,10 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
     CC *B = A + nx * g.tk;
     CC *D = B + nx * g.tk;
     ColTile t = col_tile(g, true);
-    const R bx = gcst<PR>(g.bx, g.bxf), by = gcst<PR>(g.by, g.byf), bz = gcst<PR>(g.bz, g.bzf);
-    const R fourpi = gcst<PR>(12.566370614359172954, 12.566370614359172954f);
-    const R invN = gcst<PR>(g.invN, g.invNf);
+    const R bx = gcst<PR>(g.bx, g.bxf, g.bx2), by = gcst<PR>(g.by, g.byf, g.by2),
+            bz = gcst<PR>(g.bz, g.bzf, g.bz2);
+    const R fpi = fourpi<PR>();
+    const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i / g.tk, c = i - r * g.tk;
         if (c >= t.ncol) continue;
@@ -593,7 +605,7 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
         if (k.g2 > R(0)) {
             CC n = ldc<PR>(nG[t.base + r * t.rstride + c]);
             CC ve = ldc<PR>(vext[t.base + r * t.rstride + c]);
-            R kh = fourpi / k.g2;
+            R kh = fpi / k.g2;
             out = cmk<CC>(kh * n.x + ve.x, kh * n.y + ve.y);
         }
         D[i] = out;

@@ -116,6 +116,7 @@ struct GridInfo {
     int tk;                  // y/x passes: half-spectrum columns per tile (4, 8 or 16)
     int zth, xth;            // threads per block of the z and of the y/x passes (0: default rule)
     int dd;                  // FP64 fields: FFT and G-space arithmetic in double-float
+    float bx2[2], by2[2], bz2[2], invN2[2], hr2[2];   // the same constants as double-float pairs
 };
 
 // Derived quantities of a grid (call after setting sizes, cell and rc).
@@ -128,6 +129,12 @@ inline void grid_reciprocal(GridInfo &g)
     g.bz = tp / g.Lz;
     g.invN = 1.0 / (double)g.N;
     g.hr = 0.5 * g.rc * g.rc;
+    const double dc[5] = {g.bx, g.by, g.bz, g.invN, g.hr};
+    float *pc[5] = {g.bx2, g.by2, g.bz2, g.invN2, g.hr2};
+    for (int i = 0; i < 5; ++i) {
+        pc[i][0] = (float)dc[i];
+        pc[i][1] = (float)(dc[i] - (double)pc[i][0]);
+    }
     g.bxf = (float)g.bx;
     g.byf = (float)g.by;
     g.bzf = (float)g.bz;
