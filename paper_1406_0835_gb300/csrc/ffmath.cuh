@@ -32,8 +32,10 @@ namespace ff {
 
 #ifdef __CUDACC__
 #define FF_HD __host__ __device__ __forceinline__
+#define FF_CALL static __host__ __device__ __noinline__   // one copy of a long routine per kernel
 #else
 #define FF_HD inline
+#define FF_CALL static inline
 #endif
 
 struct f2 {
@@ -300,7 +302,7 @@ constexpr double kLn2Rest = kLn2 - 0.693145751953125;
 constexpr float kLn2B = (float)kLn2Rest;
 constexpr float kLn2C = (float)(kLn2Rest - (double)(float)kLn2Rest);
 
-FF_HD f2 exp(f2 x)
+FF_CALL f2 exp(f2 x)
 {
     if (x.hi < -87.0f) return {0.0f, 0.0f};
     const float k = rintf(x.hi * 1.44269504088896341f);

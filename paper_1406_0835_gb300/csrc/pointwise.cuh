@@ -309,7 +309,7 @@ OF_HD void tfunc_eval_f2(const ff::f2 *__restrict__ tab, ff::f2 t, ff::f2 out[8]
     const float ul = 8.0f * t.lo * inv2e;
     const float dudt = 8.0f * inv2e;
     const ff::f2 *c = tab + ((size_t)((e - kTfEmin) * kTfSub + sub) * kTfFuncs) * kTfNc;
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NF; ++q) {
         const ff::f2 *cq = c + q * kTfNc;
         ff::f2 p = cq[kTfDeg], dp = {0.0f, 0.0f};
@@ -328,7 +328,7 @@ OF_HD void tfunc_eval_f2(const ff::f2 *__restrict__ tab, ff::f2 t, ff::f2 out[8]
 }
 
 // Enhancement factor F(x) and dF/dx in double-float (forms as in enhance).
-OF_HD void enhance_f2(const FuncParams &fp, ff::f2 x, ff::f2 &F, ff::f2 &dF)
+FF_CALL void enhance_f2(const FuncParams &fp, ff::f2 x, ff::f2 &F, ff::f2 &dF)
 {
     using namespace ff;
     if (fp.kind == 1) {                                     // SGA form
