@@ -161,9 +161,15 @@ def fft_flops(n):
 # factors with their s^2-derivatives, n^(-1/3), PZ81, W and the energy
 # densities): about 150-250 flop per point; 200 is used.
 POINTWISE_FLOP = 200.0
-# DRAM bytes per grid point of one k_zgga<double> launch, from the ncu capture
-# summarised in profiles/k_zgga_f64_128.md (83.4 MB at 128^3).
-ZGGA_F64_TRAFFIC_PER_POINT = 83.4e6 / 128 ** 3
+# DRAM bytes per grid point of one k_zgga<DD> launch (the FP64 contexts'
+# double-float kernel), from the ncu capture summarised in
+# profiles/fields_dd_128.md.
+ZGGA_DD_TRAFFIC_PER_POINT = (68.135424e6 + 27.309568e6) / 128 ** 3
+# FP32-unit instructions per FP64-equivalent flop of the double-float
+# arithmetic: a sum (two_sum + tail + fast_two_sum) takes 11, a product
+# (two_prod + two FMAs + fast_two_sum) 9; FFT and pointwise work is about two
+# sums per product, so 10.3.
+DD_INSTR_PER_FLOP = (2 * 11 + 9) / 3.0
 
 
 def kernel_model(name, g):
@@ -239,26 +245,33 @@ def run_eval(args, rank, world):
     return res, 1.0
 
 
-def roofline_entry(dominant, grid, kms, kcount, clk, peaks):
+def roofline_entry(dominant, grid, kms, kcount, clk, peaks, precision="fp64"):
+    """Roofline position of the dominant kernel class.  FP64 contexts run it
+    in double-float on the FP32 units, so its ceiling is the SM issue rate
+    (152 SMs x 128 lanes x clock) over the instructions one FP64-equivalent
+    flop costs there (DD_INSTR_PER_FLOP); achieved = algorithmic flops
+    (FFT flops + the pointwise functional) over the mean event-timed launch."""
     flops, byts = kernel_model(dominant, grid)
     avg_s = (kms / 1e3) / max(kcount, 1)
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # FP64 FMA issue: 2 per SM per clock (GB300); 152 SMs
-    fp64_peak = 152 * 2 * 2 * (sm_mhz * 1e6) / 1e12
+    issue = 152 * 128 * (sm_mhz * 1e6)                      # thread instructions / s
+    dd_peak = issue / DD_INSTR_PER_FLOP / 1e12              # FP64-equivalent TFLOP/s
+    fp64_peak = 152 * 2 * 2 * (sm_mhz * 1e6) / 1e12         # the FP64 units: 2 DFMA / SM / clock
     ok = kcount > 0
     npts = grid[0] * grid[1] * grid[2]
-    traffic = ZGGA_F64_TRAFFIC_PER_POINT * npts if dominant == "zgga" else None
-    return {"bound": "alu", "kernel": dominant, "achieved": flops / avg_s / 1e12 if ok else None,
-            "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
-            "frac": (flops / avg_s / 1e12) / fp64_peak if ok else None,
-            "traffic": traffic, "launches": kcount, "avg_launch_us": avg_s * 1e6,
+    achieved = flops / avg_s / 1e12 if ok else None
+    traffic = (ZGGA_DD_TRAFFIC_PER_POINT * npts
+               if dominant == "zgga" and precision == "fp64" and ZGGA_DD_TRAFFIC_PER_POINT else None)
+    return {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": dd_peak,
+            "unit": "TFLOP/s (FP64-equivalent, double-float on the FP32 units)",
+            "frac": achieved / dd_peak if ok else None, "traffic": traffic,
+            "launches": kcount, "avg_launch_us": avg_s * 1e6, "algorithmic_flops": flops,
             "algorithmic_bytes": byts, "hbm_gbs": byts / avg_s / 1e9 if ok else None,
-            "hbm_peak_gbs": peaks.get("hbm_gbs"),
-            "fp64_pipe_active_pct_ncu": 86.4 if dominant == "zgga" else None,
-            "peak_note": "FP64 peak derived from 152 SMs x 2 DFMA/clk x median SM clock (1.19 TFLOP/s "
-                         "measured on GB300); achieved = FFT flops + 200 flop/pt pointwise over the mean "
-                         "event-timed launch in one extra host-driven step; traffic = ncu DRAM bytes "
-                         "at 128^3 scaled by the point count"}
+            "hbm_peak_gbs": peaks.get("hbm_gbs"), "fp64_unit_peak": fp64_peak,
+            "achieved_over_fp64_unit_peak": achieved / fp64_peak if ok else None,
+            "timed_launches": "FP64 and FP32 launches of the class averaged" if precision == "mixed" else "FP64",
+            "peak_note": "peak = 152 SMs x 128 lanes x median SM clock / %.1f FP32 instructions per "
+                         "FP64-equivalent flop; fp64_unit_peak = 152 x 2 DFMA/clk x clock" % DD_INSTR_PER_FLOP}
 
 
 def time_dominant(ctx, ofdft, dominant, stream, work):
@@ -385,7 +398,7 @@ def run_ours(args, rank, world):
            "evals_per_s": world * evals / t_total, "evals_per_step": evals / args.steps,
            "cg_iterations_per_step": iters / args.steps,
            "gpu_launches": launches, "clocks": clk, "e2e": e2e,
-           "roofline": roofline_entry(dominant, cfg["grid"], kms, kcount, clk, read_peaks())}
+           "roofline": roofline_entry(dominant, cfg["grid"], kms, kcount, clk, read_peaks(), wl["precision"])}
     return res, evals / args.steps
 
 
@@ -470,7 +483,7 @@ def run_solve(args, rank, world):
            "evals_per_step": evals / args.steps, "fp32_evals_per_step": evals_lo / args.steps,
            "cg_iterations_per_step": iters / args.steps, "evals_per_s": world * evals / t_total,
            "gpu_launches": launches, "clocks": clk, "e2e": e2e,
-           "roofline": roofline_entry(dominant, cfg["grid"], kms, kcount, clk, read_peaks())}
+           "roofline": roofline_entry(dominant, cfg["grid"], kms, kcount, clk, read_peaks(), wl["precision"])}
     return res, evals / args.steps
 
 
