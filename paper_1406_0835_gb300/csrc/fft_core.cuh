@@ -112,17 +112,30 @@ template <typename C, int R, bool INV> __device__ __forceinline__ void dftR(C *v
 // One Stockham stage over nl lines.  Element e of line l lives at
 // buf[l * lstride + e * estride].  lines_fast selects whether consecutive
 // threads walk lines (column tiles) or butterflies (contiguous lines).
+// Column tiles have a power-of-two element stride: their threads then walk
+// estride line slots (slots >= nl idle) and take line and butterfly from a
+// mask and a shift; a power-of-two Ns (every stage that follows radix-2, 4
+// or 8 stages only) splits j the same way.  Other shapes divide.
 template <typename C, int R, bool INV>
 __device__ __forceinline__ void stage(const C *__restrict__ src, C *__restrict__ dst, int n, int Ns,
                                       const C *__restrict__ tw, int nl, int lstride, int estride,
                                       bool lines_fast)
 {
     const int nb = n / R;
-    const int total = nb * nl;
     const int tws = n / (Ns * R);
+    const bool pslot = lines_fast && (estride & (estride - 1)) == 0;
+    const int slots = pslot ? estride : nl;
+    const int ssh = __ffs(slots) - 1;
+    const bool pns = (Ns & (Ns - 1)) == 0;
+    const int nsh = __ffs(Ns) - 1;
+    const int total = nb * slots;
     for (int it = threadIdx.x; it < total; it += blockDim.x) {
         int l, j;
-        if (lines_fast) {
+        if (pslot) {
+            l = it & (slots - 1);
+            j = it >> ssh;
+            if (l >= nl) continue;
+        } else if (lines_fast) {
             l = it % nl;
             j = it / nl;
         } else {
@@ -133,7 +146,8 @@ __device__ __forceinline__ void stage(const C *__restrict__ src, C *__restrict__
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * estride];
-        const int k = j % Ns;
+        const int k = pns ? (j & (Ns - 1)) : j % Ns;
+        const int q = pns ? (j >> nsh) : j / Ns;
         if (k != 0) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -144,7 +158,7 @@ __device__ __forceinline__ void stage(const C *__restrict__ src, C *__restrict__
         }
         dftR<C, R, INV>(v);
         C *d = dst + l * lstride;
-        const int base = (j / Ns) * Ns * R + k;
+        const int base = q * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) d[(base + r * Ns) * estride] = v[r];
     }

@@ -395,7 +395,7 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const typename KT<PR>::C
 struct ColTile {
     long long base;   // offset of (row 0, kz0) in the field
     long long rstride;
-    int kz0, ncol, outer, tk;
+    int kz0, ncol, outer, tk, tsh;   // tk = 2^tsh columns (4, 8 or 16)
 };
 
 __device__ __forceinline__ ColTile col_tile(const GridInfo &g, bool xaxis)
@@ -404,6 +404,7 @@ __device__ __forceinline__ ColTile col_tile(const GridInfo &g, bool xaxis)
     const int ntk = (g.K + tk - 1) / tk;
     ColTile t;
     t.tk = tk;
+    t.tsh = __ffs(tk) - 1;
     t.outer = blockIdx.x / ntk;
     t.kz0 = (blockIdx.x - t.outer * ntk) * tk;
     t.ncol = min(tk, g.K - t.kz0);
@@ -422,7 +423,7 @@ __device__ __forceinline__ void load_tile(const typename KT<PR>::C *__restrict__
                                           typename KT<PR>::CC *dst)
 {
     for (int i = threadIdx.x; i < nrows * t.tk; i += blockDim.x) {
-        const int r = i / t.tk, c = i - r * t.tk;
+        const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c < t.ncol) dst[i] = ldc<PR>(src[t.base + r * t.rstride + c]);
     }
 }
@@ -432,7 +433,7 @@ __device__ __forceinline__ void store_tile(typename KT<PR>::C *__restrict__ dst,
                                            const typename KT<PR>::CC *src)
 {
     for (int i = threadIdx.x; i < nrows * t.tk; i += blockDim.x) {
-        const int r = i / t.tk, c = i - r * t.tk;
+        const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c < t.ncol) dst[t.base + r * t.rstride + c] = stc<PR>(src[i]);
     }
 }
@@ -479,7 +480,7 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
     const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
     R acc[3] = {R(0), R(0), R(0)};   // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
-        const int r = i / g.tk, c = i - r * g.tk;
+        const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c >= t.ncol) continue;
         CC nG = cscale(X[i], invN);
         N[i] = nG;
@@ -498,7 +499,7 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
     C *outs[3] = {g0, g1, g2};
     for (int a = 0; a < 3; ++a) {
         for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
-            const int r = i / g.tk, c = i - r * g.tk;
+            const int r = i >> t.tsh, c = i & (t.tk - 1);
             Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + min(c, t.ncol - 1));
             R d = a == 0 ? k.dx : (a == 1 ? k.dy : k.dz);
             CC v = N[i];
@@ -544,7 +545,7 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
     const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
     R acc[3] = {R(0), R(0), R(0)};
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
-        const int r = i / g.tk, c = i - r * g.tk;
+        const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c >= t.ncol) continue;
         CC nG = cscale(X[i], invN);
         Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
@@ -598,7 +599,7 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
     const R fpi = fourpi<PR>();
     const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
-        const int r = i / g.tk, c = i - r * g.tk;
+        const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c >= t.ncol) continue;
         Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
         CC out = cmk<CC>(R(0), R(0));
@@ -616,7 +617,7 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
         __syncthreads();
         CC *X = fft_lines<CC, false>(A, B, ax, t.ncol, 1, g.tk, true);
         for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
-            const int r = i / g.tk, c = i - r * g.tk;
+            const int r = i >> t.tsh, c = i & (t.tk - 1);
             if (c >= t.ncol) continue;
             Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
             R d = (a == 0 ? k.dx : (a == 1 ? k.dy : k.dz)) * invN;

@@ -294,6 +294,11 @@ template <typename T> struct PwOut {
 
 constexpr double kPwNmin = 1e-18, kPwNmax = 1e18, kPwS2max = 1e10;
 
+#ifndef OFDFT_TF_UNROLL
+#define OFDFT_TF_UNROLL 1
+#endif
+constexpr int kTfUnroll = OFDFT_TF_UNROLL;   // functions evaluated side by side
+
 // Table polynomials with a double-float table (same layout as tfunc_eval's).
 // The panel variable u = uh + ul: uh is exact in binary32 and the Horner
 // sums run with it; ul (below 5e-7) enters through the first and second
@@ -309,7 +314,7 @@ OF_HD void tfunc_eval_f2(const ff::f2 *__restrict__ tab, ff::f2 t, ff::f2 out[8]
     const float ul = 8.0f * t.lo * inv2e;
     const float dudt = 8.0f * inv2e;
     const ff::f2 *c = tab + ((size_t)((e - kTfEmin) * kTfSub + sub) * kTfFuncs) * kTfNc;
-#pragma unroll 1
+#pragma unroll kTfUnroll
     for (int q = 0; q < NF; ++q) {
         const ff::f2 *cq = c + q * kTfNc;
         ff::f2 p = cq[kTfDeg], dp = {0.0f, 0.0f};
