@@ -114,8 +114,10 @@ template <typename C, int R, bool INV> __device__ __forceinline__ void dftR(C *v
 // threads walk lines (column tiles) or butterflies (contiguous lines).
 // Column tiles have a power-of-two element stride: their threads then walk
 // estride line slots (slots >= nl idle) and take line and butterfly from a
-// mask and a shift; a power-of-two Ns (every stage that follows radix-2, 4
-// or 8 stages only) splits j the same way.  Other shapes divide.
+// mask and a shift.  Contiguous lines walk the butterflies in slots rounded
+// up to a power of two (slots >= n/R idle).  A power-of-two Ns (every stage
+// that follows radix-2, 4 or 8 stages only) splits j the same way; other
+// Ns divide.
 template <typename C, int R, bool INV>
 __device__ __forceinline__ void stage(const C *__restrict__ src, C *__restrict__ dst, int n, int Ns,
                                       const C *__restrict__ tw, int nl, int lstride, int estride,
@@ -126,9 +128,10 @@ __device__ __forceinline__ void stage(const C *__restrict__ src, C *__restrict__
     const bool pslot = lines_fast && (estride & (estride - 1)) == 0;
     const int slots = pslot ? estride : nl;
     const int ssh = __ffs(slots) - 1;
+    const int bsh = nb > 1 ? 32 - __clz(nb - 1) : 0;   // butterfly slots 2^bsh >= nb
     const bool pns = (Ns & (Ns - 1)) == 0;
     const int nsh = __ffs(Ns) - 1;
-    const int total = nb * slots;
+    const int total = lines_fast ? nb * slots : (nl << bsh);
     for (int it = threadIdx.x; it < total; it += blockDim.x) {
         int l, j;
         if (pslot) {
@@ -139,8 +142,9 @@ __device__ __forceinline__ void stage(const C *__restrict__ src, C *__restrict__
             l = it % nl;
             j = it / nl;
         } else {
-            j = it % nb;
-            l = it / nb;
+            j = it & ((1 << bsh) - 1);
+            l = it >> bsh;
+            if (j >= nb) continue;
         }
         const C *s = src + l * lstride;
         C v[R];

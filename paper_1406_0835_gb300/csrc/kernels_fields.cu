@@ -132,6 +132,28 @@ __device__ __forceinline__ PwF2 pw_dd(const FuncParams &fp, const double *__rest
     return o;
 }
 
+// (row, column) of the element indices threadIdx.x, threadIdx.x +
+// blockDim.x, ... in rows of width w, stepped without a division.
+struct RowCol {
+    int r, c, dr, dc, w;
+    __device__ __forceinline__ explicit RowCol(int w_) : w(w_)
+    {
+        r = threadIdx.x / w_;
+        c = threadIdx.x - r * w_;
+        dr = blockDim.x / w_;
+        dc = blockDim.x - dr * w_;
+    }
+    __device__ __forceinline__ void next()
+    {
+        r += dr;
+        c += dc;
+        if (c >= w) {
+            c -= w;
+            ++r;
+        }
+    }
+};
+
 // ------------------------------------------------------------------ z pass
 // Pair p of a block holds real lines 2p (real part) and 2p+1 (imaginary part).
 
@@ -157,8 +179,9 @@ __global__ void k_zfwd(GridInfo g, FftAxis az, int P, const typename KT<PR>::T *
     const int nl = (int)min((long long)P, npairs - p0);
     const int nz = g.nz, K = g.K;
     const long long base = 2 * p0 * nz;
-    for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
-        const int line = i / nz, e = i - line * nz;
+    RowCol rc(nz);
+    for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x, rc.next()) {
+        const int line = rc.r, e = rc.c;
         R val;
         if (MODE == 0) {
             val = ldr<PR>(in[base + i]);
@@ -177,8 +200,9 @@ __global__ void k_zfwd(GridInfo g, FftAxis az, int P, const typename KT<PR>::T *
     CC *X = fft_lines<CC, false>(A, B, az, nl, nz, 1, false);
     const long long obase = 2 * p0 * K;
     const R half = R(0.5), mhalf = R(-0.5);
-    for (int i = threadIdx.x; i < 2 * nl * K; i += blockDim.x) {
-        const int line = i / K, k = i - line * K;
+    RowCol rk(K);
+    for (int i = threadIdx.x; i < 2 * nl * K; i += blockDim.x, rk.next()) {
+        const int line = rk.r, k = rk.c;
         const CC *row = X + (line >> 1) * nz;
         CC z = row[k], zc = cconj(row[k == 0 ? 0 : nz - k]);
         CC r = (line & 1) ? cmk<CC>(half * (z.y - zc.y), mhalf * (z.x - zc.x))
@@ -196,8 +220,9 @@ __device__ __forceinline__ void pack_c2r(const typename KT<PR>::C *__restrict__ 
 {
     typedef typename KT<PR>::R R;
     typedef typename KT<PR>::CC CC;
-    for (int i = threadIdx.x; i < nl * K; i += blockDim.x) {
-        const int p = i / K, k = i - p * K;
+    RowCol rc(K);
+    for (int i = threadIdx.x; i < nl * K; i += blockDim.x, rc.next()) {
+        const int p = rc.r, k = rc.c;
         CC a = ldc<PR>(src[obase + (2 * p) * (long long)K + k]);
         CC b = ldc<PR>(src[obase + (2 * p + 1) * (long long)K + k]);
         if (k == 0 || 2 * k == nz) {
@@ -217,8 +242,9 @@ __device__ __forceinline__ void unpack_r2c(const typename KT<PR>::CC *X, long lo
     typedef typename KT<PR>::R R;
     typedef typename KT<PR>::CC CC;
     const R half = R(0.5), mhalf = R(-0.5);
-    for (int i = threadIdx.x; i < 2 * nl * K; i += blockDim.x) {
-        const int line = i / K, k = i - line * K;
+    RowCol rc(K);
+    for (int i = threadIdx.x; i < 2 * nl * K; i += blockDim.x, rc.next()) {
+        const int line = rc.r, k = rc.c;
         const CC *row = X + (line >> 1) * nz;
         CC z = row[k], zc = cconj(row[k == 0 ? 0 : nz - k]);
         out[obase + i] = stc<PR>((line & 1) ? cmk<CC>(half * (z.y - zc.y), mhalf * (z.x - zc.x))
@@ -260,8 +286,9 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__rest
     }
     R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     const ff::f2 tcoef = is_dd<PR>() ? ff::f2(2.0 / OF_K23 * (double)temp) : ff::f2(0.0f, 0.0f);
-    for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
-        const int line = i / nz, e = i - line * nz;
+    RowCol rc(nz);
+    for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x, rc.next()) {
+        const int line = rc.r, e = rc.c;
         const int p = line >> 1, hi = line & 1;
         R gr[3];
         for (int a = 0; a < 3; ++a)   // each thread owns one component of the packed pair
@@ -348,8 +375,9 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const typename KT<PR>::C
     CC *X = fft_lines<CC, true>(A, B, az, nl, nz, 1, false);
     R acc[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     const ff::f2 tcoef = is_dd<PR>() && FTTF ? ff::f2(2.0 / OF_K23 * (double)temp) : ff::f2(0.0f, 0.0f);
-    for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x) {
-        const int line = i / nz, e = i - line * nz;
+    RowCol rc(nz);
+    for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x, rc.next()) {
+        const int line = rc.r, e = rc.c;
         CC d = X[(line >> 1) * nz + e];
         R dr = (line & 1) ? d.y : d.x;
         R ph = ldr<PR>(phit[rbase + i]);
