@@ -50,6 +50,13 @@ def test_setup_rejects_bad_input_without_a_gpu(lib):
     tri[0, 1] = 0.5
     with pytest.raises(ofdft.OfdftError):
         ofdft.ofdft_setup(tri, (16, 16, 16), ions, [1.0], 1e4, "fttf")
+    # FP64 arithmetic selector: only OFDFT_PW_F32X2 (0) and OFDFT_PW_F64 (1)
+    p = ofdft.ofdft_default_params()
+    assert p.pointwise == 0
+    p.pointwise = 7
+    with pytest.raises(ofdft.OfdftError) as e:
+        ofdft.ofdft_setup(cfg_cell, (16, 16, 16), ions, [1.0], 1e4, "fttf", p)
+    assert e.value.status == -1
 
 
 def test_tabulated_temperature_functions_match_oracle(lib):
