@@ -1020,12 +1020,12 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
             best = g;
         }
     }
-    // threads per block of the z passes, then of the y/x passes (the register
-    // budget of the FP64 kernels allows 256 at most)
-    const int thmax = sizeof(T) == 8 ? 256 : 512;
+    // threads per block of the z passes, then of the y/x passes (the FP64 z
+    // passes use up to 128 registers a thread: 256 threads at most there)
     for (int pass = 0; pass < 2; ++pass) {
         best_ms = 1e30f;
         GridInfo base2 = best;
+        const int thmax = (sizeof(T) == 8 && pass == 0) ? 256 : 512;
         for (int th : {128, 256, 512}) {
             if (th > thmax) continue;
             GridInfo g = base2;
