@@ -222,7 +222,7 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     SCK(cudaMemcpyAsync(twd, tw, sizeof(tw), cudaMemcpyHostToDevice, st), "twiddle upload failed");
     SCK(cudaMemcpyAsync(twfd, twf, sizeof(twf), cudaMemcpyHostToDevice, st), "twiddle upload failed");
     FftAxis ax = fft_axis(g.nx, twd), ay = fft_axis(g.ny, twd + kSMaxEdge),
-            az = fft_axis(g.nz, twd + 2 * kSMaxEdge);
+            az = fft_axis(g.nz, twd + 2 * kSMaxEdge, 4);   // the FP64 contexts' z schedule
     ax.twf = twfd;
     ay.twf = twfd + kSMaxEdge;
     az.twf = twfd + 2 * kSMaxEdge;

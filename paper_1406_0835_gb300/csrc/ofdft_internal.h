@@ -79,12 +79,13 @@ struct FftAxis {
 };
 
 // Stockham schedule of one axis: radix-8 stages first, then 4, 2, 3, 5.
-inline FftAxis fft_axis(int n, const void *tw)
+inline FftAxis fft_axis(int n, const void *tw, int maxrad = 8)
 {
     FftAxis a{};
     a.n = n;
     int m = n, ns = 1, k = 0;
     for (int r : {8, 4, 2, 3, 5}) {
+        if (r > maxrad) continue;
         while (m % r == 0 && k < kMaxStages) {
             a.rad[k] = r;
             a.ns[k] = ns;
