@@ -78,14 +78,16 @@ struct FftAxis {
     const void *twf;         // FP64 sets: the same twiddles as double-float pairs (ff::cf2[n])
 };
 
-// Stockham schedule of one axis: radix-8 stages first, then 4, 2, 3, 5.
-inline FftAxis fft_axis(int n, const void *tw, int maxrad = 8)
+// Stockham schedule of one axis: radix-8 stages first, then 4, 2, 3, 5;
+// max_pow2 (8 or 4) caps the power-of-two radices only (2, 3 and 5 always
+// take part, so every {2,3,5}-smooth n factors completely).
+inline FftAxis fft_axis(int n, const void *tw, int max_pow2 = 8)
 {
     FftAxis a{};
     a.n = n;
     int m = n, ns = 1, k = 0;
     for (int r : {8, 4, 2, 3, 5}) {
-        if (r > maxrad) continue;
+        if ((r == 8 || r == 4) && r > max_pow2) continue;
         while (m % r == 0 && k < kMaxStages) {
             a.rad[k] = r;
             a.ns[k] = ns;
