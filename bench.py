@@ -29,8 +29,8 @@ sys.path.insert(0, ROOT)
 # CG evaluations (energy + potential) per step, measured on the GPU path
 # (bench.py reports evals_per_step); converts the oracle's evaluations/s to
 # MD steps/s in the reference arm, which runs without a GPU.
-EVALS_PER_STEP = {"md-vt84f-96": 920.0, "md-sga-96": 300.0, "md-vt84f-96-mixed": 1013.0,
-                  "solve-vt84f-128": 541.0, "solve-vt84f-128-mixed": 630.0, "eval-vt84f-128": 1.0}
+EVALS_PER_STEP = {"md-vt84f-96": 643.0, "md-sga-96": 339.0, "md-vt84f-96-mixed": 700.0,
+                  "solve-vt84f-128": 539.0, "solve-vt84f-128-mixed": 630.0, "eval-vt84f-128": 1.0}
 
 WORKLOADS = {
     "md-vt84f-96": dict(kind="md", functional="vt84f", grid=96, precision="fp64"),
@@ -163,8 +163,8 @@ def fft_flops(n):
 POINTWISE_FLOP = 200.0
 # DRAM bytes per grid point of one k_zgga<DD> launch (the FP64 contexts'
 # double-float kernel), from the ncu capture summarised in
-# profiles/fields_dd_128.md.
-ZGGA_DD_TRAFFIC_PER_POINT = (68.135424e6 + 27.309568e6) / 128 ** 3
+# profiles/k_zgga_dd_96.md (30.8 MB per launch at 96^3).
+ZGGA_DD_TRAFFIC_PER_POINT = (28.92288e6 + 1.876224e6) / 96 ** 3
 # FP32-unit instructions per FP64-equivalent flop of the double-float
 # arithmetic: a sum (two_sum + tail + fast_two_sum) takes 11, a product
 # (two_prod + two FMAs + fast_two_sum) 9; FFT and pointwise work is about two
