@@ -268,22 +268,20 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__rest
     typedef typename KT<PR>::CC CC;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nz = g.nz, K = g.K;
-    CC *buf[4];
-    for (int q = 0; q < 4; ++q) buf[q] = reinterpret_cast<CC *>(smraw) + q * P * nz;
+    // the three components' lines side by side (field a at line a nl), so
+    // each transform is one batch of 3 nl lines; the other half is scratch
     const long long npairs = (long long)g.nx * g.ny / 2;
     const long long p0 = (long long)blockIdx.x * P;
     const int nl = (int)min((long long)P, npairs - p0);
     const long long obase = 2 * p0 * K;
     const long long rbase = 2 * p0 * nz;
+    CC *A = reinterpret_cast<CC *>(smraw);
+    CC *B = A + 3 * P * nz;
     C *spec[3] = {g0, g1, g2};
-    CC *res[3];
-    CC *scratch = buf[3];
-    for (int a = 0; a < 3; ++a) {
-        pack_c2r<PR>(spec[a], obase, nl, nz, K, buf[a]);
-        __syncthreads();
-        res[a] = fft_lines<CC, true>(buf[a], scratch, az, nl, nz, 1, false);
-        if (res[a] == scratch) scratch = buf[a];
-    }
+    for (int a = 0; a < 3; ++a) pack_c2r<PR>(spec[a], obase, nl, nz, K, A + a * nl * nz);
+    __syncthreads();
+    CC *X = fft_lines<CC, true>(A, B, az, 3 * nl, nz, 1, false);
+    CC *res[3] = {X, X + nl * nz, X + 2 * nl * nz};
     R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     const ff::f2 tcoef = is_dd<PR>() ? ff::f2(2.0 / OF_K23 * (double)temp) : ff::f2(0.0f, 0.0f);
     RowCol rc(nz);
@@ -328,13 +326,8 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__rest
         }
     }
     __syncthreads();
-    // scratch is the one buffer not holding a field
-    for (int a = 0; a < 3; ++a) {
-        CC *X = fft_lines<CC, false>(res[a], scratch, az, nl, nz, 1, false);
-        unpack_r2c<PR>(X, obase, nl, nz, K, spec[a]);
-        __syncthreads();
-        if (X == scratch) scratch = res[a];
-    }
+    CC *Y = fft_lines<CC, false>(X, X == A ? B : A, az, 3 * nl, nz, 1, false);
+    for (int a = 0; a < 3; ++a) unpack_r2c<PR>(Y + a * nl * nz, obase, nl, nz, K, spec[a]);
     double tot[6];
     block_total<6, PR>(acc, tot);
     if (threadIdx.x == 0)
@@ -716,7 +709,7 @@ int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, 
     int P = zpairs_per_block(g);
     long long npairs = (long long)g.nx * g.ny / 2;
     int blocks = (int)((npairs + P - 1) / P);
-    size_t sm = 4 * (size_t)P * g.nz * sizeof(cplx<T>);
+    size_t sm = 6 * (size_t)P * g.nz * sizeof(cplx<T>);
     int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
 #define CALL(PR) k_zgga<PR><<<blocks, th, sm, st>>>(g, az, P, g0, g1, g2, phit, temp, fp, tab, xc, vpart, part)
     OFDFT_DISPATCH(T, g, CALL);
@@ -806,7 +799,7 @@ void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const 
 size_t field_smem_max(const GridInfo &g, size_t csize)
 {
     int P = zpairs_per_block(g);
-    size_t z = 4 * (size_t)P * g.nz * csize;
+    size_t z = 6 * (size_t)P * g.nz * csize;
     size_t y = 2 * (size_t)g.ny * g.tk * csize;
     size_t x = 3 * (size_t)g.nx * g.tk * csize;
     size_t m = z > y ? z : y;
