@@ -277,7 +277,7 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
         launch_ypass<T>(g, ay, false, s0, 1, fs, st);
     }
     DBG("k_ypass fwd");
-    int nbz;
+    int nbz, nbg = 0;   // blocks of the z passes (zfinal, zgga): their partial sums
     if (fttf) {
         {
             TimerScope ts(c, TM_XHL);
@@ -305,7 +305,7 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
         DBG("k_ypass inv x3");
         {
             TimerScope ts(c, TM_ZGGA);
-            launch_zgga<T>(g, az, s1, s2, s3, ph, (T)c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, st);
+            nbg = launch_zgga<T>(g, az, s1, s2, s3, ph, (T)c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, st);
         }
         DBG("k_zgga");
         {
@@ -329,7 +329,7 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
     }
     DBG("k_zfinal");
     launch_reduce(pA, nbx, 3, sums, st);
-    if (!fttf) launch_reduce(pB, nbz, 6, sums + 3, st);
+    if (!fttf) launch_reduce(pB, nbg, 6, sums + 3, st);
     launch_reduce(pC, nbz, 9, sums + 9, st);
     DBG("k_reduce");
     c->launches += eval_kernel_count(c);

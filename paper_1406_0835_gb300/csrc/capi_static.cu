@@ -250,7 +250,7 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     const bool fttf = fp.kind == 0;
     launch_zfwd<double>(g, az, 1, nullptr, ph, nullptr, 0.0, 0.0, nullptr, nullptr, s0, st);
     launch_ypass<double>(g, ay, false, s0, 1, specN, st);
-    int nbz;
+    int nbz, nbg = 0;   // blocks of the z passes (zfinal, zgga): their partial sums
     if (fttf) {
         launch_xhl<double>(g, ax, s0, vext, nullptr, 1, pA, st);
         launch_ypass<double>(g, ay, true, s0, 1, specN, st);
@@ -259,7 +259,7 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     } else {
         launch_xgrad<double>(g, ax, s0, vext, s1, s2, s3, pA, st);
         launch_ypass<double>(g, ay, true, s1, 3, specN, st);
-        launch_zgga<double>(g, az, s1, s2, s3, ph, T, fp, tab, xc, vpart, pB, st);
+        nbg = launch_zgga<double>(g, az, s1, s2, s3, ph, T, fp, tab, xc, vpart, pB, st);
         launch_ypass<double>(g, ay, false, s1, 3, specN, st);
         launch_xdiv<double>(g, ax, s0, vext, s1, s2, s3, st);
         launch_ypass<double>(g, ay, true, s1, 1, specN, st);
@@ -267,7 +267,7 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
                                     tab, xc, v_dev, pC, st);
     }
     launch_reduce(pA, nbx, 3, scal, st);
-    if (!fttf) launch_reduce(pB, nbz, 6, scal + 3, st);
+    if (!fttf) launch_reduce(pB, nbg, 6, scal + 3, st);
     launch_reduce(pC, nbz, 9, scal + 9, st);
     double h[18];
     SCK(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, st), "scalar read-back failed");

@@ -70,9 +70,9 @@ template <> __device__ __forceinline__ ff::f2 fourpi<DD>()
     constexpr ff::f2 c(kFourPi);
     return c;
 }
-// scalar read in binary64 (double-float: correctly rounded split)
+// scalar read in binary64 (double-float: the integer split, no FP64 unit work)
 template <typename PR> __device__ __forceinline__ typename KT<PR>::R scal(typename KT<PR>::T x) { return x; }
-template <> __device__ __forceinline__ ff::f2 scal<DD>(double x) { return ff::f2(x); }
+template <> __device__ __forceinline__ ff::f2 scal<DD>(double x) { return ff::split_int(x); }
 
 // Block totals of per-thread accumulators (double-float ones are converted
 // to binary64 first).
@@ -662,6 +662,16 @@ int zpairs_per_block(const GridInfo &g)
     return P;
 }
 
+// zfwd and zfinal do little work per point: at least 4 pairs per block
+// (when the tuned z shape has fewer) so their transforms fill the block.
+int zpairs_light(const GridInfo &g)
+{
+    int P = zpairs_per_block(g);
+    if (P < 4) P = 4;
+    while (P > 1 && (long long)P * g.nz > 2048) --P;
+    return P;
+}
+
 int threads_for(int work)
 {
     int t = 64;
@@ -688,7 +698,7 @@ template <typename T>
 void launch_zfwd(const GridInfo &g, const FftAxis &az, int mode, const T *in, const T *phi,
                  const T *dhat, T c, T s, const void *cs, T *phit, cplx<T> *out, cudaStream_t st)
 {
-    int P = zpairs_per_block(g);
+    int P = zpairs_light(g);
     long long npairs = (long long)g.nx * g.ny / 2;
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 2 * (size_t)P * g.nz * sizeof(cplx<T>);
@@ -723,7 +733,7 @@ int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T>
                   const void *cs, T temp, const FuncParams &fp, const T *tab, int xc, T *vout,
                   double *part, cudaStream_t st)
 {
-    int P = zpairs_per_block(g);
+    int P = zpairs_light(g);
     long long npairs = (long long)g.nx * g.ny / 2;
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 2 * (size_t)P * g.nz * sizeof(cplx<T>);
