@@ -20,11 +20,17 @@ STATUS = {0: "OFDFT_OK", -1: "OFDFT_EINVAL", -2: "OFDFT_ENOMEM", -3: "OFDFT_ENOC
 
 _P = ctypes.POINTER(ctypes.c_double)
 
-# Gradient tolerance of the batched and serving mixed-precision forms: their
-# results then stay within 1e-6 Ha/atom (free energy), 1e-4 Ha/bohr (forces)
-# and 1e-3 relative (pressure) of the FP64 path at gtol 1e-8, with margin
-# (tests/test_gpu_mixed.py checks it at 10 kK, 250 kK and 4 MK).
-MIXED_FORM_GTOL = 1e-6
+# Gradient tolerances of the batched and serving mixed-precision forms.
+# Single points (the batched form) to 1e-5 stay within 1e-6 Ha/atom (free
+# energy), 1e-4 Ha/bohr (forces) and 1e-3 relative (pressure) of the FP64
+# path at gtol 1e-8, with margin (measured over the 64-instance batch:
+# 5e-8 Ha/atom, 1.1e-6 Ha/bohr, 1.4e-5; tests/test_gpu_mixed.py checks it at
+# 10 kK, 250 kK and 4 MK).  MD requests (the serving form) converge every
+# step to 1e-6: their per-step force errors feed the trajectory, and at 1e-5
+# five steps already moved the free energy by 4.5e-6 Ha/atom (at 1e-6:
+# 1.7e-7).
+MIXED_FORM_GTOL = 1e-5
+MIXED_MD_GTOL = 1e-6
 
 
 class Params(ctypes.Structure):
