@@ -113,6 +113,14 @@ __device__ __forceinline__ Gk<A> gvec(const GridInfo &g, A bx, A by, A bz, int i
     return r;
 }
 
+// First-derivative multiplier along one axis: k b with k the signed index
+// of i on an axis of n points, 0 on the Nyquist plane (as Gk's dx, dy, dz).
+template <typename A> __device__ __forceinline__ A dmul(int i, int n, A b)
+{
+    const int k = i <= n / 2 ? i : i - n;
+    return (2 * i == n) ? A(0) : A(k) * b;
+}
+
 // Pointwise functional of the double-float z passes: the double-float
 // routine, and binary64 outside its domain.  n and gr[3] in double-float.
 __device__ __forceinline__ PwF2 pw_dd(const FuncParams &fp, const double *__restrict__ tab, ff::f2 tcoef,
@@ -518,11 +526,12 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
     __syncthreads();
     store_tile<PR>(nspec, t, nx, N);
     C *outs[3] = {g0, g1, g2};
+    const R dy = dmul<R>(t.outer, g.ny, by);   // the tile's one iy
     for (int a = 0; a < 3; ++a) {
         for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
             const int r = i >> t.tsh, c = i & (t.tk - 1);
-            Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + min(c, t.ncol - 1));
-            R d = a == 0 ? k.dx : (a == 1 ? k.dy : k.dz);
+            const R d = a == 0 ? dmul<R>(r, g.nx, bx)
+                               : (a == 1 ? dy : dmul<R>(t.kz0 + min(c, t.ncol - 1), g.nz, bz));
             CC v = N[i];
             A[i] = cmk<CC>(-d * v.y, d * v.x);      // i D_a n(G)
         }
@@ -633,6 +642,7 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
         D[i] = out;
     }
     const C *ws[3] = {w0, w1, w2};
+    const R dy = dmul<R>(t.outer, g.ny, by);   // the tile's one iy
     for (int a = 0; a < 3; ++a) {
         load_tile<PR>(ws[a], t, nx, A);
         __syncthreads();
@@ -640,8 +650,7 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
         for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
             const int r = i >> t.tsh, c = i & (t.tk - 1);
             if (c >= t.ncol) continue;
-            Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
-            R d = (a == 0 ? k.dx : (a == 1 ? k.dy : k.dz)) * invN;
+            const R d = (a == 0 ? dmul<R>(r, g.nx, bx) : (a == 1 ? dy : dmul<R>(t.kz0 + c, g.nz, bz))) * invN;
             CC wv = X[i];
             D[i] = cmk<CC>(D[i].x + d * wv.y, D[i].y - d * wv.x);   // -= i d W
         }
