@@ -163,8 +163,8 @@ def fft_flops(n):
 POINTWISE_FLOP = 200.0
 # DRAM bytes per grid point of one k_zgga<DD> launch (the FP64 contexts'
 # double-float kernel), from the ncu capture summarised in
-# profiles/k_zgga_dd_96.md (30.8 MB per launch at 96^3).
-ZGGA_DD_TRAFFIC_PER_POINT = (28.92288e6 + 1.876224e6) / 96 ** 3
+# profiles/k_zgga_dd_96.md (29.6 MB per launch at 96^3).
+ZGGA_DD_TRAFFIC_PER_POINT = (28.925952e6 + 0.652288e6) / 96 ** 3
 # FP32-unit instructions per FP64-equivalent flop of the double-float
 # arithmetic: a sum (two_sum + tail + fast_two_sum) takes 11, a product
 # (two_prod + two FMAs + fast_two_sum) 9; FFT and pointwise work is about two
