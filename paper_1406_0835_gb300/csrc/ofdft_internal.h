@@ -39,28 +39,6 @@ template <typename C, bool INV> __host__ __device__ __forceinline__ C cmuli(C a)
     return INV ? cmk<C>(-a.y, a.x) : cmk<C>(a.y, -a.x);
 }
 
-// ------------------------------------------------- division by constants
-// Division by a fixed d (1 <= d < 2^16) of dividends 0 <= x < 2^16 with one
-// wide multiply: with m = ceil(2^32 / d), floor(x m / 2^32) = floor(x / d),
-// since the excess x (m d - 2^32) / (d 2^32) < x / 2^32 < 1 / d.
-struct FastDiv {
-    unsigned long long m;
-    int d;
-};
-
-inline FastDiv make_fastdiv(int d)
-{
-    FastDiv f;
-    f.d = d;
-    f.m = ((1ull << 32) + (unsigned long long)d - 1) / (unsigned long long)d;
-    return f;
-}
-
-__host__ __device__ __forceinline__ int fdiv(int x, const FastDiv &f)
-{
-    return (int)(((unsigned long long)(unsigned)x * f.m) >> 32);
-}
-
 // ------------------------------------------------------------ FFT plans
 constexpr int kMaxStages = 16;
 
@@ -72,8 +50,6 @@ struct FftAxis {
     int rad[kMaxStages];
     int ns[kMaxStages];      // product of the radices before each stage
     int tws[kMaxStages];     // twiddle stride n / (ns * rad)
-    FastDiv nbd[kMaxStages]; // division by n / rad (butterflies per line)
-    FastDiv nsd[kMaxStages]; // division by ns
     const void *tw;          // cplx<T>[n]
     const void *twf;         // FP64 sets: the same twiddles as double-float pairs (ff::cf2[n])
 };
@@ -92,8 +68,6 @@ inline FftAxis fft_axis(int n, const void *tw, int max_pow2 = 8)
             a.rad[k] = r;
             a.ns[k] = ns;
             a.tws[k] = n / (ns * r);
-            a.nbd[k] = make_fastdiv(n / r);
-            a.nsd[k] = make_fastdiv(ns);
             ns *= r;
             m /= r;
             ++k;
@@ -114,7 +88,6 @@ struct GridInfo {
     double bx, by, bz;       // reciprocal spacing 2 pi / L per axis
     double invN, hr;         // 1 / N, rc^2 / 2
     float bxf, byf, bzf, invNf, hrf;   // the same in FP32 (for the FP32 kernels)
-    FastDiv dnz, dK;         // division by nz and by K
     int zP;                  // z passes: line pairs per block (0: default rule)
     int tk;                  // y/x passes: half-spectrum columns per tile (4, 8 or 16)
     int zth, xth;            // threads per block of the z and of the y/x passes (0: default rule)
@@ -143,8 +116,6 @@ inline void grid_reciprocal(GridInfo &g)
     g.bzf = (float)g.bz;
     g.invNf = (float)g.invN;
     g.hrf = (float)g.hr;
-    g.dnz = make_fastdiv(g.nz);
-    g.dK = make_fastdiv(g.K);
 }
 
 // The FP64 or FP32 copy of a grid constant, for kernels templated on A.
