@@ -263,7 +263,7 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
     const C *vext = (const C *)f.vext;
     const T *tab = (const T *)f.tab;
     const bool fttf = c->fp.kind == 0;
-    const int ntk = (g.K + g.tk - 1) / g.tk, nbx = g.ny * ntk;
+    const int nbx = xpass_blocks(g);
     const long long npairs = (long long)g.nx * g.ny / 2;
     double *pA = c->part, *pB = pA + 3 * nbx, *pC = pB + 6 * npairs;
     {

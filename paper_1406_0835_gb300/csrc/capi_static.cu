@@ -94,8 +94,8 @@ ofdft_status device_setup(int dev, unsigned char **base)
         int optin = 0;
         SCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
             "device attribute query failed");
-        set_field_smem_limits<double>((size_t)optin);
-        SCK(cudaGetLastError(), "shared-memory limit set-up failed");
+        // leave room for the kernels' static shared memory, as ofdft_setup does
+        SCK(set_field_smem_limits<double>((size_t)optin - 8192), "shared-memory limit set-up failed");
         d.ready = true;
     }
     *base = d.base;
@@ -243,7 +243,7 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     double *vpart = (double *)(base + kOffVpart);
     double *part = (double *)(base + kOffPart), *scal = (double *)(base + kOffScal);
     SCK(cudaMemsetAsync(scal, 0, 64 * sizeof(double), st), "scalar clear failed");
-    const int ntk = (g.K + 7) / 8, nbx = g.ny * ntk;
+    const int nbx = xpass_blocks(g);
     const long long npairs = (long long)g.nx * g.ny / 2;
     double *pA = part, *pB = pA + 3 * nbx, *pC = pB + 6 * npairs;
     double *ph = const_cast<double *>(phi_dev);

@@ -31,6 +31,8 @@ template <typename T>
 void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const cplx<T> *vext,
                  cplx<T> *w0, const cplx<T> *w1, const cplx<T> *w2, cudaStream_t st);
 size_t field_smem_max(const GridInfo &g, size_t csize);
+// blocks (and partial sums per quantity) of the x passes
+int xpass_blocks(const GridInfo &g);
 template <typename T> cudaError_t set_field_smem_limits(size_t bytes);
 
 // ---- vectors, reductions, ions (kernels_misc.cu)

@@ -418,33 +418,51 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const typename KT<PR>::C
 }
 
 // ------------------------------------------------------------- y/x passes
-// Tile: g.tk consecutive kz columns of one ix-plane (y pass) or one iy-row
-// (x pass); rows are the transformed axis.
+// Tile: g.tk consecutive columns of the flattened (ix, kz) index space (y
+// pass, rows iy) or (iy, kz) space (x pass, rows ix), so every tile but the
+// last is full although kz runs over K = nz/2 + 1 values; rows are the
+// transformed axis.  Each column's base offset, outer index (ix or iy) and
+// kz are worked out once per block into shared memory (columns past the end
+// repeat the last one).
 
 struct ColTile {
-    long long base;   // offset of (row 0, kz0) in the field
     long long rstride;
-    int kz0, ncol, outer, tk, tsh;   // tk = 2^tsh columns (4, 8 or 16)
+    int ncol, tk, tsh;                // tk = 2^tsh columns (4, 8 or 16)
+    const long long *cbase;           // offset of (row 0, column c)
+    const int *couter, *ckz;          // ix (y pass) or iy (x pass), and kz
 };
 
 __device__ __forceinline__ ColTile col_tile(const GridInfo &g, bool xaxis)
 {
+    __shared__ long long s_cb[16];
+    __shared__ int s_co[16], s_ck[16];
     const int tk = g.tk;
-    const int ntk = (g.K + tk - 1) / tk;
+    const long long total = (long long)(xaxis ? g.ny : g.nx) * g.K;
+    const long long col0 = (long long)blockIdx.x * tk;
     ColTile t;
     t.tk = tk;
     t.tsh = __ffs(tk) - 1;
-    t.outer = blockIdx.x / ntk;
-    t.kz0 = (blockIdx.x - t.outer * ntk) * tk;
-    t.ncol = min(tk, g.K - t.kz0);
-    if (xaxis) {
-        t.base = (long long)t.outer * g.K + t.kz0;   // outer = iy
-        t.rstride = (long long)g.ny * g.K;
-    } else {
-        t.base = (long long)t.outer * g.ny * g.K + t.kz0;  // outer = ix
-        t.rstride = g.K;
+    t.ncol = (int)min((long long)tk, total - col0);
+    t.rstride = xaxis ? (long long)g.ny * g.K : (long long)g.K;
+    if (threadIdx.x < tk) {
+        const long long col = col0 + min((int)threadIdx.x, t.ncol - 1);
+        const int outer = (int)(col / g.K), kz = (int)(col - (long long)outer * g.K);
+        s_co[threadIdx.x] = outer;
+        s_ck[threadIdx.x] = kz;
+        s_cb[threadIdx.x] = xaxis ? col : (long long)outer * g.ny * g.K + kz;
     }
+    __syncthreads();
+    t.cbase = s_cb;
+    t.couter = s_co;
+    t.ckz = s_ck;
     return t;
+}
+
+// Column tiles of one field: the grid's x dimension of the y and x passes.
+__host__ __device__ __forceinline__ int tiles_of(const GridInfo &g, bool xaxis)
+{
+    const long long total = (long long)(xaxis ? g.ny : g.nx) * g.K;
+    return (int)((total + g.tk - 1) / g.tk);
 }
 
 template <typename PR>
@@ -453,7 +471,7 @@ __device__ __forceinline__ void load_tile(const typename KT<PR>::C *__restrict__
 {
     for (int i = threadIdx.x; i < nrows * t.tk; i += blockDim.x) {
         const int r = i >> t.tsh, c = i & (t.tk - 1);
-        if (c < t.ncol) dst[i] = ldc<PR>(src[t.base + r * t.rstride + c]);
+        if (c < t.ncol) dst[i] = ldc<PR>(src[t.cbase[c] + r * t.rstride]);
     }
 }
 
@@ -463,7 +481,7 @@ __device__ __forceinline__ void store_tile(typename KT<PR>::C *__restrict__ dst,
 {
     for (int i = threadIdx.x; i < nrows * t.tk; i += blockDim.x) {
         const int r = i >> t.tsh, c = i & (t.tk - 1);
-        if (c < t.ncol) dst[t.base + r * t.rstride + c] = stc<PR>(src[i]);
+        if (c < t.ncol) dst[t.cbase[c] + r * t.rstride] = stc<PR>(src[i]);
     }
 }
 
@@ -513,9 +531,9 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
         if (c >= t.ncol) continue;
         CC nG = cscale(X[i], invN);
         N[i] = nG;
-        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
+        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.couter[c], t.ckz[c]);
         if (k.g2 > R(0)) {
-            CC ve = ldc<PR>(vext[t.base + r * t.rstride + c]);
+            CC ve = ldc<PR>(vext[t.cbase[c] + r * t.rstride]);
             R n2 = nG.x * nG.x + nG.y * nG.y;
             R re = nG.x * ve.x + nG.y * ve.y;
             acc[0] += k.w * n2 / k.g2;
@@ -526,12 +544,11 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
     __syncthreads();
     store_tile<PR>(nspec, t, nx, N);
     C *outs[3] = {g0, g1, g2};
-    const R dy = dmul<R>(t.outer, g.ny, by);   // the tile's one iy
     for (int a = 0; a < 3; ++a) {
         for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
             const int r = i >> t.tsh, c = i & (t.tk - 1);
             const R d = a == 0 ? dmul<R>(r, g.nx, bx)
-                               : (a == 1 ? dy : dmul<R>(t.kz0 + min(c, t.ncol - 1), g.nz, bz));
+                               : (a == 1 ? dmul<R>(t.couter[c], g.ny, by) : dmul<R>(t.ckz[c], g.nz, bz));
             CC v = N[i];
             A[i] = cmk<CC>(-d * v.y, d * v.x);      // i D_a n(G)
         }
@@ -578,8 +595,8 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
         const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c >= t.ncol) continue;
         CC nG = cscale(X[i], invN);
-        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
-        CC ve = ldc<PR>(vext[t.base + r * t.rstride + c]);
+        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.couter[c], t.ckz[c]);
+        CC ve = ldc<PR>(vext[t.cbase[c] + r * t.rstride]);
         CC out = cmk<CC>(R(0), R(0));
         if (k.g2 > R(0)) {
             R n2 = nG.x * nG.x + nG.y * nG.y;
@@ -590,7 +607,7 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
             R kh = fpi / k.g2;
             out = cmk<CC>(kh * nG.x + ve.x, kh * nG.y + ve.y);
         }
-        if (nG_out != nullptr) nG_out[t.base + r * t.rstride + c] = stc<PR>(nG);
+        if (nG_out != nullptr) nG_out[t.cbase[c] + r * t.rstride] = stc<PR>(nG);
         X[i] = out;
     }
     __syncthreads();
@@ -631,18 +648,17 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c >= t.ncol) continue;
-        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.outer, t.kz0 + c);
+        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.couter[c], t.ckz[c]);
         CC out = cmk<CC>(R(0), R(0));
         if (k.g2 > R(0)) {
-            CC n = ldc<PR>(nG[t.base + r * t.rstride + c]);
-            CC ve = ldc<PR>(vext[t.base + r * t.rstride + c]);
+            CC n = ldc<PR>(nG[t.cbase[c] + r * t.rstride]);
+            CC ve = ldc<PR>(vext[t.cbase[c] + r * t.rstride]);
             R kh = fpi / k.g2;
             out = cmk<CC>(kh * n.x + ve.x, kh * n.y + ve.y);
         }
         D[i] = out;
     }
     const C *ws[3] = {w0, w1, w2};
-    const R dy = dmul<R>(t.outer, g.ny, by);   // the tile's one iy
     for (int a = 0; a < 3; ++a) {
         load_tile<PR>(ws[a], t, nx, A);
         __syncthreads();
@@ -650,7 +666,8 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
         for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
             const int r = i >> t.tsh, c = i & (t.tk - 1);
             if (c >= t.ncol) continue;
-            const R d = (a == 0 ? dmul<R>(r, g.nx, bx) : (a == 1 ? dy : dmul<R>(t.kz0 + c, g.nz, bz))) * invN;
+            const R d = (a == 0 ? dmul<R>(r, g.nx, bx)
+                                : (a == 1 ? dmul<R>(t.couter[c], g.ny, by) : dmul<R>(t.ckz[c], g.nz, bz))) * invN;
             CC wv = X[i];
             D[i] = cmk<CC>(D[i].x + d * wv.y, D[i].y - d * wv.x);   // -= i d W
         }
@@ -763,8 +780,7 @@ template <typename T>
 void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data, int nfields,
                   long long fstride, cudaStream_t st)
 {
-    int ntk = (g.K + g.tk - 1) / g.tk;
-    dim3 grid(g.nx * ntk, nfields);
+    dim3 grid(tiles_of(g, false), nfields);
     size_t sm = 2 * (size_t)g.ny * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.ny * g.tk / 2);
 #define CALL(PR)                                                            \
@@ -778,8 +794,7 @@ template <typename T>
 int launch_xgrad(const GridInfo &g, const FftAxis &ax, cplx<T> *nspec, const cplx<T> *vext,
                  cplx<T> *g0, cplx<T> *g1, cplx<T> *g2, double *part, cudaStream_t st)
 {
-    int ntk = (g.K + g.tk - 1) / g.tk;
-    int blocks = g.ny * ntk;
+    int blocks = tiles_of(g, true);
     size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
 #define CALL(PR) k_xgrad<PR><<<blocks, th, sm, st>>>(g, ax, nspec, vext, g0, g1, g2, part)
@@ -792,8 +807,7 @@ template <typename T>
 int launch_xhl(const GridInfo &g, const FftAxis &ax, cplx<T> *spec, const cplx<T> *vext,
                cplx<T> *nG_out, int inverse, double *part, cudaStream_t st)
 {
-    int ntk = (g.K + g.tk - 1) / g.tk;
-    int blocks = g.ny * ntk;
+    int blocks = tiles_of(g, true);
     size_t sm = 2 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
 #define CALL(PR) k_xhl<PR><<<blocks, th, sm, st>>>(g, ax, spec, vext, nG_out, inverse, part)
@@ -806,14 +820,15 @@ template <typename T>
 void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const cplx<T> *vext,
                  cplx<T> *w0, const cplx<T> *w1, const cplx<T> *w2, cudaStream_t st)
 {
-    int ntk = (g.K + g.tk - 1) / g.tk;
-    int blocks = g.ny * ntk;
+    int blocks = tiles_of(g, true);
     size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
 #define CALL(PR) k_xdiv<PR><<<blocks, th, sm, st>>>(g, ax, nG, vext, w0, w1, w2)
     OFDFT_DISPATCH(T, g, CALL);
 #undef CALL
 }
+
+int xpass_blocks(const GridInfo &g) { return tiles_of(g, true); }
 
 size_t field_smem_max(const GridInfo &g, size_t csize)
 {
