@@ -61,15 +61,19 @@ typedef enum {
                          search, Ewald and forces; final energies in FP64 */
 } ofdft_precision;
 
-/* Arithmetic of the pointwise functional (f_s, its derivatives and PZ81,
- * Eqs. (FGGA), (vftGGA), (vxc1)) on FP64 field sets.  The FFTs, reductions
- * and CG stay in binary64 either way. */
+/* Arithmetic of the FP64 field sets' evaluation kernels: the FFTs, the
+ * G-space terms and the pointwise functional (f_s, its derivatives and PZ81,
+ * Eqs. (FGGA), (vftGGA), (vxc1)).  Fields and spectra stay binary64 in
+ * memory, and the reductions, CG scalars, forces and MD stay binary64,
+ * either way. */
 typedef enum {
     OFDFT_PW_F32X2 = 0,  /* double-float pairs on the FP32 units (about 48
-                            significant bits; agrees with binary64 to a few
-                            parts in 1e14); points outside its range (n
-                            outside [1e-18, 1e18], s^2 > 1e10, t outside the
-                            tabulated [2^-20, 2^34)) use binary64 */
+                            significant bits): the energy agrees with the
+                            binary64 kernels to about 1e-13 relative, the
+                            pointwise terms to about 1e-13 of their size;
+                            points outside the pointwise routine's range
+                            (n outside [1e-18, 1e18], s^2 > 1e10, t outside
+                            the tabulated [2^-20, 2^34)) use binary64 */
     OFDFT_PW_F64 = 1     /* binary64 throughout */
 } ofdft_pointwise;
 
@@ -80,7 +84,7 @@ typedef struct {
     int precision;    /* ofdft_precision */
     int device;       /* CUDA device ordinal */
     void *stream;     /* cudaStream_t to run on, or NULL for a library stream */
-    int pointwise;    /* ofdft_pointwise (FP64 field sets only) */
+    int pointwise;    /* ofdft_pointwise: arithmetic of the FP64 field sets */
 } ofdft_params;
 
 /* Energy partition (Sec. V C sample output) and pressure terms; hartree,

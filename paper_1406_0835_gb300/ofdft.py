@@ -381,7 +381,9 @@ def ofdft_destroy(ctx):
 
 # ------------------------------------------------------------ convenience
 class Context:
-    """One OF-DFT system on one GPU (owns a libofdft context)."""
+    """One OF-DFT system on one GPU (owns a libofdft context).  precision:
+    "fp64" or "mixed"; pointwise: arithmetic of the FP64 field sets, "f32x2"
+    (double-float on the FP32 units, the default) or "f64" (binary64)."""
 
     def __init__(self, L, grid, ions, Z, T_kelvin, functional="fttf", xc=True, rc=0.25,
                  precision="fp64", device=0, stream=None, pointwise="f32x2"):
