@@ -73,7 +73,11 @@ typedef enum {
                             pointwise terms to about 1e-13 of their size;
                             points outside the pointwise routine's range
                             (n outside [1e-18, 1e18], s^2 > 1e10, t outside
-                            the tabulated [2^-20, 2^34)) use binary64 */
+                            the tabulated [2^-20, 2^34)) use binary64.
+                            Intermediate values keep the binary32 exponent
+                            range: a density whose potential passes 3e38
+                            (GGA functionals next to n ~ 1e-20) gives
+                            OFDFT_ENUMERIC here and needs OFDFT_PW_F64 */
     OFDFT_PW_F64 = 1     /* binary64 throughout */
 } ofdft_pointwise;
 

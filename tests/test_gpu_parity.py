@@ -81,6 +81,31 @@ def test_double_float_pointwise_matches_binary64(fn):
     assert rel(Ema["F_tot"], Emb["F_tot"]) <= 1e-11
 
 
+@pytest.mark.parametrize("fn,tiny", [("fttf", 1e-11), ("vt84f", 1e-6)])
+def test_double_float_kernels_fall_back_to_binary64(fn, tiny):
+    """Points outside the double-float pointwise domain take the binary64
+    routine inside the double-float kernels: n < 1e-18 (ftTF, phi = 1e-11 at
+    every 97th point), s^2 > 1e10 (VT84F, phi = 1e-6 there) and t below the
+    table at every point (0.1 K).  The result matches the binary64 kernels.
+    (The VT84F potential then reaches 6e22; a density whose potential
+    leaves the binary32 exponent range, 3.4e38, is outside what the
+    double-float kernels represent.)"""
+    cfg = inputs.config_single_point()
+    grid = (16, 16, 16)
+    rng = np.random.default_rng(5)
+    for T in (cfg["T"], 0.1):
+        so = O.System(cfg["L"], grid, cfg["ions"], cfg["Z"], T, fn)
+        phi = so.uniform_phi() * (1.0 + 0.1 * rng.standard_normal(grid))
+        phi.reshape(-1)[::97] = tiny
+        out = {}
+        for pw in ("f32x2", "f64"):
+            with ofdft.Context(cfg["L"], grid, cfg["ions"], cfg["Z"], T, fn, pointwise=pw) as ctx:
+                out[pw] = ctx.energy_potential(phi)
+        (Ea, va), (Eb, vb) = out["f32x2"], out["f64"]
+        assert abs(Ea["F_tot"] - Eb["F_tot"]) <= 1e-12 * abs(Eb["F_tot"]), (T, Ea["F_tot"], Eb["F_tot"])
+        assert np.max(np.abs(va - vb)) <= 1e-11 * np.max(np.abs(vb)), T
+
+
 def test_uniform_density_and_temperature_extremes():
     """s = 0 exactly (removable 0/0 of VT84F) and t over the table's range."""
     for T, rho in ((2.0e3, 10.0), (4.0e6, 0.1), (1.0e5, 1.0)):
