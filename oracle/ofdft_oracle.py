@@ -308,6 +308,47 @@ def lpp_form(G2, omega, rc):
     return w
 
 
+# Heine-Abarenkov hydrogen LPP, Eq. (E4A): parameters printed for H.
+HA_H = dict(rc=0.25, A=6.18, qc=29.97)
+
+
+def lpp_form_ha(G2, omega, Z, rc, A, qc):
+    """Heine-Abarenkov local pseudopotential of one ion, Eq. (E4A):
+    w(q) = -4 pi/(Omega q^2) [(Z - A rc) cos(q rc) + (A/q) sin(q rc)] f(q),
+    f(q) = exp(-(q/qc)^6), q = |G|, G = 0 dropped.  Not proportional to Z."""
+    q = np.sqrt(G2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        B = (Z - A * rc) * np.cos(q * rc) + (A / q) * np.sin(q * rc)
+        w = -4.0 * math.pi * B * np.exp(-(q / qc) ** 6) / (omega * G2)
+    w[G2 == 0.0] = 0.0
+    return w
+
+
+def lpp_pform_ha(G2, omega, Z, rc, A, qc):
+    """Volume-derivative weight of Eq. (E4A) for the pressure: the LPP term is
+    sum_G Re[n*(G) sum_I wp_I(G) e^{-iG.R_I}] with wp = w + (q/3) dw/dq
+    (Omega w(q) depends on the cell only through q; Omega n(G) and the
+    fractional coordinates are fixed under a uniform dilation)."""
+    q = np.sqrt(G2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s, c = np.sin(q * rc), np.cos(q * rc)
+        B = (Z - A * rc) * c + (A / q) * s
+        dB = -(Z - A * rc) * rc * s + A * (rc * c / q - s / (q * q))   # dB/dq
+        f = np.exp(-(q / qc) ** 6)
+        df = -6.0 * q ** 5 / qc ** 6 * f                              # df/dq
+        w = -4.0 * math.pi * B * f / (omega * G2)
+        dw = -4.0 * math.pi / omega * ((dB * f + B * df) / G2 - 2.0 * B * f / (G2 * q))
+        wp = w + q * dw / 3.0
+    wp[G2 == 0.0] = 0.0
+    return wp
+
+
+def alpha_z_ha(Z, rc, A):
+    """G -> 0 limit of Omega w(q) + 4 pi Z/q^2 for Eq. (E4A): the integral of
+    v(r) + Z/r over the core of the model (v = -A inside rc, -Z/r outside)."""
+    return 2.0 * math.pi * Z * rc * rc - 4.0 * math.pi / 3.0 * A * rc ** 3
+
+
 def structure_phase(grid, R):
     """exp(-i G.R) on the full box (separable in x, y, z), + Nyquist convention."""
     return (np.exp(-1j * grid.Gx * R[0]) * np.exp(-1j * grid.Gy * R[1])
@@ -320,6 +361,15 @@ def lpp_vG(grid, R, Z, rc):
     vG = np.zeros(grid.shape, dtype=np.complex128)
     for I in range(len(Z)):
         vG += Z[I] * w * structure_phase(grid, R[I])
+    return vG
+
+
+def lpp_vG_ha(grid, R, Z, rc, A, qc, form=lpp_form_ha):
+    """v_ext(G) = sum_I w_I(G) exp(-i G.R_I) with the Eq. (E4A) form of each
+    ion (form=lpp_pform_ha gives the pressure weights instead)."""
+    vG = np.zeros(grid.shape, dtype=np.complex128)
+    for I in range(len(Z)):
+        vG += form(grid.G2, grid.omega, Z[I], rc, A, qc) * structure_phase(grid, R[I])
     return vG
 
 
@@ -390,7 +440,12 @@ class System:
     """
 
     def __init__(self, L, shape, ions, Z, T_kelvin, functional="fttf",
-                 rc=0.25, xc=True):
+                 rc=0.25, xc=True, lpp="gauss", ha_A=HA_H["A"], ha_qc=HA_H["qc"]):
+        if lpp not in ("gauss", "ha"):
+            raise ValueError("lpp must be 'gauss' or 'ha'")
+        self.lpp = lpp
+        self.ha_A = float(ha_A)
+        self.ha_qc = float(ha_qc)
         self.grid = Grid(L, shape)
         self.R = np.array(ions, dtype=np.float64).reshape(-1, 3)
         self.Z = np.array(Z, dtype=np.float64).reshape(-1)
@@ -403,7 +458,12 @@ class System:
 
     def set_positions(self, R):
         self.R = np.array(R, dtype=np.float64).reshape(-1, 3)
-        self.vG = lpp_vG(self.grid, self.R, self.Z, self.rc)
+        if self.lpp == "ha":
+            args = (self.grid, self.R, self.Z, self.rc, self.ha_A, self.ha_qc)
+            self.vG = lpp_vG_ha(*args)
+            self.vpG = lpp_vG_ha(*args, form=lpp_pform_ha)
+        else:
+            self.vG = lpp_vG(self.grid, self.R, self.Z, self.rc)
         self.v_ext = self.grid.to_r(self.vG)
         self.E_ion, self.F_ion = ewald(self.grid.L, self.R, self.Z)
 
@@ -454,10 +514,14 @@ def evaluate(sys, phi):
     # pressure: P = -(1/3) Tr Sigma (Eq. (pressure)), term by term
     P_s = (g.integrate(n * v_s - fs["f"]) + WdotG / 3.0) / g.omega  # Eqs. (stressTF_a,b)
     P_H = E_H / (3.0 * g.omega)
-    P_loc = (1.0 / 3.0) * float(np.real(np.sum(
-        np.conj(nG) * sys.vG * (1.0 - g.G2 * sys.rc ** 2 / 2.0))))
+    if sys.lpp == "ha":
+        P_loc = float(np.real(np.sum(np.conj(nG) * sys.vpG)))
+        E_alphaZ = sys.Ne * float(np.sum(alpha_z_ha(sys.Z, sys.rc, sys.ha_A))) / g.omega
+    else:
+        P_loc = (1.0 / 3.0) * float(np.real(np.sum(
+            np.conj(nG) * sys.vG * (1.0 - g.G2 * sys.rc ** 2 / 2.0))))
+        E_alphaZ = sys.Ne * float(np.sum(math.pi * sys.Z * sys.rc ** 2)) / g.omega
     P_ion = sys.E_ion / (3.0 * g.omega)
-    E_alphaZ = sys.Ne * float(np.sum(math.pi * sys.Z * sys.rc ** 2)) / g.omega
     return dict(F_tot=F_tot, F_el=F_el, F_s=F_s, minus_TS=-TS, E_H=E_H,
                 E_loc=E_loc, F_xc=F_xc, E_ion=sys.E_ion, E_int=F_tot + TS,
                 v=v, v_s=v_s, n=n, nG=nG, gradn=gradn,
@@ -587,14 +651,18 @@ def forces(sys, ev):
     """F_I = -int n grad_I v_ext - grad_I E_ion (Eq. (M12)).
 
     With the discrete v_ext = Re sum_G v(G) e^{iG.r}:
-    F_I^loc = Omega Re sum_G i G Z_I w(G) e^{-iG.R_I} conj(n(G)).
+    F_I^loc = Omega Re sum_G i G w_I(G) e^{-iG.R_I} conj(n(G)), where
+    w_I = Z_I w(G) for the Gaussian ion and Eq. (E4A)'s form for Heine-Abarenkov.
     """
     g = sys.grid
-    w = lpp_form(g.G2, g.omega, sys.rc)
     F = np.zeros((len(sys.Z), 3))
     cn = np.conj(ev["nG"])
     for I in range(len(sys.Z)):
-        base = sys.Z[I] * w * structure_phase(g, sys.R[I]) * cn
+        if sys.lpp == "ha":
+            wI = lpp_form_ha(g.G2, g.omega, sys.Z[I], sys.rc, sys.ha_A, sys.ha_qc)
+        else:
+            wI = sys.Z[I] * lpp_form(g.G2, g.omega, sys.rc)
+        base = wI * structure_phase(g, sys.R[I]) * cn
         for a, Ga in enumerate((g.Gx, g.Gy, g.Gz)):
             F[I, a] = g.omega * float(np.real(np.sum(1j * Ga * base)))
     return F + sys.F_ion
