@@ -81,14 +81,26 @@ typedef enum {
     OFDFT_PW_F64 = 1     /* binary64 throughout */
 } ofdft_pointwise;
 
+/* Local pseudopotential of the ions (Sec. V A).  Either form drops G = 0;
+ * the dropped non-Coulomb constant is reported as ofdft_energy.E_alphaZ. */
+typedef enum {
+    OFDFT_LPP_GAUSS = 0,  /* Gaussian ion: v(G) = -4 pi Z exp(-G^2 rc^2/4)/(Omega G^2) */
+    OFDFT_LPP_HA = 1      /* Heine-Abarenkov, Eq. (E4A): v(q) = -4 pi/(Omega q^2)
+                             [(Z - A rc) cos(q rc) + (A/q) sin(q rc)] exp(-(q/qc)^6);
+                             one parameter set, so every ion must have the same Z
+                             (else OFDFT_EINVAL).  H: rc = 0.25, A = 6.18, qc = 29.97 */
+} ofdft_lpp;
+
 typedef struct {
     int xc;           /* 1: Perdew-Zunger LDA XC (Sec. IV, used in Sec. VI); 0: none */
-    double rc;        /* Gaussian local pseudopotential radius in bohr:
-                         v(G) = -4 pi Z exp(-G^2 rc^2/4)/(Omega G^2), G=0 dropped */
+    double rc;        /* local pseudopotential core radius in bohr (both forms; > 0) */
     int precision;    /* ofdft_precision */
     int device;       /* CUDA device ordinal */
     void *stream;     /* cudaStream_t to run on, or NULL for a library stream */
     int pointwise;    /* ofdft_pointwise: arithmetic of the FP64 field sets */
+    int lpp;          /* ofdft_lpp */
+    double lpp_A;     /* OFDFT_LPP_HA: core depth A in hartree (finite) */
+    double lpp_qc;    /* OFDFT_LPP_HA: cutoff wave number qc in 1/bohr (> 0) */
 } ofdft_params;
 
 /* Energy partition (Sec. V C sample output) and pressure terms; hartree,
@@ -125,7 +137,8 @@ typedef struct {
 } ofdft_md_params;
 
 /* Fill *p with defaults: xc = 1, rc = 0.25, FP64, device 0, library stream,
- * double-float pointwise functional. */
+ * double-float pointwise functional, Gaussian LPP (lpp_A = 6.18 and
+ * lpp_qc = 29.97, the Eq. (E4A) values for H, for when lpp is switched). */
 void ofdft_default_params(ofdft_params *p);
 
 /*

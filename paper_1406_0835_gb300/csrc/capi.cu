@@ -362,8 +362,13 @@ void fill_energy(const ofdft_ctx *c, const EvalScalars &es, ofdft_energy &E)
     E.F_tot = E.F_s + E.E_H + E.E_loc + E.F_xc + E.E_ion;
     E.E_int = E.F_tot + dV * es.TS;
     E.mu = es.PHI2V / es.PHI2;
+    // G -> 0 limit of Omega w(G) + 4 pi Z/G^2 per ion: pi Z rc^2 (Gaussian),
+    // 2 pi Z rc^2 - (4 pi/3) A rc^3 (Eq. (E4A): -A inside rc, -Z/r outside)
+    const double rc = c->g.rc;
     double zs = 0.0;
-    for (int i = 0; i < c->nat; ++i) zs += kPi * c->Z[i] * c->g.rc * c->g.rc;
+    for (int i = 0; i < c->nat; ++i)
+        zs += c->g.lpp ? 2.0 * kPi * c->Z[i] * rc * rc - (4.0 / 3.0) * kPi * c->g.ha_A * rc * rc * rc
+                       : kPi * c->Z[i] * rc * rc;
     E.E_alphaZ = c->Ne * zs / om;
     E.P_s = (dV * es.PS + (4.0 / 3.0) * dV * es.WG) / om;
     E.P_xc = dV * es.PXC / om;
@@ -421,7 +426,8 @@ ofdft_status update_ions(ofdft_ctx *c)
     launch_phases(g, c->nat, c->Rd, c->px, c->py, c->pz, st);
     launch_vext(g, c->nat, c->Zd, c->px, c->py, c->pz, (double2 *)c->f[0].vext, st);
     if (c->f[1].valid)
-        launch_convert<double, float>(2 * g.NH, (const double *)c->f[0].vext, (float *)c->f[1].vext, st);
+        launch_convert<double, float>((g.lpp ? 4 : 2) * g.NH, (const double *)c->f[0].vext, (float *)c->f[1].vext,
+                                      st);
     double L[3] = {g.Lx, g.Ly, g.Lz};
     launch_ewald_real(c->nat, c->Rd, c->Zd, L, c->ew_alpha, c->ew_rcut, c->ew_nimg, c->eion, c->ewF, st);
     int nb = launch_ewald_recip(c->nat, c->Rd, c->Zd, c->nGe, c->Gv, c->wG, c->Se, c->ewpart, c->ewF, st);
@@ -825,7 +831,8 @@ template <typename T> ofdft_status alloc_fieldset(ofdft_ctx *c, FieldSet &f)
     for (void **p : fields) CK(cudaMallocAsync(p, rb, c->st));
     CK(cudaMallocAsync((void **)&f.spec, 4 * cb, c->st));
     f.spec_stride = cb / sizeof(cplx<T>);
-    CK(cudaMallocAsync((void **)&f.vext, (size_t)g.NH * sizeof(cplx<T>), c->st));
+    // v_ext(G); the Heine-Abarenkov form appends its pressure weights
+    CK(cudaMallocAsync((void **)&f.vext, (size_t)(g.lpp ? 2 : 1) * g.NH * sizeof(cplx<T>), c->st));
     // temperature table; FP64 sets append its double-float split (hi, lo
     // binary32 pairs) for the double-float pointwise functional
     const std::vector<double> &tab = tfunc_table_host();
@@ -911,7 +918,8 @@ double footprint_bytes(const int grid[3], int nat, int precision)
     const double tab = (double)tfunc_table_host().size();
     auto fieldset = [&](double sz) {
         double cb = std::ceil(NH * 2 * sz / 256.0) * 256.0;
-        return 9 * N * sz + 4 * cb + NH * 2 * sz + tab * sz + (nx + ny + nz) * 2 * sz + sizeof(CgState);
+        // v_ext(G) counted twice: the Heine-Abarenkov form adds its pressure weights
+        return 9 * N * sz + 4 * cb + 2 * NH * 2 * sz + tab * sz + (nx + ny + nz) * 2 * sz + sizeof(CgState);
     };
     double b = fieldset(8.0) + (precision == OFDFT_MIXED ? fieldset(4.0) : 0.0);
     b += N * 8;                                                        // phiprev
@@ -1081,6 +1089,9 @@ void ofdft_default_params(ofdft_params *p)
     p->device = 0;
     p->stream = nullptr;
     p->pointwise = OFDFT_PW_F32X2;
+    p->lpp = OFDFT_LPP_GAUSS;
+    p->lpp_A = 6.18;      // Eq. (E4A), hydrogen
+    p->lpp_qc = 29.97;
 }
 
 ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const double *ions,
@@ -1109,6 +1120,14 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     if (p.pointwise != OFDFT_PW_F32X2 && p.pointwise != OFDFT_PW_F64)
         return fail(nullptr, OFDFT_EINVAL, "bad pointwise arithmetic");
     const bool dd = p.pointwise == OFDFT_PW_F32X2;
+    if (p.lpp != OFDFT_LPP_GAUSS && p.lpp != OFDFT_LPP_HA) return fail(nullptr, OFDFT_EINVAL, "unknown lpp");
+    if (p.lpp == OFDFT_LPP_HA) {
+        if (!isfinite(p.lpp_A) || !(p.lpp_qc > 0.0) || !isfinite(p.lpp_qc))
+            return fail(nullptr, OFDFT_EINVAL, "Heine-Abarenkov LPP needs finite A and qc > 0");
+        for (int i = 1; i < nat; ++i)
+            if (Z[i] != Z[0])
+                return fail(nullptr, OFDFT_EINVAL, "Heine-Abarenkov LPP takes one species (equal Z)");
+    }
     for (int i = 0; i < nat; ++i) {
         if (!(Z[i] > 0.0)) return fail(nullptr, OFDFT_EINVAL, "Z must be > 0");
         for (int a = 0; a < 3; ++a)
@@ -1143,6 +1162,10 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     g.omega = g.Lx * g.Ly * g.Lz;
     g.dV = g.omega / (double)g.N;
     g.rc = p.rc;
+    g.lpp = p.lpp;
+    g.ha_A = p.lpp_A;
+    g.ha_qc = p.lpp_qc;
+    g.ha_Z = Z[0];
     grid_reciprocal(g);
     g.dd = dd ? 1 : 0;
     c->nat = nat;

@@ -501,6 +501,25 @@ __global__ void k_ypass(GridInfo g, FftAxis ay, typename KT<PR>::C *__restrict__
     store_tile<PR>(f, t, g.ny, X);
 }
 
+// One G-point's share of the LPP pressure (Eq. (pressure), LPP term, at
+// fixed Omega n(G) and fractional coordinates).  Gaussian ion: 3x the share,
+// Re(n* v_ext)(1 - G^2 rc^2/2) (the caller divides by 3); Heine-Abarenkov
+// (Eq. (E4A)): Re(n* v_p) with the pressure weights v_p stored after v_ext.
+template <typename PR>
+__device__ __forceinline__ typename KT<PR>::R ploc_term(const GridInfo &g, const typename KT<PR>::C *vext,
+                                                      long long vi, const typename KT<PR>::CC &nG,
+                                                      typename KT<PR>::R re, typename KT<PR>::R hr,
+                                                      typename KT<PR>::R g2)
+{
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::CC CC;
+    if (g.lpp) {
+        CC vp = ldc<PR>(vext[g.NH + vi]);
+        return nG.x * vp.x + nG.y * vp.y;
+    }
+    return re * (R(1) - hr * g2);
+}
+
 // x pass, gradient variant: forward x -> n(G) (stored), energies, then
 // i D_a n(G) inverse-x for a = x, y, z.  Partials: E_H, E_loc, P_loc.
 template <typename PR>
@@ -533,12 +552,13 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
         N[i] = nG;
         Gk<R> k = gvec<R>(g, bx, by, bz, r, t.couter[c], t.ckz[c]);
         if (k.g2 > R(0)) {
-            CC ve = ldc<PR>(vext[t.cbase[c] + r * t.rstride]);
+            const long long vi = t.cbase[c] + r * t.rstride;
+            CC ve = ldc<PR>(vext[vi]);
             R n2 = nG.x * nG.x + nG.y * nG.y;
             R re = nG.x * ve.x + nG.y * ve.y;
             acc[0] += k.w * n2 / k.g2;
             acc[1] += k.w * re;
-            acc[2] += k.w * re * (R(1) - hr * k.g2);
+            acc[2] += k.w * ploc_term<PR>(g, vext, vi, nG, re, hr, k.g2);
         }
     }
     __syncthreads();
@@ -561,10 +581,10 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
     block_total<3, PR>(acc, tot);
     if (threadIdx.x == 0) {
         // E_H = (Omega/2) sum 4 pi |n|^2/G^2, E_loc = Omega sum Re(n* v_ext),
-        // P_loc = (1/3) sum Re(n* v_ext)(1 - G^2 rc^2/2)
+        // P_loc = sum Re(n* v_p) (ploc_term)
         part[blockIdx.x] = 0.5 * g.omega * 12.566370614359172954 * tot[0];
         part[(size_t)gridDim.x + blockIdx.x] = g.omega * tot[1];
-        part[(size_t)2 * gridDim.x + blockIdx.x] = (1.0 / 3.0) * tot[2];
+        part[(size_t)2 * gridDim.x + blockIdx.x] = (g.lpp ? 1.0 : 1.0 / 3.0) * tot[2];
     }
 }
 
@@ -596,14 +616,15 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
         if (c >= t.ncol) continue;
         CC nG = cscale(X[i], invN);
         Gk<R> k = gvec<R>(g, bx, by, bz, r, t.couter[c], t.ckz[c]);
-        CC ve = ldc<PR>(vext[t.cbase[c] + r * t.rstride]);
+        const long long vi = t.cbase[c] + r * t.rstride;
+        CC ve = ldc<PR>(vext[vi]);
         CC out = cmk<CC>(R(0), R(0));
         if (k.g2 > R(0)) {
             R n2 = nG.x * nG.x + nG.y * nG.y;
             R re = nG.x * ve.x + nG.y * ve.y;
             acc[0] += k.w * n2 / k.g2;
             acc[1] += k.w * re;
-            acc[2] += k.w * re * (R(1) - hr * k.g2);
+            acc[2] += k.w * ploc_term<PR>(g, vext, vi, nG, re, hr, k.g2);
             R kh = fpi / k.g2;
             out = cmk<CC>(kh * nG.x + ve.x, kh * nG.y + ve.y);
         }
@@ -621,7 +642,7 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
     if (threadIdx.x == 0) {
         part[blockIdx.x] = 0.5 * g.omega * 12.566370614359172954 * tot[0];
         part[(size_t)gridDim.x + blockIdx.x] = g.omega * tot[1];
-        part[(size_t)2 * gridDim.x + blockIdx.x] = (1.0 / 3.0) * tot[2];
+        part[(size_t)2 * gridDim.x + blockIdx.x] = (g.lpp ? 1.0 : 1.0 / 3.0) * tot[2];
     }
 }
 

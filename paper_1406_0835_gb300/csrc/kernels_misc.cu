@@ -208,11 +208,36 @@ __device__ __forceinline__ double2 zmul(double2 a, double2 b)
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Local pseudopotential form factor per unit charge (Gaussian ion):
-// w(G) = -4 pi exp(-G^2 rc^2/4) / (Omega G^2), 0 at G = 0.
+// Local pseudopotential form factor per unit charge, 0 at G = 0.
+// Gaussian ion: w(G) = -4 pi exp(-G^2 rc^2/4) / (Omega G^2).
+// Heine-Abarenkov, Eq. (E4A), q = |G|, divided by the common charge Z:
+// w(q) = -4 pi/(Omega q^2 Z) [(Z - A rc) cos(q rc) + (A/q) sin(q rc)] exp(-(q/qc)^6).
 __device__ __forceinline__ double lpp_w(const GridInfo &g, double g2)
 {
-    return g2 > 0.0 ? -12.566370614359172954 * exp(-0.25 * g2 * g.rc * g.rc) / (g.omega * g2) : 0.0;
+    if (!(g2 > 0.0)) return 0.0;
+    if (g.lpp == 0) return -12.566370614359172954 * exp(-0.25 * g2 * g.rc * g.rc) / (g.omega * g2);
+    const double q = sqrt(g2), u = q / g.ha_qc, u2 = u * u;
+    double s, c;
+    sincos(q * g.rc, &s, &c);
+    const double B = (g.ha_Z - g.ha_A * g.rc) * c + g.ha_A * s / q;
+    return -12.566370614359172954 * B * exp(-u2 * u2 * u2) / (g.omega * g2 * g.ha_Z);
+}
+
+// Pressure weight of the Heine-Abarenkov form per unit charge: the LPP
+// pressure is sum_G Re[n*(G) wp(G) sum_I Z_I e^{-iG.R_I}] with
+// wp = w + (q/3) dw/dq (Omega w depends on the cell only through q), i.e.
+// wp = -4 pi f/(3 Omega q^2 Z) [B + q B' - 6 (q/qc)^6 B],
+// q B' = -(Z - A rc) q rc sin(q rc) + A (rc cos(q rc) - sin(q rc)/q).
+__device__ __forceinline__ double lpp_wp_ha(const GridInfo &g, double g2)
+{
+    if (!(g2 > 0.0)) return 0.0;
+    const double q = sqrt(g2), u = q / g.ha_qc, u2 = u * u, u6 = u2 * u2 * u2;
+    double s, c;
+    sincos(q * g.rc, &s, &c);
+    const double zc = g.ha_Z - g.ha_A * g.rc;
+    const double B = zc * c + g.ha_A * s / q;
+    const double qdB = -zc * q * g.rc * s + g.ha_A * (g.rc * c - s / q);
+    return -4.1887902047863909846 * exp(-u6) * (B + qdB - 6.0 * u6 * B) / (g.omega * g2 * g.ha_Z);
 }
 
 // Half-spectrum point (ix, iy, kz): G from the reciprocal spacings, Nyquist
@@ -254,6 +279,8 @@ __device__ __forceinline__ Hk hk_flat(const GridInfo &g, int q)
 // folded onto the stored plane).  Off the Nyquist planes P' = P.
 // One block per (ix, iy) row; the row factors Z_I e^{-i(Gx X_I + Gy Y_I)} are
 // staged in shared memory in chunks of atoms, and thread kz sums over atoms.
+// The Heine-Abarenkov form also writes its pressure weights wp(G) times the
+// same sum to vext[NH + q].
 __global__ void k_vext(GridInfo g, int nat, const double *__restrict__ Z,
                        const double2 *__restrict__ px, const double2 *__restrict__ py,
                        const double2 *__restrict__ pz, double2 *__restrict__ vext)
@@ -310,6 +337,10 @@ __global__ void k_vext(GridInfo g, int nat, const double *__restrict__ Z,
         double2 v = acc[h];
         if (rnyq || k.nz_) v = make_double2(0.5 * (v.x + acc2[h].x), 0.5 * (v.y + acc2[h].y));
         vext[(size_t)blockIdx.x * g.K + kz] = make_double2(w * v.x, w * v.y);
+        if (g.lpp) {
+            const double wp = lpp_wp_ha(g, k.g2);
+            vext[(size_t)g.NH + (size_t)blockIdx.x * g.K + kz] = make_double2(wp * v.x, wp * v.y);
+        }
     }
 }
 

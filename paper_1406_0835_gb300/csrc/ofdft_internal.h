@@ -84,7 +84,9 @@ struct GridInfo {
     int nx, ny, nz, K;
     long long N, NH;
     double Lx, Ly, Lz, omega, dV;
-    double rc;               // Gaussian local pseudopotential radius
+    double rc;               // local pseudopotential core radius
+    int lpp;                 // 0 Gaussian ion, 1 Heine-Abarenkov (Eq. (E4A))
+    double ha_A, ha_qc, ha_Z;   // Heine-Abarenkov depth, cutoff and the common ion charge
     double bx, by, bz;       // reciprocal spacing 2 pi / L per axis
     double invN, hr;         // 1 / N, rc^2 / 2
     float bxf, byf, bzf, invNf, hrf;   // the same in FP32 (for the FP32 kernels)

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libofdft.so")
 FUNCTIONALS = {"fttf": 0, "sga": 1, "vt84f": 2, "kst2": 3, "vwtf": 4, "tw": 5, "apbef": 6}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 POINTWISE = {"f32x2": 0, "f64": 1}
+LPP = {"gauss": 0, "ha": 1}
 STATUS = {0: "OFDFT_OK", -1: "OFDFT_EINVAL", -2: "OFDFT_ENOMEM", -3: "OFDFT_ENOCONV",
           -4: "OFDFT_ENUMERIC", -5: "OFDFT_ETIMEOUT", -6: "OFDFT_EDEVICE", -7: "OFDFT_EBUSY"}
 
@@ -35,7 +36,8 @@ MIXED_MD_GTOL = 1e-6
 
 class Params(ctypes.Structure):
     _fields_ = [("xc", ctypes.c_int), ("rc", ctypes.c_double), ("precision", ctypes.c_int),
-                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("pointwise", ctypes.c_int)]
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("pointwise", ctypes.c_int),
+                ("lpp", ctypes.c_int), ("lpp_A", ctypes.c_double), ("lpp_qc", ctypes.c_double)]
 
 
 class Energy(ctypes.Structure):
@@ -383,13 +385,19 @@ def ofdft_destroy(ctx):
 class Context:
     """One OF-DFT system on one GPU (owns a libofdft context).  precision:
     "fp64" or "mixed"; pointwise: arithmetic of the FP64 field sets, "f32x2"
-    (double-float on the FP32 units, the default) or "f64" (binary64)."""
+    (double-float on the FP32 units, the default) or "f64" (binary64);
+    lpp: "gauss" (Gaussian ion of radius rc) or "ha" (Heine-Abarenkov,
+    Eq. (E4A), core radius rc, depth lpp_A, cutoff lpp_qc; one species)."""
 
     def __init__(self, L, grid, ions, Z, T_kelvin, functional="fttf", xc=True, rc=0.25,
-                 precision="fp64", device=0, stream=None, pointwise="f32x2"):
+                 precision="fp64", device=0, stream=None, pointwise="f32x2", lpp="gauss",
+                 lpp_A=6.18, lpp_qc=29.97):
         p = ofdft_default_params()
         p.xc = int(bool(xc))
         p.rc = float(rc)
+        p.lpp = LPP.get(lpp, lpp)
+        p.lpp_A = float(lpp_A)
+        p.lpp_qc = float(lpp_qc)
         p.precision = PRECISIONS[precision]
         p.pointwise = POINTWISE[pointwise]
         p.device = int(device)

@@ -57,6 +57,18 @@ def test_setup_rejects_bad_input_without_a_gpu(lib):
     with pytest.raises(ofdft.OfdftError) as e:
         ofdft.ofdft_setup(cfg_cell, (16, 16, 16), ions, [1.0], 1e4, "fttf", p)
     assert e.value.status == -1
+    # local pseudopotential: Gaussian by default, Eq. (E4A)'s H values ready
+    p = ofdft.ofdft_default_params()
+    assert (p.lpp, p.lpp_A, p.lpp_qc) == (0, 6.18, 29.97)
+    two = np.array([[0.0, 0.0, 0.0], [2.0, 2.0, 2.0]])
+    for lpp, A, qc, Z in ((2, 6.18, 29.97, [1.0, 1.0]),             # unknown form
+                          (1, 6.18, 0.0, [1.0, 1.0]),               # qc <= 0
+                          (1, float("nan"), 29.97, [1.0, 1.0]),     # A not finite
+                          (1, 6.18, 29.97, [1.0, 2.0])):            # two species
+        p.lpp, p.lpp_A, p.lpp_qc = lpp, A, qc
+        with pytest.raises(ofdft.OfdftError) as e:
+            ofdft.ofdft_setup(cfg_cell, (16, 16, 16), two, Z, 1e4, "fttf", p)
+        assert e.value.status == -1
 
 
 def test_tabulated_temperature_functions_match_oracle(lib):
