@@ -261,6 +261,22 @@ ofdft_status ofdft_md_step(ofdft_ctx *ctx, const ofdft_md_params *mp, int nsteps
                            double *pos, double *vel, double *F,
                            ofdft_energy *E, ofdft_stats *stats);
 
+/*
+ * Andersen thermostat (the NVT ensemble of the paper's MD runs, Sec. VI):
+ * ion I collides when u[I] < prob and then takes the velocity
+ * sqrt(kT/m_I) xi[I], a Maxwell-Boltzmann draw at T_kelvin.  u[nat]
+ * (uniform in [0, 1)) and xi[nat][3] (standard normal) are the caller's
+ * random numbers, host arrays copied by the call.  Acts on the
+ * device-resident MD velocities: run ofdft_md_step with T_kelvin <= 0 (no
+ * Nose-Hoover) and pos = vel = NULL between calls, e.g. one call per step
+ * with prob = dt / (collision time).  ncoll (may be NULL) receives the
+ * number of collisions.  Velocities redrawn this way leave
+ * ofdft_md_conserved without meaning.  OFDFT_EINVAL for NULL arrays,
+ * T_kelvin <= 0, prob outside [0, 1] or a non-finite xi.
+ */
+ofdft_status ofdft_md_andersen(ofdft_ctx *ctx, double T_kelvin, double prob, const double *u,
+                               const double *xi, int *ncoll);
+
 /* Copy the MD state out: pos, vel [nat][3] (either may be NULL). */
 ofdft_status ofdft_md_state(ofdft_ctx *ctx, double *pos, double *vel);
 

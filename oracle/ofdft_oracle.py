@@ -736,6 +736,18 @@ def md_step(sys, st, gtol=1e-8, thermostat=True):
     return stats
 
 
+def md_andersen(st, T_kelvin, prob, u, xi):
+    """Andersen collisions (the thermostat of the paper's NVT runs, Sec. VI):
+    ion I collides when u_I < prob and then takes a velocity drawn from the
+    Maxwell-Boltzmann distribution at T, v_I = sqrt(kT/m_I) xi_I.  The
+    uniform u[nat] and standard normal xi[nat,3] come in as inputs."""
+    kT = T_kelvin * KB_HA_PER_K
+    hit = np.asarray(u, dtype=np.float64) < prob
+    xi = np.asarray(xi, dtype=np.float64).reshape(-1, 3)
+    st.V[hit] = np.sqrt(kT / st.m[hit])[:, None] * xi[hit]
+    return int(np.count_nonzero(hit))
+
+
 def md_conserved(st):
     """Nose-Hoover extended energy K + F_tot + Q xi^2/2 + g kT eta."""
     return (st.kinetic() + st.ev["F_tot"] + 0.5 * st.Q * st.xi ** 2

@@ -1484,6 +1484,32 @@ ofdft_status ofdft_md_step(ofdft_ctx *c, const ofdft_md_params *mp, int nsteps, 
     return OFDFT_OK;
 }
 
+ofdft_status ofdft_md_andersen(ofdft_ctx *c, double T_kelvin, double prob, const double *u, const double *xi,
+                               int *ncoll)
+{
+    if (!c || !u || !xi) return fail(c, OFDFT_EINVAL, "NULL argument");
+    NOT_BUSY(c);
+    if (!(T_kelvin > 0.0) || !isfinite(T_kelvin) || !(prob >= 0.0 && prob <= 1.0))
+        return fail(c, OFDFT_EINVAL, "Andersen collisions need T > 0 and 0 <= prob <= 1");
+    const int nat = c->nat;
+    int hits = 0;
+    for (int i = 0; i < nat; ++i) hits += u[i] < prob;
+    for (int i = 0; i < 3 * nat; ++i)
+        if (!isfinite(xi[i])) return fail(c, OFDFT_EINVAL, "non-finite normal deviate");
+    cudaSetDevice(c->dev);
+    double *d = nullptr;
+    CK(cudaMallocAsync((void **)&d, 4 * (size_t)nat * sizeof(double), c->st));
+    CK(cudaMemcpyAsync(d, u, nat * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(d + nat, xi, 3 * nat * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    launch_andersen(nat, c->Md, c->Vd, T_kelvin * kKbHa, prob, d, d + nat, c->nh, c->st);
+    c->launches++;
+    CK(cudaFreeAsync(d, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaGetLastError());
+    if (ncoll) *ncoll = hits;
+    return OFDFT_OK;
+}
+
 ofdft_status ofdft_md_state(ofdft_ctx *c, double *pos, double *vel)
 {
     if (!c) return fail(c, OFDFT_EINVAL, "NULL context");

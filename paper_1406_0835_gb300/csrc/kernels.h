@@ -93,6 +93,8 @@ void launch_md_a(int nat, const double *m, double *R, double *V, const double *F
                  double kT, double Q, int ndof, int thermo, double *nh, cudaStream_t st);
 void launch_md_b(int nat, const double *m, double *V, const double *F, double dt, double kT,
                  double Q, int ndof, int thermo, double *nh, cudaStream_t st);
+void launch_andersen(int nat, const double *m, double *V, double kT, double prob, const double *u,
+                     const double *xi, double *nh, cudaStream_t st);
 
 // ---- device CG controller (cg_control.cu); single-thread kernels.
 // use_cond = 0 outside a graph (the handles are then ignored).

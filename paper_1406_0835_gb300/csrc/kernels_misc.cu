@@ -551,9 +551,34 @@ __global__ void k_md_b(int nat, const double *m, double *V, const double *F, dou
     if (threadIdx.x == 0) nh[2] = k[0];
 }
 
+// Andersen collisions: ion i with u[i] < prob takes v = sqrt(kT/m_i) xi[i];
+// then the kinetic energy into nh[2].  One block.
+__global__ void k_andersen(int nat, const double *m, double *V, double kT, double prob,
+                           const double *__restrict__ u, const double *__restrict__ xi, double *nh)
+{
+    for (int i = threadIdx.x; i < nat; i += blockDim.x) {
+        if (u[i] < prob) {
+            const double sd = sqrt(kT / m[i]);
+            for (int a = 0; a < 3; ++a) V[3 * i + a] = sd * xi[3 * i + a];
+        }
+    }
+    __syncthreads();
+    double k[1] = {0.0};
+    for (int i = threadIdx.x; i < nat; i += blockDim.x)
+        k[0] += 0.5 * m[i] * (V[3 * i] * V[3 * i] + V[3 * i + 1] * V[3 * i + 1] + V[3 * i + 2] * V[3 * i + 2]);
+    block_sum<1>(k);
+    if (threadIdx.x == 0) nh[2] = k[0];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
+void launch_andersen(int nat, const double *m, double *V, double kT, double prob, const double *u,
+                     const double *xi, double *nh, cudaStream_t st)
+{
+    k_andersen<<<1, 256, 0, st>>>(nat, m, V, kT, prob, u, xi, nh);
+}
+
 void launch_reduce(const double *part, int nblk, int nq, double *out, cudaStream_t st)
 {
     k_reduce<<<nq, 256, 0, st>>>(part, nblk, out);

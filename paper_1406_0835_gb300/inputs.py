@@ -72,6 +72,13 @@ def maxwell_boltzmann(n_atoms, T_kelvin, seed, mass_amu=M_H_AMU):
     return v
 
 
+def andersen_draws(n_atoms, seed):
+    """Random numbers of one round of Andersen collisions: u[n] uniform in
+    [0, 1) and xi[n, 3] standard normal (PCG64, seeded)."""
+    rng = np.random.default_rng(seed)
+    return rng.random(n_atoms), rng.standard_normal((n_atoms, 3))
+
+
 def hydrogen(n_atoms, rho_gcc, T_kelvin, grid, seed, functional,
              min_dist=0.8, vel_seed=None):
     """One synthetic hydrogen workload as a plain dict."""

@@ -113,6 +113,8 @@ SIGNATURES = {
     "ofdft_set_masses": (ctypes.c_int, [ctypes.c_void_p, _P]),
     "ofdft_md_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(MDParams), ctypes.c_int, _P, _P,
                                      _P, ctypes.POINTER(Energy), ctypes.POINTER(Stats)]),
+    "ofdft_md_andersen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _P, _P,
+                                         ctypes.POINTER(ctypes.c_int)]),
     "ofdft_md_state": (ctypes.c_int, [ctypes.c_void_p, _P, _P]),
     "ofdft_md_conserved": (ctypes.c_int, [ctypes.c_void_p, _P]),
     "ofdft_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
@@ -305,6 +307,16 @@ def ofdft_md_step(ctx, dt_fs, T_kelvin, nsteps=1, pos=None, vel=None, tau_steps=
     return dict(pos=pos, vel=vel, F=F, E=E.as_dict(), stats=S.as_dict())
 
 
+def ofdft_md_andersen(ctx, T_kelvin, prob, u, xi):
+    nat = ofdft_sizes(ctx)[1]
+    u = _f64(u, (nat,))
+    xi = _f64(xi, (nat, 3))
+    n = ctypes.c_int()
+    _check(ctx, load().ofdft_md_andersen(ctx, float(T_kelvin), float(prob), _ptr(u), _ptr(xi),
+                                         ctypes.byref(n)))
+    return n.value
+
+
 def ofdft_md_state(ctx):
     nat = ofdft_sizes(ctx)[1]
     pos = np.empty((nat, 3))
@@ -453,6 +465,9 @@ class Context:
 
     def md_step(self, dt_fs, T_kelvin, nsteps=1, pos=None, vel=None, **kw):
         return ofdft_md_step(self.ctx, dt_fs, T_kelvin, nsteps, pos, vel, **kw)
+
+    def md_andersen(self, T_kelvin, prob, u, xi):
+        return ofdft_md_andersen(self.ctx, T_kelvin, prob, u, xi)
 
     def md_state(self):
         return ofdft_md_state(self.ctx)

@@ -302,3 +302,28 @@ def test_md_time_reversible_and_second_order():
             d = max(d, abs(O.md_conserved(st) - H0))
         dev.append(d)
     assert 2.5 < dev[0] / dev[1] < 6.0
+
+
+def test_andersen_collisions():
+    """Andersen thermostat (the paper's NVT runs, Sec. VI): exactly the ions
+    with u < prob are redrawn, from Maxwell-Boltzmann at T (equipartition:
+    mean kinetic energy 3 kT/2 per ion, per-component variance kT/m)."""
+    n = 20000
+    masses = np.where(np.arange(n) % 2 == 0, 1.0, 4.0) * I.M_H_AMU * I.AMU_ME
+    V0 = np.full((n, 3), 1e-3)
+    st = O.MDState(np.zeros((n, 3)), V0, masses, 1e5, dt_fs=0.2)
+    u, xi = I.andersen_draws(n, seed=5)
+    assert O.md_andersen(st, 1e5, 0.0, u, xi) == 0
+    assert np.array_equal(st.V, V0)
+    hit = O.md_andersen(st, 1e5, 0.3, u, xi)
+    changed = np.any(st.V != V0, axis=1)
+    assert hit == np.count_nonzero(u < 0.3) and np.array_equal(changed, u < 0.3)
+    assert abs(hit / n - 0.3) < 0.02
+    O.md_andersen(st, 1e5, 1.0, u, xi)
+    kT = 1e5 * O.KB_HA_PER_K
+    K = 0.5 * np.sum(masses[:, None] * st.V ** 2, axis=1)
+    # sampling error of the mean of (kT/2) chi^2_3 over n ions: 0.82 kT/sqrt(n)
+    assert abs(np.mean(K) / (1.5 * kT) - 1.0) < 4 * 0.816 / math.sqrt(n)
+    for sel in (slice(0, None, 2), slice(1, None, 2)):
+        var = np.var(st.V[sel]) * masses[sel][0] / kT
+        assert abs(var - 1.0) < 0.03
