@@ -137,6 +137,42 @@ class Grid:
         return self.dV * float(np.sum(f))
 
 
+class CellGrid(Grid):
+    """Periodic grid of a general (triclinic) cell: rows of `cell` are the
+    lattice vectors a_1..a_3 (bohr), grid point (i, j, k) sits at
+    (i/n1) a_1 + (j/n2) a_2 + (k/n3) a_3.  G = k_1 b_1 + k_2 b_2 + k_3 b_3
+    with a_i . b_j = 2 pi delta_ij and the same integer wave numbers and
+    Nyquist conventions as the orthorhombic grid (a first derivative is
+    zeroed where its own integer k_a sits on the a-Nyquist plane)."""
+
+    def __init__(self, cell, shape):
+        self.cell = np.asarray(cell, dtype=np.float64).reshape(3, 3)
+        self.L = None
+        self.shape = tuple(int(n) for n in shape)
+        self.N = int(np.prod(self.shape))
+        self.omega = abs(float(np.linalg.det(self.cell)))
+        self.dV = self.omega / self.N
+        self.B = 2.0 * math.pi * np.linalg.inv(self.cell).T     # rows b_j
+        kint, kd = [], []
+        for n in self.shape:
+            k = np.fft.fftfreq(n, 1.0 / n)
+            if n % 2 == 0:
+                k[n // 2] = n // 2
+            d = k.copy()
+            if n % 2 == 0:
+                d[n // 2] = 0.0
+            kint.append(k)
+            kd.append(d)
+        self.kint = kint
+        sh = [(-1, 1, 1), (1, -1, 1), (1, 1, -1)]
+
+        def cart(ks):
+            return [sum(ks[j].reshape(sh[j]) * self.B[j, a] for j in range(3)) for a in range(3)]
+        self.Gx, self.Gy, self.Gz = cart(kint)
+        self.G2 = self.Gx ** 2 + self.Gy ** 2 + self.Gz ** 2
+        self.Dx, self.Dy, self.Dz = cart(kd)
+
+
 # --------------------------------------------- enhancement factors (Sec. III B)
 def F_sga(mu):
     """Eq. (SGA-F): F_tau = 1 + mu x with x = s_tau^2 (mu = 5/27 SGA, 5/3 VWTF)."""
@@ -432,6 +468,70 @@ def ewald(L, R, Z, alpha=None):
     return E, F
 
 
+def ewald_cell(cell, R, Z, alpha=None):
+    """Ewald sum of Eq. (E1)'s E_ion for a general cell (rows = lattice
+    vectors), with forces and the stress tensor
+    Sigma_ab = (1/Omega) dE/d eps_ab at fixed fractional coordinates:
+      real space   -(1/2 Omega) sum' Z_I Z_J [erfc(a r)/r + (2a/sqrt pi) e^{-a^2 r^2}] r_a r_b / r^2,
+      reciprocal   -delta_ab E_G/Omega + (4 pi/Omega^2) sum_{G!=0} |S|^2 e^{-G^2/4a^2}/G^2
+                   (1/(4a^2) + 1/G^2) G_a G_b,
+      background   -delta_ab E_bg/Omega  (E_bg = -pi (sum Z)^2/(2 Omega a^2));
+    the self term does not depend on the cell.  Returns (E, F [nat,3], Sigma [3,3])."""
+    from scipy.special import erfc
+    A = np.asarray(cell, dtype=np.float64).reshape(3, 3)
+    R = np.asarray(R, dtype=np.float64).reshape(-1, 3)
+    Z = np.asarray(Z, dtype=np.float64)
+    nat = len(Z)
+    omega = abs(float(np.linalg.det(A)))
+    B = 2.0 * math.pi * np.linalg.inv(A).T
+    if alpha is None:
+        alpha = math.sqrt(math.pi) * (nat / omega ** 2) ** (1.0 / 6.0)
+    rcut = 6.5 / alpha
+    gcut = 2.0 * alpha * 6.5
+    E = 0.0
+    F = np.zeros((nat, 3))
+    S = np.zeros((3, 3))
+    # real space: lattice planes a_i are 2 pi/|b_i| apart
+    nimg = [int(math.ceil(rcut * np.linalg.norm(B[i]) / (2.0 * math.pi))) + 1 for i in range(3)]
+    n = np.array([(i, j, k) for i in range(-nimg[0], nimg[0] + 1)
+                  for j in range(-nimg[1], nimg[1] + 1)
+                  for k in range(-nimg[2], nimg[2] + 1)], dtype=np.float64)
+    shifts = n @ A
+    for I in range(nat):
+        d = R[I][None, None, :] - R[None, :, :] - shifts[:, None, :]
+        r = np.sqrt(np.sum(d * d, axis=2))
+        mask = (r > 1e-12) & (r < rcut)
+        rr = np.where(mask, r, 1.0)
+        zz = Z[I] * Z[None, :]
+        e = np.where(mask, zz * erfc(alpha * rr) / rr, 0.0)
+        E += 0.5 * float(np.sum(e))
+        g = np.where(mask, zz * (erfc(alpha * rr) / rr
+                                 + 2.0 * alpha / math.sqrt(math.pi) * np.exp(-(alpha * rr) ** 2)), 0.0)
+        F[I] += np.sum((g / rr ** 2)[:, :, None] * d, axis=(0, 1))
+        S -= 0.5 / omega * np.einsum("ij,ija,ijb->ab", g / rr ** 2, d, d)
+    # reciprocal space
+    km = [int(math.ceil(gcut * np.linalg.norm(A[i]) / (2.0 * math.pi))) for i in range(3)]
+    K = np.array(np.meshgrid(*[np.arange(-m, m + 1) for m in km], indexing="ij")).reshape(3, -1).T
+    G = K @ B
+    G2 = np.sum(G * G, axis=1)
+    sel = (G2 > 0) & (G2 < gcut * gcut)
+    G, G2 = G[sel], G2[sel]
+    wG = np.exp(-G2 / (4.0 * alpha * alpha)) / G2
+    ph = np.exp(1j * (G @ R.T))
+    SG = ph @ Z
+    S2 = np.abs(SG) ** 2
+    EG = (2.0 * math.pi / omega) * float(np.sum(wG * S2))
+    E += EG
+    F += (4.0 * math.pi / omega) * Z[:, None] * ((wG[:, None] * np.imag(np.conj(SG)[:, None] * ph)).T @ G)
+    c = S2 * wG * (1.0 / (4.0 * alpha * alpha) + 1.0 / G2)
+    S += -EG / omega * np.eye(3) + (4.0 * math.pi / omega ** 2) * np.einsum("g,ga,gb->ab", c, G, G)
+    E -= alpha / math.sqrt(math.pi) * float(np.sum(Z * Z))
+    Ebg = -math.pi * float(np.sum(Z)) ** 2 / (2.0 * omega * alpha * alpha)
+    E += Ebg
+    S += -Ebg / omega * np.eye(3)
+    return E, F, S
+
+
 # -------------------------------------------------------------- the system
 class System:
     """Cell, ions, grid, temperature and functional choice (Sec. II, V C).
@@ -440,13 +540,15 @@ class System:
     """
 
     def __init__(self, L, shape, ions, Z, T_kelvin, functional="fttf",
-                 rc=0.25, xc=True, lpp="gauss", ha_A=HA_H["A"], ha_qc=HA_H["qc"]):
+                 rc=0.25, xc=True, lpp="gauss", ha_A=HA_H["A"], ha_qc=HA_H["qc"], cell=None):
         if lpp not in ("gauss", "ha"):
             raise ValueError("lpp must be 'gauss' or 'ha'")
         self.lpp = lpp
         self.ha_A = float(ha_A)
         self.ha_qc = float(ha_qc)
-        self.grid = Grid(L, shape)
+        # cell: lattice vectors as rows for a general cell (L is then unused)
+        self.cell = None if cell is None else np.asarray(cell, dtype=np.float64).reshape(3, 3)
+        self.grid = Grid(L, shape) if cell is None else CellGrid(cell, shape)
         self.R = np.array(ions, dtype=np.float64).reshape(-1, 3)
         self.Z = np.array(Z, dtype=np.float64).reshape(-1)
         self.T = float(T_kelvin) * KB_HA_PER_K
@@ -465,7 +567,10 @@ class System:
         else:
             self.vG = lpp_vG(self.grid, self.R, self.Z, self.rc)
         self.v_ext = self.grid.to_r(self.vG)
-        self.E_ion, self.F_ion = ewald(self.grid.L, self.R, self.Z)
+        if self.cell is None:
+            self.E_ion, self.F_ion = ewald(self.grid.L, self.R, self.Z)
+        else:
+            self.E_ion, self.F_ion, _ = ewald_cell(self.cell, self.R, self.Z)
 
     def uniform_phi(self):
         return np.full(self.grid.shape, math.sqrt(self.Ne / self.grid.omega))
@@ -491,11 +596,13 @@ def evaluate(sys, phi):
     if fun is None:
         fs = fs_fttf(n, sys.T)
         gradn = None
+        W = None
         v_s = fs["dfdn"]
         WdotG = 0.0
     else:
         gradn = g.grad(n)
         fs = fs_gga(n, gradn, sys.T, fun)
+        W = fs["W"]
         v_s = fs["dfdn"] - g.div(fs["W"])                            # Eq. (vftGGA)
         WdotG = g.integrate(np.sum(fs["W"] * gradn, axis=0))
     F_s = g.integrate(fs["f"])
@@ -524,9 +631,53 @@ def evaluate(sys, phi):
     P_ion = sys.E_ion / (3.0 * g.omega)
     return dict(F_tot=F_tot, F_el=F_el, F_s=F_s, minus_TS=-TS, E_H=E_H,
                 E_loc=E_loc, F_xc=F_xc, E_ion=sys.E_ion, E_int=F_tot + TS,
-                v=v, v_s=v_s, n=n, nG=nG, gradn=gradn,
+                v=v, v_s=v_s, n=n, nG=nG, gradn=gradn, W=W,
                 P=P_s + P_xc + P_H + P_loc + P_ion, P_s=P_s, P_xc=P_xc,
                 P_H=P_H, P_loc=P_loc, P_ion=P_ion, E_alphaZ=E_alphaZ)
+
+
+# ------------------------------------------- stress tensor (Eq. (StressTensor))
+def stress(sys, ev):
+    """Stress tensor Sigma_ab = (1/V) sum_nu (dF/dh_a,nu) h_b,nu of
+    Eq. (StressTensor) at the density of `ev` (P = -Tr Sigma/3,
+    Eq. (pressure)), term by term, under a homogeneous strain at fixed
+    fractional coordinates and fixed V n(G):
+      non-interacting  delta_ab/V int (f_s - n v_s) - (1/V) int W_a d_b n
+                       (Eqs. (stressTF_a), (stressTF_b); W = d f_s/d grad n,
+                       v_s the full functional derivative)
+      XC               delta_ab/V int n (eps_xc - v_xc)   (Eq. (stressLSDAxc))
+      Hartree          -delta_ab E_H/V + sum_G 4 pi |n(G)|^2 G_a G_b/G^4
+      LPP              -delta_ab E_loc/V - 2 sum_G Re[n*(G) v'(G)] G_a G_b,
+                       v' = dv/dG^2 at fixed V v(G) (Gaussian ion:
+                       v (-rc^2/4 - 1/G^2); Eq. (E4A): from its dilation weights)
+      ions             the Ewald stress (ewald_cell).
+    Returns a dict of 3x3 arrays per term and their sum "Sigma"."""
+    g = sys.grid
+    V = g.omega
+    I3 = np.eye(3)
+    Gs = [np.broadcast_to(x, g.shape) for x in (g.Gx, g.Gy, g.Gz)]
+    nG = ev["nG"]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv2 = np.where(g.G2 > 0.0, 1.0 / g.G2, 0.0)
+    Ss = (ev["F_s"] - g.integrate(ev["n"] * ev["v_s"])) / V * I3
+    if ev["W"] is not None:
+        for a in range(3):
+            for b in range(3):
+                Ss[a, b] -= 0.5 / V * g.integrate(ev["W"][a] * ev["gradn"][b] + ev["W"][b] * ev["gradn"][a])
+    Sxc = -ev["P_xc"] * I3
+    hw = 4.0 * math.pi * np.abs(nG) ** 2 * inv2 * inv2
+    SH = -ev["E_H"] / V * I3 + np.array([[np.sum(hw * Gs[a] * Gs[b]) for b in range(3)] for a in range(3)])
+    if sys.lpp == "ha":
+        dv = 1.5 * (sys.vpG - sys.vG) * inv2
+    else:
+        dv = sys.vG * (-sys.rc ** 2 / 4.0 - inv2)
+    lw = np.real(np.conj(nG) * dv)
+    Sloc = -ev["E_loc"] / V * I3 - 2.0 * np.array([[np.sum(lw * Gs[a] * Gs[b]) for b in range(3)]
+                                                   for a in range(3)])
+    cell = np.diag(g.L) if sys.cell is None else sys.cell
+    Sion = ewald_cell(cell, sys.R, sys.Z)[2]
+    tot = Ss + Sxc + SH + Sloc + Sion
+    return dict(Sigma=tot, s=Ss, xc=Sxc, H=SH, loc=Sloc, ion=Sion)
 
 
 # ---------------------------------------------------- minimisation (Sec. II)
