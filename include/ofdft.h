@@ -234,6 +234,23 @@ ofdft_status ofdft_autotune(ofdft_ctx *ctx, int reps);
  */
 ofdft_status ofdft_forces(ofdft_ctx *ctx, double *F, double *pressure);
 
+/*
+ * Stress tensor at the current density, Eq. (StressTensor):
+ * Sigma_ab = (1/V) sum_nu (dF/dh_a,nu) h_b,nu (hartree/bohr^3, row-major
+ * sigma[9], symmetric), so that P = -Tr Sigma / 3 (Eq. (pressure)); call it
+ * after ofdft_minimize for the equilibrium value.  Terms, for a homogeneous
+ * strain at fixed fractional coordinates and V n(G):
+ *   non-interacting  delta_ab/V int (f_s - n v_s) - (1/V) int W_a d_b n,
+ *                    W = d f_s/d grad n (Eqs. (stressTF_a), (stressTF_b))
+ *   XC               delta_ab/V int n (eps_xc - v_xc)   (Eq. (stressLSDAxc))
+ *   Hartree          -delta_ab E_H/V + sum_G 4 pi |n(G)|^2 G_a G_b/G^4
+ *   local pseudo.    -delta_ab E_loc/V - 2 sum_G Re[n*(G) dv/dG^2] G_a G_b
+ *   ions             Ewald stress (real-space pairs, reciprocal sum, background)
+ * terms (may be NULL) receives the five tensors in that order ([5][9]).
+ * One evaluation plus the stress sums; the density is not changed.
+ */
+ofdft_status ofdft_stress(ofdft_ctx *ctx, double *sigma, double *terms);
+
 /* Copy the current density n = phi^2 to host n[N]. */
 ofdft_status ofdft_get_density(ofdft_ctx *ctx, double *n);
 

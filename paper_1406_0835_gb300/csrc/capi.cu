@@ -248,10 +248,13 @@ int eval_kernel_count(const ofdft_ctx *c) { return c->fp.kind == 0 ? 7 : 12; }
 // Enqueue one energy + potential evaluation at ph (or, with phi0 and dh, at the
 // trial phi0 cos + dh sin written into ph; angles from csd (two T values in
 // device memory) if given).  Sums go
-// to sums[0..17].  No synchronisation.
+// to sums[0..17].  With spart (FP64 GGA sets), the z pass also writes the
+// gradient stress sums: spart holds 12 partial rows of *nbg_out columns.
+// No synchronisation.
 template <typename T>
 ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const T *dh, double cth,
-                          double sth, const void *csd, T *vout, bool keep_nG, double *sums)
+                          double sth, const void *csd, T *vout, bool keep_nG, double *sums,
+                          double *spart = nullptr, int *nbg_out = nullptr)
 {
     const GridInfo &g = f.gt;
     const FftAxis &ax = f.ax[0], &ay = f.ax[1], &az = f.ax[2];
@@ -305,7 +308,17 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
         DBG("k_ypass inv x3");
         {
             TimerScope ts(c, TM_ZGGA);
-            nbg = launch_zgga<T>(g, az, s1, s2, s3, ph, (T)c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, st);
+            bool stress_pass = false;
+            if constexpr (std::is_same<T, double>::value) {
+                if (spart) {
+                    pB = spart;
+                    nbg = launch_zgga_stress(g, az, s1, s2, s3, ph, c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, st);
+                    if (nbg_out) *nbg_out = nbg;
+                    stress_pass = true;
+                }
+            }
+            if (!stress_pass)
+                nbg = launch_zgga<T>(g, az, s1, s2, s3, ph, (T)c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, st);
         }
         DBG("k_zgga");
         {
@@ -1373,6 +1386,80 @@ ofdft_status ofdft_forces(ofdft_ctx *c, double *F, double *pressure)
         CK(cudaStreamSynchronize(c->st));
     }
     if (pressure) *pressure = e.P;
+    return OFDFT_OK;
+}
+
+ofdft_status ofdft_stress(ofdft_ctx *c, double *sigma, double *terms)
+{
+    if (!c || !sigma) return fail(c, OFDFT_EINVAL, "NULL argument");
+    NOT_BUSY(c);
+    cudaSetDevice(c->dev);
+    FieldSet &f = c->f[0];
+    const GridInfo &g = c->g;
+    cudaStream_t st = c->st;
+    const bool fttf = c->fp.kind == 0;
+    const long long npairs = (long long)g.nx * g.ny / 2;
+    const size_t nxy = (size_t)g.nx * g.ny;
+    const int nbr = std::max(1, (c->nGe + 255) / 256);
+    const size_t nzp = fttf ? 0 : 12 * (size_t)npairs;
+    const size_t ntot = nzp + 12 * nxy + 6 * (size_t)c->nat + 7 * (size_t)nbr + 32;
+    double *buf = nullptr;
+    CK(cudaMallocAsync((void **)&buf, ntot * sizeof(double), st));
+    double *zpart = buf, *gpart = buf + nzp, *rpart = gpart + 12 * nxy, *kpart = rpart + 6 * (size_t)c->nat;
+    double *out = kpart + 7 * (size_t)nbr;
+    int nbg = 0;
+    ofdft_status s = enqueue_eval<double>(c, f, (double *)f.phi, nullptr, nullptr, 1.0, 0.0, nullptr,
+                                          (double *)f.vt, true, c->scal, fttf ? nullptr : zpart, &nbg);
+    if (s != OFDFT_OK) {
+        cudaFreeAsync(buf, st);
+        return s;
+    }
+    // out[0..5] sum W_a d_b n, [6..11] Hartree, [12..17] LPP, [18..23] Ewald real, [24..30] Ewald G
+    if (!fttf) launch_reduce(zpart + 6 * (size_t)nbg, nbg, 6, out, st);
+    else CK(cudaMemsetAsync(out, 0, 6 * sizeof(double), st));
+    const double2 *nG = (const double2 *)f.spec + (fttf ? f.spec_stride : 0);
+    const int ng = launch_gstress(g, c->nat, c->Zd, c->px, c->py, c->pz, nG, gpart, st);
+    launch_reduce(gpart, ng, 12, out + 6, st);
+    double L[3] = {g.Lx, g.Ly, g.Lz};
+    const int nb = launch_ewald_stress(c->nat, c->Rd, c->Zd, L, c->ew_alpha, c->ew_rcut, c->ew_nimg, c->nGe,
+                                       c->Gv, c->wG, (const double2 *)c->Se, rpart, kpart, st);
+    launch_reduce(rpart, c->nat, 6, out + 18, st);
+    launch_reduce(kpart, nb, 7, out + 24, st);
+    c->launches += (fttf ? 0 : 1) + 2 + 4;
+    double o[31], h[18];
+    CK(cudaMemcpyAsync(o, out, sizeof(o), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h, c->scal, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(buf, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    const EvalScalars es = unpack_sums(h, fttf);
+    const double V = g.omega, dV = g.dV;
+    double zs = 0.0;
+    for (int i = 0; i < c->nat; ++i) zs += c->Z[i];
+    const double Ebg = -kPi * zs * zs / (2.0 * V * c->ew_alpha * c->ew_alpha);
+    // terms: non-interacting, XC, Hartree, LPP, ions (Sigma = sum); Eq. (StressTensor)
+    double S[5][9] = {};
+    for (int d = 0; d < 3; ++d) {
+        S[0][4 * d] = -dV * (es.PS + es.WG) / V;             // delta/V int (f_s - n v_s)
+        S[1][4 * d] = -dV * es.PXC / V;                      // delta/V int n (eps_xc - v_xc)
+        S[2][4 * d] = -es.EH / V;
+        S[3][4 * d] = -es.Eloc / V;
+        S[4][4 * d] = -o[24] / V - Ebg / V;
+    }
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int q = 0; q < 6; ++q) {
+        const double add[5] = {-dV * o[q] / V, 0.0, o[6 + q], -2.0 * o[12 + q],
+                               -0.5 / V * o[18 + q] + 2.0 / V * o[25 + q]};
+        for (int t = 0; t < 5; ++t) {
+            S[t][3 * ia[q] + ib[q]] += add[t];
+            if (ia[q] != ib[q]) S[t][3 * ib[q] + ia[q]] += add[t];
+        }
+    }
+    for (int k = 0; k < 9; ++k) {
+        sigma[k] = S[0][k] + S[1][k] + S[2][k] + S[3][k] + S[4][k];
+        if (terms)
+            for (int t = 0; t < 5; ++t) terms[9 * t + k] = S[t][k];
+    }
     return OFDFT_OK;
 }
 

@@ -13,6 +13,11 @@ template <typename T>
 int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, cplx<T> *g2,
                 const T *phit, T temp, const FuncParams &fp, const T *tab, int xc, T *vpart,
                 double *part, cudaStream_t st);
+// The same evaluation stage for an FP64 set, also writing sum W_a d_b n
+// (xx, yy, zz, xy, xz, yz) into partial rows 6..11 (part holds 12 rows).
+int launch_zgga_stress(const GridInfo &g, const FftAxis &az, double2 *g0, double2 *g1, double2 *g2,
+                       const double *phit, double temp, const FuncParams &fp, const double *tab, int xc,
+                       double *vpart, double *part, cudaStream_t st);
 template <typename T>
 int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T> *dspec,
                   const T *vpart, const T *phit, const T *phi, const T *dhat, T c, T s,
@@ -95,6 +100,15 @@ void launch_md_b(int nat, const double *m, double *V, const double *F, double dt
                  double Q, int ndof, int thermo, double *nh, cudaStream_t st);
 void launch_andersen(int nat, const double *m, double *V, double kT, double prob, const double *u,
                      const double *xi, double *nh, cudaStream_t st);
+// Stress tensor parts: Hartree and LPP sums over the half spectrum (12
+// partial rows, nx ny columns; returns the column count), and the Ewald
+// real-space (6 rows, nat columns) and reciprocal (7 rows; returns the
+// column count) sums.
+int launch_gstress(const GridInfo &g, int nat, const double *Z, const double2 *px, const double2 *py,
+                   const double2 *pz, const double2 *nG, double *part, cudaStream_t st);
+int launch_ewald_stress(int nat, const double *R, const double *Z, const double *L, double alpha, double rcut,
+                        int3 nimg, int nG, const double *Gv, const double *wG, const double2 *S,
+                        double *preal, double *precip, cudaStream_t st);
 
 // ---- device CG controller (cg_control.cu); single-thread kernels.
 // use_cond = 0 outside a graph (the handles are then ignored).

@@ -262,8 +262,10 @@ __device__ __forceinline__ void unpack_r2c(const typename KT<PR>::CC *X, long lo
 
 // Fused GGA stage: C2R of grad n (3 fields), pointwise functional + XC,
 // R2C of W (3 fields, written over grad n).  Partials: F_s, TS, F_xc,
-// sum(n df/dn - f), sum W.grad n, sum n(v_xc - eps_xc).
-template <typename PR>
+// sum(n df/dn - f), sum W.grad n, sum n(v_xc - eps_xc); with STRESS also
+// sum W_a d_b n for ab = xx, yy, zz, xy, xz, yz (the gradient part of
+// Eq. (stressTF_b)) in partial rows 6..11.
+template <typename PR, bool STRESS>
 __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__restrict__ g0,
                        typename KT<PR>::C *__restrict__ g1, typename KT<PR>::C *__restrict__ g2,
                        const typename KT<PR>::T *__restrict__ phit, typename KT<PR>::T temp, FuncParams fp,
@@ -291,6 +293,9 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__rest
     CC *X = fft_lines<CC, true>(A, B, az, 3 * nl, nz, 1, false);
     CC *res[3] = {X, X + nl * nz, X + 2 * nl * nz};
     R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    R sacc[STRESS ? 6 : 1];
+    if constexpr (STRESS)
+        for (int q = 0; q < 6; ++q) sacc[q] = R(0);
     const ff::f2 tcoef = is_dd<PR>() ? ff::f2(2.0 / OF_K23 * (double)temp) : ff::f2(0.0f, 0.0f);
     RowCol rc(nz);
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x, rc.next()) {
@@ -310,6 +315,14 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__rest
             acc[3] += n * o.dfdn - o.f;
             acc[4] += o.w[0] * gr[0] + o.w[1] * gr[1] + o.w[2] * gr[2];
             acc[5] += n * (o.vxc - o.eps);
+            if constexpr (STRESS) {
+                sacc[0] += o.w[0] * gr[0];
+                sacc[1] += o.w[1] * gr[1];
+                sacc[2] += o.w[2] * gr[2];
+                sacc[3] += o.w[0] * gr[1];
+                sacc[4] += o.w[0] * gr[2];
+                sacc[5] += o.w[1] * gr[2];
+            }
             for (int a = 0; a < 3; ++a) {
                 R *d = reinterpret_cast<R *>(&res[a][p * nz + e]);
                 d[hi] = o.w[a];
@@ -327,6 +340,14 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__rest
             acc[3] += n * o.dfdn - o.f;
             acc[4] += o.wc * gg;
             acc[5] += n * (vxc - eps);
+            if constexpr (STRESS) {
+                sacc[0] += o.wc * gr[0] * gr[0];
+                sacc[1] += o.wc * gr[1] * gr[1];
+                sacc[2] += o.wc * gr[2] * gr[2];
+                sacc[3] += o.wc * gr[0] * gr[1];
+                sacc[4] += o.wc * gr[0] * gr[2];
+                sacc[5] += o.wc * gr[1] * gr[2];
+            }
             for (int a = 0; a < 3; ++a) {
                 T *d = reinterpret_cast<T *>(&res[a][p * nz + e]);
                 d[hi] = o.wc * gr[a];
@@ -340,6 +361,12 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__rest
     block_total<6, PR>(acc, tot);
     if (threadIdx.x == 0)
         for (int q = 0; q < 6; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
+    if constexpr (STRESS) {
+        __syncthreads();
+        block_total<6, PR>(sacc, tot);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 6; ++q) part[(size_t)(6 + q) * gridDim.x + blockIdx.x] = tot[q];
+    }
 }
 
 // Final stage: C2R of D(G); v = D(r) + v_part (GGA) or, for ftTF, the
@@ -768,8 +795,23 @@ int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, 
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 6 * (size_t)P * g.nz * sizeof(cplx<T>);
     int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
-#define CALL(PR) k_zgga<PR><<<blocks, th, sm, st>>>(g, az, P, g0, g1, g2, phit, temp, fp, tab, xc, vpart, part)
+#define CALL(PR) k_zgga<PR, false><<<blocks, th, sm, st>>>(g, az, P, g0, g1, g2, phit, temp, fp, tab, xc, vpart, part)
     OFDFT_DISPATCH(T, g, CALL);
+#undef CALL
+    return blocks;
+}
+
+int launch_zgga_stress(const GridInfo &g, const FftAxis &az, double2 *g0, double2 *g1, double2 *g2,
+                       const double *phit, double temp, const FuncParams &fp, const double *tab, int xc,
+                       double *vpart, double *part, cudaStream_t st)
+{
+    int P = zpairs_per_block(g);
+    long long npairs = (long long)g.nx * g.ny / 2;
+    int blocks = (int)((npairs + P - 1) / P);
+    size_t sm = 6 * (size_t)P * g.nz * sizeof(double2);
+    int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
+#define CALL(PR) k_zgga<PR, true><<<blocks, th, sm, st>>>(g, az, P, g0, g1, g2, phit, temp, fp, tab, xc, vpart, part)
+    OFDFT_DISPATCH(double, g, CALL);
 #undef CALL
     return blocks;
 }
@@ -868,7 +910,7 @@ template <typename PR> cudaError_t smem_limits(int b)
         cudaFuncSetAttribute(k_zfwd<PR, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_zfwd<PR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_zfwd<PR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_zgga<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zgga<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_zfinal<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_zfinal<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_ypass<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
@@ -878,6 +920,8 @@ template <typename PR> cudaError_t smem_limits(int b)
         cudaFuncSetAttribute(k_xdiv<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return x;
+    if constexpr (!std::is_same<PR, float>::value)   // the stress variant (FP64 sets only)
+        return cudaFuncSetAttribute(k_zgga<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     return cudaSuccess;
 }
 }  // namespace

@@ -344,6 +344,106 @@ __global__ void k_vext(GridInfo g, int nat, const double *__restrict__ Z,
     }
 }
 
+// dw/dG^2 per unit charge at fixed Omega w (the strain derivative of the
+// form factor): Gaussian ion w (-rc^2/4 - 1/G^2); Heine-Abarenkov from its
+// dilation weight, wp = w + (2/3) G^2 dw/dG^2.
+__device__ __forceinline__ double lpp_dw(const GridInfo &g, double g2)
+{
+    if (!(g2 > 0.0)) return 0.0;
+    const double w = lpp_w(g, g2);
+    if (g.lpp == 0) return w * (-0.25 * g.rc * g.rc - 1.0 / g2);
+    return 1.5 * (lpp_wp_ha(g, g2) - w) / g2;
+}
+
+// Hartree and local-pseudopotential parts of the stress tensor
+// (Eq. (StressTensor): homogeneous strain at fixed Omega n(G) and fractional
+// coordinates), summed over the full FFT box from the half spectrum:
+//   H_ab = sum_G 4 pi |n(G)|^2 G_a G_b / G^4,
+//   L_ab = sum_G Re[conj(n(G)) w'(G^2) S(G)] G_a G_b,
+// w' = dw/dG^2 per unit charge, S(G) = sum_I Z_I e^{-iG.R_I}.  A point with
+// 0 < kz < nz/2 also stands for its partner G' = -G (with +n/2 kept on the
+// Nyquist axes): n(G') = conj(n(G)) and conj(S(G')) = sum_I Z_I times the
+// phase factors conjugated on the Nyquist axes only, as in k_vext.
+// One block per (ix, iy) row; partial rows H xx yy zz xy xz yz, then L.
+__global__ void k_gstress(GridInfo g, int nat, const double *__restrict__ Z,
+                          const double2 *__restrict__ px, const double2 *__restrict__ py,
+                          const double2 *__restrict__ pz, const double2 *__restrict__ nG,
+                          double *__restrict__ part)
+{
+    constexpr int kChunk = 256;
+    __shared__ double2 a[kChunk], b[kChunk];
+    const int ix = blockIdx.x / g.ny, iy = blockIdx.x - ix * g.ny;
+    const bool rnyq = (2 * ix == g.nx) || (2 * iy == g.ny);
+    double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    double2 acc2[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    for (int I0 = 0; I0 < nat; I0 += kChunk) {
+        const int nI = min(kChunk, nat - I0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < nI; j += blockDim.x) {
+            const int I = I0 + j;
+            double2 u = px[(size_t)I * g.nx + ix], v = py[(size_t)I * g.ny + iy];
+            double2 p = zmul(u, v);
+            a[j] = make_double2(Z[I] * p.x, Z[I] * p.y);
+            if (rnyq) {
+                if (2 * ix == g.nx) u.y = -u.y;
+                if (2 * iy == g.ny) v.y = -v.y;
+                double2 pp = zmul(u, v);
+                b[j] = make_double2(Z[I] * pp.x, Z[I] * pp.y);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kz = threadIdx.x + h * blockDim.x;
+            if (kz >= g.K) continue;
+            const double2 *pzc = pz + (size_t)I0 * g.K + kz;
+            for (int j = 0; j < nI; ++j) {
+                const double2 c = pzc[(size_t)j * g.K];
+                double2 t = zmul(a[j], c);
+                acc[h].x += t.x;
+                acc[h].y += t.y;
+                if (rnyq) {
+                    double2 t2 = zmul(b[j], c);
+                    acc2[h].x += t2.x;
+                    acc2[h].y += t2.y;
+                }
+            }
+        }
+    }
+    double sm[12];
+    for (int q = 0; q < 12; ++q) sm[q] = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int kz = threadIdx.x + h * blockDim.x;
+        if (kz >= g.K) continue;
+        Hk k = hk_at(g, ix, iy, kz);
+        if (!(k.g2 > 0.0)) continue;
+        const double2 n = nG[(size_t)blockIdx.x * g.K + kz];
+        const double inv = 1.0 / k.g2;
+        const double hw = 12.566370614359172954 * (n.x * n.x + n.y * n.y) * inv * inv;
+        const double wd = lpp_dw(g, k.g2);
+        const double lw = wd * (n.x * acc[h].x + n.y * acc[h].y);
+        const double f[6] = {k.gx * k.gx, k.gy * k.gy, k.gz * k.gz, k.gx * k.gy, k.gx * k.gz, k.gy * k.gz};
+        for (int q = 0; q < 6; ++q) {
+            sm[q] += hw * f[q];
+            sm[6 + q] += lw * f[q];
+        }
+        if (kz > 0 && !k.nz_) {
+            const double2 sp = rnyq ? acc2[h] : acc[h];
+            const double lp = wd * (n.x * sp.x + n.y * sp.y);
+            const double gx = k.nx_ ? k.gx : -k.gx, gy = k.ny_ ? k.gy : -k.gy, gz = -k.gz;
+            const double fp[6] = {gx * gx, gy * gy, gz * gz, gx * gy, gx * gz, gy * gz};
+            for (int q = 0; q < 6; ++q) {
+                sm[q] += hw * fp[q];
+                sm[6 + q] += lp * fp[q];
+            }
+        }
+    }
+    block_sum<12>(sm);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 12; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = sm[q];
+}
+
 // Per-point weight of the local forces: cn(G) = -Omega w_k w(G) conj(n(G)).
 template <typename T>
 __global__ void k_lpp_prep(GridInfo g, const cplx<T> *__restrict__ nG, double2 *__restrict__ cn)
@@ -455,6 +555,77 @@ __global__ void k_ewald_real(int nat, const double *__restrict__ R, const double
         F[3 * I + 1] = acc[2];
         F[3 * I + 2] = acc[3];
     }
+}
+
+// Real-space Ewald stress: per ion I, sum over J and images of
+// g(r) r_a r_b / r^2 with g = Z_I Z_J (erfc(a r)/r + (2a/sqrt pi) e^{-a^2 r^2})
+// (the pair sum of Sigma_real = -(1/2 Omega) sum' g r_a r_b / r^2), rows
+// xx yy zz xy xz yz, one column per ion.  Same pair loop as k_ewald_real.
+__global__ void k_ewald_stress_real(int nat, const double *__restrict__ R, const double *__restrict__ Z,
+                                    double Lx, double Ly, double Lz, double alpha, double rcut, int3 nimg,
+                                    double *part)
+{
+    const int I = blockIdx.x;
+    const int ix = 2 * nimg.x + 1, iy = 2 * nimg.y + 1, iz = 2 * nimg.z + 1;
+    const long long total = (long long)nat * ix * iy * iz;
+    const double twosqpi = 1.1283791670955125739;   // 2/sqrt(pi)
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const double xi = R[3 * I], yi = R[3 * I + 1], zi = R[3 * I + 2], ZI = Z[I];
+    for (long long q = threadIdx.x; q < total; q += blockDim.x) {
+        long long r0 = q;
+        const int J = (int)(r0 % nat);
+        r0 /= nat;
+        const int a = (int)(r0 % ix) - nimg.x;
+        r0 /= ix;
+        const int b = (int)(r0 % iy) - nimg.y;
+        const int c = (int)(r0 / iy) - nimg.z;
+        double dx = xi - R[3 * J], dy = yi - R[3 * J + 1], dz = zi - R[3 * J + 2];
+        dx -= Lx * rint(dx / Lx);
+        dy -= Ly * rint(dy / Ly);
+        dz -= Lz * rint(dz / Lz);
+        dx -= a * Lx;
+        dy -= b * Ly;
+        dz -= c * Lz;
+        double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < 1e-24 || r2 >= rcut * rcut) continue;
+        double r = sqrt(r2);
+        double gr = ZI * Z[J] * (erfc(alpha * r) / r + twosqpi * alpha * exp(-alpha * alpha * r2)) / r2;
+        acc[0] += gr * dx * dx;
+        acc[1] += gr * dy * dy;
+        acc[2] += gr * dz * dz;
+        acc[3] += gr * dx * dy;
+        acc[4] += gr * dx * dz;
+        acc[5] += gr * dy * dz;
+    }
+    block_sum<6>(acc);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) part[(size_t)k * nat + I] = acc[k];
+}
+
+// Reciprocal Ewald stress from S(G) (k_ewald_S): rows sum wG |S|^2 (the
+// reciprocal energy) and sum wG |S|^2 (1/(4 a^2) + 1/G^2) G_a G_b for
+// xx yy zz xy xz yz.
+__global__ void k_ewald_stress_recip(int nG, const double *__restrict__ Gv, const double *__restrict__ wG,
+                                     const double2 *__restrict__ S, double alpha, double *part)
+{
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const double q4 = 0.25 / (alpha * alpha);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nG; q += gridDim.x * blockDim.x) {
+        const double gx = Gv[3 * q], gy = Gv[3 * q + 1], gz = Gv[3 * q + 2];
+        const double2 Sq = S[q];
+        const double e = wG[q] * (Sq.x * Sq.x + Sq.y * Sq.y);
+        const double c = e * (q4 + 1.0 / (gx * gx + gy * gy + gz * gz));
+        acc[0] += e;
+        acc[1] += c * gx * gx;
+        acc[2] += c * gy * gy;
+        acc[3] += c * gz * gz;
+        acc[4] += c * gx * gy;
+        acc[5] += c * gx * gz;
+        acc[6] += c * gy * gz;
+    }
+    block_sum<7>(acc);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 7; ++k) part[(size_t)k * gridDim.x + blockIdx.x] = acc[k];
 }
 
 // S(G) = sum_I Z_I exp(i G.R_I); energy partial sum wG |S|^2.
@@ -692,6 +863,26 @@ int launch_ewald_recip(int nat, const double *R, const double *Z, int nG, const 
     if (b < 1) b = 1;
     k_ewald_S<<<b, 256, 0, st>>>(nat, R, Z, nG, Gv, wG, S, epart);
     k_ewald_F<<<nat, 256, 0, st>>>(nat, R, Z, nG, Gv, wG, S, F);
+    return b;
+}
+
+int launch_gstress(const GridInfo &g, int nat, const double *Z, const double2 *px, const double2 *py,
+                   const double2 *pz, const double2 *nG, double *part, cudaStream_t st)
+{
+    int th = 32 * ((g.K + 31) / 32);
+    if (th > 128) th = 32 * ((((g.K + 1) / 2) + 31) / 32);    // two columns per thread
+    k_gstress<<<g.nx * g.ny, th, 0, st>>>(g, nat, Z, px, py, pz, nG, part);
+    return g.nx * g.ny;
+}
+
+int launch_ewald_stress(int nat, const double *R, const double *Z, const double *L, double alpha, double rcut,
+                        int3 nimg, int nG, const double *Gv, const double *wG, const double2 *S,
+                        double *preal, double *precip, cudaStream_t st)
+{
+    k_ewald_stress_real<<<nat, 256, 0, st>>>(nat, R, Z, L[0], L[1], L[2], alpha, rcut, nimg, preal);
+    int b = (nG + 255) / 256;
+    if (b < 1) b = 1;
+    k_ewald_stress_recip<<<b, 256, 0, st>>>(nG, Gv, wG, S, alpha, precip);
     return b;
 }
 

@@ -110,6 +110,7 @@ SIGNATURES = {
                                       ctypes.POINTER(Energy), ctypes.POINTER(Stats)]),
     "ofdft_forces": (ctypes.c_int, [ctypes.c_void_p, _P, _P]),
     "ofdft_get_density": (ctypes.c_int, [ctypes.c_void_p, _P]),
+    "ofdft_stress": (ctypes.c_int, [ctypes.c_void_p, _P, _P]),
     "ofdft_set_masses": (ctypes.c_int, [ctypes.c_void_p, _P]),
     "ofdft_md_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(MDParams), ctypes.c_int, _P, _P,
                                      _P, ctypes.POINTER(Energy), ctypes.POINTER(Stats)]),
@@ -307,6 +308,19 @@ def ofdft_md_step(ctx, dt_fs, T_kelvin, nsteps=1, pos=None, vel=None, tau_steps=
     return dict(pos=pos, vel=vel, F=F, E=E.as_dict(), stats=S.as_dict())
 
 
+STRESS_TERMS = ("s", "xc", "H", "loc", "ion")
+
+
+def ofdft_stress(ctx):
+    """Stress tensor Sigma (3x3, hartree/bohr^3) and its five terms."""
+    sig = np.empty(9)
+    terms = np.empty(45)
+    _check(ctx, load().ofdft_stress(ctx, _ptr(sig), _ptr(terms)))
+    out = {k: terms[9 * i:9 * i + 9].reshape(3, 3) for i, k in enumerate(STRESS_TERMS)}
+    out["Sigma"] = sig.reshape(3, 3)
+    return out
+
+
 def ofdft_md_andersen(ctx, T_kelvin, prob, u, xi):
     nat = ofdft_sizes(ctx)[1]
     u = _f64(u, (nat,))
@@ -459,6 +473,9 @@ class Context:
 
     def forces(self):
         return ofdft_forces(self.ctx)
+
+    def stress(self):
+        return ofdft_stress(self.ctx)
 
     def density(self):
         return ofdft_get_density(self.ctx).reshape(self.grid)
