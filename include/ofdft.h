@@ -144,8 +144,13 @@ void ofdft_default_params(ofdft_params *p);
 /*
  * Create a context: cell, ions, grid, temperature and functional
  * (Sec. V C, create_ofdftgeom + the PROFESS input of Sec. V B).
- *  cell[9]     rows a, b, c in bohr; must be orthorhombic (off-diagonals 0),
- *              else OFDFT_EINVAL.
+ *  cell[9]     rows a, b, c: the lattice vectors in bohr (Cartesian
+ *              components).  Orthorhombic (off-diagonals 0, positive
+ *              diagonal) or general (triclinic, right-handed: det > 0);
+ *              grid point (i, j, k) sits at (i/nx) a + (j/ny) b + (k/nz) c
+ *              and G = kx b* + ky b* + kz c* with the reciprocal vectors.
+ *              Otherwise OFDFT_EINVAL.  (ofdft_energy_potential_static
+ *              takes orthorhombic cells only.)
  *  grid[3]     nx, ny, nz: even, factors in {2,3,5} only, 8 <= n <= 512.
  *  nat, ions   ions[nat][3] Cartesian bohr; Z[nat] valence charges (> 0).
  *  T_kelvin    electron temperature (> 0).

@@ -392,23 +392,51 @@ void fill_energy(const ofdft_ctx *c, const EvalScalars &es, ofdft_energy &E)
 }
 
 // ---------------------------------------------------------- ions & Ewald
+EwCell ew_cell(const GridInfo &g)
+{
+    EwCell e;
+    for (int k = 0; k < 9; ++k) {
+        e.a[k] = g.Am[k];
+        e.ai[k] = g.Ainv[k];
+    }
+    e.tri = g.tri;
+    return e;
+}
+
 ofdft_status setup_ewald(ofdft_ctx *c)
 {
     const GridInfo &g = c->g;
-    double L[3] = {g.Lx, g.Ly, g.Lz};
     double om = g.omega;
     c->ew_alpha = 1.2 * sqrt(kPi) * pow((double)c->nat / (om * om), 1.0 / 6.0);
     c->ew_rcut = 6.3 / c->ew_alpha;
-    c->ew_nimg = make_int3((int)ceil(c->ew_rcut / L[0] + 0.5), (int)ceil(c->ew_rcut / L[1] + 0.5),
-                           (int)ceil(c->ew_rcut / L[2] + 0.5));
+    // lattice planes normal to b_j are h_j = 2 pi/|b_j| apart; |a_j| bounds G.a_j/2 pi
+    double h[3], La[3];
+    for (int j = 0; j < 3; ++j) {
+        const double *b = g.Bm + 3 * j, *a = g.Am + 3 * j;
+        h[j] = 2.0 * kPi / sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+        La[j] = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    }
+    if (!g.tri) {
+        h[0] = La[0] = g.Lx;
+        h[1] = La[1] = g.Ly;
+        h[2] = La[2] = g.Lz;
+    }
+    c->ew_nimg = make_int3((int)ceil(c->ew_rcut / h[0] + 0.5), (int)ceil(c->ew_rcut / h[1] + 0.5),
+                           (int)ceil(c->ew_rcut / h[2] + 0.5));
     double gcut = 2.0 * c->ew_alpha * 6.3;
     int km[3];
-    for (int a = 0; a < 3; ++a) km[a] = (int)ceil(gcut * L[a] / (2.0 * kPi));
+    for (int a = 0; a < 3; ++a) km[a] = (int)ceil(gcut * La[a] / (2.0 * kPi));
     std::vector<double> Gv, wG;
+    const double *B = g.Bm;
     for (int i = -km[0]; i <= km[0]; ++i)
         for (int j = -km[1]; j <= km[1]; ++j)
             for (int k = -km[2]; k <= km[2]; ++k) {
-                double gx = 2 * kPi * i / L[0], gy = 2 * kPi * j / L[1], gz = 2 * kPi * k / L[2];
+                double gx = 2 * kPi * i / g.Lx, gy = 2 * kPi * j / g.Ly, gz = 2 * kPi * k / g.Lz;
+                if (g.tri) {
+                    gx = i * B[0] + j * B[3] + k * B[6];
+                    gy = i * B[1] + j * B[4] + k * B[7];
+                    gz = i * B[2] + j * B[5] + k * B[8];
+                }
                 double g2 = gx * gx + gy * gy + gz * gz;
                 if (g2 == 0.0 || g2 >= gcut * gcut) continue;
                 Gv.push_back(gx);
@@ -441,8 +469,7 @@ ofdft_status update_ions(ofdft_ctx *c)
     if (c->f[1].valid)
         launch_convert<double, float>((g.lpp ? 4 : 2) * g.NH, (const double *)c->f[0].vext, (float *)c->f[1].vext,
                                       st);
-    double L[3] = {g.Lx, g.Ly, g.Lz};
-    launch_ewald_real(c->nat, c->Rd, c->Zd, L, c->ew_alpha, c->ew_rcut, c->ew_nimg, c->eion, c->ewF, st);
+    launch_ewald_real(c->nat, c->Rd, c->Zd, ew_cell(g), c->ew_alpha, c->ew_rcut, c->ew_nimg, c->eion, c->ewF, st);
     int nb = launch_ewald_recip(c->nat, c->Rd, c->Zd, c->nGe, c->Gv, c->wG, c->Se, c->ewpart, c->ewF, st);
     c->launches += 5 + (c->f[1].valid ? 1 : 0);
     std::vector<double> e(c->nat + nb);
@@ -1114,11 +1141,17 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     if (!out) return fail(nullptr, OFDFT_EINVAL, "out is NULL");
     *out = nullptr;
     if (!cell || !grid || !ions || !Z || nat <= 0) return fail(nullptr, OFDFT_EINVAL, "NULL input or nat <= 0");
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            if (i != j && cell[3 * i + j] != 0.0)
-                return fail(nullptr, OFDFT_EINVAL, "cell is not orthorhombic");
-    if (!(cell[0] > 0 && cell[4] > 0 && cell[8] > 0)) return fail(nullptr, OFDFT_EINVAL, "non-positive cell edge");
+    bool tri = false;
+    for (int i = 0; i < 9; ++i) {
+        if (!isfinite(cell[i])) return fail(nullptr, OFDFT_EINVAL, "non-finite cell");
+        if (i % 4 != 0 && cell[i] != 0.0) tri = true;
+    }
+    const double det = cell[0] * (cell[4] * cell[8] - cell[5] * cell[7]) -
+                       cell[1] * (cell[3] * cell[8] - cell[5] * cell[6]) +
+                       cell[2] * (cell[3] * cell[7] - cell[4] * cell[6]);
+    if (!tri && !(cell[0] > 0 && cell[4] > 0 && cell[8] > 0))
+        return fail(nullptr, OFDFT_EINVAL, "non-positive cell edge");
+    if (tri && !(det > 0.0)) return fail(nullptr, OFDFT_EINVAL, "cell vectors must be right-handed (det > 0)");
     for (int a = 0; a < 3; ++a)
         if (!smooth_even(grid[a]))
             return fail(nullptr, OFDFT_EINVAL, "grid edges must be even, {2,3,5}-smooth, in [8, 512]");
@@ -1169,10 +1202,19 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     g.K = g.nz / 2 + 1;
     g.N = (long long)g.nx * g.ny * g.nz;
     g.NH = (long long)g.nx * g.ny * g.K;
-    g.Lx = cell[0];
-    g.Ly = cell[4];
-    g.Lz = cell[8];
-    g.omega = g.Lx * g.Ly * g.Lz;
+    g.tri = tri ? 1 : 0;
+    if (tri) {
+        for (int k = 0; k < 9; ++k) g.Am[k] = cell[k];
+        g.Lx = sqrt(cell[0] * cell[0] + cell[1] * cell[1] + cell[2] * cell[2]);
+        g.Ly = sqrt(cell[3] * cell[3] + cell[4] * cell[4] + cell[5] * cell[5]);
+        g.Lz = sqrt(cell[6] * cell[6] + cell[7] * cell[7] + cell[8] * cell[8]);
+        g.omega = det;
+    } else {
+        g.Lx = cell[0];
+        g.Ly = cell[4];
+        g.Lz = cell[8];
+        g.omega = g.Lx * g.Ly * g.Lz;
+    }
     g.dV = g.omega / (double)g.N;
     g.rc = p.rc;
     g.lpp = p.lpp;
@@ -1420,8 +1462,7 @@ ofdft_status ofdft_stress(ofdft_ctx *c, double *sigma, double *terms)
     const double2 *nG = (const double2 *)f.spec + (fttf ? f.spec_stride : 0);
     const int ng = launch_gstress(g, c->nat, c->Zd, c->px, c->py, c->pz, nG, gpart, st);
     launch_reduce(gpart, ng, 12, out + 6, st);
-    double L[3] = {g.Lx, g.Ly, g.Lz};
-    const int nb = launch_ewald_stress(c->nat, c->Rd, c->Zd, L, c->ew_alpha, c->ew_rcut, c->ew_nimg, c->nGe,
+    const int nb = launch_ewald_stress(c->nat, c->Rd, c->Zd, ew_cell(g), c->ew_alpha, c->ew_rcut, c->ew_nimg, c->nGe,
                                        c->Gv, c->wG, (const double2 *)c->Se, rpart, kpart, st);
     launch_reduce(rpart, c->nat, 6, out + 18, st);
     launch_reduce(kpart, nb, 7, out + 24, st);

@@ -86,9 +86,17 @@ int launch_lpp_forces(const GridInfo &g, int nat, const double *Z, const double2
 void launch_force_reduce(int nat, int nchunk, const double *part, double *F, int accumulate,
                          cudaStream_t st);
 
+// The cell of the Ewald real-space sums: rows a_j of a (bohr), ai = a^-1;
+// tri = 0 for an orthorhombic cell (a diagonal).
+struct EwCell {
+    double a[9], ai[9];
+    int tri;
+};
+
 // Ewald: real-space part per ion -> eparts[nat], F[nat][3];
 // reciprocal part over the G list -> S[nG], energy partials, forces added.
-void launch_ewald_real(int nat, const double *R, const double *Z, const double *L, double alpha,
+
+void launch_ewald_real(int nat, const double *R, const double *Z, const EwCell &cl, double alpha,
                        double rcut, int3 nimg, double *eion, double *F, cudaStream_t st);
 int launch_ewald_recip(int nat, const double *R, const double *Z, int nG, const double *Gv,
                        const double *wG, double2 *S, double *epart, double *F, cudaStream_t st);
@@ -106,7 +114,7 @@ void launch_andersen(int nat, const double *m, double *V, double kT, double prob
 // column count) sums.
 int launch_gstress(const GridInfo &g, int nat, const double *Z, const double2 *px, const double2 *py,
                    const double2 *pz, const double2 *nG, double *part, cudaStream_t st);
-int launch_ewald_stress(int nat, const double *R, const double *Z, const double *L, double alpha, double rcut,
+int launch_ewald_stress(int nat, const double *R, const double *Z, const EwCell &cl, double alpha, double rcut,
                         int3 nimg, int nG, const double *Gv, const double *wG, const double2 *S,
                         double *preal, double *precip, cudaStream_t st);
 

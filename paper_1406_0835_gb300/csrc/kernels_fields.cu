@@ -121,6 +121,58 @@ template <typename A> __device__ __forceinline__ A dmul(int i, int n, A b)
     return (2 * i == n) ? A(0) : A(k) * b;
 }
 
+// Reciprocal basis of the x passes in the computed precision.  Orthorhombic
+// (TRI = false): per-axis spacings, G_a = k_a b_a.  General cell (TRI =
+// true): G = kx b_0 + ky b_1 + kz b_2 (+n/2 on Nyquist planes), and the
+// Cartesian first-derivative multiplier D_a = sum_j kd_j (b_j)_a with each
+// integer kd_j zeroed on its own Nyquist plane (so gradient and divergence
+// stay exact adjoints).  gk: G^2 and Hermitian weight; d: D_a.
+template <typename PR, bool TRI> struct RecipB;
+template <typename PR> struct RecipB<PR, false> {
+    typedef typename KT<PR>::R R;
+    R bx, by, bz;
+    __device__ __forceinline__ explicit RecipB(const GridInfo &g)
+        : bx(gcst<PR>(g.bx, g.bxf, g.bx2)), by(gcst<PR>(g.by, g.byf, g.by2)), bz(gcst<PR>(g.bz, g.bzf, g.bz2))
+    {
+    }
+    __device__ __forceinline__ Gk<R> gk(const GridInfo &g, int ix, int iy, int kz) const
+    {
+        return gvec<R>(g, bx, by, bz, ix, iy, kz);
+    }
+    __device__ __forceinline__ R d(const GridInfo &g, int a, int ix, int iy, int kz) const
+    {
+        return a == 0 ? dmul<R>(ix, g.nx, bx) : (a == 1 ? dmul<R>(iy, g.ny, by) : dmul<R>(kz, g.nz, bz));
+    }
+};
+template <typename PR> struct RecipB<PR, true> {
+    typedef typename KT<PR>::R R;
+    R b[9];
+    __device__ __forceinline__ explicit RecipB(const GridInfo &g)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) b[k] = gcst<PR>(g.Bm[k], g.Bmf[k], g.Bm2[k]);
+    }
+    __device__ __forceinline__ Gk<R> gk(const GridInfo &g, int ix, int iy, int kz) const
+    {
+        Gk<R> r;
+        const R kx = R(ix <= g.nx / 2 ? ix : ix - g.nx), ky = R(iy <= g.ny / 2 ? iy : iy - g.ny), kzr = R(kz);
+        r.gx = kx * b[0] + ky * b[3] + kzr * b[6];
+        r.gy = kx * b[1] + ky * b[4] + kzr * b[7];
+        r.gz = kx * b[2] + ky * b[5] + kzr * b[8];
+        r.g2 = r.gx * r.gx + r.gy * r.gy + r.gz * r.gz;
+        r.dx = r.dy = r.dz = R(0);
+        r.w = (kz == 0 || 2 * kz == g.nz) ? R(1) : R(2);
+        return r;
+    }
+    __device__ __forceinline__ R d(const GridInfo &g, int a, int ix, int iy, int kz) const
+    {
+        const int kx = (2 * ix == g.nx) ? 0 : (ix <= g.nx / 2 ? ix : ix - g.nx);
+        const int ky = (2 * iy == g.ny) ? 0 : (iy <= g.ny / 2 ? iy : iy - g.ny);
+        const int kd = (2 * kz == g.nz) ? 0 : kz;
+        return R(kx) * b[a] + R(ky) * b[3 + a] + R(kd) * b[6 + a];
+    }
+};
+
 // Pointwise functional of the double-float z passes: the double-float
 // routine, and binary64 outside its domain.  n and gr[3] in double-float.
 __device__ __forceinline__ PwF2 pw_dd(const FuncParams &fp, const double *__restrict__ tab, ff::f2 tcoef,
@@ -549,7 +601,7 @@ __device__ __forceinline__ typename KT<PR>::R ploc_term(const GridInfo &g, const
 
 // x pass, gradient variant: forward x -> n(G) (stored), energies, then
 // i D_a n(G) inverse-x for a = x, y, z.  Partials: E_H, E_loc, P_loc.
-template <typename PR>
+template <typename PR, bool TRI>
 __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ nspec,
                         const typename KT<PR>::C *__restrict__ vext, typename KT<PR>::C *__restrict__ g0,
                         typename KT<PR>::C *__restrict__ g1, typename KT<PR>::C *__restrict__ g2,
@@ -567,8 +619,7 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
     load_tile<PR>(nspec, t, nx, A);
     __syncthreads();
     CC *X = fft_lines<CC, false>(A, B, ax, t.ncol, 1, g.tk, true);
-    const R bx = gcst<PR>(g.bx, g.bxf, g.bx2), by = gcst<PR>(g.by, g.byf, g.by2),
-            bz = gcst<PR>(g.bz, g.bzf, g.bz2);
+    const RecipB<PR, TRI> rb(g);
     const R hr = gcst<PR>(g.hr, g.hrf, g.hr2);
     const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
     R acc[3] = {R(0), R(0), R(0)};   // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
@@ -577,7 +628,7 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
         if (c >= t.ncol) continue;
         CC nG = cscale(X[i], invN);
         N[i] = nG;
-        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.couter[c], t.ckz[c]);
+        Gk<R> k = rb.gk(g, r, t.couter[c], t.ckz[c]);
         if (k.g2 > R(0)) {
             const long long vi = t.cbase[c] + r * t.rstride;
             CC ve = ldc<PR>(vext[vi]);
@@ -594,8 +645,7 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
     for (int a = 0; a < 3; ++a) {
         for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
             const int r = i >> t.tsh, c = i & (t.tk - 1);
-            const R d = a == 0 ? dmul<R>(r, g.nx, bx)
-                               : (a == 1 ? dmul<R>(t.couter[c], g.ny, by) : dmul<R>(t.ckz[c], g.nz, bz));
+            const R d = rb.d(g, a, r, t.couter[c], t.ckz[c]);
             CC v = N[i];
             A[i] = cmk<CC>(-d * v.y, d * v.x);      // i D_a n(G)
         }
@@ -617,7 +667,7 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
 
 // x pass, ftTF variant: forward x -> energies -> v_HL(G) = 4 pi n/G^2 + v_ext
 // inverse-x, written over the spectrum.  If keep_n, n(G) is also stored in nG_out.
-template <typename PR>
+template <typename PR, bool TRI>
 __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ spec,
                       const typename KT<PR>::C *__restrict__ vext, typename KT<PR>::C *__restrict__ nG_out,
                       int inverse, double *__restrict__ part)
@@ -632,8 +682,7 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
     load_tile<PR>(spec, t, nx, A);
     __syncthreads();
     CC *X = fft_lines<CC, false>(A, B, ax, t.ncol, 1, g.tk, true);
-    const R bx = gcst<PR>(g.bx, g.bxf, g.bx2), by = gcst<PR>(g.by, g.byf, g.by2),
-            bz = gcst<PR>(g.bz, g.bzf, g.bz2);
+    const RecipB<PR, TRI> rb(g);
     const R hr = gcst<PR>(g.hr, g.hrf, g.hr2);
     const R fpi = fourpi<PR>();
     const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
@@ -642,7 +691,7 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
         const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c >= t.ncol) continue;
         CC nG = cscale(X[i], invN);
-        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.couter[c], t.ckz[c]);
+        Gk<R> k = rb.gk(g, r, t.couter[c], t.ckz[c]);
         const long long vi = t.cbase[c] + r * t.rstride;
         CC ve = ldc<PR>(vext[vi]);
         CC out = cmk<CC>(R(0), R(0));
@@ -675,7 +724,7 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
 
 // x pass, divergence variant: D(G) = v_H(G) + v_ext(G) - sum_a i D_a W_a(G)
 // from n(G) and the y-transformed W_a; inverse-x result written over W_0.
-template <typename PR>
+template <typename PR, bool TRI>
 __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restrict__ nG,
                        const typename KT<PR>::C *__restrict__ vext, typename KT<PR>::C *__restrict__ w0,
                        const typename KT<PR>::C *__restrict__ w1, const typename KT<PR>::C *__restrict__ w2)
@@ -689,14 +738,13 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
     CC *B = A + nx * g.tk;
     CC *D = B + nx * g.tk;
     ColTile t = col_tile(g, true);
-    const R bx = gcst<PR>(g.bx, g.bxf, g.bx2), by = gcst<PR>(g.by, g.byf, g.by2),
-            bz = gcst<PR>(g.bz, g.bzf, g.bz2);
+    const RecipB<PR, TRI> rb(g);
     const R fpi = fourpi<PR>();
     const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c >= t.ncol) continue;
-        Gk<R> k = gvec<R>(g, bx, by, bz, r, t.couter[c], t.ckz[c]);
+        Gk<R> k = rb.gk(g, r, t.couter[c], t.ckz[c]);
         CC out = cmk<CC>(R(0), R(0));
         if (k.g2 > R(0)) {
             CC n = ldc<PR>(nG[t.cbase[c] + r * t.rstride]);
@@ -714,8 +762,7 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
         for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
             const int r = i >> t.tsh, c = i & (t.tk - 1);
             if (c >= t.ncol) continue;
-            const R d = (a == 0 ? dmul<R>(r, g.nx, bx)
-                                : (a == 1 ? dmul<R>(t.couter[c], g.ny, by) : dmul<R>(t.ckz[c], g.nz, bz))) * invN;
+            const R d = rb.d(g, a, r, t.couter[c], t.ckz[c]) * invN;
             CC wv = X[i];
             D[i] = cmk<CC>(D[i].x + d * wv.y, D[i].y - d * wv.x);   // -= i d W
         }
@@ -860,7 +907,9 @@ int launch_xgrad(const GridInfo &g, const FftAxis &ax, cplx<T> *nspec, const cpl
     int blocks = tiles_of(g, true);
     size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
-#define CALL(PR) k_xgrad<PR><<<blocks, th, sm, st>>>(g, ax, nspec, vext, g0, g1, g2, part)
+#define CALL(PR)                                                                         \
+    if (g.tri) k_xgrad<PR, true><<<blocks, th, sm, st>>>(g, ax, nspec, vext, g0, g1, g2, part); \
+    else k_xgrad<PR, false><<<blocks, th, sm, st>>>(g, ax, nspec, vext, g0, g1, g2, part)
     OFDFT_DISPATCH(T, g, CALL);
 #undef CALL
     return blocks;
@@ -873,7 +922,9 @@ int launch_xhl(const GridInfo &g, const FftAxis &ax, cplx<T> *spec, const cplx<T
     int blocks = tiles_of(g, true);
     size_t sm = 2 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
-#define CALL(PR) k_xhl<PR><<<blocks, th, sm, st>>>(g, ax, spec, vext, nG_out, inverse, part)
+#define CALL(PR)                                                                             \
+    if (g.tri) k_xhl<PR, true><<<blocks, th, sm, st>>>(g, ax, spec, vext, nG_out, inverse, part); \
+    else k_xhl<PR, false><<<blocks, th, sm, st>>>(g, ax, spec, vext, nG_out, inverse, part)
     OFDFT_DISPATCH(T, g, CALL);
 #undef CALL
     return blocks;
@@ -886,7 +937,9 @@ void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const 
     int blocks = tiles_of(g, true);
     size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
     int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
-#define CALL(PR) k_xdiv<PR><<<blocks, th, sm, st>>>(g, ax, nG, vext, w0, w1, w2)
+#define CALL(PR)                                                                   \
+    if (g.tri) k_xdiv<PR, true><<<blocks, th, sm, st>>>(g, ax, nG, vext, w0, w1, w2); \
+    else k_xdiv<PR, false><<<blocks, th, sm, st>>>(g, ax, nG, vext, w0, w1, w2)
     OFDFT_DISPATCH(T, g, CALL);
 #undef CALL
 }
@@ -915,9 +968,12 @@ template <typename PR> cudaError_t smem_limits(int b)
         cudaFuncSetAttribute(k_zfinal<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_ypass<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_ypass<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_xgrad<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_xhl<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_xdiv<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)};
+        cudaFuncSetAttribute(k_xgrad<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xhl<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xdiv<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xgrad<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xhl<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_xdiv<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return x;
     if constexpr (!std::is_same<PR, float>::value)   // the stress variant (FP64 sets only)

@@ -180,22 +180,29 @@ __global__ void k_phases(GridInfo g, int nat, const double *__restrict__ R, doub
         const int I = i / per, j = i - I * per;
         double G, r;
         double2 *dst;
+        int axis, k;
         if (j < g.nx) {
-            int k = j <= g.nx / 2 ? j : j - g.nx;
+            k = j <= g.nx / 2 ? j : j - g.nx;
             G = (double)k * g.bx;
-            r = R[3 * I];
+            axis = 0;
             dst = px + (size_t)I * g.nx + j;
         } else if (j < g.nx + g.ny) {
             int jj = j - g.nx;
-            int k = jj <= g.ny / 2 ? jj : jj - g.ny;
+            k = jj <= g.ny / 2 ? jj : jj - g.ny;
             G = (double)k * g.by;
-            r = R[3 * I + 1];
+            axis = 1;
             dst = py + (size_t)I * g.ny + jj;
         } else {
-            int jj = j - g.nx - g.ny;
-            G = (double)jj * g.bz;
-            r = R[3 * I + 2];
-            dst = pz + (size_t)I * g.K + jj;
+            k = j - g.nx - g.ny;
+            G = (double)k * g.bz;
+            axis = 2;
+            dst = pz + (size_t)I * g.K + k;
+        }
+        r = R[3 * I + axis];
+        if (g.tri) {
+            // G.R = 2 pi k s_axis with the fractional coordinate s = R Ainv
+            G = 6.283185307179586477 * (double)k;
+            r = R[3 * I] * g.Ainv[axis] + R[3 * I + 1] * g.Ainv[3 + axis] + R[3 * I + 2] * g.Ainv[6 + axis];
         }
         double s, c;
         sincos(G * r, &s, &c);
@@ -240,12 +247,15 @@ __device__ __forceinline__ double lpp_wp_ha(const GridInfo &g, double g2)
     return -4.1887902047863909846 * exp(-u6) * (B + qdB - 6.0 * u6 * B) / (g.omega * g2 * g.ha_Z);
 }
 
-// Half-spectrum point (ix, iy, kz): G from the reciprocal spacings, Nyquist
-// flags and Hermitian weight.
+// Half-spectrum point (ix, iy, kz): G from the reciprocal basis, Nyquist
+// flags, Hermitian weight and the partner G' of the full box that the point
+// also stands for (-G, except that an integer index on its Nyquist plane
+// keeps +n/2).
 struct Hk {
     int ix, iy, kz;
     bool nx_, ny_, nz_;
     double gx, gy, gz, g2, wk;
+    double gpx, gpy, gpz;
 };
 
 __device__ __forceinline__ Hk hk_at(const GridInfo &g, int ix, int iy, int kz)
@@ -256,13 +266,27 @@ __device__ __forceinline__ Hk hk_at(const GridInfo &g, int ix, int iy, int kz)
     h.kz = kz;
     int kx = ix <= g.nx / 2 ? ix : ix - g.nx;
     int ky = iy <= g.ny / 2 ? iy : iy - g.ny;
-    h.gx = (double)kx * g.bx;
-    h.gy = (double)ky * g.by;
-    h.gz = (double)kz * g.bz;
-    h.g2 = h.gx * h.gx + h.gy * h.gy + h.gz * h.gz;
     h.nx_ = 2 * ix == g.nx;
     h.ny_ = 2 * iy == g.ny;
     h.nz_ = 2 * kz == g.nz;
+    const int px = h.nx_ ? kx : -kx, py = h.ny_ ? ky : -ky, pz = h.nz_ ? kz : -kz;
+    if (g.tri) {   // G = kx b_0 + ky b_1 + kz b_2
+        const double *B = g.Bm;
+        h.gx = kx * B[0] + ky * B[3] + kz * B[6];
+        h.gy = kx * B[1] + ky * B[4] + kz * B[7];
+        h.gz = kx * B[2] + ky * B[5] + kz * B[8];
+        h.gpx = px * B[0] + py * B[3] + pz * B[6];
+        h.gpy = px * B[1] + py * B[4] + pz * B[7];
+        h.gpz = px * B[2] + py * B[5] + pz * B[8];
+    } else {
+        h.gx = (double)kx * g.bx;
+        h.gy = (double)ky * g.by;
+        h.gz = (double)kz * g.bz;
+        h.gpx = (double)px * g.bx;
+        h.gpy = (double)py * g.by;
+        h.gpz = (double)pz * g.bz;
+    }
+    h.g2 = h.gx * h.gx + h.gy * h.gy + h.gz * h.gz;
     h.wk = (kz == 0 || h.nz_) ? 1.0 : 2.0;
     return h;
 }
@@ -431,7 +455,7 @@ __global__ void k_gstress(GridInfo g, int nat, const double *__restrict__ Z,
         if (kz > 0 && !k.nz_) {
             const double2 sp = rnyq ? acc2[h] : acc[h];
             const double lp = wd * (n.x * sp.x + n.y * sp.y);
-            const double gx = k.nx_ ? k.gx : -k.gx, gy = k.ny_ ? k.gy : -k.gy, gz = -k.gz;
+            const double gx = k.gpx, gy = k.gpy, gz = k.gpz;
             const double fp[6] = {gx * gx, gy * gy, gz * gz, gx * gy, gx * gz, gy * gz};
             for (int q = 0; q < 6; ++q) {
                 sm[q] += hw * fp[q];
@@ -487,11 +511,10 @@ __global__ void k_lpp_forces(GridInfo g, int nat, const double *__restrict__ Z,
             if (h.nz_) c.y = -c.y;
             double2 Pp = zmul(zmul(a, b), c);
             double imPp = w.x * Pp.y + w.y * Pp.x;  // Im(cn P')
-            // i G'_a P' enters with the opposite sign; G'_a = +G_a on Nyquist axes
-            double gpx = h.nx_ ? h.gx : -h.gx, gpy = h.ny_ ? h.gy : -h.gy, gpz = h.nz_ ? h.gz : -h.gz;
-            acc[0] += 0.5 * (h.gx * imP - gpx * imPp);
-            acc[1] += 0.5 * (h.gy * imP - gpy * imPp);
-            acc[2] += 0.5 * (h.gz * imP - gpz * imPp);
+            // i G'_a P' enters with the opposite sign (G' = -G off the Nyquist planes)
+            acc[0] += 0.5 * (h.gx * imP - h.gpx * imPp);
+            acc[1] += 0.5 * (h.gy * imP - h.gpy * imPp);
+            acc[2] += 0.5 * (h.gz * imP - h.gpz * imPp);
         }
     }
     block_sum<3>(acc);
@@ -511,9 +534,35 @@ __global__ void k_force_reduce(int nat, int nchunk, const double *__restrict__ p
 }
 
 // ---------------------------------------------------------------- Ewald
+// Separation R_I - R_J reduced to the cell (fractional coordinates in
+// [-1/2, 1/2]) and shifted by the lattice vector (a, b, c).
+__device__ __forceinline__ void ew_sep(const EwCell &cl, double dx, double dy, double dz, int a, int b, int c,
+                                       double &ox, double &oy, double &oz)
+{
+    if (!cl.tri) {
+        const double Lx = cl.a[0], Ly = cl.a[4], Lz = cl.a[8];
+        dx -= Lx * rint(dx / Lx);
+        dy -= Ly * rint(dy / Ly);
+        dz -= Lz * rint(dz / Lz);
+        ox = dx - a * Lx;
+        oy = dy - b * Ly;
+        oz = dz - c * Lz;
+        return;
+    }
+    const double *A = cl.a, *Ai = cl.ai;
+    double s0 = dx * Ai[0] + dy * Ai[3] + dz * Ai[6];
+    double s1 = dx * Ai[1] + dy * Ai[4] + dz * Ai[7];
+    double s2 = dx * Ai[2] + dy * Ai[5] + dz * Ai[8];
+    s0 -= rint(s0) + a;
+    s1 -= rint(s1) + b;
+    s2 -= rint(s2) + c;
+    ox = s0 * A[0] + s1 * A[3] + s2 * A[6];
+    oy = s0 * A[1] + s1 * A[4] + s2 * A[7];
+    oz = s0 * A[2] + s1 * A[5] + s2 * A[8];
+}
+
 __global__ void k_ewald_real(int nat, const double *__restrict__ R, const double *__restrict__ Z,
-                             double Lx, double Ly, double Lz, double alpha, double rcut, int3 nimg,
-                             double *eion, double *F)
+                             EwCell cl, double alpha, double rcut, int3 nimg, double *eion, double *F)
 {
     const int I = blockIdx.x;
     const int ix = 2 * nimg.x + 1, iy = 2 * nimg.y + 1, iz = 2 * nimg.z + 1;
@@ -530,13 +579,8 @@ __global__ void k_ewald_real(int nat, const double *__restrict__ R, const double
         const int b = (int)(r0 % iy) - nimg.y;
         const int c = (int)(r0 / iy) - nimg.z;
         // minimum image of R_I - R_J, then the lattice shift
-        double dx = xi - R[3 * J], dy = yi - R[3 * J + 1], dz = zi - R[3 * J + 2];
-        dx -= Lx * rint(dx / Lx);
-        dy -= Ly * rint(dy / Ly);
-        dz -= Lz * rint(dz / Lz);
-        dx -= a * Lx;
-        dy -= b * Ly;
-        dz -= c * Lz;
+        double dx, dy, dz;
+        ew_sep(cl, xi - R[3 * J], yi - R[3 * J + 1], zi - R[3 * J + 2], a, b, c, dx, dy, dz);
         double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < 1e-24 || r2 >= rcut * rcut) continue;
         double r = sqrt(r2);
@@ -562,8 +606,7 @@ __global__ void k_ewald_real(int nat, const double *__restrict__ R, const double
 // (the pair sum of Sigma_real = -(1/2 Omega) sum' g r_a r_b / r^2), rows
 // xx yy zz xy xz yz, one column per ion.  Same pair loop as k_ewald_real.
 __global__ void k_ewald_stress_real(int nat, const double *__restrict__ R, const double *__restrict__ Z,
-                                    double Lx, double Ly, double Lz, double alpha, double rcut, int3 nimg,
-                                    double *part)
+                                    EwCell cl, double alpha, double rcut, int3 nimg, double *part)
 {
     const int I = blockIdx.x;
     const int ix = 2 * nimg.x + 1, iy = 2 * nimg.y + 1, iz = 2 * nimg.z + 1;
@@ -579,13 +622,8 @@ __global__ void k_ewald_stress_real(int nat, const double *__restrict__ R, const
         r0 /= ix;
         const int b = (int)(r0 % iy) - nimg.y;
         const int c = (int)(r0 / iy) - nimg.z;
-        double dx = xi - R[3 * J], dy = yi - R[3 * J + 1], dz = zi - R[3 * J + 2];
-        dx -= Lx * rint(dx / Lx);
-        dy -= Ly * rint(dy / Ly);
-        dz -= Lz * rint(dz / Lz);
-        dx -= a * Lx;
-        dy -= b * Ly;
-        dz -= c * Lz;
+        double dx, dy, dz;
+        ew_sep(cl, xi - R[3 * J], yi - R[3 * J + 1], zi - R[3 * J + 2], a, b, c, dx, dy, dz);
         double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < 1e-24 || r2 >= rcut * rcut) continue;
         double r = sqrt(r2);
@@ -850,10 +888,10 @@ void launch_force_reduce(int nat, int nchunk, const double *part, double *F, int
     k_force_reduce<<<(3 * nat + 255) / 256, 256, 0, st>>>(nat, nchunk, part, F, accumulate);
 }
 
-void launch_ewald_real(int nat, const double *R, const double *Z, const double *L, double alpha,
+void launch_ewald_real(int nat, const double *R, const double *Z, const EwCell &cl, double alpha,
                        double rcut, int3 nimg, double *eion, double *F, cudaStream_t st)
 {
-    k_ewald_real<<<nat, 256, 0, st>>>(nat, R, Z, L[0], L[1], L[2], alpha, rcut, nimg, eion, F);
+    k_ewald_real<<<nat, 256, 0, st>>>(nat, R, Z, cl, alpha, rcut, nimg, eion, F);
 }
 
 int launch_ewald_recip(int nat, const double *R, const double *Z, int nG, const double *Gv,
@@ -875,11 +913,11 @@ int launch_gstress(const GridInfo &g, int nat, const double *Z, const double2 *p
     return g.nx * g.ny;
 }
 
-int launch_ewald_stress(int nat, const double *R, const double *Z, const double *L, double alpha, double rcut,
+int launch_ewald_stress(int nat, const double *R, const double *Z, const EwCell &cl, double alpha, double rcut,
                         int3 nimg, int nG, const double *Gv, const double *wG, const double2 *S,
                         double *preal, double *precip, cudaStream_t st)
 {
-    k_ewald_stress_real<<<nat, 256, 0, st>>>(nat, R, Z, L[0], L[1], L[2], alpha, rcut, nimg, preal);
+    k_ewald_stress_real<<<nat, 256, 0, st>>>(nat, R, Z, cl, alpha, rcut, nimg, preal);
     int b = (nG + 255) / 256;
     if (b < 1) b = 1;
     k_ewald_stress_recip<<<b, 256, 0, st>>>(nG, Gv, wG, S, alpha, precip);

@@ -95,16 +95,53 @@ struct GridInfo {
     int zth, xth;            // threads per block of the z and of the y/x passes (0: default rule)
     int dd;                  // FP64 fields: FFT and G-space arithmetic in double-float
     float bx2[2], by2[2], bz2[2], invN2[2], hr2[2];   // the same constants as double-float pairs
+    // general (triclinic) cell: tri = 1 when the lattice vectors a_j (rows of
+    // Am) are not along the axes.  G = kx b_0 + ky b_1 + kz b_2 with
+    // a_i . b_j = 2 pi delta_ij; Bm[3 j + c] = component c of b_j; fractional
+    // coordinates s = r Ainv.  (Orthorhombic: Bm diagonal = bx, by, bz.)
+    int tri;
+    double Am[9], Bm[9], Ainv[9];
+    float Bmf[9], Bm2[9][2];
 };
 
 // Derived quantities of a grid (call after setting sizes, cell and rc).
+// An orthorhombic grid needs Lx, Ly, Lz; a triclinic one (tri = 1) also Am.
 inline void grid_reciprocal(GridInfo &g)
 {
     if (g.tk <= 0) g.tk = 8;
     const double tp = 6.283185307179586477;
+    if (!g.tri) {
+        for (int k = 0; k < 9; ++k) g.Am[k] = 0.0;
+        g.Am[0] = g.Lx;
+        g.Am[4] = g.Ly;
+        g.Am[8] = g.Lz;
+    }
+    {
+        // inverse of Am by cofactors; Bm = 2 pi Ainv^T
+        const double *a = g.Am;
+        const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                           a[2] * (a[3] * a[7] - a[4] * a[6]);
+        double inv[9] = {a[4] * a[8] - a[5] * a[7], a[2] * a[7] - a[1] * a[8], a[1] * a[5] - a[2] * a[4],
+                         a[5] * a[6] - a[3] * a[8], a[0] * a[8] - a[2] * a[6], a[2] * a[3] - a[0] * a[5],
+                         a[3] * a[7] - a[4] * a[6], a[1] * a[6] - a[0] * a[7], a[0] * a[4] - a[1] * a[3]};
+        for (int k = 0; k < 9; ++k) g.Ainv[k] = inv[k] / det;
+        for (int j = 0; j < 3; ++j)
+            for (int c = 0; c < 3; ++c) g.Bm[3 * j + c] = tp * g.Ainv[3 * c + j];
+    }
     g.bx = tp / g.Lx;
     g.by = tp / g.Ly;
     g.bz = tp / g.Lz;
+    if (!g.tri) {   // exactly the per-axis spacings
+        for (int k = 0; k < 9; ++k) g.Bm[k] = 0.0;
+        g.Bm[0] = g.bx;
+        g.Bm[4] = g.by;
+        g.Bm[8] = g.bz;
+    }
+    for (int k = 0; k < 9; ++k) {
+        g.Bmf[k] = (float)g.Bm[k];
+        g.Bm2[k][0] = (float)g.Bm[k];
+        g.Bm2[k][1] = (float)(g.Bm[k] - (double)g.Bm2[k][0]);
+    }
     g.invN = 1.0 / (double)g.N;
     g.hr = 0.5 * g.rc * g.rc;
     const double dc[5] = {g.bx, g.by, g.bz, g.invN, g.hr};

@@ -413,11 +413,12 @@ class Context:
     "fp64" or "mixed"; pointwise: arithmetic of the FP64 field sets, "f32x2"
     (double-float on the FP32 units, the default) or "f64" (binary64);
     lpp: "gauss" (Gaussian ion of radius rc) or "ha" (Heine-Abarenkov,
-    Eq. (E4A), core radius rc, depth lpp_A, cutoff lpp_qc; one species)."""
+    Eq. (E4A), core radius rc, depth lpp_A, cutoff lpp_qc; one species);
+    cell: lattice vectors as rows (3x3) for a general cell, else diag(L)."""
 
     def __init__(self, L, grid, ions, Z, T_kelvin, functional="fttf", xc=True, rc=0.25,
                  precision="fp64", device=0, stream=None, pointwise="f32x2", lpp="gauss",
-                 lpp_A=6.18, lpp_qc=29.97):
+                 lpp_A=6.18, lpp_qc=29.97, cell=None):
         p = ofdft_default_params()
         p.xc = int(bool(xc))
         p.rc = float(rc)
@@ -428,8 +429,8 @@ class Context:
         p.pointwise = POINTWISE[pointwise]
         p.device = int(device)
         p.stream = stream
-        self.ctx = ofdft_setup(np.diag(np.asarray(L, dtype=np.float64)), grid, ions, Z, T_kelvin,
-                               functional, p)
+        cm = np.diag(np.asarray(L, dtype=np.float64)) if cell is None else np.asarray(cell, dtype=np.float64)
+        self.ctx = ofdft_setup(cm, grid, ions, Z, T_kelvin, functional, p)
         self.grid = tuple(int(x) for x in grid)
 
     def close(self):

@@ -46,10 +46,14 @@ def test_setup_rejects_bad_input_without_a_gpu(lib):
         with pytest.raises(ofdft.OfdftError) as e:
             ofdft.ofdft_setup(cfg_cell, grid, ions, [1.0], T, fn)
         assert e.value.status == -1
-    tri = cfg_cell.copy()
-    tri[0, 1] = 0.5
-    with pytest.raises(ofdft.OfdftError):
-        ofdft.ofdft_setup(tri, (16, 16, 16), ions, [1.0], 1e4, "fttf")
+    # general cells must be right-handed and finite (triclinic cells are accepted)
+    left = np.array([[0.0, 4.0, 0.0], [4.0, 0.0, 0.0], [0.5, 0.0, 4.0]])
+    bad = cfg_cell.copy()
+    bad[1, 0] = np.nan
+    for cell in (left, bad):
+        with pytest.raises(ofdft.OfdftError) as e:
+            ofdft.ofdft_setup(cell, (16, 16, 16), ions, [1.0], 1e4, "fttf")
+        assert e.value.status == -1
     # FP64 arithmetic selector: only OFDFT_PW_F32X2 (0) and OFDFT_PW_F64 (1)
     p = ofdft.ofdft_default_params()
     assert p.pointwise == 0
