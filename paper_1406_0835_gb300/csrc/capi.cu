@@ -467,7 +467,7 @@ ofdft_status update_ions(ofdft_ctx *c)
     launch_phases(g, c->nat, c->Rd, c->px, c->py, c->pz, st);
     launch_vext(g, c->nat, c->Zd, c->px, c->py, c->pz, (double2 *)c->f[0].vext, st);
     if (c->f[1].valid)
-        launch_convert<double, float>((g.lpp ? 4 : 2) * g.NH, (const double *)c->f[0].vext, (float *)c->f[1].vext,
+        launch_convert<double, float>(((g.lpp || g.tri) ? 4 : 2) * g.NH, (const double *)c->f[0].vext, (float *)c->f[1].vext,
                                       st);
     launch_ewald_real(c->nat, c->Rd, c->Zd, ew_cell(g), c->ew_alpha, c->ew_rcut, c->ew_nimg, c->eion, c->ewF, st);
     int nb = launch_ewald_recip(c->nat, c->Rd, c->Zd, c->nGe, c->Gv, c->wG, c->Se, c->ewpart, c->ewF, st);
@@ -871,8 +871,8 @@ template <typename T> ofdft_status alloc_fieldset(ofdft_ctx *c, FieldSet &f)
     for (void **p : fields) CK(cudaMallocAsync(p, rb, c->st));
     CK(cudaMallocAsync((void **)&f.spec, 4 * cb, c->st));
     f.spec_stride = cb / sizeof(cplx<T>);
-    // v_ext(G); the Heine-Abarenkov form appends its pressure weights
-    CK(cudaMallocAsync((void **)&f.vext, (size_t)(g.lpp ? 2 : 1) * g.NH * sizeof(cplx<T>), c->st));
+    // v_ext(G); the Heine-Abarenkov form and triclinic cells append the pressure weights
+    CK(cudaMallocAsync((void **)&f.vext, (size_t)((g.lpp || g.tri) ? 2 : 1) * g.NH * sizeof(cplx<T>), c->st));
     // temperature table; FP64 sets append its double-float split (hi, lo
     // binary32 pairs) for the double-float pointwise functional
     const std::vector<double> &tab = tfunc_table_host();

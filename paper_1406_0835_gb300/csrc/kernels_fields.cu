@@ -94,6 +94,7 @@ template <typename A> struct Gk {
     A gx, gy, gz, g2;  // G with +n/2 on Nyquist planes
     A dx, dy, dz;      // first-derivative multipliers (0 on the own-axis Nyquist plane)
     A w;               // Hermitian weight of the half spectrum (1 on kz = 0, nz/2)
+    A ig2;             // triclinic cells: (1/G^2 + 1/G'^2)/2 (see RecipB)
 };
 
 template <typename A>
@@ -126,7 +127,12 @@ template <typename A> __device__ __forceinline__ A dmul(int i, int n, A b)
 // true): G = kx b_0 + ky b_1 + kz b_2 (+n/2 on Nyquist planes), and the
 // Cartesian first-derivative multiplier D_a = sum_j kd_j (b_j)_a with each
 // integer kd_j zeroed on its own Nyquist plane (so gradient and divergence
-// stay exact adjoints).  gk: G^2 and Hermitian weight; d: D_a.
+// stay exact adjoints).  gk: G^2 and Hermitian weight; d: D_a.  In a
+// triclinic cell the Nyquist partner G' of a point (its integer indices
+// negated except those on their Nyquist plane) is not -G, so |G'| != |G|
+// there: even kernels enter as the Hermitian part of the full-box spectrum,
+// 1/G^2 -> (1/G^2 + 1/G'^2)/2 (gk's ig2), which is what the real part of
+// the full-box inverse transform gives.
 template <typename PR, bool TRI> struct RecipB;
 template <typename PR> struct RecipB<PR, false> {
     typedef typename KT<PR>::R R;
@@ -160,6 +166,13 @@ template <typename PR> struct RecipB<PR, true> {
         r.gy = kx * b[1] + ky * b[4] + kzr * b[7];
         r.gz = kx * b[2] + ky * b[5] + kzr * b[8];
         r.g2 = r.gx * r.gx + r.gy * r.gy + r.gz * r.gz;
+        const R px = (2 * ix == g.nx) ? kx : R(0) - kx, py = (2 * iy == g.ny) ? ky : R(0) - ky,
+                pz = (2 * kz == g.nz) ? kzr : R(0) - kzr;
+        const R qx = px * b[0] + py * b[3] + pz * b[6];
+        const R qy = px * b[1] + py * b[4] + pz * b[7];
+        const R qz = px * b[2] + py * b[5] + pz * b[8];
+        const R g2p = qx * qx + qy * qy + qz * qz;
+        r.ig2 = r.g2 > R(0) ? (R(1) / r.g2 + R(1) / g2p) * R(0.5) : R(0);
         r.dx = r.dy = r.dz = R(0);
         r.w = (kz == 0 || 2 * kz == g.nz) ? R(1) : R(2);
         return r;
@@ -583,7 +596,8 @@ __global__ void k_ypass(GridInfo g, FftAxis ay, typename KT<PR>::C *__restrict__
 // One G-point's share of the LPP pressure (Eq. (pressure), LPP term, at
 // fixed Omega n(G) and fractional coordinates).  Gaussian ion: 3x the share,
 // Re(n* v_ext)(1 - G^2 rc^2/2) (the caller divides by 3); Heine-Abarenkov
-// (Eq. (E4A)): Re(n* v_p) with the pressure weights v_p stored after v_ext.
+// (Eq. (E4A)) and any form in a triclinic cell: Re(n* v_p) with the
+// pressure weights v_p stored after v_ext.
 template <typename PR>
 __device__ __forceinline__ typename KT<PR>::R ploc_term(const GridInfo &g, const typename KT<PR>::C *vext,
                                                       long long vi, const typename KT<PR>::CC &nG,
@@ -592,7 +606,7 @@ __device__ __forceinline__ typename KT<PR>::R ploc_term(const GridInfo &g, const
 {
     typedef typename KT<PR>::R R;
     typedef typename KT<PR>::CC CC;
-    if (g.lpp) {
+    if (g.lpp || g.tri) {
         CC vp = ldc<PR>(vext[g.NH + vi]);
         return nG.x * vp.x + nG.y * vp.y;
     }
@@ -634,7 +648,8 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
             CC ve = ldc<PR>(vext[vi]);
             R n2 = nG.x * nG.x + nG.y * nG.y;
             R re = nG.x * ve.x + nG.y * ve.y;
-            acc[0] += k.w * n2 / k.g2;
+            if constexpr (TRI) acc[0] += k.w * n2 * k.ig2;
+            else acc[0] += k.w * n2 / k.g2;
             acc[1] += k.w * re;
             acc[2] += k.w * ploc_term<PR>(g, vext, vi, nG, re, hr, k.g2);
         }
@@ -661,7 +676,7 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
         // P_loc = sum Re(n* v_p) (ploc_term)
         part[blockIdx.x] = 0.5 * g.omega * 12.566370614359172954 * tot[0];
         part[(size_t)gridDim.x + blockIdx.x] = g.omega * tot[1];
-        part[(size_t)2 * gridDim.x + blockIdx.x] = (g.lpp ? 1.0 : 1.0 / 3.0) * tot[2];
+        part[(size_t)2 * gridDim.x + blockIdx.x] = ((g.lpp || g.tri) ? 1.0 : 1.0 / 3.0) * tot[2];
     }
 }
 
@@ -698,10 +713,13 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
         if (k.g2 > R(0)) {
             R n2 = nG.x * nG.x + nG.y * nG.y;
             R re = nG.x * ve.x + nG.y * ve.y;
-            acc[0] += k.w * n2 / k.g2;
+            if constexpr (TRI) acc[0] += k.w * n2 * k.ig2;
+            else acc[0] += k.w * n2 / k.g2;
             acc[1] += k.w * re;
             acc[2] += k.w * ploc_term<PR>(g, vext, vi, nG, re, hr, k.g2);
-            R kh = fpi / k.g2;
+            R kh;
+            if constexpr (TRI) kh = fpi * k.ig2;
+            else kh = fpi / k.g2;
             out = cmk<CC>(kh * nG.x + ve.x, kh * nG.y + ve.y);
         }
         if (nG_out != nullptr) nG_out[t.cbase[c] + r * t.rstride] = stc<PR>(nG);
@@ -718,7 +736,7 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
     if (threadIdx.x == 0) {
         part[blockIdx.x] = 0.5 * g.omega * 12.566370614359172954 * tot[0];
         part[(size_t)gridDim.x + blockIdx.x] = g.omega * tot[1];
-        part[(size_t)2 * gridDim.x + blockIdx.x] = (g.lpp ? 1.0 : 1.0 / 3.0) * tot[2];
+        part[(size_t)2 * gridDim.x + blockIdx.x] = ((g.lpp || g.tri) ? 1.0 : 1.0 / 3.0) * tot[2];
     }
 }
 
@@ -749,7 +767,9 @@ __global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restr
         if (k.g2 > R(0)) {
             CC n = ldc<PR>(nG[t.cbase[c] + r * t.rstride]);
             CC ve = ldc<PR>(vext[t.cbase[c] + r * t.rstride]);
-            R kh = fpi / k.g2;
+            R kh;
+            if constexpr (TRI) kh = fpi * k.ig2;
+            else kh = fpi / k.g2;
             out = cmk<CC>(kh * n.x + ve.x, kh * n.y + ve.y);
         }
         D[i] = out;

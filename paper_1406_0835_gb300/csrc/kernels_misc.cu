@@ -247,6 +247,13 @@ __device__ __forceinline__ double lpp_wp_ha(const GridInfo &g, double g2)
     return -4.1887902047863909846 * exp(-u6) * (B + qdB - 6.0 * u6 * B) / (g.omega * g2 * g.ha_Z);
 }
 
+// Pressure weight of either form (Gaussian ion: w (1 - G^2 rc^2/2)/3).
+__device__ __forceinline__ double lpp_wp(const GridInfo &g, double g2)
+{
+    if (g.lpp) return lpp_wp_ha(g, g2);
+    return lpp_w(g, g2) * (1.0 - 0.5 * g2 * g.rc * g.rc) * (1.0 / 3.0);
+}
+
 // Half-spectrum point (ix, iy, kz): G from the reciprocal basis, Nyquist
 // flags, Hermitian weight and the partner G' of the full box that the point
 // also stands for (-G, except that an integer index on its Nyquist plane
@@ -255,7 +262,7 @@ struct Hk {
     int ix, iy, kz;
     bool nx_, ny_, nz_;
     double gx, gy, gz, g2, wk;
-    double gpx, gpy, gpz;
+    double gpx, gpy, gpz, g2p;   // G' and |G'|^2 (= G^2 unless the cell is triclinic)
 };
 
 __device__ __forceinline__ Hk hk_at(const GridInfo &g, int ix, int iy, int kz)
@@ -287,6 +294,7 @@ __device__ __forceinline__ Hk hk_at(const GridInfo &g, int ix, int iy, int kz)
         h.gpz = (double)pz * g.bz;
     }
     h.g2 = h.gx * h.gx + h.gy * h.gy + h.gz * h.gz;
+    h.g2p = h.gpx * h.gpx + h.gpy * h.gpy + h.gpz * h.gpz;
     h.wk = (kz == 0 || h.nz_) ? 1.0 : 2.0;
     return h;
 }
@@ -304,7 +312,10 @@ __device__ __forceinline__ Hk hk_flat(const GridInfo &g, int q)
 // One block per (ix, iy) row; the row factors Z_I e^{-i(Gx X_I + Gy Y_I)} are
 // staged in shared memory in chunks of atoms, and thread kz sums over atoms.
 // The Heine-Abarenkov form also writes its pressure weights wp(G) times the
-// same sum to vext[NH + q].
+// same sum to vext[NH + q].  In a triclinic cell |G'| differs from |G| on
+// the Nyquist planes, so the stored value is the Hermitian part of the
+// full-box v, (w(G) P + w(G') P')/2, and the pressure weights (of either
+// form) go to vext[NH + q] the same way.
 __global__ void k_vext(GridInfo g, int nat, const double *__restrict__ Z,
                        const double2 *__restrict__ px, const double2 *__restrict__ py,
                        const double2 *__restrict__ pz, double2 *__restrict__ vext)
@@ -357,13 +368,22 @@ __global__ void k_vext(GridInfo g, int nat, const double *__restrict__ Z,
         const int kz = threadIdx.x + h * blockDim.x;
         if (kz >= g.K) continue;
         Hk k = hk_at(g, ix, iy, kz);
+        const size_t q = (size_t)blockIdx.x * g.K + kz;
+        if (g.tri) {
+            const double2 a1 = acc[h], a2 = (rnyq || k.nz_) ? acc2[h] : acc[h];
+            const double w1 = lpp_w(g, k.g2), w2 = lpp_w(g, k.g2p);
+            vext[q] = make_double2(0.5 * (w1 * a1.x + w2 * a2.x), 0.5 * (w1 * a1.y + w2 * a2.y));
+            const double p1 = lpp_wp(g, k.g2), p2 = lpp_wp(g, k.g2p);
+            vext[(size_t)g.NH + q] = make_double2(0.5 * (p1 * a1.x + p2 * a2.x), 0.5 * (p1 * a1.y + p2 * a2.y));
+            continue;
+        }
         const double w = lpp_w(g, k.g2);
         double2 v = acc[h];
         if (rnyq || k.nz_) v = make_double2(0.5 * (v.x + acc2[h].x), 0.5 * (v.y + acc2[h].y));
-        vext[(size_t)blockIdx.x * g.K + kz] = make_double2(w * v.x, w * v.y);
+        vext[q] = make_double2(w * v.x, w * v.y);
         if (g.lpp) {
             const double wp = lpp_wp_ha(g, k.g2);
-            vext[(size_t)g.NH + (size_t)blockIdx.x * g.K + kz] = make_double2(wp * v.x, wp * v.y);
+            vext[(size_t)g.NH + q] = make_double2(wp * v.x, wp * v.y);
         }
     }
 }
@@ -454,11 +474,13 @@ __global__ void k_gstress(GridInfo g, int nat, const double *__restrict__ Z,
         }
         if (kz > 0 && !k.nz_) {
             const double2 sp = rnyq ? acc2[h] : acc[h];
-            const double lp = wd * (n.x * sp.x + n.y * sp.y);
+            const double invp = 1.0 / k.g2p;   // |G'| = |G| unless the cell is triclinic
+            const double hwp = 12.566370614359172954 * (n.x * n.x + n.y * n.y) * invp * invp;
+            const double lp = lpp_dw(g, k.g2p) * (n.x * sp.x + n.y * sp.y);
             const double gx = k.gpx, gy = k.gpy, gz = k.gpz;
             const double fp[6] = {gx * gx, gy * gy, gz * gz, gx * gy, gx * gz, gy * gz};
             for (int q = 0; q < 6; ++q) {
-                sm[q] += hw * fp[q];
+                sm[q] += hwp * fp[q];
                 sm[6 + q] += lp * fp[q];
             }
         }
@@ -468,13 +490,14 @@ __global__ void k_gstress(GridInfo g, int nat, const double *__restrict__ Z,
         for (int q = 0; q < 12; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = sm[q];
 }
 
-// Per-point weight of the local forces: cn(G) = -Omega w_k w(G) conj(n(G)).
+// Per-point weight of the local forces: cn(G) = -Omega w_k w(G) conj(n(G));
+// in a triclinic cell without w(G), which k_lpp_forces applies at G and G'.
 template <typename T>
 __global__ void k_lpp_prep(GridInfo g, const cplx<T> *__restrict__ nG, double2 *__restrict__ cn)
 {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < (int)g.NH; q += gridDim.x * blockDim.x) {
         Hk h = hk_flat(g, q);
-        const double s = -g.omega * h.wk * lpp_w(g, h.g2);
+        const double s = -g.omega * h.wk * (g.tri ? 1.0 : lpp_w(g, h.g2));
         cplx<T> n = nG[q];
         cn[q] = make_double2(s * (double)n.x, -s * (double)n.y);
     }
@@ -501,6 +524,11 @@ __global__ void k_lpp_forces(GridInfo g, int nat, const double *__restrict__ Z,
         double2 P = zmul(zmul(a, b), c);
         double2 w = cn[q];
         double imP = w.x * P.y + w.y * P.x;        // Im(cn P)
+        double wpart = 1.0;                        // the partner's w(G') in a triclinic cell
+        if (g.tri) {
+            wpart = lpp_w(g, h.g2p);
+            imP *= lpp_w(g, h.g2);
+        }
         if (!(h.nx_ || h.ny_ || h.nz_)) {
             acc[0] += h.gx * imP;
             acc[1] += h.gy * imP;
@@ -510,7 +538,7 @@ __global__ void k_lpp_forces(GridInfo g, int nat, const double *__restrict__ Z,
             if (h.ny_) b.y = -b.y;
             if (h.nz_) c.y = -c.y;
             double2 Pp = zmul(zmul(a, b), c);
-            double imPp = w.x * Pp.y + w.y * Pp.x;  // Im(cn P')
+            double imPp = (w.x * Pp.y + w.y * Pp.x) * wpart;   // Im(cn P'), with w(G') if triclinic
             // i G'_a P' enters with the opposite sign (G' = -G off the Nyquist planes)
             acc[0] += 0.5 * (h.gx * imP - h.gpx * imPp);
             acc[1] += 0.5 * (h.gy * imP - h.gpy * imPp);
