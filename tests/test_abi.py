@@ -108,3 +108,15 @@ def test_missing_library_fails_loudly(tmp_path):
             ofdft.load(str(tmp_path / "nope.so"))
     finally:
         ofdft._lib = saved
+
+
+def test_null_contexts_are_rejected_without_a_gpu(lib):
+    """Entry points taking a context check it before any device call."""
+    sig = np.zeros(9)
+    assert lib.ofdft_stress(None, sig.ctypes.data_as(ofdft._P), None) == -1
+    u, xi = np.zeros(2), np.zeros(6)
+    n = ofdft.ctypes.c_int()
+    assert lib.ofdft_md_andersen(None, 1e4, 0.5, u.ctypes.data_as(ofdft._P),
+                                 xi.ctypes.data_as(ofdft._P), ofdft.ctypes.byref(n)) == -1
+    assert lib.ofdft_forces(None, None, None) == -1
+    assert b"NULL" in lib.ofdft_last_error(None)

@@ -156,3 +156,26 @@ def test_stress_in_a_triclinic_cell():
         Fp = _F_min(*_strained(cell0, R0, _eps(*ab, d)), "vt84f", "gauss", phi)[2]["F_tot"]
         Fm = _F_min(*_strained(cell0, R0, _eps(*ab, -d)), "vt84f", "gauss", phi)[2]["F_tot"]
         assert (Fp - Fm) / (2 * d) / V == pytest.approx(S["Sigma"][ab], rel=2e-6, abs=2e-8), ab
+
+
+def test_stress_rotates_as_a_tensor():
+    """A rigid rotation of cell and ions leaves the discrete free energy
+    unchanged (the grid lives in fractional coordinates) and rotates the
+    stress tensor: Sigma' = Q Sigma Q^T."""
+    cfg = I.config_single_point()
+    cell0 = np.diag(cfg["L"]) + np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [0.0, -0.4, 0.0]])
+    R0 = (cfg["ions"] / np.array(cfg["L"])) @ cell0
+    th = 0.37
+    Q = np.array([[np.cos(th), -np.sin(th), 0.0], [np.sin(th), np.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    Q = Q @ np.array([[1.0, 0.0, 0.0], [0.0, np.cos(0.8), -np.sin(0.8)], [0.0, np.sin(0.8), np.cos(0.8)]])
+    out = []
+    for cell, R in ((cell0, R0), (cell0 @ Q.T, R0 @ Q.T)):
+        s = O.System(None, (12, 12, 12), R, cfg["Z"], 1e5, "vt84f", cell=cell)
+        rng = np.random.default_rng(8)
+        phi = s.uniform_phi() * (1.0 + 0.1 * rng.standard_normal(s.grid.shape))
+        ev = O.evaluate(s, phi)
+        out.append((ev, O.stress(s, ev), O.forces(s, ev)))
+    (e0, s0, f0), (e1, s1, f1) = out
+    assert e1["F_tot"] == pytest.approx(e0["F_tot"], rel=1e-12)
+    np.testing.assert_allclose(s1["Sigma"], Q @ s0["Sigma"] @ Q.T, atol=1e-12 * np.max(np.abs(s0["Sigma"])))
+    np.testing.assert_allclose(f1, f0 @ Q.T, atol=1e-11 * np.max(np.abs(f0)))
