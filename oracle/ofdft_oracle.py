@@ -6,8 +6,9 @@ section; each function names the equation it follows.  Only tests/,
 It shares no code with the CUDA library and imports nothing from it.
 
 Discretisation (a reading; the paper works in the continuum): integrals are
-dV * sum over a periodic orthorhombic grid; n(G) = fftn(n)/N over the full FFT
-box with integer wave numbers k in {-n/2+1, ..., n/2}.  Even-order operators
+dV * sum over a periodic grid (orthorhombic, or a general cell through
+CellGrid); n(G) = fftn(n)/N over the full FFT box with integer wave numbers
+k in {-n/2+1, ..., n/2}.  Even-order operators
 (G^2, Hartree, local pseudopotential) use k = +n/2 on a Nyquist plane and the
 real part of the inverse transform; first derivatives i G_a are zeroed on the
 a-Nyquist plane, so gradient and divergence are exact adjoints and the
