@@ -148,7 +148,7 @@ void ofdft_default_params(ofdft_params *p);
  *              components).  Orthorhombic (off-diagonals 0, positive
  *              diagonal) or general (triclinic, right-handed: det > 0);
  *              grid point (i, j, k) sits at (i/nx) a + (j/ny) b + (k/nz) c
- *              and G = kx b* + ky b* + kz c* with the reciprocal vectors.
+ *              and G = kx a* + ky b* + kz c* with the reciprocal vectors.
  *              Otherwise OFDFT_EINVAL.  (ofdft_energy_potential_static
  *              takes orthorhombic cells only.)
  *  grid[3]     nx, ny, nz: even, factors in {2,3,5} only, 8 <= n <= 512.
@@ -366,8 +366,9 @@ void ofdft_destroy(ofdft_ctx *ctx);
  * into the library: about 2.4 MB that each GPU loading the library holds
  * until the process exits.  The call allocates no memory, on the device or
  * the host.
- *  cell[9], grid[3], nat, ions, Z, T_kelvin, functional: as ofdft_setup.
- *  xc, rc: as ofdft_params.
+ *  cell[9], grid[3], nat, ions, Z, T_kelvin, functional: as ofdft_setup,
+ *              but orthorhombic cells only (else OFDFT_EINVAL).
+ *  xc, rc: as ofdft_params (Gaussian ion only).
  *  phi_dev  device pointer, N doubles (input; not modified).
  *  v_dev    device pointer, N doubles (output potential).
  *  E        host output (may be NULL).
