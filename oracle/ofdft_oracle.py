@@ -748,6 +748,80 @@ def minimize(sys, phi0=None, gtol=1e-8, maxit=2000, theta0=0.05, ls_tol=0.1,
                          mu=mu, status=status)
 
 
+def minimize_tn(sys, phi0=None, gtol=1e-8, maxit=500, inner_max=20, eta=0.1,
+                fd_rel=1e-4, ls_tol=0.1, max_ls=20, e_tol=1e-11):
+    """Truncated-Newton minimisation of F_tot[phi^2] under int n = N_e, the
+    alternative to CG that PROFESS offers (Sec. II); the paper gives no
+    details, so this is a reading.  Each outer step solves H d = -g on the
+    tangent space (orthogonal to phi) by an inner CG truncated when
+    ||r|| <= eta ||g||, after inner_max steps, or at non-positive curvature
+    (then the last iterate, or -g at the first step).  H x is the central
+    difference of the gradient map g(psi) = 2 psi (v[psi^2] - mu) along x,
+    mu held at its current value, projected orthogonal to phi.  The step
+    then takes the CG's norm-preserving rotation and line search, starting
+    from the Newton angle ||d|| / ||phi||.  Returns (phi, ev, stats) with
+    the evaluations spent on Hessian products counted in stats."""
+    g = sys.grid
+    phi = (sys.uniform_phi() if phi0 is None else np.array(phi0, dtype=np.float64))
+    phi *= math.sqrt(sys.Ne / g.integrate(phi * phi))
+    ev = evaluate(sys, phi)
+    nevals, nhess = 1, 0
+    mu, gr, gnorm = _mu_grad(sys, phi, ev["v"])
+    it = 0
+    status = "maxit"
+
+    def proj(x):
+        return x - phi * (float(np.sum(phi * x)) / float(np.sum(phi * phi)))
+
+    while it < maxit:
+        if gnorm < gtol:
+            status = "converged"
+            break
+        b = -proj(gr)
+        x = np.zeros_like(phi)
+        r = b.copy()
+        p = r.copy()
+        rr = float(np.sum(r * r))
+        bn = math.sqrt(float(np.sum(b * b)))
+        for j in range(inner_max):
+            h = fd_rel * math.sqrt(float(np.sum(phi * phi)) / float(np.sum(p * p)))
+            gp = [2.0 * q * (evaluate(sys, q)["v"] - mu) for q in (phi + h * p, phi - h * p)]
+            nevals += 2
+            nhess += 1
+            Hp = proj((gp[0] - gp[1]) / (2.0 * h))
+            pHp = float(np.sum(p * Hp))
+            if pHp <= 0.0:
+                if j == 0:
+                    x = b
+                break
+            a = rr / pHp
+            x = x + a * p
+            r = r - a * Hp
+            rr_new = float(np.sum(r * r))
+            if math.sqrt(rr_new) <= eta * bn:
+                break
+            p = r + (rr_new / rr) * p
+            rr = rr_new
+        d = proj(x)
+        if float(np.sum(d * gr)) >= 0.0:
+            d = b
+        pp = float(np.sum(phi * phi))
+        theta1 = min(math.sqrt(float(np.sum(d * d)) / pp), 1.0)
+        dhat = d * math.sqrt(pp / float(np.sum(d * d)))
+        D0 = g.dV * float(np.sum(2.0 * phi * ev["v"] * dhat))
+        th, ev_new, phi_new, nls = _line_search(sys, phi, dhat, D0, theta1, ls_tol, max_ls,
+                                                ev["F_tot"], e_tol)
+        nevals += nls
+        if th is None:
+            status = "linesearch"
+            break
+        phi, ev = phi_new, ev_new
+        mu, gr, gnorm = _mu_grad(sys, phi, ev["v"])
+        it += 1
+    return phi, ev, dict(iterations=it, evaluations=nevals, hessian_products=nhess,
+                         gnorm=gnorm, mu=mu, status=status)
+
+
 def _line_search(sys, phi, dhat, D0, theta1, ls_tol, max_ls, E0=None, e_tol=0.0):
     """Derivative line search in theta (reading of the CG step, Sec. II).
 

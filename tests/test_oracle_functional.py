@@ -327,3 +327,17 @@ def test_andersen_collisions():
     for sel in (slice(0, None, 2), slice(1, None, 2)):
         var = np.var(st.V[sel]) * masses[sel][0] / kT
         assert abs(var - 1.0) < 0.03
+
+
+@pytest.mark.parametrize("fn", ["fttf", "sga"])
+def test_truncated_newton_reaches_the_cg_minimum(fn):
+    """The truncated-Newton alternative (Sec. II) stops at the same
+    constrained minimum as the CG: one density, one free energy."""
+    s = small_system(fn)
+    p1, e1, s1 = O.minimize(s, gtol=1e-9)
+    p2, e2, s2 = O.minimize_tn(s, gtol=1e-9)
+    assert s2["status"] == "converged" and s2["gnorm"] < 1e-9
+    assert e2["F_tot"] == pytest.approx(e1["F_tot"], rel=1e-12)
+    assert np.max(np.abs(e2["n"] - e1["n"])) < 1e-8 * np.max(e1["n"])
+    assert abs(s.grid.integrate(e2["n"]) - s.Ne) < 1e-12 * s.Ne
+    assert s2["iterations"] < s1["iterations"]       # Newton steps: fewer, dearer
