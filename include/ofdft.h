@@ -336,6 +336,23 @@ const char *ofdft_last_error(ofdft_ctx *ctx);
 ofdft_status ofdft_tfunc_eval(long long n, const double *t, double *out);
 
 /*
+ * Host-side evaluation of the double-float primitives the FP64 field
+ * kernels compute with (no GPU needed), for checks against their error
+ * bounds.  Each input is first rounded to the nearest double-float (hi =
+ * (float)x, lo = (float)(x - hi)); out[i] is the result as a binary64.
+ *   op 0  x + y         (Joldes-Muller-Popescu accurate sum)
+ *   op 1  x * y         (FMA-based product)
+ *   op 2  x / y         (binary32 quotient plus one correction)
+ *   op 3  sqrt(x)       x > 0
+ *   op 4  exp(x)        x > -87 (0 below)
+ *   op 5  e^x - 1       x <= 0
+ *   op 6  ln(x)         x > 0, normal binary32 range
+ *   op 7  x^(-1/3)      x > 0, normal binary32 range
+ * y is read for ops 0-2 only.  OFDFT_EINVAL for a bad op, count or pointer.
+ */
+ofdft_status ofdft_ffmath_eval(int op, long long count, const double *x, const double *y, double *out);
+
+/*
  * Host-side evaluation of the pointwise functional the field kernels apply
  * (no GPU needed), for checks of its arithmetic.  For each of count points
  * with density n[i] > 0 (bohr^-3) and g2[i] = |grad n|^2, at T_kelvin:

@@ -1698,6 +1698,29 @@ long long ofdft_kernel_launches(ofdft_ctx *c) { return c ? c->launches : 0; }
 
 const char *ofdft_last_error(ofdft_ctx *c) { return c ? c->err.c_str() : g_setup_error.c_str(); }
 
+ofdft_status ofdft_ffmath_eval(int op, long long count, const double *x, const double *y, double *out)
+{
+    if (op < 0 || op > 7 || count < 0) return OFDFT_EINVAL;
+    if (count > 0 && (!x || !out || (op <= 2 && !y))) return OFDFT_EINVAL;
+    for (long long i = 0; i < count; ++i) {
+        const ff::f2 a = ff::from_double(x[i]);
+        const ff::f2 b = op <= 2 ? ff::from_double(y[i]) : ff::f2(0.0f, 0.0f);
+        ff::f2 r;
+        switch (op) {
+        case 0: r = ff::add(a, b); break;
+        case 1: r = ff::mul(a, b); break;
+        case 2: r = ff::div(a, b); break;
+        case 3: r = ff::sqrt(a); break;
+        case 4: r = ff::exp(a); break;
+        case 5: r = ff::expm1_neg(a); break;
+        case 6: r = ff::log(a); break;
+        default: r = ff::rcbrt(a); break;
+        }
+        out[i] = ff::to_double(r);
+    }
+    return OFDFT_OK;
+}
+
 ofdft_status ofdft_pointwise_eval(int functional, int xc, double T_kelvin, long long count, const double *n,
                                   const double *g2, int arith, double *out, long long *n_f2)
 {

@@ -128,6 +128,7 @@ SIGNATURES = {
     "ofdft_tfunc_eval": (ctypes.c_int, [ctypes.c_longlong, _P, _P]),
     "ofdft_pointwise_eval": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
                                             _P, _P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong)]),
+    "ofdft_ffmath_eval": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, _P, _P, _P]),
     "ofdft_destroy": (None, [ctypes.c_void_p]),
     "ofdft_minimize_start": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
     "ofdft_minimize_query": (ctypes.c_int, [ctypes.c_void_p]),
@@ -306,6 +307,20 @@ def ofdft_md_step(ctx, dt_fs, T_kelvin, nsteps=1, pos=None, vel=None, tau_steps=
     _check(ctx, load().ofdft_md_step(ctx, ctypes.byref(mp), int(nsteps), _ptr(pos), _ptr(vel),
                                      _ptr(F), ctypes.byref(E), ctypes.byref(S)))
     return dict(pos=pos, vel=vel, F=F, E=E.as_dict(), stats=S.as_dict())
+
+
+FFMATH_OPS = {"add": 0, "mul": 1, "div": 2, "sqrt": 3, "exp": 4, "expm1_neg": 5, "log": 6, "rcbrt": 7}
+
+
+def ofdft_ffmath_eval(op, x, y=None):
+    """The double-float primitive `op` on the host (binary64 in and out)."""
+    x = _f64(x, (-1,))
+    y = None if y is None else _f64(y, (-1,))
+    out = np.empty_like(x)
+    st = load().ofdft_ffmath_eval(FFMATH_OPS.get(op, op), x.size, _ptr(x), _ptr(y), _ptr(out))
+    if st != 0:
+        raise OfdftError(st, "ofdft_ffmath_eval")
+    return out
 
 
 STRESS_TERMS = ("s", "xc", "H", "loc", "ion")
