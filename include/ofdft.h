@@ -392,12 +392,17 @@ void ofdft_destroy(ofdft_ctx *ctx);
  *  stream   cudaStream_t to run on, or NULL for the default stream; the call
  *           returns after the stream has finished its work.
  * Limits: each grid edge even, {2,3,5}-smooth and at most 64;
- * nx*ny*nz <= 32768; 1 <= nat <= 64.  Anything larger returns OFDFT_EINVAL.
+ * nx*ny*nz <= 32768; 1 <= nat <= 64.  Anything larger returns OFDFT_EINVAL,
+ * as do Z <= 0, non-finite positions, T or rc.
  * The first call on a device does a one-time set-up on the current device
  * (looks up the array's device address, uploads the temperature table) and
- * should come before any stream capture.  All calls share the array and it
- * keeps the last call's contents: calls that overlap on the GPU (from other
- * threads or streams) race, so serialise them.
+ * should come before any stream capture.  The set-up runs under a mutex, so
+ * first calls from several host threads are safe on the host.  It is cached
+ * for the life of the device's context: after cudaDeviceReset (or a release
+ * of the primary context) the cached address and table are stale and the
+ * path must not be called again in that process.  All calls share the array
+ * and it keeps the last call's contents: calls that overlap on the GPU (from
+ * other threads or streams) race, so serialise them.
  */
 ofdft_status ofdft_energy_potential_static(const double cell[9], const int grid[3], int nat,
                                            const double *ions, const double *Z, double T_kelvin,
@@ -410,7 +415,9 @@ ofdft_status ofdft_energy_potential_static(const double cell[9], const int grid[
  * one system (cell, ions, grid, temperature, functional, precision) and a
  * number of MD steps; requests queue in arrival order and are admitted while
  * a slot is free and the request's device footprint (ofdft_footprint) fits
- * in the memory budget.  An admitted request gets its own context and
+ * in the memory budget.  A queued request that does not fit yet may be
+ * passed by up to max_bypass later requests that do; after that nothing is
+ * admitted ahead of it until it fits.  An admitted request gets its own context and
  * stream, so requests arriving while others run overlap with them on the
  * device (continuous batching), and each keeps its density, CG state and FFT
  * tables resident until it finishes.  Contexts are independent, so a
@@ -424,6 +431,8 @@ typedef struct {
     double hbm_budget_bytes;  /* admission budget; <= 0: 90% of the device memory free at start */
     int dry_run;              /* 1: no device work, each request sleeps dry_run_ms (host tests) */
     double dry_run_ms;
+    int max_bypass;           /* >= 0: how many later requests may be admitted ahead of a queued
+                                 request that does not fit yet (0: strict arrival order) */
 } ofdft_serve_params;
 
 typedef struct {
@@ -449,7 +458,7 @@ typedef struct {
     int status;               /* ofdft_status of the request */
     ofdft_energy E;           /* after the last step */
     double P_mean;            /* mean pressure over the MD steps (or the single point) */
-    int steps_done;
+    int steps_done;           /* MD steps completed (0 if the initial minimisation failed) */
     long long evaluations;    /* energy+potential evaluations, all steps */
     double t_submit, t_admit, t_done;   /* seconds on the server clock */
     double footprint_bytes;

@@ -10,9 +10,13 @@
 // Host code reaches the array only through the address cudaGetSymbolAddress
 // returns for the current device (the symbol itself is a host-side stand-in).
 // The first call on a device does that lookup and uploads the temperature
-// table.  Every call reuses the same array; overlapping calls race.
+// table, under a mutex, so first calls from several host threads do not race
+// on the host.  Every call reuses the same array; calls that overlap on the
+// GPU race.
 #include <math.h>
 #include <string.h>
+
+#include <mutex>
 
 #include "kernels.h"
 #include "pointwise.cuh"
@@ -56,6 +60,7 @@ struct DevState {
 DevState g_dev[kMaxDevices];
 double g_tab_host[2 * kTfSize];   // host temperature table + its double-float split, filled once
 bool g_tab_ready = false;
+std::mutex g_setup_mu;            // guards g_dev, g_tab_host and g_tab_ready (locking allocates nothing)
 
 // Status only: the documented limits say what OFDFT_EINVAL means here.
 ofdft_status serr(ofdft_status s, const char *, cudaError_t = cudaSuccess) { return s; }
@@ -79,6 +84,7 @@ bool edge_ok(int n)
 ofdft_status device_setup(int dev, unsigned char **base)
 {
     if (dev < 0 || dev >= kMaxDevices) return serr(OFDFT_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_setup_mu);
     DevState &d = g_dev[dev];
     if (!d.ready) {
         void *p = nullptr;
@@ -175,7 +181,13 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     long long N = (long long)grid[0] * grid[1] * grid[2];
     if (N > kSMaxN) return serr(OFDFT_EINVAL, "static path: nx*ny*nz exceeds 32768 grid points");
     if (nat <= 0 || nat > kSMaxAtoms) return serr(OFDFT_EINVAL, "static path: nat must be in 1..64");
-    if (!(T_kelvin > 0.0) || !(rc > 0.0)) return serr(OFDFT_EINVAL, "temperature and rc must be > 0");
+    if (!(T_kelvin > 0.0) || !isfinite(T_kelvin) || !(rc > 0.0) || !isfinite(rc))
+        return serr(OFDFT_EINVAL, "temperature and rc must be finite and > 0");
+    for (int i = 0; i < nat; ++i) {   // the per-ion checks of ofdft_setup
+        if (!(Z[i] > 0.0) || !isfinite(Z[i])) return serr(OFDFT_EINVAL, "ion charges must be finite and > 0");
+        for (int k = 0; k < 3; ++k)
+            if (!isfinite(ions[3 * i + k])) return serr(OFDFT_EINVAL, "ion positions must be finite");
+    }
     FuncParams fp = functional_params(functional);
     if (fp.kind < 0) return serr(OFDFT_EINVAL, "unknown functional");
     int dev = 0;

@@ -2,8 +2,10 @@
 // ofdft_serve_*).
 //
 // Requests queue in arrival order.  A pool of worker threads (one per slot)
-// admits the request at the head of the queue as soon as a slot is free and
-// its device footprint fits in what the memory budget has left; the admitted
+// admits the first queued request whose device footprint fits in what the
+// memory budget has left as soon as a slot is free; a request that does not
+// fit yet may be passed by at most max_bypass later ones, after which
+// nothing is admitted ahead of it (so it cannot starve).  The admitted
 // request gets its own context and stream and runs its MD steps there, so
 // requests that arrive while others run overlap with them on the device.
 // Contexts share nothing, which makes each result independent of the mix.
@@ -30,6 +32,7 @@ struct Pending {
     std::vector<double> ions, Z, vel;
     double footprint;
     double t_submit;
+    int bypassed = 0;     // later requests admitted ahead of this one
 };
 
 }  // namespace
@@ -98,18 +101,34 @@ ofdft_result run_request(ofdft_server *s, Pending *q)
     st = ofdft_md_step(c, &mp, 0, nullptr, q->vel.empty() ? nullptr : q->vel.data(), nullptr, &E, &stats);
     res.evaluations += stats.evaluations;
     double psum = 0.0;
-    int k = 0;
-    for (; st == OFDFT_OK && k < r.md_steps; ++k) {
+    int done = 0;         // MD steps completed (0 when the initial minimisation failed)
+    while (st == OFDFT_OK && done < r.md_steps) {
         st = ofdft_md_step(c, &mp, 1, nullptr, nullptr, nullptr, &E, &stats);
         res.evaluations += stats.evaluations;
-        if (st == OFDFT_OK) psum += E.P;
+        if (st == OFDFT_OK) {
+            psum += E.P;
+            ++done;
+        }
     }
     res.status = st;
     res.E = E;
-    res.steps_done = st == OFDFT_OK ? k : k - 1;
-    res.P_mean = r.md_steps > 0 ? (res.steps_done > 0 ? psum / res.steps_done : 0.0) : E.P;
+    res.steps_done = done;
+    res.P_mean = r.md_steps > 0 ? (done > 0 ? psum / done : 0.0) : E.P;
     ofdft_destroy(c);
     return res;
+}
+
+// Queue position of the request to admit next, or -1: the first one that
+// fits, unless an earlier one that does not fit has been passed max_bypass
+// times already (with max_bypass 0 only the head is ever admitted).
+long pick(const ofdft_server *s)
+{
+    for (size_t j = 0; j < s->queue.size(); ++j) {
+        const Pending *q = s->queue[j];
+        if (s->used + q->footprint <= s->budget) return (long)j;
+        if (q->bypassed >= s->p.max_bypass) return -1;
+    }
+    return -1;
 }
 
 void worker(ofdft_server *s)
@@ -117,13 +136,16 @@ void worker(ofdft_server *s)
     if (!s->p.dry_run) cudaSetDevice(s->p.device);
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
-        s->cv.wait(lk, [s] {
+        long j = -1;
+        s->cv.wait(lk, [s, &j] {
             if (s->queue.empty()) return s->stopping;
-            return s->used + s->queue.front()->footprint <= s->budget;
+            j = pick(s);
+            return j >= 0;
         });
         if (s->queue.empty()) break;          // stopping and nothing left
-        Pending *q = s->queue.front();
-        s->queue.pop_front();
+        Pending *q = s->queue[j];
+        for (long i = 0; i < j; ++i) s->queue[i]->bypassed += 1;
+        s->queue.erase(s->queue.begin() + j);
         s->used += q->footprint;
         s->running += 1;
         if (s->used > s->peak_used) s->peak_used = s->used;
@@ -149,7 +171,7 @@ extern "C" {
 
 ofdft_status ofdft_serve_start(const ofdft_serve_params *p, ofdft_server **out)
 {
-    if (!p || !out || p->max_slots < 1) return OFDFT_EINVAL;
+    if (!p || !out || p->max_slots < 1 || p->max_bypass < 0) return OFDFT_EINVAL;
     *out = nullptr;
     ofdft_server *s = new (std::nothrow) ofdft_server();
     if (!s) return OFDFT_ENOMEM;

@@ -66,7 +66,7 @@ class MDParams(ctypes.Structure):
 class ServeParams(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_slots", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_double), ("dry_run", ctypes.c_int),
-                ("dry_run_ms", ctypes.c_double)]
+                ("dry_run_ms", ctypes.c_double), ("max_bypass", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -316,6 +316,8 @@ def ofdft_ffmath_eval(op, x, y=None):
     """The double-float primitive `op` on the host (binary64 in and out)."""
     x = _f64(x, (-1,))
     y = None if y is None else _f64(y, (-1,))
+    if FFMATH_OPS.get(op, op) in (0, 1, 2) and (y is None or y.size != x.size):
+        raise ValueError("ofdft_ffmath_eval: binary operations need y with x's length")
     out = np.empty_like(x)
     st = load().ofdft_ffmath_eval(FFMATH_OPS.get(op, op), x.size, _ptr(x), _ptr(y), _ptr(out))
     if st != 0:
@@ -540,11 +542,12 @@ def ofdft_energy_potential_static(cell, grid, ions, Z, T_kelvin, functional, phi
 # ------------------------------------------------------------------ serving
 class Server:
     """Request loop of the serving form (ofdft_serve_*): submit systems with
-    a number of MD steps, poll or drain for results."""
+    a number of MD steps, poll or drain for results.  max_bypass: how many
+    later requests may be admitted ahead of one that does not fit yet."""
 
-    def __init__(self, max_slots=4, hbm_budget_bytes=0.0, device=0, dry_run_ms=None):
+    def __init__(self, max_slots=4, hbm_budget_bytes=0.0, device=0, dry_run_ms=None, max_bypass=8):
         p = ServeParams(int(device), int(max_slots), float(hbm_budget_bytes),
-                        0 if dry_run_ms is None else 1, float(dry_run_ms or 0.0))
+                        0 if dry_run_ms is None else 1, float(dry_run_ms or 0.0), int(max_bypass))
         h = ctypes.c_void_p()
         st = load().ofdft_serve_start(ctypes.byref(p), ctypes.byref(h))
         if st != 0:

@@ -81,3 +81,15 @@ def test_exp_expm1_log():
     assert ofdft.ofdft_ffmath_eval("exp", np.array([-90.0]))[0] == 0.0
     with pytest.raises(ofdft.OfdftError):
         ofdft.ofdft_ffmath_eval(9, np.array([1.0]))
+
+
+def test_binary_operations_check_the_second_operand():
+    """add, mul and div read y[i] for every x[i]: a missing or shorter y is
+    refused before the library is called."""
+    x = np.linspace(1.0, 2.0, 8)
+    for op in ("add", "mul", "div"):
+        with pytest.raises(ValueError):
+            ofdft.ofdft_ffmath_eval(op, x, x[:3])
+        with pytest.raises(ValueError):
+            ofdft.ofdft_ffmath_eval(op, x)
+    assert ofdft.ofdft_ffmath_eval("sqrt", x).shape == x.shape

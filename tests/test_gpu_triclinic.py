@@ -63,3 +63,85 @@ def test_minimisation_forces_stress_match_oracle():
     assert rel(P, ev_o["P"]) < 1e-8
     for k in ("s", "xc", "H", "loc", "ion", "Sigma"):
         np.testing.assert_allclose(S[k], S_o[k], rtol=0, atol=1e-8 * np.max(np.abs(S_o[k])), err_msg=k)
+
+
+@pytest.mark.parametrize("gtol", [1e-10, ofdft.MIXED_FORM_GTOL])
+def test_mixed_precision_in_sheared_cell(gtol):
+    """Mixed precision (FP32 field kernels, FP64 reductions and polish) in a
+    general cell: at gtol 1e-10 the FP64 stage reaches the oracle's minimum
+    to the FP64 bars; at the batched form's tolerance the stated per-result
+    bars hold (1e-6 Ha/atom, 1e-4 Ha/bohr, 1e-3 relative in P)."""
+    cfg, cell, ions = sheared()
+    grid = (24, 20, 30)
+    so = O.System(None, grid, ions, cfg["Z"], cfg["T"], "vt84f", cell=cell)
+    phi_o, ev_o, _ = O.minimize(so, gtol=1e-10)
+    F_o = O.forces(so, ev_o)
+    with ofdft.Context(None, grid, ions, cfg["Z"], cfg["T"], "vt84f", cell=cell, precision="mixed") as ctx:
+        E, st = ctx.minimize(gtol=gtol, maxit=20000)
+        assert st["status"] == 0 and st["evaluations_lo"] > 0
+        n = ctx.density()
+        F, P = ctx.forces()
+    if gtol <= 1e-10:
+        assert rel(E["F_tot"], ev_o["F_tot"]) < 1e-10
+        assert np.max(np.abs(n - ev_o["n"])) <= 1e-9 * np.max(ev_o["n"])
+        np.testing.assert_allclose(F, F_o, rtol=0, atol=1e-8)
+        assert rel(P, ev_o["P"]) < 1e-8
+    else:
+        assert abs(E["F_tot"] - ev_o["F_tot"]) / len(cfg["Z"]) < 1e-6
+        assert np.max(np.abs(F - F_o)) < 1e-4
+        assert abs(P - ev_o["P"]) <= 1e-3 * abs(ev_o["P"])
+
+
+def test_md_steps_in_sheared_cell():
+    """Three velocity-Verlet + Nose-Hoover steps in the sheared cell against
+    the oracle's integrator (FP64 bars of the orthorhombic MD test)."""
+    cfg, cell, ions = sheared()
+    d = inputs.hydrogen(8, 1.0, 3.125e4, 16, seed=2, functional="sga", vel_seed=3)
+    grid = (16, 16, 16)
+    so = O.System(None, grid, ions, cfg["Z"], d["T"], "sga", cell=cell)
+    st = O.MDState(ions, d["vel"], d["masses"], d["T"], dt_fs=0.2)
+    O.md_prepare(so, st, gtol=1e-10)
+    with ofdft.Context(None, grid, ions, cfg["Z"], d["T"], "sga", cell=cell) as ctx:
+        out = ctx.md_step(0.2, d["T"], nsteps=0, pos=ions, vel=d["vel"], gtol=1e-10)
+        np.testing.assert_allclose(out["F"], st.F, rtol=0, atol=1e-8)
+        for _ in range(3):
+            O.md_step(so, st, gtol=1e-10)
+            out = ctx.md_step(0.2, d["T"], nsteps=1, gtol=1e-10)
+        pos, vel = ctx.md_state()
+        np.testing.assert_allclose(pos, st.R, rtol=0, atol=1e-10)
+        np.testing.assert_allclose(vel, st.V, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(out["F"], st.F, rtol=0, atol=1e-8)
+        assert rel(out["E"]["F_tot"], st.ev["F_tot"]) < 1e-10
+        assert rel(ctx.md_conserved(), O.md_conserved(st)) < 1e-10
+
+
+def test_heine_abarenkov_lpp_in_sheared_cell():
+    """Eq. (E4A) pseudopotential in the general cell: one evaluation at a
+    random density, then the minimised density, forces, pressure and stress."""
+    cfg, cell, ions = sheared()
+    grid = (20, 20, 20)
+    so = O.System(None, grid, ions, cfg["Z"], cfg["T"], "sga", cell=cell, lpp="ha")
+    rng = np.random.default_rng(31)
+    phi = so.uniform_phi() * (1.0 + 0.1 * rng.standard_normal(grid))
+    ev = O.evaluate(so, phi)
+    phi_o, ev_o, _ = O.minimize(so, gtol=1e-10)
+    S_o = O.stress(so, ev_o)
+    with ofdft.Context(None, grid, ions, cfg["Z"], cfg["T"], "sga", cell=cell, lpp="ha") as ctx:
+        E, v = ctx.energy_potential(phi)
+        for k in ("F_tot", "F_s", "E_H", "E_loc", "F_xc", "E_ion"):
+            assert abs(E[k] - ev[k]) <= 1e-10 * abs(ev["F_tot"]), (k, E[k], ev[k])
+        for k in ("P", "P_loc"):
+            assert abs(E[k] - ev[k]) <= 1e-9 * abs(ev["P"]), (k, E[k], ev[k])
+        assert np.max(np.abs(v - ev["v"])) <= 1e-9 * np.max(np.abs(ev["v"]))
+        ctx.set_phi(None)
+        E, st = ctx.minimize(gtol=1e-10)
+        assert st["status"] == 0
+        assert rel(E["F_tot"], ev_o["F_tot"]) < 1e-10
+        n = ctx.density()
+        assert np.max(np.abs(n - ev_o["n"])) <= 1e-9 * np.max(ev_o["n"])
+        F, P = ctx.forces()
+        S = ctx.stress()
+    np.testing.assert_allclose(F, O.forces(so, ev_o), rtol=0, atol=1e-8)
+    assert rel(P, ev_o["P"]) < 1e-8
+    for k in ("s", "xc", "H", "loc", "ion", "Sigma"):
+        np.testing.assert_allclose(S[k], S_o[k], rtol=0, atol=1e-8 * np.max(np.abs(S_o[k])), err_msg=k)

@@ -35,7 +35,7 @@ def test_admission_order_budget_and_slots():
     small = ofdft.ofdft_footprint((32, 32, 32), 8, "fp64")
     big = ofdft.ofdft_footprint((64, 64, 64), 8, "fp64")
     budget = big + 1.5 * small          # the big one and one small, never two small beside it
-    with ofdft.Server(max_slots=3, hbm_budget_bytes=budget, dry_run_ms=60) as s:
+    with ofdft.Server(max_slots=3, hbm_budget_bytes=budget, dry_run_ms=60, max_bypass=0) as s:
         ids = [_req(s, (64, 64, 64)), _req(s, (32, 32, 32)), _req(s, (32, 32, 32)),
                _req(s, (32, 32, 32)), _req(s, (64, 64, 64))]
         assert s.poll(ids[-1]) is None or s.poll(ids[-1])["status"] == 0
@@ -51,6 +51,27 @@ def test_admission_order_budget_and_slots():
         assert r["t_submit"] <= r["t_admit"] < r["t_done"]
     # the last big request had to wait for the memory the others held
     assert res[4]["t_admit"] >= max(r["t_done"] for r in res[:3]) - 1e-3
+
+
+def test_smaller_requests_pass_a_waiting_one_a_bounded_number_of_times():
+    """A big request that does not fit yet is passed by later small ones
+    that do, at most max_bypass of them; the next small one waits behind it,
+    so the big one is not starved."""
+    small = ofdft.ofdft_footprint((32, 32, 32), 8, "fp64")
+    big = ofdft.ofdft_footprint((96, 96, 96), 8, "fp64")
+    budget = big + 3.5 * small        # beside a big one: three small (memory), never a second big
+    assert 2 * big > budget
+    with ofdft.Server(max_slots=5, hbm_budget_bytes=budget, dry_run_ms=150, max_bypass=2) as s:
+        ids = [_req(s, (96, 96, 96)), _req(s, (96, 96, 96)), _req(s, (32, 32, 32)),
+               _req(s, (32, 32, 32)), _req(s, (32, 32, 32))]
+        s.drain(timeout_s=30.0)
+        A, B, C, D, E = [s.poll(i) for i in ids]
+        peak_bytes, _ = s.peaks()
+    assert all(r["status"] == 0 for r in (A, B, C, D, E))
+    assert peak_bytes <= budget
+    assert C["t_admit"] < B["t_admit"] and D["t_admit"] < B["t_admit"]   # passed the waiting big one
+    assert B["t_admit"] >= A["t_done"] - 1e-3                           # it waited for memory
+    assert E["t_admit"] >= B["t_admit"]                                 # the third could not pass it
 
 
 def test_oversize_and_bad_requests_are_refused():
@@ -69,3 +90,5 @@ def test_oversize_and_bad_requests_are_refused():
 def test_dry_run_needs_a_budget():
     with pytest.raises(ofdft.OfdftError):
         ofdft.Server(max_slots=1, hbm_budget_bytes=0.0, dry_run_ms=1)
+    with pytest.raises(ofdft.OfdftError):
+        ofdft.Server(max_slots=1, hbm_budget_bytes=1e9, dry_run_ms=1, max_bypass=-1)

@@ -43,3 +43,42 @@ def test_static_entry_point_matches_context_path():
         ofdft.ofdft_energy_potential_static(np.diag(cfg["L"]), (64, 64, 64), cfg["ions"], cfg["Z"],
                                             cfg["T"], "fttf", big.data_ptr(), big.data_ptr())
     assert e.value.status == -1
+
+
+def test_static_entry_point_at_its_limits():
+    """The largest systems the fixed scratch holds (an edge of 64, 32768
+    points, 64 ions) match the context path, and each input the path does
+    not take is rejected before any device work: 65 ions, a sheared cell,
+    a non-positive charge, a non-finite position."""
+    torch = pytest.importorskip("torch")
+    import __graft_entry__
+    __graft_entry__.build()
+    d = inputs.hydrogen(64, 1.0, 5.0e4, 8, seed=17, functional="vt84f")
+    for fn, grid in [("vt84f", (64, 64, 8)), ("fttf", (8, 64, 64)), ("sga", (32, 32, 32))]:
+        N = int(np.prod(grid))
+        rng = np.random.default_rng(N + len(fn))
+        phi = np.sqrt(64.0 / np.prod(d["L"])) * (1.0 + 0.1 * rng.standard_normal(N))
+        with ofdft.Context(d["L"], grid, d["ions"], d["Z"], d["T"], fn) as ctx:
+            E_ref, v_ref = ctx.energy_potential(phi)
+        phi_d = torch.tensor(phi, dtype=torch.float64, device="cuda")
+        v_d = torch.full((N,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        E = ofdft.ofdft_energy_potential_static(np.diag(d["L"]), grid, d["ions"], d["Z"], d["T"], fn,
+                                                phi_d.data_ptr(), v_d.data_ptr())
+        v = v_d.cpu().numpy().reshape(grid)
+        for k in ("F_tot", "F_s", "E_H", "E_loc", "F_xc", "E_ion", "P"):
+            assert abs(E[k] - E_ref[k]) <= 1e-10 * max(abs(E_ref["F_tot"]), 1.0), (fn, grid, k)
+        assert np.max(np.abs(v - v_ref)) <= 1e-9 * np.max(np.abs(v_ref)), (fn, grid)
+    buf = torch.zeros(16 ** 3, dtype=torch.float64, device="cuda")
+    ions65 = np.vstack([d["ions"], d["ions"][:1] + 0.3])
+    sheared = np.diag(d["L"]) + np.array([[0.0, 0.0, 0.0], [0.4, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    bad_Z = d["Z"].copy()
+    bad_Z[3] = 0.0
+    bad_pos = d["ions"].copy()
+    bad_pos[5, 1] = np.nan
+    for cell, ions, Z in [(np.diag(d["L"]), ions65, np.ones(65)), (sheared, d["ions"], d["Z"]),
+                          (np.diag(d["L"]), d["ions"], bad_Z), (np.diag(d["L"]), bad_pos, d["Z"])]:
+        with pytest.raises(ofdft.OfdftError) as e:
+            ofdft.ofdft_energy_potential_static(cell, (16, 16, 16), ions, Z, d["T"], "fttf",
+                                                buf.data_ptr(), buf.data_ptr())
+        assert e.value.status == -1
