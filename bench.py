@@ -26,11 +26,26 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# CG evaluations (energy + potential) per step, measured on the GPU path
-# (bench.py reports evals_per_step); converts the oracle's evaluations/s to
-# MD steps/s in the reference arm, which runs without a GPU.
-EVALS_PER_STEP = {"md-vt84f-96": 643.0, "md-sga-96": 339.0, "md-vt84f-96-mixed": 700.0,
-                  "solve-vt84f-128": 539.0, "solve-vt84f-128-mixed": 630.0, "eval-vt84f-128": 1.0}
+# Energy + potential evaluations per step of the FP64 CG (the same
+# algorithm, decision for decision, in the oracle and on the GPU), as the GPU
+# arm of this script measures them on each workload (its evals_per_step: 622
+# per MD step of md-vt84f-96 in the driver's 20-step run, 334 for md-sga-96,
+# 548 per solve of solve-vt84f-128).  The reference arm runs without the
+# GPU path, so it converts the oracle's measured evaluations/s with these;
+# mixed workloads use the FP64 count, since the oracle is FP64 throughout.
+EVALS_PER_STEP = {"md-vt84f-96": 622.0, "md-sga-96": 334.0, "md-vt84f-96-mixed": 622.0,
+                  "solve-vt84f-128": 548.0, "solve-vt84f-128-mixed": 548.0, "eval-vt84f-128": 1.0}
+
+# Arithmetic of each precision form.  FP64 contexts keep every field in
+# binary64 in HBM and compute FFTs, G-space terms and the pointwise
+# functional in double-float (two binary32 words, about 48 significant
+# bits) on the FP32 units; reductions, CG scalars, Ewald, forces and the
+# integrator run in binary64.  Mixed contexts run the field kernels in
+# binary32 (per-thread partial sums in double-float, binary64 above) and
+# finish in an FP64 context's arithmetic.
+DTYPE = {"fp64": "f64 (double-float compute, binary64 storage and reductions)",
+         "mixed": "f32 fields + f64 (f32 FFTs/pointwise, f64 reductions, double-float FP64 polish)",
+         "binary64": "f64 (binary64 throughout)"}
 
 WORKLOADS = {
     "md-vt84f-96": dict(kind="md", functional="vt84f", grid=96, precision="fp64"),
@@ -86,6 +101,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ref", action="store_true",
                     help="batch/serve workloads: skip the sequential FP64 reference run")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="MD workloads: skip the sub-records (binary64 and mixed-precision MD, "
+                         "batched form, serving form) that the default line carries")
     ap.add_argument("--maxit", type=int, default=20000,
                     help="CG iteration cap per solve (solve workloads; a small cap makes a short "
                          "profiling case, whose solves then stop unconverged)")
@@ -238,7 +256,7 @@ def run_eval(args, rank, world):
     res = {"metric": "functional+grad evals/s", "value": world * args.steps / t,
            "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": DTYPE[wl["precision"]], "data": "synthetic",
            "config": {"workload": args.workload, "atoms": len(cfg["Z"]), "grid": list(cfg["grid"]),
                       "functional": wl["functional"], "T_K": cfg["T"], "rho_gcc": 4.0,
                       "l2": "flushed (256 MB write) before every timed step"}}
@@ -391,7 +409,7 @@ def run_ours(args, rank, world):
     res = {"metric": "MD steps/s", "value": value, "unit": "MD steps/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if wl["precision"] == "fp64" else "f32+f64",
+           "dtype": DTYPE[wl["precision"]],
            "data": "synthetic (seeded hydrogen, random positions and Maxwell-Boltzmann velocities)",
            "config": {"workload": args.workload, "atoms": len(cfg["Z"]), "grid": list(cfg["grid"]),
                       "functional": wl["functional"], "xc": "PZ81", "T_K": mdT, "rho_gcc": 1.0,
@@ -402,7 +420,65 @@ def run_ours(args, rank, world):
            "cg_iterations_per_step": iters / args.steps,
            "gpu_launches": launches, "clocks": clk, "e2e": e2e,
            "roofline": roofline_entry(dominant, cfg["grid"], kms, kcount, clk, read_peaks(), wl["precision"])}
+    if world == 1 and not args.no_extra:
+        res["extra"] = extra_records(args, cfg, wl, dev, stream)
     return res, evals / args.steps
+
+
+def md_rate(cfg, wl, dev, stream, steps, warmup, precision, pointwise="f32x2"):
+    """MD steps/s of another arithmetic on the same workload: a fresh
+    context, step 0 and `warmup` steps untimed, then `steps` steps timed with
+    CUDA events on the context's stream (L2 flushed before each)."""
+    import torch
+    from paper_1406_0835_gb300 import ofdft
+    c = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
+                      precision=precision, pointwise=pointwise, device=dev, stream=stream.cuda_stream)
+    c.autotune(reps=3)
+    c.md_step(0.2, cfg["T"], nsteps=0, pos=cfg["ions"], vel=cfg["vel"])
+    for _ in range(warmup):
+        c.md_step(0.2, cfg["T"], nsteps=1)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t, evals, evals_lo = 0.0, 0, 0
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = c.md_step(0.2, cfg["T"], nsteps=1)
+            e1.record(stream)
+            e1.synchronize()
+            t += e0.elapsed_time(e1) / 1e3
+            evals += out["stats"]["evaluations"]
+            evals_lo += out["stats"]["evaluations_lo"]
+    E = out["E"]
+    c.close()
+    return {"value": steps / t, "unit": "MD steps/s", "steps": steps, "warmup": warmup,
+            "ms_per_step": 1e3 * t / steps, "evals_per_step": evals / steps,
+            "fp32_evals_per_step": evals_lo / steps, "dtype": DTYPE[precision if pointwise != "f64" else "binary64"],
+            "F_tot_last": E["F_tot"]}
+
+
+def extra_records(args, cfg, wl, dev, stream):
+    """Sub-records of the default line: the same MD workload in binary64
+    and in mixed precision, the batched form and the serving form, each with
+    its plain-FP64 comparator, so that one run carries every part of the
+    metric (MD steps/s, evals/s, batched solves/s, served p50/p99)."""
+    import copy
+    out = {}
+    out["binary64_md"] = md_rate(cfg, wl, dev, stream, steps=3, warmup=1, precision="fp64", pointwise="f64")
+    if wl["precision"] == "fp64":
+        out["mixed_md"] = md_rate(cfg, wl, dev, stream, steps=5, warmup=2, precision="mixed")
+    for name, fn in (("batch-64-mixed", run_batch), ("serve-eos-mixed", run_serve)):
+        a = copy.copy(args)
+        a.workload, a.steps, a.warmup, a.no_ref = name, 2, 1, False
+        r, _ = fn(a, 0, 1)
+        keep = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "converged",
+                "completed", "evals_per_step", "fp32_evals_per_step", "p50_latency_s", "p99_latency_s",
+                "peak_running", "reference_fp64", "clocks", "gpu_launches")
+        out[name] = {k: r[k] for k in keep if k in r}
+    return out
 
 
 def run_solve(args, rank, world):
@@ -477,7 +553,7 @@ def run_solve(args, rank, world):
     res = {"metric": "single-point solves/s", "value": world * args.steps / t_total, "unit": "solves/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if wl["precision"] == "fp64" else "f32+f64",
+           "vs_baseline": None, "dtype": DTYPE[wl["precision"]],
            "data": "synthetic (seeded hydrogen, random positions)",
            "config": {"workload": args.workload, "atoms": len(cfg["Z"]), "grid": list(cfg["grid"]),
                       "functional": wl["functional"], "xc": "PZ81", "T_K": cfg["T"], "rho_gcc": 4.0,
@@ -583,7 +659,7 @@ def run_batch(args, rank, world):
     res = {"metric": "batched solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if wl["precision"] == "fp64" else "f32+f64",
+           "dtype": DTYPE[wl["precision"]],
            "data": "synthetic (seeded hydrogen instances)",
            "config": {"workload": args.workload, "instances": wl["count"], "grid_edges": grids,
                       "atoms": [min(len(d["Z"]) for d in systems), max(len(d["Z"]) for d in systems)],
@@ -655,7 +731,7 @@ def run_serve(args, rank, world):
     out = {"metric": "served requests/s", "value": value, "unit": "requests/s", "n_gpus": world,
            "steps": len(stream), "warmup": 1, "ms_per_step": 1e3 * span / len(stream),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32+f64" if wl["precision"] == "mixed" else "f64",
+           "dtype": DTYPE[wl["precision"]],
            "data": "synthetic (seeded Poisson EOS request stream)",
            "config": {"workload": args.workload, "requests": len(stream), "rate_per_s": 50.0,
                       "md_steps": wl["md_steps"], "slots": 8, "grid_max": 96,
@@ -668,44 +744,75 @@ def run_serve(args, rank, world):
     return out, 1.0
 
 
-def cpu_baseline(args, evals_per_step, budget_s=15.0):
-    """The oracle timed on a bounded sample: full-size energy + potential
-    evaluations for about budget_s seconds, converted to the workload's
-    metric with the CG evaluations per step (MD step or solve)."""
-    import numpy as np
+def oracle_system(args):
+    """The oracle's System for the workload, and its metric unit."""
     import oracle as O
     from paper_1406_0835_gb300 import inputs
     wl = WORKLOADS[args.workload]
     if wl["kind"] == "solve":
-        cfg = inputs.config_mixed(wl["T"], grid=wl["grid"])
-        unit = "solves/s"
+        cfg, unit = inputs.config_mixed(wl["T"], grid=wl["grid"]), "solves/s"
     elif wl["kind"] == "eval":
-        cfg = inputs.config_mixed(2.5e5, grid=wl["grid"])
-        unit = "evals/s"
+        cfg, unit = inputs.config_mixed(2.5e5, grid=wl["grid"]), "evals/s"
     else:
-        cfg = inputs.config_md(wl["functional"], grid=wl["grid"])
-        unit = "MD steps/s"
+        cfg, unit = inputs.config_md(wl["functional"], grid=wl["grid"]), "MD steps/s"
     so = O.System(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"])
-    phi = so.uniform_phi() * (1.0 + 0.05 * np.random.default_rng(1).standard_normal(cfg["grid"]))
-    O.evaluate(so, phi)
-    n = 0
+    return so, cfg, unit
+
+
+def oracle_sample(args, so, phi, evals_per_step, budget_s):
+    """One bounded sample of the oracle's own CG minimiser on the full-size
+    workload: CG iterations (each one energy + potential evaluation per
+    line-search trial) continued from phi until budget_s seconds have passed.
+    Returns the new phi and the sample's record; the sample covers
+    evaluations / evals_per_step of a step of the workload.  cores is the
+    process CPU time over the wall time (the oracle's FD integrals run on
+    OpenMP threads, its FFTs on one)."""
+    import resource
+    import oracle as O
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
+    n = iters = 0
     while True:
-        O.evaluate(so, phi)
-        n += 1
+        if args.workload.startswith("eval"):
+            O.evaluate(so, phi)
+            n += 1
+        else:
+            phi, _, st = O.minimize(so, phi, gtol=1e-8, maxit=1)
+            n += st["evaluations"]
+            iters += max(st["iterations"], 1)
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    eps = n / dt
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": eps / evals_per_step, "unit": unit, "cores": cores, "kind": "oracle",
-            "sample": "%d full-size (%s) energy+potential evaluations in %.1f s = %.3f evals/s, "
-                      "divided by %.1f evaluations per step" % (n, "x".join(map(str, cfg["grid"])),
-                                                                   dt, eps, evals_per_step)}
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    return phi, {"evaluations": n, "iterations": iters, "seconds": dt, "fraction": n / evals_per_step,
+                 "cores": cpu / dt}
+
+
+def cpu_baseline(args, evals_per_step, budget_s=15.0):
+    """The oracle timed on a bounded sample of the workload (its own CG at
+    full size for about budget_s seconds), converted to the workload's
+    metric with the CG evaluations per step."""
+    so, cfg, unit = oracle_system(args)
+    import oracle as O
+    phi = so.uniform_phi()
+    O.evaluate(so, phi)                                             # warm-up (threads, caches)
+    phi, rec = oracle_sample(args, so, phi, evals_per_step, budget_s)
+    eps = rec["evaluations"] / rec["seconds"]
+    return {"value": eps / evals_per_step, "unit": unit, "cores": int(round(rec["cores"])),
+            "cores_measured": rec["cores"], "kind": "oracle",
+            "sample": "the oracle's CG on the full-size (%s) workload: %d iterations, %d energy+potential "
+                      "evaluations in %.1f s = %.3f evals/s, over %.1f evaluations per step; cores = "
+                      "process CPU time / wall time" % ("x".join(map(str, cfg["grid"])), rec["iterations"],
+                                                        rec["evaluations"], rec["seconds"], eps, evals_per_step)}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on bounded samples of the workload."""
+    """Reference arm: the FP64 CPU oracle.  Each step is a bounded sample of
+    the workload, about 4 s of the oracle's own CG at full size (a fraction
+    of one MD step or solve: its evaluations over the evaluations a step
+    takes); value = the steps' fractions over their measured time, so
+    ms_per_step is the time actually timed per sample."""
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -714,25 +821,34 @@ def run_reference(args):
         return {"impl": "reference", "unavailable": "the oracle is timed on the md, solve and eval "
                 "workloads; the batched and serving forms are GPU-only and carry their own "
                 "sequential FP64 reference"}
+    eps_step = EVALS_PER_STEP[args.workload]
+    so, cfg, unit = oracle_system(args)
+    import oracle as O
+    phi = so.uniform_phi()
     for _ in range(args.warmup):
-        cpu_baseline(args, EVALS_PER_STEP[args.workload], budget_s=2.0)
-    vals = []
-    samples = []
+        O.evaluate(so, phi)
+    recs = []
     for _ in range(args.steps):
-        cb = cpu_baseline(args, EVALS_PER_STEP[args.workload], budget_s=8.0)
-        vals.append(cb["value"])
-        samples.append(cb["sample"])
-    value = statistics.mean(vals)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        phi, rec = oracle_sample(args, so, phi, eps_step, 4.0)
+        recs.append(rec)
+    t = sum(r["seconds"] for r in recs)
+    frac = sum(r["fraction"] for r in recs)
+    nev = sum(r["evaluations"] for r in recs)
+    value = frac / t
+    cores = sum(r["cores"] * r["seconds"] for r in recs) / t
     metric, unit, conf = workload_meta(args.workload)
     conf["parallelism"] = "single process (host cores)"
+    sample = ("each step: about 4 s of the oracle's CG on the full-size (%s) workload; %d evaluations "
+              "in %.1f s over %d steps = %.3f evals/s, over %.1f evaluations per %s"
+              % ("x".join(map(str, cfg["grid"])), nev, t, len(recs), nev / t, eps_step,
+                 "MD step" if wl["kind"] == "md" else "solve"))
     return {"impl": "reference", "metric": metric, "value": value, "unit": unit,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": conf,
-            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
-                             "sample": samples[0]},
+            "ms_per_step": 1e3 * t / len(recs), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (binary64 throughout)", "data": "synthetic",
+            "config": conf, "step_fraction": frac / len(recs),
+            "cpu_baseline": {"value": value, "unit": unit, "cores": int(round(cores)),
+                             "cores_measured": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

@@ -192,12 +192,36 @@ __device__ C *fft_lines(C *a, C *b, const FftAxis &ax, int nl, int lstride, int 
     return a;
 }
 
-// Per-thread accumulator type of the reductions: FP64 fields accumulate in
-// FP64; FP32 fields accumulate within a block in FP32 (a few thousand terms)
-// and across blocks in FP64, which keeps the FP64 pipe out of the
-// single-precision kernels.
-template <typename T> struct AccT { typedef double type; };
-template <> struct AccT<float> { typedef float type; };
+// Per-thread accumulator of the FP32 kernels: the running sum is a
+// double-float pair (hi + lo, two binary32 words) and each binary32 term
+// enters by the DWPlusFP sum of ffmath.cuh (relative error <= 2u^2), so a
+// thread's partial carries about 48 significant bits while the FP64 units
+// stay idle.  It enters the block reduction as the binary64 value hi + lo;
+// from the warp level up every sum is binary64.
+struct AccF {
+    ff::f2 v;
+    __device__ __forceinline__ AccF() : v(0.0f, 0.0f) {}
+    __device__ __forceinline__ explicit AccF(float x) : v(x, 0.0f) {}
+    __device__ __forceinline__ AccF &operator+=(float x)
+    {
+        v = ff::add(v, x);
+        return *this;
+    }
+    __device__ __forceinline__ double value() const { return (double)v.hi + (double)v.lo; }
+};
+
+// Per-thread accumulator type of the reductions (AccT<T>::type) and the
+// type the terms are formed in (AccT<T>::term): FP64 fields accumulate
+// binary64 terms in binary64; FP32 fields accumulate binary32 terms in
+// AccF.
+template <typename T> struct AccT {
+    typedef double type;
+    typedef double term;
+};
+template <> struct AccT<float> {
+    typedef AccF type;
+    typedef float term;
+};
 
 // Deterministic block sum of NQ values; thread 0 returns the totals in tot
 // (FP64).  Warp and cross-warp sums in the accumulator type; the block totals
@@ -232,6 +256,15 @@ template <int NQ, typename A> __device__ __forceinline__ void block_sum(A *v, do
 template <int NQ> __device__ __forceinline__ void block_sum(double *v)
 {
     block_sum<NQ, double>(v, v);
+}
+
+// Double-float per-thread partials: binary64 from the warp level up.
+template <int NQ> __device__ __forceinline__ void block_sum(AccF *v, double *tot)
+{
+    double d[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) d[q] = v[q].value();
+    block_sum<NQ, double>(d, tot);
 }
 
 }  // namespace ofdft

@@ -74,17 +74,25 @@ template <> __device__ __forceinline__ ff::f2 fourpi<DD>()
 template <typename PR> __device__ __forceinline__ typename KT<PR>::R scal(typename KT<PR>::T x) { return x; }
 template <> __device__ __forceinline__ ff::f2 scal<DD>(double x) { return ff::split_int(x); }
 
+// Per-thread accumulator of the field kernels' reductions: binary64 for
+// double, double-float for DD (the computed type) and for float (AccF: the
+// binary32 terms summed in a double-float pair).
+template <typename PR> struct AccK { typedef typename KT<PR>::R type; };
+template <> struct AccK<float> { typedef AccF type; };
+
 // Block totals of per-thread accumulators (double-float ones are converted
-// to binary64 first).
-template <int NQ, typename PR> __device__ __forceinline__ void block_total(typename KT<PR>::R *acc, double *tot)
+// to binary64 first; from the warp level up the sums are binary64).
+template <int NQ, typename PR> __device__ __forceinline__ void block_total(typename AccK<PR>::type *acc, double *tot)
 {
     if constexpr (is_dd<PR>()) {
         double d[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) d[q] = ff::to_double(acc[q]);
         block_sum<NQ, double>(d, tot);
+    } else if constexpr (std::is_same<PR, float>::value) {
+        block_sum<NQ>(acc, tot);
     } else {
-        block_sum<NQ, typename AccT<PR>::type>(acc, tot);
+        block_sum<NQ, double>(acc, tot);
     }
 }
 
@@ -357,10 +365,11 @@ __global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__rest
     __syncthreads();
     CC *X = fft_lines<CC, true>(A, B, az, 3 * nl, nz, 1, false);
     CC *res[3] = {X, X + nl * nz, X + 2 * nl * nz};
-    R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-    R sacc[STRESS ? 6 : 1];
+    typedef typename AccK<PR>::type AC;
+    AC acc[6] = {AC(0), AC(0), AC(0), AC(0), AC(0), AC(0)};
+    AC sacc[STRESS ? 6 : 1];
     if constexpr (STRESS)
-        for (int q = 0; q < 6; ++q) sacc[q] = R(0);
+        for (int q = 0; q < 6; ++q) sacc[q] = AC(0);
     const ff::f2 tcoef = is_dd<PR>() ? ff::f2(2.0 / OF_K23 * (double)temp) : ff::f2(0.0f, 0.0f);
     RowCol rc(nz);
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x, rc.next()) {
@@ -466,7 +475,8 @@ __global__ void k_zfinal(GridInfo g, FftAxis az, int P, const typename KT<PR>::C
     pack_c2r<PR>(dspec, obase, nl, nz, K, A);
     __syncthreads();
     CC *X = fft_lines<CC, true>(A, B, az, nl, nz, 1, false);
-    R acc[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    typedef typename AccK<PR>::type AC;
+    AC acc[9] = {AC(0), AC(0), AC(0), AC(0), AC(0), AC(0), AC(0), AC(0), AC(0)};
     const ff::f2 tcoef = is_dd<PR>() && FTTF ? ff::f2(2.0 / OF_K23 * (double)temp) : ff::f2(0.0f, 0.0f);
     RowCol rc(nz);
     for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x, rc.next()) {
@@ -636,7 +646,8 @@ __global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__
     const RecipB<PR, TRI> rb(g);
     const R hr = gcst<PR>(g.hr, g.hrf, g.hr2);
     const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
-    R acc[3] = {R(0), R(0), R(0)};   // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
+    typedef typename AccK<PR>::type AC;
+    AC acc[3] = {AC(0), AC(0), AC(0)};   // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c >= t.ncol) continue;
@@ -701,7 +712,8 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
     const R hr = gcst<PR>(g.hr, g.hrf, g.hr2);
     const R fpi = fourpi<PR>();
     const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
-    R acc[3] = {R(0), R(0), R(0)};
+    typedef typename AccK<PR>::type AC;
+    AC acc[3] = {AC(0), AC(0), AC(0)};
     for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
         const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c >= t.ncol) continue;

@@ -53,14 +53,15 @@ template <typename T, typename U> __global__ void k_convert(long long n, const T
 template <typename T> __global__ void k_sumsq(long long n, const T *__restrict__ x, double *part)
 {
     typedef typename AccT<T>::type A;
+    typedef typename AccT<T>::term P;
     A v[1] = {A(0)};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        A a = (A)x[i];
+        P a = (P)x[i];
         v[0] += a * a;
     }
     double tot[1];
-    block_sum<1, A>(v, tot);
+    block_sum<1>(v, tot);
     if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
 }
 
@@ -86,17 +87,18 @@ __global__ void k_cg_grad(long long n, const T *__restrict__ phi, const T *__res
 {
     if (mup != nullptr) mu = *mup;
     typedef typename AccT<T>::type A;
+    typedef typename AccT<T>::term P;
     const T mut = T(mu);
     A acc[2] = {A(0), A(0)};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         T gi = T(2) * phi[i] * (v[i] - mut);
         g[i] = gi;
-        acc[0] += (A)gi * (A)gi;
-        if (gprev != nullptr) acc[1] += (A)gi * (A)gprev[i];
+        acc[0] += (P)gi * (P)gi;
+        if (gprev != nullptr) acc[1] += (P)gi * (P)gprev[i];
     }
     double tot[2];
-    block_sum<2, A>(acc, tot);
+    block_sum<2>(acc, tot);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = tot[0];
         part[gridDim.x + blockIdx.x] = tot[1];
@@ -109,22 +111,23 @@ __global__ void k_cg_dir(long long n, const T *__restrict__ g, T *__restrict__ d
 {
     if (betap != nullptr) beta = *betap;
     typedef typename AccT<T>::type A;
-    const A ba = A(beta);
-    A acc[5] = {0, 0, 0, 0, 0};
+    typedef typename AccT<T>::term P;
+    const P ba = P(beta);
+    A acc[5] = {A(0), A(0), A(0), A(0), A(0)};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         T gi = g[i];
-        T di = (beta == 0.0) ? -gi : (T)(-(A)gi + ba * (A)d[i]);
+        T di = (beta == 0.0) ? -gi : (T)(-(P)gi + ba * (P)d[i]);
         d[i] = di;
-        A p = (A)phi[i];
-        acc[0] += p * (A)di;
-        acc[1] += (A)di * (A)di;
-        acc[2] += (A)di * (A)gi;
+        P p = (P)phi[i];
+        acc[0] += p * (P)di;
+        acc[1] += (P)di * (P)di;
+        acc[2] += (P)di * (P)gi;
         acc[3] += p * p;
-        acc[4] += p * (A)gi;
+        acc[4] += p * (P)gi;
     }
     double tot[5];
-    block_sum<5, A>(acc, tot);
+    block_sum<5>(acc, tot);
     if (threadIdx.x == 0)
         for (int q = 0; q < 5; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
 }
@@ -140,18 +143,19 @@ __global__ void k_cg_dhat(long long n, const T *__restrict__ g, T *__restrict__ 
         restart = c12r[2] != 0.0;
     }
     typedef typename AccT<T>::type A;
-    const A c1a = A(c1), c2a = A(c2);
+    typedef typename AccT<T>::term P;
+    const P c1a = P(c1), c2a = P(c2);
     A acc[1] = {A(0)};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        A di = restart ? -(A)g[i] : (A)d[i] - c1a * (A)phi[i];
+        P di = restart ? -(P)g[i] : (P)d[i] - c1a * (P)phi[i];
         d[i] = (T)di;
         T dh = (T)(c2a * di);
         dhat[i] = dh;
-        acc[0] += A(2) * (A)phi[i] * (A)v[i] * (A)dh;
+        acc[0] += P(2) * (P)phi[i] * (P)v[i] * (P)dh;
     }
     double tot[1];
-    block_sum<1, A>(acc, tot);
+    block_sum<1>(acc, tot);
     if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
 }
 
