@@ -190,29 +190,31 @@ ZGGA_DD_TRAFFIC_PER_POINT = (28.925952e6 + 0.652288e6) / 96 ** 3
 DD_INSTR_PER_FLOP = (2 * 11 + 9) / 3.0
 
 
-def kernel_model(name, g):
-    """Algorithmic FLOPs and HBM bytes of one launch (FP64) of a timed kernel
-    class: FFT flops 5 n log2 n per complex line, 2.5 n log2 n per real line,
-    plus the pointwise functional; bytes = fields read + written once."""
+def kernel_model(name, g, fttf=False):
+    """Algorithmic FLOPs and HBM bytes of one launch (FP64 fields) of a timed
+    kernel class: FFT flops 5 n log2 n per complex line (two real lines
+    travel as one complex line), plus the pointwise functional; bytes =
+    fields read + written once."""
     nx, ny, nz = g
     K = nz // 2 + 1
     N = nx * ny * nz
     NH = nx * ny * K
-    if name == "zgga":
-        flops = 6 * (nx * ny / 2) * fft_flops(nz) + POINTWISE_FLOP * N   # 3 C2R + 3 R2C, pair packed
-        byts = 16 * NH * 3 * 2 + 8 * N * 2                 # grad spectra in, W spectra out, phi in, vpart out
-    elif name == "zfinal":
-        flops = (nx * ny / 2) * fft_flops(nz) + POINTWISE_FLOP * N
-        byts = 16 * NH + 8 * N * 3
+    if name == "pw":           # pointwise functional: phi, 3 derivatives in; v_part, 3 U out
+        flops = POINTWISE_FLOP * N
+        byts = 8 * N * 8
+    elif name == "dline":      # one derivative along x or y: forward + inverse line transforms
+        n = (nx + ny) / 2.0
+        flops = 2 * (N / 2 / n) * fft_flops(n)
+        byts = 8 * N * 2.5                                 # field in, derivative out (div: half accumulate)
+    elif name == "zfinal":     # GGA: U_z forward + one inverse; ftTF: inverse + pointwise
+        flops = (nx * ny / 2) * fft_flops(nz) * (1 if fttf else 2) + (POINTWISE_FLOP * N if fttf else 0)
+        byts = 16 * NH + 8 * N * (3 if fttf else 6)
     elif name == "ypass":
         flops = nx * K * fft_flops(ny)
         byts = 16 * NH * 2
-    elif name == "xgrad":
-        flops = 4 * ny * K * fft_flops(nx)
-        byts = 16 * NH * 2 + 16 * NH + 16 * NH * 3          # n in/out, vext in, 3 grads out
-    elif name == "xdiv":
-        flops = 4 * ny * K * fft_flops(nx)
-        byts = 16 * NH * 5 + 16 * NH                       # n, vext, 3 W in; D out
+    elif name == "xhl":
+        flops = 2 * ny * K * fft_flops(nx)
+        byts = 16 * NH * 3
     else:
         flops, byts = 0.0, 0.0
     return flops, byts
@@ -359,7 +361,7 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    dominant = "zgga" if wl["functional"] != "fttf" else "zfinal"
+    dominant = "pw" if wl["functional"] != "fttf" else "zfinal"
     launches0 = ctx.kernel_launches()
     clocks = ClockSampler(dev)
     clocks.start()
@@ -533,7 +535,7 @@ def run_solve(args, rank, world):
     clk = clocks.stop()
     launches = ctx.kernel_launches() - launches0
     t_total = max_over_ranks(sum(times), world)
-    dominant = "zgga" if wl["functional"] != "fttf" else "zfinal"
+    dominant = "pw" if wl["functional"] != "fttf" else "zfinal"
     kms, kcount = time_dominant(ctx, ofdft, dominant, stream, lambda: solve(ctx))
     e2e = None
     if not args.no_e2e:

@@ -311,9 +311,10 @@ ofdft_status ofdft_sizes(ofdft_ctx *ctx, long long *N, int *nat);
 /*
  * Diagnostics: record CUDA events around every launch of one kernel class on
  * the context's stream (no extra synchronisation).  id: 0 off,
- * 1 z pass with the pointwise GGA functional, 2 x pass with gradients,
- * 3 x pass with the divergence, 4 y pass, 5 z forward pass, 6 z final pass,
- * 7 x pass of the ftTF potential.  ofdft_timer_read synchronises the stream,
+ * 1 pointwise GGA functional, 2 derivative passes along x and y (gradient of
+ * n, divergence of W), 4 y pass, 5 z forward pass, 6 z final pass, 7 x pass
+ * of the Hartree and local-pseudopotential potential.  ofdft_timer_read
+ * synchronises the stream,
  * returns the summed event time (ms) and the launch count, and optionally
  * clears them.
  */
@@ -386,8 +387,9 @@ void ofdft_destroy(ofdft_ctx *ctx);
  *  cell[9], grid[3], nat, ions, Z, T_kelvin, functional: as ofdft_setup,
  *              but orthorhombic cells only (else OFDFT_EINVAL).
  *  xc, rc: as ofdft_params (Gaussian ion only).
- *  phi_dev  device pointer, N doubles (input; not modified).
- *  v_dev    device pointer, N doubles (output potential).
+ *  phi_dev  device pointer, N doubles (input; not modified), 16-byte aligned.
+ *  v_dev    device pointer, N doubles (output potential), 16-byte aligned;
+ *           also the call's scratch for one field before v is written.
  *  E        host output (may be NULL).
  *  stream   cudaStream_t to run on, or NULL for the default stream; the call
  *           returns after the stream has finished its work.

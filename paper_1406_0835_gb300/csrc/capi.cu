@@ -190,7 +190,7 @@ ofdft_status sync_read(ofdft_ctx *c, int n)
     return OFDFT_OK;
 }
 
-enum TimerId { TM_ZGGA = 1, TM_XGRAD = 2, TM_XDIV = 3, TM_Y = 4, TM_ZFWD = 5, TM_ZFINAL = 6, TM_XHL = 7 };
+enum TimerId { TM_PW = 1, TM_DLINE = 2, TM_Y = 4, TM_ZFWD = 5, TM_ZFINAL = 6, TM_XHL = 7 };
 
 // Event pair around a launch of the selected kernel class (host-driven mode only).
 struct TimerScope {
@@ -243,14 +243,23 @@ EvalScalars unpack_sums(const double *h, bool fttf)
     return es;
 }
 
-int eval_kernel_count(const ofdft_ctx *c) { return c->fp.kind == 0 ? 7 : 12; }
+int eval_kernel_count(const ofdft_ctx *c) { return c->fp.kind == 0 ? 7 : 13; }
 
 // Enqueue one energy + potential evaluation at ph (or, with phi0 and dh, at the
 // trial phi0 cos + dh sin written into ph; angles from csd (two T values in
-// device memory) if given).  Sums go
-// to sums[0..17].  With spart (FP64 GGA sets), the z pass also writes the
-// gradient stress sums: spart holds 12 partial rows of *nbg_out columns.
-// No synchronisation.
+// device memory) if given).  Sums go to sums[0..17].  With keep_nG, n(G) is
+// left in the second spectrum (forces, stress).  With spart (FP64 GGA sets),
+// the pointwise stage also writes the gradient stress sums: spart holds 12
+// partial rows of *nbg_out columns.  No synchronisation.
+//
+// ftTF:  zfwd (n, R2C z) -> y -> x [Hartree, LPP, energies, v_HL(G), x^-1]
+//        -> y^-1 -> zfinal [C2R z, pointwise, potential, sums].
+// GGA:   the same Hartree path, and the gradient and divergence one axis at
+//        a time (the derivative along axis j needs transforms along j only):
+//        zfwd also writes d_z n; dline x, y: d_x n, d_y n (second to fourth
+//        spectra, used as real fields); pointwise: v_part and U_j over the
+//        derivatives; dline x, y: d_x U_x + d_y U_y into vout; zfinal_gga:
+//        v = v_HL - d_z U_z + v_part - (d_x U_x + d_y U_y), sums.
 template <typename T>
 ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const T *dh, double cth,
                           double sth, const void *csd, T *vout, bool keep_nG, double *sums,
@@ -263,6 +272,7 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
     C *s0 = (C *)f.spec;
     const long long fs = (long long)f.spec_stride;
     C *s1 = s0 + fs, *s2 = s1 + fs, *s3 = s2 + fs;
+    T *d0 = (T *)s1, *d1 = (T *)s2, *d2 = (T *)s3;   // real fields of N values (a spectrum holds 2 NH >= N)
     const C *vext = (const C *)f.vext;
     const T *tab = (const T *)f.tab;
     const bool fttf = c->fp.kind == 0;
@@ -271,8 +281,9 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
     double *pA = c->part, *pB = pA + 3 * nbx, *pC = pB + 6 * npairs;
     {
         TimerScope ts(c, TM_ZFWD);
-        if (phi0) launch_zfwd<T>(g, az, 2, nullptr, phi0, dh, (T)cth, (T)sth, csd, ph, s0, st);
-        else launch_zfwd<T>(g, az, 1, nullptr, ph, nullptr, T(0), T(0), nullptr, nullptr, s0, st);
+        T *dz = fttf ? nullptr : d2;
+        if (phi0) launch_zfwd<T>(g, az, 2, nullptr, phi0, dh, (T)cth, (T)sth, csd, ph, s0, st, dz);
+        else launch_zfwd<T>(g, az, 1, nullptr, ph, nullptr, T(0), T(0), nullptr, nullptr, s0, st, dz);
     }
     DBG("k_zfwd");
     {
@@ -280,65 +291,54 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
         launch_ypass<T>(g, ay, false, s0, 1, fs, st);
     }
     DBG("k_ypass fwd");
-    int nbz, nbg = 0;   // blocks of the z passes (zfinal, zgga): their partial sums
+    {
+        TimerScope ts(c, TM_XHL);
+        launch_xhl<T>(g, ax, s0, vext, (keep_nG && fttf) ? s1 : nullptr, 1, pA, st);
+    }
+    DBG("k_xhl");
+    {
+        TimerScope ts(c, TM_Y);
+        launch_ypass<T>(g, ay, true, s0, 1, fs, st);
+    }
+    DBG("k_ypass inv");
+    int nbz, nbg = 0;   // blocks of the z passes (zfinal) and of the pointwise stage: their partial sums
     if (fttf) {
-        {
-            TimerScope ts(c, TM_XHL);
-            launch_xhl<T>(g, ax, s0, vext, keep_nG ? s1 : nullptr, 1, pA, st);
-        }
-        DBG("k_xhl");
-        {
-            TimerScope ts(c, TM_Y);
-            launch_ypass<T>(g, ay, true, s0, 1, fs, st);
-        }
-        DBG("k_ypass inv");
         TimerScope ts(c, TM_ZFINAL);
         nbz = launch_zfinal<T>(g, az, true, s0, nullptr, ph, phi0, dh, (T)cth, (T)sth, csd, (T)c->T,
                                c->fp, tab, c->xc, vout, pC, st);
     } else {
         {
-            TimerScope ts(c, TM_XGRAD);
-            launch_xgrad<T>(g, ax, s0, vext, s1, s2, s3, pA, st);
+            TimerScope ts(c, TM_DLINE);
+            launch_dline<T>(g, ax, 0, 0, 0, ph, d0, st);
         }
-        DBG("k_xgrad");
         {
-            TimerScope ts(c, TM_Y);
-            launch_ypass<T>(g, ay, true, s1, 3, fs, st);
+            TimerScope ts(c, TM_DLINE);
+            launch_dline<T>(g, ay, 1, 0, 0, ph, d1, st);
         }
-        DBG("k_ypass inv x3");
+        DBG("k_dline (grad n)");
         {
-            TimerScope ts(c, TM_ZGGA);
-            bool stress_pass = false;
-            if constexpr (std::is_same<T, double>::value) {
-                if (spart) {
-                    pB = spart;
-                    nbg = launch_zgga_stress(g, az, s1, s2, s3, ph, c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, st);
-                    if (nbg_out) *nbg_out = nbg;
-                    stress_pass = true;
-                }
+            TimerScope ts(c, TM_PW);
+            if (spart) {
+                pB = spart;
+                nbg = launch_pw<T>(g, d0, d1, d2, ph, (T)c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, true, st);
+                if (nbg_out) *nbg_out = nbg;
+            } else {
+                nbg = launch_pw<T>(g, d0, d1, d2, ph, (T)c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, false, st);
             }
-            if (!stress_pass)
-                nbg = launch_zgga<T>(g, az, s1, s2, s3, ph, (T)c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, st);
         }
-        DBG("k_zgga");
+        DBG("k_pw");
         {
-            TimerScope ts(c, TM_Y);
-            launch_ypass<T>(g, ay, false, s1, 3, fs, st);
+            TimerScope ts(c, TM_DLINE);
+            launch_dline<T>(g, ax, 0, 1, 0, d0, vout, st);
         }
-        DBG("k_ypass fwd x3");
         {
-            TimerScope ts(c, TM_XDIV);
-            launch_xdiv<T>(g, ax, s0, vext, s1, s2, s3, st);
+            TimerScope ts(c, TM_DLINE);
+            launch_dline<T>(g, ay, 1, 1, 1, d1, vout, st);
         }
-        DBG("k_xdiv");
-        {
-            TimerScope ts(c, TM_Y);
-            launch_ypass<T>(g, ay, true, s1, 1, fs, st);
-        }
-        DBG("k_ypass inv x1");
+        DBG("k_dline (div W)");
         TimerScope ts(c, TM_ZFINAL);
-        nbz = launch_zfinal<T>(g, az, false, s1, (const T *)f.vpart, ph, phi0, dh, (T)cth, (T)sth, csd,
-                               (T)c->T, c->fp, tab, c->xc, vout, pC, st);
+        nbz = launch_zfinal_gga<T>(g, az, s0, d2, (const T *)f.vpart, vout, ph, phi0, dh, (T)cth, (T)sth, csd,
+                                   vout, pC, st);
     }
     DBG("k_zfinal");
     launch_reduce(pA, nbx, 3, sums, st);
@@ -346,6 +346,14 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
     launch_reduce(pC, nbz, 9, sums + 9, st);
     DBG("k_reduce");
     c->launches += eval_kernel_count(c);
+    if (keep_nG && !fttf) {
+        // n(G) for forces and stress: forward z, y, x of n into the second spectrum
+        launch_zfwd<T>(g, az, 1, nullptr, ph, nullptr, T(0), T(0), nullptr, nullptr, s1, st);
+        launch_ypass<T>(g, ay, false, s1, 1, fs, st);
+        launch_xhl<T>(g, ax, s1, vext, s1, 0, pA, st);
+        c->launches += 3;
+        DBG("n(G)");
+    }
     return OFDFT_OK;
 }
 
@@ -802,7 +810,7 @@ ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
     ofdft_status s = evaluate<double>(c, f, (double *)f.phi, (double *)f.vt, true, es);
     if (s != OFDFT_OK) return s;
     const GridInfo &g = c->g;
-    const double2 *nG = (const double2 *)f.spec + (c->fp.kind == 0 ? f.spec_stride : 0);
+    const double2 *nG = (const double2 *)f.spec + f.spec_stride;
     size_t need = (size_t)c->nat * 1216 * 3 + 16;
     if (need > c->fpart_len) {
         if (c->fpart) cudaFreeAsync(c->fpart, c->st);
@@ -1459,7 +1467,7 @@ ofdft_status ofdft_stress(ofdft_ctx *c, double *sigma, double *terms)
     // out[0..5] sum W_a d_b n, [6..11] Hartree, [12..17] LPP, [18..23] Ewald real, [24..30] Ewald G
     if (!fttf) launch_reduce(zpart + 6 * (size_t)nbg, nbg, 6, out, st);
     else CK(cudaMemsetAsync(out, 0, 6 * sizeof(double), st));
-    const double2 *nG = (const double2 *)f.spec + (fttf ? f.spec_stride : 0);
+    const double2 *nG = (const double2 *)f.spec + f.spec_stride;
     const int ng = launch_gstress(g, c->nat, c->Zd, c->px, c->py, c->pz, nG, gpart, st);
     launch_reduce(gpart, ng, 12, out + 6, st);
     const int nb = launch_ewald_stress(c->nat, c->Rd, c->Zd, ew_cell(g), c->ew_alpha, c->ew_rcut, c->ew_nimg, c->nGe,

@@ -171,6 +171,8 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
 {
     if (!cell || !grid || !ions || !Z || !phi_dev || !v_dev)
         return serr(OFDFT_EINVAL, "NULL argument");
+    if ((((uintptr_t)phi_dev) | ((uintptr_t)v_dev)) & 15)
+        return serr(OFDFT_EINVAL, "phi_dev and v_dev must be 16-byte aligned");
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
             if (i != j && cell[3 * i + j] != 0.0) return serr(OFDFT_EINVAL, "cell is not orthorhombic");
@@ -260,23 +262,26 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     double *pA = part, *pB = pA + 3 * nbx, *pC = pB + 6 * npairs;
     double *ph = const_cast<double *>(phi_dev);
     const bool fttf = fp.kind == 0;
-    launch_zfwd<double>(g, az, 1, nullptr, ph, nullptr, 0.0, 0.0, nullptr, nullptr, s0, st);
+    // the second to fourth spectra double as real fields (2 NH >= N values):
+    // derivatives of n, then the fields whose derivatives make up div W;
+    // v_dev holds d_x U_x + d_y U_y until the final pass overwrites it with v
+    double *d0 = (double *)s1, *d1 = (double *)s2, *d2 = (double *)s3;
+    launch_zfwd<double>(g, az, 1, nullptr, ph, nullptr, 0.0, 0.0, nullptr, nullptr, s0, st, fttf ? nullptr : d2);
     launch_ypass<double>(g, ay, false, s0, 1, specN, st);
-    int nbz, nbg = 0;   // blocks of the z passes (zfinal, zgga): their partial sums
+    launch_xhl<double>(g, ax, s0, vext, nullptr, 1, pA, st);
+    launch_ypass<double>(g, ay, true, s0, 1, specN, st);
+    int nbz, nbg = 0;   // blocks of the final z pass and of the pointwise stage: their partial sums
     if (fttf) {
-        launch_xhl<double>(g, ax, s0, vext, nullptr, 1, pA, st);
-        launch_ypass<double>(g, ay, true, s0, 1, specN, st);
         nbz = launch_zfinal<double>(g, az, true, s0, nullptr, ph, nullptr, nullptr, 1.0, 0.0, nullptr, T, fp,
                                     tab, xc, v_dev, pC, st);
     } else {
-        launch_xgrad<double>(g, ax, s0, vext, s1, s2, s3, pA, st);
-        launch_ypass<double>(g, ay, true, s1, 3, specN, st);
-        nbg = launch_zgga<double>(g, az, s1, s2, s3, ph, T, fp, tab, xc, vpart, pB, st);
-        launch_ypass<double>(g, ay, false, s1, 3, specN, st);
-        launch_xdiv<double>(g, ax, s0, vext, s1, s2, s3, st);
-        launch_ypass<double>(g, ay, true, s1, 1, specN, st);
-        nbz = launch_zfinal<double>(g, az, false, s1, vpart, ph, nullptr, nullptr, 1.0, 0.0, nullptr, T, fp,
-                                    tab, xc, v_dev, pC, st);
+        launch_dline<double>(g, ax, 0, 0, 0, ph, d0, st);
+        launch_dline<double>(g, ay, 1, 0, 0, ph, d1, st);
+        nbg = launch_pw<double>(g, d0, d1, d2, ph, T, fp, tab, xc, vpart, pB, false, st);
+        launch_dline<double>(g, ax, 0, 1, 0, d0, v_dev, st);
+        launch_dline<double>(g, ay, 1, 1, 1, d1, v_dev, st);
+        nbz = launch_zfinal_gga<double>(g, az, s0, d2, vpart, v_dev, ph, nullptr, nullptr, 1.0, 0.0, nullptr,
+                                        v_dev, pC, st);
     }
     launch_reduce(pA, nbx, 3, scal, st);
     if (!fttf) launch_reduce(pB, nbg, 6, scal + 3, st);

@@ -6,35 +6,43 @@
 namespace ofdft {
 
 // ---- grid fields (kernels_fields.cu)
+// z pass, forward: n = phi^2 (mode 1), the trial rotation phi cos + dhat sin
+// written to phit (mode 2) or a plain field (mode 0), R2C along z into the
+// half spectrum out; with dz also d_z n into the real field dz.
 template <typename T>
 void launch_zfwd(const GridInfo &g, const FftAxis &az, int mode, const T *in, const T *phi,
-                 const T *dhat, T c, T s, const void *cs, T *phit, cplx<T> *out, cudaStream_t st);
+                 const T *dhat, T c, T s, const void *cs, T *phit, cplx<T> *out, cudaStream_t st,
+                 T *dz = nullptr);
+// Derivative of a real field along grid axis 0 (x) or 1 (y) by 1-D
+// transforms along that axis: out (= or, acc != 0, +=) d f, f = phi^2 for
+// mode 0 and f = in for mode 1 (scale GridInfo::ds).
 template <typename T>
-int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, cplx<T> *g2,
-                const T *phit, T temp, const FuncParams &fp, const T *tab, int xc, T *vpart,
-                double *part, cudaStream_t st);
-// The same evaluation stage for an FP64 set, also writing sum W_a d_b n
-// (xx, yy, zz, xy, xz, yz) into partial rows 6..11 (part holds 12 rows).
-int launch_zgga_stress(const GridInfo &g, const FftAxis &az, double2 *g0, double2 *g1, double2 *g2,
-                       const double *phit, double temp, const FuncParams &fp, const double *tab, int xc,
-                       double *vpart, double *part, cudaStream_t st);
+void launch_dline(const GridInfo &g, const FftAxis &fa, int axis, int mode, int acc, const T *in, T *out,
+                  cudaStream_t st);
+// Pointwise functional + XC: reads phi and the derivatives of n in d0..d2,
+// writes v_part and, over d0..d2, the fields U_j whose derivatives sum to
+// div W.  Partials: 6 rows (12 with stress: sum W_a d_b n in rows 6..11, FP64
+// sets only) of the returned number of columns.
+template <typename T>
+int launch_pw(const GridInfo &g, T *d0, T *d1, T *d2, const T *phit, T temp, const FuncParams &fp, const T *tab,
+              int xc, T *vpart, double *part, bool stress, cudaStream_t st);
+// z pass, final (ftTF): C2R of v_HL, pointwise functional, potential and sums.
 template <typename T>
 int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T> *dspec,
                   const T *vpart, const T *phit, const T *phi, const T *dhat, T c, T s,
                   const void *cs, T temp, const FuncParams &fp, const T *tab, int xc, T *vout,
                   double *part, cudaStream_t st);
+// z pass, final (GGA): v = v_HL - d_z U_z + v_part - div (div may alias vout).
+template <typename T>
+int launch_zfinal_gga(const GridInfo &g, const FftAxis &az, const cplx<T> *dspec, const T *uz, const T *vpart,
+                      const T *div, const T *phit, const T *phi, const T *dhat, T c, T s, const void *cs, T *vout,
+                      double *part, cudaStream_t st);
 template <typename T>
 void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data, int nfields,
                   long long fstride, cudaStream_t st);
 template <typename T>
-int launch_xgrad(const GridInfo &g, const FftAxis &ax, cplx<T> *nspec, const cplx<T> *vext,
-                 cplx<T> *g0, cplx<T> *g1, cplx<T> *g2, double *part, cudaStream_t st);
-template <typename T>
 int launch_xhl(const GridInfo &g, const FftAxis &ax, cplx<T> *spec, const cplx<T> *vext,
                cplx<T> *nG_out, int inverse, double *part, cudaStream_t st);
-template <typename T>
-void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const cplx<T> *vext,
-                 cplx<T> *w0, const cplx<T> *w1, const cplx<T> *w2, cudaStream_t st);
 size_t field_smem_max(const GridInfo &g, size_t csize);
 // blocks (and partial sums per quantity) of the x passes
 int xpass_blocks(const GridInfo &g);

@@ -13,6 +13,7 @@
 // compute in their own type; DD keeps the fields in binary64 in memory and
 // computes in double-float (ffmath.cuh) in registers and shared memory, so
 // the FP64 path runs on the FP32 units.  KT<PR> names the types.
+#include <algorithm>
 #include <type_traits>
 
 #include "fft_core.cuh"
@@ -235,14 +236,27 @@ struct RowCol {
     }
 };
 
+// Multiply element e of a line of n by i kt(e) s (kt = 0 on the Nyquist plane).
+template <typename CC, typename R>
+__device__ __forceinline__ CC times_ik(CC x, int e, int n, R s)
+{
+    const int k = (2 * e == n) ? 0 : (e <= n / 2 ? e : e - n);
+    const R m = R(k) * s;
+    return cmk<CC>(R(0) - m * x.y, m * x.x);
+}
+
 // ------------------------------------------------------------------ z pass
 // Pair p of a block holds real lines 2p (real part) and 2p+1 (imaginary part).
 
+// With dzout the kernel also writes d_z n (the derivative along z by the
+// line transforms it already holds: the forward spectrum times i kt ds_z,
+// transformed back).
 template <typename PR, int MODE>
 __global__ void k_zfwd(GridInfo g, FftAxis az, int P, const typename KT<PR>::T *__restrict__ in,
                        const typename KT<PR>::T *__restrict__ phi, const typename KT<PR>::T *__restrict__ dhat,
                        typename KT<PR>::T c, typename KT<PR>::T s, const void *__restrict__ cs,
-                       typename KT<PR>::T *__restrict__ phit, typename KT<PR>::C *__restrict__ out)
+                       typename KT<PR>::T *__restrict__ phit, typename KT<PR>::C *__restrict__ out,
+                       typename KT<PR>::T *__restrict__ dzout)
 {
     typedef typename KT<PR>::T T;
     typedef typename KT<PR>::R R;
@@ -290,6 +304,20 @@ __global__ void k_zfwd(GridInfo g, FftAxis az, int P, const typename KT<PR>::T *
                           : cmk<CC>(half * (z.x + zc.x), half * (z.y + zc.y));
         out[obase + i] = stc<PR>(r);
     }
+    if (dzout != nullptr) {
+        __syncthreads();
+        const R sz = gcst<PR>(g.ds[2], g.dsf[2], g.ds2[2]);
+        RowCol re(nz);
+        for (int i = threadIdx.x; i < nl * nz; i += blockDim.x, re.next())
+            X[i] = times_ik<CC, R>(X[i], re.c, nz, sz);
+        __syncthreads();
+        CC *Y = fft_lines<CC, true>(X, X == A ? B : A, az, nl, nz, 1, false);
+        RowCol ro(nz);
+        for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x, ro.next()) {
+            const R *src = reinterpret_cast<const R *>(&Y[(ro.r >> 1) * nz + ro.c]);
+            dzout[base + i] = str<PR>(src[ro.r & 1]);
+        }
+    }
 }
 
 // Build the pair-packed complex line C_k = A_k + i B_k (k <= nz/2) and its
@@ -330,116 +358,6 @@ __device__ __forceinline__ void unpack_r2c(const typename KT<PR>::CC *X, long lo
         CC z = row[k], zc = cconj(row[k == 0 ? 0 : nz - k]);
         out[obase + i] = stc<PR>((line & 1) ? cmk<CC>(half * (z.y - zc.y), mhalf * (z.x - zc.x))
                                             : cmk<CC>(half * (z.x + zc.x), half * (z.y + zc.y)));
-    }
-}
-
-// Fused GGA stage: C2R of grad n (3 fields), pointwise functional + XC,
-// R2C of W (3 fields, written over grad n).  Partials: F_s, TS, F_xc,
-// sum(n df/dn - f), sum W.grad n, sum n(v_xc - eps_xc); with STRESS also
-// sum W_a d_b n for ab = xx, yy, zz, xy, xz, yz (the gradient part of
-// Eq. (stressTF_b)) in partial rows 6..11.
-template <typename PR, bool STRESS>
-__global__ void k_zgga(GridInfo g, FftAxis az, int P, typename KT<PR>::C *__restrict__ g0,
-                       typename KT<PR>::C *__restrict__ g1, typename KT<PR>::C *__restrict__ g2,
-                       const typename KT<PR>::T *__restrict__ phit, typename KT<PR>::T temp, FuncParams fp,
-                       const typename KT<PR>::T *__restrict__ tab, int xc, typename KT<PR>::T *__restrict__ vpart,
-                       double *__restrict__ part)
-{
-    typedef typename KT<PR>::T T;
-    typedef typename KT<PR>::R R;
-    typedef typename KT<PR>::C C;
-    typedef typename KT<PR>::CC CC;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int nz = g.nz, K = g.K;
-    // the three components' lines side by side (field a at line a nl), so
-    // each transform is one batch of 3 nl lines; the other half is scratch
-    const long long npairs = (long long)g.nx * g.ny / 2;
-    const long long p0 = (long long)blockIdx.x * P;
-    const int nl = (int)min((long long)P, npairs - p0);
-    const long long obase = 2 * p0 * K;
-    const long long rbase = 2 * p0 * nz;
-    CC *A = reinterpret_cast<CC *>(smraw);
-    CC *B = A + 3 * P * nz;
-    C *spec[3] = {g0, g1, g2};
-    for (int a = 0; a < 3; ++a) pack_c2r<PR>(spec[a], obase, nl, nz, K, A + a * nl * nz);
-    __syncthreads();
-    CC *X = fft_lines<CC, true>(A, B, az, 3 * nl, nz, 1, false);
-    CC *res[3] = {X, X + nl * nz, X + 2 * nl * nz};
-    typedef typename AccK<PR>::type AC;
-    AC acc[6] = {AC(0), AC(0), AC(0), AC(0), AC(0), AC(0)};
-    AC sacc[STRESS ? 6 : 1];
-    if constexpr (STRESS)
-        for (int q = 0; q < 6; ++q) sacc[q] = AC(0);
-    const ff::f2 tcoef = is_dd<PR>() ? ff::f2(2.0 / OF_K23 * (double)temp) : ff::f2(0.0f, 0.0f);
-    RowCol rc(nz);
-    for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x, rc.next()) {
-        const int line = rc.r, e = rc.c;
-        const int p = line >> 1, hi = line & 1;
-        R gr[3];
-        for (int a = 0; a < 3; ++a)   // each thread owns one component of the packed pair
-            gr[a] = reinterpret_cast<const R *>(&res[a][p * nz + e])[hi];
-        if constexpr (is_dd<PR>()) {
-            const R ph = ldr<PR>(phit[rbase + i]);
-            const R n = ph * ph;
-            const PwF2 o = pw_dd(fp, tab, tcoef, (double)temp, n, gr, xc);
-            vpart[rbase + i] = str<PR>(o.dfdn + o.vxc);
-            acc[0] += o.f;
-            acc[1] += o.ts;
-            acc[2] += n * o.eps;
-            acc[3] += n * o.dfdn - o.f;
-            acc[4] += o.w[0] * gr[0] + o.w[1] * gr[1] + o.w[2] * gr[2];
-            acc[5] += n * (o.vxc - o.eps);
-            if constexpr (STRESS) {
-                sacc[0] += o.w[0] * gr[0];
-                sacc[1] += o.w[1] * gr[1];
-                sacc[2] += o.w[2] * gr[2];
-                sacc[3] += o.w[0] * gr[1];
-                sacc[4] += o.w[0] * gr[2];
-                sacc[5] += o.w[1] * gr[2];
-            }
-            for (int a = 0; a < 3; ++a) {
-                R *d = reinterpret_cast<R *>(&res[a][p * nz + e]);
-                d[hi] = o.w[a];
-            }
-        } else {
-            T ph = phit[rbase + i];
-            T n = ph * ph;
-            T gg = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
-            PwOut<T> o = pw_point_native<T>(fp, tab, temp, n, gg, xc);
-            const T eps = o.eps, vxc = o.vxc;
-            vpart[rbase + i] = o.dfdn + vxc;
-            acc[0] += o.f;
-            acc[1] += o.ts;
-            acc[2] += n * eps;
-            acc[3] += n * o.dfdn - o.f;
-            acc[4] += o.wc * gg;
-            acc[5] += n * (vxc - eps);
-            if constexpr (STRESS) {
-                sacc[0] += o.wc * gr[0] * gr[0];
-                sacc[1] += o.wc * gr[1] * gr[1];
-                sacc[2] += o.wc * gr[2] * gr[2];
-                sacc[3] += o.wc * gr[0] * gr[1];
-                sacc[4] += o.wc * gr[0] * gr[2];
-                sacc[5] += o.wc * gr[1] * gr[2];
-            }
-            for (int a = 0; a < 3; ++a) {
-                T *d = reinterpret_cast<T *>(&res[a][p * nz + e]);
-                d[hi] = o.wc * gr[a];
-            }
-        }
-    }
-    __syncthreads();
-    CC *Y = fft_lines<CC, false>(X, X == A ? B : A, az, 3 * nl, nz, 1, false);
-    for (int a = 0; a < 3; ++a) unpack_r2c<PR>(Y + a * nl * nz, obase, nl, nz, K, spec[a]);
-    double tot[6];
-    block_total<6, PR>(acc, tot);
-    if (threadIdx.x == 0)
-        for (int q = 0; q < 6; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
-    if constexpr (STRESS) {
-        __syncthreads();
-        block_total<6, PR>(sacc, tot);
-        if (threadIdx.x == 0)
-            for (int q = 0; q < 6; ++q) part[(size_t)(6 + q) * gridDim.x + blockIdx.x] = tot[q];
     }
 }
 
@@ -623,74 +541,6 @@ __device__ __forceinline__ typename KT<PR>::R ploc_term(const GridInfo &g, const
     return re * (R(1) - hr * g2);
 }
 
-// x pass, gradient variant: forward x -> n(G) (stored), energies, then
-// i D_a n(G) inverse-x for a = x, y, z.  Partials: E_H, E_loc, P_loc.
-template <typename PR, bool TRI>
-__global__ void k_xgrad(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ nspec,
-                        const typename KT<PR>::C *__restrict__ vext, typename KT<PR>::C *__restrict__ g0,
-                        typename KT<PR>::C *__restrict__ g1, typename KT<PR>::C *__restrict__ g2,
-                        double *__restrict__ part)
-{
-    typedef typename KT<PR>::R R;
-    typedef typename KT<PR>::C C;
-    typedef typename KT<PR>::CC CC;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int nx = g.nx;
-    CC *A = reinterpret_cast<CC *>(smraw);
-    CC *B = A + nx * g.tk;
-    CC *N = B + nx * g.tk;
-    ColTile t = col_tile(g, true);
-    load_tile<PR>(nspec, t, nx, A);
-    __syncthreads();
-    CC *X = fft_lines<CC, false>(A, B, ax, t.ncol, 1, g.tk, true);
-    const RecipB<PR, TRI> rb(g);
-    const R hr = gcst<PR>(g.hr, g.hrf, g.hr2);
-    const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
-    typedef typename AccK<PR>::type AC;
-    AC acc[3] = {AC(0), AC(0), AC(0)};   // sum w |n|^2/G^2, sum w Re(n* v_ext), sum w Re(n* v_ext)(1 - G^2 rc^2/2)
-    for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
-        const int r = i >> t.tsh, c = i & (t.tk - 1);
-        if (c >= t.ncol) continue;
-        CC nG = cscale(X[i], invN);
-        N[i] = nG;
-        Gk<R> k = rb.gk(g, r, t.couter[c], t.ckz[c]);
-        if (k.g2 > R(0)) {
-            const long long vi = t.cbase[c] + r * t.rstride;
-            CC ve = ldc<PR>(vext[vi]);
-            R n2 = nG.x * nG.x + nG.y * nG.y;
-            R re = nG.x * ve.x + nG.y * ve.y;
-            if constexpr (TRI) acc[0] += k.w * n2 * k.ig2;
-            else acc[0] += k.w * n2 / k.g2;
-            acc[1] += k.w * re;
-            acc[2] += k.w * ploc_term<PR>(g, vext, vi, nG, re, hr, k.g2);
-        }
-    }
-    __syncthreads();
-    store_tile<PR>(nspec, t, nx, N);
-    C *outs[3] = {g0, g1, g2};
-    for (int a = 0; a < 3; ++a) {
-        for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
-            const int r = i >> t.tsh, c = i & (t.tk - 1);
-            const R d = rb.d(g, a, r, t.couter[c], t.ckz[c]);
-            CC v = N[i];
-            A[i] = cmk<CC>(-d * v.y, d * v.x);      // i D_a n(G)
-        }
-        __syncthreads();
-        CC *Y = fft_lines<CC, true>(A, B, ax, t.ncol, 1, g.tk, true);
-        store_tile<PR>(outs[a], t, nx, Y);
-        __syncthreads();
-    }
-    double tot[3];
-    block_total<3, PR>(acc, tot);
-    if (threadIdx.x == 0) {
-        // E_H = (Omega/2) sum 4 pi |n|^2/G^2, E_loc = Omega sum Re(n* v_ext),
-        // P_loc = sum Re(n* v_p) (ploc_term)
-        part[blockIdx.x] = 0.5 * g.omega * 12.566370614359172954 * tot[0];
-        part[(size_t)gridDim.x + blockIdx.x] = g.omega * tot[1];
-        part[(size_t)2 * gridDim.x + blockIdx.x] = ((g.lpp || g.tri) ? 1.0 : 1.0 / 3.0) * tot[2];
-    }
-}
-
 // x pass, ftTF variant: forward x -> energies -> v_HL(G) = 4 pi n/G^2 + v_ext
 // inverse-x, written over the spectrum.  If keep_n, n(G) is also stored in nG_out.
 template <typename PR, bool TRI>
@@ -752,56 +602,288 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
     }
 }
 
-// x pass, divergence variant: D(G) = v_H(G) + v_ext(G) - sum_a i D_a W_a(G)
-// from n(G) and the y-transformed W_a; inverse-x result written over W_0.
-template <typename PR, bool TRI>
-__global__ void k_xdiv(GridInfo g, FftAxis ax, const typename KT<PR>::C *__restrict__ nG,
-                       const typename KT<PR>::C *__restrict__ vext, typename KT<PR>::C *__restrict__ w0,
-                       const typename KT<PR>::C *__restrict__ w1, const typename KT<PR>::C *__restrict__ w2)
+// ------------------------------------------------- derivative line passes
+// A GGA evaluation takes the gradient of n and the divergence of W one grid
+// axis at a time.  The 3-D transform is a product of commuting 1-D
+// transforms and the derivative multiplier along lattice direction j, kt_j
+// (the signed integer index, zeroed on its own Nyquist plane), depends on
+// k_j alone, so F^-1 (i kt_j) F f = F_j^-1 (i kt_j) F_j f: each derivative
+// needs transforms along its own axis only.  The pass multiplies by
+// i kt_j ds_j, ds_j = b_j / n_j in an orthorhombic cell (the Cartesian
+// derivative) or 1 / n_j in a general cell (the lattice-direction
+// derivative; the pointwise kernel combines the three with the reciprocal
+// basis, D_a = sum_j kt_j (b_j)_a as in the x passes).  Two real columns
+// travel as one complex line c = a + i b: the operator maps real fields to
+// real fields, so F^-1 M F c = (d a) + i (d b) needs no unpacking.
+
+// Pair-column tile of a real field for the passes along x (AX 0) or y
+// (AX 1): g.tk consecutive pairs of adjacent iz columns of the flattened
+// (iy, iz) (x pass) or (ix, iz) (y pass) space; rows run along the axis.
+struct PairTile {
+    long long rstride;
+    int ncol, tk, tsh;
+    const long long *cbase;   // offset of (row 0, even column of pair c)
+};
+
+__device__ __forceinline__ PairTile pair_tile(const GridInfo &g, int ax)
 {
+    __shared__ long long s_pb[16];
+    const int tk = g.tk;
+    const int hz = g.nz / 2;
+    const long long total = (long long)(ax == 0 ? g.ny : g.nx) * hz;
+    const long long p0 = (long long)blockIdx.x * tk;
+    PairTile t;
+    t.tk = tk;
+    t.tsh = __ffs(tk) - 1;
+    t.ncol = (int)min((long long)tk, total - p0);
+    t.rstride = ax == 0 ? (long long)g.ny * g.nz : (long long)g.nz;
+    if (threadIdx.x < tk) {
+        const long long p = p0 + min((int)threadIdx.x, t.ncol - 1);
+        long long b = 2 * p;   // x pass: pairs of the yz plane are contiguous
+        if (ax == 1) {
+            const long long ix = p / hz;
+            b = ix * g.ny * g.nz + 2 * (p - ix * hz);
+        }
+        s_pb[threadIdx.x] = b;
+    }
+    __syncthreads();
+    t.cbase = s_pb;
+    return t;
+}
+
+__host__ __device__ __forceinline__ int pair_tiles_of(const GridInfo &g, int ax)
+{
+    const long long total = (long long)(ax == 0 ? g.ny : g.nx) * (g.nz / 2);
+    return (int)((total + g.tk - 1) / g.tk);
+}
+
+// Stored pair of reals (two adjacent iz columns; even offset, so aligned).
+template <typename T> struct Pair2;
+template <> struct Pair2<double> { typedef double2 type; };
+template <> struct Pair2<float> { typedef float2 type; };
+
+// out (= or +=) d_j f along grid axis AX for f = phi^2 (MODE 0) or f = in
+// (MODE 1); ACC 1 adds to out.
+template <typename PR, int AX, int MODE, int ACC>
+__global__ void k_dline(GridInfo g, FftAxis fa, const typename KT<PR>::T *__restrict__ in,
+                        typename KT<PR>::T *__restrict__ out)
+{
+    typedef typename KT<PR>::T T;
     typedef typename KT<PR>::R R;
-    typedef typename KT<PR>::C C;
     typedef typename KT<PR>::CC CC;
+    typedef typename Pair2<T>::type T2;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int nx = g.nx;
+    const int n = AX == 0 ? g.nx : g.ny;
     CC *A = reinterpret_cast<CC *>(smraw);
-    CC *B = A + nx * g.tk;
-    CC *D = B + nx * g.tk;
-    ColTile t = col_tile(g, true);
-    const RecipB<PR, TRI> rb(g);
-    const R fpi = fourpi<PR>();
-    const R invN = gcst<PR>(g.invN, g.invNf, g.invN2);
-    for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
+    CC *B = A + n * g.tk;
+    const PairTile t = pair_tile(g, AX);
+    for (int i = threadIdx.x; i < n * t.tk; i += blockDim.x) {
+        const int r = i >> t.tsh, c = i & (t.tk - 1);
+        if (c < t.ncol) {
+            const T2 v = *reinterpret_cast<const T2 *>(in + t.cbase[c] + r * t.rstride);
+            R a = ldr<PR>(v.x), b = ldr<PR>(v.y);
+            if (MODE == 0) {
+                a = a * a;
+                b = b * b;
+            }
+            A[i] = cmk<CC>(a, b);
+        }
+    }
+    __syncthreads();
+    CC *X = fft_lines<CC, false>(A, B, fa, t.ncol, 1, t.tk, true);
+    const R s = gcst<PR>(g.ds[AX], g.dsf[AX], g.ds2[AX]);
+    for (int i = threadIdx.x; i < n * t.tk; i += blockDim.x) {
+        const int r = i >> t.tsh, c = i & (t.tk - 1);
+        if (c < t.ncol) X[i] = times_ik<CC, R>(X[i], r, n, s);
+    }
+    __syncthreads();
+    CC *Y = fft_lines<CC, true>(X, X == A ? B : A, fa, t.ncol, 1, t.tk, true);
+    for (int i = threadIdx.x; i < n * t.tk; i += blockDim.x) {
         const int r = i >> t.tsh, c = i & (t.tk - 1);
         if (c >= t.ncol) continue;
-        Gk<R> k = rb.gk(g, r, t.couter[c], t.ckz[c]);
-        CC out = cmk<CC>(R(0), R(0));
-        if (k.g2 > R(0)) {
-            CC n = ldc<PR>(nG[t.cbase[c] + r * t.rstride]);
-            CC ve = ldc<PR>(vext[t.cbase[c] + r * t.rstride]);
-            R kh;
-            if constexpr (TRI) kh = fpi * k.ig2;
-            else kh = fpi / k.g2;
-            out = cmk<CC>(kh * n.x + ve.x, kh * n.y + ve.y);
+        T2 *p = reinterpret_cast<T2 *>(out + t.cbase[c] + r * t.rstride);
+        const CC y = Y[i];
+        T2 o;
+        if (ACC) {
+            const T2 q = *p;
+            o.x = str<PR>(ldr<PR>(q.x) + y.x);
+            o.y = str<PR>(ldr<PR>(q.y) + y.y);
+        } else {
+            o.x = str<PR>(y.x);
+            o.y = str<PR>(y.y);
         }
-        D[i] = out;
+        *p = o;
     }
-    const C *ws[3] = {w0, w1, w2};
-    for (int a = 0; a < 3; ++a) {
-        load_tile<PR>(ws[a], t, nx, A);
-        __syncthreads();
-        CC *X = fft_lines<CC, false>(A, B, ax, t.ncol, 1, g.tk, true);
-        for (int i = threadIdx.x; i < nx * g.tk; i += blockDim.x) {
-            const int r = i >> t.tsh, c = i & (t.tk - 1);
-            if (c >= t.ncol) continue;
-            const R d = rb.d(g, a, r, t.couter[c], t.ckz[c]) * invN;
-            CC wv = X[i];
-            D[i] = cmk<CC>(D[i].x + d * wv.y, D[i].y - d * wv.x);   // -= i d W
+}
+
+// ------------------------------------------------------ pointwise stage
+// Pointwise functional + XC at every grid point (Eqs. (tred), (FGGA),
+// (vftGGA) first two lines, (vxc1)), no transforms: reads phi and the three
+// derivatives of n from d0..d2, writes v_part = df/dn + v_xc and, over
+// d0..d2, the fields whose derivatives make up div W: U_j = W_j
+// (orthorhombic) or U_j = sum_a (b_j)_a W_a (general cell, where d_j are
+// lattice-direction derivatives and grad_a n = sum_j (b_j)_a d_j n).
+// Partials: F_s, TS, F_xc, sum(n df/dn - f), sum W.grad n,
+// sum n(v_xc - eps_xc); with STRESS also sum W_a d_b n for ab = xx, yy,
+// zz, xy, xz, yz (the gradient part of Eq. (stressTF_b)) in rows 6..11.
+template <typename PR, bool STRESS, bool TRI>
+__global__ void k_pw(GridInfo g, typename KT<PR>::T *__restrict__ d0, typename KT<PR>::T *__restrict__ d1,
+                     typename KT<PR>::T *__restrict__ d2, const typename KT<PR>::T *__restrict__ phit,
+                     typename KT<PR>::T temp, FuncParams fp, const typename KT<PR>::T *__restrict__ tab, int xc,
+                     typename KT<PR>::T *__restrict__ vpart, double *__restrict__ part)
+{
+    typedef typename KT<PR>::T T;
+    typedef typename KT<PR>::R R;
+    typedef typename AccK<PR>::type AC;
+    AC acc[6] = {AC(0), AC(0), AC(0), AC(0), AC(0), AC(0)};
+    AC sacc[STRESS ? 6 : 1];
+    if constexpr (STRESS)
+        for (int q = 0; q < 6; ++q) sacc[q] = AC(0);
+    R bm[TRI ? 9 : 1];
+    if constexpr (TRI)
+        for (int k = 0; k < 9; ++k) bm[k] = gcst<PR>(g.Bm[k], g.Bmf[k], g.Bm2[k]);
+    const ff::f2 tcoef = is_dd<PR>() ? ff::f2(2.0 / OF_K23 * (double)temp) : ff::f2(0.0f, 0.0f);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const R dj[3] = {ldr<PR>(d0[i]), ldr<PR>(d1[i]), ldr<PR>(d2[i])};
+        R gr[3];
+        if constexpr (TRI) {
+            for (int a = 0; a < 3; ++a) gr[a] = bm[a] * dj[0] + bm[3 + a] * dj[1] + bm[6 + a] * dj[2];
+        } else {
+            for (int a = 0; a < 3; ++a) gr[a] = dj[a];
         }
-        __syncthreads();
+        R w[3];
+        if constexpr (is_dd<PR>()) {
+            const R ph = ldr<PR>(phit[i]);
+            const R n = ph * ph;
+            const PwF2 o = pw_dd(fp, tab, tcoef, (double)temp, n, gr, xc);
+            vpart[i] = str<PR>(o.dfdn + o.vxc);
+            acc[0] += o.f;
+            acc[1] += o.ts;
+            acc[2] += n * o.eps;
+            acc[3] += n * o.dfdn - o.f;
+            acc[4] += o.w[0] * gr[0] + o.w[1] * gr[1] + o.w[2] * gr[2];
+            acc[5] += n * (o.vxc - o.eps);
+            for (int a = 0; a < 3; ++a) w[a] = o.w[a];
+        } else {
+            const T ph = phit[i];
+            const T n = ph * ph;
+            const T gg = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+            const PwOut<T> o = pw_point_native<T>(fp, tab, temp, n, gg, xc);
+            vpart[i] = o.dfdn + o.vxc;
+            acc[0] += o.f;
+            acc[1] += o.ts;
+            acc[2] += n * o.eps;
+            acc[3] += n * o.dfdn - o.f;
+            acc[4] += o.wc * gg;
+            acc[5] += n * (o.vxc - o.eps);
+            for (int a = 0; a < 3; ++a) w[a] = o.wc * gr[a];
+        }
+        if constexpr (STRESS) {
+            sacc[0] += w[0] * gr[0];
+            sacc[1] += w[1] * gr[1];
+            sacc[2] += w[2] * gr[2];
+            sacc[3] += w[0] * gr[1];
+            sacc[4] += w[0] * gr[2];
+            sacc[5] += w[1] * gr[2];
+        }
+        if constexpr (TRI) {
+            d0[i] = str<PR>(bm[0] * w[0] + bm[1] * w[1] + bm[2] * w[2]);
+            d1[i] = str<PR>(bm[3] * w[0] + bm[4] * w[1] + bm[5] * w[2]);
+            d2[i] = str<PR>(bm[6] * w[0] + bm[7] * w[1] + bm[8] * w[2]);
+        } else {
+            d0[i] = str<PR>(w[0]);
+            d1[i] = str<PR>(w[1]);
+            d2[i] = str<PR>(w[2]);
+        }
     }
-    CC *Y = fft_lines<CC, true>(D, A, ax, t.ncol, 1, g.tk, true);
-    store_tile<PR>(w0, t, nx, Y);
+    double tot[6];
+    block_total<6, PR>(acc, tot);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 6; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
+    if constexpr (STRESS) {
+        __syncthreads();
+        block_total<6, PR>(sacc, tot);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 6; ++q) part[(size_t)(6 + q) * gridDim.x + blockIdx.x] = tot[q];
+    }
+}
+
+// Final stage of a GGA evaluation: v = v_HL - d_z U_z + v_part - div, with
+// v_HL from the half spectrum dspec (Hartree + LPP after the inverse x and
+// y passes), d_z U_z from the pair-packed lines of U_z (forward z transform,
+// times i kt ds_z, added to the packed spectrum of v_HL, so one inverse
+// transform serves both) and div = d_x U_x + d_y U_y.  div may alias vout
+// (each point is read before it is written, by the same thread).  Partials
+// (as k_zfinal's GGA form): rows 0..5 zero, then sum phi^2 v, sum phi^2,
+// sum 2 phi v dphi/dtheta.
+template <typename PR>
+__global__ void k_zfinal_g(GridInfo g, FftAxis az, int P, const typename KT<PR>::C *__restrict__ dspec,
+                           const typename KT<PR>::T *__restrict__ uz, const typename KT<PR>::T *__restrict__ vpart,
+                           const typename KT<PR>::T *div, const typename KT<PR>::T *__restrict__ phit,
+                           const typename KT<PR>::T *__restrict__ phi, const typename KT<PR>::T *__restrict__ dhat,
+                           typename KT<PR>::T c, typename KT<PR>::T s, const void *__restrict__ cs,
+                           typename KT<PR>::T *vout, double *__restrict__ part)
+{
+    typedef typename KT<PR>::T T;
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::CC CC;
+    typedef typename AccK<PR>::type AC;
+    if (cs != nullptr) {
+        c = reinterpret_cast<const T *>(cs)[0];
+        s = reinterpret_cast<const T *>(cs)[1];
+    }
+    const R cr = scal<PR>(c), sr = scal<PR>(s);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nz = g.nz, K = g.K;
+    CC *A = reinterpret_cast<CC *>(smraw);
+    CC *B = A + P * nz;
+    CC *D = B + P * nz;
+    const long long npairs = (long long)g.nx * g.ny / 2;
+    const long long p0 = (long long)blockIdx.x * P;
+    const int nl = (int)min((long long)P, npairs - p0);
+    const long long obase = 2 * p0 * K;
+    const long long rbase = 2 * p0 * nz;
+    pack_c2r<PR>(dspec, obase, nl, nz, K, A);
+    {
+        RowCol rc(nz);
+        for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x, rc.next()) {
+            R *dst = reinterpret_cast<R *>(&B[(rc.r >> 1) * nz + rc.c]);
+            dst[rc.r & 1] = ldr<PR>(uz[rbase + i]);
+        }
+    }
+    __syncthreads();
+    CC *Z = fft_lines<CC, false>(B, D, az, nl, nz, 1, false);
+    const R sz = gcst<PR>(g.ds[2], g.dsf[2], g.ds2[2]);
+    {
+        RowCol re(nz);
+        for (int i = threadIdx.x; i < nl * nz; i += blockDim.x, re.next()) {
+            const CC d = times_ik<CC, R>(Z[i], re.c, nz, sz);
+            A[i] = cmk<CC>(A[i].x - d.x, A[i].y - d.y);
+        }
+    }
+    __syncthreads();
+    CC *X = fft_lines<CC, true>(A, Z, az, nl, nz, 1, false);
+    AC acc[9] = {AC(0), AC(0), AC(0), AC(0), AC(0), AC(0), AC(0), AC(0), AC(0)};
+    RowCol rc(nz);
+    for (int i = threadIdx.x; i < 2 * nl * nz; i += blockDim.x, rc.next()) {
+        const CC d = X[(rc.r >> 1) * nz + rc.c];
+        const R dr = (rc.r & 1) ? d.y : d.x;
+        const R ph = ldr<PR>(phit[rbase + i]);
+        const R n = ph * ph;
+        const R v = ldr<PR>(vpart[rbase + i]) + dr - ldr<PR>(div[rbase + i]);
+        vout[rbase + i] = str<PR>(v);
+        acc[6] += n * v;
+        acc[7] += n;
+        if (dhat != nullptr) {
+            const R dphi = -sr * ldr<PR>(phi[rbase + i]) + cr * ldr<PR>(dhat[rbase + i]);
+            acc[8] += R(2) * (ph * v) * dphi;
+        }
+    }
+    double tot[9];
+    block_total<9, PR>(acc, tot);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 9; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
 }
 
 int zpairs_per_block(const GridInfo &g)
@@ -849,48 +931,77 @@ int threads_for(int work)
 // ---------------------------------------------------------------- launchers
 template <typename T>
 void launch_zfwd(const GridInfo &g, const FftAxis &az, int mode, const T *in, const T *phi,
-                 const T *dhat, T c, T s, const void *cs, T *phit, cplx<T> *out, cudaStream_t st)
+                 const T *dhat, T c, T s, const void *cs, T *phit, cplx<T> *out, cudaStream_t st, T *dz)
 {
     int P = zpairs_light(g);
     long long npairs = (long long)g.nx * g.ny / 2;
     int blocks = (int)((npairs + P - 1) / P);
     size_t sm = 2 * (size_t)P * g.nz * sizeof(cplx<T>);
     int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
-#define CALL(PR)                                                                                          \
-    if (mode == 0) k_zfwd<PR, 0><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out);     \
-    else if (mode == 1) k_zfwd<PR, 1><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out); \
-    else k_zfwd<PR, 2><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out)
+#define CALL(PR)                                                                                              \
+    if (mode == 0) k_zfwd<PR, 0><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out, dz);     \
+    else if (mode == 1) k_zfwd<PR, 1><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out, dz); \
+    else k_zfwd<PR, 2><<<blocks, th, sm, st>>>(g, az, P, in, phi, dhat, c, s, cs, phit, out, dz)
     OFDFT_DISPATCH(T, g, CALL);
 #undef CALL
+}
+
+namespace {
+template <typename PR>
+void dline_call(const GridInfo &g, const FftAxis &fa, int axis, int mode, int acc, const typename KT<PR>::T *in,
+                typename KT<PR>::T *out, int blocks, int th, size_t sm, cudaStream_t st)
+{
+    if (axis == 0) {
+        if (mode == 0) k_dline<PR, 0, 0, 0><<<blocks, th, sm, st>>>(g, fa, in, out);
+        else if (acc == 0) k_dline<PR, 0, 1, 0><<<blocks, th, sm, st>>>(g, fa, in, out);
+        else k_dline<PR, 0, 1, 1><<<blocks, th, sm, st>>>(g, fa, in, out);
+    } else {
+        if (mode == 0) k_dline<PR, 1, 0, 0><<<blocks, th, sm, st>>>(g, fa, in, out);
+        else if (acc == 0) k_dline<PR, 1, 1, 0><<<blocks, th, sm, st>>>(g, fa, in, out);
+        else k_dline<PR, 1, 1, 1><<<blocks, th, sm, st>>>(g, fa, in, out);
+    }
+}
+}  // namespace
+
+template <typename T>
+void launch_dline(const GridInfo &g, const FftAxis &fa, int axis, int mode, int acc, const T *in, T *out,
+                  cudaStream_t st)
+{
+    const int n = axis == 0 ? g.nx : g.ny;
+    const int blocks = pair_tiles_of(g, axis);
+    const size_t sm = 2 * (size_t)n * g.tk * sizeof(cplx<T>);
+    const int th = g.xth > 0 ? g.xth : threads_for(n * g.tk / 2);
+#define CALL(PR) dline_call<PR>(g, fa, axis, mode, acc, in, out, blocks, th, sm, st)
+    OFDFT_DISPATCH(T, g, CALL);
+#undef CALL
+}
+
+// Blocks of the pointwise kernel: one point a thread, at most one block per
+// z line pair (the partial-sum rows hold nx ny / 2 columns).
+int pw_blocks(const GridInfo &g, int th)
+{
+    const long long npairs = (long long)g.nx * g.ny / 2;
+    return (int)std::min<long long>((g.N + th - 1) / th, npairs);
 }
 
 template <typename T>
-int launch_zgga(const GridInfo &g, const FftAxis &az, cplx<T> *g0, cplx<T> *g1, cplx<T> *g2,
-                const T *phit, T temp, const FuncParams &fp, const T *tab, int xc, T *vpart,
-                double *part, cudaStream_t st)
+int launch_pw(const GridInfo &g, T *d0, T *d1, T *d2, const T *phit, T temp, const FuncParams &fp, const T *tab,
+              int xc, T *vpart, double *part, bool stress, cudaStream_t st)
 {
-    int P = zpairs_per_block(g);
-    long long npairs = (long long)g.nx * g.ny / 2;
-    int blocks = (int)((npairs + P - 1) / P);
-    size_t sm = 6 * (size_t)P * g.nz * sizeof(cplx<T>);
-    int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
-#define CALL(PR) k_zgga<PR, false><<<blocks, th, sm, st>>>(g, az, P, g0, g1, g2, phit, temp, fp, tab, xc, vpart, part)
+    const int th = 128;
+    const int blocks = pw_blocks(g, th);
+#define CALL(PR)                                                                                              \
+    if (stress) {                                                                                             \
+        if constexpr (!std::is_same<PR, float>::value) {                                                      \
+            if (g.tri) k_pw<PR, true, true><<<blocks, th, 0, st>>>(g, d0, d1, d2, phit, temp, fp, tab, xc, vpart, part); \
+            else k_pw<PR, true, false><<<blocks, th, 0, st>>>(g, d0, d1, d2, phit, temp, fp, tab, xc, vpart, part);     \
+        }                                                                                                     \
+    } else if (g.tri) {                                                                                       \
+        k_pw<PR, false, true><<<blocks, th, 0, st>>>(g, d0, d1, d2, phit, temp, fp, tab, xc, vpart, part);    \
+    } else {                                                                                                  \
+        k_pw<PR, false, false><<<blocks, th, 0, st>>>(g, d0, d1, d2, phit, temp, fp, tab, xc, vpart, part);   \
+    }
     OFDFT_DISPATCH(T, g, CALL);
-#undef CALL
-    return blocks;
-}
-
-int launch_zgga_stress(const GridInfo &g, const FftAxis &az, double2 *g0, double2 *g1, double2 *g2,
-                       const double *phit, double temp, const FuncParams &fp, const double *tab, int xc,
-                       double *vpart, double *part, cudaStream_t st)
-{
-    int P = zpairs_per_block(g);
-    long long npairs = (long long)g.nx * g.ny / 2;
-    int blocks = (int)((npairs + P - 1) / P);
-    size_t sm = 6 * (size_t)P * g.nz * sizeof(double2);
-    int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
-#define CALL(PR) k_zgga<PR, true><<<blocks, th, sm, st>>>(g, az, P, g0, g1, g2, phit, temp, fp, tab, xc, vpart, part)
-    OFDFT_DISPATCH(double, g, CALL);
 #undef CALL
     return blocks;
 }
@@ -919,6 +1030,23 @@ int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T>
 }
 
 template <typename T>
+int launch_zfinal_gga(const GridInfo &g, const FftAxis &az, const cplx<T> *dspec, const T *uz, const T *vpart,
+                      const T *div, const T *phit, const T *phi, const T *dhat, T c, T s, const void *cs, T *vout,
+                      double *part, cudaStream_t st)
+{
+    int P = zpairs_light(g);
+    long long npairs = (long long)g.nx * g.ny / 2;
+    int blocks = (int)((npairs + P - 1) / P);
+    size_t sm = 3 * (size_t)P * g.nz * sizeof(cplx<T>);
+    int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
+#define CALL(PR) \
+    k_zfinal_g<PR><<<blocks, th, sm, st>>>(g, az, P, dspec, uz, vpart, div, phit, phi, dhat, c, s, cs, vout, part)
+    OFDFT_DISPATCH(T, g, CALL);
+#undef CALL
+    return blocks;
+}
+
+template <typename T>
 void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data, int nfields,
                   long long fstride, cudaStream_t st)
 {
@@ -930,21 +1058,6 @@ void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data,
     else k_ypass<PR, false><<<grid, th, sm, st>>>(g, ay, data, fstride)
     OFDFT_DISPATCH(T, g, CALL);
 #undef CALL
-}
-
-template <typename T>
-int launch_xgrad(const GridInfo &g, const FftAxis &ax, cplx<T> *nspec, const cplx<T> *vext,
-                 cplx<T> *g0, cplx<T> *g1, cplx<T> *g2, double *part, cudaStream_t st)
-{
-    int blocks = tiles_of(g, true);
-    size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
-    int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
-#define CALL(PR)                                                                         \
-    if (g.tri) k_xgrad<PR, true><<<blocks, th, sm, st>>>(g, ax, nspec, vext, g0, g1, g2, part); \
-    else k_xgrad<PR, false><<<blocks, th, sm, st>>>(g, ax, nspec, vext, g0, g1, g2, part)
-    OFDFT_DISPATCH(T, g, CALL);
-#undef CALL
-    return blocks;
 }
 
 template <typename T>
@@ -962,28 +1075,14 @@ int launch_xhl(const GridInfo &g, const FftAxis &ax, cplx<T> *spec, const cplx<T
     return blocks;
 }
 
-template <typename T>
-void launch_xdiv(const GridInfo &g, const FftAxis &ax, const cplx<T> *nG, const cplx<T> *vext,
-                 cplx<T> *w0, const cplx<T> *w1, const cplx<T> *w2, cudaStream_t st)
-{
-    int blocks = tiles_of(g, true);
-    size_t sm = 3 * (size_t)g.nx * g.tk * sizeof(cplx<T>);
-    int th = g.xth > 0 ? g.xth : threads_for(g.nx * g.tk / 2);
-#define CALL(PR)                                                                   \
-    if (g.tri) k_xdiv<PR, true><<<blocks, th, sm, st>>>(g, ax, nG, vext, w0, w1, w2); \
-    else k_xdiv<PR, false><<<blocks, th, sm, st>>>(g, ax, nG, vext, w0, w1, w2)
-    OFDFT_DISPATCH(T, g, CALL);
-#undef CALL
-}
-
 int xpass_blocks(const GridInfo &g) { return tiles_of(g, true); }
 
 size_t field_smem_max(const GridInfo &g, size_t csize)
 {
-    int P = zpairs_per_block(g);
-    size_t z = 6 * (size_t)P * g.nz * csize;
+    int P = zpairs_light(g);
+    size_t z = 3 * (size_t)P * g.nz * csize;
     size_t y = 2 * (size_t)g.ny * g.tk * csize;
-    size_t x = 3 * (size_t)g.nx * g.tk * csize;
+    size_t x = 2 * (size_t)g.nx * g.tk * csize;
     size_t m = z > y ? z : y;
     return m > x ? m : x;
 }
@@ -995,21 +1094,21 @@ template <typename PR> cudaError_t smem_limits(int b)
         cudaFuncSetAttribute(k_zfwd<PR, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_zfwd<PR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_zfwd<PR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_zgga<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_zfinal<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_zfinal<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_zfinal_g<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_ypass<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_ypass<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_xgrad<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_xhl<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_xdiv<PR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_xgrad<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_xhl<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_xdiv<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)};
+        cudaFuncSetAttribute(k_dline<PR, 0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline<PR, 0, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline<PR, 0, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline<PR, 1, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline<PR, 1, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline<PR, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return x;
-    if constexpr (!std::is_same<PR, float>::value)   // the stress variant (FP64 sets only)
-        return cudaFuncSetAttribute(k_zgga<PR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     return cudaSuccess;
 }
 }  // namespace
@@ -1023,23 +1122,22 @@ template <typename T> cudaError_t set_field_smem_limits(size_t bytes)
 
 #define OFDFT_INST(T)                                                                              \
     template void launch_zfwd<T>(const GridInfo &, const FftAxis &, int, const T *, const T *,     \
-                                 const T *, T, T, const void *, T *, cplx<T> *, cudaStream_t); \
-    template int launch_zgga<T>(const GridInfo &, const FftAxis &, cplx<T> *, cplx<T> *,           \
-                                cplx<T> *, const T *, T, const FuncParams &, const T *, int, T *, \
-                                double *, cudaStream_t);                                          \
+                                 const T *, T, T, const void *, T *, cplx<T> *, cudaStream_t, T *); \
+    template void launch_dline<T>(const GridInfo &, const FftAxis &, int, int, int, const T *, T *, \
+                                  cudaStream_t);                                                  \
+    template int launch_pw<T>(const GridInfo &, T *, T *, T *, const T *, T, const FuncParams &,   \
+                              const T *, int, T *, double *, bool, cudaStream_t);                 \
     template int launch_zfinal<T>(const GridInfo &, const FftAxis &, bool, const cplx<T> *,        \
                                   const T *, const T *, const T *, const T *, T, T, const void *,   \
                                   T, const FuncParams &, const T *, int, T *, double *,            \
                                   cudaStream_t);                                                  \
+    template int launch_zfinal_gga<T>(const GridInfo &, const FftAxis &, const cplx<T> *, const T *, \
+                                      const T *, const T *, const T *, const T *, const T *, T, T,  \
+                                      const void *, T *, double *, cudaStream_t);                 \
     template void launch_ypass<T>(const GridInfo &, const FftAxis &, bool, cplx<T> *, int,         \
                                   long long, cudaStream_t);                                       \
-    template int launch_xgrad<T>(const GridInfo &, const FftAxis &, cplx<T> *, const cplx<T> *,    \
-                                 cplx<T> *, cplx<T> *, cplx<T> *, double *, cudaStream_t);        \
     template int launch_xhl<T>(const GridInfo &, const FftAxis &, cplx<T> *, const cplx<T> *,      \
                                cplx<T> *, int, double *, cudaStream_t);                          \
-    template void launch_xdiv<T>(const GridInfo &, const FftAxis &, const cplx<T> *,               \
-                                 const cplx<T> *, cplx<T> *, const cplx<T> *, const cplx<T> *,    \
-                                 cudaStream_t);                                                   \
     template cudaError_t set_field_smem_limits<T>(size_t);
 
 OFDFT_INST(double)

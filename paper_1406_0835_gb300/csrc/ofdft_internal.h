@@ -102,6 +102,12 @@ struct GridInfo {
     int tri;
     double Am[9], Bm[9], Ainv[9];
     float Bmf[9], Bm2[9][2];
+    // derivative passes: multiplier scale per grid axis j including the 1/n_j
+    // of the 1-D inverse transform: b_j / n_j in an orthorhombic cell (the
+    // pass yields the Cartesian derivative), 1 / n_j in a general cell (the
+    // lattice-direction derivative, combined with Bm pointwise)
+    double ds[3];
+    float dsf[3], ds2[3][2];
 };
 
 // Derived quantities of a grid (call after setting sizes, cell and rc).
@@ -155,6 +161,14 @@ inline void grid_reciprocal(GridInfo &g)
     g.bzf = (float)g.bz;
     g.invNf = (float)g.invN;
     g.hrf = (float)g.hr;
+    const int na[3] = {g.nx, g.ny, g.nz};
+    const double ba[3] = {g.bx, g.by, g.bz};
+    for (int j = 0; j < 3; ++j) {
+        g.ds[j] = (g.tri ? 1.0 : ba[j]) / (double)na[j];
+        g.dsf[j] = (float)g.ds[j];
+        g.ds2[j][0] = (float)g.ds[j];
+        g.ds2[j][1] = (float)(g.ds[j] - (double)g.ds2[j][0]);
+    }
 }
 
 // The FP64 or FP32 copy of a grid constant, for kernels templated on A.

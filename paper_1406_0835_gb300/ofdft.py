@@ -369,7 +369,7 @@ def ofdft_sizes(ctx):
     return N.value, nat.value
 
 
-TIMERS = {"zgga": 1, "xgrad": 2, "xdiv": 3, "ypass": 4, "zfwd": 5, "zfinal": 6, "xhl": 7}
+TIMERS = {"pw": 1, "dline": 2, "ypass": 4, "zfwd": 5, "zfinal": 6, "xhl": 7}
 
 
 def ofdft_timer_select(ctx, which):
