@@ -195,13 +195,12 @@ template <typename PR> struct RecipB<PR, true> {
     }
 };
 
-// Pointwise functional of the double-float z passes: the double-float
-// routine, and binary64 outside its domain.  n and gr[3] in double-float.
-__device__ __forceinline__ PwF2 pw_dd(const FuncParams &fp, const double *__restrict__ tab, ff::f2 tcoef,
-                                      double temp, ff::f2 n, const ff::f2 *gr, int xc)
+// The binary64 routine for points outside the double-float domain, out of
+// line so that its registers do not count against the common path.
+__device__ __noinline__ PwF2 pw_dd_fallback(const FuncParams &fp, const double *__restrict__ tab, double temp,
+                                            ff::f2 n, const ff::f2 *gr, int xc)
 {
     PwF2 o;
-    if (pw_core_f2(fp, reinterpret_cast<const ff::f2 *>(tab + kTfSize), tcoef, n, gr, xc, o)) return o;
     const double nd = ff::to_double(n);
     const double gd[3] = {ff::to_double(gr[0]), ff::to_double(gr[1]), ff::to_double(gr[2])};
     PwOut<double> b = pw_point_native<double>(fp, tab, temp, nd, gd[0] * gd[0] + gd[1] * gd[1] + gd[2] * gd[2], xc);
@@ -212,6 +211,16 @@ __device__ __forceinline__ PwF2 pw_dd(const FuncParams &fp, const double *__rest
     o.vxc = ff::f2(b.vxc);
     for (int a = 0; a < 3; ++a) o.w[a] = ff::f2(b.wc * gd[a]);
     return o;
+}
+
+// Pointwise functional of the double-float kernels: the double-float
+// routine, and binary64 outside its domain.  n and gr[3] in double-float.
+__device__ __forceinline__ PwF2 pw_dd(const FuncParams &fp, const double *__restrict__ tab, ff::f2 tcoef,
+                                      double temp, ff::f2 n, const ff::f2 *gr, int xc)
+{
+    PwF2 o;
+    if (pw_core_f2(fp, reinterpret_cast<const ff::f2 *>(tab + kTfSize), tcoef, n, gr, xc, o)) return o;
+    return pw_dd_fallback(fp, tab, temp, n, gr, xc);
 }
 
 // (row, column) of the element indices threadIdx.x, threadIdx.x +
@@ -726,8 +735,17 @@ __global__ void k_dline(GridInfo g, FftAxis fa, const typename KT<PR>::T *__rest
 // Partials: F_s, TS, F_xc, sum(n df/dn - f), sum W.grad n,
 // sum n(v_xc - eps_xc); with STRESS also sum W_a d_b n for ab = xx, yy,
 // zz, xy, xz, yz (the gradient part of Eq. (stressTF_b)) in rows 6..11.
+// Threads per block of the pointwise kernel and the blocks per SM its
+// register budget is sized for (launch bounds).
+#ifndef OFDFT_PW_THREADS
+#define OFDFT_PW_THREADS 128
+#endif
+#ifndef OFDFT_PW_MINB
+#define OFDFT_PW_MINB 4
+#endif
+
 template <typename PR, bool STRESS, bool TRI>
-__global__ void k_pw(GridInfo g, typename KT<PR>::T *__restrict__ d0, typename KT<PR>::T *__restrict__ d1,
+__global__ void __launch_bounds__(OFDFT_PW_THREADS, OFDFT_PW_MINB) k_pw(GridInfo g, typename KT<PR>::T *__restrict__ d0, typename KT<PR>::T *__restrict__ d1,
                      typename KT<PR>::T *__restrict__ d2, const typename KT<PR>::T *__restrict__ phit,
                      typename KT<PR>::T temp, FuncParams fp, const typename KT<PR>::T *__restrict__ tab, int xc,
                      typename KT<PR>::T *__restrict__ vpart, double *__restrict__ part)
@@ -988,7 +1006,7 @@ template <typename T>
 int launch_pw(const GridInfo &g, T *d0, T *d1, T *d2, const T *phit, T temp, const FuncParams &fp, const T *tab,
               int xc, T *vpart, double *part, bool stress, cudaStream_t st)
 {
-    const int th = 128;
+    const int th = OFDFT_PW_THREADS;
     const int blocks = pw_blocks(g, th);
 #define CALL(PR)                                                                                              \
     if (stress) {                                                                                             \
