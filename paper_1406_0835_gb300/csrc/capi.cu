@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <tuple>
 #include <mutex>
@@ -101,6 +102,12 @@ struct ofdft_ctx {
     int timer_id = 0;
     std::vector<cudaEvent_t> tev;
     size_t tev_used = 0;
+    // batched form: this context's identity and launch-shape epoch, and the
+    // executable graph of the last batch it led (one branch per instance)
+    unsigned long long uid = 0;
+    unsigned shape_epoch = 0;
+    std::vector<unsigned long long> batch_key;
+    cudaGraphExec_t batch_exec = nullptr;
 };
 
 namespace {
@@ -595,31 +602,18 @@ ofdft_status add_while(ofdft_ctx *c, cudaStream_t stream, cudaGraphConditionalHa
     return OFDFT_OK;
 }
 
-// Capture the whole minimisation of field set f into an executable graph:
-//   prologue; WHILE(outer) { direction; WHILE(ls) { trial }; update }
-// Capture runs on the private stream cap2 (the context's stream may be the
-// legacy stream, which cannot be captured); the bodies of the two loops are
-// captured one after the other into the graphs their nodes own.
-template <typename T> ofdft_status capture_graph(ofdft_ctx *c, FieldSet &f, cudaGraph_t *whole)
+// Fill the body of a minimisation's outer WHILE node (field set f, outer
+// handle):  direction; WHILE(ls) { trial }; update.  The bodies of the two
+// loops are captured one after the other into the graphs their nodes own.
+template <typename T>
+ofdft_status capture_body(ofdft_ctx *c, FieldSet &f, cudaGraphConditionalHandle outer, cudaGraph_t body)
 {
     cudaStream_t cs = c->cap2;
-    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t gr = nullptr;
-    cudaGraphConditionalHandle outer = 0, ls = 0;
-    cudaGraph_t body = nullptr, ls_body = nullptr;
+    cudaGraphConditionalHandle ls = 0;
+    cudaGraph_t ls_body = nullptr;
     ofdft_status r = OFDFT_OK;
-    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &gr, nullptr, nullptr, nullptr);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&outer, gr, 0, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) r = fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph handle");
-    if (r == OFDFT_OK) r = enqueue_prologue<T>(c, f, outer, 1);
-    if (r == OFDFT_OK) r = add_while(c, cs, outer, &body);
-    e = cudaStreamEndCapture(cs, whole);
-    if (r != OFDFT_OK) return r;
-    if (e != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph capture");
-
     CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    e = cudaGraphConditionalHandleCreate(&ls, body, 0, cudaGraphCondAssignDefault);
+    cudaError_t e = cudaGraphConditionalHandleCreate(&ls, body, 0, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) r = fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph handle");
     if (r == OFDFT_OK) r = enqueue_direction<T>(c, f, ls, 1);
     if (r == OFDFT_OK) r = add_while(c, cs, ls, &ls_body);
@@ -634,6 +628,42 @@ template <typename T> ofdft_status capture_graph(ofdft_ctx *c, FieldSet &f, cuda
     if (r != OFDFT_OK) return r;
     if (e != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph capture (line search)");
     return OFDFT_OK;
+}
+
+// Enqueue (on the capturing stream c->cap2) the prologue of field set f's
+// minimisation and its outer WHILE node, whose handle is created on graph
+// gr; returns the handle and the node's body graph.
+template <typename T>
+ofdft_status capture_outer(ofdft_ctx *c, FieldSet &f, cudaGraph_t gr, cudaGraphConditionalHandle *outer,
+                           cudaGraph_t *body)
+{
+    cudaError_t e = cudaGraphConditionalHandleCreate(outer, gr, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph handle");
+    ofdft_status r = enqueue_prologue<T>(c, f, *outer, 1);
+    if (r == OFDFT_OK) r = add_while(c, c->cap2, *outer, body);
+    return r;
+}
+
+// Capture the whole minimisation of field set f into a graph:
+//   prologue; WHILE(outer) { direction; WHILE(ls) { trial }; update }
+// Capture runs on the private stream cap2 (the context's stream may be the
+// legacy stream, which cannot be captured).
+template <typename T> ofdft_status capture_graph(ofdft_ctx *c, FieldSet &f, cudaGraph_t *whole)
+{
+    cudaStream_t cs = c->cap2;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t gr = nullptr;
+    cudaGraphConditionalHandle outer = 0;
+    cudaGraph_t body = nullptr;
+    ofdft_status r = OFDFT_OK;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &gr, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) r = fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph capture info");
+    if (r == OFDFT_OK) r = capture_outer<T>(c, f, gr, &outer, &body);
+    e = cudaStreamEndCapture(cs, whole);
+    if (r != OFDFT_OK) return r;
+    if (e != cudaSuccess) return fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "graph capture");
+    return capture_body<T>(c, f, outer, body);
 }
 
 template <typename T> ofdft_status build_graph(ofdft_ctx *c, FieldSet &f)
@@ -661,7 +691,7 @@ template <typename T> ofdft_status build_graph(ofdft_ctx *c, FieldSet &f)
 
 // Field set k's CG configuration is staged in pinned memory (one buffer per
 // set, so the two copies of a mixed-precision minimisation never race).
-ofdft_status write_config(ofdft_ctx *c, int k, double gtol, int maxit, int stagnate)
+ofdft_status write_config(ofdft_ctx *c, int k, double gtol, int maxit, int stagnate, cudaStream_t on = nullptr)
 {
     CgState *h = c->cfg_h[k];
     memset(h, 0, sizeof(CgState));
@@ -680,7 +710,7 @@ ofdft_status write_config(ofdft_ctx *c, int k, double gtol, int maxit, int stagn
     h->max_ls = 20;
     h->stagnate = stagnate;
     h->status = OFDFT_OK;
-    CK(cudaMemcpyAsync(c->f[k].cs, h, sizeof(CgState), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->f[k].cs, h, sizeof(CgState), cudaMemcpyHostToDevice, on ? on : c->st));
     return OFDFT_OK;
 }
 
@@ -767,6 +797,8 @@ long long graph_launches(const ofdft_ctx *c, const CgState &h)
            (long long)(h.nevals - 1) * (eval_kernel_count(c) + 1);
 }
 
+ofdft_status finish_minimize(ofdft_ctx *c, bool graph, ofdft_stats &stats, EvalScalars &es);
+
 // Wait for the minimisation started last; fill stats and the energies.
 ofdft_status minimize_wait(ofdft_ctx *c, ofdft_stats &stats, EvalScalars &es)
 {
@@ -775,25 +807,142 @@ ofdft_status minimize_wait(ofdft_ctx *c, ofdft_stats &stats, EvalScalars &es)
     c->pending = false;
     CK(cudaEventSynchronize(c->done_ev));
     CK(cudaGetLastError());
+    return finish_minimize(c, c->pend_graph, stats, es);
+}
+
+// Statistics and energies of a finished minimisation from the final CG
+// states in st_h (graph: count the launches the graph made).
+ofdft_status finish_minimize(ofdft_ctx *c, bool graph, ofdft_stats &stats, EvalScalars &es)
+{
+    stats = ofdft_stats{};
     const bool mixed = c->precision == OFDFT_MIXED;
     const CgState &h = *c->st_h[0];
     stats.iterations = h.it;
     stats.evaluations = h.nevals;
     stats.gnorm = h.gnorm;
     stats.status = h.status == kCgStagnated ? OFDFT_OK : h.status;
-    if (c->pend_graph) c->launches += graph_launches(c, h);
+    if (graph) c->launches += graph_launches(c, h);
     if (mixed) {
         const CgState &l = *c->st_h[1];
         stats.iterations += l.it;
         stats.evaluations_lo = l.nevals;
         stats.evaluations += l.nevals;
-        if (c->pend_graph) c->launches += graph_launches(c, l);
+        if (graph) c->launches += graph_launches(c, l);
     }
     es = unpack_sums(h.ev_acc, c->fp.kind == 0);
     if (h.status == OFDFT_ENUMERIC) return fail(c, OFDFT_ENUMERIC, "non-finite energy, gradient or norm");
     fill_energy(c, es, c->last);
     c->last_valid = true;
     return stats.status == OFDFT_OK ? OFDFT_OK : (ofdft_status)stats.status;
+}
+
+// ------------------------------------------------------------ batched form
+// Every instance's minimisation (for a mixed context: FP32 CG, conversion,
+// FP64 CG) as an independent root branch of one graph, so a batch is one
+// graph launch.  Each branch is captured on its context's private stream
+// into the common graph; the loop bodies are the same captures as a single
+// minimisation's, so every instance takes exactly the steps it takes alone.
+ofdft_status build_batch_graph(int n, ofdft_ctx *const *ctxs, cudaGraphExec_t *out)
+{
+    ofdft_ctx *c0 = ctxs[0];
+    cudaGraph_t G = nullptr;
+    if (cudaGraphCreate(&G, 0) != cudaSuccess) return fail(c0, OFDFT_EDEVICE, "cudaGraphCreate failed");
+    ofdft_status r = OFDFT_OK;
+    for (int i = 0; i < n && r == OFDFT_OK; ++i) {
+        ofdft_ctx *c = ctxs[i];
+        cudaStream_t user = c->st;
+        const long long before = c->launches;
+        const bool dbg_saved = c->debug_sync;
+        c->st = c->cap2;
+        c->debug_sync = false;
+        const bool mixed = c->precision == OFDFT_MIXED;
+        cudaGraphConditionalHandle o0 = 0, o1 = 0;
+        cudaGraph_t b0 = nullptr, b1 = nullptr;
+        cudaGraph_t cap = G;
+        cudaError_t e = cudaStreamBeginCaptureToGraph(c->cap2, G, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) r = fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "batch capture");
+        if (r == OFDFT_OK && mixed) {
+            launch_convert<double, float>(c->g.N, (const double *)c->f[0].phi, (float *)c->f[1].phi, c->st);
+            r = capture_outer<float>(c, c->f[1], G, &o1, &b1);
+            if (r == OFDFT_OK)
+                launch_convert<float, double>(c->g.N, (const float *)c->f[1].phi, (double *)c->f[0].phi, c->st);
+        }
+        if (r == OFDFT_OK) r = capture_outer<double>(c, c->f[0], G, &o0, &b0);
+        if (e == cudaSuccess) {
+            e = cudaStreamEndCapture(c->cap2, &cap);
+            if (e != cudaSuccess && r == OFDFT_OK) r = fail(c, OFDFT_EDEVICE, cudaGetErrorString(e), "batch capture");
+        }
+        if (r == OFDFT_OK && mixed) r = capture_body<float>(c, c->f[1], o1, b1);
+        if (r == OFDFT_OK) r = capture_body<double>(c, c->f[0], o0, b0);
+        c->st = user;
+        c->debug_sync = dbg_saved;
+        c->launches = before;
+        if (r != OFDFT_OK && c != c0) c0->err = c->err;
+    }
+    if (r == OFDFT_OK) {
+        cudaError_t e = cudaGraphInstantiate(out, G, 0);
+        if (e != cudaSuccess) {
+            *out = nullptr;
+            r = fail(c0, OFDFT_EDEVICE, cudaGetErrorString(e), "batch graph instantiation");
+        }
+    }
+    cudaGraphDestroy(G);
+    return r;
+}
+
+// One graph launch for the whole batch on the first context's stream, after
+// the work already queued on every context's stream; the contexts' streams
+// then wait for it.  The executable graph is kept by the first context and
+// reused while the same contexts (same launch shapes) come in the same order.
+ofdft_status batch_graph_minimize(int n, ofdft_ctx *const *ctxs, double gtol, int maxit, ofdft_energy *E,
+                                  ofdft_stats *stats)
+{
+    ofdft_ctx *c0 = ctxs[0];
+    ofdft_ctx *const c = c0;   // device errors are reported on the first context
+    std::vector<unsigned long long> key;
+    for (int i = 0; i < n; ++i) {
+        key.push_back(ctxs[i]->uid);
+        key.push_back(ctxs[i]->shape_epoch);
+    }
+    if (!c0->batch_exec || c0->batch_key != key) {
+        if (c0->batch_exec) cudaGraphExecDestroy(c0->batch_exec);
+        c0->batch_exec = nullptr;
+        c0->batch_key.clear();
+        ofdft_status r = build_batch_graph(n, ctxs, &c0->batch_exec);
+        if (r != OFDFT_OK) return r;
+        c0->batch_key = key;
+    }
+    cudaStream_t S = c0->st;
+    for (int i = 0; i < n; ++i) {
+        ofdft_ctx *ci = ctxs[i];
+        if (ci != c0) {
+            CK(cudaEventRecord(ci->done_ev, ci->st));
+            CK(cudaStreamWaitEvent(S, ci->done_ev, 0));
+        }
+        if (ci->precision == OFDFT_MIXED && write_config(ci, 1, gtol, maxit, kStagnateIts, S) != OFDFT_OK)
+            return OFDFT_EDEVICE;
+        if (write_config(ci, 0, gtol, maxit, 0, S) != OFDFT_OK) return OFDFT_EDEVICE;
+    }
+    CK(cudaGraphLaunch(c0->batch_exec, S));
+    for (int i = 0; i < n; ++i) {
+        ofdft_ctx *ci = ctxs[i];
+        for (int k = 0; k < (ci->precision == OFDFT_MIXED ? 2 : 1); ++k)
+            CK(cudaMemcpyAsync(ci->st_h[k], ci->f[k].cs, sizeof(CgState), cudaMemcpyDeviceToHost, S));
+    }
+    CK(cudaEventRecord(c0->done_ev, S));
+    for (int i = 1; i < n; ++i) CK(cudaStreamWaitEvent(ctxs[i]->st, c0->done_ev, 0));
+    CK(cudaEventSynchronize(c0->done_ev));
+    CK(cudaGetLastError());
+    ofdft_status first = OFDFT_OK;
+    for (int i = 0; i < n; ++i) {
+        ofdft_stats st{};
+        EvalScalars es;
+        ofdft_status s = finish_minimize(ctxs[i], true, st, es);
+        if (E) E[i] = s == OFDFT_OK || s == OFDFT_ENOCONV ? ctxs[i]->last : ofdft_energy{};
+        if (stats) stats[i] = st;
+        if (s != OFDFT_OK && first == OFDFT_OK) first = s;
+    }
+    return first;
 }
 
 ofdft_status run_minimize(ofdft_ctx *c, double gtol, int maxit, ofdft_stats &stats, EvalScalars &es)
@@ -863,6 +1012,7 @@ void free_ctx(ofdft_ctx *c)
         if (c->cfg_h[k]) cudaFreeHost(c->cfg_h[k]);
         if (c->st_h[k]) cudaFreeHost(c->st_h[k]);
     }
+    if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     if (c->done_ev) cudaEventDestroy(c->done_ev);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -1000,7 +1150,17 @@ struct TuneKey {
 std::mutex g_tune_mu;
 struct Tuned {
     int zP, tk, zth, xth;
+    int mp[3];   // largest power-of-two radix per axis
 };
+
+// Rebuild axis a's Stockham schedule with power-of-two radices up to m (the
+// twiddle tables do not depend on the schedule).
+void set_radix(FieldSet &f, int a, int m)
+{
+    const void *twf = f.ax[a].twf;
+    f.ax[a] = fft_axis(f.ax[a].n, f.ax[a].tw, m);
+    f.ax[a].twf = twf;
+}
 std::map<TuneKey, Tuned> g_tune;
 
 // Mean time of `reps` evaluations of field set f at its current phi.
@@ -1038,8 +1198,10 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
             f.gt.tk = it->second.tk;
             f.gt.zth = it->second.zth;
             f.gt.xth = it->second.xth;
+            for (int a = 0; a < 3; ++a) set_radix(f, a, it->second.mp[a]);
             if (f.graph) cudaGraphExecDestroy(f.graph);
             f.graph = nullptr;
+            c->shape_epoch++;
             return OFDFT_OK;
         }
     }
@@ -1100,10 +1262,29 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
         }
     }
     f.gt = best;
+    // the Stockham schedule of each axis: power-of-two radices up to 8 or
+    // up to 4 (fewer stages against shorter butterflies; same twiddles)
+    int mp[3];
+    for (int a = 0; a < 3; ++a) {
+        best_ms = 1e30f;
+        mp[a] = f.ax[a].mp;
+        for (int m : {4, 8}) {
+            set_radix(f, a, m);
+            float ms;
+            ofdft_status r = time_evals<T>(c, f, reps, ms);
+            if (r != OFDFT_OK) return r;
+            if (ms < best_ms) {
+                best_ms = ms;
+                mp[a] = m;
+            }
+        }
+        set_radix(f, a, mp[a]);
+    }
     if (f.graph) cudaGraphExecDestroy(f.graph);
     f.graph = nullptr;
+    c->shape_epoch++;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = Tuned{best.zP, best.tk, best.zth, best.xth};
+    g_tune[key] = Tuned{best.zP, best.tk, best.zth, best.xth, {mp[0], mp[1], mp[2]}};
     return OFDFT_OK;
 }
 
@@ -1189,6 +1370,8 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     }
     ofdft_ctx *c = new (std::nothrow) ofdft_ctx();
     if (!c) return fail(nullptr, OFDFT_ENOMEM, "host allocation failed");
+    static std::atomic<unsigned long long> next_uid{1};
+    c->uid = next_uid++;
     c->dev = p.device;
     if (cudaSetDevice(c->dev) != cudaSuccess) {
         delete c;
@@ -1380,6 +1563,18 @@ ofdft_status ofdft_batch_minimize(int n, ofdft_ctx *const *ctxs, double gtol, in
     if (n < 0 || (n > 0 && !ctxs)) return fail(nullptr, OFDFT_EINVAL, "bad batch");
     for (int i = 0; i < n; ++i)
         if (!ctxs[i]) return fail(nullptr, OFDFT_EINVAL, "NULL context in batch");
+    if (!(gtol > 0.0) || maxit <= 0) return fail(nullptr, OFDFT_EINVAL, "gtol must be > 0 and maxit > 0");
+    // one graph launch for the batch when every context can take part
+    bool one = n > 0;
+    for (int i = 0; i < n && one; ++i) {
+        ofdft_ctx *c = ctxs[i];
+        one = graphs_on(c) && !c->pending && c->dev == ctxs[0]->dev;
+        for (int j = 0; j < i && one; ++j) one = ctxs[j] != c;
+    }
+    if (one) {
+        cudaSetDevice(ctxs[0]->dev);
+        return batch_graph_minimize(n, ctxs, gtol, maxit, E, stats);
+    }
     ofdft_status first = OFDFT_OK;
     std::vector<char> started(n, 0);
     for (int i = 0; i < n; ++i) {

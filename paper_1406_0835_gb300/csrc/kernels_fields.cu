@@ -738,10 +738,10 @@ __global__ void k_dline(GridInfo g, FftAxis fa, const typename KT<PR>::T *__rest
 // Threads per block of the pointwise kernel and the blocks per SM its
 // register budget is sized for (launch bounds).
 #ifndef OFDFT_PW_THREADS
-#define OFDFT_PW_THREADS 128
+#define OFDFT_PW_THREADS 256
 #endif
 #ifndef OFDFT_PW_MINB
-#define OFDFT_PW_MINB 4
+#define OFDFT_PW_MINB 3
 #endif
 
 template <typename PR, bool STRESS, bool TRI>

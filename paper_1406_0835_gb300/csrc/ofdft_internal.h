@@ -52,6 +52,7 @@ struct FftAxis {
     int tws[kMaxStages];     // twiddle stride n / (ns * rad)
     const void *tw;          // cplx<T>[n]
     const void *twf;         // FP64 sets: the same twiddles as double-float pairs (ff::cf2[n])
+    int mp;                  // the largest power-of-two radix of the schedule (4 or 8)
 };
 
 // Stockham schedule of one axis: radix-8 stages first, then 4, 2, 3, 5;
@@ -75,6 +76,7 @@ inline FftAxis fft_axis(int n, const void *tw, int max_pow2 = 8)
     }
     a.nst = k;
     a.tw = tw;
+    a.mp = max_pow2;
     return a;
 }
 
