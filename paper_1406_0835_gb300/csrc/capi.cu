@@ -250,7 +250,7 @@ EvalScalars unpack_sums(const double *h, bool fttf)
     return es;
 }
 
-int eval_kernel_count(const ofdft_ctx *c) { return c->fp.kind == 0 ? 7 : 13; }
+int eval_kernel_count(const ofdft_ctx *c) { return c->fp.kind == 0 ? 6 : 11; }
 
 // Enqueue one energy + potential evaluation at ph (or, with phi0 and dh, at the
 // trial phi0 cos + dh sin written into ph; angles from csd (two T values in
@@ -348,10 +348,8 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
                                    vout, pC, st);
     }
     DBG("k_zfinal");
-    launch_reduce(pA, nbx, 3, sums, st);
-    if (!fttf) launch_reduce(pB, nbg, 6, sums + 3, st);
-    launch_reduce(pC, nbz, 9, sums + 9, st);
-    DBG("k_reduce");
+    launch_reduce_eval(pA, nbx, pB, nbg, pC, nbz, !fttf, sums, st);
+    DBG("k_reduce_eval");
     c->launches += eval_kernel_count(c);
     if (keep_nG && !fttf) {
         // n(G) for forces and stress: forward z, y, x of n into the second spectrum

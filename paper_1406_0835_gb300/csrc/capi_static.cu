@@ -283,9 +283,7 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
         nbz = launch_zfinal_gga<double>(g, az, s0, d2, vpart, v_dev, ph, nullptr, nullptr, 1.0, 0.0, nullptr,
                                         v_dev, pC, st);
     }
-    launch_reduce(pA, nbx, 3, scal, st);
-    if (!fttf) launch_reduce(pB, nbg, 6, scal + 3, st);
-    launch_reduce(pC, nbz, 9, scal + 9, st);
+    launch_reduce_eval(pA, nbx, pB, nbg, pC, nbz, !fttf, scal, st);
     double h[18];
     SCK(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, st), "scalar read-back failed");
     SCK(cudaStreamSynchronize(st), "stream synchronisation failed");

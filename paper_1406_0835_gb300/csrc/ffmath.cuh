@@ -133,8 +133,11 @@ FF_HD f2 from_double(double d)
 }
 FF_HD double to_double(f2 x) { return widen_bits(x.hi) + widen_bits(x.lo); }
 
-// Compile-time constant split of a double.
-constexpr f2 cst(double d) { return f2(d); }
+// Compile-time constant split of a double: the constexpr local makes the
+// compiler fold the split (a plain call of the constexpr constructor inside
+// an expression may be evaluated at run time, by the FP64 units).
+constexpr f2 cst_split(double d) { return f2(d); }
+#define FFC(d) ([] { constexpr ::ofdft::ff::f2 k_ = ::ofdft::ff::cst_split(d); return k_; }())
 
 FF_HD f2 neg(f2 x) { return {-x.hi, -x.lo}; }
 
@@ -281,8 +284,8 @@ FF_HD f2 expm1_reduced(f2 r)
     const float q = ffma(ffma(ffma(sh, 1.0f / 40320.0f, 1.0f / 5040.0f), sh, 1.0f / 720.0f), sh,
                          1.0f / 120.0f);
     f2 p = {q, 0.0f};
-    p = fma_step(p, sh, cst(1.0 / 24.0));
-    p = fma_step(p, sh, cst(1.0 / 6.0));
+    p = fma_step(p, sh, FFC(1.0 / 24.0));
+    p = fma_step(p, sh, FFC(1.0 / 6.0));
     p = fma_step(p, sh, f2{0.5f, 0.0f});
     p = fma_step(p, sh, f2{1.0f, 0.0f});
     f2 E = mul(p, sh);

@@ -51,6 +51,11 @@ template <typename T> cudaError_t set_field_smem_limits(size_t bytes);
 // ---- vectors, reductions, ions (kernels_misc.cu)
 // Sum part[q * nblk + b] over b for q < nq into out[q] (one block per q, fixed order).
 void launch_reduce(const double *part, int nblk, int nq, double *out, cudaStream_t st);
+// The three reductions of an evaluation in one launch: rows 0..2 of pA (na
+// columns) into out[0..2], rows 0..5 of pB (nb columns, GGA only) into
+// out[3..8], rows 0..8 of pC (nc columns) into out[9..17].
+void launch_reduce_eval(const double *pA, int na, const double *pB, int nb, const double *pC, int nc, bool gga,
+                        double *out, cudaStream_t st);
 template <typename T> void launch_fill(long long n, T *x, T val, cudaStream_t st);
 template <typename T> void launch_scale(long long n, T *x, double s, const double *sp, cudaStream_t st);
 // if *accepted: phi <- phit, v <- vt, gprev <- g

@@ -27,6 +27,36 @@ __global__ void k_reduce(const double *__restrict__ part, int nblk, double *__re
     if (threadIdx.x == 0) out[blockIdx.x] = v[0];
 }
 
+// The reductions of one evaluation in one launch: block q sums row q of the
+// x-pass partials (q < 3), of the pointwise partials (GGA, 3 <= q < 9) or
+// of the final z-pass partials (the rest) into out[q] (ftTF: out[9 + r] for
+// final row r), in the same fixed order as k_reduce.
+__global__ void k_reduce_eval(const double *__restrict__ pA, int na, const double *__restrict__ pB, int nb,
+                              const double *__restrict__ pC, int nc, int gga, double *__restrict__ out)
+{
+    const int q = blockIdx.x;
+    const double *p;
+    int n, o;
+    if (q < 3) {
+        p = pA + (size_t)q * na;
+        n = na;
+        o = q;
+    } else if (gga && q < 9) {
+        p = pB + (size_t)(q - 3) * nb;
+        n = nb;
+        o = q;
+    } else {
+        const int r = q - (gga ? 9 : 3);
+        p = pC + (size_t)r * nc;
+        n = nc;
+        o = 9 + r;
+    }
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += p[i];
+    block_sum<1>(v);
+    if (threadIdx.x == 0) out[o] = v[0];
+}
+
 template <typename T> __global__ void k_fill(long long n, T *x, T val)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -823,6 +853,12 @@ void launch_andersen(int nat, const double *m, double *V, double kT, double prob
 void launch_reduce(const double *part, int nblk, int nq, double *out, cudaStream_t st)
 {
     k_reduce<<<nq, 256, 0, st>>>(part, nblk, out);
+}
+
+void launch_reduce_eval(const double *pA, int na, const double *pB, int nb, const double *pC, int nc, bool gga,
+                        double *out, cudaStream_t st)
+{
+    k_reduce_eval<<<gga ? 18 : 12, 256, 0, st>>>(pA, na, pB, nb, pC, nc, gga ? 1 : 0, out);
 }
 
 template <typename T> void launch_fill(long long n, T *x, T val, cudaStream_t st)

@@ -346,10 +346,10 @@ FF_CALL void enhance_f2(const FuncParams &fp, ff::f2 x, ff::f2 &F, ff::f2 &dF)
         F = add(mul(mul(x, p0), den), 1.0f);
         dF = mul(p0, mul(den, den));
     } else {                                                // VT84F, m = 8, n = 4
-        const f2 mu = cst(2.778), al = cst(1.2965);
+        const f2 mu = FFC(2.778), al = FFC(1.2965);
         if (x.hi <= 1e-15f) {                               // F = 1 + O(x)
             F = {1.0f, 0.0f};
-            dF = cst(-2.778 + 1.2965 + 5.0 / 3.0);
+            dF = FFC(-2.778 + 1.2965 + 5.0 / 3.0);
             return;
         }
         const f2 ax = mul(x, al);
@@ -364,13 +364,13 @@ FF_CALL void enhance_f2(const FuncParams &fp, ff::f2 x, ff::f2 &F, ff::f2 &dF)
         // F = 1 - mu x e1 den + em (rx - 1) + (5/3) x
         f2 Fv = add(neg(mul(mul(mx, e1), den)), 1.0f);
         Fv = add(Fv, mul(em, add(rx, -1.0f)));
-        F = add(Fv, mul(x, cst(5.0 / 3.0)));
+        F = add(Fv, mul(x, FFC(5.0 / 3.0)));
         // dF = -mu e1 (1 - al x - al mu x^2) den^2 + 2 al (1 - em)(1 - x) - em rx^2 + 5/3
         const f2 poly = add(neg(add(ax, mul(mul(x2, al), mu))), 1.0f);
         f2 d = neg(mul(mul(mul(mu, e1), poly), mul(den, den)));
         d = add(d, mul(mul(al, add(neg(em), 1.0f)), scale(add(neg(x), 1.0f), 2.0f)));
         d = sub(d, mul(em, mul(rx, rx)));
-        dF = add(d, cst(5.0 / 3.0));
+        dF = add(d, FFC(5.0 / 3.0));
     }
 }
 
@@ -379,24 +379,24 @@ FF_CALL void enhance_f2(const FuncParams &fp, ff::f2 x, ff::f2 &F, ff::f2 &dF)
 OF_HD void pz81_f2(ff::f2 c13, ff::f2 y, ff::f2 &eps, ff::f2 &v)
 {
     using namespace ff;
-    const f2 rs = mul(y, cst(0.62035049089940001667));
-    const f2 ex = mul(c13, cst(-0.73855876638202240587));
+    const f2 rs = mul(y, FFC(0.62035049089940001667));
+    const f2 ex = mul(c13, FFC(-0.73855876638202240587));
     f2 ec, vc;
     if (rs.hi >= 1.0f) {
         const f2 sq = sqrt(rs);
-        const f2 den = recip(add(add(mul(sq, cst(1.0529)), mul(rs, cst(0.3334))), 1.0f));
-        ec = mul(den, cst(-0.1423));
-        const f2 num = add(add(mul(sq, cst(7.0 / 6.0 * 1.0529)), mul(rs, cst(4.0 / 3.0 * 0.3334))), 1.0f);
+        const f2 den = recip(add(add(mul(sq, FFC(1.0529)), mul(rs, FFC(0.3334))), 1.0f));
+        ec = mul(den, FFC(-0.1423));
+        const f2 num = add(add(mul(sq, FFC(7.0 / 6.0 * 1.0529)), mul(rs, FFC(4.0 / 3.0 * 0.3334))), 1.0f);
         vc = mul(mul(ec, num), den);
     } else {
         const f2 lr = log(rs);
         const f2 rlr = mul(rs, lr);
-        ec = add(add(mul(lr, cst(0.0311)), cst(-0.048)), add(mul(rlr, cst(kPzC)), mul(rs, cst(kPzD))));
-        vc = add(add(mul(lr, cst(0.0311)), cst(-0.048 - 0.0311 / 3.0)),
-                 add(mul(rlr, cst(2.0 / 3.0 * kPzC)), mul(rs, cst((2.0 * kPzD - kPzC) / 3.0))));
+        ec = add(add(mul(lr, FFC(0.0311)), FFC(-0.048)), add(mul(rlr, FFC(kPzC)), mul(rs, FFC(kPzD))));
+        vc = add(add(mul(lr, FFC(0.0311)), FFC(-0.048 - 0.0311 / 3.0)),
+                 add(mul(rlr, FFC(2.0 / 3.0 * kPzC)), mul(rs, FFC((2.0 * kPzD - kPzC) / 3.0))));
     }
     eps = add(ex, ec);
-    v = add(mul(ex, cst(4.0 / 3.0)), vc);
+    v = add(mul(ex, FFC(4.0 / 3.0)), vc);
 }
 
 // Double-float outputs of the pointwise functional at one point.
@@ -422,9 +422,9 @@ OF_HD bool pw_core_f2(const FuncParams &fp, const ff::f2 *__restrict__ tab, ff::
     const f2 c13 = mul(n, y2);                               // n^(1/3)
     const f2 n23 = mul(c13, c13);
     const f2 rn = mul(y2, y);                                // 1/n
-    const f2 tau0 = mul(mul(n, n23), cst(OF_CTF));           // Eq. (tauTFdefn)
-    const f2 dtau0 = mul(n23, cst(5.0 / 3.0 * OF_CTF));
-    const f2 dtdn = mul(mul(t, rn), cst(-2.0 / 3.0));
+    const f2 tau0 = mul(mul(n, n23), FFC(OF_CTF));           // Eq. (tauTFdefn)
+    const f2 dtau0 = mul(n23, FFC(5.0 / 3.0 * OF_CTF));
+    const f2 dtdn = mul(mul(t, rn), FFC(-2.0 / 3.0));
     f2 tf[8];
     if (fp.kind == 0) {                                      // ftTF
         tfunc_eval_f2<2>(tab, t, tf);
@@ -436,7 +436,7 @@ OF_HD bool pw_core_f2(const FuncParams &fp, const ff::f2 *__restrict__ tab, ff::
     } else {
         const f2 rn43 = mul(y2, y2);                         // n^(-4/3)
         const f2 q0 = mul(gr[0], rn43), q1 = mul(gr[1], rn43), q2 = mul(gr[2], rn43);
-        const f2 s2 = mul(add(add(mul(q0, q0), mul(q1, q1)), mul(q2, q2)), cst(OF_CS));   // Eq. (s_0defn)
+        const f2 s2 = mul(add(add(mul(q0, q0), mul(q1, q1)), mul(q2, q2)), FFC(OF_CS));   // Eq. (s_0defn)
         if (!(s2.hi <= (float)kPwS2max)) return false;
         tfunc_eval_f2<4>(tab, t, tf);
         const f2 xi = tf[0], ze = tf[1], A = tf[2], B = tf[3];
@@ -449,7 +449,7 @@ OF_HD bool pw_core_f2(const FuncParams &fp, const ff::f2 *__restrict__ tab, ff::
         const f2 kin = mul(tau0, xi), ent = mul(tau0, ze);
         o.f = sub(mul(kin, Ft), mul(ent, Fs));              // Eq. (FGGA)
         o.ts = mul(ent, Fs);
-        const f2 e83 = mul(rn, cst(-8.0 / 3.0));
+        const f2 e83 = mul(rn, FFC(-8.0 / 3.0));
         const f2 s2dt = mul(s2, dtdn);
         // Eq. (vftGGA), first two lines
         f2 d = mul(dtau0, sub(mul(xi, Ft), mul(ze, Fs)));
@@ -459,7 +459,7 @@ OF_HD bool pw_core_f2(const FuncParams &fp, const ff::f2 *__restrict__ tab, ff::
         o.dfdn = d;
         // last line: W = [tau0 xi F_tau' A - tau0 zeta F_sigma' B] d s^2 / d grad n
         const f2 wpre = sub(mul(mul(kin, dFt), A), mul(mul(ent, dFs), B));
-        const f2 wr = mul(mul(wpre, rn43), cst(2.0 * OF_CS));
+        const f2 wr = mul(mul(wpre, rn43), FFC(2.0 * OF_CS));
         for (int a = 0; a < 3; ++a) o.w[a] = mul(wr, mul(gr[a], rn43));
     }
     if (xc) {
