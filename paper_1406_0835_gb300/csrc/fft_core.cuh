@@ -196,8 +196,8 @@ __device__ C *fft_lines(C *a, C *b, const FftAxis &ax, int nl, int lstride, int 
 // double-float pair (hi + lo, two binary32 words) and each binary32 term
 // enters by the DWPlusFP sum of ffmath.cuh (relative error <= 2u^2), so a
 // thread's partial carries about 48 significant bits while the FP64 units
-// stay idle.  It enters the block reduction as the binary64 value hi + lo;
-// from the warp level up every sum is binary64.
+// stay idle.  Warps add the pairs in double-float, blocks in binary64
+// (block_sum_f2).
 struct AccF {
     ff::f2 v;
     __device__ __forceinline__ AccF() : v(0.0f, 0.0f) {}
@@ -258,13 +258,45 @@ template <int NQ> __device__ __forceinline__ void block_sum(double *v)
     block_sum<NQ, double>(v, v);
 }
 
-// Double-float per-thread partials: binary64 from the warp level up.
+// Deterministic block sum of double-float per-thread partials: the warp
+// stage adds double-float pairs (shuffles of both words, DWPlusDW), so the
+// FP64 units see one conversion per warp and the cross-warp sum by thread 0
+// (binary64, fixed order); thread 0 returns the totals in tot.
+template <int NQ> __device__ __forceinline__ void block_sum_f2(const ff::f2 *v, double *tot)
+{
+    __shared__ double red[32][NQ];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        ff::f2 x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ff::f2 y;
+            y.hi = __shfl_down_sync(0xffffffffu, x.hi, o);
+            y.lo = __shfl_down_sync(0xffffffffu, x.lo, o);
+            x = ff::add(x, y);
+        }
+        if (lane == 0) red[wid][q] = ff::to_double(x);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w][q];
+            tot[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// The FP32 kernels' per-thread partials.
 template <int NQ> __device__ __forceinline__ void block_sum(AccF *v, double *tot)
 {
-    double d[NQ];
+    ff::f2 d[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) d[q] = v[q].value();
-    block_sum<NQ, double>(d, tot);
+    for (int q = 0; q < NQ; ++q) d[q] = v[q].v;
+    block_sum_f2<NQ>(d, tot);
 }
 
 }  // namespace ofdft

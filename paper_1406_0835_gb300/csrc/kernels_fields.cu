@@ -81,15 +81,12 @@ template <> __device__ __forceinline__ ff::f2 scal<DD>(double x) { return ff::sp
 template <typename PR> struct AccK { typedef typename KT<PR>::R type; };
 template <> struct AccK<float> { typedef AccF type; };
 
-// Block totals of per-thread accumulators (double-float ones are converted
-// to binary64 first; from the warp level up the sums are binary64).
+// Block totals of per-thread accumulators (double-float ones are added in
+// double-float across the warp and in binary64 across warps).
 template <int NQ, typename PR> __device__ __forceinline__ void block_total(typename AccK<PR>::type *acc, double *tot)
 {
     if constexpr (is_dd<PR>()) {
-        double d[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) d[q] = ff::to_double(acc[q]);
-        block_sum<NQ, double>(d, tot);
+        block_sum_f2<NQ>(acc, tot);
     } else if constexpr (std::is_same<PR, float>::value) {
         block_sum<NQ>(acc, tot);
     } else {
@@ -994,12 +991,26 @@ void launch_dline(const GridInfo &g, const FftAxis &fa, int axis, int mode, int 
 #undef CALL
 }
 
-// Blocks of the pointwise kernel: one point a thread, at most one block per
-// z line pair (the partial-sum rows hold nx ny / 2 columns).
+// Blocks of the pointwise kernel: about eight points a thread (the block
+// sums cost a few hundred instructions a thread), at least one full wave of
+// the GPU's SMs, at most one block per z line pair (the partial-sum rows
+// hold nx ny / 2 columns).
 int pw_blocks(const GridInfo &g, int th)
 {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            sms = n;
+        else
+            sms = 152;
+    }
     const long long npairs = (long long)g.nx * g.ny / 2;
-    return (int)std::min<long long>((g.N + th - 1) / th, npairs);
+    long long b = (g.N + 8LL * th - 1) / (8LL * th);
+    b = std::max<long long>(b, (long long)sms * OFDFT_PW_MINB);
+    b = std::min<long long>(b, (g.N + th - 1) / th);
+    return (int)std::min<long long>(b, npairs);
 }
 
 template <typename T>
