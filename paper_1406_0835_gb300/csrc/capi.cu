@@ -1030,12 +1030,14 @@ template <typename T> ofdft_status alloc_fieldset(ofdft_ctx *c, FieldSet &f)
     // v_ext(G); the Heine-Abarenkov form and triclinic cells append the pressure weights
     CK(cudaMallocAsync((void **)&f.vext, (size_t)((g.lpp || g.tri) ? 2 : 1) * g.NH * sizeof(cplx<T>), c->st));
     // temperature table; FP64 sets append its double-float split (hi, lo
-    // binary32 pairs) for the double-float pointwise functional
+    // binary32 pairs) and the double-float VT84F enhancement table for the
+    // double-float pointwise functional
     const std::vector<double> &tab = tfunc_table_host();
     std::vector<T> tt(tab.begin(), tab.end());
     if (sizeof(T) == 8) {
-        tt.resize(2 * (size_t)kTfSize);
-        tfunc_table_split(tab.data(), reinterpret_cast<float *>(tt.data() + kTfSize));
+        std::vector<double> dd((size_t)kDdTabSize);
+        dd_tables_fill(tab.data(), dd.data());
+        tt.assign(dd.begin(), dd.end());
     }
     CK(cudaMallocAsync((void **)&f.tab, tt.size() * sizeof(T), c->st));
     CK(cudaMemcpyAsync(f.tab, tt.data(), tt.size() * sizeof(T), cudaMemcpyHostToDevice, c->st));
@@ -1930,9 +1932,8 @@ ofdft_status ofdft_pointwise_eval(int functional, int xc, double T_kelvin, long 
         return OFDFT_EINVAL;
     if (count > 0 && (!n || !g2 || !out)) return OFDFT_EINVAL;
     const std::vector<double> &tab = tfunc_table_host();
-    std::vector<double> tt(tab.begin(), tab.end());
-    tt.resize(2 * (size_t)kTfSize);
-    tfunc_table_split(tab.data(), reinterpret_cast<float *>(tt.data() + kTfSize));
+    std::vector<double> tt((size_t)kDdTabSize);
+    dd_tables_fill(tab.data(), tt.data());
     const ff::f2 *tab2 = reinterpret_cast<const ff::f2 *>(tt.data() + kTfSize);
     const double temp = T_kelvin * kKbHa;
     const ff::f2 tcoef = ff::from_double(2.0 / OF_K23 * temp);

@@ -48,7 +48,7 @@ constexpr size_t kOffPart = kOffZ + align256(kSMaxAtoms * sizeof(double));
 constexpr size_t kOffScal = kOffPart + align256((size_t)kSMaxPart * sizeof(double));
 constexpr size_t kOffTw = kOffScal + align256(64 * sizeof(double));
 constexpr size_t kOffTab = kOffTw + align256(3 * kSMaxEdge * 2 * sizeof(double2));   // + double-float copy
-constexpr size_t kScratchBytes = kOffTab + align256(2 * (size_t)kTfSize * sizeof(double));   // + split
+constexpr size_t kScratchBytes = kOffTab + align256((size_t)kDdTabSize * sizeof(double));   // + splits
 
 static __device__ __align__(256) unsigned char g_ofdft_scratch[kScratchBytes];
 
@@ -58,7 +58,7 @@ struct DevState {
     unsigned char *base;
 };
 DevState g_dev[kMaxDevices];
-double g_tab_host[2 * kTfSize];   // host temperature table + its double-float split, filled once
+double g_tab_host[kDdTabSize];    // host temperature table + double-float tables, filled once
 bool g_tab_ready = false;
 std::mutex g_setup_mu;            // guards g_dev, g_tab_host and g_tab_ready (locking allocates nothing)
 
@@ -91,8 +91,9 @@ ofdft_status device_setup(int dev, unsigned char **base)
         SCK(cudaGetSymbolAddress(&p, g_ofdft_scratch), "cudaGetSymbolAddress of the static scratch failed");
         d.base = (unsigned char *)p;
         if (!g_tab_ready) {
-            tfunc_table_fill(g_tab_host);
-            tfunc_table_split(g_tab_host, reinterpret_cast<float *>(g_tab_host + kTfSize));
+            static double ttab[kTfSize];
+            tfunc_table_fill(ttab);
+            dd_tables_fill(ttab, g_tab_host);
             g_tab_ready = true;
         }
         SCK(cudaMemcpy(d.base + kOffTab, g_tab_host, sizeof(g_tab_host), cudaMemcpyHostToDevice),

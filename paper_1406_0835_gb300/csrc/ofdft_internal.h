@@ -188,8 +188,26 @@ constexpr int kTfPanels = (kTfEmax - kTfEmin) * kTfSub;
 constexpr int kTfFuncs = 4;                // xi, zeta, A, B
 constexpr int kTfSize = kTfPanels * kTfFuncs * kTfNc;
 
+// VT84F enhancement factor F(x), x = s^2 (Eq. (VT84F)), as a table of
+// G = (F - 1)/x for the double-float kernels: 16 panels per octave of x
+// over [2^-20, 2^6), degree 10 in the panel variable u in [-1, 1) (below:
+// the quadratic series of F, above: the closed form 5x/3 + 1/x, where
+// e^(-alpha x) < 1e-36).
+constexpr int kEnDeg = 10;
+constexpr int kEnNc = kEnDeg + 1;
+constexpr int kEnSub = 16;
+constexpr int kEnEmin = -20;
+constexpr int kEnEmax = 6;
+constexpr int kEnPanels = (kEnEmax - kEnEmin) * kEnSub;
+constexpr int kEnSize = kEnPanels * kEnNc;
+// Storage of the FP64 field sets' tables, in doubles: the binary64
+// temperature table, its double-float split, the enhancement table's split.
+constexpr int kDdTabSize = 2 * kTfSize + kEnSize;
+
 // Build the table on the host (FP64 monomial coefficients per panel).
 const std::vector<double> &tfunc_table_host();
+// The enhancement table (binary64 monomial coefficients, kEnSize doubles).
+void enh_table_fill(double *tab);
 // The same table written into caller storage of kTfSize doubles.
 void tfunc_table_fill(double *tab);
 

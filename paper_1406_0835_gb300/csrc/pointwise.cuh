@@ -374,6 +374,53 @@ FF_CALL void enhance_f2(const FuncParams &fp, ff::f2 x, ff::f2 &F, ff::f2 &dF)
     }
 }
 
+// VT84F F(x) and dF/dx in double-float from the enhancement table etab of
+// G = (F - 1)/x (kEnSize pairs): F = 1 + x G, dF = G + x G' with G' the
+// polynomial's derivative, so the potential is the exact derivative of the
+// tabulated energy; x < 2^-20: the cubic series (the next terms are below
+// 1e-16 in F and dF), x >= 64: F = 5x/3 + 1/x.
+OF_HD void enhance_vt84f_tab(const ff::f2 *__restrict__ etab, ff::f2 x, ff::f2 &F, ff::f2 &dF)
+{
+    using namespace ff;
+    if (x.hi < 9.5367431640625e-07f) {
+        // series of Eq. (VT84F): c1 = alpha - mu + 5/3, c2 = mu (alpha + mu) - alpha,
+        // c3 = -mu (alpha^2/2 + alpha mu + mu^2) - alpha^2/2 (the x^3 term matters
+        // for dF at the 1e-12 level)
+        constexpr double mu = 2.778, al = 1.2965;
+        constexpr double c1 = al - mu + 5.0 / 3.0, c2 = mu * (al + mu) - al;
+        constexpr double c3 = -mu * (0.5 * al * al + al * mu + mu * mu) - 0.5 * al * al;
+        F = add(mul(x, add(mul(x, add(mul(x, FFC(c3)), FFC(c2))), FFC(c1))), 1.0f);
+        dF = add(mul(x, add(mul(x, FFC(3.0 * c3)), FFC(2.0 * c2))), FFC(c1));
+        return;
+    }
+    if (x.hi >= 64.0f) {
+        const f2 r = recip(x);
+        F = add(mul(x, FFC(5.0 / 3.0)), r);
+        dF = sub(FFC(5.0 / 3.0), mul(r, r));
+        return;
+    }
+    int e;
+    float inv2e;
+    const float m = split_pow2(x.hi, e, inv2e);
+    const int sub = (int)((m - 1.0f) * (float)kEnSub);
+    const float uh = (float)(2 * kEnSub) * (m - 1.0f) - (float)(2 * sub + 1);
+    const float ul = (float)(2 * kEnSub) * x.lo * inv2e;
+    const float dudx = (float)(2 * kEnSub) * inv2e;
+    const f2 *c = etab + (size_t)((e - kEnEmin) * kEnSub + sub) * kEnNc;
+    f2 p = c[kEnDeg], dp = {0.0f, 0.0f};
+    float d2 = 0.0f;   // half the second derivative
+#pragma unroll
+    for (int j = kEnDeg - 1; j >= 0; --j) {
+        d2 = d2 * uh + dp.hi;
+        dp = fma_step(dp, uh, p);
+        p = fma_step(p, uh, c[j]);
+    }
+    const f2 G = add(p, dp.hi * ul);
+    const f2 dG = scale(add(dp, 2.0f * d2 * ul), dudx);
+    F = add(mul(x, G), 1.0f);
+    dF = add(G, mul(x, dG));
+}
+
 // PZ81 (same branches and constants as pz81_point) from n, n^(1/3) and
 // y = n^(-1/3) in double-float.
 OF_HD void pz81_f2(ff::f2 c13, ff::f2 y, ff::f2 &eps, ff::f2 &v)
@@ -443,8 +490,14 @@ OF_HD bool pw_core_f2(const FuncParams &fp, const ff::f2 *__restrict__ tab, ff::
         const f2 dxi = tf[4], dze = tf[5], dA = tf[6], dB = tf[7];
         const f2 xt = mul(s2, A), xs = mul(s2, B);           // Eq. (s_s)
         f2 Ft, dFt, Fsg, dFsg;
-        enhance_f2(fp, xt, Ft, dFt);
-        enhance_f2(fp, xs, Fsg, dFsg);
+        if (fp.kind == 2) {                                  // VT84F: the enhancement table
+            const f2 *etab = tab + kTfSize;
+            enhance_vt84f_tab(etab, xt, Ft, dFt);
+            enhance_vt84f_tab(etab, xs, Fsg, dFsg);
+        } else {
+            enhance_f2(fp, xt, Ft, dFt);
+            enhance_f2(fp, xs, Fsg, dFsg);
+        }
         const f2 Fs = add(neg(Fsg), 2.0f), dFs = neg(dFsg); // F_sigma = 2 - F_tau(s_sigma)
         const f2 kin = mul(tau0, xi), ent = mul(tau0, ze);
         o.f = sub(mul(kin, Ft), mul(ent, Fs));              // Eq. (FGGA)
@@ -489,13 +542,26 @@ OF_HD PwOut<T> pw_point_native(const FuncParams &fp, const T *__restrict__ tab, 
 
 
 // Double-float table written from the binary64 one (hi, lo per coefficient).
-inline void tfunc_table_split(const double *tab, float *out)
+inline void tfunc_table_split(const double *tab, float *out, int count = kTfSize)
 {
-    for (int i = 0; i < kTfSize; ++i) {
+    for (int i = 0; i < count; ++i) {
         ff::f2 c = ff::from_double(tab[i]);
         out[2 * i] = c.hi;
         out[2 * i + 1] = c.lo;
     }
+}
+
+// The FP64 field sets' tables in dst[kDdTabSize]: the binary64 temperature
+// table, its double-float split, the double-float VT84F enhancement table
+// (the split temperature table and the enhancement table are contiguous,
+// as pw_core_f2 reads them).
+inline void dd_tables_fill(const double *ttab, double *dst)
+{
+    for (int i = 0; i < kTfSize; ++i) dst[i] = ttab[i];
+    tfunc_table_split(ttab, reinterpret_cast<float *>(dst + kTfSize));
+    double etab[kEnSize];
+    enh_table_fill(etab);
+    tfunc_table_split(etab, reinterpret_cast<float *>(dst + 2 * kTfSize), kEnSize);
 }
 
 }  // namespace ofdft

@@ -10,7 +10,8 @@
 // finite-T Lindhard function: h~ = 6 I_{1/2} I'_{-1/2} / I_{-1/2}^2.
 //
 // This file builds, once per process, piecewise polynomial fits of xi, zeta,
-// A, B in t: 4 panels per octave of t over [2^-20, 2^34), degree 10 in the
+// A, B in t (and, for the double-float kernels, of the VT84F enhancement
+// factor in x = s^2, enh_table_fill): 4 panels per octave of t over [2^-20, 2^34), degree 10 in the
 // panel variable u in [-1, 1).  The kernels differentiate the polynomials, so
 // the potential is the exact derivative of the tabulated energy.
 //
@@ -242,6 +243,55 @@ void tfunc_table_fill(double *tab)
                     for (int i = j; i < nc; ++i) a += cheb[i] * Tm[i][j];
                     out[j] = a;
                 }
+            }
+        }
+    }
+}
+
+// VT84F (Eq. (VT84F) with m = 8, n = 4, written in x = s^2) through
+// G(x) = (F(x) - 1)/x, which stays of order one as x -> 0 (so the fitted
+// slope keeps its relative accuracy there):
+//   G = -mu e^(-alpha x)/(1 + mu x) + (1 - e^(-alpha x^2))/x^2
+//       - (1 - e^(-alpha x^2))/x + 5/3,
+// evaluated in long double and fitted per panel: Chebyshev interpolation
+// at kEnNc nodes, then monomial coefficients in the panel variable u
+// (x = 2^e (1 + (sub + (u + 1)/2)/kEnSub)).
+void enh_table_fill(double *tab)
+{
+    // the fit runs in long double: the slope of G on a narrow panel is small
+    // next to G, and binary64 rounding of the interpolation would swamp it
+    const long double mu = 2.778L, al = 1.2965L, pi = 3.14159265358979323846264338327950288L;
+    const int d = kEnDeg, nc = kEnNc;
+    long double un[nc];
+    for (int k = 0; k < nc; ++k) un[k] = std::cos(pi * (k + 0.5L) / nc);
+    long double Tm[nc][nc];
+    for (int i = 0; i < nc; ++i)
+        for (int j = 0; j < nc; ++j) Tm[i][j] = 0.0L;
+    Tm[0][0] = 1.0L;
+    Tm[1][1] = 1.0L;
+    for (int i = 2; i <= d; ++i)
+        for (int j = 0; j <= i; ++j)
+            Tm[i][j] = (j > 0 ? 2.0L * Tm[i - 1][j - 1] : 0.0L) - Tm[i - 2][j];
+    for (int e = kEnEmin; e < kEnEmax; ++e) {
+        for (int sub = 0; sub < kEnSub; ++sub) {
+            long double vals[nc];
+            for (int k = 0; k < nc; ++k) {
+                const long double x = std::ldexp(1.0L + (sub + 0.5L * (un[k] + 1.0L)) / kEnSub, e);
+                const long double e1 = std::exp(-al * x);
+                const long double em = -std::expm1(-al * x * x);     // 1 - e^(-alpha x^2)
+                vals[k] = -mu * e1 / (1.0L + mu * x) + em / (x * x) - em / x + 5.0L / 3.0L;
+            }
+            long double cheb[nc];
+            for (int j = 0; j < nc; ++j) {
+                long double acc = 0.0L;
+                for (int k = 0; k < nc; ++k) acc += vals[k] * std::cos(pi * j * (k + 0.5L) / nc);
+                cheb[j] = (j == 0 ? 1.0L : 2.0L) * acc / nc;
+            }
+            double *out = &tab[(size_t)((e - kEnEmin) * kEnSub + sub) * nc];
+            for (int j = 0; j < nc; ++j) {
+                long double a = 0.0L;
+                for (int i = j; i < nc; ++i) a += cheb[i] * Tm[i][j];
+                out[j] = (double)a;
             }
         }
     }

@@ -22,9 +22,11 @@ def lib():
 
 
 def _points(seed, count=3000):
+    # s^2 from 1e-9 (the enhancement factor's small-x series in the
+    # double-float kernels) to 1e3 (its closed large-x form)
     rng = np.random.default_rng(seed)
     n = 10.0 ** rng.uniform(-5, 2, count)
-    s2 = 10.0 ** rng.uniform(-5, 3, count)
+    s2 = 10.0 ** rng.uniform(-9, 3, count)
     g2 = s2 * n ** (8.0 / 3.0) / OF_CS
     return n, g2
 
