@@ -1151,6 +1151,7 @@ std::mutex g_tune_mu;
 struct Tuned {
     int zP, tk, zth, xth;
     int mp[3];   // largest power-of-two radix per axis
+    int dk, dth; // derivative passes: tile width, threads
 };
 
 // Rebuild axis a's Stockham schedule with power-of-two radices up to m (the
@@ -1198,6 +1199,8 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
             f.gt.tk = it->second.tk;
             f.gt.zth = it->second.zth;
             f.gt.xth = it->second.xth;
+            f.gt.dk = it->second.dk;
+            f.gt.dth = it->second.dth;
             for (int a = 0; a < 3; ++a) set_radix(f, a, it->second.mp[a]);
             if (f.graph) cudaGraphExecDestroy(f.graph);
             f.graph = nullptr;
@@ -1261,6 +1264,28 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
             }
         }
     }
+    // the derivative passes' tile width and threads (GGA evaluations only)
+    if (c->fp.kind != 0) {
+        for (int pass = 0; pass < 2; ++pass) {
+            best_ms = 1e30f;
+            GridInfo base3 = best;
+            const int opts[3] = {4, 8, 16}, topts[3] = {64, 128, 256};
+            for (int k = 0; k < 3; ++k) {
+                GridInfo g = base3;
+                if (pass == 0) g.dk = opts[k];
+                else g.dth = topts[k];
+                if (field_smem_max(g, sizeof(cplx<T>)) > dyn) continue;
+                f.gt = g;
+                float ms;
+                ofdft_status r = time_evals<T>(c, f, reps, ms);
+                if (r != OFDFT_OK) return r;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = g;
+                }
+            }
+        }
+    }
     f.gt = best;
     // the Stockham schedule of each axis: power-of-two radices up to 8 or
     // up to 4 (fewer stages against shorter butterflies; same twiddles)
@@ -1284,7 +1309,7 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
     f.graph = nullptr;
     c->shape_epoch++;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = Tuned{best.zP, best.tk, best.zth, best.xth, {mp[0], mp[1], mp[2]}};
+    g_tune[key] = Tuned{best.zP, best.tk, best.zth, best.xth, {mp[0], mp[1], mp[2]}, best.dk, best.dth};
     return OFDFT_OK;
 }
 

@@ -623,7 +623,7 @@ __global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ s
 // real fields, so F^-1 M F c = (d a) + i (d b) needs no unpacking.
 
 // Pair-column tile of a real field for the passes along x (AX 0) or y
-// (AX 1): g.tk consecutive pairs of adjacent iz columns of the flattened
+// (AX 1): g.dk consecutive pairs of adjacent iz columns of the flattened
 // (iy, iz) (x pass) or (ix, iz) (y pass) space; rows run along the axis.
 struct PairTile {
     long long rstride;
@@ -634,7 +634,7 @@ struct PairTile {
 __device__ __forceinline__ PairTile pair_tile(const GridInfo &g, int ax)
 {
     __shared__ long long s_pb[16];
-    const int tk = g.tk;
+    const int tk = g.dk;
     const int hz = g.nz / 2;
     const long long total = (long long)(ax == 0 ? g.ny : g.nx) * hz;
     const long long p0 = (long long)blockIdx.x * tk;
@@ -660,7 +660,7 @@ __device__ __forceinline__ PairTile pair_tile(const GridInfo &g, int ax)
 __host__ __device__ __forceinline__ int pair_tiles_of(const GridInfo &g, int ax)
 {
     const long long total = (long long)(ax == 0 ? g.ny : g.nx) * (g.nz / 2);
-    return (int)((total + g.tk - 1) / g.tk);
+    return (int)((total + g.dk - 1) / g.dk);
 }
 
 // Stored pair of reals (two adjacent iz columns; even offset, so aligned).
@@ -681,7 +681,7 @@ __global__ void k_dline(GridInfo g, FftAxis fa, const typename KT<PR>::T *__rest
     extern __shared__ __align__(16) unsigned char smraw[];
     const int n = AX == 0 ? g.nx : g.ny;
     CC *A = reinterpret_cast<CC *>(smraw);
-    CC *B = A + n * g.tk;
+    CC *B = A + n * g.dk;
     const PairTile t = pair_tile(g, AX);
     for (int i = threadIdx.x; i < n * t.tk; i += blockDim.x) {
         const int r = i >> t.tsh, c = i & (t.tk - 1);
@@ -984,8 +984,8 @@ void launch_dline(const GridInfo &g, const FftAxis &fa, int axis, int mode, int 
 {
     const int n = axis == 0 ? g.nx : g.ny;
     const int blocks = pair_tiles_of(g, axis);
-    const size_t sm = 2 * (size_t)n * g.tk * sizeof(cplx<T>);
-    const int th = g.xth > 0 ? g.xth : threads_for(n * g.tk / 2);
+    const size_t sm = 2 * (size_t)n * g.dk * sizeof(cplx<T>);
+    const int th = g.dth > 0 ? g.dth : threads_for(n * g.dk / 2);
 #define CALL(PR) dline_call<PR>(g, fa, axis, mode, acc, in, out, blocks, th, sm, st)
     OFDFT_DISPATCH(T, g, CALL);
 #undef CALL
@@ -1112,8 +1112,10 @@ size_t field_smem_max(const GridInfo &g, size_t csize)
     size_t z = 3 * (size_t)P * g.nz * csize;
     size_t y = 2 * (size_t)g.ny * g.tk * csize;
     size_t x = 2 * (size_t)g.nx * g.tk * csize;
+    size_t d = 2 * (size_t)(g.nx > g.ny ? g.nx : g.ny) * g.dk * csize;
     size_t m = z > y ? z : y;
-    return m > x ? m : x;
+    m = m > x ? m : x;
+    return m > d ? m : d;
 }
 
 namespace {

@@ -95,6 +95,7 @@ struct GridInfo {
     int zP;                  // z passes: line pairs per block (0: default rule)
     int tk;                  // y/x passes: half-spectrum columns per tile (4, 8 or 16)
     int zth, xth;            // threads per block of the z and of the y/x passes (0: default rule)
+    int dk, dth;             // derivative passes: pair columns per tile (4, 8 or 16) and threads (0: default)
     int dd;                  // FP64 fields: FFT and G-space arithmetic in double-float
     float bx2[2], by2[2], bz2[2], invN2[2], hr2[2];   // the same constants as double-float pairs
     // general (triclinic) cell: tri = 1 when the lattice vectors a_j (rows of
@@ -117,6 +118,7 @@ struct GridInfo {
 inline void grid_reciprocal(GridInfo &g)
 {
     if (g.tk <= 0) g.tk = 8;
+    if (g.dk <= 0) g.dk = 4;
     const double tp = 6.283185307179586477;
     if (!g.tri) {
         for (int k = 0; k < 9; ++k) g.Am[k] = 0.0;

@@ -298,6 +298,10 @@ constexpr double kPwNmin = 1e-18, kPwNmax = 1e18, kPwS2max = 1e10;
 #define OFDFT_TF_UNROLL 1
 #endif
 constexpr int kTfUnroll = OFDFT_TF_UNROLL;   // functions evaluated side by side
+#ifndef OFDFT_HORNER_UNROLL
+#define OFDFT_HORNER_UNROLL 10
+#endif
+constexpr int kHornerUnroll = OFDFT_HORNER_UNROLL;   // Horner steps unrolled (code size against loop overhead)
 
 // Table polynomials with a double-float table (same layout as tfunc_eval's).
 // The panel variable u = uh + ul: uh is exact in binary32 and the Horner
@@ -319,7 +323,7 @@ OF_HD void tfunc_eval_f2(const ff::f2 *__restrict__ tab, ff::f2 t, ff::f2 out[8]
         const ff::f2 *cq = c + q * kTfNc;
         ff::f2 p = cq[kTfDeg], dp = {0.0f, 0.0f};
         float d2 = 0.0f;   // half the second derivative
-#pragma unroll
+#pragma unroll kHornerUnroll
         for (int j = kTfDeg - 1; j >= 0; --j) {
             d2 = d2 * uh + dp.hi;
             dp = ff::fma_step(dp, uh, p);
@@ -409,7 +413,7 @@ OF_HD void enhance_vt84f_tab(const ff::f2 *__restrict__ etab, ff::f2 x, ff::f2 &
     const f2 *c = etab + (size_t)((e - kEnEmin) * kEnSub + sub) * kEnNc;
     f2 p = c[kEnDeg], dp = {0.0f, 0.0f};
     float d2 = 0.0f;   // half the second derivative
-#pragma unroll
+#pragma unroll kHornerUnroll
     for (int j = kEnDeg - 1; j >= 0; --j) {
         d2 = d2 * uh + dp.hi;
         dp = fma_step(dp, uh, p);
