@@ -1248,7 +1248,7 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
     for (int pass = 0; pass < 2; ++pass) {
         best_ms = 1e30f;
         GridInfo base2 = best;
-        const int thmax = (sizeof(T) == 8 && pass == 0) ? 256 : 512;
+        const int thmax = std::min((sizeof(T) == 8 && pass == 0) ? 256 : 512, fft_max_threads());
         for (int th : {128, 256, 512}) {
             if (th > thmax) continue;
             GridInfo g = base2;
@@ -1274,6 +1274,7 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
                 GridInfo g = base3;
                 if (pass == 0) g.dk = opts[k];
                 else g.dth = topts[k];
+                if (g.dth > fft_max_threads()) continue;
                 if (field_smem_max(g, sizeof(cplx<T>)) > dyn) continue;
                 f.gt = g;
                 float ms;

@@ -46,6 +46,8 @@ int launch_xhl(const GridInfo &g, const FftAxis &ax, cplx<T> *spec, const cplx<T
 size_t field_smem_max(const GridInfo &g, size_t csize);
 // blocks (and partial sums per quantity) of the x passes
 int xpass_blocks(const GridInfo &g);
+// Largest block the transform kernels were built for.
+int fft_max_threads();
 template <typename T> cudaError_t set_field_smem_limits(size_t bytes);
 
 // ---- vectors, reductions, ions (kernels_misc.cu)

@@ -251,6 +251,17 @@ __device__ __forceinline__ CC times_ik(CC x, int e, int n, R s)
     return cmk<CC>(R(0) - m * x.y, m * x.x);
 }
 
+// Blocks per SM the transform kernels' registers are sized for (launch
+// bounds with 256 threads; 0: no bound).
+#ifndef OFDFT_FFT_MINB
+#define OFDFT_FFT_MINB 0
+#endif
+#if OFDFT_FFT_MINB > 0
+#define OFDFT_FFT_BOUNDS __launch_bounds__(256, OFDFT_FFT_MINB)
+#else
+#define OFDFT_FFT_BOUNDS
+#endif
+
 // ------------------------------------------------------------------ z pass
 // Pair p of a block holds real lines 2p (real part) and 2p+1 (imaginary part).
 
@@ -258,7 +269,7 @@ __device__ __forceinline__ CC times_ik(CC x, int e, int n, R s)
 // line transforms it already holds: the forward spectrum times i kt ds_z,
 // transformed back).
 template <typename PR, int MODE>
-__global__ void k_zfwd(GridInfo g, FftAxis az, int P, const typename KT<PR>::T *__restrict__ in,
+__global__ void OFDFT_FFT_BOUNDS k_zfwd(GridInfo g, FftAxis az, int P, const typename KT<PR>::T *__restrict__ in,
                        const typename KT<PR>::T *__restrict__ phi, const typename KT<PR>::T *__restrict__ dhat,
                        typename KT<PR>::T c, typename KT<PR>::T s, const void *__restrict__ cs,
                        typename KT<PR>::T *__restrict__ phit, typename KT<PR>::C *__restrict__ out,
@@ -512,7 +523,7 @@ __device__ __forceinline__ void store_tile(typename KT<PR>::C *__restrict__ dst,
 }
 
 template <typename PR, bool INV>
-__global__ void k_ypass(GridInfo g, FftAxis ay, typename KT<PR>::C *__restrict__ data, long long fstride)
+__global__ void OFDFT_FFT_BOUNDS k_ypass(GridInfo g, FftAxis ay, typename KT<PR>::C *__restrict__ data, long long fstride)
 {
     typedef typename KT<PR>::C C;
     typedef typename KT<PR>::CC CC;
@@ -550,7 +561,7 @@ __device__ __forceinline__ typename KT<PR>::R ploc_term(const GridInfo &g, const
 // x pass, ftTF variant: forward x -> energies -> v_HL(G) = 4 pi n/G^2 + v_ext
 // inverse-x, written over the spectrum.  If keep_n, n(G) is also stored in nG_out.
 template <typename PR, bool TRI>
-__global__ void k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ spec,
+__global__ void OFDFT_FFT_BOUNDS k_xhl(GridInfo g, FftAxis ax, typename KT<PR>::C *__restrict__ spec,
                       const typename KT<PR>::C *__restrict__ vext, typename KT<PR>::C *__restrict__ nG_out,
                       int inverse, double *__restrict__ part)
 {
@@ -671,7 +682,7 @@ template <> struct Pair2<float> { typedef float2 type; };
 // out (= or +=) d_j f along grid axis AX for f = phi^2 (MODE 0) or f = in
 // (MODE 1); ACC 1 adds to out.
 template <typename PR, int AX, int MODE, int ACC>
-__global__ void k_dline(GridInfo g, FftAxis fa, const typename KT<PR>::T *__restrict__ in,
+__global__ void OFDFT_FFT_BOUNDS k_dline(GridInfo g, FftAxis fa, const typename KT<PR>::T *__restrict__ in,
                         typename KT<PR>::T *__restrict__ out)
 {
     typedef typename KT<PR>::T T;
@@ -833,7 +844,7 @@ __global__ void __launch_bounds__(OFDFT_PW_THREADS, OFDFT_PW_MINB) k_pw(GridInfo
 // (as k_zfinal's GGA form): rows 0..5 zero, then sum phi^2 v, sum phi^2,
 // sum 2 phi v dphi/dtheta.
 template <typename PR>
-__global__ void k_zfinal_g(GridInfo g, FftAxis az, int P, const typename KT<PR>::C *__restrict__ dspec,
+__global__ void OFDFT_FFT_BOUNDS k_zfinal_g(GridInfo g, FftAxis az, int P, const typename KT<PR>::C *__restrict__ dspec,
                            const typename KT<PR>::T *__restrict__ uz, const typename KT<PR>::T *__restrict__ vpart,
                            const typename KT<PR>::T *div, const typename KT<PR>::T *__restrict__ phit,
                            const typename KT<PR>::T *__restrict__ phi, const typename KT<PR>::T *__restrict__ dhat,
@@ -1105,6 +1116,8 @@ int launch_xhl(const GridInfo &g, const FftAxis &ax, cplx<T> *spec, const cplx<T
 }
 
 int xpass_blocks(const GridInfo &g) { return tiles_of(g, true); }
+
+int fft_max_threads() { return OFDFT_FFT_MINB > 0 ? 256 : 1024; }
 
 size_t field_smem_max(const GridInfo &g, size_t csize)
 {

@@ -299,7 +299,7 @@ constexpr double kPwNmin = 1e-18, kPwNmax = 1e18, kPwS2max = 1e10;
 #endif
 constexpr int kTfUnroll = OFDFT_TF_UNROLL;   // functions evaluated side by side
 #ifndef OFDFT_HORNER_UNROLL
-#define OFDFT_HORNER_UNROLL 10
+#define OFDFT_HORNER_UNROLL 2
 #endif
 constexpr int kHornerUnroll = OFDFT_HORNER_UNROLL;   // Horner steps unrolled (code size against loop overhead)
 
