@@ -56,6 +56,9 @@ WORKLOADS = {
     # one single-point minimisation per step (256 H, 4 g/cm^3, 128^3, 250 kK)
     "solve-vt84f-128": dict(kind="solve", functional="vt84f", grid=128, precision="fp64", T=2.5e5),
     "solve-vt84f-128-mixed": dict(kind="solve", functional="vt84f", grid=128, precision="mixed", T=2.5e5),
+    # the same solve by truncated Newton (central-difference Hessian products)
+    "solve-vt84f-128-tn": dict(kind="solve", functional="vt84f", grid=128, precision="fp64", T=2.5e5,
+                               method="tn"),
     # batched form: 64 uneven single-point solves (8-512 H, 0.1-10 g/cm^3,
     # 2 kK-4 MK, 32^3-160^3, ftTF/SGA/VT84F) per step, all in flight at once
     "batch-64-mixed": dict(kind="batch", precision="mixed", count=64),
@@ -504,7 +507,11 @@ def run_solve(args, rank, world):
 
     def solve(c):
         c.set_phi(None)
-        E, st = c.minimize(gtol=1e-8, maxit=args.maxit, raise_on_noconv=args.maxit >= 20000)
+        if wl.get("method") == "tn":
+            E, st, nh = c.minimize_tn(gtol=1e-8, maxit=min(args.maxit, 500), raise_on_noconv=args.maxit >= 20000)
+            st["hessian_products"] = nh
+        else:
+            E, st = c.minimize(gtol=1e-8, maxit=args.maxit, raise_on_noconv=args.maxit >= 20000)
         F, P = c.forces()
         return st
 
@@ -563,7 +570,8 @@ def run_solve(args, rank, world):
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "flushed (256 MB write) before every timed step"},
            "evals_per_step": evals / args.steps, "fp32_evals_per_step": evals_lo / args.steps,
-           "cg_iterations_per_step": iters / args.steps, "evals_per_s": world * evals / t_total,
+           "iterations_per_step": iters / args.steps, "method": wl.get("method", "cg"),
+           "evals_per_s": world * evals / t_total,
            "gpu_launches": launches, "clocks": clk, "e2e": e2e,
            "roofline": roofline_entry(dominant, cfg["grid"], kms, kcount, clk, read_peaks(), wl["precision"])}
     return res, evals / args.steps

@@ -194,6 +194,25 @@ ofdft_status ofdft_minimize(ofdft_ctx *ctx, double gtol, int maxit,
                             ofdft_energy *E, ofdft_stats *stats);
 
 /*
+ * The same minimisation by truncated Newton, the alternative to CG that
+ * Sec. II names (details are this library's reading, identical to the
+ * oracle's minimize_tn): each outer step solves H d = -g on the tangent
+ * space of the constraint by an inner CG of at most inner_max steps,
+ * truncated when ||r|| <= eta ||g|| or at non-positive curvature; H p is
+ * the central difference of the gradient map along p (two evaluations);
+ * the step takes the CG's norm-preserving rotation and line search from the
+ * Newton angle.  Runs host-driven on the FP64 field set (also for
+ * OFDFT_MIXED contexts).  stats->evaluations counts every energy +
+ * potential evaluation, *hessian_products (may be NULL) the Hessian
+ * products.  gtol > 0, maxit > 0, inner_max > 0 and 0 < eta < 1, else
+ * OFDFT_EINVAL; OFDFT_ENOCONV (stats filled, last state kept) when maxit
+ * is reached or the line search fails; device scratch: nine fields of N
+ * doubles for the duration of the call.
+ */
+ofdft_status ofdft_minimize_tn(ofdft_ctx *ctx, double gtol, int maxit, int inner_max, double eta,
+                               ofdft_energy *E, ofdft_stats *stats, int *hessian_products);
+
+/*
  * ofdft_minimize in two halves, so that many contexts (each on its own
  * stream) minimise concurrently: _start enqueues the whole minimisation on
  * the context's stream and returns at once; _query returns OFDFT_OK once it
@@ -208,9 +227,15 @@ ofdft_status ofdft_minimize_wait(ofdft_ctx *ctx, ofdft_energy *E, ofdft_stats *s
 
 /*
  * Batched single-point solves: minimise n independent contexts at once (the
- * uneven-size batch of the library's batched form).  Each context's
- * minimisation is one graph launch on its own stream, so the solves overlap
- * on the device; E[n] and stats[n] (either may be NULL) receive the results.
+ * uneven-size batch of the library's batched form).  All minimisations are
+ * the independent branches of one CUDA graph, launched once on the first
+ * context's stream after the work already queued on every context's stream
+ * (the executable graph is kept by the first context and reused while the
+ * same contexts come in the same order); the solves overlap on the device
+ * and each takes exactly the steps it takes alone.  Contexts on different
+ * devices, or with host-driven loops (OFDFT_DEBUG_SYNC, kernel timer), run
+ * as one graph launch each on their own streams.  E[n] and stats[n]
+ * (either may be NULL) receive the results.
  * Returns OFDFT_OK when every solve converged, else the first failing
  * status (all results are still filled).
  */

@@ -8,6 +8,8 @@
 // minimisation without host synchronisation.  With OFDFT_DEBUG_SYNC=1 or an
 // active kernel timer the same kernel sequence is driven from the host.
 #include <math.h>
+
+#include <cmath>
 #include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -951,6 +953,247 @@ ofdft_status run_minimize(ofdft_ctx *c, double gtol, int maxit, ofdft_stats &sta
     return minimize_wait(c, stats, es);
 }
 
+// ------------------------------------------------ truncated Newton
+// The paper's alternative to CG (Sec. II names CG and truncated Newton and
+// gives no details).  Reading, the same steps as the oracle's minimize_tn:
+// each outer step solves H d = -g on the tangent space (orthogonal to phi)
+// by an inner CG, truncated when ||r|| <= eta ||g||, after inner_max steps
+// or at non-positive curvature (then the last iterate, or -g at the first
+// step).  H p is the central difference of the gradient map
+// g(psi) = 2 psi (v[psi^2] - mu) along p (mu held), projected orthogonal to
+// phi; the step then takes the CG's norm-preserving rotation and line
+// search from the Newton angle min(||d|| / ||phi||, 1).  Host-driven: the
+// field work runs in the FP64 field set's kernels, the scalars on the host.
+struct TnVec {
+    double *x = nullptr, *r = nullptr, *p = nullptr, *hp = nullptr, *psi = nullptr, *gp = nullptr,
+           *gq = nullptr, *vpsi = nullptr, *b = nullptr;
+};
+
+ofdft_status tn_dot(ofdft_ctx *c, const double *a, const double *b, double &out)
+{
+    const int nb = launch_dot<double>(c->g.N, a, b, c->part, c->st);
+    launch_reduce(c->part, nb, 1, c->scal, c->st);
+    c->launches += 2;
+    if (sync_read(c, 1) != OFDFT_OK) return OFDFT_EDEVICE;
+    out = c->scal_h[0];
+    return OFDFT_OK;
+}
+
+double e_elec_host(const ofdft_ctx *c, const EvalScalars &es) { return es.EH + es.Eloc + c->g.dV * (es.FS + es.FXC); }
+
+// One trial of the line search: phit = phi cos + dhat sin, its energy and
+// dE/dtheta (the same sums the device line search reads).
+ofdft_status tn_trial(ofdft_ctx *c, FieldSet &f, double th, EvalScalars &es)
+{
+    ofdft_status s = enqueue_eval<double>(c, f, (double *)f.phit, (const double *)f.phi, (const double *)f.dhat,
+                                          cos(th), sin(th), nullptr, (double *)f.vt, false, c->scal);
+    if (s != OFDFT_OK) return s;
+    if (sync_read(c, 18) != OFDFT_OK) return OFDFT_EDEVICE;
+    es = unpack_sums(c->scal_h, c->fp.kind == 0);
+    return OFDFT_OK;
+}
+
+// The gradient map at psi = phi + h p: gout = 2 psi (v[psi^2] - mu).
+ofdft_status tn_grad_at(ofdft_ctx *c, FieldSet &f, const TnVec &w, double h, double mu, double *gout)
+{
+    const long long N = c->g.N;
+    launch_axpby<double>(N, 1.0, (const double *)f.phi, h, w.p, w.psi, c->st);
+    ofdft_status s = enqueue_eval<double>(c, f, w.psi, nullptr, nullptr, 1.0, 0.0, nullptr, w.vpsi, false, c->scal);
+    if (s != OFDFT_OK) return s;
+    launch_cg_grad<double>(N, w.psi, w.vpsi, mu, nullptr, gout, nullptr, c->part, c->st);
+    c->launches += 2;
+    return OFDFT_OK;
+}
+
+ofdft_status minimize_tn(ofdft_ctx *c, double gtol, int maxit, int inner_max, double eta, ofdft_stats &stats,
+                         int &nhess, EvalScalars &es)
+{
+    FieldSet &f = c->f[0];
+    const long long N = c->g.N;
+    const double dV = c->g.dV;
+    const double fd_rel = 1e-4, ls_tol = 0.1, e_tol = 1e-11;
+    const int max_ls = 20;
+    stats = ofdft_stats{};
+    nhess = 0;
+    TnVec w;
+    double **bufs[] = {&w.x, &w.r, &w.p, &w.hp, &w.psi, &w.gp, &w.gq, &w.vpsi, &w.b};
+    for (double **b : bufs) CK(cudaMallocAsync((void **)b, N * sizeof(double), c->st));
+    auto release = [&]() {
+        for (double **b : bufs)
+            if (*b) cudaFreeAsync(*b, c->st);
+    };
+    double *phi = (double *)f.phi, *v = (double *)f.v, *g = (double *)f.g, *d = (double *)f.d;
+    ofdft_status s = OFDFT_OK;
+    int nevals = 0, it = 0;
+    double mu = 0.0, gnorm = 0.0, pp = 0.0;
+    stats.status = OFDFT_ENOCONV;
+#define TN_TRY(call)                \
+    do {                            \
+        s = (call);                 \
+        if (s != OFDFT_OK) {        \
+            release();              \
+            return s;               \
+        }                           \
+    } while (0)
+    // normalise (dV sum phi^2 = N_e) and evaluate
+    TN_TRY(tn_dot(c, phi, phi, pp));
+    if (!(pp > 0.0) || !std::isfinite(pp)) {
+        release();
+        return fail(c, OFDFT_ENUMERIC, "non-finite or zero density");
+    }
+    launch_scale<double>(N, phi, sqrt(c->Ne / (dV * pp)), nullptr, c->st);
+    TN_TRY(evaluate<double>(c, f, phi, v, false, es));
+    nevals = 1;
+    auto grad = [&]() -> ofdft_status {
+        mu = es.PHI2V / es.PHI2;
+        launch_cg_grad<double>(N, phi, v, mu, nullptr, g, nullptr, c->part, c->st);
+        c->launches++;
+        double gg;
+        ofdft_status r = tn_dot(c, g, g, gg);
+        gnorm = sqrt(dV * gg);
+        return r;
+    };
+    TN_TRY(grad());
+    while (it < maxit) {
+        if (!std::isfinite(gnorm)) {
+            release();
+            return fail(c, OFDFT_ENUMERIC, "non-finite gradient");
+        }
+        if (gnorm < gtol) {
+            stats.status = OFDFT_OK;
+            break;
+        }
+        TN_TRY(tn_dot(c, phi, phi, pp));
+        double pg;
+        TN_TRY(tn_dot(c, phi, g, pg));
+        launch_axpby<double>(N, -1.0, g, pg / pp, phi, w.b, c->st);          // b = -proj(g)
+        launch_fill<double>(N, w.x, 0.0, c->st);
+        CK(cudaMemcpyAsync(w.r, w.b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(w.p, w.b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        c->launches += 2;
+        double rr, bb;
+        TN_TRY(tn_dot(c, w.r, w.r, rr));
+        bb = rr;
+        const double bn = sqrt(bb);
+        for (int j = 0; j < inner_max; ++j) {
+            double ppp;
+            TN_TRY(tn_dot(c, w.p, w.p, ppp));
+            const double h = fd_rel * sqrt(pp / ppp);
+            TN_TRY(tn_grad_at(c, f, w, h, mu, w.gp));
+            TN_TRY(tn_grad_at(c, f, w, -h, mu, w.gq));
+            nevals += 2;
+            ++nhess;
+            launch_axpby<double>(N, 0.5 / h, w.gp, -0.5 / h, w.gq, w.hp, c->st);
+            c->launches++;
+            double ph;
+            TN_TRY(tn_dot(c, phi, w.hp, ph));
+            launch_axpby<double>(N, 1.0, w.hp, -ph / pp, phi, w.hp, c->st);   // project
+            c->launches++;
+            double pHp;
+            TN_TRY(tn_dot(c, w.p, w.hp, pHp));
+            if (!(pHp > 0.0)) {
+                if (j == 0) CK(cudaMemcpyAsync(w.x, w.b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+                break;
+            }
+            const double a = rr / pHp;
+            launch_axpby<double>(N, 1.0, w.x, a, w.p, w.x, c->st);
+            launch_axpby<double>(N, 1.0, w.r, -a, w.hp, w.r, c->st);
+            c->launches += 2;
+            double rr_new;
+            TN_TRY(tn_dot(c, w.r, w.r, rr_new));
+            if (sqrt(rr_new) <= eta * bn) break;
+            launch_axpby<double>(N, 1.0, w.r, rr_new / rr, w.p, w.p, c->st);
+            c->launches++;
+            rr = rr_new;
+        }
+        // d = proj(x), or -proj(g) when it does not descend
+        double px;
+        TN_TRY(tn_dot(c, phi, w.x, px));
+        launch_axpby<double>(N, 1.0, w.x, -px / pp, phi, d, c->st);
+        c->launches++;
+        double dg;
+        TN_TRY(tn_dot(c, d, g, dg));
+        if (dg >= 0.0) CK(cudaMemcpyAsync(d, w.b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        double dd;
+        TN_TRY(tn_dot(c, d, d, dd));
+        const double theta1 = std::min(sqrt(dd / pp), 1.0);
+        // dhat = d sqrt(pp/dd) and D0 = dV sum 2 phi v dhat (the CG's kernel with c1 = 0)
+        const int nb = launch_cg_dhat<double>(N, g, d, phi, v, 0.0, sqrt(pp / dd), 0, nullptr, (double *)f.dhat,
+                                              c->part, c->st);
+        launch_reduce(c->part, nb, 1, c->scal, c->st);
+        c->launches += 2;
+        if (sync_read(c, 1) != OFDFT_OK) {
+            release();
+            return OFDFT_EDEVICE;
+        }
+        const double D0 = dV * c->scal_h[0];
+        // line search on theta (the CG's rules)
+        const double E0 = e_elec_host(c, es);
+        double lo = 0.0, Dlo = D0, hi = -1.0, Dhi = 0.0, pa = 0.0, Da = D0, th = theta1;
+        bool hi_nod = false, accepted = false;
+        EvalScalars et;
+        for (int k = 0; k < max_ls && !accepted; ++k) {
+            TN_TRY(tn_trial(c, f, th, et));
+            ++nevals;
+            const double D = dV * et.DTH;
+            const bool up = e_elec_host(c, et) > E0 + 1e-4 * th * D0 + e_tol * fabs(E0);
+            if (!up && fabs(D) <= ls_tol * fabs(D0)) {
+                accepted = true;
+                break;
+            }
+            if (up) {
+                hi = th;
+                Dhi = D;
+                hi_nod = !(D > 0.0);
+            } else if (D < 0.0) {
+                lo = th;
+                Dlo = D;
+            } else {
+                hi = th;
+                Dhi = D;
+                hi_nod = false;
+            }
+            double nxt;
+            if (hi < 0.0) {
+                nxt = 4.0 * th;
+                if (D > Da) nxt = std::min(th - D * (th - pa) / (D - Da), 4.0 * th);
+                nxt = std::max(nxt, 1.1 * th);
+                pa = th;
+                Da = D;
+            } else if (hi_nod) {
+                nxt = 0.5 * (lo + hi);
+            } else {
+                nxt = lo - Dlo * (hi - lo) / (Dhi - Dlo);
+                const double wdt = hi - lo;
+                nxt = std::min(std::max(nxt, lo + 0.01 * wdt), hi - 0.01 * wdt);
+            }
+            th = std::min(nxt, 1.5);
+        }
+        if (!accepted && lo > 0.0) {   // the best descent point found
+            TN_TRY(tn_trial(c, f, lo, et));
+            ++nevals;
+            accepted = true;
+        }
+        if (!accepted) {
+            stats.status = OFDFT_ENOCONV;
+            break;
+        }
+        CK(cudaMemcpyAsync(phi, f.phit, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(v, f.vt, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        es = et;
+        ++it;
+        TN_TRY(grad());
+    }
+#undef TN_TRY
+    release();
+    stats.iterations = it;
+    stats.evaluations = nevals;
+    stats.gnorm = gnorm;
+    fill_energy(c, es, c->last);
+    c->last_valid = true;
+    return (ofdft_status)stats.status;
+}
+
 ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
 {
     FieldSet &f = c->f[0];
@@ -1547,6 +1790,26 @@ ofdft_status ofdft_minimize(ofdft_ctx *c, double gtol, int maxit, ofdft_energy *
     if (s != OFDFT_OK && s != OFDFT_ENOCONV) return s;
     if (E) *E = c->last;
     if (s == OFDFT_ENOCONV) return fail(c, OFDFT_ENOCONV, "CG did not reach the tolerance");
+    return OFDFT_OK;
+}
+
+ofdft_status ofdft_minimize_tn(ofdft_ctx *c, double gtol, int maxit, int inner_max, double eta, ofdft_energy *E,
+                               ofdft_stats *stats, int *hessian_products)
+{
+    if (!c) return fail(c, OFDFT_EINVAL, "NULL context");
+    NOT_BUSY(c);
+    if (!(gtol > 0.0) || maxit <= 0 || inner_max <= 0 || !(eta > 0.0) || !(eta < 1.0))
+        return fail(c, OFDFT_EINVAL, "gtol > 0, maxit > 0, inner_max > 0 and 0 < eta < 1 required");
+    cudaSetDevice(c->dev);
+    ofdft_stats st{};
+    int nh = 0;
+    EvalScalars es;
+    ofdft_status s = minimize_tn(c, gtol, maxit, inner_max, eta, st, nh, es);
+    if (stats) *stats = st;
+    if (hessian_products) *hessian_products = nh;
+    if (s != OFDFT_OK && s != OFDFT_ENOCONV) return s;
+    if (E) *E = c->last;
+    if (s == OFDFT_ENOCONV) return fail(c, OFDFT_ENOCONV, "truncated Newton did not reach the tolerance");
     return OFDFT_OK;
 }
 

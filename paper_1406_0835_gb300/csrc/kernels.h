@@ -70,6 +70,10 @@ template <typename T> int launch_sumsq(long long n, const T *x, double *part, cu
 // y = 2 x - xp; part: sum y^2
 template <typename T>
 int launch_extrap(long long n, const T *x, const T *xp, T *y, double *part, cudaStream_t st);
+// part <- block sums of a.b (returns blocks); out = alpha x + beta y
+template <typename T> int launch_dot(long long n, const T *a, const T *b, double *part, cudaStream_t st);
+template <typename T>
+void launch_axpby(long long n, double alpha, const T *x, double beta, const T *y, T *out, cudaStream_t st);
 // g = 2 phi (v - mu); part: sum g^2, sum g.gprev
 template <typename T>
 int launch_cg_grad(long long n, const T *phi, const T *v, double mu, const double *mup, T *g,

@@ -189,6 +189,27 @@ __global__ void k_cg_dhat(long long n, const T *__restrict__ g, T *__restrict__ 
     if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
 }
 
+// Truncated Newton: part <- block sums of a.b (binary64).
+template <typename T>
+__global__ void k_dot(long long n, const T *__restrict__ a, const T *__restrict__ b, double *part)
+{
+    double v[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        v[0] += (double)a[i] * (double)b[i];
+    block_sum<1>(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+// out = alpha x + beta y (out may alias x or y).
+template <typename T>
+__global__ void k_axpby(long long n, double alpha, const T *x, double beta, const T *y, T *out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (T)(alpha * (double)x[i] + beta * (double)y[i]);
+}
+
 // Accept a line-search trial: phi <- phi_trial, v <- v_trial, g_prev <- g,
 // when the device CG state says so.
 template <typename T>
@@ -893,6 +914,18 @@ int launch_extrap(long long n, const T *x, const T *xp, T *y, double *part, cuda
     k_extrap<T><<<b, kVecThreads, 0, st>>>(n, x, xp, y, part);
     return b;
 }
+template <typename T> int launch_dot(long long n, const T *a, const T *b, double *part, cudaStream_t st)
+{
+    int nb = vec_blocks(n);
+    k_dot<T><<<nb, kVecThreads, 0, st>>>(n, a, b, part);
+    return nb;
+}
+template <typename T>
+void launch_axpby(long long n, double alpha, const T *x, double beta, const T *y, T *out, cudaStream_t st)
+{
+    k_axpby<T><<<vec_blocks(n), kVecThreads, 0, st>>>(n, alpha, x, beta, y, out);
+}
+
 template <typename T>
 int launch_cg_grad(long long n, const T *phi, const T *v, double mu, const double *mup, T *g,
                    const T *gprev, double *part, cudaStream_t st)
@@ -1011,6 +1044,8 @@ void launch_md_b(int nat, const double *m, double *V, const double *F, double dt
                                    const T *, T *, cudaStream_t);                                 \
     template int launch_sumsq<T>(long long, const T *, double *, cudaStream_t);                    \
     template int launch_extrap<T>(long long, const T *, const T *, T *, double *, cudaStream_t);   \
+    template int launch_dot<T>(long long, const T *, const T *, double *, cudaStream_t);          \
+    template void launch_axpby<T>(long long, double, const T *, double, const T *, T *, cudaStream_t); \
     template int launch_cg_grad<T>(long long, const T *, const T *, double, const double *, T *,   \
                                    const T *, double *, cudaStream_t);                            \
     template int launch_cg_dir<T>(long long, const T *, T *, double, const double *, const T *,    \

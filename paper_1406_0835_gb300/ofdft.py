@@ -108,6 +108,9 @@ SIGNATURES = {
     "ofdft_energy_potential": (ctypes.c_int, [ctypes.c_void_p, _P, ctypes.POINTER(Energy), _P]),
     "ofdft_minimize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
                                       ctypes.POINTER(Energy), ctypes.POINTER(Stats)]),
+    "ofdft_minimize_tn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.POINTER(Energy), ctypes.POINTER(Stats),
+                                         ctypes.POINTER(ctypes.c_int)]),
     "ofdft_forces": (ctypes.c_int, [ctypes.c_void_p, _P, _P]),
     "ofdft_get_density": (ctypes.c_int, [ctypes.c_void_p, _P]),
     "ofdft_stress": (ctypes.c_int, [ctypes.c_void_p, _P, _P]),
@@ -234,6 +237,16 @@ def ofdft_minimize(ctx, gtol=1e-8, maxit=5000, raise_on_noconv=True):
     if st != -3 or raise_on_noconv:
         _check(ctx, st)
     return E.as_dict(), S.as_dict()
+
+
+def ofdft_minimize_tn(ctx, gtol=1e-8, maxit=500, inner_max=20, eta=0.1, raise_on_noconv=True):
+    """Truncated-Newton minimisation; returns (energy dict, stats dict, Hessian products)."""
+    E, S, nh = Energy(), Stats(), ctypes.c_int()
+    st = load().ofdft_minimize_tn(ctx, float(gtol), int(maxit), int(inner_max), float(eta), ctypes.byref(E),
+                                  ctypes.byref(S), ctypes.byref(nh))
+    if st != 0 and not (st == -3 and not raise_on_noconv):
+        _check(ctx, st)
+    return E.as_dict(), S.as_dict(), nh.value
 
 
 def ofdft_minimize_start(ctx, gtol=1e-8, maxit=5000):
@@ -479,6 +492,9 @@ class Context:
 
     def minimize(self, gtol=1e-8, maxit=5000, raise_on_noconv=True):
         return ofdft_minimize(self.ctx, gtol, maxit, raise_on_noconv)
+
+    def minimize_tn(self, gtol=1e-8, maxit=500, inner_max=20, eta=0.1, raise_on_noconv=True):
+        return ofdft_minimize_tn(self.ctx, gtol, maxit, inner_max, eta, raise_on_noconv)
 
     def minimize_start(self, gtol=1e-8, maxit=5000):
         ofdft_minimize_start(self.ctx, gtol, maxit)
