@@ -254,7 +254,7 @@ __device__ __forceinline__ CC times_ik(CC x, int e, int n, R s)
 // Blocks per SM the transform kernels' registers are sized for (launch
 // bounds with 256 threads; 0: no bound).
 #ifndef OFDFT_FFT_MINB
-#define OFDFT_FFT_MINB 0
+#define OFDFT_FFT_MINB 4
 #endif
 #if OFDFT_FFT_MINB > 0
 #define OFDFT_FFT_BOUNDS __launch_bounds__(256, OFDFT_FFT_MINB)
