@@ -182,14 +182,17 @@ def fft_flops(n):
 # factors with their s^2-derivatives, n^(-1/3), PZ81, W and the energy
 # densities): about 150-250 flop per point; 200 is used.
 POINTWISE_FLOP = 200.0
-# DRAM bytes per grid point of one k_zgga<DD> launch (the FP64 contexts'
-# double-float kernel), from the ncu capture summarised in
-# profiles/k_zgga_dd_96.md (29.6 MB per launch at 96^3).
-ZGGA_DD_TRAFFIC_PER_POINT = (28.925952e6 + 0.652288e6) / 96 ** 3
+# Issued warp instructions and DRAM bytes per grid point of one k_pw<DD>
+# launch (the FP64 contexts' pointwise kernel, VT84F at an MD density, 96^3),
+# from the ncu capture summarised in profiles/k_pw_dd_96.md (114,446,727
+# warp instructions, 33.75 MB per launch).  Valid for that kernel only: set
+# to None when it changes until the capture is repeated.
+PW_DD_WARP_INST_PER_POINT = 114446727.0 / 96 ** 3
+PW_DD_TRAFFIC_PER_POINT = (28.428544e6 + 5.320960e6) / 96 ** 3
 # FP32-unit instructions per FP64-equivalent flop of the double-float
-# arithmetic: a sum (two_sum + tail + fast_two_sum) takes 11, a product
-# (two_prod + two FMAs + fast_two_sum) 9; FFT and pointwise work is about two
-# sums per product, so 10.3.
+# arithmetic in the cost model of the FFT and pointwise work: a sum
+# (two_sum + tail + fast_two_sum) takes 11, a product (two_prod + two FMAs
+# + fast_two_sum) 9, about two sums per product: 10.3.
 DD_INSTR_PER_FLOP = (2 * 11 + 9) / 3.0
 
 
@@ -270,32 +273,46 @@ def run_eval(args, rank, world):
 
 
 def roofline_entry(dominant, grid, kms, kcount, clk, peaks, precision="fp64"):
-    """Roofline position of the dominant kernel class.  FP64 contexts run it
-    in double-float on the FP32 units, so its ceiling is the SM issue rate
-    (152 SMs x 128 lanes x clock) over the instructions one FP64-equivalent
-    flop costs there (DD_INSTR_PER_FLOP); achieved = algorithmic flops
-    (FFT flops + the pointwise functional) over the mean event-timed launch."""
+    """Roofline position of the dominant kernel class.  On FP64 contexts the
+    pointwise kernel runs double-float arithmetic on the FP32 units and is
+    bound by instruction issue: achieved = its issued instructions (warp
+    instructions per grid point from the ncu capture x 32 lanes x points)
+    over the mean CUDA-event-timed launch; peak = 152 SMs x 4 schedulers x
+    32 lanes x the median SM clock of the timed region.  The model figures
+    beside it: FP64-equivalent TFLOP/s of the algorithmic flops (FFT flops +
+    200 flop per point for the pointwise functional) against the issue rate
+    over DD_INSTR_PER_FLOP, and against the FP64 units' peak."""
     flops, byts = kernel_model(dominant, grid)
     avg_s = (kms / 1e3) / max(kcount, 1)
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     issue = 152 * 128 * (sm_mhz * 1e6)                      # thread instructions / s
-    dd_peak = issue / DD_INSTR_PER_FLOP / 1e12              # FP64-equivalent TFLOP/s
+    dd_peak = issue / DD_INSTR_PER_FLOP / 1e12              # FP64-equivalent TFLOP/s (model)
     fp64_peak = 152 * 2 * 2 * (sm_mhz * 1e6) / 1e12         # the FP64 units: 2 DFMA / SM / clock
     ok = kcount > 0
     npts = grid[0] * grid[1] * grid[2]
-    achieved = flops / avg_s / 1e12 if ok else None
-    traffic = (ZGGA_DD_TRAFFIC_PER_POINT * npts
-               if dominant == "zgga" and precision == "fp64" and ZGGA_DD_TRAFFIC_PER_POINT else None)
-    return {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": dd_peak,
-            "unit": "TFLOP/s (FP64-equivalent, double-float on the FP32 units)",
-            "frac": achieved / dd_peak if ok else None, "traffic": traffic,
-            "launches": kcount, "avg_launch_us": avg_s * 1e6, "algorithmic_flops": flops,
-            "algorithmic_bytes": byts, "hbm_gbs": byts / avg_s / 1e9 if ok else None,
-            "hbm_peak_gbs": peaks.get("hbm_gbs"), "fp64_unit_peak": fp64_peak,
-            "achieved_over_fp64_unit_peak": achieved / fp64_peak if ok else None,
-            "timed_launches": "FP64 and FP32 launches of the class averaged" if precision == "mixed" else "FP64",
-            "peak_note": "peak = 152 SMs x 128 lanes x median SM clock / %.1f FP32 instructions per "
-                         "FP64-equivalent flop; fp64_unit_peak = 152 x 2 DFMA/clk x clock" % DD_INSTR_PER_FLOP}
+    flops_rate = flops / avg_s / 1e12 if ok else None
+    measured = dominant == "pw" and precision == "fp64" and PW_DD_WARP_INST_PER_POINT is not None
+    out = {"bound": "alu", "kernel": dominant, "launches": kcount, "avg_launch_us": avg_s * 1e6,
+           "algorithmic_flops": flops, "algorithmic_bytes": byts,
+           "hbm_gbs": byts / avg_s / 1e9 if ok else None, "hbm_peak_gbs": peaks.get("hbm_gbs"),
+           "fp64_equiv_tflops": flops_rate, "fp64_equiv_model_peak": dd_peak,
+           "frac_model": flops_rate / dd_peak if ok else None, "fp64_unit_peak": fp64_peak,
+           "timed_launches": "FP64 and FP32 launches of the class averaged" if precision == "mixed" else "FP64"}
+    if measured and ok:
+        inst = PW_DD_WARP_INST_PER_POINT * 32 * npts
+        out.update({"achieved": inst / avg_s / 1e12, "peak": issue / 1e12,
+                    "unit": "T thread-instructions/s (issue, FP32 units)",
+                    "frac": inst / avg_s / issue, "traffic": PW_DD_TRAFFIC_PER_POINT * npts,
+                    "instructions_per_launch": inst,
+                    "peak_note": "peak = 152 SMs x 128 lanes x median SM clock; instructions per launch "
+                                 "from ncu (smsp__inst_executed x 32), time from CUDA events"})
+    else:
+        out.update({"achieved": flops_rate, "peak": dd_peak,
+                    "unit": "TFLOP/s (FP64-equivalent, double-float on the FP32 units)",
+                    "frac": out["frac_model"], "traffic": None,
+                    "peak_note": "peak = 152 SMs x 128 lanes x median SM clock / %.1f FP32 instructions "
+                                 "per FP64-equivalent flop" % DD_INSTR_PER_FLOP})
+    return out
 
 
 def time_dominant(ctx, ofdft, dominant, stream, work):
