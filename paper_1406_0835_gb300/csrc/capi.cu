@@ -1428,8 +1428,10 @@ template <typename T> ofdft_status time_evals(ofdft_ctx *c, FieldSet &f, int rep
     return OFDFT_OK;
 }
 
-// Pick the column-tile width of the y/x passes (the z kernels do not depend
-// on it), then the z line pairs per block, by timing whole evaluations.
+// Pick the launch shapes by timing whole evaluations: tile width and
+// threads of the y/x passes together, then line pairs per block and threads
+// of the z passes, then tile width and threads of the derivative passes,
+// then each axis's radix schedule.
 template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
 {
     FieldSet &f = c->f[k];
@@ -1456,79 +1458,60 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
     const size_t dyn = (size_t)optin - 8192;
     GridInfo best = f.gt;
     float best_ms = 1e30f;
-    for (int tk : {4, 8, 16}) {
-        GridInfo g = best;
-        g.tk = tk;
-        if (tk > g.K && tk != 4) continue;
-        if (field_smem_max(g, sizeof(cplx<T>)) > dyn) continue;
+    // try g (if it fits); keep it when faster than the best so far
+    auto trial = [&](const GridInfo &g) -> ofdft_status {
+        if (field_smem_max(g, sizeof(cplx<T>)) > dyn) return OFDFT_OK;
         f.gt = g;
         float ms;
         ofdft_status r = time_evals<T>(c, f, reps, ms);
-        if (r != OFDFT_OK) return r;
-        if (ms < best_ms) {
+        if (r == OFDFT_OK && ms < best_ms) {
             best_ms = ms;
             best = g;
         }
-    }
-    best_ms = 1e30f;
-    GridInfo base = best;
-    for (int zp : {1, 2, 4, 8}) {
-        GridInfo g = base;
-        g.zP = zp;
-        if ((long long)zp * g.nz > 2048 || (long long)zp > (long long)g.nx * g.ny / 2) continue;
-        if (field_smem_max(g, sizeof(cplx<T>)) > dyn) continue;
-        f.gt = g;
-        float ms;
-        ofdft_status r = time_evals<T>(c, f, reps, ms);
-        if (r != OFDFT_OK) return r;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = g;
-        }
-    }
-    // threads per block of the z passes, then of the y/x passes (the FP64 z
-    // passes use up to 128 registers a thread: 256 threads at most there)
-    for (int pass = 0; pass < 2; ++pass) {
-        best_ms = 1e30f;
-        GridInfo base2 = best;
-        const int thmax = std::min((sizeof(T) == 8 && pass == 0) ? 256 : 512, fft_max_threads());
-        for (int th : {128, 256, 512}) {
-            if (th > thmax) continue;
-            GridInfo g = base2;
-            if (pass == 0) g.zth = th;
-            else g.xth = th;
-            f.gt = g;
-            float ms;
-            ofdft_status r = time_evals<T>(c, f, reps, ms);
-            if (r != OFDFT_OK) return r;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = g;
-            }
-        }
-    }
-    // the derivative passes' tile width and threads (GGA evaluations only)
-    if (c->fp.kind != 0) {
-        for (int pass = 0; pass < 2; ++pass) {
-            best_ms = 1e30f;
-            GridInfo base3 = best;
-            const int opts[3] = {4, 8, 16}, topts[3] = {64, 128, 256};
-            for (int k = 0; k < 3; ++k) {
-                GridInfo g = base3;
-                if (pass == 0) g.dk = opts[k];
-                else g.dth = topts[k];
-                if (g.dth > fft_max_threads()) continue;
-                if (field_smem_max(g, sizeof(cplx<T>)) > dyn) continue;
-                f.gt = g;
-                float ms;
-                ofdft_status r = time_evals<T>(c, f, reps, ms);
+        return r;
+    };
+    const int tmax = fft_max_threads();
+    // the y/x passes: tile width and threads together (a stage's butterflies
+    // per tile set how many threads can work)
+    {
+        const GridInfo base = best;
+        for (int tk : {4, 8, 16})
+            for (int th : {128, 256, 512}) {
+                if ((tk > base.K && tk != 4) || th > tmax) continue;
+                GridInfo g = base;
+                g.tk = tk;
+                g.xth = th;
+                ofdft_status r = trial(g);
                 if (r != OFDFT_OK) return r;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = g;
-                }
             }
-        }
+    }
+    // the z passes: line pairs per block and threads together (the FP64 z
+    // passes keep at most 256 threads)
+    {
+        const GridInfo base = best;
+        for (int zp : {1, 2, 4, 8})
+            for (int th : {128, 256, 512}) {
+                if ((long long)zp * base.nz > 2048 || (long long)zp > (long long)base.nx * base.ny / 2) continue;
+                if (th > tmax || (sizeof(T) == 8 && th > 256)) continue;
+                GridInfo g = base;
+                g.zP = zp;
+                g.zth = th;
+                ofdft_status r = trial(g);
+                if (r != OFDFT_OK) return r;
+            }
+    }
+    // the derivative passes' tile width and threads together (GGA only)
+    if (c->fp.kind != 0) {
+        const GridInfo base = best;
+        for (int dk : {4, 8, 16})
+            for (int th : {64, 128, 256}) {
+                if (th > tmax) continue;
+                GridInfo g = base;
+                g.dk = dk;
+                g.dth = th;
+                ofdft_status r = trial(g);
+                if (r != OFDFT_OK) return r;
+            }
     }
     f.gt = best;
     // the Stockham schedule of each axis: power-of-two radices up to 8 or

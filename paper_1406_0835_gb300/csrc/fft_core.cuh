@@ -52,9 +52,10 @@ template <typename C, bool INV> __device__ __forceinline__ void dft4(C *v)
 template <typename C, bool INV> __device__ __forceinline__ void dft3(C *v)
 {
     typedef decltype(C::x) T;
-    const T s3 = T(0.86602540378443864676);   // sin(2 pi/3)
+    constexpr T s3(0.86602540378443864676);   // sin(2 pi/3); constexpr: split at compile time
+    constexpr T half(0.5);
     C t1 = cadd(v[1], v[2]);
-    C t2 = csub(v[0], cscale(t1, T(0.5)));
+    C t2 = csub(v[0], cscale(t1, half));
     C t3 = cmuli<C, INV>(cscale(csub(v[1], v[2]), s3));
     v[0] = cadd(v[0], t1);
     v[1] = cadd(t2, t3);
@@ -64,8 +65,8 @@ template <typename C, bool INV> __device__ __forceinline__ void dft3(C *v)
 template <typename C, bool INV> __device__ __forceinline__ void dft5(C *v)
 {
     typedef decltype(C::x) T;
-    const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);
-    const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);
+    constexpr T c1(0.30901699437494742410), c2(-0.80901699437494742410);
+    constexpr T s1(0.95105651629515357212), s2(0.58778525229247312917);
     C p14 = cadd(v[1], v[4]), m14 = csub(v[1], v[4]);
     C p23 = cadd(v[2], v[3]), m23 = csub(v[2], v[3]);
     C a1 = cadd(v[0], cadd(cscale(p14, c1), cscale(p23, c2)));
@@ -82,7 +83,7 @@ template <typename C, bool INV> __device__ __forceinline__ void dft5(C *v)
 template <typename C, bool INV> __device__ __forceinline__ void dft8(C *v)
 {
     typedef decltype(C::x) T;
-    const T r = T(0.70710678118654752440);
+    constexpr T r(0.70710678118654752440);
     C e[4] = {v[0], v[2], v[4], v[6]};
     C o[4] = {v[1], v[3], v[5], v[7]};
     dft4<C, INV>(e);

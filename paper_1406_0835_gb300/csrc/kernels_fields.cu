@@ -311,7 +311,7 @@ __global__ void OFDFT_FFT_BOUNDS k_zfwd(GridInfo g, FftAxis az, int P, const typ
     __syncthreads();
     CC *X = fft_lines<CC, false>(A, B, az, nl, nz, 1, false);
     const long long obase = 2 * p0 * K;
-    const R half = R(0.5), mhalf = R(-0.5);
+    constexpr R half(0.5), mhalf(-0.5);
     RowCol rk(K);
     for (int i = threadIdx.x; i < 2 * nl * K; i += blockDim.x, rk.next()) {
         const int line = rk.r, k = rk.c;
@@ -367,7 +367,7 @@ __device__ __forceinline__ void unpack_r2c(const typename KT<PR>::CC *X, long lo
 {
     typedef typename KT<PR>::R R;
     typedef typename KT<PR>::CC CC;
-    const R half = R(0.5), mhalf = R(-0.5);
+    constexpr R half(0.5), mhalf(-0.5);
     RowCol rc(K);
     for (int i = threadIdx.x; i < 2 * nl * K; i += blockDim.x, rc.next()) {
         const int line = rc.r, k = rc.c;
