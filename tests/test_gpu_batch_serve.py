@@ -154,3 +154,23 @@ def test_serving_results_are_the_same_alone_and_in_the_mix():
         assert m["E"]["F_tot"] == a["E"]["F_tot"]
         assert m["P_mean"] == a["P_mean"]
         assert m["evaluations"] == a["evaluations"]
+
+
+def test_largest_served_request_matches_fp64():
+    """One request at the largest size of the serving workload's range
+    (1024 H, 256^3 grid, VT84F, 0.1 g/cm^3, 100 kK): the served mixed-
+    precision result after one MD step against the same step on an FP64
+    context, within the stated per-result bars (free energy 1e-6 Ha/atom,
+    pressure 1e-3 relative)."""
+    d = inputs.hydrogen(1024, 0.1, 1.0e5, 256, seed=21, functional="vt84f", vel_seed=22)
+    with ofdft.Server(max_slots=1) as s:
+        rid = s.submit(d["L"], d["grid"], d["ions"], d["Z"], d["T"], "vt84f", "mixed", md_steps=1,
+                       dt_fs=0.2, vel=d["vel"], gtol=ofdft.MIXED_MD_GTOL, maxit=20000)
+        s.drain(timeout_s=900)
+        r = s.poll(rid)
+    assert r["status"] == 0 and r["steps_done"] == 1
+    with _ctx(d) as c:
+        c.md_step(0.2, d["T"], nsteps=0, pos=d["ions"], vel=d["vel"], gtol=1e-8, maxit=20000)
+        out = c.md_step(0.2, d["T"], nsteps=1, gtol=1e-8, maxit=20000)
+    assert abs(r["E"]["F_tot"] - out["E"]["F_tot"]) / 1024 < 1e-6
+    assert abs(r["P_mean"] - out["E"]["P"]) <= 1e-3 * abs(out["E"]["P"])
