@@ -570,13 +570,11 @@ ofdft_status enqueue_update(ofdft_ctx *c, FieldSet &f, cudaGraphConditionalHandl
     const long long N = c->g.N;
     cudaStream_t st = c->st;
     CgState *s = f.cs;
-    launch_accept<T>(N, &s->accepted, (T *)f.phi, (const T *)f.phit, (T *)f.v, (const T *)f.vt,
-                     (const T *)f.g, (T *)f.gprev, st);
-    int nb = launch_cg_grad<T>(N, (const T *)f.phi, (const T *)f.v, 0.0, &s->mu, (T *)f.g,
-                               (const T *)f.gprev, c->part, st);
+    int nb = launch_cg_update<T>(N, &s->accepted, (T *)f.phi, (const T *)f.phit, (T *)f.v, (const T *)f.vt,
+                                 &s->mu, (T *)f.g, (T *)f.gprev, c->part, st);
     launch_reduce(c->part, nb, 2, s->rg, st);
     launch_ctl_grad(s, 0, outer, use_cond, st);
-    c->launches += 4;
+    c->launches += 3;
     DBG("cg update");
     return OFDFT_OK;
 }
@@ -793,7 +791,7 @@ ofdft_status minimize_start(ofdft_ctx *c, double gtol, int maxit)
 // (direction + update), per line-search trial (evaluation + controller).
 long long graph_launches(const ofdft_ctx *c, const CgState &h)
 {
-    return 8 + eval_kernel_count(c) + (long long)h.nouter * 10 +
+    return 8 + eval_kernel_count(c) + (long long)h.nouter * 9 +
            (long long)(h.nevals - 1) * (eval_kernel_count(c) + 1);
 }
 

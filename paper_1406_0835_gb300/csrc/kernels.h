@@ -60,10 +60,11 @@ void launch_reduce_eval(const double *pA, int na, const double *pB, int nb, cons
                         double *out, cudaStream_t st);
 template <typename T> void launch_fill(long long n, T *x, T val, cudaStream_t st);
 template <typename T> void launch_scale(long long n, T *x, double s, const double *sp, cudaStream_t st);
-// if *accepted: phi <- phit, v <- vt, gprev <- g
+// if *accepted: phi <- phit, v <- vt, gprev <- g; then g = 2 phi (v - *mup);
+// part: sum g^2, sum g.gprev (returns blocks)
 template <typename T>
-void launch_accept(long long n, const int *accepted, T *phi, const T *phit, T *v, const T *vt,
-                   const T *g, T *gprev, cudaStream_t st);
+int launch_cg_update(long long n, const int *accepted, T *phi, const T *phit, T *v, const T *vt,
+                     const double *mup, T *g, T *gprev, double *part, cudaStream_t st);
 template <typename T, typename U> void launch_convert(long long n, const T *x, U *y, cudaStream_t st);
 // sum x^2 -> part (returns blocks)
 template <typename T> int launch_sumsq(long long n, const T *x, double *part, cudaStream_t st);

@@ -18,6 +18,36 @@ int vec_blocks(long long n)
     return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);   // 8 blocks per SM at most
 }
 
+// Blocks of the vector kernels that also reduce: two per SM, so that each
+// thread sums many elements before the block reduction (whose cost is per
+// thread, not per element).
+int red_blocks(long long n)
+{
+    static const int sms = [] {
+        int dev = 0, c = 0;
+        return (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && c > 0)
+                   ? c
+                   : 152;
+    }();
+    long long b = (n + kVecThreads - 1) / kVecThreads;
+    const long long cap = 2LL * sms;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+// Block sum of binary64 per-thread partials through the double-float warp
+// stage (block_sum_f2): each partial is split into a double-float pair with
+// integer operations (split_int, relative error < 2^-46), so the shuffles and
+// adds run on the integer and FP32 units instead of the FP64 ones.
+template <int NQ> __device__ __forceinline__ void block_sum_split(const double *v, double *tot)
+{
+    ff::f2 d[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) d[q] = ff::split_int(v[q]);
+    block_sum_f2<NQ>(d, tot);
+}
+template <int NQ> __device__ __forceinline__ void block_sum_split(AccF *v, double *tot) { block_sum<NQ>(v, tot); }
+
 __global__ void k_reduce(const double *__restrict__ part, int nblk, double *__restrict__ out)
 {
     double v[1] = {0.0};
@@ -91,7 +121,7 @@ template <typename T> __global__ void k_sumsq(long long n, const T *__restrict__
         v[0] += a * a;
     }
     double tot[1];
-    block_sum<1>(v, tot);
+    block_sum_split<1>(v, tot);
     if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
 }
 
@@ -128,7 +158,7 @@ __global__ void k_cg_grad(long long n, const T *__restrict__ phi, const T *__res
         if (gprev != nullptr) acc[1] += (P)gi * (P)gprev[i];
     }
     double tot[2];
-    block_sum<2>(acc, tot);
+    block_sum_split<2>(acc, tot);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = tot[0];
         part[gridDim.x + blockIdx.x] = tot[1];
@@ -157,7 +187,7 @@ __global__ void k_cg_dir(long long n, const T *__restrict__ g, T *__restrict__ d
         acc[4] += p * (P)gi;
     }
     double tot[5];
-    block_sum<5>(acc, tot);
+    block_sum_split<5>(acc, tot);
     if (threadIdx.x == 0)
         for (int q = 0; q < 5; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = tot[q];
 }
@@ -185,7 +215,7 @@ __global__ void k_cg_dhat(long long n, const T *__restrict__ g, T *__restrict__ 
         acc[0] += P(2) * (P)phi[i] * (P)v[i] * (P)dh;
     }
     double tot[1];
-    block_sum<1>(acc, tot);
+    block_sum_split<1>(acc, tot);
     if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
 }
 
@@ -197,8 +227,9 @@ __global__ void k_dot(long long n, const T *__restrict__ a, const T *__restrict_
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         v[0] += (double)a[i] * (double)b[i];
-    block_sum<1>(v);
-    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+    double tot[1];
+    block_sum_split<1>(v, tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
 }
 
 // out = alpha x + beta y (out may alias x or y).
@@ -210,19 +241,46 @@ __global__ void k_axpby(long long n, double alpha, const T *x, double beta, cons
         out[i] = (T)(alpha * (double)x[i] + beta * (double)y[i]);
 }
 
-// Accept a line-search trial: phi <- phi_trial, v <- v_trial, g_prev <- g,
-// when the device CG state says so.
+// One CG update after a line search: when the device CG state says the
+// trial was accepted, phi <- phi_trial, v <- v_trial, g_prev <- g first;
+// then g = 2 phi (v - mu) as in k_cg_grad, with the partials sum g^2 and
+// sum g.g_prev.  Each element is read once (the accepted trial's phi and v
+// feed the gradient directly).
 template <typename T>
-__global__ void k_accept(long long n, const int *accepted, T *__restrict__ phi,
-                         const T *__restrict__ phit, T *__restrict__ v, const T *__restrict__ vt,
-                         const T *__restrict__ g, T *__restrict__ gprev)
+__global__ void k_cg_update(long long n, const int *__restrict__ accepted, T *__restrict__ phi,
+                            const T *__restrict__ phit, T *__restrict__ v, const T *__restrict__ vt,
+                            const double *mup, T *__restrict__ g, T *__restrict__ gprev, double *part)
 {
-    if (*accepted == 0) return;
+    typedef typename AccT<T>::type A;
+    typedef typename AccT<T>::term P;
+    const bool acc_t = *accepted != 0;
+    const T mut = T(*mup);
+    A acc[2] = {A(0), A(0)};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        phi[i] = phit[i];
-        v[i] = vt[i];
-        gprev[i] = g[i];
+        T p, vv, go;
+        if (acc_t) {
+            p = phit[i];
+            vv = vt[i];
+            go = g[i];
+            phi[i] = p;
+            v[i] = vv;
+            gprev[i] = go;
+        } else {
+            p = phi[i];
+            vv = v[i];
+            go = gprev[i];
+        }
+        T gi = T(2) * p * (vv - mut);
+        g[i] = gi;
+        acc[0] += (P)gi * (P)gi;
+        acc[1] += (P)gi * (P)go;
+    }
+    double tot[2];
+    block_sum_split<2>(acc, tot);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tot[0];
+        part[gridDim.x + blockIdx.x] = tot[1];
     }
 }
 
@@ -892,10 +950,12 @@ template <typename T> void launch_scale(long long n, T *x, double s, const doubl
 }
 
 template <typename T>
-void launch_accept(long long n, const int *accepted, T *phi, const T *phit, T *v, const T *vt,
-                   const T *g, T *gprev, cudaStream_t st)
+int launch_cg_update(long long n, const int *accepted, T *phi, const T *phit, T *v, const T *vt,
+                     const double *mup, T *g, T *gprev, double *part, cudaStream_t st)
 {
-    k_accept<T><<<vec_blocks(n), kVecThreads, 0, st>>>(n, accepted, phi, phit, v, vt, g, gprev);
+    int b = red_blocks(n);
+    k_cg_update<T><<<b, kVecThreads, 0, st>>>(n, accepted, phi, phit, v, vt, mup, g, gprev, part);
+    return b;
 }
 template <typename T, typename U> void launch_convert(long long n, const T *x, U *y, cudaStream_t st)
 {
@@ -903,7 +963,7 @@ template <typename T, typename U> void launch_convert(long long n, const T *x, U
 }
 template <typename T> int launch_sumsq(long long n, const T *x, double *part, cudaStream_t st)
 {
-    int b = vec_blocks(n);
+    int b = red_blocks(n);
     k_sumsq<T><<<b, kVecThreads, 0, st>>>(n, x, part);
     return b;
 }
@@ -916,7 +976,7 @@ int launch_extrap(long long n, const T *x, const T *xp, T *y, double *part, cuda
 }
 template <typename T> int launch_dot(long long n, const T *a, const T *b, double *part, cudaStream_t st)
 {
-    int nb = vec_blocks(n);
+    int nb = red_blocks(n);
     k_dot<T><<<nb, kVecThreads, 0, st>>>(n, a, b, part);
     return nb;
 }
@@ -930,7 +990,7 @@ template <typename T>
 int launch_cg_grad(long long n, const T *phi, const T *v, double mu, const double *mup, T *g,
                    const T *gprev, double *part, cudaStream_t st)
 {
-    int b = vec_blocks(n);
+    int b = red_blocks(n);
     k_cg_grad<T><<<b, kVecThreads, 0, st>>>(n, phi, v, mu, mup, g, gprev, part);
     return b;
 }
@@ -938,7 +998,7 @@ template <typename T>
 int launch_cg_dir(long long n, const T *g, T *d, double beta, const double *betap, const T *phi,
                   double *part, cudaStream_t st)
 {
-    int b = vec_blocks(n);
+    int b = red_blocks(n);
     k_cg_dir<T><<<b, kVecThreads, 0, st>>>(n, g, d, beta, betap, phi, part);
     return b;
 }
@@ -946,7 +1006,7 @@ template <typename T>
 int launch_cg_dhat(long long n, const T *g, T *d, const T *phi, const T *v, double c1, double c2,
                    int restart, const double *c12r, T *dhat, double *part, cudaStream_t st)
 {
-    int b = vec_blocks(n);
+    int b = red_blocks(n);
     k_cg_dhat<T><<<b, kVecThreads, 0, st>>>(n, g, d, phi, v, c1, c2, restart, c12r, dhat, part);
     return b;
 }
@@ -1040,8 +1100,8 @@ void launch_md_b(int nat, const double *m, double *V, const double *F, double dt
 #define OFDFT_MISC_INST(T)                                                                         \
     template void launch_fill<T>(long long, T *, T, cudaStream_t);                                 \
     template void launch_scale<T>(long long, T *, double, const double *, cudaStream_t);           \
-    template void launch_accept<T>(long long, const int *, T *, const T *, T *, const T *,         \
-                                   const T *, T *, cudaStream_t);                                 \
+    template int launch_cg_update<T>(long long, const int *, T *, const T *, T *, const T *,      \
+                                     const double *, T *, T *, double *, cudaStream_t);           \
     template int launch_sumsq<T>(long long, const T *, double *, cudaStream_t);                    \
     template int launch_extrap<T>(long long, const T *, const T *, T *, double *, cudaStream_t);   \
     template int launch_dot<T>(long long, const T *, const T *, double *, cudaStream_t);          \
