@@ -338,7 +338,8 @@ ofdft_status ofdft_sizes(ofdft_ctx *ctx, long long *N, int *nat);
  * the context's stream (no extra synchronisation).  id: 0 off,
  * 1 pointwise GGA functional, 2 derivative passes along x and y (gradient of
  * n, divergence of W), 4 y pass, 5 z forward pass, 6 z final pass, 7 x pass
- * of the Hartree and local-pseudopotential potential.  ofdft_timer_read
+ * of the Hartree and local-pseudopotential potential; id + 8 times only the
+ * class's FP32 launches, id + 16 only its FP64 ones.  ofdft_timer_read
  * synchronises the stream,
  * returns the summed event time (ms) and the launch count, and optionally
  * clears them.

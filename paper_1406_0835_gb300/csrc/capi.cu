@@ -81,6 +81,7 @@ struct ofdft_ctx {
     // ions
     double *Rd = nullptr, *Zd = nullptr, *Fd = nullptr, *Vd = nullptr, *Md = nullptr, *nh = nullptr;
     double2 *px = nullptr, *py = nullptr, *pz = nullptr;
+    PhaseTablesDD pdd = {nullptr, nullptr, nullptr, nullptr};   // double-float copies (one allocation at xT)
     double *fpart = nullptr;
     size_t fpart_len = 0;
     // Ewald
@@ -100,6 +101,11 @@ struct ofdft_ctx {
     std::string err;
     bool debug_sync = false;    // OFDFT_DEBUG_SYNC=1: check every launch, no graphs
     bool use_graphs = true;     // OFDFT_NO_GRAPHS=1: host-driven loops
+    // fork/join of a GGA evaluation: two auxiliary streams (the Hartree
+    // chain; the second derivative pass of a pair) and the events between
+    // them and the evaluation's stream
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t fj[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     // kernel timer (diagnostics)
     int timer_id = 0;
     std::vector<cudaEvent_t> tev;
@@ -201,11 +207,14 @@ ofdft_status sync_read(ofdft_ctx *c, int n)
 
 enum TimerId { TM_PW = 1, TM_DLINE = 2, TM_Y = 4, TM_ZFWD = 5, TM_ZFINAL = 6, TM_XHL = 7 };
 
-// Event pair around a launch of the selected kernel class (host-driven mode only).
+// Event pair around a launch of the selected kernel class (host-driven mode
+// only).  The selection's bit 8 restricts it to the FP32 launches, bit 16 to
+// the FP64 ones.
 struct TimerScope {
     ofdft_ctx *c;
     bool on;
-    TimerScope(ofdft_ctx *c_, int id) : c(c_), on(c_->timer_id == id)
+    TimerScope(ofdft_ctx *c_, int id, bool f32)
+        : c(c_), on((c_->timer_id & 7) == id && !((c_->timer_id & 8) && !f32) && !((c_->timer_id & 16) && f32))
     {
         if (!on) return;
         if (c->tev_used + 2 > c->tev.size()) {
@@ -289,44 +298,63 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
     const long long npairs = (long long)g.nx * g.ny / 2;
     double *pA = c->part, *pB = pA + 3 * nbx, *pC = pB + 6 * npairs;
     {
-        TimerScope ts(c, TM_ZFWD);
+        TimerScope ts(c, TM_ZFWD, sizeof(T) == 4);
         T *dz = fttf ? nullptr : d2;
         if (phi0) launch_zfwd<T>(g, az, 2, nullptr, phi0, dh, (T)cth, (T)sth, csd, ph, s0, st, dz);
         else launch_zfwd<T>(g, az, 1, nullptr, ph, nullptr, T(0), T(0), nullptr, nullptr, s0, st, dz);
     }
     DBG("k_zfwd");
+    // GGA: the Hartree chain (y, x, y^-1 on the first spectrum) needs only
+    // zfwd's spectrum and the gradient chain only phi and d_z n, so the
+    // chain runs on aux[0] beside the derivative passes and the pointwise
+    // stage; the two derivative passes of each pair run side by side
+    // (aux[1]).  Timers and per-launch checks keep one stream.
+    const bool fork = !fttf && c->aux[0] && c->timer_id == 0 && !c->debug_sync;
+    cudaStream_t sh = st;   // stream of the Hartree chain
+    if (fork) {
+        CK(cudaEventRecord(c->fj[0], st));
+        CK(cudaStreamWaitEvent(c->aux[0], c->fj[0], 0));
+        CK(cudaStreamWaitEvent(c->aux[1], c->fj[0], 0));
+        sh = c->aux[0];
+    }
     {
-        TimerScope ts(c, TM_Y);
-        launch_ypass<T>(g, ay, false, s0, 1, fs, st);
+        TimerScope ts(c, TM_Y, sizeof(T) == 4);
+        launch_ypass<T>(g, ay, false, s0, 1, fs, sh);
     }
     DBG("k_ypass fwd");
     {
-        TimerScope ts(c, TM_XHL);
-        launch_xhl<T>(g, ax, s0, vext, (keep_nG && fttf) ? s1 : nullptr, 1, pA, st);
+        TimerScope ts(c, TM_XHL, sizeof(T) == 4);
+        launch_xhl<T>(g, ax, s0, vext, (keep_nG && fttf) ? s1 : nullptr, 1, pA, sh);
     }
     DBG("k_xhl");
     {
-        TimerScope ts(c, TM_Y);
-        launch_ypass<T>(g, ay, true, s0, 1, fs, st);
+        TimerScope ts(c, TM_Y, sizeof(T) == 4);
+        launch_ypass<T>(g, ay, true, s0, 1, fs, sh);
     }
     DBG("k_ypass inv");
+    if (fork) CK(cudaEventRecord(c->fj[1], sh));
     int nbz, nbg = 0;   // blocks of the z passes (zfinal) and of the pointwise stage: their partial sums
     if (fttf) {
-        TimerScope ts(c, TM_ZFINAL);
+        TimerScope ts(c, TM_ZFINAL, sizeof(T) == 4);
         nbz = launch_zfinal<T>(g, az, true, s0, nullptr, ph, phi0, dh, (T)cth, (T)sth, csd, (T)c->T,
                                c->fp, tab, c->xc, vout, pC, st);
     } else {
+        cudaStream_t s2nd = fork ? c->aux[1] : st;   // stream of each pair's second pass
         {
-            TimerScope ts(c, TM_DLINE);
+            TimerScope ts(c, TM_DLINE, sizeof(T) == 4);
             launch_dline<T>(g, ax, 0, 0, 0, ph, d0, st);
         }
         {
-            TimerScope ts(c, TM_DLINE);
-            launch_dline<T>(g, ay, 1, 0, 0, ph, d1, st);
+            TimerScope ts(c, TM_DLINE, sizeof(T) == 4);
+            launch_dline<T>(g, ay, 1, 0, 0, ph, d1, s2nd);
+        }
+        if (fork) {
+            CK(cudaEventRecord(c->fj[2], s2nd));
+            CK(cudaStreamWaitEvent(st, c->fj[2], 0));
         }
         DBG("k_dline (grad n)");
         {
-            TimerScope ts(c, TM_PW);
+            TimerScope ts(c, TM_PW, sizeof(T) == 4);
             if (spart) {
                 pB = spart;
                 nbg = launch_pw<T>(g, d0, d1, d2, ph, (T)c->T, c->fp, tab, c->xc, (T *)f.vpart, pB, true, st);
@@ -336,18 +364,29 @@ ofdft_status enqueue_eval(ofdft_ctx *c, FieldSet &f, T *ph, const T *phi0, const
             }
         }
         DBG("k_pw");
+        if (fork) {
+            CK(cudaEventRecord(c->fj[3], st));
+            CK(cudaStreamWaitEvent(s2nd, c->fj[3], 0));
+        }
+        // d_y U_y into vout, d_x U_x in place over U_x (d0); the final z pass
+        // subtracts both
         {
-            TimerScope ts(c, TM_DLINE);
-            launch_dline<T>(g, ax, 0, 1, 0, d0, vout, st);
+            TimerScope ts(c, TM_DLINE, sizeof(T) == 4);
+            launch_dline<T>(g, ay, 1, 1, 0, d1, vout, st);
         }
         {
-            TimerScope ts(c, TM_DLINE);
-            launch_dline<T>(g, ay, 1, 1, 1, d1, vout, st);
+            TimerScope ts(c, TM_DLINE, sizeof(T) == 4);
+            launch_dline<T>(g, ax, 0, 1, 0, d0, d0, s2nd);
+        }
+        if (fork) {
+            CK(cudaEventRecord(c->fj[4], s2nd));
+            CK(cudaStreamWaitEvent(st, c->fj[4], 0));
+            CK(cudaStreamWaitEvent(st, c->fj[1], 0));
         }
         DBG("k_dline (div W)");
-        TimerScope ts(c, TM_ZFINAL);
-        nbz = launch_zfinal_gga<T>(g, az, s0, d2, (const T *)f.vpart, vout, ph, phi0, dh, (T)cth, (T)sth, csd,
-                                   vout, pC, st);
+        TimerScope ts(c, TM_ZFINAL, sizeof(T) == 4);
+        nbz = launch_zfinal_gga<T>(g, az, s0, d2, (const T *)f.vpart, vout, d0, ph, phi0, dh, (T)cth, (T)sth,
+                                   csd, vout, pC, st);
     }
     DBG("k_zfinal");
     launch_reduce_eval(pA, nbx, pB, nbg, pC, nbz, !fttf, sums, st);
@@ -479,8 +518,9 @@ ofdft_status update_ions(ofdft_ctx *c)
 {
     const GridInfo &g = c->g;
     cudaStream_t st = c->st;
-    launch_phases(g, c->nat, c->Rd, c->px, c->py, c->pz, st);
-    launch_vext(g, c->nat, c->Zd, c->px, c->py, c->pz, (double2 *)c->f[0].vext, st);
+    const PhaseTablesDD *dd = g.dd ? &c->pdd : nullptr;
+    launch_phases(g, c->nat, c->Rd, c->px, c->py, c->pz, dd, st);
+    launch_vext(g, c->nat, c->Zd, c->px, c->py, c->pz, dd, (double2 *)c->f[0].vext, st);
     if (c->f[1].valid)
         launch_convert<double, float>(((g.lpp || g.tri) ? 4 : 2) * g.NH, (const double *)c->f[0].vext, (float *)c->f[1].vext,
                                       st);
@@ -1199,7 +1239,8 @@ ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
     if (s != OFDFT_OK) return s;
     const GridInfo &g = c->g;
     const double2 *nG = (const double2 *)f.spec + f.spec_stride;
-    size_t need = (size_t)c->nat * 1216 * 3 + 16;
+    const PhaseTablesDD *dd = g.dd ? &c->pdd : nullptr;
+    size_t need = (size_t)c->nat * lpp_force_chunks(g, c->nat, dd != nullptr) * 3 + 16;
     if (need > c->fpart_len) {
         if (c->fpart) cudaFreeAsync(c->fpart, c->st);
         c->fpart = nullptr;
@@ -1208,7 +1249,7 @@ ofdft_status forces_now(ofdft_ctx *c, EvalScalars &es)
     }
     // the third spectrum is free after an evaluation (ftTF and GGA alike)
     double2 *cn = (double2 *)f.spec + 2 * f.spec_stride;
-    int nchunk = launch_lpp_forces<double>(g, c->nat, c->Zd, c->px, c->py, c->pz, nG, cn, c->fpart, c->st);
+    int nchunk = launch_lpp_forces<double>(g, c->nat, c->Zd, c->px, c->py, c->pz, dd, nG, cn, c->fpart, c->st);
     launch_force_reduce(c->nat, nchunk, c->fpart, c->Fd, 0, c->st);
     c->launches += 3;
     std::vector<double> F(3 * c->nat), Fe(3 * c->nat);
@@ -1242,7 +1283,7 @@ void free_ctx(ofdft_ctx *c)
     free_fieldset(c->f[0], c->st);
     free_fieldset(c->f[1], c->st);
     void *ptrs[] = {c->phiprev, c->part, c->scal, c->Rd, c->Zd, c->Fd, c->Vd, c->Md, c->nh, c->px, c->py,
-                    c->pz, c->fpart, c->Gv, c->wG, c->eion, c->ewF, c->ewpart, c->Se};
+                    c->pz, c->pdd.xT, c->fpart, c->Gv, c->wG, c->eion, c->ewF, c->ewpart, c->Se};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, c->st);
     if (c->st) cudaStreamSynchronize(c->st);
@@ -1256,6 +1297,10 @@ void free_ctx(ofdft_ctx *c)
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     if (c->cap2) cudaStreamDestroy(c->cap2);
+    for (cudaStream_t a : c->aux)
+        if (a) cudaStreamDestroy(a);
+    for (cudaEvent_t e : c->fj)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 
@@ -1321,6 +1366,13 @@ ofdft_status alloc_ctx(ofdft_ctx *c)
     CK(cudaMallocAsync((void **)&c->px, (size_t)nat * g.nx * sizeof(double2), c->st));
     CK(cudaMallocAsync((void **)&c->py, (size_t)nat * g.ny * sizeof(double2), c->st));
     CK(cudaMallocAsync((void **)&c->pz, (size_t)nat * g.K * sizeof(double2), c->st));
+    if (g.dd) {
+        const size_t nx = (size_t)nat * g.nx, ny = (size_t)nat * g.ny, nk = (size_t)nat * g.K;
+        CK(cudaMallocAsync((void **)&c->pdd.xT, (nx + ny + 2 * nk) * sizeof(double2), c->st));
+        c->pdd.yT = c->pdd.xT + nx;
+        c->pdd.zT = c->pdd.yT + ny;
+        c->pdd.zd = c->pdd.zT + nk;
+    }
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
     // leave room for the kernels' static shared memory (block reductions)
@@ -1330,6 +1382,8 @@ ofdft_status alloc_ctx(ofdft_ctx *c)
     CK(set_field_smem_limits<double>(dyn));
     CK(set_field_smem_limits<float>(dyn));
     CK(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+    for (cudaStream_t &a : c->aux) CK(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : c->fj) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return OFDFT_OK;
 }
 
@@ -1363,8 +1417,8 @@ double footprint_bytes(const int grid[3], int nat, int precision)
     double b = fieldset(8.0) + (precision == OFDFT_MIXED ? fieldset(4.0) : 0.0);
     b += N * 8;                                                        // phiprev
     b += (3 * ny * std::ceil(K / 4) + 15 * (nx * ny / 2) + 64) * 8 + 64 * 8;  // partials, scalars
-    b += nat * 11.0 * 8 + 32 + nat * (nx + ny + K) * 16.0;             // ions, phase factors
-    b += nat * 1216.0 * 3 * 8 + 16 * 8;                                // force partials
+    b += nat * 11.0 * 8 + 32 + nat * (2 * nx + 2 * ny + 3 * K) * 16.0;  // ions, phase factors (+ double-float)
+    b += nat * std::max(1216.0, (double)lpp_force_chunks_dd((long long)(nx * ny), nat)) * 3 * 8 + 16 * 8;   // force partials
     double km = std::ceil(4.27 * std::pow((double)nat, 1.0 / 6.0)) + 1;
     b += std::pow(2 * km + 1, 3) * 6 * 8 + nat * 4.0 * 8;             // Ewald tables
     return 1.05 * b + 8.0 * (1 << 20);                                 // pool granularity, graphs
@@ -2144,7 +2198,7 @@ ofdft_status ofdft_sizes(ofdft_ctx *c, long long *N, int *nat)
 
 ofdft_status ofdft_timer_select(ofdft_ctx *c, int id)
 {
-    if (!c || id < 0 || id > 7) return fail(c, OFDFT_EINVAL, "bad timer id");
+    if (!c || id < 0 || id > 23 || (id & 24) == 24) return fail(c, OFDFT_EINVAL, "bad timer id");
     c->timer_id = id;
     c->tev_used = 0;
     return OFDFT_OK;

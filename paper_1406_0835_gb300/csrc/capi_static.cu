@@ -248,8 +248,8 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     double2 *px = (double2 *)(base + kOffPhase);
     double2 *py = px + (size_t)nat * g.nx, *pz = py + (size_t)nat * g.ny;
     double2 *vext = (double2 *)(base + kOffVext);
-    launch_phases(g, nat, Rd, px, py, pz, st);
-    launch_vext(g, nat, Zd, px, py, pz, vext, st);
+    launch_phases(g, nat, Rd, px, py, pz, nullptr, st);
+    launch_vext(g, nat, Zd, px, py, pz, nullptr, vext, st);
 
     // evaluation (same kernel sequence as the context path)
     const size_t specN = kSpecBytes / sizeof(double2);
@@ -281,8 +281,8 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
         nbg = launch_pw<double>(g, d0, d1, d2, ph, T, fp, tab, xc, vpart, pB, false, st);
         launch_dline<double>(g, ax, 0, 1, 0, d0, v_dev, st);
         launch_dline<double>(g, ay, 1, 1, 1, d1, v_dev, st);
-        nbz = launch_zfinal_gga<double>(g, az, s0, d2, vpart, v_dev, ph, nullptr, nullptr, 1.0, 0.0, nullptr,
-                                        v_dev, pC, st);
+        nbz = launch_zfinal_gga<double>(g, az, s0, d2, vpart, v_dev, nullptr, ph, nullptr, nullptr, 1.0, 0.0,
+                                        nullptr, v_dev, pC, st);
     }
     launch_reduce_eval(pA, nbx, pB, nbg, pC, nbz, !fttf, scal, st);
     double h[18];

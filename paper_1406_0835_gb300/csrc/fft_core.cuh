@@ -197,8 +197,9 @@ __device__ C *fft_lines(C *a, C *b, const FftAxis &ax, int nl, int lstride, int 
 // double-float pair (hi + lo, two binary32 words) and each binary32 term
 // enters by the DWPlusFP sum of ffmath.cuh (relative error <= 2u^2), so a
 // thread's partial carries about 48 significant bits while the FP64 units
-// stay idle.  Warps add the pairs in double-float, blocks in binary64
-// (block_sum_f2).
+// stay idle.  Warps and blocks add the pairs in double-float, and each
+// block total is rounded to binary64 once (block_sum_f2); the totals of
+// the blocks are added in binary64 by the second reduction stage.
 struct AccF {
     ff::f2 v;
     __device__ __forceinline__ AccF() : v(0.0f, 0.0f) {}
@@ -260,12 +261,17 @@ template <int NQ> __device__ __forceinline__ void block_sum(double *v)
 }
 
 // Deterministic block sum of double-float per-thread partials: the warp
-// stage adds double-float pairs (shuffles of both words, DWPlusDW), so the
-// FP64 units see one conversion per warp and the cross-warp sum by thread 0
-// (binary64, fixed order); thread 0 returns the totals in tot.
+// stage adds double-float pairs (shuffles of both words, DWPlusDW), warp 0
+// adds the warps' pairs in double-float (lane q sums quantity q in warp
+// order) and converts each total to binary64 once; thread 0 returns the
+// totals in tot.  The FP64 units see one warp instruction per block: on a
+// part whose FP64 rate is 1/64 of FP32, binary64 cross-warp sums had cost
+// a visible share of the short field kernels.
 template <int NQ> __device__ __forceinline__ void block_sum_f2(const ff::f2 *v, double *tot)
 {
-    __shared__ double red[32][NQ];
+    static_assert(NQ <= 32, "one lane per quantity");
+    __shared__ float2 red[32][NQ];
+    __shared__ double btot[NQ];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -277,17 +283,19 @@ template <int NQ> __device__ __forceinline__ void block_sum_f2(const ff::f2 *v, 
             y.lo = __shfl_down_sync(0xffffffffu, x.lo, o);
             x = ff::add(x, y);
         }
-        if (lane == 0) red[wid][q] = ff::to_double(x);
+        if (lane == 0) red[wid][q] = make_float2(x.hi, x.lo);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (wid == 0 && lane < NQ) {
         const int nw = (blockDim.x + 31) >> 5;
-        for (int q = 0; q < NQ; ++q) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += red[w][q];
-            tot[q] = s;
-        }
+        ff::f2 s(0.0f, 0.0f);
+        for (int w = 0; w < nw; ++w) s = ff::add(s, ff::f2(red[w][lane].x, red[w][lane].y));
+        btot[lane] = ff::to_double(s);
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) tot[q] = btot[q];
     __syncthreads();
 }
 

@@ -32,11 +32,12 @@ int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T>
                   const T *vpart, const T *phit, const T *phi, const T *dhat, T c, T s,
                   const void *cs, T temp, const FuncParams &fp, const T *tab, int xc, T *vout,
                   double *part, cudaStream_t st);
-// z pass, final (GGA): v = v_HL - d_z U_z + v_part - div (div may alias vout).
+// z pass, final (GGA): v = v_HL - d_z U_z + v_part - div - div2 (div may
+// alias vout; div2 may be null).
 template <typename T>
 int launch_zfinal_gga(const GridInfo &g, const FftAxis &az, const cplx<T> *dspec, const T *uz, const T *vpart,
-                      const T *div, const T *phit, const T *phi, const T *dhat, T c, T s, const void *cs, T *vout,
-                      double *part, cudaStream_t st);
+                      const T *div, const T *div2, const T *phit, const T *phi, const T *dhat, T c, T s,
+                      const void *cs, T *vout, double *part, cudaStream_t st);
 template <typename T>
 void launch_ypass(const GridInfo &g, const FftAxis &ay, bool inv, cplx<T> *data, int nfields,
                   long long fstride, cudaStream_t st);
@@ -88,20 +89,32 @@ template <typename T>
 int launch_cg_dhat(long long n, const T *g, T *d, const T *phi, const T *v, double c1, double c2,
                    int restart, const double *c12r, T *dhat, double *part, cudaStream_t st);
 
+// Double-float copies of the phase tables (16 bytes per complex entry, the
+// size of a double2): xT[ix][I], yT[iy][I], zT[kz][I] (atoms fastest) and
+// zd[I][kz].
+struct PhaseTablesDD {
+    double2 *xT, *yT, *zT, *zd;
+};
 // Per-ion axis phase tables exp(-i G_a R_a) for a = x, y, z (complex double,
-// [nat][nx], [nat][ny], [nat][K]).
+// [nat][nx], [nat][ny], [nat][K]); with dd also their double-float copies.
 void launch_phases(const GridInfo &g, int nat, const double *R, double2 *px, double2 *py,
-                   double2 *pz, cudaStream_t st);
-// v_ext(G) on the half spectrum, Hermitian-symmetrised on Nyquist planes.
-// (FP64; a single-precision copy is made with launch_convert.)
+                   double2 *pz, const PhaseTablesDD *dd, cudaStream_t st);
+// v_ext(G) on the half spectrum, Hermitian-symmetrised on Nyquist planes:
+// sums over atoms in double-float when dd is given and the grid computes in
+// double-float, else binary64.  (A single-precision copy is made with
+// launch_convert.)
 void launch_vext(const GridInfo &g, int nat, const double *Z, const double2 *px,
-                 const double2 *py, const double2 *pz, double2 *vext, cudaStream_t st);
-// Local-pseudopotential forces from n(G): part[(I * nchunk + c) * 3 + a]; returns nchunk.
-// cn is scratch of NH double2.
+                 const double2 *py, const double2 *pz, const PhaseTablesDD *dd, double2 *vext, cudaStream_t st);
+// Local-pseudopotential forces from n(G): part[(I * nchunk + c) * 3 + a];
+// returns nchunk (= lpp_force_chunks(g, nat, dd != nullptr)).  cn is
+// scratch of NH double2.  Double-float sums as launch_vext.
 template <typename T>
 int launch_lpp_forces(const GridInfo &g, int nat, const double *Z, const double2 *px,
-                      const double2 *py, const double2 *pz, const cplx<T> *nG, double2 *cn,
-                      double *part, cudaStream_t st);
+                      const double2 *py, const double2 *pz, const PhaseTablesDD *dd, const cplx<T> *nG,
+                      double2 *cn, double *part, cudaStream_t st);
+int lpp_force_chunks(const GridInfo &g, int nat, bool dd);
+// Chunks of the double-float force kernel for nx * ny = rows (footprints).
+int lpp_force_chunks_dd(long long rows, int nat);
 // Sum force partials over chunks into F[nat][3] (+= if accumulate).
 void launch_force_reduce(int nat, int nchunk, const double *part, double *F, int accumulate,
                          cudaStream_t st);

@@ -680,10 +680,11 @@ template <> struct Pair2<double> { typedef double2 type; };
 template <> struct Pair2<float> { typedef float2 type; };
 
 // out (= or +=) d_j f along grid axis AX for f = phi^2 (MODE 0) or f = in
-// (MODE 1); ACC 1 adds to out.
+// (MODE 1); ACC 1 adds to out.  out may be in (each block reads its columns
+// whole before it writes them, and no other block touches them).
 template <typename PR, int AX, int MODE, int ACC>
-__global__ void OFDFT_FFT_BOUNDS k_dline(GridInfo g, FftAxis fa, const typename KT<PR>::T *__restrict__ in,
-                        typename KT<PR>::T *__restrict__ out)
+__global__ void OFDFT_FFT_BOUNDS k_dline(GridInfo g, FftAxis fa, const typename KT<PR>::T *in,
+                        typename KT<PR>::T *out)
 {
     typedef typename KT<PR>::T T;
     typedef typename KT<PR>::R R;
@@ -839,14 +840,16 @@ __global__ void __launch_bounds__(OFDFT_PW_THREADS, OFDFT_PW_MINB) k_pw(GridInfo
 // v_HL from the half spectrum dspec (Hartree + LPP after the inverse x and
 // y passes), d_z U_z from the pair-packed lines of U_z (forward z transform,
 // times i kt ds_z, added to the packed spectrum of v_HL, so one inverse
-// transform serves both) and div = d_x U_x + d_y U_y.  div may alias vout
-// (each point is read before it is written, by the same thread).  Partials
+// transform serves both) and div = d_x U_x + d_y U_y, given as one field or
+// as two (div + div2; div2 may be null).  div may alias vout (each point is
+// read before it is written, by the same thread).  Partials
 // (as k_zfinal's GGA form): rows 0..5 zero, then sum phi^2 v, sum phi^2,
 // sum 2 phi v dphi/dtheta.
 template <typename PR>
 __global__ void OFDFT_FFT_BOUNDS k_zfinal_g(GridInfo g, FftAxis az, int P, const typename KT<PR>::C *__restrict__ dspec,
                            const typename KT<PR>::T *__restrict__ uz, const typename KT<PR>::T *__restrict__ vpart,
-                           const typename KT<PR>::T *div, const typename KT<PR>::T *__restrict__ phit,
+                           const typename KT<PR>::T *div, const typename KT<PR>::T *__restrict__ div2,
+                           const typename KT<PR>::T *__restrict__ phit,
                            const typename KT<PR>::T *__restrict__ phi, const typename KT<PR>::T *__restrict__ dhat,
                            typename KT<PR>::T c, typename KT<PR>::T s, const void *__restrict__ cs,
                            typename KT<PR>::T *vout, double *__restrict__ part)
@@ -897,7 +900,8 @@ __global__ void OFDFT_FFT_BOUNDS k_zfinal_g(GridInfo g, FftAxis az, int P, const
         const R dr = (rc.r & 1) ? d.y : d.x;
         const R ph = ldr<PR>(phit[rbase + i]);
         const R n = ph * ph;
-        const R v = ldr<PR>(vpart[rbase + i]) + dr - ldr<PR>(div[rbase + i]);
+        R v = ldr<PR>(vpart[rbase + i]) + dr - ldr<PR>(div[rbase + i]);
+        if (div2 != nullptr) v = v - ldr<PR>(div2[rbase + i]);
         vout[rbase + i] = str<PR>(v);
         acc[6] += n * v;
         acc[7] += n;
@@ -1071,8 +1075,8 @@ int launch_zfinal(const GridInfo &g, const FftAxis &az, bool fttf, const cplx<T>
 
 template <typename T>
 int launch_zfinal_gga(const GridInfo &g, const FftAxis &az, const cplx<T> *dspec, const T *uz, const T *vpart,
-                      const T *div, const T *phit, const T *phi, const T *dhat, T c, T s, const void *cs, T *vout,
-                      double *part, cudaStream_t st)
+                      const T *div, const T *div2, const T *phit, const T *phi, const T *dhat, T c, T s,
+                      const void *cs, T *vout, double *part, cudaStream_t st)
 {
     int P = zpairs_light(g);
     long long npairs = (long long)g.nx * g.ny / 2;
@@ -1080,7 +1084,8 @@ int launch_zfinal_gga(const GridInfo &g, const FftAxis &az, const cplx<T> *dspec
     size_t sm = 3 * (size_t)P * g.nz * sizeof(cplx<T>);
     int th = g.zth > 0 ? g.zth : threads_for(P * g.nz);
 #define CALL(PR) \
-    k_zfinal_g<PR><<<blocks, th, sm, st>>>(g, az, P, dspec, uz, vpart, div, phit, phi, dhat, c, s, cs, vout, part)
+    k_zfinal_g<PR><<<blocks, th, sm, st>>>(g, az, P, dspec, uz, vpart, div, div2, phit, phi, dhat, c, s, cs, vout, \
+                                           part)
     OFDFT_DISPATCH(T, g, CALL);
 #undef CALL
     return blocks;
@@ -1176,8 +1181,8 @@ template <typename T> cudaError_t set_field_smem_limits(size_t bytes)
                                   T, const FuncParams &, const T *, int, T *, double *,            \
                                   cudaStream_t);                                                  \
     template int launch_zfinal_gga<T>(const GridInfo &, const FftAxis &, const cplx<T> *, const T *, \
-                                      const T *, const T *, const T *, const T *, const T *, T, T,  \
-                                      const void *, T *, double *, cudaStream_t);                 \
+                                      const T *, const T *, const T *, const T *, const T *,      \
+                                      const T *, T, T, const void *, T *, double *, cudaStream_t); \
     template void launch_ypass<T>(const GridInfo &, const FftAxis &, bool, cplx<T> *, int,         \
                                   long long, cudaStream_t);                                       \
     template int launch_xhl<T>(const GridInfo &, const FftAxis &, cplx<T> *, const cplx<T> *,      \

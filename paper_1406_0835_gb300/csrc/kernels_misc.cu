@@ -18,11 +18,13 @@ int vec_blocks(long long n)
     return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);   // 8 blocks per SM at most
 }
 
-// Blocks of the vector kernels that also reduce: two per SM, so that each
-// thread sums many elements before the block reduction (whose cost is per
-// thread, not per element).
-int red_blocks(long long n)
+// Blocks of the FP64 vector kernels that also reduce: two per SM, so that
+// each thread sums many elements before the block reduction (whose cost is
+// per thread, not per element).  The FP32 kernels' double-float partials
+// are cheap to reduce, and there the occupancy of vec_blocks wins.
+template <typename T> int red_blocks(long long n)
 {
+    if (sizeof(T) != 8) return vec_blocks(n);
     static const int sms = [] {
         int dev = 0, c = 0;
         return (cudaGetDevice(&dev) == cudaSuccess &&
@@ -663,15 +665,236 @@ __global__ void k_lpp_forces(GridInfo g, int nat, const double *__restrict__ Z,
         for (int k = 0; k < 3; ++k) part[((size_t)I * nchunk + chunk) * 3 + k] = Z[I] * acc[k];
 }
 
-__global__ void k_force_reduce(int nat, int nchunk, const double *__restrict__ part, double *F,
-                               int accumulate)
+// ----------------------------------------- double-float structure factor
+// The FP64 contexts' O(N_G N_at) sums (v_ext and the local forces) in
+// double-float arithmetic on the FP32 units (the FP64 unit issues 1/64 of
+// their rate); the binary64 kernels above remain for binary64 contexts.
+// Products use the complex double-float product (cmul, absolute error a few
+// u^2 of the operands' size, u = 2^-24), sums the accurate double-float
+// addition.
+
+// Double-float copies of the axis phase tables: pxT[ix][I], pyT[iy][I],
+// pzT[kz][I] (atoms fastest, for the force kernel's one-thread-per-atom
+// loads) and pzd[I][kz] (for v_ext's one-thread-per-kz loads).
+__global__ void k_phase_tables_dd(GridInfo g, int nat, const double2 *__restrict__ px,
+                                  const double2 *__restrict__ py, const double2 *__restrict__ pz,
+                                  ff::cf2 *pxT, ff::cf2 *pyT, ff::cf2 *pzT, ff::cf2 *pzd)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nat * 3; i += gridDim.x * blockDim.x) {
-        const int I = i / 3, k = i - I * 3;
-        double s = 0.0;
-        for (int c = 0; c < nchunk; ++c) s += part[((size_t)I * nchunk + c) * 3 + k];
-        F[i] = accumulate ? F[i] + s : s;
+    const int per = g.nx + g.ny + g.K;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nat * per; i += gridDim.x * blockDim.x) {
+        const int I = i / per, j = i - I * per;
+        double2 v;
+        ff::cf2 *dst, *dst2 = nullptr;
+        if (j < g.nx) {
+            v = px[(size_t)I * g.nx + j];
+            dst = pxT + (size_t)j * nat + I;
+        } else if (j < g.nx + g.ny) {
+            const int jj = j - g.nx;
+            v = py[(size_t)I * g.ny + jj];
+            dst = pyT + (size_t)jj * nat + I;
+        } else {
+            const int kz = j - g.nx - g.ny;
+            v = pz[(size_t)I * g.K + kz];
+            dst = pzT + (size_t)kz * nat + I;
+            dst2 = pzd + (size_t)I * g.K + kz;
+        }
+        ff::cf2 d;
+        d.x = ff::from_double(v.x);
+        d.y = ff::from_double(v.y);
+        *dst = d;
+        if (dst2) *dst2 = d;
     }
+}
+
+__device__ __forceinline__ ff::cf2 cf2_conj_if(ff::cf2 a, bool c)
+{
+    if (c) a.y = ff::neg(a.y);
+    return a;
+}
+
+// v_ext(G) as k_vext (same Nyquist handling and outputs), with the sums
+// over atoms in double-float: the row factors Z_I px py come from the
+// double-float tables, thread kz multiplies them by pzd[I][kz] and adds.
+__global__ void k_vext_dd(GridInfo g, int nat, const double *__restrict__ Z, const ff::cf2 *__restrict__ pxT,
+                          const ff::cf2 *__restrict__ pyT, const ff::cf2 *__restrict__ pzd,
+                          double2 *__restrict__ vext)
+{
+    constexpr int kChunk = 256;
+    __shared__ ff::cf2 a[kChunk], b[kChunk];
+    const int ix = blockIdx.x / g.ny, iy = blockIdx.x - ix * g.ny;
+    const bool xq = 2 * ix == g.nx, yq = 2 * iy == g.ny, rnyq = xq || yq;
+    const ff::f2 z0(0.0f, 0.0f);
+    ff::cf2 acc[2] = {{z0, z0}, {z0, z0}}, acc2[2] = {{z0, z0}, {z0, z0}};
+    for (int I0 = 0; I0 < nat; I0 += kChunk) {
+        const int nI = min(kChunk, nat - I0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < nI; j += blockDim.x) {
+            const int I = I0 + j;
+            const ff::cf2 u = pxT[(size_t)ix * nat + I], v = pyT[(size_t)iy * nat + I];
+            const ff::f2 zi = ff::split_int(Z[I]);
+            ff::cf2 p = ff::cmul(u, v);
+            a[j] = {ff::mul(p.x, zi), ff::mul(p.y, zi)};
+            if (rnyq) {
+                p = ff::cmul(cf2_conj_if(u, xq), cf2_conj_if(v, yq));
+                b[j] = {ff::mul(p.x, zi), ff::mul(p.y, zi)};
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kz = threadIdx.x + h * blockDim.x;
+            if (kz >= g.K) continue;
+            const bool znyq = 2 * kz == g.nz;
+            const ff::cf2 *pzc = pzd + (size_t)I0 * g.K + kz;
+            for (int j = 0; j < nI; ++j) {
+                ff::cf2 c = pzc[(size_t)j * g.K];
+                const ff::cf2 t = ff::cmul(a[j], c);
+                acc[h].x = ff::add(acc[h].x, t.x);
+                acc[h].y = ff::add(acc[h].y, t.y);
+                if (rnyq || znyq) {
+                    const ff::cf2 t2 = ff::cmul(rnyq ? b[j] : a[j], cf2_conj_if(c, znyq));
+                    acc2[h].x = ff::add(acc2[h].x, t2.x);
+                    acc2[h].y = ff::add(acc2[h].y, t2.y);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int kz = threadIdx.x + h * blockDim.x;
+        if (kz >= g.K) continue;
+        Hk k = hk_at(g, ix, iy, kz);
+        const size_t q = (size_t)blockIdx.x * g.K + kz;
+        const double2 s1 = make_double2(ff::to_double(acc[h].x), ff::to_double(acc[h].y));
+        const double2 s2 = make_double2(ff::to_double(acc2[h].x), ff::to_double(acc2[h].y));
+        if (g.tri) {
+            const double2 a1 = s1, a2 = (rnyq || k.nz_) ? s2 : s1;
+            const double w1 = lpp_w(g, k.g2), w2 = lpp_w(g, k.g2p);
+            vext[q] = make_double2(0.5 * (w1 * a1.x + w2 * a2.x), 0.5 * (w1 * a1.y + w2 * a2.y));
+            const double p1 = lpp_wp(g, k.g2), p2 = lpp_wp(g, k.g2p);
+            vext[(size_t)g.NH + q] = make_double2(0.5 * (p1 * a1.x + p2 * a2.x), 0.5 * (p1 * a1.y + p2 * a2.y));
+            continue;
+        }
+        const double w = lpp_w(g, k.g2);
+        double2 v = s1;
+        if (rnyq || k.nz_) v = make_double2(0.5 * (v.x + s2.x), 0.5 * (v.y + s2.y));
+        vext[q] = make_double2(w * v.x, w * v.y);
+        if (g.lpp) {
+            const double wp = lpp_wp_ha(g, k.g2);
+            vext[(size_t)g.NH + q] = make_double2(wp * v.x, wp * v.y);
+        }
+    }
+}
+
+// cn(G) = -Omega w_k w(G) conj(n(G)) as a double-float pair (w included in
+// every cell, the partner's w(G') of a triclinic cell is applied by the
+// force kernel).
+template <typename T>
+__global__ void k_lpp_prep_dd(GridInfo g, const cplx<T> *__restrict__ nG, ff::cf2 *__restrict__ cn)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < (int)g.NH; q += gridDim.x * blockDim.x) {
+        Hk h = hk_flat(g, q);
+        const double s = -g.omega * h.wk * lpp_w(g, h.g2);
+        const cplx<T> n = nG[q];
+        cn[q] = {ff::from_double(s * (double)n.x), ff::from_double(-s * (double)n.y)};
+    }
+}
+
+// Local-pseudopotential forces in double-float (same sums as k_lpp_forces):
+// F_I,a = Z_I sum_G G_a Im(cn(G) P_I(G)), P_I = px py pz, off the Nyquist
+// planes; on them the half-and-half form with the partner G' (conjugated
+// phases on the Nyquist axes, w(G') in a triclinic cell).  With G = kx b_0 +
+// ky b_1 + kz b_2 the sum is carried as T_j = sum k_j (...) per lattice
+// direction and F_I = Z_I sum_j T_j b_j at the end, so the per-point work
+// has no G vector.  Block (row chunk, atom chunk), one thread per atom: the
+// block walks its rows (ix, iy), stages the row's cn (and the partner
+// weights) in shared memory, and each thread runs over kz with its atom's
+// row factor px py.  part[(I * gridDim.x + row chunk) * 3 + a].
+template <typename T>
+__global__ void k_lpp_forces_dd(GridInfo g, int nat, int rows_per_block, const double *__restrict__ Z,
+                                const ff::cf2 *__restrict__ pxT, const ff::cf2 *__restrict__ pyT,
+                                const ff::cf2 *__restrict__ pzT, const ff::cf2 *__restrict__ cn,
+                                const cplx<T> *__restrict__ nG, double *__restrict__ part)
+{
+    extern __shared__ ff::cf2 scn[];   // [K] row weights, then [K] partner weights (triclinic)
+    ff::cf2 *scnp = scn + g.K;
+    const int I = blockIdx.y * blockDim.x + threadIdx.x;
+    const bool act = I < nat;
+    const int nrows = g.nx * g.ny;
+    const int r0 = blockIdx.x * rows_per_block, r1 = min(nrows, r0 + rows_per_block);
+    const ff::f2 z0(0.0f, 0.0f);
+    ff::f2 Tx = z0, Ty = z0, Tz = z0;
+    for (int r = r0; r < r1; ++r) {
+        const int ix = r / g.ny, iy = r - ix * g.ny;
+        const bool xq = 2 * ix == g.nx, yq = 2 * iy == g.ny, rnyq = xq || yq;
+        __syncthreads();
+        for (int kz = threadIdx.x; kz < g.K; kz += blockDim.x) {
+            const size_t q = (size_t)r * g.K + kz;
+            scn[kz] = cn[q];
+            if (g.tri && (rnyq || 2 * kz == g.nz)) {
+                const Hk h = hk_at(g, ix, iy, kz);
+                const double s = -g.omega * h.wk * lpp_w(g, h.g2p);
+                const cplx<T> n = nG[q];
+                scnp[kz] = {ff::from_double(s * (double)n.x), ff::from_double(-s * (double)n.y)};
+            }
+        }
+        __syncthreads();
+        if (!act) continue;
+        const ff::cf2 u = pxT[(size_t)ix * nat + I], v = pyT[(size_t)iy * nat + I];
+        const ff::cf2 ab = ff::cmul(u, v);
+        const ff::cf2 abp = rnyq ? ff::cmul(cf2_conj_if(u, xq), cf2_conj_if(v, yq)) : ab;
+        ff::f2 A0 = z0, NX = z0, NY = z0, Az = z0;
+        const ff::cf2 *pzI = pzT + I;
+        for (int kz = 0; kz < g.K; ++kz) {
+            const ff::cf2 c = pzI[(size_t)kz * nat];
+            const ff::cf2 w = scn[kz];
+            const ff::cf2 P = ff::cmul(ab, c);
+            const ff::f2 e1 = ff::dot2_sub(w.x, P.y, ff::neg(w.y), P.x);   // Im(w P)
+            const bool znyq = 2 * kz == g.nz;
+            if (!(rnyq || znyq)) {
+                A0 = ff::add(A0, e1);
+                Az = ff::add(Az, ff::mul(e1, (float)kz));
+            } else {
+                const ff::cf2 Pp = ff::cmul(abp, cf2_conj_if(c, znyq));
+                const ff::cf2 wp = g.tri ? scnp[kz] : w;
+                const ff::f2 e2 = ff::dot2_sub(wp.x, Pp.y, ff::neg(wp.y), Pp.x);   // Im(w' P')
+                // (k_j e1 - k'_j e2)/2 with k'_j = k_j on the Nyquist axes, -k_j off them
+                const ff::f2 dm = ff::scale(ff::sub(e1, e2), 0.5f), dp = ff::scale(ff::add(e1, e2), 0.5f);
+                NX = ff::add(NX, xq ? dm : dp);
+                NY = ff::add(NY, yq ? dm : dp);
+                Az = ff::add(Az, ff::mul(znyq ? dm : dp, (float)kz));
+            }
+        }
+        const int kx = ix <= g.nx / 2 ? ix : ix - g.nx, ky = iy <= g.ny / 2 ? iy : iy - g.ny;
+        Tx = ff::add(Tx, ff::mul(ff::add(A0, NX), (float)kx));
+        Ty = ff::add(Ty, ff::mul(ff::add(A0, NY), (float)ky));
+        Tz = ff::add(Tz, Az);
+    }
+    if (!act) return;
+    const double t[3] = {ff::to_double(Tx), ff::to_double(Ty), ff::to_double(Tz)};
+    double F[3];
+    if (g.tri) {
+        for (int a = 0; a < 3; ++a) F[a] = t[0] * g.Bm[a] + t[1] * g.Bm[3 + a] + t[2] * g.Bm[6 + a];
+    } else {
+        F[0] = t[0] * g.bx;
+        F[1] = t[1] * g.by;
+        F[2] = t[2] * g.bz;
+    }
+    for (int a = 0; a < 3; ++a) part[((size_t)I * gridDim.x + blockIdx.x) * 3 + a] = Z[I] * F[a];
+}
+
+// Sum of force partials: one warp per (atom, component), lanes over the
+// chunks in a fixed pattern, then a fixed shuffle tree.
+__global__ void k_force_reduce_w(int nat, int nchunk, const double *__restrict__ part, double *F, int accumulate)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= 3 * nat) return;
+    const int I = w / 3, k = w - 3 * I;
+    double s = 0.0;
+    for (int c = lane; c < nchunk; c += 32) s += part[((size_t)I * nchunk + c) * 3 + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) F[w] = accumulate ? F[w] + s : s;
 }
 
 // ---------------------------------------------------------------- Ewald
@@ -953,7 +1176,7 @@ template <typename T>
 int launch_cg_update(long long n, const int *accepted, T *phi, const T *phit, T *v, const T *vt,
                      const double *mup, T *g, T *gprev, double *part, cudaStream_t st)
 {
-    int b = red_blocks(n);
+    int b = red_blocks<T>(n);
     k_cg_update<T><<<b, kVecThreads, 0, st>>>(n, accepted, phi, phit, v, vt, mup, g, gprev, part);
     return b;
 }
@@ -963,7 +1186,7 @@ template <typename T, typename U> void launch_convert(long long n, const T *x, U
 }
 template <typename T> int launch_sumsq(long long n, const T *x, double *part, cudaStream_t st)
 {
-    int b = red_blocks(n);
+    int b = red_blocks<T>(n);
     k_sumsq<T><<<b, kVecThreads, 0, st>>>(n, x, part);
     return b;
 }
@@ -976,7 +1199,7 @@ int launch_extrap(long long n, const T *x, const T *xp, T *y, double *part, cuda
 }
 template <typename T> int launch_dot(long long n, const T *a, const T *b, double *part, cudaStream_t st)
 {
-    int nb = red_blocks(n);
+    int nb = red_blocks<T>(n);
     k_dot<T><<<nb, kVecThreads, 0, st>>>(n, a, b, part);
     return nb;
 }
@@ -990,7 +1213,7 @@ template <typename T>
 int launch_cg_grad(long long n, const T *phi, const T *v, double mu, const double *mup, T *g,
                    const T *gprev, double *part, cudaStream_t st)
 {
-    int b = red_blocks(n);
+    int b = red_blocks<T>(n);
     k_cg_grad<T><<<b, kVecThreads, 0, st>>>(n, phi, v, mu, mup, g, gprev, part);
     return b;
 }
@@ -998,7 +1221,7 @@ template <typename T>
 int launch_cg_dir(long long n, const T *g, T *d, double beta, const double *betap, const T *phi,
                   double *part, cudaStream_t st)
 {
-    int b = red_blocks(n);
+    int b = red_blocks<T>(n);
     k_cg_dir<T><<<b, kVecThreads, 0, st>>>(n, g, d, beta, betap, phi, part);
     return b;
 }
@@ -1006,38 +1229,93 @@ template <typename T>
 int launch_cg_dhat(long long n, const T *g, T *d, const T *phi, const T *v, double c1, double c2,
                    int restart, const double *c12r, T *dhat, double *part, cudaStream_t st)
 {
-    int b = red_blocks(n);
+    int b = red_blocks<T>(n);
     k_cg_dhat<T><<<b, kVecThreads, 0, st>>>(n, g, d, phi, v, c1, c2, restart, c12r, dhat, part);
     return b;
 }
 
 void launch_phases(const GridInfo &g, int nat, const double *R, double2 *px, double2 *py,
-                   double2 *pz, cudaStream_t st)
+                   double2 *pz, const PhaseTablesDD *dd, cudaStream_t st)
 {
     int total = nat * (g.nx + g.ny + g.K);
     int b = (total + 255) / 256;
     k_phases<<<b, 256, 0, st>>>(g, nat, R, px, py, pz);
+    if (dd)
+        k_phase_tables_dd<<<b, 256, 0, st>>>(g, nat, px, py, pz, (ff::cf2 *)dd->xT, (ff::cf2 *)dd->yT,
+                                             (ff::cf2 *)dd->zT, (ff::cf2 *)dd->zd);
 }
 
 void launch_vext(const GridInfo &g, int nat, const double *Z, const double2 *px,
-                 const double2 *py, const double2 *pz, double2 *vext, cudaStream_t st)
+                 const double2 *py, const double2 *pz, const PhaseTablesDD *dd, double2 *vext, cudaStream_t st)
 {
     int th = 32 * ((g.K + 31) / 32);
     if (th > 128) th = 32 * ((((g.K + 1) / 2) + 31) / 32);    // two columns per thread
-    k_vext<<<g.nx * g.ny, th, 0, st>>>(g, nat, Z, px, py, pz, vext);
+    if (dd && g.dd)
+        k_vext_dd<<<g.nx * g.ny, th, 0, st>>>(g, nat, Z, (const ff::cf2 *)dd->xT, (const ff::cf2 *)dd->yT,
+                                               (const ff::cf2 *)dd->zd, vext);
+    else
+        k_vext<<<g.nx * g.ny, th, 0, st>>>(g, nat, Z, px, py, pz, vext);
 }
 
-template <typename T>
-int launch_lpp_forces(const GridInfo &g, int nat, const double *Z, const double2 *px,
-                      const double2 *py, const double2 *pz, const cplx<T> *nG, double2 *cn,
-                      double *part, cudaStream_t st)
+namespace {
+// Launch shape of the double-float force kernel: one thread per atom in
+// blocks of up to 256, rows of the half spectrum split so that about two
+// waves of blocks are resident.
+struct ForceShape {
+    int tpb, achunks, rows_per_block, rchunks;
+};
+ForceShape force_shape(long long rows, int nat)
 {
-    long long b = (g.NH + 255) / 256;
-    k_lpp_prep<T><<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(g, nG, cn);
+    ForceShape f;
+    const int n = nat > 0 ? nat : 1;
+    f.tpb = n >= 256 ? 256 : 32 * ((n + 31) / 32);
+    f.achunks = (n + f.tpb - 1) / f.tpb;
+    static const int sms = [] {
+        int dev = 0, c = 0;
+        return (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && c > 0)
+                   ? c
+                   : 152;
+    }();
+    const int resident = std::min(32, 2048 / f.tpb);
+    long long rc = (2LL * sms * resident + f.achunks - 1) / f.achunks;
+    rc = std::max(1LL, std::min(rc, rows));
+    f.rows_per_block = (int)((rows + rc - 1) / rc);
+    f.rchunks = (int)((rows + f.rows_per_block - 1) / f.rows_per_block);
+    return f;
+}
+}  // namespace
+
+int lpp_force_chunks_dd(long long rows, int nat) { return force_shape(rows, nat).rchunks; }
+
+int lpp_force_chunks(const GridInfo &g, int nat, bool dd)
+{
+    if (dd && g.dd) return force_shape((long long)g.nx * g.ny, nat).rchunks;
     int nchunk = 1216 / (nat > 0 ? nat : 1);
     if (nchunk < 1) nchunk = 1;
     long long maxc = (g.NH + 1023) / 1024;
     if (nchunk > maxc) nchunk = (int)maxc;
+    return nchunk;
+}
+
+template <typename T>
+int launch_lpp_forces(const GridInfo &g, int nat, const double *Z, const double2 *px,
+                      const double2 *py, const double2 *pz, const PhaseTablesDD *dd, const cplx<T> *nG,
+                      double2 *cn, double *part, cudaStream_t st)
+{
+    long long b = (g.NH + 255) / 256;
+    const int pb = (int)(b < 4864 ? b : 4864);
+    if (dd && g.dd) {
+        k_lpp_prep_dd<T><<<pb, 256, 0, st>>>(g, nG, (ff::cf2 *)cn);
+        const ForceShape f = force_shape((long long)g.nx * g.ny, nat);
+        dim3 grid(f.rchunks, f.achunks);
+        k_lpp_forces_dd<T><<<grid, f.tpb, 2 * g.K * sizeof(ff::cf2), st>>>(
+            g, nat, f.rows_per_block, Z, (const ff::cf2 *)dd->xT, (const ff::cf2 *)dd->yT,
+            (const ff::cf2 *)dd->zT, (const ff::cf2 *)cn, nG, part);
+        return f.rchunks;
+    }
+    k_lpp_prep<T><<<pb, 256, 0, st>>>(g, nG, cn);
+    const int nchunk = lpp_force_chunks(g, nat, false);
     dim3 grid(nat, nchunk);
     k_lpp_forces<<<grid, 256, 0, st>>>(g, nat, Z, px, py, pz, cn, part);
     return nchunk;
@@ -1046,7 +1324,8 @@ int launch_lpp_forces(const GridInfo &g, int nat, const double *Z, const double2
 void launch_force_reduce(int nat, int nchunk, const double *part, double *F, int accumulate,
                          cudaStream_t st)
 {
-    k_force_reduce<<<(3 * nat + 255) / 256, 256, 0, st>>>(nat, nchunk, part, F, accumulate);
+    const long long threads = 32LL * 3 * nat;
+    k_force_reduce_w<<<(int)((threads + 255) / 256), 256, 0, st>>>(nat, nchunk, part, F, accumulate);
 }
 
 void launch_ewald_real(int nat, const double *R, const double *Z, const EwCell &cl, double alpha,
@@ -1113,8 +1392,8 @@ void launch_md_b(int nat, const double *m, double *V, const double *F, double dt
     template int launch_cg_dhat<T>(long long, const T *, T *, const T *, const T *, double,       \
                                    double, int, const double *, T *, double *, cudaStream_t);     \
     template int launch_lpp_forces<T>(const GridInfo &, int, const double *, const double2 *,     \
-                                      const double2 *, const double2 *, const cplx<T> *,          \
-                                      double2 *, double *, cudaStream_t);
+                                      const double2 *, const double2 *, const PhaseTablesDD *,   \
+                                      const cplx<T> *, double2 *, double *, cudaStream_t);
 
 OFDFT_MISC_INST(double)
 OFDFT_MISC_INST(float)

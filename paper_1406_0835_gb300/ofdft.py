@@ -386,7 +386,15 @@ TIMERS = {"pw": 1, "dline": 2, "ypass": 4, "zfwd": 5, "zfinal": 6, "xhl": 7}
 
 
 def ofdft_timer_select(ctx, which):
-    _check(ctx, load().ofdft_timer_select(ctx, TIMERS.get(which, which) if which else 0))
+    """which: a TIMERS name or id, optionally suffixed ":f32" or ":f64" to
+    time only that precision's launches; 0 or None switches timing off."""
+    if not which:
+        _check(ctx, load().ofdft_timer_select(ctx, 0))
+        return
+    name, _, prec = str(which).partition(":") if isinstance(which, str) else (which, "", "")
+    tid = TIMERS.get(name, name)
+    tid = int(tid) + {"": 0, "f32": 8, "f64": 16}[prec]
+    _check(ctx, load().ofdft_timer_select(ctx, tid))
 
 
 def ofdft_timer_read(ctx, reset=True):
