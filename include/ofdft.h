@@ -23,6 +23,11 @@
  *  - Every call returns an ofdft_status.  On error, outputs are left
  *    untouched (except ofdft_minimize, which fills its stats and keeps the
  *    last state on OFDFT_ENOCONV) and ofdft_last_error() describes it.
+ *  - Environment, read by ofdft_setup (diagnostics): OFDFT_DEBUG_SYNC=1
+ *    checks every launch and runs loops from the host; OFDFT_NO_GRAPHS=1
+ *    runs loops from the host; OFDFT_DLINE_WS="dk,threads" (dk 8 or 16,
+ *    threads <= 256, a multiple of 32 dividing 32 dk) starts the context
+ *    with the warp-synchronous derivative passes.
  */
 #ifndef OFDFT_H
 #define OFDFT_H

@@ -1447,6 +1447,7 @@ struct Tuned {
     int zP, tk, zth, xth;
     int mp[3];   // largest power-of-two radix per axis
     int dk, dth; // derivative passes: tile width, threads
+    int dws;     // derivative passes with warp-owned lines
 };
 
 // Rebuild axis a's Stockham schedule with power-of-two radices up to m (the
@@ -1498,6 +1499,7 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
             f.gt.xth = it->second.xth;
             f.gt.dk = it->second.dk;
             f.gt.dth = it->second.dth;
+            f.gt.dws = it->second.dws;
             for (int a = 0; a < 3; ++a) set_radix(f, a, it->second.mp[a]);
             if (f.graph) cudaGraphExecDestroy(f.graph);
             f.graph = nullptr;
@@ -1561,6 +1563,19 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
                 GridInfo g = base;
                 g.dk = dk;
                 g.dth = th;
+                g.dws = 0;
+                ofdft_status r = trial(g);
+                if (r != OFDFT_OK) return r;
+            }
+        // warp-owned lines: 1, 2 or 4 lines a warp
+        for (int dk : {8, 16})
+            for (int lpw : {1, 2, 4}) {
+                const int th = 32 * dk / lpw;
+                if (th > tmax || th < 64) continue;
+                GridInfo g = base;
+                g.dk = dk;
+                g.dth = th;
+                g.dws = 1;
                 ofdft_status r = trial(g);
                 if (r != OFDFT_OK) return r;
             }
@@ -1588,7 +1603,7 @@ template <typename T> ofdft_status autotune_set(ofdft_ctx *c, int k, int reps)
     f.graph = nullptr;
     c->shape_epoch++;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = Tuned{best.zP, best.tk, best.zth, best.xth, {mp[0], mp[1], mp[2]}, best.dk, best.dth};
+    g_tune[key] = Tuned{best.zP, best.tk, best.zth, best.xth, {mp[0], mp[1], mp[2]}, best.dk, best.dth, best.dws};
     return OFDFT_OK;
 }
 
@@ -1733,6 +1748,19 @@ ofdft_status ofdft_setup(const double cell[9], const int grid[3], int nat, const
     c->debug_sync = dbgenv && dbgenv[0] == '1';
     const char *gr = getenv("OFDFT_NO_GRAPHS");
     c->use_graphs = !(gr && gr[0] == '1');
+    // OFDFT_DLINE_WS="dk,threads": start from derivative passes with
+    // warp-owned lines (checks of that kernel form; ofdft_autotune may
+    // choose it by itself)
+    const char *ws = getenv("OFDFT_DLINE_WS");
+    if (ws) {
+        int dk = 0, th = 0;
+        if (sscanf(ws, "%d,%d", &dk, &th) == 2 && (dk == 8 || dk == 16) && th >= 32 && th <= 256 && th % 32 == 0 &&
+            dk % (th / 32) == 0) {
+            c->g.dws = 1;
+            c->g.dk = dk;
+            c->g.dth = th;
+        }
+    }
     ofdft_status s = alloc_ctx(c);
     if (s == OFDFT_OK) s = setup_ewald(c);
     if (s != OFDFT_OK) {

@@ -169,6 +169,71 @@ __device__ __forceinline__ void stage(const C *__restrict__ src, C *__restrict__
     }
 }
 
+// One stage over the lines l0 .. l0 + nlw - 1 that the calling warp owns,
+// in a line-major tile (element e of line l at buf[l * lstride + e]); the
+// warp's lanes walk the butterflies of each line.
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void stage_w(const C *__restrict__ src, C *__restrict__ dst, int n, int Ns,
+                                        const C *__restrict__ tw, int l0, int nlw, int lstride)
+{
+    const int nb = n / R;
+    const int tws = n / (Ns * R);
+    const int bsh = nb > 1 ? 32 - __clz(nb - 1) : 0;
+    const bool pns = (Ns & (Ns - 1)) == 0;
+    const int nsh = __ffs(Ns) - 1;
+    const int total = nlw << bsh;
+    for (int it = threadIdx.x & 31; it < total; it += 32) {
+        const int j = it & ((1 << bsh) - 1);
+        if (j >= nb) continue;
+        const int l = l0 + (it >> bsh);
+        const C *s = src + l * lstride;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[j + r * nb];
+        const int k = pns ? (j & (Ns - 1)) : j % Ns;
+        const int q = pns ? (j >> nsh) : j / Ns;
+        if (k != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = ld_tw(tw + r * k * tws);
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dftR<C, R, INV>(v);
+        C *d = dst + l * lstride;
+        const int base = q * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[base + r * Ns] = v[r];
+    }
+}
+
+// Full transform of the calling warp's lines (stage_w); stages are
+// separated by __syncwarp only, so warps run through their lines
+// independently.  The caller synchronises the block before the call (tile
+// written by other threads) and before other warps read the result.
+// Returns the buffer holding the result (the same for every warp).
+template <typename C, bool INV>
+__device__ C *fft_lines_w(C *a, C *b, const FftAxis &ax, int l0, int nlw, int lstride)
+{
+    const C *tw = axis_tw<C>(ax);
+    for (int s = 0; s < ax.nst; ++s) {
+        const int R = ax.rad[s], Ns = ax.ns[s];
+        switch (R) {
+        case 2: stage_w<C, 2, INV>(a, b, ax.n, Ns, tw, l0, nlw, lstride); break;
+        case 3: stage_w<C, 3, INV>(a, b, ax.n, Ns, tw, l0, nlw, lstride); break;
+        case 4: stage_w<C, 4, INV>(a, b, ax.n, Ns, tw, l0, nlw, lstride); break;
+        case 5: stage_w<C, 5, INV>(a, b, ax.n, Ns, tw, l0, nlw, lstride); break;
+        default: stage_w<C, 8, INV>(a, b, ax.n, Ns, tw, l0, nlw, lstride); break;
+        }
+        __syncwarp();
+        C *t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
 // Full transform of nl lines; data starts in a, b is scratch.  Returns the
 // buffer holding the result.  Callers must __syncthreads() before the call
 // (data written) and may read the result right after it returns.

@@ -734,6 +734,70 @@ __global__ void OFDFT_FFT_BOUNDS k_dline(GridInfo g, FftAxis fa, const typename 
     }
 }
 
+// k_dline with warp-owned lines: the tile is line-major with a padded line
+// stride n + 1 (column loads and stores stay coalesced in global memory and
+// spread over the shared-memory banks), warp w transforms, multiplies and
+// back-transforms lines [w L, (w + 1) L), L = tile width / warps, with
+// warp-level synchronisation between stages; the block synchronises only
+// after the load and before the store.
+template <typename PR, int AX, int MODE, int ACC>
+__global__ void OFDFT_FFT_BOUNDS k_dline_ws(GridInfo g, FftAxis fa, const typename KT<PR>::T *in,
+                                            typename KT<PR>::T *out)
+{
+    typedef typename KT<PR>::T T;
+    typedef typename KT<PR>::R R;
+    typedef typename KT<PR>::CC CC;
+    typedef typename Pair2<T>::type T2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = AX == 0 ? g.nx : g.ny;
+    const int ls = n + 1;
+    CC *A = reinterpret_cast<CC *>(smraw);
+    CC *B = A + ls * g.dk;
+    const PairTile t = pair_tile(g, AX);
+    for (int i = threadIdx.x; i < n * t.tk; i += blockDim.x) {
+        const int r = i >> t.tsh, c = i & (t.tk - 1);
+        if (c < t.ncol) {
+            const T2 v = *reinterpret_cast<const T2 *>(in + t.cbase[c] + r * t.rstride);
+            R a = ldr<PR>(v.x), b = ldr<PR>(v.y);
+            if (MODE == 0) {
+                a = a * a;
+                b = b * b;
+            }
+            A[c * ls + r] = cmk<CC>(a, b);
+        }
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5, lpw = t.tk / nw;
+    const int l0 = (threadIdx.x >> 5) * lpw;
+    const int nlw = max(0, min(lpw, t.ncol - l0));
+    CC *X = fft_lines_w<CC, false>(A, B, fa, l0, nlw, ls);
+    const R s = gcst<PR>(g.ds[AX], g.dsf[AX], g.ds2[AX]);
+    for (int it = threadIdx.x & 31; it < nlw * n; it += 32) {
+        const int m = it / n, r = it - m * n;
+        CC *p = X + (l0 + m) * ls + r;
+        *p = times_ik<CC, R>(*p, r, n, s);
+    }
+    __syncwarp();
+    CC *Y = fft_lines_w<CC, true>(X, X == A ? B : A, fa, l0, nlw, ls);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n * t.tk; i += blockDim.x) {
+        const int r = i >> t.tsh, c = i & (t.tk - 1);
+        if (c >= t.ncol) continue;
+        T2 *p = reinterpret_cast<T2 *>(out + t.cbase[c] + r * t.rstride);
+        const CC y = Y[c * ls + r];
+        T2 o;
+        if (ACC) {
+            const T2 q = *p;
+            o.x = str<PR>(ldr<PR>(q.x) + y.x);
+            o.y = str<PR>(ldr<PR>(q.y) + y.y);
+        } else {
+            o.x = str<PR>(y.x);
+            o.y = str<PR>(y.y);
+        }
+        *p = o;
+    }
+}
+
 // ------------------------------------------------------ pointwise stage
 // Pointwise functional + XC at every grid point (Eqs. (tred), (FGGA),
 // (vftGGA) first two lines, (vxc1)), no transforms: reads phi and the three
@@ -981,6 +1045,18 @@ template <typename PR>
 void dline_call(const GridInfo &g, const FftAxis &fa, int axis, int mode, int acc, const typename KT<PR>::T *in,
                 typename KT<PR>::T *out, int blocks, int th, size_t sm, cudaStream_t st)
 {
+    if (g.dws && th % 32 == 0 && g.dk % (th / 32) == 0) {   // whole lines for every warp
+        if (axis == 0) {
+            if (mode == 0) k_dline_ws<PR, 0, 0, 0><<<blocks, th, sm, st>>>(g, fa, in, out);
+            else if (acc == 0) k_dline_ws<PR, 0, 1, 0><<<blocks, th, sm, st>>>(g, fa, in, out);
+            else k_dline_ws<PR, 0, 1, 1><<<blocks, th, sm, st>>>(g, fa, in, out);
+        } else {
+            if (mode == 0) k_dline_ws<PR, 1, 0, 0><<<blocks, th, sm, st>>>(g, fa, in, out);
+            else if (acc == 0) k_dline_ws<PR, 1, 1, 0><<<blocks, th, sm, st>>>(g, fa, in, out);
+            else k_dline_ws<PR, 1, 1, 1><<<blocks, th, sm, st>>>(g, fa, in, out);
+        }
+        return;
+    }
     if (axis == 0) {
         if (mode == 0) k_dline<PR, 0, 0, 0><<<blocks, th, sm, st>>>(g, fa, in, out);
         else if (acc == 0) k_dline<PR, 0, 1, 0><<<blocks, th, sm, st>>>(g, fa, in, out);
@@ -999,8 +1075,8 @@ void launch_dline(const GridInfo &g, const FftAxis &fa, int axis, int mode, int 
 {
     const int n = axis == 0 ? g.nx : g.ny;
     const int blocks = pair_tiles_of(g, axis);
-    const size_t sm = 2 * (size_t)n * g.dk * sizeof(cplx<T>);
-    const int th = g.dth > 0 ? g.dth : threads_for(n * g.dk / 2);
+    const size_t sm = 2 * (size_t)(g.dws ? n + 1 : n) * g.dk * sizeof(cplx<T>);
+    const int th = g.dth > 0 ? g.dth : threads_for(n * g.dk / 2);   // warp-owned lines: dk a multiple of th / 32
 #define CALL(PR) dline_call<PR>(g, fa, axis, mode, acc, in, out, blocks, th, sm, st)
     OFDFT_DISPATCH(T, g, CALL);
 #undef CALL
@@ -1130,7 +1206,7 @@ size_t field_smem_max(const GridInfo &g, size_t csize)
     size_t z = 3 * (size_t)P * g.nz * csize;
     size_t y = 2 * (size_t)g.ny * g.tk * csize;
     size_t x = 2 * (size_t)g.nx * g.tk * csize;
-    size_t d = 2 * (size_t)(g.nx > g.ny ? g.nx : g.ny) * g.dk * csize;
+    size_t d = 2 * (size_t)((g.nx > g.ny ? g.nx : g.ny) + (g.dws ? 1 : 0)) * g.dk * csize;
     size_t m = z > y ? z : y;
     m = m > x ? m : x;
     return m > d ? m : d;
@@ -1155,7 +1231,13 @@ template <typename PR> cudaError_t smem_limits(int b)
         cudaFuncSetAttribute(k_dline<PR, 0, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_dline<PR, 1, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
         cudaFuncSetAttribute(k_dline<PR, 1, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
-        cudaFuncSetAttribute(k_dline<PR, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)};
+        cudaFuncSetAttribute(k_dline<PR, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline_ws<PR, 0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline_ws<PR, 0, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline_ws<PR, 0, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline_ws<PR, 1, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline_ws<PR, 1, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
+        cudaFuncSetAttribute(k_dline_ws<PR, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return x;
     return cudaSuccess;

@@ -96,6 +96,7 @@ struct GridInfo {
     int tk;                  // y/x passes: half-spectrum columns per tile (4, 8 or 16)
     int zth, xth;            // threads per block of the z and of the y/x passes (0: default rule)
     int dk, dth;             // derivative passes: pair columns per tile (4, 8 or 16) and threads (0: default)
+    int dws;                 // derivative passes with warp-owned lines (stages synchronised per warp)
     int dd;                  // FP64 fields: FFT and G-space arithmetic in double-float
     float bx2[2], by2[2], bz2[2], invN2[2], hr2[2];   // the same constants as double-float pairs
     // general (triclinic) cell: tri = 1 when the lattice vectors a_j (rows of
