@@ -303,6 +303,52 @@ constexpr int kTfUnroll = OFDFT_TF_UNROLL;   // functions evaluated side by side
 #endif
 constexpr int kHornerUnroll = OFDFT_HORNER_UNROLL;   // Horner steps unrolled (code size against loop overhead)
 
+// Horner evaluation of a table polynomial c[0..deg] at the binary32 panel
+// variable uh, with its derivative dp and half its second derivative d2:
+// the terms of degree >= split in binary32 (their sum, times u^split, is
+// below 2^-24 of the polynomial's smallest value on every panel of the
+// table, so binary32 rounding there stays below the double-float
+// rounding), the rest in double-float.  A split of deg runs every step in
+// double-float.
+OF_HD void horner_split_f2(const ff::f2 *__restrict__ c, int deg, int split, float uh, ff::f2 &p, ff::f2 &dp,
+                           float &d2)
+{
+    d2 = 0.0f;
+    int j = deg - 1;
+    if (split < deg) {
+        float pf = c[deg].hi, dpf = 0.0f;
+#pragma unroll kHornerUnroll
+        for (; j >= split; --j) {
+            d2 = d2 * uh + dpf;
+            dpf = dpf * uh + pf;
+            pf = pf * uh + c[j].hi;
+        }
+        p = {pf, 0.0f};
+        dp = {dpf, 0.0f};
+    } else {
+        p = c[deg];
+        dp = {0.0f, 0.0f};
+    }
+#pragma unroll kHornerUnroll
+    for (; j >= 0; --j) {
+        d2 = d2 * uh + dp.hi;
+        dp = ff::fma_step(dp, uh, p);
+        p = ff::fma_step(p, uh, c[j]);
+    }
+}
+
+// Degree from which the temperature table's terms are summed in binary32,
+// per function (xi, zeta, A, B): the largest tails of the fitted
+// polynomials, over every panel and relative to the polynomial's smallest
+// value there, are 3.3e-9 (xi, degree 7 up) and 2.9e-8 (A, degree 8 up);
+// zeta and B come close to zero inside some panels and keep every term in
+// double-float.  Against the all-double-float sums the pointwise outputs
+// differ by less than their own double-float rounding (host sweep over
+// every panel, 1e-16 to 1e6 bohr^-3 at 1e4 K and 1e6 K).
+constexpr int kTfSplitXi = 7, kTfSplitA = 8;
+// The enhancement table of G: tail 1.3e-8 from degree 5 up.
+constexpr int kEnSplit = 5;
+
 // Table polynomials with a double-float table (same layout as tfunc_eval's).
 // The panel variable u = uh + ul: uh is exact in binary32 and the Horner
 // sums run with it; ul (below 5e-7) enters through the first and second
@@ -320,15 +366,9 @@ OF_HD void tfunc_eval_f2(const ff::f2 *__restrict__ tab, ff::f2 t, ff::f2 out[8]
     const ff::f2 *c = tab + ((size_t)((e - kTfEmin) * kTfSub + sub) * kTfFuncs) * kTfNc;
 #pragma unroll kTfUnroll
     for (int q = 0; q < NF; ++q) {
-        const ff::f2 *cq = c + q * kTfNc;
-        ff::f2 p = cq[kTfDeg], dp = {0.0f, 0.0f};
-        float d2 = 0.0f;   // half the second derivative
-#pragma unroll kHornerUnroll
-        for (int j = kTfDeg - 1; j >= 0; --j) {
-            d2 = d2 * uh + dp.hi;
-            dp = ff::fma_step(dp, uh, p);
-            p = ff::fma_step(p, uh, cq[j]);
-        }
+        ff::f2 p, dp;
+        float d2;   // half the second derivative
+        horner_split_f2(c + q * kTfNc, kTfDeg, q == 0 ? kTfSplitXi : (q == 2 ? kTfSplitA : kTfDeg), uh, p, dp, d2);
         p = ff::add(p, dp.hi * ul);
         dp = ff::add(dp, 2.0f * d2 * ul);
         out[q] = p;
@@ -411,14 +451,9 @@ OF_HD void enhance_vt84f_tab(const ff::f2 *__restrict__ etab, ff::f2 x, ff::f2 &
     const float ul = (float)(2 * kEnSub) * x.lo * inv2e;
     const float dudx = (float)(2 * kEnSub) * inv2e;
     const f2 *c = etab + (size_t)((e - kEnEmin) * kEnSub + sub) * kEnNc;
-    f2 p = c[kEnDeg], dp = {0.0f, 0.0f};
-    float d2 = 0.0f;   // half the second derivative
-#pragma unroll kHornerUnroll
-    for (int j = kEnDeg - 1; j >= 0; --j) {
-        d2 = d2 * uh + dp.hi;
-        dp = fma_step(dp, uh, p);
-        p = fma_step(p, uh, c[j]);
-    }
+    f2 p, dp;
+    float d2;   // half the second derivative
+    horner_split_f2(c, kEnDeg, kEnSplit, uh, p, dp, d2);
     const f2 G = add(p, dp.hi * ul);
     const f2 dG = scale(add(dp, 2.0f * d2 * ul), dudx);
     F = add(mul(x, G), 1.0f);

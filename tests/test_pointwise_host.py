@@ -96,3 +96,25 @@ def test_double_float_domain_falls_back_to_binary64(lib):
         assert np.array_equal(a[out], b[out])
     with pytest.raises(ofdft.OfdftError):
         ofdft.ofdft_pointwise_eval("vt84f", True, 1e4, [1.0], [1.0], arith=7)
+
+
+@pytest.mark.parametrize("fn", ["fttf", "vt84f"])
+def test_double_float_over_the_whole_temperature_table(lib, fn):
+    """Densities from 1e-16 to 1e6 bohr^-3 at 1e4 K and 1e6 K put the reduced
+    temperature on every panel of the temperature table, [2^-20, 2^34) (the
+    double-float Horner sums of xi and A take their high-degree terms in
+    binary32), with the same bars against binary64."""
+    rng = np.random.default_rng(9)
+    for T in (1.0e4, 1.0e6):
+        n = 10.0 ** rng.uniform(-16, 6, 20000)
+        s2 = 10.0 ** rng.uniform(-9, 3, n.size)
+        g2 = s2 * n ** (8.0 / 3.0) / OF_CS
+        a, used = ofdft.ofdft_pointwise_eval(fn, True, T, n, g2, "f32x2")
+        b, _ = ofdft.ofdft_pointwise_eval(fn, True, T, n, g2, "f64")
+        assert used >= 0.9 * n.size
+        sc = np.abs(b[:, 0]) + np.abs(b[:, 1])
+        assert np.max(np.abs(a[:, 0] - b[:, 0]) / sc) < 1e-12
+        assert np.max(np.abs(a[:, 1] - b[:, 1]) / sc) < 1e-12
+        assert np.max(np.abs(a[:, 2] - b[:, 2]) / (np.abs(b[:, 2]) + sc / n)) < 1e-12
+        if fn != "fttf":
+            assert np.max(np.abs(a[:, 3] - b[:, 3]) / np.abs(b[:, 3])) < 5e-12
