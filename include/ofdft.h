@@ -427,9 +427,11 @@ void ofdft_destroy(ofdft_ctx *ctx);
  * Limits: each grid edge even, {2,3,5}-smooth and at most 64;
  * nx*ny*nz <= 32768; 1 <= nat <= 64.  Anything larger returns OFDFT_EINVAL,
  * as do Z <= 0, non-finite positions, T or rc.
- * The first call on a device does a one-time set-up on the current device
- * (looks up the array's device address, uploads the temperature table) and
- * should come before any stream capture.  The set-up runs under a mutex, so
+ * No call may be made on a stream that is being captured (the call copies
+ * from pageable host memory and synchronises): OFDFT_EINVAL.  The first
+ * call on a device does a one-time set-up on the current device (looks up
+ * the array's device address, uploads the temperature table).  The set-up
+ * runs under a mutex, so
  * first calls from several host threads are safe on the host.  It is cached
  * for the life of the device's context: after cudaDeviceReset (or a release
  * of the primary context) the cached address and table are stale and the

@@ -193,12 +193,19 @@ extern "C" ofdft_status ofdft_energy_potential_static(const double cell[9], cons
     }
     FuncParams fp = functional_params(functional);
     if (fp.kind < 0) return serr(OFDFT_EINVAL, "unknown functional");
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        // the call copies from pageable host memory and synchronises: not
+        // capturable
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+            return serr(OFDFT_EINVAL, "the stream is being captured");
+    }
     int dev = 0;
     SCK(cudaGetDevice(&dev), "cudaGetDevice failed");
     unsigned char *base = nullptr;
     ofdft_status s = device_setup(dev, &base);
     if (s != OFDFT_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
 
     GridInfo g{};
     g.nx = grid[0];

@@ -82,3 +82,30 @@ def test_static_entry_point_at_its_limits():
             ofdft.ofdft_energy_potential_static(cell, (16, 16, 16), ions, Z, d["T"], "fttf",
                                                 buf.data_ptr(), buf.data_ptr())
         assert e.value.status == -1
+
+
+def test_static_entry_point_refuses_a_capturing_stream():
+    """The call copies from pageable host memory and synchronises, which a
+    stream capture cannot hold: on a capturing stream it returns
+    OFDFT_EINVAL before any work, and the capture stays valid."""
+    torch = pytest.importorskip("torch")
+    import __graft_entry__
+    __graft_entry__.build()
+    cfg = inputs.config_single_point()
+    grid = (16, 16, 16)
+    buf = torch.ones(16 ** 3, dtype=torch.float64, device="cuda")
+    x = torch.zeros(1, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    status = None
+    with torch.cuda.graph(g, stream=s):
+        x += 1.0
+        try:
+            ofdft.ofdft_energy_potential_static(np.diag(cfg["L"]), grid, cfg["ions"], cfg["Z"], cfg["T"],
+                                                "fttf", buf.data_ptr(), buf.data_ptr(), stream=s.cuda_stream)
+        except ofdft.OfdftError as e:
+            status = e.status
+    assert status == -1
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x.item()) == 1.0
