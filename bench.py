@@ -66,6 +66,11 @@ WORKLOADS = {
     # serving form: Poisson arrivals (50/s) of EOS requests, each an initial
     # minimisation and 5 VT84F MD steps (16-128 H, 0.1-20 g/cm^3, <= 96^3)
     "serve-eos-mixed": dict(kind="serve", precision="mixed", count=24, md_steps=5),
+    # the same stream at the large end of the serving range: 6 requests of
+    # 128-1024 H at 0.03-2 g/cm^3, grids 96^3-256^3 (not part of the default
+    # line: minutes of device time with its sequential FP64 comparison)
+    "serve-eos-large-mixed": dict(kind="serve", precision="mixed", count=6, md_steps=5, seed=7,
+                                  n_range=(128, 1024), rho_range=(0.03, 2.0), grid_hi=256),
 }
 
 
@@ -718,7 +723,10 @@ def run_serve(args, rank, world):
     wl = WORKLOADS[args.workload]
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    stream = inputs.config_serve(count=wl["count"])
+    n_range, grid_hi = wl.get("n_range", (16, 128)), wl.get("grid_hi", 96)
+    rho_range = wl.get("rho_range", (0.1, 20.0))
+    stream = inputs.config_serve(count=wl["count"], seed=wl.get("seed", 6), n_range=n_range,
+                                 rho_range=rho_range, grid_hi=grid_hi)
 
     def serve(precision, slots, paced):
         with ofdft.Server(max_slots=slots, device=dev) as s:
@@ -766,9 +774,10 @@ def run_serve(args, rank, world):
            "dtype": DTYPE[wl["precision"]],
            "data": "synthetic (seeded Poisson EOS request stream)",
            "config": {"workload": args.workload, "requests": len(stream), "rate_per_s": 50.0,
-                      "md_steps": wl["md_steps"], "slots": 8, "grid_max": 96,
+                      "md_steps": wl["md_steps"], "slots": 8, "grid_max": grid_hi,
+                      "grids": sorted({d["grid"][0] for _, d in stream}),
                       "gtol": ofdft.MIXED_MD_GTOL, "fp64_gtol": 1e-8,
-                      "atoms": [16, 128], "rho_gcc": [0.1, 20.0], "T_K": [2e3, 4e6]},
+                      "atoms": list(n_range), "rho_gcc": list(rho_range), "T_K": [2e3, 4e6]},
            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
            "completed": ok, "peak_admitted_bytes": peak[0], "peak_running": peak[1],
            "evaluations": int(sum(r["evaluations"] for r in res)),
