@@ -457,18 +457,19 @@ def run_ours(args, rank, world):
     return res, evals / args.steps
 
 
-def md_rate(cfg, wl, dev, stream, steps, warmup, precision, pointwise="f32x2"):
-    """MD steps/s of another arithmetic on the same workload: a fresh
-    context, step 0 and `warmup` steps untimed, then `steps` steps timed with
-    CUDA events on the context's stream (L2 flushed before each)."""
+def md_rate(cfg, wl, dev, stream, steps, warmup, precision, pointwise="f32x2", gtol=1e-8):
+    """MD steps/s of another arithmetic (or per-step tolerance) on the same
+    workload: a fresh context, step 0 and `warmup` steps untimed, then
+    `steps` steps timed with CUDA events on the context's stream (L2 flushed
+    before each)."""
     import torch
     from paper_1406_0835_gb300 import ofdft
     c = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
                       precision=precision, pointwise=pointwise, device=dev, stream=stream.cuda_stream)
     c.autotune(reps=3)
-    c.md_step(0.2, cfg["T"], nsteps=0, pos=cfg["ions"], vel=cfg["vel"])
+    c.md_step(0.2, cfg["T"], nsteps=0, pos=cfg["ions"], vel=cfg["vel"], gtol=gtol)
     for _ in range(warmup):
-        c.md_step(0.2, cfg["T"], nsteps=1)
+        c.md_step(0.2, cfg["T"], nsteps=1, gtol=gtol)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t, evals, evals_lo = 0.0, 0, 0
@@ -478,7 +479,7 @@ def md_rate(cfg, wl, dev, stream, steps, warmup, precision, pointwise="f32x2"):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            out = c.md_step(0.2, cfg["T"], nsteps=1)
+            out = c.md_step(0.2, cfg["T"], nsteps=1, gtol=gtol)
             e1.record(stream)
             e1.synchronize()
             t += e0.elapsed_time(e1) / 1e3
@@ -489,7 +490,7 @@ def md_rate(cfg, wl, dev, stream, steps, warmup, precision, pointwise="f32x2"):
     return {"value": steps / t, "unit": "MD steps/s", "steps": steps, "warmup": warmup,
             "ms_per_step": 1e3 * t / steps, "evals_per_step": evals / steps,
             "fp32_evals_per_step": evals_lo / steps, "dtype": DTYPE[precision if pointwise != "f64" else "binary64"],
-            "F_tot_last": E["F_tot"]}
+            "gtol": gtol, "F_tot_last": E["F_tot"]}
 
 
 def extra_records(args, cfg, wl, dev, stream):
@@ -502,6 +503,11 @@ def extra_records(args, cfg, wl, dev, stream):
     out["binary64_md"] = md_rate(cfg, wl, dev, stream, steps=3, warmup=1, precision="fp64", pointwise="f64")
     if wl["precision"] == "fp64":
         out["mixed_md"] = md_rate(cfg, wl, dev, stream, steps=5, warmup=2, precision="mixed")
+        # the mixed form at the serving form's per-step tolerance (its
+        # stated bars against FP64: tests/test_gpu_md_forms.py)
+        from paper_1406_0835_gb300 import ofdft
+        out["mixed_md_serving_gtol"] = md_rate(cfg, wl, dev, stream, steps=5, warmup=2, precision="mixed",
+                                               gtol=ofdft.MIXED_MD_GTOL)
     for name, fn in (("batch-64-mixed", run_batch), ("serve-eos-mixed", run_serve)):
         a = copy.copy(args)
         a.workload, a.steps, a.warmup, a.no_ref = name, 2, 1, False
