@@ -250,7 +250,7 @@ def run_eval(args, rank, world):
     cfg = inputs.config_mixed(2.5e5, grid=wl["grid"])
     ctx = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
                         precision=wl["precision"], device=dev, stream=stream.cuda_stream)
-    ctx.autotune(reps=3)
+    ctx.autotune(reps=8)
     # a partly minimised density (60 CG iterations from the uniform start)
     # is the realistic input; the evaluation repeats at it
     ctx.minimize(gtol=1e-8, maxit=60, raise_on_noconv=False)
@@ -379,7 +379,7 @@ def run_ours(args, rank, world):
     def prepared_context():
         c = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
                           precision=wl["precision"], device=dev, stream=stream.cuda_stream)
-        c.autotune(reps=3)       # launch shapes for this grid (cached per process)
+        c.autotune(reps=8)       # launch shapes for this grid (cached per process)
         # step 0: minimise at the initial geometry and compute forces
         c.md_step(0.2, mdT, nsteps=0, pos=cfg["ions"], vel=cfg["vel"])
         for _ in range(args.warmup):
@@ -466,7 +466,7 @@ def md_rate(cfg, wl, dev, stream, steps, warmup, precision, pointwise="f32x2", g
     from paper_1406_0835_gb300 import ofdft
     c = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
                       precision=precision, pointwise=pointwise, device=dev, stream=stream.cuda_stream)
-    c.autotune(reps=3)
+    c.autotune(reps=8)
     c.md_step(0.2, cfg["T"], nsteps=0, pos=cfg["ions"], vel=cfg["vel"], gtol=gtol)
     for _ in range(warmup):
         c.md_step(0.2, cfg["T"], nsteps=1, gtol=gtol)
@@ -536,7 +536,7 @@ def run_solve(args, rank, world):
     cfg = inputs.config_mixed(wl["T"], grid=wl["grid"])
     ctx = ofdft.Context(cfg["L"], cfg["grid"], cfg["ions"], cfg["Z"], cfg["T"], wl["functional"],
                         precision=wl["precision"], device=dev, stream=stream.cuda_stream)
-    ctx.autotune(reps=3)
+    ctx.autotune(reps=8)
 
     def solve(c):
         c.set_phi(None)

@@ -245,7 +245,7 @@ FF_HD bool operator>(f2 x, f2 y) { return x.hi > y.hi || (x.hi == y.hi && x.lo >
 // leading 24 significand bits (truncated), lo the next 23 (exact, built with
 // the 2^23 trick); the 6 bits left are dropped (relative error < 2^-46).
 // Magnitudes below 2^-126 (and zero) give zero; beyond the binary32 range
-// (and NaN) the binary32 conversion (inf, NaN) with lo = 0.  The result is a
+// inf of the same sign, NaN for NaN, with lo = 0.  The result is a
 // valid double-float with |lo| < ulp(hi).
 FF_HD f2 split_int(double d)
 {
@@ -257,9 +257,15 @@ FF_HD f2 split_int(double d)
 #endif
     const uint32_t top = (uint32_t)(b >> 32);
     const int E = (int)((top >> 20) & 0x7ff) - 1023;
-    if (E < -126) return f2(0.0f, 0.0f);
-    if (E > 127) return f2((float)d, 0.0f);
     const uint32_t sign = top & 0x80000000u;
+    if (E < -126) return f2(0.0f, 0.0f);
+    if (E > 127) {
+        // beyond the binary32 range: inf of the sign, NaN for NaN (built from
+        // bits: a conversion instruction would run on the FP64 units, and the
+        // compiler may evaluate this branch for every element)
+        const bool nan = E == 1024 && (b & 0xfffffffffffffull) != 0;
+        return f2(int_bits_float(nan ? 0x7fc00000u : (sign | 0x7f800000u)), 0.0f);
+    }
     const uint32_t hib = sign | ((uint32_t)(E + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffffu);
     const uint32_t lint = (uint32_t)(b >> 6) & 0x7fffffu;    // significand bits 28..6
     float lo = fsub(int_bits_float(0x4b000000u | lint), 8388608.0f);   // exact integer < 2^23
