@@ -340,12 +340,14 @@ OF_HD void horner_split_f2(const ff::f2 *__restrict__ c, int deg, int split, flo
 // Degree from which the temperature table's terms are summed in binary32,
 // per function (xi, zeta, A, B): the largest tails of the fitted
 // polynomials, over every panel and relative to the polynomial's smallest
-// value there, are 3.3e-9 (xi, degree 7 up) and 2.9e-8 (A, degree 8 up);
-// zeta and B come close to zero inside some panels and keep every term in
-// double-float.  Against the all-double-float sums the pointwise outputs
+// value there, are 3.3e-9 (xi, degree 7 up) and 2.9e-8 (A, degree 8 up).
+// zeta comes close to zero inside some panels, but it enters only beside
+// xi (f = tau0 xi F_tau - tau0 zeta F_sigma): its tail from degree 7 up is
+// 5.1e-9 of the panel's largest |xi|.  B keeps every term in double-float
+// (its monomial coefficients do not decay on the low-t panels).  Against the all-double-float sums the pointwise outputs
 // differ by less than their own double-float rounding (host sweep over
 // every panel, 1e-16 to 1e6 bohr^-3 at 1e4 K and 1e6 K).
-constexpr int kTfSplitXi = 7, kTfSplitA = 8;
+constexpr int kTfSplitXi = 7, kTfSplitZeta = 7, kTfSplitA = 8;
 // The enhancement table of G: tail 1.3e-8 from degree 5 up.
 constexpr int kEnSplit = 5;
 
@@ -368,7 +370,7 @@ OF_HD void tfunc_eval_f2(const ff::f2 *__restrict__ tab, ff::f2 t, ff::f2 out[8]
     for (int q = 0; q < NF; ++q) {
         ff::f2 p, dp;
         float d2;   // half the second derivative
-        horner_split_f2(c + q * kTfNc, kTfDeg, q == 0 ? kTfSplitXi : (q == 2 ? kTfSplitA : kTfDeg), uh, p, dp, d2);
+        horner_split_f2(c + q * kTfNc, kTfDeg, q == 0 ? kTfSplitXi : (q == 1 ? kTfSplitZeta : (q == 2 ? kTfSplitA : kTfDeg)), uh, p, dp, d2);
         p = ff::add(p, dp.hi * ul);
         dp = ff::add(dp, 2.0f * d2 * ul);
         out[q] = p;
