@@ -295,9 +295,11 @@ template <typename T> struct PwOut {
 constexpr double kPwNmin = 1e-18, kPwNmax = 1e18, kPwS2max = 1e10;
 
 #ifndef OFDFT_TF_UNROLL
-#define OFDFT_TF_UNROLL 1
+#define OFDFT_TF_UNROLL 4
 #endif
-constexpr int kTfUnroll = OFDFT_TF_UNROLL;   // functions evaluated side by side
+// functions evaluated side by side: fully unrolled, the table values stay
+// in registers (a runtime-indexed out[] would live in local memory)
+constexpr int kTfUnroll = OFDFT_TF_UNROLL;
 #ifndef OFDFT_HORNER_UNROLL
 #define OFDFT_HORNER_UNROLL 2
 #endif
