@@ -193,11 +193,11 @@ def fft_flops(n):
 POINTWISE_FLOP = 200.0
 # Issued warp instructions and DRAM bytes per grid point of one k_pw<DD>
 # launch (the FP64 contexts' pointwise kernel, VT84F at an MD density, 96^3),
-# from the ncu capture summarised in profiles/k_pw_dd_96.md (88,567,584
-# warp instructions, 33.54 MB per launch).  Valid for that kernel only: set
+# from the ncu capture summarised in profiles/k_pw_dd_96.md (84,671,328
+# warp instructions, 30.09 MB per launch).  Valid for that kernel only: set
 # to None when it changes until the capture is repeated.
-PW_DD_WARP_INST_PER_POINT = 88567584.0 / 96 ** 3
-PW_DD_TRAFFIC_PER_POINT = (28.382208e6 + 5.161984e6) / 96 ** 3
+PW_DD_WARP_INST_PER_POINT = 84671328.0 / 96 ** 3
+PW_DD_TRAFFIC_PER_POINT = (28.388608e6 + 1.700864e6) / 96 ** 3
 # FP32-unit instructions per FP64-equivalent flop of the double-float
 # arithmetic in the cost model of the FFT and pointwise work: a sum
 # (two_sum + tail + fast_two_sum) takes 11, a product (two_prod + two FMAs
