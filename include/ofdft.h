@@ -68,9 +68,11 @@ typedef enum {
 
 /* Arithmetic of the FP64 field sets' evaluation kernels: the FFTs, the
  * G-space terms and the pointwise functional (f_s, its derivatives and PZ81,
- * Eqs. (FGGA), (vftGGA), (vxc1)).  Fields and spectra stay binary64 in
- * memory, and the reductions, CG scalars, forces and MD stay binary64,
- * either way. */
+ * Eqs. (FGGA), (vftGGA), (vxc1)), and of the structure factor and local
+ * forces (sums over ions, Eq. (M12)).  Fields and spectra stay binary64 in
+ * memory, and the reduction totals (block partials add in double-float
+ * within a block with F32X2, in binary64 across blocks), CG scalars, Ewald
+ * terms and MD stay binary64. */
 typedef enum {
     OFDFT_PW_F32X2 = 0,  /* double-float pairs on the FP32 units (about 48
                             significant bits): the energy agrees with the
