@@ -45,7 +45,7 @@ EVALS_PER_STEP = {"md-vt84f-96": 622.0, "md-sga-96": 334.0, "md-vt84f-96-mixed":
 # finish in an FP64 context's arithmetic.
 DTYPE = {"fp64": "f64 (double-float compute, binary64 storage and reductions)",
          "mixed": "f32 fields + f64 (f32 FFTs/pointwise, f64 reductions, double-float FP64 polish)",
-         "binary64": "f64 (binary64 throughout)"}
+         "binary64": "f64 (binary64 evaluation)"}
 
 WORKLOADS = {
     "md-vt84f-96": dict(kind="md", functional="vt84f", grid=96, precision="fp64"),

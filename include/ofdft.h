@@ -70,9 +70,10 @@ typedef enum {
  * G-space terms and the pointwise functional (f_s, its derivatives and PZ81,
  * Eqs. (FGGA), (vftGGA), (vxc1)), and of the structure factor and local
  * forces (sums over ions, Eq. (M12)).  Fields and spectra stay binary64 in
- * memory, and the reduction totals (block partials add in double-float
- * within a block with F32X2, in binary64 across blocks), CG scalars, Ewald
- * terms and MD stay binary64. */
+ * memory, and the reduction totals, CG scalars, Ewald terms and MD stay
+ * binary64 either way (the evaluation's block partials add in double-float
+ * within a block with F32X2; the CG vector kernels' partials always do,
+ * from binary64 per-thread sums; blocks are added in binary64). */
 typedef enum {
     OFDFT_PW_F32X2 = 0,  /* double-float pairs on the FP32 units (about 48
                             significant bits): the energy agrees with the
@@ -85,7 +86,7 @@ typedef enum {
                             range: a density whose potential passes 3e38
                             (GGA functionals next to n ~ 1e-20) gives
                             OFDFT_ENUMERIC here and needs OFDFT_PW_F64 */
-    OFDFT_PW_F64 = 1     /* binary64 throughout */
+    OFDFT_PW_F64 = 1     /* binary64 throughout the evaluation */
 } ofdft_pointwise;
 
 /* Local pseudopotential of the ions (Sec. V A).  Either form drops G = 0;
