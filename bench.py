@@ -220,8 +220,9 @@ def kernel_model(name, g, fttf=False):
     elif name == "dline":      # one derivative along x or y: forward + inverse line transforms
         n = (nx + ny) / 2.0
         flops = 2 * (N / 2 / n) * fft_flops(n)
-        byts = 8 * N * 2.5                                 # field in, derivative out (div: half accumulate)
+        byts = 8 * N * 2                                   # field in, derivative out
     elif name == "zfinal":     # GGA: U_z forward + one inverse; ftTF: inverse + pointwise
+        # GGA fields: U_z, v_part, d_y U_y, d_x U_x, phi in; v out
         flops = (nx * ny / 2) * fft_flops(nz) * (1 if fttf else 2) + (POINTWISE_FLOP * N if fttf else 0)
         byts = 16 * NH + 8 * N * (3 if fttf else 6)
     elif name == "ypass":
