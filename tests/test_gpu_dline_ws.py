@@ -71,3 +71,24 @@ def test_warp_owned_lines_mixed_minimisation(monkeypatch):
         E, st = ctx.minimize(gtol=1e-8)
         assert st["status"] == 0 and st["evaluations_lo"] > 0
     assert abs(E["F_tot"] - ev["F_tot"]) / 16 < 1e-6
+
+
+def test_warp_owned_lines_at_the_md_size(monkeypatch):
+    """At the MD workload's size (96^3, 128 H, VT84F) the warp-synchronous
+    derivative passes reproduce the block-synchronous ones: the same
+    arithmetic in another order of threads, so energies agree to 1e-13 of
+    F_tot and the potential to 1e-12 of its maximum."""
+    d = inputs.config_md("vt84f")
+    grid = d["grid"]
+    rng = np.random.default_rng(12)
+    phi = np.sqrt(128.0 / np.prod(d["L"])) * (1.0 + 0.05 * rng.standard_normal(grid))
+    out = []
+    for shape in (None, "16,128"):
+        if shape:
+            monkeypatch.setenv("OFDFT_DLINE_WS", shape)
+        with ofdft.Context(d["L"], grid, d["ions"], d["Z"], d["T"], "vt84f") as ctx:
+            out.append(ctx.energy_potential(phi))
+    (Ea, va), (Eb, vb) = out
+    for k in ("F_tot", "F_s", "F_xc", "E_H"):
+        assert abs(Ea[k] - Eb[k]) <= 1e-13 * abs(Ea["F_tot"]), k
+    assert np.max(np.abs(va - vb)) <= 1e-12 * np.max(np.abs(va))
