@@ -2015,7 +2015,7 @@ ofdft_status ofdft_stress(ofdft_ctx *c, double *sigma, double *terms)
     if (!fttf) launch_reduce(zpart + 6 * (size_t)nbg, nbg, 6, out, st);
     else CK(cudaMemsetAsync(out, 0, 6 * sizeof(double), st));
     const double2 *nG = (const double2 *)f.spec + f.spec_stride;
-    const int ng = launch_gstress(g, c->nat, c->Zd, c->px, c->py, c->pz, nG, gpart, st);
+    const int ng = launch_gstress(g, c->nat, c->Zd, c->px, c->py, c->pz, g.dd ? &c->pdd : nullptr, nG, gpart, st);
     launch_reduce(gpart, ng, 12, out + 6, st);
     const int nb = launch_ewald_stress(c->nat, c->Rd, c->Zd, ew_cell(g), c->ew_alpha, c->ew_rcut, c->ew_nimg, c->nGe,
                                        c->Gv, c->wG, (const double2 *)c->Se, rpart, kpart, st);

@@ -146,7 +146,7 @@ void launch_andersen(int nat, const double *m, double *V, double kT, double prob
 // real-space (6 rows, nat columns) and reciprocal (7 rows; returns the
 // column count) sums.
 int launch_gstress(const GridInfo &g, int nat, const double *Z, const double2 *px, const double2 *py,
-                   const double2 *pz, const double2 *nG, double *part, cudaStream_t st);
+                   const double2 *pz, const PhaseTablesDD *dd, const double2 *nG, double *part, cudaStream_t st);
 int launch_ewald_stress(int nat, const double *R, const double *Z, const EwCell &cl, double alpha, double rcut,
                         int3 nimg, int nG, const double *Gv, const double *wG, const double2 *S,
                         double *preal, double *precip, cudaStream_t st);

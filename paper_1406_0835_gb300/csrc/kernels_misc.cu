@@ -514,6 +514,50 @@ __device__ __forceinline__ double lpp_dw(const GridInfo &g, double g2)
     return 1.5 * (lpp_wp_ha(g, g2) - w) / g2;
 }
 
+// Hartree and local-pseudopotential stress sums of one (ix, iy) row (the
+// block's), from the row's structure-factor sums s1 = S(G) and s2 (the
+// partner's, on Nyquist rows), thread columns kz = threadIdx.x + h
+// blockDim.x; writes the block's 12 partial rows.
+__device__ __forceinline__ void gstress_row(const GridInfo &g, int ix, int iy, bool rnyq, const double2 s1[2],
+                                            const double2 s2[2], const double2 *__restrict__ nG,
+                                            double *__restrict__ part)
+{
+    double sm[12];
+    for (int q = 0; q < 12; ++q) sm[q] = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int kz = threadIdx.x + h * blockDim.x;
+        if (kz >= g.K) continue;
+        Hk k = hk_at(g, ix, iy, kz);
+        if (!(k.g2 > 0.0)) continue;
+        const double2 n = nG[(size_t)blockIdx.x * g.K + kz];
+        const double inv = 1.0 / k.g2;
+        const double hw = 12.566370614359172954 * (n.x * n.x + n.y * n.y) * inv * inv;
+        const double wd = lpp_dw(g, k.g2);
+        const double lw = wd * (n.x * s1[h].x + n.y * s1[h].y);
+        const double f[6] = {k.gx * k.gx, k.gy * k.gy, k.gz * k.gz, k.gx * k.gy, k.gx * k.gz, k.gy * k.gz};
+        for (int q = 0; q < 6; ++q) {
+            sm[q] += hw * f[q];
+            sm[6 + q] += lw * f[q];
+        }
+        if (kz > 0 && !k.nz_) {
+            const double2 sp = rnyq ? s2[h] : s1[h];
+            const double invp = 1.0 / k.g2p;   // |G'| = |G| unless the cell is triclinic
+            const double hwp = 12.566370614359172954 * (n.x * n.x + n.y * n.y) * invp * invp;
+            const double lp = lpp_dw(g, k.g2p) * (n.x * sp.x + n.y * sp.y);
+            const double gx = k.gpx, gy = k.gpy, gz = k.gpz;
+            const double fp[6] = {gx * gx, gy * gy, gz * gz, gx * gy, gx * gz, gy * gz};
+            for (int q = 0; q < 6; ++q) {
+                sm[q] += hwp * fp[q];
+                sm[6 + q] += lp * fp[q];
+            }
+        }
+    }
+    block_sum<12>(sm);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 12; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = sm[q];
+}
+
 // Hartree and local-pseudopotential parts of the stress tensor
 // (Eq. (StressTensor): homogeneous strain at fixed Omega n(G) and fractional
 // coordinates), summed over the full FFT box from the half spectrum:
@@ -569,40 +613,7 @@ __global__ void k_gstress(GridInfo g, int nat, const double *__restrict__ Z,
             }
         }
     }
-    double sm[12];
-    for (int q = 0; q < 12; ++q) sm[q] = 0.0;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int kz = threadIdx.x + h * blockDim.x;
-        if (kz >= g.K) continue;
-        Hk k = hk_at(g, ix, iy, kz);
-        if (!(k.g2 > 0.0)) continue;
-        const double2 n = nG[(size_t)blockIdx.x * g.K + kz];
-        const double inv = 1.0 / k.g2;
-        const double hw = 12.566370614359172954 * (n.x * n.x + n.y * n.y) * inv * inv;
-        const double wd = lpp_dw(g, k.g2);
-        const double lw = wd * (n.x * acc[h].x + n.y * acc[h].y);
-        const double f[6] = {k.gx * k.gx, k.gy * k.gy, k.gz * k.gz, k.gx * k.gy, k.gx * k.gz, k.gy * k.gz};
-        for (int q = 0; q < 6; ++q) {
-            sm[q] += hw * f[q];
-            sm[6 + q] += lw * f[q];
-        }
-        if (kz > 0 && !k.nz_) {
-            const double2 sp = rnyq ? acc2[h] : acc[h];
-            const double invp = 1.0 / k.g2p;   // |G'| = |G| unless the cell is triclinic
-            const double hwp = 12.566370614359172954 * (n.x * n.x + n.y * n.y) * invp * invp;
-            const double lp = lpp_dw(g, k.g2p) * (n.x * sp.x + n.y * sp.y);
-            const double gx = k.gpx, gy = k.gpy, gz = k.gpz;
-            const double fp[6] = {gx * gx, gy * gy, gz * gz, gx * gy, gx * gz, gy * gz};
-            for (int q = 0; q < 6; ++q) {
-                sm[q] += hwp * fp[q];
-                sm[6 + q] += lp * fp[q];
-            }
-        }
-    }
-    block_sum<12>(sm);
-    if (threadIdx.x == 0)
-        for (int q = 0; q < 12; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = sm[q];
+    gstress_row(g, ix, iy, rnyq, acc, acc2, nG, part);
 }
 
 // Per-point weight of the local forces: cn(G) = -Omega w_k w(G) conj(n(G));
@@ -712,16 +723,21 @@ __device__ __forceinline__ ff::cf2 cf2_conj_if(ff::cf2 a, bool c)
     return a;
 }
 
-// v_ext(G) as k_vext (same Nyquist handling and outputs), with the sums
-// over atoms in double-float: the row factors Z_I px py come from the
-// double-float tables, thread kz multiplies them by pzd[I][kz] and adds.
-__global__ void k_vext_dd(GridInfo g, int nat, const double *__restrict__ Z, const ff::cf2 *__restrict__ pxT,
-                          const ff::cf2 *__restrict__ pyT, const ff::cf2 *__restrict__ pzd,
-                          double2 *__restrict__ vext)
+// Structure-factor sums of one (ix, iy) row in double-float, for thread
+// columns kz = threadIdx.x + h blockDim.x (h = 0, 1): s1 = sum_I Z_I px py
+// pz, and s2 the partner sum with the phases conjugated on the Nyquist axes
+// (rows on an x or y Nyquist plane; with ZNYQ also the kz = nz/2 column).
+// The row factors Z_I px py come from the double-float tables in chunks of
+// atoms staged in shared memory; thread kz multiplies them by pzd[I][kz].
+// Called by every thread of the block.
+template <bool ZNYQ>
+__device__ __forceinline__ void row_sf_dd(const GridInfo &g, int nat, const double *__restrict__ Z,
+                                          const ff::cf2 *__restrict__ pxT, const ff::cf2 *__restrict__ pyT,
+                                          const ff::cf2 *__restrict__ pzd, int ix, int iy, double2 s1[2],
+                                          double2 s2[2])
 {
     constexpr int kChunk = 256;
     __shared__ ff::cf2 a[kChunk], b[kChunk];
-    const int ix = blockIdx.x / g.ny, iy = blockIdx.x - ix * g.ny;
     const bool xq = 2 * ix == g.nx, yq = 2 * iy == g.ny, rnyq = xq || yq;
     const ff::f2 z0(0.0f, 0.0f);
     ff::cf2 acc[2] = {{z0, z0}, {z0, z0}}, acc2[2] = {{z0, z0}, {z0, z0}};
@@ -744,10 +760,10 @@ __global__ void k_vext_dd(GridInfo g, int nat, const double *__restrict__ Z, con
         for (int h = 0; h < 2; ++h) {
             const int kz = threadIdx.x + h * blockDim.x;
             if (kz >= g.K) continue;
-            const bool znyq = 2 * kz == g.nz;
+            const bool znyq = ZNYQ && 2 * kz == g.nz;
             const ff::cf2 *pzc = pzd + (size_t)I0 * g.K + kz;
             for (int j = 0; j < nI; ++j) {
-                ff::cf2 c = pzc[(size_t)j * g.K];
+                const ff::cf2 c = pzc[(size_t)j * g.K];
                 const ff::cf2 t = ff::cmul(a[j], c);
                 acc[h].x = ff::add(acc[h].x, t.x);
                 acc[h].y = ff::add(acc[h].y, t.y);
@@ -761,12 +777,28 @@ __global__ void k_vext_dd(GridInfo g, int nat, const double *__restrict__ Z, con
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+        s1[h] = make_double2(ff::to_double(acc[h].x), ff::to_double(acc[h].y));
+        s2[h] = make_double2(ff::to_double(acc2[h].x), ff::to_double(acc2[h].y));
+    }
+}
+
+// v_ext(G) as k_vext (same Nyquist handling and outputs), with the sums
+// over atoms in double-float (row_sf_dd).
+__global__ void k_vext_dd(GridInfo g, int nat, const double *__restrict__ Z, const ff::cf2 *__restrict__ pxT,
+                          const ff::cf2 *__restrict__ pyT, const ff::cf2 *__restrict__ pzd,
+                          double2 *__restrict__ vext)
+{
+    const int ix = blockIdx.x / g.ny, iy = blockIdx.x - ix * g.ny;
+    const bool rnyq = (2 * ix == g.nx) || (2 * iy == g.ny);
+    double2 sa[2], sb[2];
+    row_sf_dd<true>(g, nat, Z, pxT, pyT, pzd, ix, iy, sa, sb);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
         const int kz = threadIdx.x + h * blockDim.x;
         if (kz >= g.K) continue;
         Hk k = hk_at(g, ix, iy, kz);
         const size_t q = (size_t)blockIdx.x * g.K + kz;
-        const double2 s1 = make_double2(ff::to_double(acc[h].x), ff::to_double(acc[h].y));
-        const double2 s2 = make_double2(ff::to_double(acc2[h].x), ff::to_double(acc2[h].y));
+        const double2 s1 = sa[h], s2 = sb[h];
         if (g.tri) {
             const double2 a1 = s1, a2 = (rnyq || k.nz_) ? s2 : s1;
             const double w1 = lpp_w(g, k.g2), w2 = lpp_w(g, k.g2p);
@@ -784,6 +816,19 @@ __global__ void k_vext_dd(GridInfo g, int nat, const double *__restrict__ Z, con
             vext[(size_t)g.NH + q] = make_double2(wp * v.x, wp * v.y);
         }
     }
+}
+
+// Hartree and LPP stress sums as k_gstress, with the structure factor in
+// double-float (row_sf_dd; no partner column at kz = nz/2, as there).
+__global__ void k_gstress_dd(GridInfo g, int nat, const double *__restrict__ Z, const ff::cf2 *__restrict__ pxT,
+                             const ff::cf2 *__restrict__ pyT, const ff::cf2 *__restrict__ pzd,
+                             const double2 *__restrict__ nG, double *__restrict__ part)
+{
+    const int ix = blockIdx.x / g.ny, iy = blockIdx.x - ix * g.ny;
+    const bool rnyq = (2 * ix == g.nx) || (2 * iy == g.ny);
+    double2 s1[2], s2[2];
+    row_sf_dd<false>(g, nat, Z, pxT, pyT, pzd, ix, iy, s1, s2);
+    gstress_row(g, ix, iy, rnyq, s1, s2, nG, part);
 }
 
 // cn(G) = -Omega w_k w(G) conj(n(G)) as a double-float pair (w included in
@@ -1345,11 +1390,15 @@ int launch_ewald_recip(int nat, const double *R, const double *Z, int nG, const 
 }
 
 int launch_gstress(const GridInfo &g, int nat, const double *Z, const double2 *px, const double2 *py,
-                   const double2 *pz, const double2 *nG, double *part, cudaStream_t st)
+                   const double2 *pz, const PhaseTablesDD *dd, const double2 *nG, double *part, cudaStream_t st)
 {
     int th = 32 * ((g.K + 31) / 32);
     if (th > 128) th = 32 * ((((g.K + 1) / 2) + 31) / 32);    // two columns per thread
-    k_gstress<<<g.nx * g.ny, th, 0, st>>>(g, nat, Z, px, py, pz, nG, part);
+    if (dd && g.dd)
+        k_gstress_dd<<<g.nx * g.ny, th, 0, st>>>(g, nat, Z, (const ff::cf2 *)dd->xT, (const ff::cf2 *)dd->yT,
+                                                  (const ff::cf2 *)dd->zd, nG, part);
+    else
+        k_gstress<<<g.nx * g.ny, th, 0, st>>>(g, nat, Z, px, py, pz, nG, part);
     return g.nx * g.ny;
 }
 
