@@ -31,6 +31,19 @@ def test_footprint_grows_with_grid_and_precision():
         ofdft.ofdft_footprint((31, 32, 32), 8, "fp64")
 
 
+def test_footprint_counts_the_per_ion_tables():
+    """Per ion a context holds its axis phase tables (binary64, nx + ny +
+    nz/2 + 1 complex values) and their double-float copies (x, y and z
+    ions-fastest, z per ion), plus force partials: growing the ion count
+    at fixed grid grows the footprint by at least that much."""
+    nx, ny, nz = 96, 96, 96
+    K = nz // 2 + 1
+    a = ofdft.ofdft_footprint((nx, ny, nz), 128, "fp64")
+    b = ofdft.ofdft_footprint((nx, ny, nz), 1024, "fp64")
+    tables = (1024 - 128) * (2 * nx + 2 * ny + 3 * K) * 16
+    assert b - a >= tables
+
+
 def test_admission_order_budget_and_slots():
     small = ofdft.ofdft_footprint((32, 32, 32), 8, "fp64")
     big = ofdft.ofdft_footprint((64, 64, 64), 8, "fp64")
