@@ -46,7 +46,8 @@ typedef enum {
     OFDFT_ENUMERIC = -4,  /* NaN/Inf or non-positive density met */
     OFDFT_ETIMEOUT = -5,  /* reserved: a bounded device wait ran out */
     OFDFT_EDEVICE = -6,   /* CUDA error (message in ofdft_last_error) */
-    OFDFT_EBUSY = -7      /* work still in flight (ofdft_minimize_query, ofdft_serve_poll) */
+    OFDFT_EBUSY = -7,     /* work still in flight (ofdft_minimize_query, ofdft_serve_poll) */
+    OFDFT_ECANCELED = -8  /* a served request cancelled by ofdft_serve_cancel */
 } ofdft_status;
 
 /* Non-interacting free-energy functional (Table I keywords, Sec. III). */
@@ -467,7 +468,8 @@ typedef struct {
     int device;               /* CUDA device ordinal */
     int max_slots;            /* requests running at once (worker threads), >= 1 */
     double hbm_budget_bytes;  /* admission budget; <= 0: 90% of the device memory free at start */
-    int dry_run;              /* 1: no device work, each request sleeps dry_run_ms (host tests) */
+    int dry_run;              /* 1: no device work, each request sleeps dry_run_ms in md_steps + 1
+                                 equal parts (host tests) */
     double dry_run_ms;
     int max_bypass;           /* >= 0: how many later requests may be admitted ahead of a queued
                                  request that does not fit yet (0: strict arrival order) */
@@ -498,7 +500,8 @@ typedef struct {
     double P_mean;            /* mean pressure over the MD steps (or the single point) */
     int steps_done;           /* MD steps completed (0 if the initial minimisation failed) */
     long long evaluations;    /* energy+potential evaluations, all steps */
-    double t_submit, t_admit, t_done;   /* seconds on the server clock */
+    double t_submit, t_admit, t_done;   /* seconds on the server clock (t_admit -1 for a
+                                           request cancelled while queued) */
     double footprint_bytes;
 } ofdft_result;
 
@@ -509,6 +512,14 @@ ofdft_status ofdft_serve_submit(ofdft_server *s, const ofdft_request *r, long lo
 /* OFDFT_OK and *res filled once request id has finished, OFDFT_EBUSY while
  * it is queued or running, OFDFT_EINVAL for an unknown id. */
 ofdft_status ofdft_serve_poll(ofdft_server *s, long long id, ofdft_result *res);
+/* Cancel request id.  A queued request is removed at once and finishes with
+ * status OFDFT_ECANCELED and no steps; a running one stops before its next
+ * MD step (the initial minimisation or a step already started runs to its
+ * end) and finishes with OFDFT_ECANCELED, the steps it completed, and the
+ * energy and mean pressure of those.  OFDFT_OK also for a request that has
+ * already finished (its result is unchanged); OFDFT_EINVAL for an unknown
+ * id. */
+ofdft_status ofdft_serve_cancel(ofdft_server *s, long long id);
 /* Block until every submitted request has finished (timeout_s <= 0: no limit;
  * OFDFT_ETIMEOUT when it runs out). */
 ofdft_status ofdft_serve_drain(ofdft_server *s, double timeout_s);

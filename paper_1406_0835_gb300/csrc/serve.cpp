@@ -11,6 +11,7 @@
 // Contexts share nothing, which makes each result independent of the mix.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -33,6 +34,7 @@ struct Pending {
     double footprint;
     double t_submit;
     int bypassed = 0;     // later requests admitted ahead of this one
+    std::atomic<bool> cancel{false};   // set by ofdft_serve_cancel while it runs
 };
 
 }  // namespace
@@ -45,6 +47,7 @@ struct ofdft_server {
     std::condition_variable cv;
     std::deque<Pending *> queue;
     std::map<long long, ofdft_result> done;
+    std::map<long long, Pending *> active;   // admitted and running
     long long next_id = 1, submitted = 0, finished = 0;
     int running = 0, peak_running = 0;
     double used = 0.0, peak_used = 0.0;
@@ -69,9 +72,17 @@ ofdft_result run_request(ofdft_server *s, Pending *q)
     res.t_submit = q->t_submit;
     const ofdft_request &r = q->r;
     if (s->p.dry_run) {
-        std::this_thread::sleep_for(std::chrono::duration<double, std::milli>(s->p.dry_run_ms));
+        // the initial minimisation and each step take an equal share
+        const double part_ms = s->p.dry_run_ms / (r.md_steps + 1);
         res.status = OFDFT_OK;
-        res.steps_done = r.md_steps;
+        for (int k = 0; k <= r.md_steps; ++k) {
+            if (k > 0 && q->cancel.load()) {
+                res.status = OFDFT_ECANCELED;
+                break;
+            }
+            std::this_thread::sleep_for(std::chrono::duration<double, std::milli>(part_ms));
+            if (k > 0) res.steps_done = k;
+        }
         return res;
     }
     ofdft_params pr;
@@ -103,6 +114,10 @@ ofdft_result run_request(ofdft_server *s, Pending *q)
     double psum = 0.0;
     int done = 0;         // MD steps completed (0 when the initial minimisation failed)
     while (st == OFDFT_OK && done < r.md_steps) {
+        if (q->cancel.load()) {
+            st = OFDFT_ECANCELED;
+            break;
+        }
         st = ofdft_md_step(c, &mp, 1, nullptr, nullptr, nullptr, &E, &stats);
         res.evaluations += stats.evaluations;
         if (st == OFDFT_OK) {
@@ -151,10 +166,12 @@ void worker(ofdft_server *s)
         if (s->used > s->peak_used) s->peak_used = s->used;
         if (s->running > s->peak_running) s->peak_running = s->running;
         const double t_admit = s->now();
+        s->active[q->id] = q;
         lk.unlock();
         ofdft_result res = run_request(s, q);
         res.t_admit = t_admit;
         lk.lock();
+        s->active.erase(q->id);
         res.t_done = s->now();
         s->used -= q->footprint;
         s->running -= 1;
@@ -234,6 +251,36 @@ ofdft_status ofdft_serve_poll(ofdft_server *s, long long id, ofdft_result *res)
         return OFDFT_OK;
     }
     return (id >= 1 && id < s->next_id) ? OFDFT_EBUSY : OFDFT_EINVAL;
+}
+
+ofdft_status ofdft_serve_cancel(ofdft_server *s, long long id)
+{
+    if (!s) return OFDFT_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        Pending *q = *it;
+        if (q->id != id) continue;
+        s->queue.erase(it);
+        ofdft_result res;
+        std::memset(&res, 0, sizeof(res));
+        res.id = id;
+        res.status = OFDFT_ECANCELED;
+        res.t_submit = q->t_submit;
+        res.t_admit = -1.0;          // never admitted
+        res.t_done = s->now();
+        res.footprint_bytes = q->footprint;
+        s->done[id] = res;
+        s->finished += 1;
+        delete q;
+        s->cv.notify_all();          // a request behind it may fit now
+        return OFDFT_OK;
+    }
+    auto a = s->active.find(id);
+    if (a != s->active.end()) {
+        a->second->cancel.store(true);
+        return OFDFT_OK;
+    }
+    return s->done.count(id) ? OFDFT_OK : OFDFT_EINVAL;
 }
 
 ofdft_status ofdft_serve_drain(ofdft_server *s, double timeout_s)

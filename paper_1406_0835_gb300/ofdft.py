@@ -17,7 +17,8 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 POINTWISE = {"f32x2": 0, "f64": 1}
 LPP = {"gauss": 0, "ha": 1}
 STATUS = {0: "OFDFT_OK", -1: "OFDFT_EINVAL", -2: "OFDFT_ENOMEM", -3: "OFDFT_ENOCONV",
-          -4: "OFDFT_ENUMERIC", -5: "OFDFT_ETIMEOUT", -6: "OFDFT_EDEVICE", -7: "OFDFT_EBUSY"}
+          -4: "OFDFT_ENUMERIC", -5: "OFDFT_ETIMEOUT", -6: "OFDFT_EDEVICE", -7: "OFDFT_EBUSY",
+          -8: "OFDFT_ECANCELED"}
 
 _P = ctypes.POINTER(ctypes.c_double)
 
@@ -147,6 +148,7 @@ SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_longlong)]),
     "ofdft_serve_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.POINTER(Result)]),
     "ofdft_serve_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "ofdft_serve_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     "ofdft_serve_clock": (ctypes.c_double, [ctypes.c_void_p]),
     "ofdft_serve_peaks": (ctypes.c_int, [ctypes.c_void_p, _P, ctypes.POINTER(ctypes.c_int)]),
     "ofdft_serve_stop": (ctypes.c_int, [ctypes.c_void_p]),
@@ -610,6 +612,13 @@ class Server:
         if st != 0:
             raise OfdftError(st, "ofdft_serve_poll failed")
         return res.as_dict()
+
+    def cancel(self, rid):
+        """Cancel request rid (queued: removed; running: stops before its
+        next MD step); its result then carries status OFDFT_ECANCELED."""
+        st = load().ofdft_serve_cancel(self.h, int(rid))
+        if st != 0:
+            raise OfdftError(st, "ofdft_serve_cancel")
 
     def drain(self, timeout_s=0.0):
         st = load().ofdft_serve_drain(self.h, float(timeout_s))

@@ -107,3 +107,38 @@ def test_dry_run_needs_a_budget():
         ofdft.Server(max_slots=1, hbm_budget_bytes=0.0, dry_run_ms=1)
     with pytest.raises(ofdft.OfdftError):
         ofdft.Server(max_slots=1, hbm_budget_bytes=1e9, dry_run_ms=1, max_bypass=-1)
+
+
+def _req_steps(server, grid, md_steps, nat=8):
+    ions = np.random.default_rng(nat).uniform(0, 5.0, (nat, 3))
+    return server.submit((5.0, 5.0, 5.0), grid, ions, np.ones(nat), 1e5, "vt84f", "fp64", md_steps=md_steps)
+
+
+def test_cancel_queued_running_finished_and_unknown_requests():
+    """A queued request cancels at once (status OFDFT_ECANCELED, no steps,
+    never admitted) and frees its place for the one behind it; a running
+    one stops before its next MD step with the steps it completed; a
+    finished one keeps its result; an unknown id is an error."""
+    small = ofdft.ofdft_footprint((32, 32, 32), 8, "fp64")
+    with ofdft.Server(max_slots=1, hbm_budget_bytes=4 * small, dry_run_ms=400, max_bypass=0) as s:
+        run = _req_steps(s, (32, 32, 32), 10)       # admitted at once: 11 parts of ~36 ms
+        queued = _req_steps(s, (32, 32, 32), 2)     # waits for the only slot
+        after = _req_steps(s, (32, 32, 32), 0)
+        t0 = s.clock()
+        while s.clock() - t0 < 0.12:                 # let the first run a few of its steps
+            pass
+        s.cancel(queued)
+        r_q = s.poll(queued)
+        assert r_q is not None and r_q["status"] == -8 and r_q["steps_done"] == 0 and r_q["t_admit"] == -1.0
+        s.cancel(run)
+        s.drain(timeout_s=30.0)
+        r_run, r_after = s.poll(run), s.poll(after)
+        s.cancel(after)                              # finished: no effect
+        assert s.poll(after) == r_after
+        with pytest.raises(ofdft.OfdftError) as e:
+            s.cancel(10 ** 9)
+        assert e.value.status == -1
+    assert r_run["status"] == -8 and 1 <= r_run["steps_done"] < 10
+    assert r_run["t_done"] - r_run["t_admit"] < 0.35     # stopped well before its 400 ms
+    assert r_after["status"] == 0
+    assert r_after["t_admit"] >= r_run["t_done"] - 1e-3   # the cancelled queued one did not hold the slot
