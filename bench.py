@@ -28,13 +28,13 @@ sys.path.insert(0, ROOT)
 
 # Energy + potential evaluations per step of the FP64 CG (the same
 # algorithm, decision for decision, in the oracle and on the GPU), as the GPU
-# arm of this script measures them on each workload (its evals_per_step: 622
-# per MD step of md-vt84f-96 in the driver's 20-step run, 334 for md-sga-96,
-# 548 per solve of solve-vt84f-128).  The reference arm runs without the
+# arm of this script measures them on each workload (its evals_per_step:
+# 632-636 per MD step of md-vt84f-96 in its recent runs, 334 for md-sga-96,
+# 550 per solve of solve-vt84f-128).  The reference arm runs without the
 # GPU path, so it converts the oracle's measured evaluations/s with these;
 # mixed workloads use the FP64 count, since the oracle is FP64 throughout.
-EVALS_PER_STEP = {"md-vt84f-96": 622.0, "md-sga-96": 334.0, "md-vt84f-96-mixed": 622.0,
-                  "solve-vt84f-128": 548.0, "solve-vt84f-128-mixed": 548.0, "eval-vt84f-128": 1.0}
+EVALS_PER_STEP = {"md-vt84f-96": 634.0, "md-sga-96": 334.0, "md-vt84f-96-mixed": 634.0,
+                  "solve-vt84f-128": 550.0, "solve-vt84f-128-mixed": 550.0, "eval-vt84f-128": 1.0}
 
 # Arithmetic of each precision form.  FP64 contexts keep every field in
 # binary64 in HBM and compute FFTs, G-space terms and the pointwise
